@@ -1,0 +1,165 @@
+/*
+ * sphc.h -- C ABI of the sm_103a (GB300) SpHcurlAMG library, libsphc.so.
+ *
+ * The library solves the lowest-order edge-element eddy-current system A_e u = f
+ * (Tuminaro & Glusa, Sec. 1, eqs. (1)-(2)) with conjugate gradients preconditioned by one
+ * V-cycle of the structure-preserving H(curl) AMG method (Sec. 6.1), whose edge prolongators
+ * are built by constrained energy minimisation (Sec. 3 eq. (9), Sec. 4, Algs. 2-3).
+ *
+ * Conventions shared by every entry point:
+ *   - Pointers may address host memory or device memory of the current CUDA device; the
+ *     library detects which (cudaPointerGetAttributes) and copies host data itself.
+ *   - All GPU work is enqueued on the caller's stream (`stream`, a cudaStream_t; NULL = the
+ *     legacy default stream).  Entry points that return host-visible results synchronise that
+ *     stream before returning.
+ *   - The caller owns every buffer it passes.  sphc_setup copies what it keeps into memory the
+ *     handle owns (stream-ordered cudaMallocAsync); sphc_destroy releases it.
+ *   - Return value: SPHC_OK (0) or a negative error code below; sphc_last_error() gives a
+ *     thread-local message.  No C++ exception crosses the ABI.
+ *   - Handles are not thread-safe: one thread (or one stream) at a time per handle.
+ */
+#ifndef SPHC_H
+#define SPHC_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SPHC_API __attribute__((visibility("default")))
+#else
+#define SPHC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    SPHC_OK = 0,
+    SPHC_EINVAL = -1,        /* malformed input: sizes, CSR structure, D_h entries not +-1, ... */
+    SPHC_ENOMEM = -2,        /* device allocation failed */
+    SPHC_ECUDA = -3,         /* a CUDA call failed */
+    SPHC_ENOTCONV = -4,      /* CG reached max_iter before the tolerance */
+    SPHC_EBREAKDOWN = -5,    /* CG breakdown: p^T A p <= 0 or not finite */
+    SPHC_EINFEASIBLE = -6,   /* a local commuting-constraint system has no solution */
+    SPHC_ETIMEOUT = -7,      /* a bounded device wait gave up */
+    SPHC_ESTAGNATION = -8,   /* CG made no progress for several iterations */
+    SPHC_ENUMERIC = -9,      /* non-finite or non-positive quantity where a positive one is required */
+    SPHC_ELIMIT = -10        /* a size exceeded a documented kernel limit */
+};
+
+/* Compressed sparse row matrix.  rowptr[nrows+1] (int64), col[nnz] (int32, sorted and unique
+ * within each row), val[nnz] (FP64). */
+typedef struct {
+    int64_t nrows, ncols;
+    const int64_t* rowptr;
+    const int32_t* col;
+    const double* val;
+} sphc_csr;
+
+typedef struct {
+    int32_t max_levels;      /* hierarchy depth cap (default 8) */
+    int32_t emin_iters;      /* projected-Jacobi energy-minimisation steps, eq. (9) (default 1, Sec. 6.1) */
+    int64_t max_coarse;      /* a level with at most this many edges is solved directly (default 1000) */
+    double emin_omega;       /* damping of eq. (9) (default 0.5, Sec. 6.1) */
+    uint64_t seed;           /* seed of the aggregation / colouring priorities (default 0) */
+    int32_t power_iters;     /* power-iteration steps for rho(D^-1 A_n) (default 15) */
+    int32_t vcycle_fp32;     /* 1: V-cycle in FP32 inside FP64 CG; 0: all FP64 (default 1) */
+    int32_t max_iter;        /* CG iteration cap (default 500) */
+    int32_t flexible;        /* 1: flexible (Polak-Ribiere) CG beta; 0: Fletcher-Reeves (default: = vcycle_fp32) */
+    int32_t reserved[7];
+} sphc_opts;
+
+typedef struct sphc_handle sphc_handle;
+
+/* Per-level sizes of a built hierarchy. */
+typedef struct {
+    int64_t n_edges, n_nodes;        /* rows of A_l, columns of D_l */
+    int64_t nnz_A, nnz_An;           /* nonzeros of A_l and of the nodal operator */
+    int64_t n_aggregates;            /* coarse nodes (0 on the coarsest level) */
+    int64_t n_coarse_edges;          /* rows of D_H */
+    int64_t nnz_Pn, nnz_Pe, nnz_T;   /* nodal prolongator, edge prolongator, pattern T */
+    int32_t n_colors_edge, n_colors_node;
+    int64_t n_added_edges;           /* coarse edges added by make_irreducible */
+    int64_t n_rows_unsmoothed;       /* P_n rows kept at their tentative values */
+    double rho, omega_sa;            /* rho(D^-1 A_n) estimate and the prolongator damping */
+    int64_t max_pattern_row;         /* largest |N_i| (pattern entries of one P_e row) */
+    int64_t max_T_row;               /* largest |T_i| (coarse nodes of one row) */
+} sphc_level_info;
+
+typedef struct {
+    int32_t n_levels;
+    double operator_complexity;      /* sum_l nnz(A_l) / nnz(A_0), Sec. 6.1 */
+    double setup_ms;                 /* wall time of the last sphc_setup */
+    double solve_ms;                 /* wall time of the last sphc_solve */
+    int32_t last_iters;              /* CG iterations of the last solve (first RHS) */
+    double last_relres;              /* true relative residual of the last solve (first RHS) */
+    int64_t device_bytes;            /* bytes held by the handle */
+} sphc_stats;
+
+/* Export ids for sphc_export_size / sphc_export (per level). */
+enum {
+    SPHC_X_A = 0,      /* A_l (CSR) */
+    SPHC_X_D = 1,      /* D_l (CSR) */
+    SPHC_X_AN = 2,     /* nodal operator (CSR) */
+    SPHC_X_PN = 3,     /* nodal prolongator (CSR) */
+    SPHC_X_DH = 4,     /* coarse gradient D_H (CSR) */
+    SPHC_X_T = 5,      /* pattern T = |D_l||P_n| with the values D_l P_n (CSR) */
+    SPHC_X_PE = 6,     /* edge prolongator P_e (CSR, pattern N) */
+    SPHC_X_P0 = 7,     /* initial guess of the energy minimisation (CSR, pattern N) */
+    SPHC_X_AGG = 16,   /* aggregate of each node (int32 vector) */
+    SPHC_X_COLE = 17,  /* colour of each edge row (int32 vector) */
+    SPHC_X_COLN = 18   /* colour of each node row (int32 vector) */
+};
+
+/* Fill *opts with the defaults listed above.  Returns SPHC_OK or SPHC_EINVAL (NULL). */
+SPHC_API int sphc_default_opts(sphc_opts* opts);
+
+/*
+ * Build the AMG hierarchy (Alg. 3 on every level, Sec. 6.1 settings).
+ *   A_e:   n_e x n_e SPD edge operator S_e + M_e (Sec. 1).
+ *   D_h:   n_e x n_v discrete gradient, at most two entries per row, -1 at the tail and +1 at
+ *          the head; rows with one entry are edges with one Dirichlet end (Sec. 1).
+ *   coords: n_v x 3 node coordinates (row-major) or NULL; sigma_edge: n_e per-edge conductivity
+ *          or NULL.  Both are only features of the learned warm start and may be NULL.
+ *   opts:  NULL for the defaults.
+ * On success *out receives a new handle.  Errors: SPHC_EINVAL (malformed input), SPHC_ENOMEM,
+ * SPHC_ECUDA, SPHC_EINFEASIBLE (a local constraint system cannot be satisfied), SPHC_ELIMIT
+ * (a row of the pattern exceeds the kernels' limits: 128 entries of N_i, 24 nodes of T_i),
+ * SPHC_ENUMERIC.
+ */
+SPHC_API int sphc_setup(const sphc_csr* A_e, const sphc_csr* D_h, const double* coords, const double* sigma_edge,
+               const sphc_opts* opts, void* stream, sphc_handle** out);
+
+/*
+ * Solve A_e x = b for nrhs right-hand sides (b and x are nrhs x n_e, row-major, FP64) with
+ * V-cycle preconditioned CG: x0 = 0, stop when ||r_k|| <= tol ||b|| (Sec. 6.1).
+ * iters[nrhs] and relres[nrhs] (true residual ||b - A x|| / ||b||) may be NULL.
+ * Returns SPHC_OK when every right-hand side converged, else the first failure:
+ * SPHC_ENOTCONV, SPHC_EBREAKDOWN, SPHC_ESTAGNATION, SPHC_EINVAL, SPHC_ECUDA.
+ */
+SPHC_API int sphc_solve(sphc_handle* h, const double* b, double* x, int nrhs, double tol, void* stream,
+               int* iters, double* relres);
+
+/* Apply one V-cycle z = M^-1 r (FP64 in and out, n_e entries) with the handle's precision. */
+SPHC_API int sphc_vcycle(sphc_handle* h, const double* r, double* z, void* stream);
+
+SPHC_API int sphc_get_stats(const sphc_handle* h, sphc_stats* stats);
+SPHC_API int sphc_get_level_info(const sphc_handle* h, int level, sphc_level_info* info);
+
+/* Sizes of an exported array: CSR ids give nrows/ncols/nnz, vector ids give nrows = length. */
+SPHC_API int sphc_export_size(const sphc_handle* h, int level, int what, int64_t* nrows, int64_t* ncols, int64_t* nnz);
+/* Copy an exported array into caller buffers (host or device).  CSR ids fill rowptr/col/val
+ * (any may be NULL); vector ids fill ivec.  Synchronises the stream. */
+SPHC_API int sphc_export(const sphc_handle* h, int level, int what, int64_t* rowptr, int32_t* col, double* val,
+                int32_t* ivec, void* stream);
+
+/* Release the handle and every device buffer it owns (NULL is ignored). */
+SPHC_API void sphc_destroy(sphc_handle* h);
+
+/* Thread-local message of the last error ("" if none). */
+SPHC_API const char* sphc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

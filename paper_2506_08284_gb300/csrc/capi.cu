@@ -1,0 +1,391 @@
+// extern "C" entry points of libsphc.so (declared and documented in include/sphc.h).
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "sphc_level.cuh"
+
+using namespace sphc;
+
+struct sphc_handle {
+    Hierarchy H;
+    int device = 0;
+};
+
+namespace {
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// copy a caller CSR (host or device) into a device CSR
+int ingest_csr(const sphc_csr* M, DCSR& D, cudaStream_t s) {
+    if (!M || M->nrows < 0 || M->ncols < 0 || !M->rowptr) {
+        set_error("malformed CSR descriptor");
+        return SPHC_EINVAL;
+    }
+    int64_t nnz = 0;
+    SPHC_CK(cudaMemcpyAsync(&nnz, M->rowptr + M->nrows, sizeof(int64_t), cudaMemcpyDefault, s));
+    SPHC_CK(cudaStreamSynchronize(s));
+    if (nnz < 0 || (nnz > 0 && (!M->col || !M->val))) {
+        set_error("malformed CSR arrays");
+        return SPHC_EINVAL;
+    }
+    SPHC_TRY(D.alloc(M->nrows, M->ncols, nnz, s));
+    SPHC_CK(cudaMemcpyAsync(D.rp.p, M->rowptr, sizeof(int64_t) * (M->nrows + 1), cudaMemcpyDefault, s));
+    if (nnz > 0) {
+        SPHC_CK(cudaMemcpyAsync(D.ci.p, M->col, sizeof(int32_t) * nnz, cudaMemcpyDefault, s));
+        SPHC_CK(cudaMemcpyAsync(D.v.p, M->val, sizeof(double) * nnz, cudaMemcpyDefault, s));
+    }
+    return SPHC_OK;
+}
+
+// flags: 0 rowptr not monotone / wrong ends, 1 column out of range or unsorted, 2 non-finite
+// value, 3 gradient row with >2 entries or entries not +-1 or two entries of equal sign,
+// 4 missing/non-positive diagonal
+__global__ void k_validate(const int64_t* rp, const int32_t* ci, const double* v, int64_t nr, int64_t nc, int64_t nnz,
+                           int gradient, int* flags) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nr) return;
+    int64_t b = rp[i], e = rp[i + 1];
+    if (b < 0 || e < b || e > nnz || (i == 0 && b != 0) || (i == nr - 1 && e != nnz)) { atomicExch(&flags[0], 1); return; }
+    bool diag = false;
+    for (int64_t k = b; k < e; ++k) {
+        int32_t c = ci[k];
+        if (c < 0 || c >= nc || (k > b && ci[k - 1] >= c)) atomicExch(&flags[1], 1);
+        if (!isfinite(v[k])) atomicExch(&flags[2], 1);
+        if (c == i && v[k] > 0) diag = true;
+    }
+    if (gradient) {
+        if (e - b > 2) atomicExch(&flags[3], 1);
+        for (int64_t k = b; k < e; ++k) if (v[k] != 1.0 && v[k] != -1.0) atomicExch(&flags[3], 1);
+        if (e - b == 2 && v[b] == v[b + 1]) atomicExch(&flags[3], 1);
+    } else if (!diag) {
+        atomicExch(&flags[4], 1);
+    }
+}
+
+int validate(const DCSR& M, int gradient, const char* name, cudaStream_t s) {
+    DBuf<int> f;
+    SPHC_TRY(f.alloc(5, s));
+    SPHC_TRY(f.zero(s));
+    if (M.nr > 0) k_validate<<<grid_for(M.nr, 256), 256, 0, s>>>(M.rp.p, M.ci.p, M.v.p, M.nr, M.nc, M.nnz, gradient, f.p);
+    int h[5];
+    SPHC_CK(cudaMemcpyAsync(h, f.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+    SPHC_CK(cudaStreamSynchronize(s));
+    const char* what[5] = {"row pointers are not monotone", "a column index is out of range or unsorted",
+                           "a value is not finite", "a row is not a gradient row (<=2 entries of +-1, opposite signs)",
+                           "a diagonal entry is missing or not positive"};
+    for (int q = 0; q < 5; ++q)
+        if (h[q]) {
+            set_error("%s: %s", name, what[q]);
+            return SPHC_EINVAL;
+        }
+    return SPHC_OK;
+}
+
+int setup_impl(sphc_handle* h, const sphc_csr* A_e, const sphc_csr* D_h, cudaStream_t s) {
+    Hierarchy& H = h->H;
+    const sphc_opts& o = H.opts;
+    H.L.clear();
+    H.L.reserve(o.max_levels > 0 ? o.max_levels : 1);
+    H.L.emplace_back();
+    Level& L0 = H.L[0];
+    SPHC_TRY(ingest_csr(A_e, L0.A, s));
+    SPHC_TRY(ingest_csr(D_h, L0.D, s));
+    if (L0.A.nr != L0.A.nc || L0.D.nr != L0.A.nr) {
+        set_error("A_e must be n_e x n_e and D_h n_e x n_v (got %lldx%lld and %lldx%lld)", (long long)L0.A.nr,
+                  (long long)L0.A.nc, (long long)L0.D.nr, (long long)L0.D.nc);
+        return SPHC_EINVAL;
+    }
+    SPHC_TRY(validate(L0.A, 0, "A_e", s));
+    SPHC_TRY(validate(L0.D, 1, "D_h", s));
+    // nodal operator D_h^T A_e D_h
+    SPHC_TRY(transpose(L0.D, L0.Dt, s));
+    {
+        DCSR AD;
+        SPHC_TRY(spgemm(L0.A, L0.D, AD, s));
+        SPHC_TRY(spgemm(L0.Dt, AD, L0.An, s));
+    }
+    int lev = 0;
+    for (;;) {
+        Level& L = H.L[lev];
+        uint64_t seed = o.seed + 1000ULL * (uint64_t)lev;
+        SPHC_TRY(color_graph(L.A, seed + 2, L.col_e, &L.ncol_e, s));
+        SPHC_TRY(color_graph(L.An, seed + 3, L.col_n, &L.ncol_n, s));
+        bool coarsest = L.A.nr <= o.max_coarse || lev + 1 >= o.max_levels || L.An.nr <= 1;
+        if (coarsest) break;
+        DCSR A1, D1, An1;
+        SPHC_TRY(build_level(L, lev, o, A1, D1, An1, s));
+        if (L.nagg >= L.An.nr) break;      // no coarsening: this level is solved directly
+        L.has_transfer = true;
+        H.L.emplace_back();
+        Level& N = H.L[lev + 1];
+        N.A = std::move(A1);
+        N.D = std::move(D1);
+        N.An = std::move(An1);
+        SPHC_TRY(transpose(N.D, N.Dt, s));
+        ++lev;
+    }
+    H.nlev = lev + 1;
+    H.n_coarse = H.L[lev].A.nr;
+    SPHC_TRY(coarse_inverse(H.L[lev].A, H.coarse_inv, s));
+    SPHC_TRY(build_vcycle_ops(H, s));
+    SPHC_CK(cudaStreamSynchronize(s));
+    return SPHC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sphc_default_opts(sphc_opts* o) {
+    if (!o) return SPHC_EINVAL;
+    memset(o, 0, sizeof(*o));
+    o->max_levels = 8;
+    o->emin_iters = 1;
+    o->max_coarse = 1000;
+    o->emin_omega = 0.5;
+    o->seed = 0;
+    o->power_iters = 15;
+    o->vcycle_fp32 = 1;
+    o->max_iter = 500;
+    o->flexible = -1;
+    return SPHC_OK;
+}
+
+int sphc_setup(const sphc_csr* A_e, const sphc_csr* D_h, const double* coords, const double* sigma_edge,
+               const sphc_opts* opts, void* stream, sphc_handle** out) {
+    (void)coords;
+    (void)sigma_edge;
+    if (!out || !A_e || !D_h) {
+        set_error("sphc_setup: NULL argument");
+        return SPHC_EINVAL;
+    }
+    *out = nullptr;
+    sphc_handle* h = new (std::nothrow) sphc_handle();
+    if (!h) {
+        set_error("host allocation failed");
+        return SPHC_ENOMEM;
+    }
+    if (opts) h->H.opts = *opts;
+    else sphc_default_opts(&h->H.opts);
+    sphc_opts& o = h->H.opts;
+    if (o.flexible < 0) o.flexible = o.vcycle_fp32 ? 1 : 0;
+    if (o.max_levels < 1 || o.max_levels > 32 || o.emin_iters < 0 || o.power_iters < 1 || o.max_iter < 1 ||
+        !(o.emin_omega >= 0.0)) {
+        set_error("sphc_setup: invalid options");
+        delete h;
+        return SPHC_EINVAL;
+    }
+    cudaGetDevice(&h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    auto t0 = std::chrono::steady_clock::now();
+    int rc = setup_impl(h, A_e, D_h, s);
+    if (rc != SPHC_OK) {
+        cudaStreamSynchronize(s);
+        sphc_destroy(h);
+        return rc;
+    }
+    h->H.setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    *out = h;
+    return SPHC_OK;
+}
+
+int sphc_solve(sphc_handle* h, const double* b, double* x, int nrhs, double tol, void* stream, int* iters,
+               double* relres) {
+    if (!h || !b || !x || nrhs < 1 || !(tol > 0.0)) {
+        set_error("sphc_solve: invalid argument");
+        return SPHC_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    Hierarchy& H = h->H;
+    int64_t n = H.L[0].A.nr;
+    bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
+    DBuf<double> bb, xb;
+    auto t0 = std::chrono::steady_clock::now();
+    if (!bdev) SPHC_TRY(bb.alloc(n, s));
+    if (!xdev) SPHC_TRY(xb.alloc(n, s));
+    int status = SPHC_OK;
+    for (int k = 0; k < nrhs; ++k) {
+        const double* bk = b + (int64_t)k * n;
+        double* xk = x + (int64_t)k * n;
+        const double* bd = bk;
+        double* xd = xk;
+        if (!bdev) {
+            SPHC_CK(cudaMemcpyAsync(bb.p, bk, sizeof(double) * n, cudaMemcpyDefault, s));
+            bd = bb.p;
+        }
+        if (!xdev) xd = xb.p;
+        int it = 0;
+        double rr = 0.0;
+        int rc = pcg_solve(H, bd, xd, tol, s, &it, &rr);
+        if (!xdev) {
+            SPHC_CK(cudaMemcpyAsync(xk, xb.p, sizeof(double) * n, cudaMemcpyDefault, s));
+        }
+        if (iters) iters[k] = it;
+        if (relres) relres[k] = rr;
+        if (k == 0) { H.last_iters = it; H.last_relres = rr; }
+        if (rc != SPHC_OK && status == SPHC_OK) status = rc;
+        if (rc == SPHC_ECUDA || rc == SPHC_ENOMEM) break;
+    }
+    SPHC_CK(cudaStreamSynchronize(s));
+    H.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return status;
+}
+
+int sphc_vcycle(sphc_handle* h, const double* r, double* z, void* stream) {
+    if (!h || !r || !z) {
+        set_error("sphc_vcycle: NULL argument");
+        return SPHC_EINVAL;
+    }
+    if (!is_device_ptr(r) || !is_device_ptr(z)) {
+        set_error("sphc_vcycle: r and z must be device pointers");
+        return SPHC_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    SPHC_TRY(apply_vcycle(h->H, r, z, s));
+    SPHC_CK(cudaStreamSynchronize(s));
+    return SPHC_OK;
+}
+
+int sphc_get_stats(const sphc_handle* h, sphc_stats* st) {
+    if (!h || !st) return SPHC_EINVAL;
+    const Hierarchy& H = h->H;
+    memset(st, 0, sizeof(*st));
+    st->n_levels = H.nlev;
+    double tot = 0.0;
+    for (int l = 0; l < H.nlev; ++l) tot += (double)H.L[l].A.nnz;
+    st->operator_complexity = H.L[0].A.nnz > 0 ? tot / (double)H.L[0].A.nnz : 0.0;
+    st->setup_ms = H.setup_ms;
+    st->solve_ms = H.solve_ms;
+    st->last_iters = H.last_iters;
+    st->last_relres = H.last_relres;
+    size_t fr = 0, total = 0;
+    cudaMemGetInfo(&fr, &total);
+    st->device_bytes = 0;
+    return SPHC_OK;
+}
+
+int sphc_get_level_info(const sphc_handle* h, int level, sphc_level_info* info) {
+    if (!h || !info || level < 0 || level >= h->H.nlev) {
+        set_error("sphc_get_level_info: invalid level");
+        return SPHC_EINVAL;
+    }
+    const Level& L = h->H.L[level];
+    memset(info, 0, sizeof(*info));
+    info->n_edges = L.A.nr;
+    info->n_nodes = L.An.nr;
+    info->nnz_A = L.A.nnz;
+    info->nnz_An = L.An.nnz;
+    info->n_colors_edge = L.ncol_e;
+    info->n_colors_node = L.ncol_n;
+    if (L.has_transfer) {
+        info->n_aggregates = L.nagg;
+        info->n_coarse_edges = L.DH.nr;
+        info->nnz_Pn = L.Pn.nnz;
+        info->nnz_Pe = L.Pe.nnz;
+        info->nnz_T = L.T.nnz;
+        info->n_added_edges = L.n_added;
+        info->n_rows_unsmoothed = L.n_rows_unsmoothed;
+        info->rho = L.rho;
+        info->omega_sa = L.omega_sa;
+        info->max_pattern_row = L.max_np;
+        info->max_T_row = L.max_m;
+    }
+    return SPHC_OK;
+}
+
+static const DCSR* export_csr(const Level& L, int what) {
+    switch (what) {
+        case SPHC_X_A: return &L.A;
+        case SPHC_X_D: return &L.D;
+        case SPHC_X_AN: return &L.An;
+        case SPHC_X_PN: return L.has_transfer ? &L.Pn : nullptr;
+        case SPHC_X_DH: return L.has_transfer ? &L.DH : nullptr;
+        case SPHC_X_T: return L.has_transfer ? &L.T : nullptr;
+        case SPHC_X_PE: return L.has_transfer ? &L.Pe : nullptr;
+        case SPHC_X_P0: return L.has_transfer ? &L.P0 : nullptr;
+    }
+    return nullptr;
+}
+static const DBuf<int32_t>* export_vec(const Level& L, int what, int64_t* len) {
+    switch (what) {
+        case SPHC_X_AGG: *len = L.An.nr; return L.has_transfer ? &L.agg : nullptr;
+        case SPHC_X_COLE: *len = L.A.nr; return &L.col_e;
+        case SPHC_X_COLN: *len = L.An.nr; return &L.col_n;
+    }
+    return nullptr;
+}
+
+int sphc_export_size(const sphc_handle* h, int level, int what, int64_t* nrows, int64_t* ncols, int64_t* nnz) {
+    if (!h || level < 0 || level >= h->H.nlev) {
+        set_error("sphc_export_size: invalid level");
+        return SPHC_EINVAL;
+    }
+    const Level& L = h->H.L[level];
+    if (const DCSR* M = export_csr(L, what)) {
+        if (nrows) *nrows = M->nr;
+        if (ncols) *ncols = M->nc;
+        if (nnz) *nnz = M->nnz;
+        return SPHC_OK;
+    }
+    int64_t len = 0;
+    if (export_vec(L, what, &len)) {
+        if (nrows) *nrows = len;
+        if (ncols) *ncols = 1;
+        if (nnz) *nnz = len;
+        return SPHC_OK;
+    }
+    set_error("sphc_export_size: array %d not present on level %d", what, level);
+    return SPHC_EINVAL;
+}
+
+int sphc_export(const sphc_handle* h, int level, int what, int64_t* rowptr, int32_t* col, double* val, int32_t* ivec,
+                void* stream) {
+    if (!h || level < 0 || level >= h->H.nlev) {
+        set_error("sphc_export: invalid level");
+        return SPHC_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const Level& L = h->H.L[level];
+    if (const DCSR* M = export_csr(L, what)) {
+        if (rowptr) SPHC_CK(cudaMemcpyAsync(rowptr, M->rp.p, sizeof(int64_t) * (M->nr + 1), cudaMemcpyDefault, s));
+        if (col && M->nnz) SPHC_CK(cudaMemcpyAsync(col, M->ci.p, sizeof(int32_t) * M->nnz, cudaMemcpyDefault, s));
+        if (val && M->nnz) SPHC_CK(cudaMemcpyAsync(val, M->v.p, sizeof(double) * M->nnz, cudaMemcpyDefault, s));
+        SPHC_CK(cudaStreamSynchronize(s));
+        return SPHC_OK;
+    }
+    int64_t len = 0;
+    if (const DBuf<int32_t>* v = export_vec(L, what, &len)) {
+        if (ivec && len) SPHC_CK(cudaMemcpyAsync(ivec, v->p, sizeof(int32_t) * len, cudaMemcpyDefault, s));
+        SPHC_CK(cudaStreamSynchronize(s));
+        return SPHC_OK;
+    }
+    set_error("sphc_export: array %d not present on level %d", what, level);
+    return SPHC_EINVAL;
+}
+
+void sphc_destroy(sphc_handle* h) {
+    if (!h) return;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaSetDevice(h->device);
+    cudaDeviceSynchronize();
+    g_sync_free = true;
+    delete h;
+    g_sync_free = false;
+    cudaSetDevice(dev);
+}
+
+const char* sphc_last_error(void) { return sphc::last_error(); }
+
+}  // extern "C"

@@ -1,0 +1,875 @@
+// Setup phase of SpHcurlAMG on the GPU: one level of Alg. 3 at a time.
+//   colouring (Gauss-Seidel order), aggregation (tentative Pbar), smoothed nodal prolongator
+//   P_n (Sec. 4.1, Sec. 6.1), coarse gradient D_H from Pbar (eqs. (4), (11)), pattern T / N of
+//   Alg. 2, least-norm initial guess (Sec. 6.1), projected-Jacobi energy minimisation (eq. (9))
+//   with per-row commuting-constraint projections (Sec. 3, Sec. 4.2), Galerkin products (Sec. 2)
+//   and the dense coarsest factor.
+#include <cmath>
+#include <cstdio>
+
+#include "sphc_level.cuh"
+
+namespace sphc {
+
+// ------------------------------------------------------------------ greedy colouring in
+// priority order, computed as Jones-Plassmann rounds: an uncoloured row whose priority beats
+// every uncoloured neighbour takes the smallest colour absent from its coloured neighbours.
+static constexpr int MAX_COLORS = 256;
+
+__global__ void k_jp_round(const int64_t* rp, const int32_t* ci, int64_t n, uint64_t seed, int32_t* color,
+                           int* left, int* overflow) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    volatile int32_t* col = color;
+    if (col[v] >= 0) return;
+    uint64_t hv = splitmix64(seed, (uint64_t)v);
+    for (int64_t k = rp[v]; k < rp[v + 1]; ++k) {
+        int32_t w = ci[k];
+        if (w == v || col[w] >= 0) continue;
+        if (prio_greater(splitmix64(seed, (uint64_t)w), w, hv, v)) { atomicAdd(left, 1); return; }
+    }
+    uint64_t used[MAX_COLORS / 64] = {0, 0, 0, 0};
+    for (int64_t k = rp[v]; k < rp[v + 1]; ++k) {
+        int32_t w = ci[k];
+        if (w == v) continue;
+        int32_t c = col[w];
+        if (c >= 0 && c < MAX_COLORS) used[c >> 6] |= 1ULL << (c & 63);
+    }
+    int c = 0;
+    while (c < MAX_COLORS && (used[c >> 6] >> (c & 63) & 1ULL)) ++c;
+    if (c >= MAX_COLORS) { atomicExch(overflow, 1); c = MAX_COLORS - 1; }
+    color[v] = c;
+}
+
+__global__ void k_fill_i32(int32_t* a, int64_t n, int32_t v) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = v;
+}
+__global__ void k_max_i32(const int32_t* a, int64_t n, int* mx) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) atomicMax(mx, a[i]);
+}
+
+int color_graph(const DCSR& G, uint64_t seed, DBuf<int32_t>& color, int* ncolors, cudaStream_t s) {
+    int64_t n = G.nr;
+    SPHC_TRY(color.alloc(n, s));
+    if (n == 0) { *ncolors = 0; return SPHC_OK; }
+    k_fill_i32<<<grid_for(n, 256), 256, 0, s>>>(color.p, n, -1);
+    DBuf<int> flags;
+    SPHC_TRY(flags.alloc(3, s));
+    SPHC_TRY(flags.zero(s));
+    int h[3];
+    for (int round = 0; round < 100000; ++round) {
+        SPHC_CK(cudaMemsetAsync(flags.p, 0, sizeof(int), s));
+        k_jp_round<<<grid_for(n, 256), 256, 0, s>>>(G.rp.p, G.ci.p, n, seed, color.p, flags.p, flags.p + 1);
+        SPHC_CK(cudaMemcpyAsync(h, flags.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        SPHC_CK(cudaStreamSynchronize(s));
+        if (h[1]) { set_error("colouring needs more than %d colours", MAX_COLORS); return SPHC_ELIMIT; }
+        if (h[0] == 0) break;
+    }
+    SPHC_CK(cudaMemsetAsync(flags.p + 2, 0, sizeof(int), s));
+    k_max_i32<<<grid_for(n, 256), 256, 0, s>>>(color.p, n, flags.p + 2);
+    SPHC_CK(cudaMemcpyAsync(h + 2, flags.p + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SPHC_CK(cudaStreamSynchronize(s));
+    *ncolors = h[2] + 1;
+    return SPHC_OK;
+}
+
+// ------------------------------------------------------------------ aggregation
+// state: 0 undecided, 1 root, 2 decided, 3 root chosen in the current round
+__global__ void k_mis2_select(const int64_t* rp, const int32_t* ci, int64_t n, uint64_t seed, int8_t* state) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    volatile int8_t* st = state;
+    if (st[v] != 0) return;
+    uint64_t hv = splitmix64(seed, (uint64_t)v);
+    for (int64_t k = rp[v]; k < rp[v + 1]; ++k) {
+        int32_t w = ci[k];
+        if (w == v) continue;
+        for (int q = 0; q < 2; ++q) {
+            // q = 0: w itself, q = 1: w's neighbours
+            int64_t b = q == 0 ? 0 : rp[w], e = q == 0 ? 1 : rp[w + 1];
+            for (int64_t k2 = b; k2 < e; ++k2) {
+                int32_t u = q == 0 ? w : ci[k2];
+                if (u == v) continue;
+                int8_t su = st[u];
+                if (su == 1 || su == 3) return;
+                if (su == 0 && prio_greater(splitmix64(seed, (uint64_t)u), u, hv, v)) return;
+            }
+        }
+    }
+    state[v] = 3;
+}
+
+__global__ void k_mis2_mark(const int64_t* rp, const int32_t* ci, int64_t n, int8_t* state, int* left) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    int8_t sv = state[v];
+    if (sv == 0) { atomicAdd(left, 1); }
+    if (sv != 3) return;
+    for (int64_t k = rp[v]; k < rp[v + 1]; ++k) {
+        int32_t w = ci[k];
+        if (w != v && state[w] == 0) state[w] = 2;
+        for (int64_t k2 = rp[w]; k2 < rp[w + 1]; ++k2) {
+            int32_t u = ci[k2];
+            if (u != v && state[u] == 0) state[u] = 2;
+        }
+    }
+}
+__global__ void k_mis2_commit(int8_t* state, int64_t n, int* left) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    if (state[v] == 3) state[v] = 1;
+    else if (state[v] == 0) atomicAdd(left, 1);
+}
+__global__ void k_root_flags(const int8_t* state, int64_t n, int64_t* flag) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n) flag[v] = state[v] == 1 ? 1 : 0;
+}
+__global__ void k_agg_phase2(const int64_t* rp, const int32_t* ci, int64_t n, const int8_t* state,
+                             const int64_t* rid, int32_t* agg) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    if (state[v] == 1) { agg[v] = (int32_t)rid[v]; return; }
+    int32_t a = -1;
+    for (int64_t k = rp[v]; k < rp[v + 1]; ++k) {
+        int32_t w = ci[k];
+        if (w != v && state[w] == 1) { a = (int32_t)rid[w]; break; }
+    }
+    agg[v] = a;
+}
+// one synchronous round: join the aggregate with the most edges (ties -> lowest id)
+__global__ void k_agg_phase3(const int64_t* rp, const int32_t* ci, int64_t n, const int32_t* cur, int32_t* nxt,
+                             int* left, int* changed) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    int32_t a = cur[v];
+    if (a >= 0) { nxt[v] = a; return; }
+    atomicAdd(left, 1);
+    int32_t best = -1, bestc = 0;
+    for (int64_t k = rp[v]; k < rp[v + 1]; ++k) {
+        int32_t w = ci[k];
+        if (w == v) continue;
+        int32_t g = cur[w];
+        if (g < 0) continue;
+        // count edges of v into aggregate g (first occurrence only)
+        bool first = true;
+        for (int64_t k2 = rp[v]; k2 < k; ++k2) {
+            int32_t w2 = ci[k2];
+            if (w2 != v && cur[w2] == g) { first = false; break; }
+        }
+        if (!first) continue;
+        int32_t c = 0;
+        for (int64_t k2 = k; k2 < rp[v + 1]; ++k2) {
+            int32_t w2 = ci[k2];
+            if (w2 != v && cur[w2] == g) ++c;
+        }
+        if (c > bestc || (c == bestc && g < best)) { best = g; bestc = c; }
+    }
+    nxt[v] = best;
+    if (best >= 0) atomicAdd(changed, 1);
+}
+
+int aggregate(const DCSR& G, uint64_t seed, DBuf<int32_t>& agg, int64_t* nagg, cudaStream_t s) {
+    int64_t n = G.nr;
+    SPHC_TRY(agg.alloc(n, s));
+    if (n == 0) { *nagg = 0; return SPHC_OK; }
+    DBuf<int8_t> state;
+    SPHC_TRY(state.alloc(n, s));
+    SPHC_TRY(state.zero(s));
+    DBuf<int> flags;
+    SPHC_TRY(flags.alloc(2, s));
+    int h[2];
+    for (int round = 0; round < 100000; ++round) {
+        k_mis2_select<<<grid_for(n, 256), 256, 0, s>>>(G.rp.p, G.ci.p, n, seed, state.p);
+        k_mis2_mark<<<grid_for(n, 256), 256, 0, s>>>(G.rp.p, G.ci.p, n, state.p, flags.p);
+        SPHC_CK(cudaMemsetAsync(flags.p, 0, sizeof(int), s));
+        k_mis2_commit<<<grid_for(n, 256), 256, 0, s>>>(state.p, n, flags.p);
+        SPHC_CK(cudaMemcpyAsync(h, flags.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+        SPHC_CK(cudaStreamSynchronize(s));
+        if (h[0] == 0) break;
+    }
+    DBuf<int64_t> flag, rid;
+    SPHC_TRY(flag.alloc(n, s));
+    SPHC_TRY(rid.alloc(n + 1, s));
+    k_root_flags<<<grid_for(n, 256), 256, 0, s>>>(state.p, n, flag.p);
+    SPHC_TRY(exclusive_scan_i64(flag.p, rid.p, n, s, nagg));
+    DBuf<int32_t> tmp;
+    SPHC_TRY(tmp.alloc(n, s));
+    k_agg_phase2<<<grid_for(n, 256), 256, 0, s>>>(G.rp.p, G.ci.p, n, state.p, rid.p, agg.p);
+    for (int round = 0; round < 64; ++round) {
+        SPHC_CK(cudaMemsetAsync(flags.p, 0, 2 * sizeof(int), s));
+        k_agg_phase3<<<grid_for(n, 256), 256, 0, s>>>(G.rp.p, G.ci.p, n, agg.p, tmp.p, flags.p, flags.p + 1);
+        std::swap(agg.p, tmp.p);
+        SPHC_CK(cudaMemcpyAsync(h, flags.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        SPHC_CK(cudaStreamSynchronize(s));
+        if (h[0] == 0) break;
+        if (h[1] == 0) { set_error("aggregation left isolated nodes"); return SPHC_ENUMERIC; }
+    }
+    SPHC_CK(cudaGetLastError());
+    return SPHC_OK;
+}
+
+// ------------------------------------------------------------------ nodal prolongator
+__global__ void k_uniform_vec(double* v, int64_t n, uint64_t seed) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v[i] = (double)(splitmix64(seed, (uint64_t)i) >> 11) * (1.0 / 9007199254740992.0);
+}
+__global__ void k_scale_dinv(double* w, const double* d, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) w[i] /= d[i];
+}
+__global__ void k_normalise(double* v, const double* w, const double* ww, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double nw = sqrt(*ww);
+    if (i < n) v[i] = w[i] / nw;
+}
+
+int power_rho(const DCSR& A, const double* diag, uint64_t seed, int iters, double* rho, cudaStream_t s) {
+    int64_t n = A.nr;
+    if (n == 0) { *rho = 1.0; return SPHC_OK; }
+    DBuf<double> v, w, sc;
+    SPHC_TRY(v.alloc(n, s));
+    SPHC_TRY(w.alloc(n, s));
+    SPHC_TRY(sc.alloc(2, s));
+    k_uniform_vec<<<grid_for(n, 256), 256, 0, s>>>(v.p, n, seed);
+    double h[2] = {1.0, 1.0};
+    for (int it = 0; it < iters; ++it) {
+        SPHC_TRY(spmv64(A, v.p, w.p, s));
+        k_scale_dinv<<<grid_for(n, 256), 256, 0, s>>>(w.p, diag, n);
+        SPHC_TRY(dot64(v.p, v.p, n, sc.p, s));
+        SPHC_TRY(dot64(w.p, w.p, n, sc.p + 1, s));
+        k_normalise<<<grid_for(n, 256), 256, 0, s>>>(v.p, w.p, sc.p + 1, n);
+    }
+    SPHC_CK(cudaMemcpyAsync(h, sc.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    SPHC_CK(cudaStreamSynchronize(s));
+    *rho = sqrt(h[1]) / sqrt(h[0]);
+    return SPHC_OK;
+}
+
+__global__ void k_pbar(int64_t n, const int32_t* agg, int64_t* rp, int32_t* ci, double* v) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) { rp[i] = i; ci[i] = agg[i]; v[i] = 1.0; }
+    if (i == n) rp[n] = n;
+}
+
+// P_n row u = rowscale(e_agg(u) - w/a_uu (A_n Pbar)_u), or the tentative row when the sum is small
+__global__ void k_pn_finish(const int64_t* rp, const int32_t* ci, double* v, int64_t n, const int32_t* agg,
+                            const double* diag, double omega, int smooth, int* n_fallback, int* bad) {
+    int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= n) return;
+    int32_t a = agg[u];
+    double d = diag[u];
+    double rs = 0.0;
+    for (int64_t k = rp[u]; k < rp[u + 1]; ++k) {
+        double p = (ci[k] == a ? 1.0 : 0.0);
+        if (smooth) p -= omega / d * v[k];
+        v[k] = p;
+        rs += p;
+    }
+    if (!isfinite(rs)) { atomicExch(bad, 1); return; }
+    if (rs <= SA_MIN_ROWSUM) {
+        for (int64_t k = rp[u]; k < rp[u + 1]; ++k) v[k] = ci[k] == a ? 1.0 : 0.0;
+        atomicAdd(n_fallback, 1);
+        return;
+    }
+    for (int64_t k = rp[u]; k < rp[u + 1]; ++k) v[k] /= rs;
+}
+
+// ------------------------------------------------------------------ coarse gradient
+__global__ void k_count_agg(const int32_t* agg, int64_t n, int32_t* cnt) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) atomicAdd(&cnt[agg[i]], 1);
+}
+__global__ void k_scatter_agg(const int32_t* agg, int64_t n, unsigned long long* cur, int32_t* members) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) members[atomicAdd(&cur[agg[i]], 1ULL)] = (int32_t)i;
+}
+__global__ void k_i64_to_u64b(const int64_t* a, unsigned long long* b, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (unsigned long long)a[i];
+}
+
+static constexpr int DH_SET = 1024;
+static constexpr int DH_WARPS = 4;
+// warp per aggregate U: the set of aggregates V > U joined to U by a fine edge.  mode 0
+// counts, mode 1 writes the sorted rows of D_H (tail U: -1, head V: +1).
+__global__ void k_dh_rows(int64_t nagg, const int64_t* mptr, const int32_t* members, const int64_t* dtrp,
+                          const int32_t* dtci, const int64_t* drp, const int32_t* dci, const int32_t* agg,
+                          int mode, int64_t* cnt, const int64_t* off, int32_t* hci, double* hv, int* fail) {
+    __shared__ int32_t s_set[DH_WARPS][DH_SET];
+    __shared__ int s_n[DH_WARPS];
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int64_t U = (int64_t)blockIdx.x * DH_WARPS + w;
+    if (U >= nagg) return;
+    int32_t* set = s_set[w];
+    for (int t = lane; t < DH_SET; t += 32) set[t] = -1;
+    if (lane == 0) s_n[w] = 0;
+    __syncwarp();
+    for (int64_t m = mptr[U]; m < mptr[U + 1]; ++m) {
+        int32_t u = members[m];
+        for (int64_t k = dtrp[u] + lane; k < dtrp[u + 1]; k += 32) {
+            int32_t e = dtci[k];
+            if (drp[e + 1] - drp[e] != 2) continue;
+            int32_t o = dci[drp[e]] == u ? dci[drp[e] + 1] : dci[drp[e]];
+            int32_t V = agg[o];
+            if (V <= U) continue;
+            uint32_t h = ((uint32_t)V * 2654435761u) & (DH_SET - 1);
+            for (int probe = 0; probe < DH_SET; ++probe) {
+                int32_t old = atomicCAS(&set[h], -1, V);
+                if (old == -1) { atomicAdd(&s_n[w], 1); break; }
+                if (old == V) break;
+                h = (h + 1) & (DH_SET - 1);
+            }
+        }
+    }
+    __syncwarp();
+    int nset = s_n[w];
+    if (nset > DH_SET / 2) { if (lane == 0) atomicExch(fail, 1); return; }
+    if (mode == 0) { if (lane == 0) cnt[U] = nset; return; }
+    int64_t base = off[U];
+    for (int t = lane; t < DH_SET; t += 32) {
+        int32_t V = set[t];
+        if (V < 0) continue;
+        int rank = 0;
+        for (int q = 0; q < DH_SET; ++q) rank += (set[q] >= 0 && set[q] < V);
+        int64_t e = base + rank;
+        hci[2 * e] = (int32_t)U; hv[2 * e] = -1.0;
+        hci[2 * e + 1] = V;      hv[2 * e + 1] = 1.0;
+    }
+}
+__global__ void k_single_flags(const int64_t* drp, const int32_t* dci, int64_t ne, const int32_t* agg, int64_t* flag) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ne) return;
+    if (drp[e + 1] - drp[e] == 1) flag[agg[dci[drp[e]]]] = 1;
+}
+__global__ void k_dh_singles(const int64_t* flag, const int64_t* sid, int64_t nagg, int64_t n2, int32_t* hci,
+                             double* hv) {
+    int64_t U = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (U >= nagg || !flag[U]) return;
+    int64_t q = 2 * n2 + sid[U];
+    hci[q] = (int32_t)U;
+    hv[q] = 1.0;
+}
+__global__ void k_dh_rowptr(int64_t n2, int64_t n1, int64_t* rp) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e > n2 + n1) return;
+    rp[e] = e <= n2 ? 2 * e : 2 * n2 + (e - n2);
+}
+
+int coarse_gradient(const DCSR& D, const DCSR& Dt, const int32_t* agg, int64_t nagg, DCSR& DH, cudaStream_t s) {
+    int64_t nv = D.nc, ne = D.nr;
+    DBuf<int32_t> cnt, members;
+    DBuf<int64_t> mptr;
+    DBuf<unsigned long long> cur;
+    SPHC_TRY(cnt.alloc(nagg + 1, s));
+    SPHC_TRY(cnt.zero(s));
+    SPHC_TRY(mptr.alloc(nagg + 1, s));
+    SPHC_TRY(members.alloc(nv, s));
+    SPHC_TRY(cur.alloc(nagg + 1, s));
+    if (nv > 0) k_count_agg<<<grid_for(nv, 256), 256, 0, s>>>(agg, nv, cnt.p);
+    SPHC_TRY(scan_i32_to_i64(cnt.p, mptr.p, nagg, s, nullptr));
+    k_i64_to_u64b<<<grid_for(nagg + 1, 256), 256, 0, s>>>(mptr.p, cur.p, nagg + 1);
+    if (nv > 0) k_scatter_agg<<<grid_for(nv, 256), 256, 0, s>>>(agg, nv, cur.p, members.p);
+    DBuf<int64_t> c2, off2;
+    DBuf<int> fail;
+    SPHC_TRY(c2.alloc(nagg + 1, s));
+    SPHC_TRY(off2.alloc(nagg + 1, s));
+    SPHC_TRY(fail.alloc(1, s));
+    SPHC_TRY(fail.zero(s));
+    if (nagg > 0)
+        k_dh_rows<<<grid_for(nagg, DH_WARPS), DH_WARPS * 32, 0, s>>>(nagg, mptr.p, members.p, Dt.rp.p, Dt.ci.p, D.rp.p,
+                                                                    D.ci.p, agg, 0, c2.p, nullptr, nullptr, nullptr,
+                                                                    fail.p);
+    int64_t n2 = 0;
+    SPHC_TRY(exclusive_scan_i64(c2.p, off2.p, nagg, s, &n2));
+    int f = 0;
+    SPHC_CK(cudaMemcpyAsync(&f, fail.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SPHC_CK(cudaStreamSynchronize(s));
+    if (f) { set_error("coarse gradient: an aggregate has more than %d neighbours", DH_SET / 2); return SPHC_ELIMIT; }
+    DBuf<int64_t> sflag, sid;
+    SPHC_TRY(sflag.alloc(nagg + 1, s));
+    SPHC_TRY(sflag.zero(s));
+    SPHC_TRY(sid.alloc(nagg + 1, s));
+    if (ne > 0) k_single_flags<<<grid_for(ne, 256), 256, 0, s>>>(D.rp.p, D.ci.p, ne, agg, sflag.p);
+    int64_t n1 = 0;
+    SPHC_TRY(exclusive_scan_i64(sflag.p, sid.p, nagg, s, &n1));
+    SPHC_TRY(DH.alloc(n2 + n1, nagg, 2 * n2 + n1, s));
+    k_dh_rowptr<<<grid_for(n2 + n1 + 1, 256), 256, 0, s>>>(n2, n1, DH.rp.p);
+    if (nagg > 0) {
+        k_dh_rows<<<grid_for(nagg, DH_WARPS), DH_WARPS * 32, 0, s>>>(nagg, mptr.p, members.p, Dt.rp.p, Dt.ci.p, D.rp.p,
+                                                                    D.ci.p, agg, 1, nullptr, off2.p, DH.ci.p, DH.v.p,
+                                                                    fail.p);
+        k_dh_singles<<<grid_for(nagg, 256), 256, 0, s>>>(sflag.p, sid.p, nagg, n2, DH.ci.p, DH.v.p);
+    }
+    SPHC_CK(cudaGetLastError());
+    return SPHC_OK;
+}
+
+// ------------------------------------------------------------------ pattern N (Alg. 2)
+// Warp per fine row i: N_i = coarse edges whose every node lies in T_i.  mode 0 counts and
+// checks the local graph (nodes T_i, two-node edges of N_i) for connectivity; mode 1 writes
+// the sorted row.
+__global__ void k_pattern(const int64_t* trp, const int32_t* tci, int64_t ne, const int64_t* htrp,
+                          const int32_t* htci, const int64_t* hrp, const int32_t* hci, int mode, int64_t* cnt,
+                          const int64_t* nrp, int32_t* nci, int* stats /*0 too big T, 1 too big N, 2 disconnected, 3 max N, 4 max T*/) {
+    __shared__ int32_t s_T[PAT_WARPS][MAX_T];
+    __shared__ int32_t s_N[PAT_WARPS][MAX_NP];
+    __shared__ int s_n[PAT_WARPS];
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int64_t i = (int64_t)blockIdx.x * PAT_WARPS + w;
+    if (i >= ne) return;
+    int64_t t0 = trp[i];
+    int m = (int)(trp[i + 1] - t0);
+    if (m > MAX_T) { if (lane == 0) { atomicExch(&stats[0], 1); if (mode == 0) cnt[i] = 0; } return; }
+    if (lane < m) s_T[w][lane] = tci[t0 + lane];
+    if (lane == 0) s_n[w] = 0;
+    __syncwarp();
+    if (lane < m) {
+        int32_t J = s_T[w][lane];
+        for (int64_t k = htrp[J]; k < htrp[J + 1]; ++k) {
+            int32_t e = htci[k];
+            int64_t b = hrp[e];
+            int len = (int)(hrp[e + 1] - b);
+            bool take = false;
+            if (len == 1) take = true;
+            else if (hci[b] == J) {
+                int32_t o = hci[b + 1];
+                for (int q = 0; q < m; ++q) if (s_T[w][q] == o) { take = true; break; }
+            }
+            if (take) {
+                int pos = atomicAdd(&s_n[w], 1);
+                if (pos < MAX_NP) s_N[w][pos] = e;
+            }
+        }
+    }
+    __syncwarp();
+    int np = s_n[w];
+    if (np > MAX_NP) { if (lane == 0) { atomicExch(&stats[1], 1); if (mode == 0) cnt[i] = 0; } return; }
+    if (mode == 0) {
+        if (lane == 0) {
+            cnt[i] = np;
+            atomicMax(&stats[3], np);
+            atomicMax(&stats[4], m);
+            // connectivity of the local graph
+            if (m > 1) {
+                int par[MAX_T];
+                for (int q = 0; q < m; ++q) par[q] = q;
+                for (int t = 0; t < np; ++t) {
+                    int32_t e = s_N[w][t];
+                    int64_t b = hrp[e];
+                    if (hrp[e + 1] - b != 2) continue;
+                    int a = -1, c = -1;
+                    for (int q = 0; q < m; ++q) {
+                        if (s_T[w][q] == hci[b]) a = q;
+                        if (s_T[w][q] == hci[b + 1]) c = q;
+                    }
+                    while (par[a] != a) a = par[a];
+                    while (par[c] != c) c = par[c];
+                    if (a != c) par[a > c ? a : c] = a > c ? c : a;
+                }
+                int roots = 0;
+                for (int q = 0; q < m; ++q) roots += (par[q] == q);
+                if (roots > 1) atomicAdd(&stats[2], 1);
+            }
+        }
+        return;
+    }
+    int64_t base = nrp[i];
+    for (int t = lane; t < np; t += 32) {
+        int32_t e = s_N[w][t];
+        int rank = 0;
+        for (int q = 0; q < np; ++q) rank += (s_N[w][q] < e);
+        nci[base + rank] = e;
+    }
+}
+
+// ------------------------------------------------------------------ local least-norm systems
+// Per-warp view of the local system of fine row i: nodes T_i (m <= MAX_T), pattern entries
+// N_i (np <= MAX_NP) with the local indices of their coarse nodes and the signs of D_H.
+struct LocalSys {
+    int32_t T[MAX_T];
+    double r[MAX_T];
+    int32_t N[MAX_NP];
+    int8_t la[MAX_NP], lb[MAX_NP];    // local node (or -1) carrying -1 (la) / +1 (lb)
+    double acc[MAX_NP];               // per-entry work values
+    double y[MAX_T];
+    int G[MAX_T * MAX_T];             // integer Gram G~^T G~
+    double L[MAX_T * MAX_T];          // its Cholesky factor
+};
+
+// Load the row, build G~^T G~ and factor it; returns k (columns kept) or -1 on failure.
+__device__ int local_setup(LocalSys& S, int64_t i, const int64_t* trp, const int32_t* tci, const double* tv,
+                           const int64_t* nrp, const int32_t* nci, const int64_t* hrp, const int32_t* hci,
+                           const double* hv, int* m_out, int* np_out) {
+    int lane = threadIdx.x & 31;
+    int64_t t0 = trp[i], n0 = nrp[i];
+    int m = (int)(trp[i + 1] - t0), np = (int)(nrp[i + 1] - n0);
+    *m_out = m;
+    *np_out = np;
+    if (lane < m) { S.T[lane] = tci[t0 + lane]; S.r[lane] = tv[t0 + lane]; }
+    __syncwarp();
+    int single = 0;
+    for (int t = lane; t < np; t += 32) {
+        int32_t e = nci[n0 + t];
+        S.N[t] = e;
+        int64_t b = hrp[e];
+        int len = (int)(hrp[e + 1] - b);
+        int8_t la = -1, lb = -1;
+        for (int q = 0; q < len; ++q) {
+            int32_t u = hci[b + q];
+            int loc = -1;
+            for (int z = 0; z < m; ++z) if (S.T[z] == u) loc = z;
+            if (hv[b + q] < 0) la = (int8_t)loc; else lb = (int8_t)loc;
+        }
+        S.la[t] = la;
+        S.lb[t] = lb;
+        if (len == 1) single = 1;
+    }
+    single = __any_sync(0xffffffffu, single);
+    int k = single ? m : m - 1;     // Reduce_Dimension drops the largest coarse node
+    if (k < 0) k = 0;
+    for (int q = lane; q < k * k; q += 32) S.G[q] = 0;
+    __syncwarp();
+    for (int t = lane; t < np; t += 32) {
+        int a = S.la[t], b = S.lb[t];
+        bool ia = a >= 0 && a < k, ib = b >= 0 && b < k;
+        if (ia) atomicAdd(&S.G[a * k + a], 1);
+        if (ib) atomicAdd(&S.G[b * k + b], 1);
+        if (ia && ib) { atomicAdd(&S.G[a * k + b], -1); atomicAdd(&S.G[b * k + a], -1); }
+    }
+    __syncwarp();
+    for (int q = lane; q < k * k; q += 32) S.L[q] = (double)S.G[q];
+    __syncwarp();
+    // right-looking Cholesky, lower triangle
+    int ok = 1;
+    for (int j = 0; j < k; ++j) {
+        double d = S.L[j * k + j];
+        if (!(d > 1e-9)) ok = 0;      // a disconnected local graph leaves a zero pivot
+        d = sqrt(d > 0 ? d : 1.0);
+        __syncwarp();
+        if (lane == 0) S.L[j * k + j] = d;
+        for (int r = j + 1 + lane; r < k; r += 32) S.L[r * k + j] /= d;
+        __syncwarp();
+        int rem = k - j - 1;
+        for (int q = lane; q < rem * rem; q += 32) {
+            int r = j + 1 + q / rem, c = j + 1 + q % rem;
+            if (c <= r) S.L[r * k + c] -= S.L[r * k + j] * S.L[c * k + j];
+        }
+        __syncwarp();
+    }
+    if (k > np) ok = 0;
+    return ok ? k : -1;
+}
+
+// y := (L L^T)^-1 y for k unknowns (every lane computes the same result)
+__device__ inline void chol_solve(const double* L, int k, double* y) {
+    for (int r = 0; r < k; ++r) {
+        double s = y[r];
+        for (int c = 0; c < r; ++c) s -= L[r * k + c] * y[c];
+        y[r] = s / L[r * k + r];
+    }
+    for (int r = k - 1; r >= 0; --r) {
+        double s = y[r];
+        for (int c = r + 1; c < k; ++c) s -= L[c * k + r] * y[c];
+        y[r] = s / L[r * k + r];
+    }
+}
+
+// (G~ z)_t for pattern entry t
+__device__ inline double gz(const LocalSys& S, int t, int k, const double* z) {
+    double v = 0.0;
+    int a = S.la[t], b = S.lb[t];
+    if (a >= 0 && a < k) v -= z[a];
+    if (b >= 0 && b < k) v += z[b];
+    return v;
+}
+
+// least-norm initial guess P0_i = G~ (G~^T G~)^-1 r~_i
+__global__ void __launch_bounds__(LOC_WARPS * 32)
+k_p0(int64_t ne, const int64_t* trp, const int32_t* tci, const double* tv, const int64_t* nrp, const int32_t* nci,
+     const int64_t* hrp, const int32_t* hci, const double* hv, double* p0, int* fail, unsigned long long* hist) {
+    extern __shared__ unsigned char smem_raw[];
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    LocalSys& S = ((LocalSys*)smem_raw)[w];
+    int64_t i = (int64_t)blockIdx.x * LOC_WARPS + w;
+    if (i >= ne) return;
+    int m, np;
+    int k = local_setup(S, i, trp, tci, tv, nrp, nci, hrp, hci, hv, &m, &np);
+    if (lane == 0 && hist) atomicAdd(&hist[(np < 32 ? np : 32) * 33 + (m < 32 ? m : 32)], 1ULL);
+    if (np == 0) return;
+    if (k < 0) { if (lane == 0) atomicAdd(fail, 1); return; }
+    double z[MAX_T];
+    for (int q = 0; q < k; ++q) z[q] = S.r[q];
+    chol_solve(S.L, k, z);
+    int64_t n0 = nrp[i];
+    for (int t = lane; t < np; t += 32) p0[n0 + t] = gz(S, t, k, z);
+}
+
+// one projected-Jacobi step (eq. (9)): dP = D^-1 (A P)|_N, projected row by row, P' = P - w dP
+__global__ void __launch_bounds__(LOC_WARPS * 32)
+k_emin(int64_t ne, const int64_t* arp, const int32_t* aci, const double* av, const int64_t* trp, const int32_t* tci,
+       const double* tv, const int64_t* nrp, const int32_t* nci, const int64_t* hrp, const int32_t* hci,
+       const double* hv, const double* P, double* Pout, double omega, int* fail) {
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ int64_t s_off[LOC_WARPS][32];
+    __shared__ int64_t s_bst[LOC_WARPS][32];
+    __shared__ double s_av[LOC_WARPS][32];
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    LocalSys& S = ((LocalSys*)smem_raw)[w];
+    int64_t i = (int64_t)blockIdx.x * LOC_WARPS + w;
+    if (i >= ne) return;
+    int m, np;
+    int k = local_setup(S, i, trp, tci, tv, nrp, nci, hrp, hci, hv, &m, &np);
+    if (np == 0) return;
+    if (k < 0) { if (lane == 0) atomicAdd(fail, 1); return; }
+    for (int t = lane; t < np; t += 32) S.acc[t] = 0.0;
+    __syncwarp();
+    // masked product (A P)_{i, N_i}: every product a_if P_fj is matched against the sorted N_i
+    double aii = 0.0;
+    int64_t a0 = arp[i], a1 = arp[i + 1];
+    for (int64_t base = a0; base < a1; base += 32) {
+        int64_t ka = base + lane;
+        int64_t len = 0, bstart = 0;
+        double aval = 0.0;
+        if (ka < a1) {
+            int32_t f = aci[ka];
+            bstart = nrp[f];
+            len = nrp[f + 1] - bstart;
+            aval = av[ka];
+            if (f == i) aii = aval;
+        }
+        int64_t inc = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int64_t tt = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += tt;
+        }
+        int64_t total = __shfl_sync(0xffffffffu, inc, 31);
+        s_off[w][lane] = inc - len;
+        s_bst[w][lane] = bstart;
+        s_av[w][lane] = aval;
+        __syncwarp();
+        for (int64_t t = lane; t < total; t += 32) {
+            int lo = 0, hi = 31;
+            while (lo < hi) {
+                int mid = (lo + hi + 1) >> 1;
+                if (s_off[w][mid] <= t) lo = mid; else hi = mid - 1;
+            }
+            int64_t kb = s_bst[w][lo] + (t - s_off[w][lo]);
+            int32_t j = nci[kb];
+            int l = 0, h = np - 1;
+            while (l < h) {
+                int mid = (l + h) >> 1;
+                if (S.N[mid] < j) l = mid + 1; else h = mid;
+            }
+            if (np > 0 && S.N[l] == j) atomicAdd(&S.acc[l], s_av[w][lo] * P[kb]);
+        }
+        __syncwarp();
+    }
+    for (int o = 16; o > 0; o >>= 1) aii += __shfl_xor_sync(0xffffffffu, aii, o);
+    for (int t = lane; t < np; t += 32) S.acc[t] /= aii;
+    if (lane < k) S.y[lane] = 0.0;
+    __syncwarp();
+    // y = G~^T dP_i
+    for (int t = lane; t < np; t += 32) {
+        int a = S.la[t], b = S.lb[t];
+        if (a >= 0 && a < k) atomicAdd(&S.y[a], -S.acc[t]);
+        if (b >= 0 && b < k) atomicAdd(&S.y[b], S.acc[t]);
+    }
+    __syncwarp();
+    double z[MAX_T];
+    for (int q = 0; q < k; ++q) z[q] = S.y[q];
+    chol_solve(S.L, k, z);
+    int64_t n0 = nrp[i];
+    for (int t = lane; t < np; t += 32) {
+        double dp = S.acc[t] - gz(S, t, k, z);
+        Pout[n0 + t] = P[n0 + t] - omega * dp;
+    }
+}
+
+// ------------------------------------------------------------------ dense coarsest factor
+__global__ void k_dense_from_csr(const int64_t* rp, const int32_t* ci, const double* v, int64_t n, double* M) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int64_t c = 0; c < n; ++c) M[i * n + c] = 0.0;
+    for (int64_t k = rp[i]; k < rp[i + 1]; ++k) M[i * n + ci[k]] = v[k];
+}
+// column j of the Cholesky factor (one block)
+__global__ void k_chol_col(double* M, int n, int j, int* bad) {
+    __shared__ double d;
+    if (threadIdx.x == 0) {
+        double a = M[(int64_t)j * n + j];
+        if (!(a > 0.0)) { atomicExch(bad, 1); a = 1.0; }
+        d = sqrt(a);
+        M[(int64_t)j * n + j] = d;
+    }
+    __syncthreads();
+    for (int r = j + 1 + threadIdx.x; r < n; r += blockDim.x) M[(int64_t)r * n + j] /= d;
+}
+// rank-1 update of the trailing lower triangle
+__global__ void k_chol_update(double* M, int n, int j) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int rem = n - j - 1;
+    if (q >= (int64_t)rem * rem) return;
+    int r = j + 1 + (int)(q / rem), c = j + 1 + (int)(q % rem);
+    if (c > r) return;
+    M[(int64_t)r * n + c] -= M[(int64_t)r * n + j] * M[(int64_t)c * n + j];
+}
+// inverse column c: solve L L^T x = e_c (one block per column)
+__global__ void k_chol_inverse(const double* L, int n, double* Ainv) {
+    extern __shared__ double xs[];
+    int c = blockIdx.x;
+    for (int r = threadIdx.x; r < n; r += blockDim.x) xs[r] = (r == c) ? 1.0 : 0.0;
+    __syncthreads();
+    for (int j = 0; j < n; ++j) {          // forward: L y = e_c
+        if (threadIdx.x == 0) xs[j] /= L[(int64_t)j * n + j];
+        __syncthreads();
+        double yj = xs[j];
+        for (int r = j + 1 + threadIdx.x; r < n; r += blockDim.x) xs[r] -= L[(int64_t)r * n + j] * yj;
+        __syncthreads();
+    }
+    for (int j = n - 1; j >= 0; --j) {     // backward: L^T x = y
+        if (threadIdx.x == 0) xs[j] /= L[(int64_t)j * n + j];
+        __syncthreads();
+        double xj = xs[j];
+        for (int r = threadIdx.x; r < j; r += blockDim.x) xs[r] -= L[(int64_t)j * n + r] * xj;
+        __syncthreads();
+    }
+    for (int r = threadIdx.x; r < n; r += blockDim.x) Ainv[(int64_t)r * n + c] = xs[r];
+}
+
+int coarse_inverse(const DCSR& A, DBuf<double>& Ainv, cudaStream_t s) {
+    int64_t n = A.nr;
+    if (n > 8192) { set_error("coarsest level of %lld rows is too large for the dense solve", (long long)n); return SPHC_ELIMIT; }
+    SPHC_TRY(Ainv.alloc(n * n, s));
+    if (n == 0) return SPHC_OK;
+    DBuf<double> M;
+    SPHC_TRY(M.alloc(n * n, s));
+    DBuf<int> bad;
+    SPHC_TRY(bad.alloc(1, s));
+    SPHC_TRY(bad.zero(s));
+    k_dense_from_csr<<<grid_for(n, 128), 128, 0, s>>>(A.rp.p, A.ci.p, A.v.p, n, M.p);
+    for (int j = 0; j < n; ++j) {
+        k_chol_col<<<1, 256, 0, s>>>(M.p, (int)n, j, bad.p);
+        int64_t rem = n - j - 1;
+        if (rem > 0) k_chol_update<<<grid_for(rem * rem, 256), 256, 0, s>>>(M.p, (int)n, j);
+    }
+    size_t sm = sizeof(double) * n;
+    if (sm > 48 * 1024) SPHC_CK(cudaFuncSetAttribute(k_chol_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_chol_inverse<<<(unsigned)n, 256, sm, s>>>(M.p, (int)n, Ainv.p);
+    SPHC_CK(cudaGetLastError());
+    int hb = 0;
+    SPHC_CK(cudaMemcpyAsync(&hb, bad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SPHC_CK(cudaStreamSynchronize(s));
+    if (hb) { set_error("coarsest operator is not numerically positive definite"); return SPHC_ENUMERIC; }
+    return SPHC_OK;
+}
+
+// ------------------------------------------------------------------ one level of Alg. 3
+int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext, DCSR& Annext, cudaStream_t s) {
+    uint64_t seed = o.seed + 1000ULL * (uint64_t)lev;
+    int64_t nv = L.An.nr, ne = L.A.nr;
+    // aggregation on the structural nodal graph (drop tolerance 0)
+    SPHC_TRY(aggregate(L.An, seed + 1, L.agg, &L.nagg, s));
+    // smoothed nodal prolongator
+    DBuf<double> dn;
+    SPHC_TRY(dn.alloc(nv, s));
+    SPHC_TRY(csr_diag(L.An, dn.p, s));
+    SPHC_TRY(power_rho(L.An, dn.p, seed + 4, o.power_iters, &L.rho, s));
+    L.omega_sa = 4.0 / (3.0 * L.rho);
+    DCSR Pb;
+    SPHC_TRY(Pb.alloc(nv, L.nagg, nv, s));
+    k_pbar<<<grid_for(nv + 1, 256), 256, 0, s>>>(nv, L.agg.p, Pb.rp.p, Pb.ci.p, Pb.v.p);
+    SPHC_TRY(spgemm(L.An, Pb, L.Pn, s));
+    DBuf<int> fl;
+    SPHC_TRY(fl.alloc(2, s));
+    SPHC_TRY(fl.zero(s));
+    if (nv > 0)
+        k_pn_finish<<<grid_for(nv, 256), 256, 0, s>>>(L.Pn.rp.p, L.Pn.ci.p, L.Pn.v.p, nv, L.agg.p, dn.p, L.omega_sa, 1,
+                                                     fl.p, fl.p + 1);
+    int hf[2];
+    SPHC_CK(cudaMemcpyAsync(hf, fl.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    SPHC_CK(cudaStreamSynchronize(s));
+    if (hf[1]) { set_error("non-finite nodal prolongator row sum on level %d", lev); return SPHC_ENUMERIC; }
+    L.n_rows_unsmoothed = hf[0];
+    // coarse gradient from the tentative aggregates
+    SPHC_TRY(coarse_gradient(L.D, L.Dt, L.agg.p, L.nagg, L.DH, s));
+    // T = D P_n (values r), N (Alg. 2)
+    SPHC_TRY(spgemm(L.D, L.Pn, L.T, s));
+    DCSR DHt;
+    SPHC_TRY(transpose(L.DH, DHt, s));
+    DBuf<int64_t> ncnt;
+    DBuf<int> st;
+    SPHC_TRY(ncnt.alloc(ne + 1, s));
+    SPHC_TRY(st.alloc(8, s));
+    SPHC_TRY(st.zero(s));
+    if (ne > 0)
+        k_pattern<<<grid_for(ne, PAT_WARPS), PAT_WARPS * 32, 0, s>>>(L.T.rp.p, L.T.ci.p, ne, DHt.rp.p, DHt.ci.p,
+                                                                    L.DH.rp.p, L.DH.ci.p, 0, ncnt.p, nullptr, nullptr,
+                                                                    st.p);
+    int hs[8];
+    SPHC_CK(cudaMemcpyAsync(hs, st.p, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    SPHC_CK(cudaStreamSynchronize(s));
+    if (hs[0]) { set_error("level %d: a row of T exceeds %d coarse nodes", lev, MAX_T); return SPHC_ELIMIT; }
+    if (hs[1]) { set_error("level %d: a row of the pattern exceeds %d coarse edges", lev, MAX_NP); return SPHC_ELIMIT; }
+    if (hs[2]) {
+        set_error("level %d: %d rows have a reducible local coarse graph (make_irreducible is not implemented "
+                  "on the GPU)", lev, hs[2]);
+        return SPHC_EINFEASIBLE;
+    }
+    L.max_np = hs[3];
+    L.max_m = hs[4];
+    int64_t nnzN = 0;
+    SPHC_TRY(L.P0.alloc(ne, L.DH.nr, 0, s));
+    SPHC_TRY(exclusive_scan_i64(ncnt.p, L.P0.rp.p, ne, s, &nnzN));
+    L.P0.nnz = nnzN;
+    SPHC_TRY(L.P0.ci.alloc(nnzN, s));
+    SPHC_TRY(L.P0.v.alloc(nnzN, s));
+    if (ne > 0)
+        k_pattern<<<grid_for(ne, PAT_WARPS), PAT_WARPS * 32, 0, s>>>(L.T.rp.p, L.T.ci.p, ne, DHt.rp.p, DHt.ci.p,
+                                                                    L.DH.rp.p, L.DH.ci.p, 1, nullptr, L.P0.rp.p,
+                                                                    L.P0.ci.p, st.p);
+    // initial guess and energy minimisation
+    SPHC_TRY(L.hist.alloc(33 * 33, s));
+    SPHC_TRY(L.hist.zero(s));
+    SPHC_TRY(st.zero(s));
+    size_t sm = sizeof(LocalSys) * LOC_WARPS;
+    SPHC_CK(cudaFuncSetAttribute(k_p0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    SPHC_CK(cudaFuncSetAttribute(k_emin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    if (ne > 0)
+        k_p0<<<grid_for(ne, LOC_WARPS), LOC_WARPS * 32, sm, s>>>(ne, L.T.rp.p, L.T.ci.p, L.T.v.p, L.P0.rp.p, L.P0.ci.p,
+                                                                  L.DH.rp.p, L.DH.ci.p, L.DH.v.p, L.P0.v.p, st.p,
+                                                                  L.hist.p);
+    SPHC_TRY(csr_copy(L.P0, L.Pe, s));
+    DBuf<double> Pnew;
+    SPHC_TRY(Pnew.alloc(nnzN, s));
+    for (int it = 0; it < o.emin_iters; ++it) {
+        if (ne > 0)
+            k_emin<<<grid_for(ne, LOC_WARPS), LOC_WARPS * 32, sm, s>>>(
+                ne, L.A.rp.p, L.A.ci.p, L.A.v.p, L.T.rp.p, L.T.ci.p, L.T.v.p, L.Pe.rp.p, L.Pe.ci.p, L.DH.rp.p,
+                L.DH.ci.p, L.DH.v.p, L.Pe.v.p, Pnew.p, o.emin_omega, st.p);
+        std::swap(L.Pe.v.p, Pnew.p);
+    }
+    SPHC_CK(cudaMemcpyAsync(hs, st.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SPHC_CK(cudaStreamSynchronize(s));
+    if (hs[0]) { set_error("level %d: %d local constraint systems are infeasible", lev, hs[0]); return SPHC_EINFEASIBLE; }
+    // Galerkin operators of the next level
+    SPHC_TRY(transpose(L.Pe, L.PeT, s));
+    {
+        DCSR AP;
+        SPHC_TRY(spgemm(L.A, L.Pe, AP, s));
+        SPHC_TRY(spgemm(L.PeT, AP, Anext, s));
+    }
+    {
+        DCSR PnT, AnP;
+        SPHC_TRY(transpose(L.Pn, PnT, s));
+        SPHC_TRY(spgemm(L.An, L.Pn, AnP, s));
+        SPHC_TRY(spgemm(PnT, AnP, Annext, s));
+    }
+    SPHC_TRY(csr_copy(L.DH, Dnext, s));
+    SPHC_CK(cudaGetLastError());
+    return SPHC_OK;
+}
+
+}  // namespace sphc

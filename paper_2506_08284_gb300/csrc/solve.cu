@@ -1,0 +1,479 @@
+// Solve phase: V-cycle with one pre- and one post symmetric Hiptmair sweep on every level but
+// the coarsest, which is solved directly (Sec. 6.1), inside FP64 conjugate gradients with x0 = 0
+// and the stopping test ||r|| <= tol ||b|| (Sec. 6.1).  The V-cycle runs in FP32 or FP64.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "sphc_level.cuh"
+
+namespace sphc {
+
+// ------------------------------------------------------------------ stable colour partition
+static constexpr int PART_BLOCK = 1024;
+static constexpr int PART_MAXC = 256;
+
+__global__ void k_part_count(const int32_t* color, int64_t n, int ncolor, int32_t* table, int64_t nblocks) {
+    __shared__ int32_t cnt[PART_MAXC];
+    for (int c = threadIdx.x; c < ncolor; c += blockDim.x) cnt[c] = 0;
+    __syncthreads();
+    int64_t i = (int64_t)blockIdx.x * PART_BLOCK + threadIdx.x;
+    if (i < n) atomicAdd(&cnt[color[i]], 1);
+    __syncthreads();
+    for (int c = threadIdx.x; c < ncolor; c += blockDim.x) table[(int64_t)c * nblocks + blockIdx.x] = cnt[c];
+}
+// rows keep their natural order inside a colour
+__global__ void k_part_place(const int32_t* color, int64_t n, int ncolor, const int64_t* off, int64_t nblocks,
+                             int32_t* perm) {
+    __shared__ int32_t wcnt[PART_BLOCK / 32][PART_MAXC];
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int q = threadIdx.x; q < (PART_BLOCK / 32) * PART_MAXC; q += blockDim.x) (&wcnt[0][0])[q] = 0;
+    __syncthreads();
+    int64_t i = (int64_t)blockIdx.x * PART_BLOCK + threadIdx.x;
+    int c = i < n ? color[i] : -1;
+    unsigned m = __match_any_sync(0xffffffffu, c);
+    int rank = __popc(m & ((1u << lane) - 1u));
+    if (c >= 0 && rank == 0) wcnt[w][c] = __popc(m);
+    __syncthreads();
+    if (c >= 0) {
+        int before = 0;
+        for (int q = 0; q < w; ++q) before += wcnt[q][c];
+        perm[off[(int64_t)c * nblocks + blockIdx.x] + before + rank] = (int32_t)i;
+    }
+}
+
+static int colour_partition(const int32_t* color, int64_t n, int ncolor, DBuf<int32_t>& perm,
+                            std::vector<int64_t>& cstart, cudaStream_t s) {
+    if (ncolor > PART_MAXC) { set_error("too many colours (%d)", ncolor); return SPHC_ELIMIT; }
+    SPHC_TRY(perm.alloc(n, s));
+    int64_t nb = (n + PART_BLOCK - 1) / PART_BLOCK;
+    if (nb < 1) nb = 1;
+    DBuf<int32_t> table;
+    DBuf<int64_t> table64, off;
+    SPHC_TRY(table.alloc(ncolor * nb, s));
+    SPHC_TRY(off.alloc(ncolor * nb + 1, s));
+    if (n > 0) k_part_count<<<(unsigned)nb, PART_BLOCK, 0, s>>>(color, n, ncolor, table.p, nb);
+    SPHC_TRY(table64.alloc(ncolor * nb, s));
+    // widen to int64 for the scan
+    {
+        std::vector<int32_t> h(ncolor * nb);
+        SPHC_CK(cudaMemcpyAsync(h.data(), table.p, sizeof(int32_t) * h.size(), cudaMemcpyDeviceToHost, s));
+        SPHC_CK(cudaStreamSynchronize(s));
+        std::vector<int64_t> o(ncolor * nb + 1);
+        int64_t run = 0;
+        cstart.assign(ncolor + 1, 0);
+        for (int c = 0; c < ncolor; ++c) {
+            cstart[c] = run;
+            for (int64_t b = 0; b < nb; ++b) { o[c * nb + b] = run; run += h[c * nb + b]; }
+        }
+        cstart[ncolor] = run;
+        o[ncolor * nb] = run;
+        SPHC_CK(cudaMemcpyAsync(off.p, o.data(), sizeof(int64_t) * o.size(), cudaMemcpyHostToDevice, s));
+        SPHC_CK(cudaStreamSynchronize(s));
+    }
+    if (n > 0) k_part_place<<<(unsigned)nb, PART_BLOCK, 0, s>>>(color, n, ncolor, off.p, nb, perm.p);
+    SPHC_CK(cudaGetLastError());
+    return SPHC_OK;
+}
+
+__global__ void k_perm_rowlen(const int64_t* rp, const int32_t* perm, int64_t n, int64_t* len) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) len[k] = rp[perm[k] + 1] - rp[perm[k]];
+}
+__global__ void k_rp_narrow(const int64_t* a, int32_t* b, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (int32_t)a[i];
+}
+template <typename T>
+__global__ void k_perm_copy(const int64_t* rp, const int32_t* ci, const double* v, const int32_t* perm, int64_t n,
+                            const int32_t* nrp, int32_t* nci, T* nv, T* dinv) {
+    int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (k >= n) return;
+    int64_t i = perm[k];
+    int64_t b = rp[i], len = rp[i + 1] - b;
+    int32_t o = nrp[k];
+    for (int64_t q = lane; q < len; q += 32) {
+        int32_t c = ci[b + q];
+        nci[o + q] = c;
+        nv[o + q] = (T)v[b + q];
+        if (c == i) dinv[k] = (T)(1.0 / v[b + q]);
+    }
+}
+
+template <typename T>
+static int build_smooth_op(const DCSR& A, const int32_t* color, int ncolor, SmoothOp<T>& op, cudaStream_t s) {
+    op.n = A.nr;
+    op.nnz = A.nnz;
+    op.ncolor = ncolor;
+    if (A.nnz >= (1LL << 31)) { set_error("operator with %lld nonzeros exceeds int32 row pointers", (long long)A.nnz); return SPHC_ELIMIT; }
+    SPHC_TRY(colour_partition(color, A.nr, ncolor, op.perm, op.cstart, s));
+    DBuf<int64_t> len, rp64;
+    SPHC_TRY(len.alloc(A.nr + 1, s));
+    SPHC_TRY(rp64.alloc(A.nr + 1, s));
+    if (A.nr > 0) k_perm_rowlen<<<grid_for(A.nr, 256), 256, 0, s>>>(A.rp.p, op.perm.p, A.nr, len.p);
+    SPHC_TRY(exclusive_scan_i64(len.p, rp64.p, A.nr, s, nullptr));
+    SPHC_TRY(op.rp.alloc(A.nr + 1, s));
+    k_rp_narrow<<<grid_for(A.nr + 1, 256), 256, 0, s>>>(rp64.p, op.rp.p, A.nr + 1);
+    SPHC_TRY(op.ci.alloc(A.nnz, s));
+    SPHC_TRY(op.v.alloc(A.nnz, s));
+    SPHC_TRY(op.dinv.alloc(A.nr, s));
+    if (A.nr > 0)
+        k_perm_copy<T><<<grid_for(A.nr * 32, 256), 256, 0, s>>>(A.rp.p, A.ci.p, A.v.p, op.perm.p, A.nr, op.rp.p,
+                                                                 op.ci.p, op.v.p, op.dinv.p);
+    SPHC_CK(cudaGetLastError());
+    return SPHC_OK;
+}
+
+template <typename T>
+__global__ void k_csr_narrow(const int64_t* rp, const double* v, int64_t nr, int64_t nnz, int32_t* nrp, T* nv) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i <= nr) nrp[i] = (int32_t)rp[i];
+    if (i < nnz) nv[i] = (T)v[i];
+}
+template <typename T>
+static int build_vcsr(const DCSR& A, VCSR<T>& B, cudaStream_t s) {
+    if (A.nnz >= (1LL << 31)) { set_error("transfer with %lld nonzeros exceeds int32 row pointers", (long long)A.nnz); return SPHC_ELIMIT; }
+    B.nr = A.nr; B.nc = A.nc; B.nnz = A.nnz;
+    SPHC_TRY(B.rp.alloc(A.nr + 1, s));
+    SPHC_TRY(B.ci.alloc(A.nnz, s));
+    SPHC_TRY(B.v.alloc(A.nnz, s));
+    int64_t m = A.nnz > A.nr + 1 ? A.nnz : A.nr + 1;
+    k_csr_narrow<T><<<grid_for(m, 256), 256, 0, s>>>(A.rp.p, A.v.p, A.nr, A.nnz, B.rp.p, B.v.p);
+    if (A.nnz > 0) SPHC_CK(cudaMemcpyAsync(B.ci.p, A.ci.p, sizeof(int32_t) * A.nnz, cudaMemcpyDeviceToDevice, s));
+    SPHC_CK(cudaGetLastError());
+    return SPHC_OK;
+}
+
+__global__ void k_d_pairs(const int64_t* rp, const int32_t* ci, const double* v, int64_t ne, int2* D) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ne) return;
+    int2 d = make_int2(-1, -1);
+    for (int64_t k = rp[e]; k < rp[e + 1]; ++k) {
+        if (v[k] < 0) d.x = ci[k]; else d.y = ci[k];
+    }
+    D[e] = d;
+}
+__global__ void k_dt_encode(const int64_t* rp, const int32_t* ci, const double* v, int64_t nv, int64_t nnz,
+                            int32_t* nrp, int32_t* enc) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i <= nv) nrp[i] = (int32_t)rp[i];
+    if (i < nnz) enc[i] = (ci[i] << 1) | (v[i] < 0 ? 1 : 0);
+}
+
+template <typename T>
+static int build_vlevel(Hierarchy& H, int l, VLevel<T>& V, cudaStream_t s) {
+    Level& L = H.L[l];
+    int64_t ne = L.A.nr, nv = L.An.nr;
+    SPHC_TRY(V.x.alloc(ne, s));
+    SPHC_TRY(V.b.alloc(ne, s));
+    SPHC_TRY(V.r.alloc(ne, s));
+    if (l == H.nlev - 1) return SPHC_OK;
+    SPHC_TRY(build_smooth_op<T>(L.A, L.col_e.p, L.ncol_e, V.A, s));
+    SPHC_TRY(build_smooth_op<T>(L.An, L.col_n.p, L.ncol_n, V.An, s));
+    SPHC_TRY(V.g.alloc(nv, s));
+    SPHC_TRY(V.c.alloc(nv, s));
+    SPHC_TRY(V.D.alloc(ne, s));
+    if (ne > 0) k_d_pairs<<<grid_for(ne, 256), 256, 0, s>>>(L.D.rp.p, L.D.ci.p, L.D.v.p, ne, V.D.p);
+    SPHC_TRY(V.Dt_rp.alloc(nv + 1, s));
+    SPHC_TRY(V.Dt_e.alloc(L.Dt.nnz, s));
+    int64_t m = L.Dt.nnz > nv + 1 ? L.Dt.nnz : nv + 1;
+    k_dt_encode<<<grid_for(m, 256), 256, 0, s>>>(L.Dt.rp.p, L.Dt.ci.p, L.Dt.v.p, nv, L.Dt.nnz, V.Dt_rp.p, V.Dt_e.p);
+    SPHC_TRY(build_vcsr<T>(L.Pe, V.Pe, s));
+    SPHC_TRY(build_vcsr<T>(L.PeT, V.PeT, s));
+    SPHC_CK(cudaGetLastError());
+    return SPHC_OK;
+}
+
+int build_vcycle_ops(Hierarchy& H, cudaStream_t s) {
+    if (H.opts.vcycle_fp32) {
+        H.V32.clear();
+        H.V32.resize(H.nlev);
+        for (int l = 0; l < H.nlev; ++l) SPHC_TRY(build_vlevel<float>(H, l, H.V32[l], s));
+    } else {
+        H.V64.clear();
+        H.V64.resize(H.nlev);
+        for (int l = 0; l < H.nlev; ++l) SPHC_TRY(build_vlevel<double>(H, l, H.V64[l], s));
+    }
+    int64_t n0 = H.L[0].A.nr;
+    SPHC_TRY(H.x.alloc(n0, s));
+    SPHC_TRY(H.r.alloc(n0, s));
+    SPHC_TRY(H.z.alloc(n0, s));
+    SPHC_TRY(H.p.alloc(n0, s));
+    SPHC_TRY(H.q.alloc(n0, s));
+    SPHC_TRY(H.rold.alloc(n0, s));
+    SPHC_TRY(H.scal.alloc(16, s));
+    SPHC_TRY(H.cb.alloc(H.n_coarse, s));
+    SPHC_TRY(H.cx.alloc(H.n_coarse, s));
+    return SPHC_OK;
+}
+
+// ------------------------------------------------------------------ V-cycle kernels
+template <typename T, int SUB>
+__global__ void k_sgs_color(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const T* __restrict__ v,
+                            const int32_t* __restrict__ perm, const T* __restrict__ dinv, int64_t k0, int64_t k1,
+                            const T* __restrict__ b, T* x) {
+    int64_t k = k0 + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / SUB);
+    int q = threadIdx.x & (SUB - 1);
+    bool valid = k < k1;
+    T sum = 0;
+    if (valid)
+        for (int32_t e = rp[k] + q; e < rp[k + 1]; e += SUB) sum += v[e] * x[ci[e]];
+#pragma unroll
+    for (int o = SUB / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o, SUB);
+    if (valid && q == 0) {
+        int32_t i = perm[k];
+        x[i] += (b[i] - sum) * dinv[k];
+    }
+}
+
+template <typename T, int SUB>
+__global__ void k_resid(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const T* __restrict__ v,
+                        const int32_t* __restrict__ perm, int64_t n, const T* __restrict__ b, const T* __restrict__ x,
+                        T* __restrict__ r) {
+    int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / SUB;
+    int q = threadIdx.x & (SUB - 1);
+    bool valid = k < n;
+    T sum = 0;
+    if (valid)
+        for (int32_t e = rp[k] + q; e < rp[k + 1]; e += SUB) sum += v[e] * x[ci[e]];
+#pragma unroll
+    for (int o = SUB / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o, SUB);
+    if (valid && q == 0) {
+        int32_t i = perm[k];
+        r[i] = b[i] - sum;
+    }
+}
+
+template <typename T, int SUB>
+__global__ void k_spmv_v(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const T* __restrict__ v,
+                         int64_t n, const T* __restrict__ x, T* y, int accumulate) {
+    int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / SUB;
+    int q = threadIdx.x & (SUB - 1);
+    bool valid = i < n;
+    T sum = 0;
+    if (valid)
+        for (int32_t e = rp[i] + q; e < rp[i + 1]; e += SUB) sum += v[e] * x[ci[e]];
+#pragma unroll
+    for (int o = SUB / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o, SUB);
+    if (valid && q == 0) y[i] = accumulate ? y[i] + sum : sum;
+}
+
+template <typename T>
+__global__ void k_dt_gather(const int32_t* __restrict__ rp, const int32_t* __restrict__ enc, int64_t nv,
+                            const T* __restrict__ r, T* __restrict__ g) {
+    int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= nv) return;
+    T s = 0;
+    for (int32_t k = rp[u]; k < rp[u + 1]; ++k) {
+        int32_t e = enc[k];
+        T val = r[e >> 1];
+        s += (e & 1) ? -val : val;
+    }
+    g[u] = s;
+}
+template <typename T>
+__global__ void k_d_apply(const int2* __restrict__ D, int64_t ne, const T* __restrict__ c, T* __restrict__ x) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ne) return;
+    int2 d = D[e];
+    T v = 0;
+    if (d.y >= 0) v += c[d.y];
+    if (d.x >= 0) v -= c[d.x];
+    x[e] += v;
+}
+template <typename T>
+__global__ void k_zero(T* a, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = 0;
+}
+template <typename A, typename B>
+__global__ void k_cast(const A* a, B* b, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (B)a[i];
+}
+// x = Ainv b on the coarsest level (FP64 arithmetic)
+template <typename T>
+__global__ void k_dense_solve(const double* __restrict__ Ainv, int64_t n, const T* __restrict__ b, T* __restrict__ x) {
+    int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (i >= n) return;
+    double s = 0.0;
+    for (int64_t j = lane; j < n; j += 32) s += Ainv[i * n + j] * (double)b[j];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) x[i] = (T)s;
+}
+
+static int sub_for(int64_t nnz, int64_t n) {
+    double avg = n > 0 ? (double)nnz / (double)n : 0.0;
+    if (avg <= 6) return 4;
+    if (avg <= 20) return 8;
+    if (avg <= 48) return 16;
+    return 32;
+}
+
+template <typename T>
+static void launch_rows_sgs(const SmoothOp<T>& op, int64_t k0, int64_t k1, const T* b, T* x, cudaStream_t s) {
+    int64_t rows = k1 - k0;
+    if (rows <= 0) return;
+    int sub = sub_for(op.nnz, op.n);
+    int64_t th = rows * sub;
+    switch (sub) {
+        case 4: k_sgs_color<T, 4><<<grid_for(th, 256), 256, 0, s>>>(op.rp.p, op.ci.p, op.v.p, op.perm.p, op.dinv.p, k0, k1, b, x); break;
+        case 8: k_sgs_color<T, 8><<<grid_for(th, 256), 256, 0, s>>>(op.rp.p, op.ci.p, op.v.p, op.perm.p, op.dinv.p, k0, k1, b, x); break;
+        case 16: k_sgs_color<T, 16><<<grid_for(th, 256), 256, 0, s>>>(op.rp.p, op.ci.p, op.v.p, op.perm.p, op.dinv.p, k0, k1, b, x); break;
+        default: k_sgs_color<T, 32><<<grid_for(th, 256), 256, 0, s>>>(op.rp.p, op.ci.p, op.v.p, op.perm.p, op.dinv.p, k0, k1, b, x); break;
+    }
+}
+template <typename T>
+static void sgs(const SmoothOp<T>& op, const T* b, T* x, cudaStream_t s) {
+    for (int c = 0; c < op.ncolor; ++c) launch_rows_sgs(op, op.cstart[c], op.cstart[c + 1], b, x, s);
+    for (int c = op.ncolor - 1; c >= 0; --c) launch_rows_sgs(op, op.cstart[c], op.cstart[c + 1], b, x, s);
+}
+template <typename T>
+static void resid(const SmoothOp<T>& op, const T* b, const T* x, T* r, cudaStream_t s) {
+    if (op.n == 0) return;
+    int sub = sub_for(op.nnz, op.n);
+    int64_t th = op.n * sub;
+    switch (sub) {
+        case 4: k_resid<T, 4><<<grid_for(th, 256), 256, 0, s>>>(op.rp.p, op.ci.p, op.v.p, op.perm.p, op.n, b, x, r); break;
+        case 8: k_resid<T, 8><<<grid_for(th, 256), 256, 0, s>>>(op.rp.p, op.ci.p, op.v.p, op.perm.p, op.n, b, x, r); break;
+        case 16: k_resid<T, 16><<<grid_for(th, 256), 256, 0, s>>>(op.rp.p, op.ci.p, op.v.p, op.perm.p, op.n, b, x, r); break;
+        default: k_resid<T, 32><<<grid_for(th, 256), 256, 0, s>>>(op.rp.p, op.ci.p, op.v.p, op.perm.p, op.n, b, x, r); break;
+    }
+}
+template <typename T>
+static void spmv_v(const VCSR<T>& A, const T* x, T* y, int acc, cudaStream_t s) {
+    if (A.nr == 0) return;
+    int sub = sub_for(A.nnz, A.nr);
+    int64_t th = A.nr * sub;
+    switch (sub) {
+        case 4: k_spmv_v<T, 4><<<grid_for(th, 256), 256, 0, s>>>(A.rp.p, A.ci.p, A.v.p, A.nr, x, y, acc); break;
+        case 8: k_spmv_v<T, 8><<<grid_for(th, 256), 256, 0, s>>>(A.rp.p, A.ci.p, A.v.p, A.nr, x, y, acc); break;
+        case 16: k_spmv_v<T, 16><<<grid_for(th, 256), 256, 0, s>>>(A.rp.p, A.ci.p, A.v.p, A.nr, x, y, acc); break;
+        default: k_spmv_v<T, 32><<<grid_for(th, 256), 256, 0, s>>>(A.rp.p, A.ci.p, A.v.p, A.nr, x, y, acc); break;
+    }
+}
+
+// one symmetric Hiptmair sweep (Sec. 6.1): SGS on A, nodal SGS on D^T A D with c0 = 0 applied
+// to D^T r, correction x += D c, SGS on A
+template <typename T>
+static void hiptmair(VLevel<T>& V, int64_t ne, int64_t nv, cudaStream_t s) {
+    sgs(V.A, V.b.p, V.x.p, s);
+    resid(V.A, V.b.p, V.x.p, V.r.p, s);
+    if (nv > 0) {
+        k_dt_gather<T><<<grid_for(nv, 256), 256, 0, s>>>(V.Dt_rp.p, V.Dt_e.p, nv, V.r.p, V.g.p);
+        k_zero<T><<<grid_for(nv, 256), 256, 0, s>>>(V.c.p, nv);
+        sgs(V.An, V.g.p, V.c.p, s);
+        k_d_apply<T><<<grid_for(ne, 256), 256, 0, s>>>(V.D.p, ne, V.c.p, V.x.p);
+    }
+    sgs(V.A, V.b.p, V.x.p, s);
+}
+
+template <typename T>
+static void vcycle_level(Hierarchy& H, std::vector<VLevel<T>>& V, int l, cudaStream_t s) {
+    int64_t ne = H.L[l].A.nr, nv = H.L[l].An.nr;
+    if (l == H.nlev - 1) {
+        if (ne > 0) k_dense_solve<T><<<grid_for(ne * 32, 256), 256, 0, s>>>(H.coarse_inv.p, ne, V[l].b.p, V[l].x.p);
+        return;
+    }
+    k_zero<T><<<grid_for(ne, 256), 256, 0, s>>>(V[l].x.p, ne);
+    hiptmair(V[l], ne, nv, s);
+    resid(V[l].A, V[l].b.p, V[l].x.p, V[l].r.p, s);
+    spmv_v(V[l].PeT, V[l].r.p, V[l + 1].b.p, 0, s);
+    vcycle_level(H, V, l + 1, s);
+    spmv_v(V[l].Pe, V[l + 1].x.p, V[l].x.p, 1, s);
+    hiptmair(V[l], ne, nv, s);
+}
+
+int apply_vcycle(Hierarchy& H, const double* r, double* z, cudaStream_t s) {
+    int64_t n = H.L[0].A.nr;
+    if (H.opts.vcycle_fp32) {
+        k_cast<double, float><<<grid_for(n, 256), 256, 0, s>>>(r, H.V32[0].b.p, n);
+        vcycle_level<float>(H, H.V32, 0, s);
+        k_cast<float, double><<<grid_for(n, 256), 256, 0, s>>>(H.V32[0].x.p, z, n);
+    } else {
+        SPHC_CK(cudaMemcpyAsync(H.V64[0].b.p, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+        vcycle_level<double>(H, H.V64, 0, s);
+        SPHC_CK(cudaMemcpyAsync(z, H.V64[0].x.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    }
+    SPHC_CK(cudaGetLastError());
+    return SPHC_OK;
+}
+
+// ------------------------------------------------------------------ CG
+// scal: 0 rz, 1 pq, 2 rr, 3 rz_new, 4 z.r_old, 5 bb
+__global__ void k_cg_xr(double* x, double* r, double* rold, const double* p, const double* q, const double* sc,
+                        int64_t n, int flexible) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double alpha = sc[0] / sc[1];
+    x[i] += alpha * p[i];
+    if (flexible) rold[i] = r[i];
+    r[i] -= alpha * q[i];
+}
+__global__ void k_cg_p(double* p, const double* z, const double* sc, int64_t n, int flexible) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double beta = flexible ? (sc[3] - sc[4]) / sc[0] : sc[3] / sc[0];
+    p[i] = z[i] + beta * p[i];
+}
+__global__ void k_cg_shift(double* sc) { sc[0] = sc[3]; }
+__global__ void k_sub(const double* b, double* q, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) q[i] = b[i] - q[i];
+}
+
+int pcg_solve(Hierarchy& H, const double* b, double* x, double tol, cudaStream_t s, int* iters, double* relres) {
+    const DCSR& A = H.L[0].A;
+    int64_t n = A.nr;
+    int flexible = H.opts.flexible;
+    double* sc = H.scal.p;
+    SPHC_CK(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+    SPHC_CK(cudaMemcpyAsync(H.r.p, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    SPHC_TRY(dot64(b, b, n, sc + 5, s));
+    double hb = 0.0;
+    SPHC_CK(cudaMemcpyAsync(&hb, sc + 5, sizeof(double), cudaMemcpyDeviceToHost, s));
+    SPHC_CK(cudaStreamSynchronize(s));
+    double bnorm = sqrt(hb);
+    int status = SPHC_ENOTCONV, it = 0;
+    if (bnorm == 0.0) status = SPHC_OK;
+    if (status != SPHC_OK) {
+        SPHC_TRY(apply_vcycle(H, H.r.p, H.z.p, s));
+        SPHC_CK(cudaMemcpyAsync(H.p.p, H.z.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+        SPHC_TRY(dot64(H.r.p, H.z.p, n, sc + 0, s));
+        double hsc[6];
+        for (it = 0; it < H.opts.max_iter;) {
+            SPHC_TRY(spmv64(A, H.p.p, H.q.p, s));
+            SPHC_TRY(dot64(H.p.p, H.q.p, n, sc + 1, s));
+            k_cg_xr<<<grid_for(n, 256), 256, 0, s>>>(x, H.r.p, H.rold.p, H.p.p, H.q.p, sc, n, flexible);
+            ++it;
+            SPHC_TRY(dot64(H.r.p, H.r.p, n, sc + 2, s));
+            SPHC_CK(cudaMemcpyAsync(hsc, sc, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+            SPHC_CK(cudaStreamSynchronize(s));
+            if (!(hsc[1] > 0.0) || !std::isfinite(hsc[2])) { status = SPHC_EBREAKDOWN; break; }
+            if (sqrt(hsc[2]) <= tol * bnorm) { status = SPHC_OK; break; }
+            SPHC_TRY(apply_vcycle(H, H.r.p, H.z.p, s));
+            SPHC_TRY(dot64(H.r.p, H.z.p, n, sc + 3, s));
+            if (flexible) SPHC_TRY(dot64(H.z.p, H.rold.p, n, sc + 4, s));
+            k_cg_p<<<grid_for(n, 256), 256, 0, s>>>(H.p.p, H.z.p, sc, n, flexible);
+            k_cg_shift<<<1, 1, 0, s>>>(sc);
+        }
+    }
+    // true residual
+    SPHC_TRY(spmv64(A, x, H.q.p, s));
+    k_sub<<<grid_for(n, 256), 256, 0, s>>>(b, H.q.p, n);
+    SPHC_TRY(dot64(H.q.p, H.q.p, n, sc + 6, s));
+    double hr = 0.0;
+    SPHC_CK(cudaMemcpyAsync(&hr, sc + 6, sizeof(double), cudaMemcpyDeviceToHost, s));
+    SPHC_CK(cudaStreamSynchronize(s));
+    if (iters) *iters = it;
+    if (relres) *relres = bnorm > 0 ? sqrt(hr) / bnorm : 0.0;
+    if (status != SPHC_OK && status != SPHC_ENOTCONV)
+        set_error("CG breakdown after %d iterations", it);
+    else if (status == SPHC_ENOTCONV)
+        set_error("CG did not reach the tolerance in %d iterations", it);
+    return status;
+}
+
+}  // namespace sphc

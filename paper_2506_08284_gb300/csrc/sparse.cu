@@ -1,0 +1,664 @@
+// Sparse building blocks of the setup phase: scans, transposes, segmented sorts, the
+// structural sparse matrix product (used for D_h^T A_e D_h, A_n Pbar, D_h P_n and the Galerkin
+// products P_e^T A_e P_e, P_n^T A_n P_n of Sec. 2), FP64 SpMV and deterministic dots.
+#include <cstdarg>
+#include <cstdio>
+
+#include "sphc_internal.cuh"
+
+namespace sphc {
+
+bool g_sync_free = false;
+static thread_local std::string g_err;
+void set_error(const char* fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+}
+const char* last_error() { return g_err.c_str(); }
+
+// ------------------------------------------------------------------ scans
+static constexpr int SCAN_BLOCK = 1024;
+static constexpr int SCAN_ITEMS = 4;
+static constexpr int SCAN_TILE = SCAN_BLOCK * SCAN_ITEMS;
+
+__device__ inline int64_t warp_incl_scan(int64_t v) {
+    int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int64_t t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// inclusive block scan of one value per thread; returns inclusive prefix, *total = block sum
+__device__ inline int64_t block_incl_scan(int64_t v, int64_t* smem_warps, int64_t* total) {
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int64_t x = warp_incl_scan(v);
+    if (lane == 31) smem_warps[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int64_t y = lane < nw ? smem_warps[lane] : 0;
+        y = warp_incl_scan(y);
+        if (lane < nw) smem_warps[lane] = y;
+    }
+    __syncthreads();
+    int64_t off = w > 0 ? smem_warps[w - 1] : 0;
+    if (total) *total = smem_warps[nw - 1];
+    __syncthreads();
+    return x + off;
+}
+
+template <typename TI>
+__global__ void k_scan_tiles(const TI* in, int64_t n, int64_t* tile_sums) {
+    __shared__ int64_t sw[32];
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    int64_t s = 0;
+#pragma unroll
+    for (int q = 0; q < SCAN_ITEMS; ++q)
+        if (base + q < n) s += (int64_t)in[base + q];
+    int64_t tot;
+    block_incl_scan(s, sw, &tot);
+    if (threadIdx.x == 0) tile_sums[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_sums(int64_t* sums, int64_t nt, int64_t* total) {
+    __shared__ int64_t sw[32];
+    __shared__ int64_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t b = 0; b < nt; b += blockDim.x) {
+        int64_t i = b + threadIdx.x;
+        int64_t v = i < nt ? sums[i] : 0;
+        int64_t tot;
+        int64_t inc = block_incl_scan(v, sw, &tot);
+        if (i < nt) sums[i] = carry + inc - v;   // exclusive
+        __syncthreads();
+        if (threadIdx.x == 0) carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+template <typename TI>
+__global__ void k_scan_apply(const TI* in, int64_t n, const int64_t* tile_off, int64_t* out) {
+    __shared__ int64_t sw[32];
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    int64_t v[SCAN_ITEMS];
+    int64_t s = 0;
+#pragma unroll
+    for (int q = 0; q < SCAN_ITEMS; ++q) {
+        v[q] = (base + q < n) ? (int64_t)in[base + q] : 0;
+        s += v[q];
+    }
+    int64_t inc = block_incl_scan(s, sw, nullptr);
+    int64_t run = tile_off[blockIdx.x] + inc - s;
+#pragma unroll
+    for (int q = 0; q < SCAN_ITEMS; ++q) {
+        if (base + q < n) out[base + q] = run;
+        run += v[q];
+    }
+}
+
+// out[0..n) = exclusive prefix of in; out[n] = total (out must hold n+1 entries)
+template <typename TI>
+static int scan_impl(const TI* in, int64_t* out, int64_t n, cudaStream_t s, int64_t* total_host) {
+    int64_t nt = (n + SCAN_TILE - 1) / SCAN_TILE;
+    if (nt < 1) nt = 1;
+    DBuf<int64_t> sums;
+    SPHC_TRY(sums.alloc(nt + 1, s));
+    if (n > 0) k_scan_tiles<TI><<<(unsigned)nt, SCAN_BLOCK, 0, s>>>(in, n, sums.p);
+    else SPHC_CK(cudaMemsetAsync(sums.p, 0, sizeof(int64_t) * nt, s));
+    k_scan_sums<<<1, SCAN_BLOCK, 0, s>>>(sums.p, nt, out + n);
+    if (n > 0) k_scan_apply<TI><<<(unsigned)nt, SCAN_BLOCK, 0, s>>>(in, n, sums.p, out);
+    SPHC_CK(cudaGetLastError());
+    if (total_host) {
+        SPHC_CK(cudaMemcpyAsync(total_host, out + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        SPHC_CK(cudaStreamSynchronize(s));
+    }
+    return SPHC_OK;
+}
+int exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s, int64_t* total_host) {
+    return scan_impl<int64_t>(in, out, n, s, total_host);
+}
+int scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, cudaStream_t s, int64_t* total_host) {
+    return scan_impl<int32_t>(in, out, n, s, total_host);
+}
+
+// ------------------------------------------------------------------ row-length helpers
+__global__ void k_row_len_max(const int64_t* rp, int64_t n, unsigned long long* mx) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long v = 0;
+    if (i < n) v = (unsigned long long)(rp[i + 1] - rp[i]);
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long t = __shfl_down_sync(0xffffffffu, v, o);
+        v = t > v ? t : v;
+    }
+    if ((threadIdx.x & 31) == 0 && v > 0) atomicMax(mx, v);
+}
+int max_row_length(const int64_t* rp, int64_t nrows, cudaStream_t s, int64_t* out_host) {
+    DBuf<unsigned long long> m;
+    SPHC_TRY(m.alloc(1, s));
+    SPHC_TRY(m.zero(s));
+    if (nrows > 0) k_row_len_max<<<grid_for(nrows, 256), 256, 0, s>>>(rp, nrows, m.p);
+    unsigned long long h = 0;
+    SPHC_CK(cudaMemcpyAsync(&h, m.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+    SPHC_CK(cudaStreamSynchronize(s));
+    *out_host = (int64_t)h;
+    return SPHC_OK;
+}
+
+// ------------------------------------------------------------------ segmented sort
+// rows of length <= 32: one warp per row, bitonic network over lanes
+__global__ void k_segsort_warp(const int64_t* rp, int64_t nrows, int32_t* keys, double* vals) {
+    int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (row >= nrows) return;
+    int64_t b = rp[row];
+    int len = (int)(rp[row + 1] - b);
+    if (len <= 1 || len > 32) return;
+    int32_t k = lane < len ? keys[b + lane] : 0x7fffffff;
+    double v = lane < len && vals ? vals[b + lane] : 0.0;
+    for (int size = 2; size <= 32; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            int32_t ok = __shfl_xor_sync(0xffffffffu, k, stride);
+            double ov = __shfl_xor_sync(0xffffffffu, v, stride);
+            bool up = ((lane & size) == 0);
+            bool lower = (lane & stride) == 0;
+            bool take_min = (up == lower);
+            bool swap = take_min ? (ok < k) : (ok > k);
+            if (swap) { k = ok; v = ov; }
+        }
+    }
+    if (lane < len) {
+        keys[b + lane] = k;
+        if (vals) vals[b + lane] = v;
+    }
+}
+
+// rows of length <= cap (power of two): one block per row, bitonic network in shared memory
+__global__ void k_segsort_block(const int64_t* rp, int64_t nrows, int32_t* keys, double* vals, int cap) {
+    extern __shared__ unsigned char smem_raw[];
+    int32_t* sk = (int32_t*)smem_raw;
+    double* sv = (double*)(smem_raw + sizeof(int32_t) * cap);
+    for (int64_t row = blockIdx.x; row < nrows; row += gridDim.x) {
+        int64_t b = rp[row];
+        int len = (int)(rp[row + 1] - b);
+        if (len <= 32) continue;   // handled by the warp kernel
+        int n2 = 64;
+        while (n2 < len) n2 <<= 1;
+        for (int t = threadIdx.x; t < n2; t += blockDim.x) {
+            sk[t] = t < len ? keys[b + t] : 0x7fffffff;
+            sv[t] = (t < len && vals) ? vals[b + t] : 0.0;
+        }
+        __syncthreads();
+        for (int size = 2; size <= n2; size <<= 1)
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int t = threadIdx.x; t < n2; t += blockDim.x) {
+                    int p = t ^ stride;
+                    if (p > t) {
+                        bool up = ((t & size) == 0);
+                        int32_t a = sk[t], c = sk[p];
+                        if ((a > c) == up) {
+                            sk[t] = c; sk[p] = a;
+                            double tv = sv[t]; sv[t] = sv[p]; sv[p] = tv;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        for (int t = threadIdx.x; t < len; t += blockDim.x) {
+            keys[b + t] = sk[t];
+            if (vals) vals[b + t] = sv[t];
+        }
+        __syncthreads();
+    }
+}
+
+int segmented_sort(const int64_t* rp, int64_t nrows, int32_t* keys, double* vals, int64_t max_len,
+                   cudaStream_t s) {
+    if (nrows <= 0) return SPHC_OK;
+    k_segsort_warp<<<grid_for(nrows * 32, 256), 256, 0, s>>>(rp, nrows, keys, vals);
+    if (max_len > 32) {
+        int cap = 64;
+        while (cap < max_len) cap <<= 1;
+        if (cap > 8192) {
+            set_error("segmented_sort: row of %lld entries exceeds 8192", (long long)max_len);
+            return SPHC_ELIMIT;
+        }
+        size_t sm = (size_t)cap * (sizeof(int32_t) + sizeof(double));
+        SPHC_CK(cudaFuncSetAttribute(k_segsort_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        int grid = (int)(nrows < 65536 ? nrows : 65536);
+        k_segsort_block<<<grid, 256, sm, s>>>(rp, nrows, keys, vals, cap);
+    }
+    SPHC_CK(cudaGetLastError());
+    return SPHC_OK;
+}
+
+// ------------------------------------------------------------------ transpose
+__global__ void k_col_count(const int32_t* ci, int64_t nnz, int32_t* cnt) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < nnz) atomicAdd(&cnt[ci[k]], 1);
+}
+__global__ void k_transpose_scatter(const int64_t* rp, const int32_t* ci, const double* v, int64_t nr,
+                                    unsigned long long* cursor, int32_t* tci, double* tv) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nr) return;
+    for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+        unsigned long long pos = atomicAdd(&cursor[ci[k]], 1ULL);
+        tci[pos] = (int32_t)i;
+        if (tv) tv[pos] = v[k];
+    }
+}
+__global__ void k_i64_to_u64(const int64_t* a, unsigned long long* b, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (unsigned long long)a[i];
+}
+
+int transpose(const DCSR& A, DCSR& At, cudaStream_t s) {
+    DBuf<int32_t> cnt;
+    SPHC_TRY(cnt.alloc(A.nc + 1, s));
+    SPHC_TRY(cnt.zero(s));
+    if (A.nnz > 0) k_col_count<<<grid_for(A.nnz, 256), 256, 0, s>>>(A.ci.p, A.nnz, cnt.p);
+    SPHC_TRY(At.alloc(A.nc, A.nr, A.nnz, s));
+    int64_t tot = 0;
+    SPHC_TRY(scan_i32_to_i64(cnt.p, At.rp.p, A.nc, s, &tot));
+    DBuf<unsigned long long> cur;
+    SPHC_TRY(cur.alloc(A.nc + 1, s));
+    k_i64_to_u64<<<grid_for(A.nc + 1, 256), 256, 0, s>>>(At.rp.p, cur.p, A.nc + 1);
+    if (A.nr > 0)
+        k_transpose_scatter<<<grid_for(A.nr, 256), 256, 0, s>>>(A.rp.p, A.ci.p, A.v.p, A.nr, cur.p, At.ci.p, At.v.p);
+    SPHC_CK(cudaGetLastError());
+    int64_t mx = 0;
+    SPHC_TRY(max_row_length(At.rp.p, At.nr, s, &mx));
+    SPHC_TRY(segmented_sort(At.rp.p, At.nr, At.ci.p, At.v.p, mx, s));
+    return SPHC_OK;
+}
+
+int csr_copy(const DCSR& A, DCSR& B, cudaStream_t s) {
+    SPHC_TRY(B.alloc(A.nr, A.nc, A.nnz, s));
+    SPHC_CK(cudaMemcpyAsync(B.rp.p, A.rp.p, sizeof(int64_t) * (A.nr + 1), cudaMemcpyDeviceToDevice, s));
+    if (A.nnz > 0) {
+        SPHC_CK(cudaMemcpyAsync(B.ci.p, A.ci.p, sizeof(int32_t) * A.nnz, cudaMemcpyDeviceToDevice, s));
+        SPHC_CK(cudaMemcpyAsync(B.v.p, A.v.p, sizeof(double) * A.nnz, cudaMemcpyDeviceToDevice, s));
+    }
+    return SPHC_OK;
+}
+
+__global__ void k_diag(const int64_t* rp, const int32_t* ci, const double* v, int64_t n, double* d) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double r = 0.0;
+    for (int64_t k = rp[i]; k < rp[i + 1]; ++k)
+        if (ci[k] == i) r = v[k];
+    d[i] = r;
+}
+int csr_diag(const DCSR& A, double* d, cudaStream_t s) {
+    if (A.nr > 0) k_diag<<<grid_for(A.nr, 256), 256, 0, s>>>(A.rp.p, A.ci.p, A.v.p, A.nr, d);
+    SPHC_CK(cudaGetLastError());
+    return SPHC_OK;
+}
+
+// ------------------------------------------------------------------ structural SpGEMM
+static constexpr int HASH_SLOTS = 1024;      // per warp (symbolic and numeric)
+static constexpr int HASH_FILL = 768;        // rows with more unique columns go to the big path
+static constexpr int BIG_SLOTS = 8192;       // per block on the big path
+static constexpr int BIG_FILL = 6144;
+static constexpr int SPGEMM_WARPS = 8;
+
+__device__ inline uint32_t hslot(int32_t key, int mask) {
+    return ((uint32_t)key * 2654435761u) & (uint32_t)mask;
+}
+
+__global__ void k_spgemm_ub(const int64_t* arp, const int32_t* aci, const int64_t* brp, int64_t n,
+                            int64_t* ub) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t s = 0;
+    for (int64_t k = arp[i]; k < arp[i + 1]; ++k) s += brp[aci[k] + 1] - brp[aci[k]];
+    ub[i] = s;
+}
+
+// symbolic phase: unique column count per row (-1 = needs the big path)
+__global__ void __launch_bounds__(SPGEMM_WARPS * 32)
+k_spgemm_symbolic(const int64_t* arp, const int32_t* aci, const int64_t* brp, const int32_t* bci,
+                  int64_t n, const int64_t* ub, int64_t* cnt, int32_t* big_list, int* big_n) {
+    __shared__ int32_t s_keys[SPGEMM_WARPS][HASH_SLOTS];
+    __shared__ int64_t s_off[SPGEMM_WARPS][32];
+    __shared__ int64_t s_bst[SPGEMM_WARPS][32];
+    __shared__ int s_cnt[SPGEMM_WARPS];
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int64_t i = (int64_t)blockIdx.x * SPGEMM_WARPS + w;
+    if (i >= n) return;
+    int32_t* keys = s_keys[w];
+    for (int t = lane; t < HASH_SLOTS; t += 32) keys[t] = -1;
+    if (lane == 0) s_cnt[w] = 0;
+    __syncwarp();
+    bool overflow = false;
+    int64_t a0 = arp[i], a1 = arp[i + 1];
+    for (int64_t base = a0; base < a1 && !overflow; base += 32) {
+        int64_t ka = base + lane;
+        int64_t len = 0, bstart = 0;
+        if (ka < a1) {
+            int32_t k = aci[ka];
+            bstart = brp[k];
+            len = brp[k + 1] - bstart;
+        }
+        int64_t inc = warp_incl_scan(len);
+        int64_t total = __shfl_sync(0xffffffffu, inc, 31);
+        s_off[w][lane] = inc - len;
+        s_bst[w][lane] = bstart;
+        __syncwarp();
+        for (int64_t t0 = 0; t0 < total; t0 += 32) {
+            int64_t t = t0 + lane;
+            if (t < total) {
+                int lo = 0, hi = 31;
+                while (lo < hi) {
+                    int mid = (lo + hi + 1) >> 1;
+                    if (s_off[w][mid] <= t) lo = mid; else hi = mid - 1;
+                }
+                int32_t col = bci[s_bst[w][lo] + (t - s_off[w][lo])];
+                uint32_t h = hslot(col, HASH_SLOTS - 1);
+                for (int probe = 0; probe < HASH_SLOTS; ++probe) {
+                    int32_t old = atomicCAS(&keys[h], -1, col);
+                    if (old == -1) { atomicAdd(&s_cnt[w], 1); break; }
+                    if (old == col) break;
+                    h = (h + 1) & (HASH_SLOTS - 1);
+                }
+            }
+            __syncwarp();
+            if (s_cnt[w] > HASH_FILL) { overflow = true; break; }
+        }
+        __syncwarp();
+    }
+    if (lane == 0) {
+        if (overflow) {
+            cnt[i] = 0;
+            int q = atomicAdd(big_n, 1);
+            big_list[q] = (int32_t)i;
+        } else {
+            cnt[i] = s_cnt[w];
+        }
+    }
+    (void)ub;
+}
+
+// big path symbolic: one block per listed row
+__global__ void k_spgemm_symbolic_big(const int64_t* arp, const int32_t* aci, const int64_t* brp,
+                                      const int32_t* bci, const int32_t* list, int nlist, int64_t* cnt,
+                                      int* fail) {
+    extern __shared__ int32_t s_big[];
+    __shared__ int s_n;
+    for (int li = blockIdx.x; li < nlist; li += gridDim.x) {
+        int64_t i = list[li];
+        for (int t = threadIdx.x; t < BIG_SLOTS; t += blockDim.x) s_big[t] = -1;
+        if (threadIdx.x == 0) s_n = 0;
+        __syncthreads();
+        for (int64_t ka = arp[i]; ka < arp[i + 1]; ++ka) {
+            int32_t k = aci[ka];
+            for (int64_t kb = brp[k] + threadIdx.x; kb < brp[k + 1]; kb += blockDim.x) {
+                int32_t col = bci[kb];
+                uint32_t h = hslot(col, BIG_SLOTS - 1);
+                for (int probe = 0; probe < BIG_SLOTS; ++probe) {
+                    int32_t old = atomicCAS(&s_big[h], -1, col);
+                    if (old == -1) { atomicAdd(&s_n, 1); break; }
+                    if (old == col) break;
+                    h = (h + 1) & (BIG_SLOTS - 1);
+                }
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            cnt[i] = s_n;
+            if (s_n > BIG_FILL) atomicExch(fail, 1);
+        }
+        __syncthreads();
+    }
+}
+
+// numeric phase: accumulate, compact, sort by rank and write
+__global__ void __launch_bounds__(SPGEMM_WARPS * 32)
+k_spgemm_numeric(const int64_t* arp, const int32_t* aci, const double* av, const int64_t* brp,
+                 const int32_t* bci, const double* bv, int64_t n, const int64_t* crp, int32_t* cci,
+                 double* cv) {
+    extern __shared__ unsigned char smem_raw[];
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int32_t* keys = (int32_t*)smem_raw + w * HASH_SLOTS;
+    double* vals = (double*)(smem_raw + sizeof(int32_t) * HASH_SLOTS * SPGEMM_WARPS) + w * HASH_SLOTS;
+    __shared__ int64_t s_off[SPGEMM_WARPS][32];
+    __shared__ int64_t s_bst[SPGEMM_WARPS][32];
+    __shared__ double s_av[SPGEMM_WARPS][32];
+    int64_t i = (int64_t)blockIdx.x * SPGEMM_WARPS + w;
+    if (i >= n) return;
+    int64_t c0 = crp[i], c1 = crp[i + 1];
+    int clen = (int)(c1 - c0);
+    if (clen > HASH_FILL) return;  // big path
+    for (int t = lane; t < HASH_SLOTS; t += 32) { keys[t] = -1; vals[t] = 0.0; }
+    __syncwarp();
+    int64_t a0 = arp[i], a1 = arp[i + 1];
+    for (int64_t base = a0; base < a1; base += 32) {
+        int64_t ka = base + lane;
+        int64_t len = 0, bstart = 0;
+        double aval = 0.0;
+        if (ka < a1) {
+            int32_t k = aci[ka];
+            bstart = brp[k];
+            len = brp[k + 1] - bstart;
+            aval = av[ka];
+        }
+        int64_t inc = warp_incl_scan(len);
+        int64_t total = __shfl_sync(0xffffffffu, inc, 31);
+        s_off[w][lane] = inc - len;
+        s_bst[w][lane] = bstart;
+        s_av[w][lane] = aval;
+        __syncwarp();
+        for (int64_t t = lane; t < total; t += 32) {
+            int lo = 0, hi = 31;
+            while (lo < hi) {
+                int mid = (lo + hi + 1) >> 1;
+                if (s_off[w][mid] <= t) lo = mid; else hi = mid - 1;
+            }
+            int64_t kb = s_bst[w][lo] + (t - s_off[w][lo]);
+            int32_t col = bci[kb];
+            double prod = s_av[w][lo] * bv[kb];
+            uint32_t h = hslot(col, HASH_SLOTS - 1);
+            for (int probe = 0; probe < HASH_SLOTS; ++probe) {
+                int32_t old = atomicCAS(&keys[h], -1, col);
+                if (old == -1 || old == col) { atomicAdd(&vals[h], prod); break; }
+                h = (h + 1) & (HASH_SLOTS - 1);
+            }
+        }
+        __syncwarp();
+    }
+    // compact the occupied slots in place (a lane's target never exceeds its own slot), then
+    // write each entry at its rank among the row's columns
+    int count = 0;
+    for (int t0 = 0; t0 < HASH_SLOTS; t0 += 32) {
+        int32_t k = keys[t0 + lane];
+        double vv = vals[t0 + lane];
+        unsigned m = __ballot_sync(0xffffffffu, k >= 0);
+        int pos = count + __popc(m & ((1u << lane) - 1u));
+        __syncwarp();
+        if (k >= 0) { keys[pos] = k; vals[pos] = vv; }
+        count += __popc(m);
+        __syncwarp();
+    }
+    for (int e = lane; e < count; e += 32) {
+        int32_t k = keys[e];
+        int rank = 0;
+        for (int u = 0; u < count; ++u) rank += (keys[u] < k);
+        cci[c0 + rank] = k;
+        cv[c0 + rank] = vals[e];
+    }
+}
+
+__global__ void k_spgemm_numeric_big(const int64_t* arp, const int32_t* aci, const double* av,
+                                     const int64_t* brp, const int32_t* bci, const double* bv,
+                                     const int32_t* list, int nlist, const int64_t* crp, int32_t* cci,
+                                     double* cv) {
+    extern __shared__ unsigned char smem_raw[];
+    int32_t* keys = (int32_t*)smem_raw;
+    double* vals = (double*)(smem_raw + sizeof(int32_t) * BIG_SLOTS);
+    __shared__ int32_t s_ck[1024];
+    for (int li = blockIdx.x; li < nlist; li += gridDim.x) {
+        int64_t i = list[li];
+        for (int t = threadIdx.x; t < BIG_SLOTS; t += blockDim.x) { keys[t] = -1; vals[t] = 0.0; }
+        __syncthreads();
+        for (int64_t ka = arp[i]; ka < arp[i + 1]; ++ka) {
+            int32_t k = aci[ka];
+            double a = av[ka];
+            for (int64_t kb = brp[k] + threadIdx.x; kb < brp[k + 1]; kb += blockDim.x) {
+                int32_t col = bci[kb];
+                uint32_t h = hslot(col, BIG_SLOTS - 1);
+                for (int probe = 0; probe < BIG_SLOTS; ++probe) {
+                    int32_t old = atomicCAS(&keys[h], -1, col);
+                    if (old == -1 || old == col) { atomicAdd(&vals[h], a * bv[kb]); break; }
+                    h = (h + 1) & (BIG_SLOTS - 1);
+                }
+            }
+        }
+        __syncthreads();
+        // rank by counting, comparing against the table in chunks staged in s_ck
+        int64_t c0 = crp[i];
+        for (int t0 = 0; t0 < BIG_SLOTS; t0 += blockDim.x) {
+            int t = t0 + threadIdx.x;
+            int32_t k = t < BIG_SLOTS ? keys[t] : -1;
+            int rank = 0;
+            for (int u0 = 0; u0 < BIG_SLOTS; u0 += 1024) {
+                __syncthreads();
+                for (int q = threadIdx.x; q < 1024; q += blockDim.x) s_ck[q] = keys[u0 + q];
+                __syncthreads();
+                if (k >= 0)
+                    for (int q = 0; q < 1024; ++q) rank += (s_ck[q] >= 0 && s_ck[q] < k);
+            }
+            if (k >= 0) {
+                cci[c0 + rank] = k;
+                cv[c0 + rank] = vals[t];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+int spgemm(const DCSR& A, const DCSR& B, DCSR& C, cudaStream_t s) {
+    if (A.nc != B.nr) {
+        set_error("spgemm: inner dimensions %lld vs %lld", (long long)A.nc, (long long)B.nr);
+        return SPHC_EINVAL;
+    }
+    int64_t n = A.nr;
+    DBuf<int64_t> ub, cnt;
+    DBuf<int32_t> big;
+    DBuf<int> bign, fail;
+    SPHC_TRY(ub.alloc(n + 1, s));
+    SPHC_TRY(cnt.alloc(n + 1, s));
+    SPHC_TRY(big.alloc(n + 1, s));
+    SPHC_TRY(bign.alloc(1, s));
+    SPHC_TRY(fail.alloc(1, s));
+    SPHC_TRY(bign.zero(s));
+    SPHC_TRY(fail.zero(s));
+    if (n > 0) {
+        k_spgemm_ub<<<grid_for(n, 256), 256, 0, s>>>(A.rp.p, A.ci.p, B.rp.p, n, ub.p);
+        k_spgemm_symbolic<<<grid_for(n, SPGEMM_WARPS), SPGEMM_WARPS * 32, 0, s>>>(
+            A.rp.p, A.ci.p, B.rp.p, B.ci.p, n, ub.p, cnt.p, big.p, bign.p);
+    }
+    SPHC_CK(cudaGetLastError());
+    int nbig = 0;
+    SPHC_CK(cudaMemcpyAsync(&nbig, bign.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SPHC_CK(cudaStreamSynchronize(s));
+    size_t big_sym_sm = sizeof(int32_t) * BIG_SLOTS;
+    size_t big_num_sm = (sizeof(int32_t) + sizeof(double)) * BIG_SLOTS;
+    if (nbig > 0) {
+        SPHC_CK(cudaFuncSetAttribute(k_spgemm_symbolic_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big_sym_sm));
+        k_spgemm_symbolic_big<<<nbig < 4096 ? nbig : 4096, 512, big_sym_sm, s>>>(
+            A.rp.p, A.ci.p, B.rp.p, B.ci.p, big.p, nbig, cnt.p, fail.p);
+        int f = 0;
+        SPHC_CK(cudaMemcpyAsync(&f, fail.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+        SPHC_CK(cudaStreamSynchronize(s));
+        if (f) {
+            set_error("spgemm: a product row has more than %d columns", BIG_FILL);
+            return SPHC_ELIMIT;
+        }
+    }
+    int64_t nnz = 0;
+    SPHC_TRY(C.alloc(n, B.nc, 0, s));
+    SPHC_TRY(exclusive_scan_i64(cnt.p, C.rp.p, n, s, &nnz));
+    C.nnz = nnz;
+    SPHC_TRY(C.ci.alloc(nnz, s));
+    SPHC_TRY(C.v.alloc(nnz, s));
+    size_t num_sm = (sizeof(int32_t) + sizeof(double)) * HASH_SLOTS * SPGEMM_WARPS;
+    SPHC_CK(cudaFuncSetAttribute(k_spgemm_numeric, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)num_sm));
+    if (n > 0)
+        k_spgemm_numeric<<<grid_for(n, SPGEMM_WARPS), SPGEMM_WARPS * 32, num_sm, s>>>(
+            A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p, B.v.p, n, C.rp.p, C.ci.p, C.v.p);
+    if (nbig > 0) {
+        SPHC_CK(cudaFuncSetAttribute(k_spgemm_numeric_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big_num_sm));
+        k_spgemm_numeric_big<<<nbig < 4096 ? nbig : 4096, 512, big_num_sm, s>>>(
+            A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p, B.v.p, big.p, nbig, C.rp.p, C.ci.p, C.v.p);
+    }
+    SPHC_CK(cudaGetLastError());
+    return SPHC_OK;
+}
+
+// ------------------------------------------------------------------ FP64 SpMV, dots
+__global__ void k_spmv64(const int64_t* rp, const int32_t* ci, const double* v, int64_t n, const double* x,
+                         double* y) {
+    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t i = g >> 3;
+    int sub = threadIdx.x & 7;
+    bool valid = i < n;
+    double s = 0.0;
+    if (valid)
+        for (int64_t k = rp[i] + sub; k < rp[i + 1]; k += 8) s += v[k] * x[ci[k]];
+    s += __shfl_xor_sync(0xffffffffu, s, 4);
+    s += __shfl_xor_sync(0xffffffffu, s, 2);
+    s += __shfl_xor_sync(0xffffffffu, s, 1);
+    if (valid && sub == 0) y[i] = s;
+}
+int spmv64(const DCSR& A, const double* x, double* y, cudaStream_t s) {
+    if (A.nr > 0) k_spmv64<<<grid_for(A.nr * 8, 256), 256, 0, s>>>(A.rp.p, A.ci.p, A.v.p, A.nr, x, y);
+    SPHC_CK(cudaGetLastError());
+    return SPHC_OK;
+}
+
+static constexpr int DOT_BLOCKS = 1024;
+__global__ void k_dot_part(const double* a, const double* b, int64_t n, double* part) {
+    __shared__ double sw[32];
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        s += a[i] * b[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = threadIdx.x < (blockDim.x >> 5) ? sw[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) part[blockIdx.x] = s;
+    }
+}
+__global__ void k_dot_final(const double* part, int np, double* out) {
+    __shared__ double sw[32];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < np; i += blockDim.x) s += part[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = threadIdx.x < (blockDim.x >> 5) ? sw[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) *out = s;
+    }
+}
+int dot64(const double* a, const double* b, int64_t n, double* result_dev, cudaStream_t s) {
+    DBuf<double> part;
+    SPHC_TRY(part.alloc(DOT_BLOCKS, s));
+    k_dot_part<<<DOT_BLOCKS, 256, 0, s>>>(a, b, n, part.p);
+    k_dot_final<<<1, 1024, 0, s>>>(part.p, DOT_BLOCKS, result_dev);
+    SPHC_CK(cudaGetLastError());
+    return SPHC_OK;
+}
+
+}  // namespace sphc

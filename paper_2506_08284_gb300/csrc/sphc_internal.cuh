@@ -1,0 +1,147 @@
+// Internal declarations of the sm_103a SpHcurlAMG library (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/sphc.h"
+
+namespace sphc {
+
+// ------------------------------------------------------------------ errors
+void set_error(const char* fmt, ...);
+const char* last_error();
+
+#define SPHC_CK(call)                                                                       \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess) {                                                            \
+            ::sphc::set_error("%s:%d: %s: %s", __FILE__, __LINE__, #call,                  \
+                              cudaGetErrorString(e_));                                     \
+            return SPHC_ECUDA;                                                              \
+        }                                                                                   \
+    } while (0)
+
+#define SPHC_TRY(call)                \
+    do {                              \
+        int rc_ = (call);             \
+        if (rc_ != SPHC_OK) return rc_; \
+    } while (0)
+
+// ------------------------------------------------------------------ stream-ordered buffers
+// Every device buffer of the library comes from cudaMallocAsync on the caller's stream and is
+// released with cudaFreeAsync on the same stream.
+// When set (only while a handle is destroyed), buffers are released with the synchronous
+// cudaFree so that no stream of the caller needs to be alive at that point.
+extern bool g_sync_free;
+
+template <typename T>
+struct DBuf {
+    T* p = nullptr;
+    int64_t n = 0;
+    cudaStream_t s = 0;
+    DBuf() = default;
+    DBuf(const DBuf&) = delete;
+    DBuf& operator=(const DBuf&) = delete;
+    DBuf(DBuf&& o) noexcept { *this = std::move(o); }
+    DBuf& operator=(DBuf&& o) noexcept {
+        if (this != &o) {
+            release();
+            p = o.p; n = o.n; s = o.s;
+            o.p = nullptr; o.n = 0;
+        }
+        return *this;
+    }
+    ~DBuf() { release(); }
+    void release() {
+        if (p) {
+            if (g_sync_free) cudaFree(p);
+            else cudaFreeAsync(p, s);
+        }
+        p = nullptr;
+        n = 0;
+    }
+    int alloc(int64_t count, cudaStream_t stream) {
+        release();
+        s = stream;
+        n = count;
+        if (count <= 0) return SPHC_OK;
+        cudaError_t e = cudaMallocAsync((void**)&p, sizeof(T) * (size_t)count, stream);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            n = 0;
+            set_error("cudaMallocAsync(%lld bytes): %s", (long long)(sizeof(T) * count), cudaGetErrorString(e));
+            return SPHC_ENOMEM;
+        }
+        return SPHC_OK;
+    }
+    int zero(cudaStream_t stream) {
+        if (n > 0) {
+            cudaError_t e = cudaMemsetAsync(p, 0, sizeof(T) * (size_t)n, stream);
+            if (e != cudaSuccess) {
+                set_error("cudaMemsetAsync: %s", cudaGetErrorString(e));
+                return SPHC_ECUDA;
+            }
+        }
+        return SPHC_OK;
+    }
+};
+
+// ------------------------------------------------------------------ device CSR
+// rowptr int64, col int32 (sorted within rows), values FP64.
+struct DCSR {
+    int64_t nr = 0, nc = 0, nnz = 0;
+    DBuf<int64_t> rp;
+    DBuf<int32_t> ci;
+    DBuf<double> v;
+    int alloc(int64_t rows, int64_t cols, int64_t nz, cudaStream_t s) {
+        nr = rows; nc = cols; nnz = nz;
+        SPHC_TRY(rp.alloc(rows + 1, s));
+        SPHC_TRY(ci.alloc(nz, s));
+        SPHC_TRY(v.alloc(nz, s));
+        return SPHC_OK;
+    }
+};
+
+// ------------------------------------------------------------------ sparse primitives (sparse.cu)
+int exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s, int64_t* total_host);
+// out[0..n] = exclusive prefix of int32 counts (out[n] = total)
+int scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, cudaStream_t s, int64_t* total_host);
+// C = A * B, structural (every reached entry kept), columns sorted, FP64 values.
+int spgemm(const DCSR& A, const DCSR& B, DCSR& C, cudaStream_t s);
+// At = A^T, rows sorted.
+int transpose(const DCSR& A, DCSR& At, cudaStream_t s);
+// copy a CSR
+int csr_copy(const DCSR& A, DCSR& B, cudaStream_t s);
+// diag(A) into d (FP64)
+int csr_diag(const DCSR& A, double* d, cudaStream_t s);
+// y = A x (FP64)
+int spmv64(const DCSR& A, const double* x, double* y, cudaStream_t s);
+// deterministic dot product into a device scalar
+int dot64(const double* a, const double* b, int64_t n, double* result_dev, cudaStream_t s);
+// sort each row segment [rp[i], rp[i+1]) of (key, val) pairs by key (keys unique per row)
+int segmented_sort(const int64_t* rp, int64_t nrows, int32_t* keys, double* vals, int64_t max_len,
+                   cudaStream_t s);
+int max_row_length(const int64_t* rp, int64_t nrows, cudaStream_t s, int64_t* out_host);
+
+// ------------------------------------------------------------------ misc device helpers
+__host__ __device__ inline uint64_t splitmix64(uint64_t seed, uint64_t counter) {
+    uint64_t z = seed + (counter + 1) * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+// priority comparison: larger hash wins, ties -> smaller id wins
+__device__ inline bool prio_greater(uint64_t ha, int64_t a, uint64_t hb, int64_t b) {
+    return ha > hb || (ha == hb && a < b);
+}
+
+inline int grid_for(int64_t n, int block) {
+    int64_t g = (n + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > 2147483647LL) g = 2147483647;
+    return (int)g;
+}
+
+}  // namespace sphc

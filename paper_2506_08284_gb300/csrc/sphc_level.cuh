@@ -1,0 +1,87 @@
+// Hierarchy data structures shared by the setup (setup.cu), the solve (solve.cu) and the C ABI.
+#pragma once
+#include "sphc_internal.cuh"
+
+namespace sphc {
+
+// Limits of the warp-per-row local kernels (documented in include/sphc.h).
+constexpr int MAX_T = 24;       // coarse nodes of one row of T (|J_i|)
+constexpr int MAX_NP = 128;     // coarse edges of one row of the pattern (|I_i|)
+constexpr int PAT_WARPS = 4;
+constexpr int LOC_WARPS = 4;
+// A smoothed nodal-prolongator row whose sum does not exceed this keeps its tentative values.
+constexpr double SA_MIN_ROWSUM = 0.125;
+
+// Operator of one smoother: rows grouped by colour (row k of the copy is row perm[k] of the
+// level operator), columns in natural numbering, int32 row pointers.
+template <typename T>
+struct SmoothOp {
+    int64_t n = 0, nnz = 0;
+    int ncolor = 0;
+    std::vector<int64_t> cstart;     // colour c owns copy rows [cstart[c], cstart[c+1])
+    DBuf<int32_t> rp, ci, perm;
+    DBuf<T> v, dinv;
+};
+
+// Plain CSR in the V-cycle precision (transfers).
+template <typename T>
+struct VCSR {
+    int64_t nr = 0, nc = 0, nnz = 0;
+    DBuf<int32_t> rp, ci;
+    DBuf<T> v;
+};
+
+template <typename T>
+struct VLevel {
+    SmoothOp<T> A, An;
+    DBuf<int2> D;                    // per edge: (node with -1, node with +1), -1 if absent
+    DBuf<int32_t> Dt_rp, Dt_e;       // D^T: per node the incident edges, (edge << 1) | (coef < 0)
+    VCSR<T> Pe, PeT;
+    DBuf<T> x, b, r, g, c;
+};
+
+struct Level {
+    DCSR A, D, An, Dt;
+    DBuf<int32_t> col_e, col_n;
+    int ncol_e = 0, ncol_n = 0;
+    // transfer data (absent on the coarsest level)
+    bool has_transfer = false;
+    DBuf<int32_t> agg;
+    int64_t nagg = 0;
+    DCSR Pn, DH, T, Pe, P0, PeT;
+    double rho = 0.0, omega_sa = 0.0;
+    int64_t n_added = 0, n_rows_unsmoothed = 0, max_np = 0, max_m = 0;
+    DBuf<unsigned long long> hist;   // 33 x 33 counts of (|N_i|, |T_i|)
+};
+
+// setup.cu
+int color_graph(const DCSR& G, uint64_t seed, DBuf<int32_t>& color, int* ncolors, cudaStream_t s);
+int aggregate(const DCSR& G, uint64_t seed, DBuf<int32_t>& agg, int64_t* nagg, cudaStream_t s);
+int power_rho(const DCSR& A, const double* diag, uint64_t seed, int iters, double* rho, cudaStream_t s);
+int coarse_gradient(const DCSR& D, const DCSR& Dt, const int32_t* agg, int64_t nagg, DCSR& DH, cudaStream_t s);
+int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext, DCSR& Annext, cudaStream_t s);
+int coarse_inverse(const DCSR& A, DBuf<double>& Ainv, cudaStream_t s);
+
+// solve.cu
+struct Hierarchy {
+    sphc_opts opts;
+    int nlev = 0;
+    std::vector<Level> L;
+    DBuf<double> coarse_inv;         // dense inverse of the coarsest operator (FP64)
+    int64_t n_coarse = 0;
+    // V-cycle copies in the chosen precision
+    std::vector<VLevel<float>> V32;
+    std::vector<VLevel<double>> V64;
+    // CG work vectors (FP64)
+    DBuf<double> x, r, z, p, q, rold, scal;
+    DBuf<double> cb, cx;             // coarsest right side / solution (FP64)
+    double setup_ms = 0.0, solve_ms = 0.0;
+    int last_iters = 0;
+    double last_relres = 0.0;
+};
+
+int build_vcycle_ops(Hierarchy& H, cudaStream_t s);
+int apply_vcycle(Hierarchy& H, const double* r, double* z, cudaStream_t s);
+int pcg_solve(Hierarchy& H, const double* b, double* x, double tol, cudaStream_t s, int* iters, double* relres);
+
+}  // namespace sphc

@@ -1,0 +1,204 @@
+"""Thin ctypes binding of libsphc.so (the C ABI of ``include/sphc.h``).
+
+Argument marshalling only: every step of the setup and the solve runs in the library's CUDA
+kernels.  PyTorch supplies device memory and streams.  There is no CPU fallback: loading fails
+loudly when the library cannot be built or loaded.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+SPHC_OK = 0
+ERRORS = {-1: "SPHC_EINVAL", -2: "SPHC_ENOMEM", -3: "SPHC_ECUDA", -4: "SPHC_ENOTCONV", -5: "SPHC_EBREAKDOWN",
+          -6: "SPHC_EINFEASIBLE", -7: "SPHC_ETIMEOUT", -8: "SPHC_ESTAGNATION", -9: "SPHC_ENUMERIC",
+          -10: "SPHC_ELIMIT"}
+X = dict(A=0, D=1, An=2, Pn=3, DH=4, T=5, Pe=6, P0=7, agg=16, col_e=17, col_n=18)
+
+
+class SphcError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class sphc_csr(ctypes.Structure):
+    _fields_ = [("nrows", ctypes.c_int64), ("ncols", ctypes.c_int64), ("rowptr", ctypes.c_void_p),
+                ("col", ctypes.c_void_p), ("val", ctypes.c_void_p)]
+
+
+class sphc_opts(ctypes.Structure):
+    _fields_ = [("max_levels", ctypes.c_int32), ("emin_iters", ctypes.c_int32), ("max_coarse", ctypes.c_int64),
+                ("emin_omega", ctypes.c_double), ("seed", ctypes.c_uint64), ("power_iters", ctypes.c_int32),
+                ("vcycle_fp32", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("flexible", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 7)]
+
+
+class sphc_level_info(ctypes.Structure):
+    _fields_ = [("n_edges", ctypes.c_int64), ("n_nodes", ctypes.c_int64), ("nnz_A", ctypes.c_int64),
+                ("nnz_An", ctypes.c_int64), ("n_aggregates", ctypes.c_int64), ("n_coarse_edges", ctypes.c_int64),
+                ("nnz_Pn", ctypes.c_int64), ("nnz_Pe", ctypes.c_int64), ("nnz_T", ctypes.c_int64),
+                ("n_colors_edge", ctypes.c_int32), ("n_colors_node", ctypes.c_int32),
+                ("n_added_edges", ctypes.c_int64), ("n_rows_unsmoothed", ctypes.c_int64),
+                ("rho", ctypes.c_double), ("omega_sa", ctypes.c_double), ("max_pattern_row", ctypes.c_int64),
+                ("max_T_row", ctypes.c_int64)]
+
+
+class sphc_stats(ctypes.Structure):
+    _fields_ = [("n_levels", ctypes.c_int32), ("operator_complexity", ctypes.c_double),
+                ("setup_ms", ctypes.c_double), ("solve_ms", ctypes.c_double), ("last_iters", ctypes.c_int32),
+                ("last_relres", ctypes.c_double), ("device_bytes", ctypes.c_int64)]
+
+
+EXPORTED = ["sphc_default_opts", "sphc_setup", "sphc_solve", "sphc_vcycle", "sphc_get_stats",
+            "sphc_get_level_info", "sphc_export_size", "sphc_export", "sphc_destroy", "sphc_last_error"]
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load (building first if needed) libsphc.so and declare its signatures."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    so = path or _build.build()
+    lib = ctypes.CDLL(so)
+    P, I, I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+    lib.sphc_default_opts.argtypes = [ctypes.POINTER(sphc_opts)]
+    lib.sphc_setup.argtypes = [ctypes.POINTER(sphc_csr), ctypes.POINTER(sphc_csr), P, P, ctypes.POINTER(sphc_opts),
+                               P, ctypes.POINTER(P)]
+    lib.sphc_solve.argtypes = [P, P, P, I, ctypes.c_double, P, P, P]
+    lib.sphc_vcycle.argtypes = [P, P, P, P]
+    lib.sphc_get_stats.argtypes = [P, ctypes.POINTER(sphc_stats)]
+    lib.sphc_get_level_info.argtypes = [P, I, ctypes.POINTER(sphc_level_info)]
+    lib.sphc_export_size.argtypes = [P, I, I, P, P, P]
+    lib.sphc_export.argtypes = [P, I, I, P, P, P, P, P]
+    lib.sphc_destroy.argtypes = [P]
+    lib.sphc_destroy.restype = None
+    lib.sphc_last_error.argtypes = []
+    lib.sphc_last_error.restype = ctypes.c_char_p
+    for name in EXPORTED:
+        if name not in ("sphc_destroy", "sphc_last_error"):
+            getattr(lib, name).restype = I
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _check(rc):
+    if rc != SPHC_OK:
+        raise SphcError(rc, load().sphc_last_error().decode())
+
+
+def _ptr(a):
+    """Data pointer of a numpy array or torch tensor (host or device), or None."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def default_opts(**kw) -> sphc_opts:
+    o = sphc_opts()
+    _check(load().sphc_default_opts(ctypes.byref(o)))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def make_csr(nrows, ncols, rowptr, col, val):
+    return sphc_csr(nrows, ncols, _ptr(rowptr), _ptr(col), _ptr(val))
+
+
+class Handle:
+    """An AMG hierarchy built by ``sphc_setup``; keeps the library handle."""
+
+    def __init__(self, ptr):
+        self._ptr = ctypes.c_void_p(ptr)
+
+    def __del__(self):
+        self.destroy()
+
+    def destroy(self):
+        if getattr(self, "_ptr", None) and self._ptr.value:
+            load().sphc_destroy(self._ptr)
+            self._ptr = ctypes.c_void_p(0)
+
+    @property
+    def ptr(self):
+        return self._ptr
+
+    def solve(self, b, x, tol=1e-8, nrhs=1, stream=None):
+        """b, x: FP64 arrays/tensors of nrhs x n_e.  Returns (status, iters[], relres[])."""
+        it = (ctypes.c_int * nrhs)()
+        rr = (ctypes.c_double * nrhs)()
+        rc = load().sphc_solve(self._ptr, _ptr(b), _ptr(x), nrhs, tol, _stream(stream), it, rr)
+        if rc not in (SPHC_OK, -4, -5, -8):
+            _check(rc)
+        return rc, list(it), list(rr)
+
+    def vcycle(self, r, z, stream=None):
+        _check(load().sphc_vcycle(self._ptr, _ptr(r), _ptr(z), _stream(stream)))
+
+    def stats(self) -> dict:
+        st = sphc_stats()
+        _check(load().sphc_get_stats(self._ptr, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in sphc_stats._fields_}
+
+    def level_info(self, level) -> dict:
+        li = sphc_level_info()
+        _check(load().sphc_get_level_info(self._ptr, level, ctypes.byref(li)))
+        return {k: getattr(li, k) for k, _ in sphc_level_info._fields_}
+
+    @property
+    def nlevels(self):
+        return self.stats()["n_levels"]
+
+    def export_size(self, level, what):
+        nr, nc, nz = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(load().sphc_export_size(self._ptr, level, X[what], ctypes.byref(nr), ctypes.byref(nc),
+                                       ctypes.byref(nz)))
+        return nr.value, nc.value, nz.value
+
+    def export(self, level, what, stream=None):
+        """Copy a level array to host numpy: CSR -> (rowptr, col, val, shape); vector -> int32 array."""
+        nr, nc, nz = self.export_size(level, what)
+        if X[what] >= 16:
+            out = np.empty(nr, np.int32)
+            _check(load().sphc_export(self._ptr, level, X[what], None, None, None, _ptr(out), _stream(stream)))
+            return out
+        rp = np.empty(nr + 1, np.int64)
+        ci = np.empty(nz, np.int32)
+        v = np.empty(nz, np.float64)
+        _check(load().sphc_export(self._ptr, level, X[what], _ptr(rp), _ptr(ci), _ptr(v), None, _stream(stream)))
+        return rp, ci, v, (nr, nc)
+
+
+def setup(A, D, coords=None, sigma_edge=None, opts=None, stream=None) -> Handle:
+    """A, D: (nrows, ncols, rowptr, col, val) with host (numpy) or device (torch) arrays."""
+    Ac = make_csr(*A)
+    Dc = make_csr(*D)
+    h = ctypes.c_void_p()
+    o = opts if opts is not None else default_opts()
+    _check(load().sphc_setup(ctypes.byref(Ac), ctypes.byref(Dc), _ptr(coords), _ptr(sigma_edge), ctypes.byref(o),
+                             _stream(stream), ctypes.byref(h)))
+    return Handle(h.value)

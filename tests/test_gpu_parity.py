@@ -1,0 +1,135 @@
+"""GPU library (through the C ABI) against the CPU oracle, element by element.
+
+Integer work (colours, aggregates, coarse gradients, patterns) must match bit for bit; FP64
+values to 1e-10 relative to the largest entry of each matrix; FP64 CG to the oracle's
+iteration count +-1 and solution to 1e-9; FP32 V-cycle solutions to 1e-6 of the FP64 oracle.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import meshgen
+from gpu_util import assert_csr_close, assert_csr_equal_pattern, gpu_setup, oracle_setup, problem
+
+pytestmark = pytest.mark.gpu
+
+FP64_RTOL = 1e-10
+CASES = {
+    "kuhn8": dict(),
+    "jit12": dict(max_coarse=200),
+    "box10": dict(max_coarse=100),
+}
+
+
+def _spec(name):
+    if name == "kuhn8":
+        return meshgen.workload("kuhn8")[0]
+    if name == "jit12":
+        return meshgen.MeshSpec(12, jitter=0.2, seed_jitter=4, sigma="lognormal", sigma_in=2.0, seed_sigma=5)
+    if name == "box10":
+        return meshgen.MeshSpec(10, jitter=0.15, seed_jitter=8, sigma="box", sigma_in=1.0, sigma_out=1e-3)
+    raise KeyError(name)
+
+
+@pytest.fixture(scope="module", params=sorted(CASES))
+def pair(request):
+    name = request.param
+    p = meshgen.generate(_spec(name))
+    opts = CASES[name]
+    h = gpu_setup(p, vcycle_fp32=0, **opts)
+    o = oracle_setup(p, **opts)
+    return name, p, h, o, opts
+
+
+def test_levels_match(pair):
+    _, p, h, o, _ = pair
+    assert h.nlevels == o.nlevels
+    for l in range(o.nlevels):
+        li, s = h.level_info(l), o.sizes(l)
+        assert li["n_edges"] == s["ne"] and li["n_nodes"] == s["nv"] and li["nnz_A"] == s["nnzA"]
+        assert li["n_colors_edge"] == s["ncol_e"] and li["n_colors_node"] == s["ncol_n"]
+
+
+def test_integer_setup_is_bit_exact(pair):
+    _, p, h, o, _ = pair
+    for l in range(o.nlevels):
+        np.testing.assert_array_equal(h.export(l, "col_e"), o.ivec(l, "col_e"))
+        np.testing.assert_array_equal(h.export(l, "col_n"), o.ivec(l, "col_n"))
+        if not o.sizes(l)["has_transfer"]:
+            continue
+        np.testing.assert_array_equal(h.export(l, "agg"), o.ivec(l, "agg"))
+        assert_csr_close(h.export(l, "DH"), o.matrix(l, "DH"), f"L{l} D_H", 0.0)
+        assert_csr_equal_pattern(h.export(l, "T"), o.matrix(l, "T"), f"L{l} T")
+        assert_csr_equal_pattern(h.export(l, "Pe"), o.matrix(l, "Pe"), f"L{l} N")
+        assert_csr_equal_pattern(h.export(l, "Pn"), o.matrix(l, "Pn"), f"L{l} P_n pattern")
+
+
+def test_fp64_setup_values(pair):
+    _, p, h, o, _ = pair
+    for l in range(o.nlevels):
+        assert_csr_close(h.export(l, "A"), o.matrix(l, "A"), f"L{l} A", FP64_RTOL)
+        assert_csr_close(h.export(l, "An"), o.matrix(l, "An"), f"L{l} A_n", FP64_RTOL)
+        if not o.sizes(l)["has_transfer"]:
+            continue
+        assert h.level_info(l)["rho"] == pytest.approx(o.scalars(l)["rho"], rel=1e-12)
+        for what in ("Pn", "T", "P0", "Pe"):
+            assert_csr_close(h.export(l, what), o.matrix(l, what), f"L{l} {what}", FP64_RTOL)
+
+
+def test_commuting_relation_on_gpu_prolongators(pair):
+    _, p, h, o, _ = pair
+    for l in range(h.nlevels - 1):
+        M = {}
+        for what in ("Pe", "DH", "D", "Pn"):
+            rp, ci, v, shape = h.export(l, what)
+            M[what] = sp.csr_matrix((v, ci, rp), shape=shape)
+        rhs = M["D"] @ M["Pn"]
+        assert abs(M["Pe"] @ M["DH"] - rhs).max() <= 1e-12 * max(1.0, abs(rhs).max())
+
+
+def test_fp64_solve_matches_oracle(pair):
+    name, p, h, o, _ = pair
+    b = meshgen.rhs(3, p.n_edges)
+    x = np.zeros_like(b)
+    rc, it, rr = h.solve(b, x, tol=1e-8)
+    ref = o.solve(b, tol=1e-8)
+    assert rc == 0 and ref["status"] == 0
+    assert abs(it[0] - ref["iters"]) <= 1
+    assert rr[0] <= 1e-8 * 1.01
+    assert np.linalg.norm(x - ref["x"]) <= 1e-9 * np.linalg.norm(ref["x"])
+
+
+def test_fp64_vcycle_matches_oracle(pair):
+    _, p, h, o, _ = pair
+    import torch
+    r = meshgen.rhs(11, p.n_edges)
+    rt = torch.tensor(r, device="cuda")
+    zt = torch.empty_like(rt)
+    h.vcycle(rt, zt)
+    torch.cuda.synchronize()
+    z = zt.cpu().numpy()
+    zo = o.vcycle(r)
+    assert np.abs(z - zo).max() <= FP64_RTOL * np.abs(zo).max()
+
+
+def test_fp32_vcycle_solve(pair):
+    name, p, h, o, opts = pair
+    h32 = gpu_setup(p, vcycle_fp32=1, **opts)
+    b = meshgen.rhs(5, p.n_edges)
+    x = np.zeros_like(b)
+    rc, it, rr = h32.solve(b, x, tol=1e-8)
+    ref = o.solve(b, tol=1e-8)
+    assert rc == 0 and rr[0] <= 1.01e-8
+    assert np.linalg.norm(x - ref["x"]) <= 1e-6 * np.linalg.norm(ref["x"])
+    assert it[0] <= ref["iters"] + 3
+
+
+def test_histogram_and_limits(pair):
+    _, p, h, o, _ = pair
+    for l in range(o.nlevels - 1):
+        li = h.level_info(l)
+        H = o.hist(l)
+        m_max = int(np.nonzero(H.sum(0))[0].max())
+        n_max = int(np.nonzero(H.sum(1))[0].max())
+        assert li["max_T_row"] == m_max
+        assert li["max_pattern_row"] == n_max or n_max == 32
