@@ -66,7 +66,8 @@ typedef struct {
     int32_t vcycle_fp32;     /* 1: V-cycle in FP32 inside FP64 CG; 0: all FP64 (default 1) */
     int32_t max_iter;        /* CG iteration cap (default 500) */
     int32_t flexible;        /* 1: flexible (Polak-Ribiere) CG beta; 0: Fletcher-Reeves (default: = vcycle_fp32) */
-    int32_t reserved[7];
+    int32_t profile;         /* 1: record CUDA-event section timers (sphc_get_profile) (default 0) */
+    int32_t reserved[6];
 } sphc_opts;
 
 typedef struct sphc_handle sphc_handle;
@@ -95,6 +96,16 @@ typedef struct {
     double last_relres;              /* true relative residual of the last solve (first RHS) */
     int64_t device_bytes;            /* bytes held by the handle */
 } sphc_stats;
+
+/* One section timer of the profile (opts.profile = 1): total device time of the section's
+ * calls, measured with CUDA events on the work stream, and the algorithmic bytes one call moves
+ * (0 where no byte count is defined). */
+typedef struct {
+    char name[32];
+    double ms;
+    int64_t calls;
+    double bytes_per_call;
+} sphc_timer;
 
 /* Export ids for sphc_export_size / sphc_export (per level). */
 enum {
@@ -155,6 +166,13 @@ SPHC_API int sphc_export(const sphc_handle* h, int level, int what, int64_t* row
 
 /* Release the handle and every device buffer it owns (NULL is ignored). */
 SPHC_API void sphc_destroy(sphc_handle* h);
+
+/* Copy up to max timers of the handle's profile into out (host memory); *n receives the number
+ * of timers.  Synchronises on the recorded events.  Timers accumulate over the handle's life. */
+SPHC_API int sphc_get_profile(sphc_handle* h, sphc_timer* out, int max, int* n);
+
+/* Number of kernels the library has launched in this process so far. */
+SPHC_API int64_t sphc_launch_count(void);
 
 /* Thread-local message of the last error ("" if none). */
 SPHC_API const char* sphc_last_error(void);

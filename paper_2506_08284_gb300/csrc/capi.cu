@@ -77,7 +77,7 @@ int validate(const DCSR& M, int gradient, const char* name, cudaStream_t s) {
     DBuf<int> f;
     SPHC_TRY(f.alloc(5, s));
     SPHC_TRY(f.zero(s));
-    if (M.nr > 0) k_validate<<<grid_for(M.nr, 256), 256, 0, s>>>(M.rp.p, M.ci.p, M.v.p, M.nr, M.nc, M.nnz, gradient, f.p);
+    if (M.nr > 0) SPHC_LAUNCH(k_validate<<<grid_for(M.nr, 256), 256, 0, s>>>(M.rp.p, M.ci.p, M.v.p, M.nr, M.nc, M.nnz, gradient, f.p));
     int h[5];
     SPHC_CK(cudaMemcpyAsync(h, f.p, sizeof(h), cudaMemcpyDeviceToHost, s));
     SPHC_CK(cudaStreamSynchronize(s));
@@ -124,7 +124,7 @@ int setup_impl(sphc_handle* h, const sphc_csr* A_e, const sphc_csr* D_h, cudaStr
         bool coarsest = L.A.nr <= o.max_coarse || lev + 1 >= o.max_levels || L.An.nr <= 1;
         if (coarsest) break;
         DCSR A1, D1, An1;
-        SPHC_TRY(build_level(L, lev, o, A1, D1, An1, s));
+        SPHC_TRY(build_level(L, lev, o, A1, D1, An1, H.prof.on && lev == 0 ? &H.prof : nullptr, s));
         if (L.nagg >= L.An.nr) break;      // no coarsening: this level is solved directly
         L.has_transfer = true;
         H.L.emplace_back();
@@ -187,6 +187,7 @@ int sphc_setup(const sphc_csr* A_e, const sphc_csr* D_h, const double* coords, c
         return SPHC_EINVAL;
     }
     cudaGetDevice(&h->device);
+    h->H.prof.on = o.profile != 0;
     cudaStream_t s = (cudaStream_t)stream;
     auto t0 = std::chrono::steady_clock::now();
     int rc = setup_impl(h, A_e, D_h, s);
@@ -385,6 +386,26 @@ void sphc_destroy(sphc_handle* h) {
     g_sync_free = false;
     cudaSetDevice(dev);
 }
+
+int sphc_get_profile(sphc_handle* h, sphc_timer* out, int max, int* n) {
+    if (!h || (max > 0 && !out) || !n) {
+        set_error("sphc_get_profile: invalid argument");
+        return SPHC_EINVAL;
+    }
+    Profiler& P = h->H.prof;
+    P.resolve();
+    *n = (int)P.timers.size();
+    for (int i = 0; i < max && i < (int)P.timers.size(); ++i) {
+        memset(&out[i], 0, sizeof(sphc_timer));
+        strncpy(out[i].name, P.timers[i].name.c_str(), sizeof(out[i].name) - 1);
+        out[i].ms = P.timers[i].ms;
+        out[i].calls = P.timers[i].calls;
+        out[i].bytes_per_call = P.timers[i].bytes;
+    }
+    return SPHC_OK;
+}
+
+int64_t sphc_launch_count(void) { return (int64_t)g_launches.load(); }
 
 const char* sphc_last_error(void) { return sphc::last_error(); }
 

@@ -54,21 +54,21 @@ int color_graph(const DCSR& G, uint64_t seed, DBuf<int32_t>& color, int* ncolors
     int64_t n = G.nr;
     SPHC_TRY(color.alloc(n, s));
     if (n == 0) { *ncolors = 0; return SPHC_OK; }
-    k_fill_i32<<<grid_for(n, 256), 256, 0, s>>>(color.p, n, -1);
+    SPHC_LAUNCH(k_fill_i32<<<grid_for(n, 256), 256, 0, s>>>(color.p, n, -1));
     DBuf<int> flags;
     SPHC_TRY(flags.alloc(3, s));
     SPHC_TRY(flags.zero(s));
     int h[3];
     for (int round = 0; round < 100000; ++round) {
         SPHC_CK(cudaMemsetAsync(flags.p, 0, sizeof(int), s));
-        k_jp_round<<<grid_for(n, 256), 256, 0, s>>>(G.rp.p, G.ci.p, n, seed, color.p, flags.p, flags.p + 1);
+        SPHC_LAUNCH(k_jp_round<<<grid_for(n, 256), 256, 0, s>>>(G.rp.p, G.ci.p, n, seed, color.p, flags.p, flags.p + 1));
         SPHC_CK(cudaMemcpyAsync(h, flags.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
         SPHC_CK(cudaStreamSynchronize(s));
         if (h[1]) { set_error("colouring needs more than %d colours", MAX_COLORS); return SPHC_ELIMIT; }
         if (h[0] == 0) break;
     }
     SPHC_CK(cudaMemsetAsync(flags.p + 2, 0, sizeof(int), s));
-    k_max_i32<<<grid_for(n, 256), 256, 0, s>>>(color.p, n, flags.p + 2);
+    SPHC_LAUNCH(k_max_i32<<<grid_for(n, 256), 256, 0, s>>>(color.p, n, flags.p + 2));
     SPHC_CK(cudaMemcpyAsync(h + 2, flags.p + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
     SPHC_CK(cudaStreamSynchronize(s));
     *ncolors = h[2] + 1;
@@ -181,10 +181,10 @@ int aggregate(const DCSR& G, uint64_t seed, DBuf<int32_t>& agg, int64_t* nagg, c
     SPHC_TRY(flags.alloc(2, s));
     int h[2];
     for (int round = 0; round < 100000; ++round) {
-        k_mis2_select<<<grid_for(n, 256), 256, 0, s>>>(G.rp.p, G.ci.p, n, seed, state.p);
-        k_mis2_mark<<<grid_for(n, 256), 256, 0, s>>>(G.rp.p, G.ci.p, n, state.p, flags.p);
+        SPHC_LAUNCH(k_mis2_select<<<grid_for(n, 256), 256, 0, s>>>(G.rp.p, G.ci.p, n, seed, state.p));
+        SPHC_LAUNCH(k_mis2_mark<<<grid_for(n, 256), 256, 0, s>>>(G.rp.p, G.ci.p, n, state.p, flags.p));
         SPHC_CK(cudaMemsetAsync(flags.p, 0, sizeof(int), s));
-        k_mis2_commit<<<grid_for(n, 256), 256, 0, s>>>(state.p, n, flags.p);
+        SPHC_LAUNCH(k_mis2_commit<<<grid_for(n, 256), 256, 0, s>>>(state.p, n, flags.p));
         SPHC_CK(cudaMemcpyAsync(h, flags.p, sizeof(int), cudaMemcpyDeviceToHost, s));
         SPHC_CK(cudaStreamSynchronize(s));
         if (h[0] == 0) break;
@@ -192,14 +192,14 @@ int aggregate(const DCSR& G, uint64_t seed, DBuf<int32_t>& agg, int64_t* nagg, c
     DBuf<int64_t> flag, rid;
     SPHC_TRY(flag.alloc(n, s));
     SPHC_TRY(rid.alloc(n + 1, s));
-    k_root_flags<<<grid_for(n, 256), 256, 0, s>>>(state.p, n, flag.p);
+    SPHC_LAUNCH(k_root_flags<<<grid_for(n, 256), 256, 0, s>>>(state.p, n, flag.p));
     SPHC_TRY(exclusive_scan_i64(flag.p, rid.p, n, s, nagg));
     DBuf<int32_t> tmp;
     SPHC_TRY(tmp.alloc(n, s));
-    k_agg_phase2<<<grid_for(n, 256), 256, 0, s>>>(G.rp.p, G.ci.p, n, state.p, rid.p, agg.p);
+    SPHC_LAUNCH(k_agg_phase2<<<grid_for(n, 256), 256, 0, s>>>(G.rp.p, G.ci.p, n, state.p, rid.p, agg.p));
     for (int round = 0; round < 64; ++round) {
         SPHC_CK(cudaMemsetAsync(flags.p, 0, 2 * sizeof(int), s));
-        k_agg_phase3<<<grid_for(n, 256), 256, 0, s>>>(G.rp.p, G.ci.p, n, agg.p, tmp.p, flags.p, flags.p + 1);
+        SPHC_LAUNCH(k_agg_phase3<<<grid_for(n, 256), 256, 0, s>>>(G.rp.p, G.ci.p, n, agg.p, tmp.p, flags.p, flags.p + 1));
         std::swap(agg.p, tmp.p);
         SPHC_CK(cudaMemcpyAsync(h, flags.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
         SPHC_CK(cudaStreamSynchronize(s));
@@ -232,14 +232,14 @@ int power_rho(const DCSR& A, const double* diag, uint64_t seed, int iters, doubl
     SPHC_TRY(v.alloc(n, s));
     SPHC_TRY(w.alloc(n, s));
     SPHC_TRY(sc.alloc(2, s));
-    k_uniform_vec<<<grid_for(n, 256), 256, 0, s>>>(v.p, n, seed);
+    SPHC_LAUNCH(k_uniform_vec<<<grid_for(n, 256), 256, 0, s>>>(v.p, n, seed));
     double h[2] = {1.0, 1.0};
     for (int it = 0; it < iters; ++it) {
         SPHC_TRY(spmv64(A, v.p, w.p, s));
-        k_scale_dinv<<<grid_for(n, 256), 256, 0, s>>>(w.p, diag, n);
+        SPHC_LAUNCH(k_scale_dinv<<<grid_for(n, 256), 256, 0, s>>>(w.p, diag, n));
         SPHC_TRY(dot64(v.p, v.p, n, sc.p, s));
         SPHC_TRY(dot64(w.p, w.p, n, sc.p + 1, s));
-        k_normalise<<<grid_for(n, 256), 256, 0, s>>>(v.p, w.p, sc.p + 1, n);
+        SPHC_LAUNCH(k_normalise<<<grid_for(n, 256), 256, 0, s>>>(v.p, w.p, sc.p + 1, n));
     }
     SPHC_CK(cudaMemcpyAsync(h, sc.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
     SPHC_CK(cudaStreamSynchronize(s));
@@ -367,10 +367,10 @@ int coarse_gradient(const DCSR& D, const DCSR& Dt, const int32_t* agg, int64_t n
     SPHC_TRY(mptr.alloc(nagg + 1, s));
     SPHC_TRY(members.alloc(nv, s));
     SPHC_TRY(cur.alloc(nagg + 1, s));
-    if (nv > 0) k_count_agg<<<grid_for(nv, 256), 256, 0, s>>>(agg, nv, cnt.p);
+    if (nv > 0) SPHC_LAUNCH(k_count_agg<<<grid_for(nv, 256), 256, 0, s>>>(agg, nv, cnt.p));
     SPHC_TRY(scan_i32_to_i64(cnt.p, mptr.p, nagg, s, nullptr));
-    k_i64_to_u64b<<<grid_for(nagg + 1, 256), 256, 0, s>>>(mptr.p, cur.p, nagg + 1);
-    if (nv > 0) k_scatter_agg<<<grid_for(nv, 256), 256, 0, s>>>(agg, nv, cur.p, members.p);
+    SPHC_LAUNCH(k_i64_to_u64b<<<grid_for(nagg + 1, 256), 256, 0, s>>>(mptr.p, cur.p, nagg + 1));
+    if (nv > 0) SPHC_LAUNCH(k_scatter_agg<<<grid_for(nv, 256), 256, 0, s>>>(agg, nv, cur.p, members.p));
     DBuf<int64_t> c2, off2;
     DBuf<int> fail;
     SPHC_TRY(c2.alloc(nagg + 1, s));
@@ -378,9 +378,9 @@ int coarse_gradient(const DCSR& D, const DCSR& Dt, const int32_t* agg, int64_t n
     SPHC_TRY(fail.alloc(1, s));
     SPHC_TRY(fail.zero(s));
     if (nagg > 0)
-        k_dh_rows<<<grid_for(nagg, DH_WARPS), DH_WARPS * 32, 0, s>>>(nagg, mptr.p, members.p, Dt.rp.p, Dt.ci.p, D.rp.p,
+        SPHC_LAUNCH(k_dh_rows<<<grid_for(nagg, DH_WARPS), DH_WARPS * 32, 0, s>>>(nagg, mptr.p, members.p, Dt.rp.p, Dt.ci.p, D.rp.p,
                                                                     D.ci.p, agg, 0, c2.p, nullptr, nullptr, nullptr,
-                                                                    fail.p);
+                                                                    fail.p));
     int64_t n2 = 0;
     SPHC_TRY(exclusive_scan_i64(c2.p, off2.p, nagg, s, &n2));
     int f = 0;
@@ -391,16 +391,16 @@ int coarse_gradient(const DCSR& D, const DCSR& Dt, const int32_t* agg, int64_t n
     SPHC_TRY(sflag.alloc(nagg + 1, s));
     SPHC_TRY(sflag.zero(s));
     SPHC_TRY(sid.alloc(nagg + 1, s));
-    if (ne > 0) k_single_flags<<<grid_for(ne, 256), 256, 0, s>>>(D.rp.p, D.ci.p, ne, agg, sflag.p);
+    if (ne > 0) SPHC_LAUNCH(k_single_flags<<<grid_for(ne, 256), 256, 0, s>>>(D.rp.p, D.ci.p, ne, agg, sflag.p));
     int64_t n1 = 0;
     SPHC_TRY(exclusive_scan_i64(sflag.p, sid.p, nagg, s, &n1));
     SPHC_TRY(DH.alloc(n2 + n1, nagg, 2 * n2 + n1, s));
-    k_dh_rowptr<<<grid_for(n2 + n1 + 1, 256), 256, 0, s>>>(n2, n1, DH.rp.p);
+    SPHC_LAUNCH(k_dh_rowptr<<<grid_for(n2 + n1 + 1, 256), 256, 0, s>>>(n2, n1, DH.rp.p));
     if (nagg > 0) {
-        k_dh_rows<<<grid_for(nagg, DH_WARPS), DH_WARPS * 32, 0, s>>>(nagg, mptr.p, members.p, Dt.rp.p, Dt.ci.p, D.rp.p,
+        SPHC_LAUNCH(k_dh_rows<<<grid_for(nagg, DH_WARPS), DH_WARPS * 32, 0, s>>>(nagg, mptr.p, members.p, Dt.rp.p, Dt.ci.p, D.rp.p,
                                                                     D.ci.p, agg, 1, nullptr, off2.p, DH.ci.p, DH.v.p,
-                                                                    fail.p);
-        k_dh_singles<<<grid_for(nagg, 256), 256, 0, s>>>(sflag.p, sid.p, nagg, n2, DH.ci.p, DH.v.p);
+                                                                    fail.p));
+        SPHC_LAUNCH(k_dh_singles<<<grid_for(nagg, 256), 256, 0, s>>>(sflag.p, sid.p, nagg, n2, DH.ci.p, DH.v.p));
     }
     SPHC_CK(cudaGetLastError());
     return SPHC_OK;
@@ -749,15 +749,15 @@ int coarse_inverse(const DCSR& A, DBuf<double>& Ainv, cudaStream_t s) {
     DBuf<int> bad;
     SPHC_TRY(bad.alloc(1, s));
     SPHC_TRY(bad.zero(s));
-    k_dense_from_csr<<<grid_for(n, 128), 128, 0, s>>>(A.rp.p, A.ci.p, A.v.p, n, M.p);
+    SPHC_LAUNCH(k_dense_from_csr<<<grid_for(n, 128), 128, 0, s>>>(A.rp.p, A.ci.p, A.v.p, n, M.p));
     for (int j = 0; j < n; ++j) {
-        k_chol_col<<<1, 256, 0, s>>>(M.p, (int)n, j, bad.p);
+        SPHC_LAUNCH(k_chol_col<<<1, 256, 0, s>>>(M.p, (int)n, j, bad.p));
         int64_t rem = n - j - 1;
-        if (rem > 0) k_chol_update<<<grid_for(rem * rem, 256), 256, 0, s>>>(M.p, (int)n, j);
+        if (rem > 0) SPHC_LAUNCH(k_chol_update<<<grid_for(rem * rem, 256), 256, 0, s>>>(M.p, (int)n, j));
     }
     size_t sm = sizeof(double) * n;
     if (sm > 48 * 1024) SPHC_CK(cudaFuncSetAttribute(k_chol_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_chol_inverse<<<(unsigned)n, 256, sm, s>>>(M.p, (int)n, Ainv.p);
+    SPHC_LAUNCH(k_chol_inverse<<<(unsigned)n, 256, sm, s>>>(M.p, (int)n, Ainv.p));
     SPHC_CK(cudaGetLastError());
     int hb = 0;
     SPHC_CK(cudaMemcpyAsync(&hb, bad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -767,7 +767,8 @@ int coarse_inverse(const DCSR& A, DBuf<double>& Ainv, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------------ one level of Alg. 3
-int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext, DCSR& Annext, cudaStream_t s) {
+int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext, DCSR& Annext, Profiler* prof,
+                cudaStream_t s) {
     uint64_t seed = o.seed + 1000ULL * (uint64_t)lev;
     int64_t nv = L.An.nr, ne = L.A.nr;
     // aggregation on the structural nodal graph (drop tolerance 0)
@@ -780,14 +781,14 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
     L.omega_sa = 4.0 / (3.0 * L.rho);
     DCSR Pb;
     SPHC_TRY(Pb.alloc(nv, L.nagg, nv, s));
-    k_pbar<<<grid_for(nv + 1, 256), 256, 0, s>>>(nv, L.agg.p, Pb.rp.p, Pb.ci.p, Pb.v.p);
+    SPHC_LAUNCH(k_pbar<<<grid_for(nv + 1, 256), 256, 0, s>>>(nv, L.agg.p, Pb.rp.p, Pb.ci.p, Pb.v.p));
     SPHC_TRY(spgemm(L.An, Pb, L.Pn, s));
     DBuf<int> fl;
     SPHC_TRY(fl.alloc(2, s));
     SPHC_TRY(fl.zero(s));
     if (nv > 0)
-        k_pn_finish<<<grid_for(nv, 256), 256, 0, s>>>(L.Pn.rp.p, L.Pn.ci.p, L.Pn.v.p, nv, L.agg.p, dn.p, L.omega_sa, 1,
-                                                     fl.p, fl.p + 1);
+        SPHC_LAUNCH(k_pn_finish<<<grid_for(nv, 256), 256, 0, s>>>(L.Pn.rp.p, L.Pn.ci.p, L.Pn.v.p, nv, L.agg.p, dn.p, L.omega_sa, 1,
+                                                     fl.p, fl.p + 1));
     int hf[2];
     SPHC_CK(cudaMemcpyAsync(hf, fl.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
     SPHC_CK(cudaStreamSynchronize(s));
@@ -805,9 +806,9 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
     SPHC_TRY(st.alloc(8, s));
     SPHC_TRY(st.zero(s));
     if (ne > 0)
-        k_pattern<<<grid_for(ne, PAT_WARPS), PAT_WARPS * 32, 0, s>>>(L.T.rp.p, L.T.ci.p, ne, DHt.rp.p, DHt.ci.p,
+        SPHC_LAUNCH(k_pattern<<<grid_for(ne, PAT_WARPS), PAT_WARPS * 32, 0, s>>>(L.T.rp.p, L.T.ci.p, ne, DHt.rp.p, DHt.ci.p,
                                                                     L.DH.rp.p, L.DH.ci.p, 0, ncnt.p, nullptr, nullptr,
-                                                                    st.p);
+                                                                    st.p));
     int hs[8];
     SPHC_CK(cudaMemcpyAsync(hs, st.p, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
     SPHC_CK(cudaStreamSynchronize(s));
@@ -827,9 +828,9 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
     SPHC_TRY(L.P0.ci.alloc(nnzN, s));
     SPHC_TRY(L.P0.v.alloc(nnzN, s));
     if (ne > 0)
-        k_pattern<<<grid_for(ne, PAT_WARPS), PAT_WARPS * 32, 0, s>>>(L.T.rp.p, L.T.ci.p, ne, DHt.rp.p, DHt.ci.p,
+        SPHC_LAUNCH(k_pattern<<<grid_for(ne, PAT_WARPS), PAT_WARPS * 32, 0, s>>>(L.T.rp.p, L.T.ci.p, ne, DHt.rp.p, DHt.ci.p,
                                                                     L.DH.rp.p, L.DH.ci.p, 1, nullptr, L.P0.rp.p,
-                                                                    L.P0.ci.p, st.p);
+                                                                    L.P0.ci.p, st.p));
     // initial guess and energy minimisation
     SPHC_TRY(L.hist.alloc(33 * 33, s));
     SPHC_TRY(L.hist.zero(s));
@@ -838,17 +839,24 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
     SPHC_CK(cudaFuncSetAttribute(k_p0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     SPHC_CK(cudaFuncSetAttribute(k_emin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     if (ne > 0)
-        k_p0<<<grid_for(ne, LOC_WARPS), LOC_WARPS * 32, sm, s>>>(ne, L.T.rp.p, L.T.ci.p, L.T.v.p, L.P0.rp.p, L.P0.ci.p,
+        SPHC_LAUNCH(k_p0<<<grid_for(ne, LOC_WARPS), LOC_WARPS * 32, sm, s>>>(ne, L.T.rp.p, L.T.ci.p, L.T.v.p, L.P0.rp.p, L.P0.ci.p,
                                                                   L.DH.rp.p, L.DH.ci.p, L.DH.v.p, L.P0.v.p, st.p,
-                                                                  L.hist.p);
+                                                                  L.hist.p));
     SPHC_TRY(csr_copy(L.P0, L.Pe, s));
     DBuf<double> Pnew;
     SPHC_TRY(Pnew.alloc(nnzN, s));
+    // algorithmic bytes of one step: A (values, columns, row pointers), the pattern rows of P
+    // (columns, values), T (columns, values), the new values and two coarse-edge ends per entry
+    double emin_bytes = (double)L.A.nnz * 12.0 + (double)ne * 8.0 * 3 + (double)nnzN * (4 + 8 + 8 + 8) +
+                        (double)L.T.nnz * 12.0;
+    int tid = prof ? prof->find("emin_level0", emin_bytes) : -1;
     for (int it = 0; it < o.emin_iters; ++it) {
+        if (tid >= 0) prof->begin(tid, s);
         if (ne > 0)
-            k_emin<<<grid_for(ne, LOC_WARPS), LOC_WARPS * 32, sm, s>>>(
+            SPHC_LAUNCH(k_emin<<<grid_for(ne, LOC_WARPS), LOC_WARPS * 32, sm, s>>>(
                 ne, L.A.rp.p, L.A.ci.p, L.A.v.p, L.T.rp.p, L.T.ci.p, L.T.v.p, L.Pe.rp.p, L.Pe.ci.p, L.DH.rp.p,
-                L.DH.ci.p, L.DH.v.p, L.Pe.v.p, Pnew.p, o.emin_omega, st.p);
+                L.DH.ci.p, L.DH.v.p, L.Pe.v.p, Pnew.p, o.emin_omega, st.p));
+        if (tid >= 0) prof->end(tid, s);
         std::swap(L.Pe.v.p, Pnew.p);
     }
     SPHC_CK(cudaMemcpyAsync(hs, st.p, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -857,9 +865,12 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
     // Galerkin operators of the next level
     SPHC_TRY(transpose(L.Pe, L.PeT, s));
     {
+        int rid = prof ? prof->find("rap_level0", 0.0) : -1;
+        if (rid >= 0) prof->begin(rid, s);
         DCSR AP;
         SPHC_TRY(spgemm(L.A, L.Pe, AP, s));
         SPHC_TRY(spgemm(L.PeT, AP, Anext, s));
+        if (rid >= 0) prof->end(rid, s);
     }
     {
         DCSR PnT, AnP;

@@ -9,6 +9,48 @@
 
 namespace sphc {
 
+// ------------------------------------------------------------------ section timers
+int Profiler::find(const char* name, double bytes) {
+    for (size_t i = 0; i < timers.size(); ++i)
+        if (timers[i].name == name) return (int)i;
+    timers.emplace_back();
+    timers.back().name = name;
+    timers.back().bytes = bytes;
+    return (int)timers.size() - 1;
+}
+void Profiler::begin(int id, cudaStream_t s) {
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, s);
+    timers[id].pending.push_back({a, b});
+}
+void Profiler::end(int id, cudaStream_t s) {
+    cudaEventRecord(timers[id].pending.back().second, s);
+    timers[id].calls++;
+}
+int Profiler::resolve() {
+    for (auto& t : timers) {
+        for (auto& pr : t.pending) {
+            float ms = 0.f;
+            cudaEventSynchronize(pr.second);
+            cudaEventElapsedTime(&ms, pr.first, pr.second);
+            t.ms += ms;
+            cudaEventDestroy(pr.first);
+            cudaEventDestroy(pr.second);
+        }
+        t.pending.clear();
+    }
+    return SPHC_OK;
+}
+Profiler::~Profiler() {
+    for (auto& t : timers)
+        for (auto& pr : t.pending) {
+            cudaEventDestroy(pr.first);
+            cudaEventDestroy(pr.second);
+        }
+}
+
 // ------------------------------------------------------------------ stable colour partition
 static constexpr int PART_BLOCK = 1024;
 static constexpr int PART_MAXC = 256;
@@ -52,7 +94,7 @@ static int colour_partition(const int32_t* color, int64_t n, int ncolor, DBuf<in
     DBuf<int64_t> table64, off;
     SPHC_TRY(table.alloc(ncolor * nb, s));
     SPHC_TRY(off.alloc(ncolor * nb + 1, s));
-    if (n > 0) k_part_count<<<(unsigned)nb, PART_BLOCK, 0, s>>>(color, n, ncolor, table.p, nb);
+    if (n > 0) SPHC_LAUNCH(k_part_count<<<(unsigned)nb, PART_BLOCK, 0, s>>>(color, n, ncolor, table.p, nb));
     SPHC_TRY(table64.alloc(ncolor * nb, s));
     // widen to int64 for the scan
     {
@@ -71,7 +113,7 @@ static int colour_partition(const int32_t* color, int64_t n, int ncolor, DBuf<in
         SPHC_CK(cudaMemcpyAsync(off.p, o.data(), sizeof(int64_t) * o.size(), cudaMemcpyHostToDevice, s));
         SPHC_CK(cudaStreamSynchronize(s));
     }
-    if (n > 0) k_part_place<<<(unsigned)nb, PART_BLOCK, 0, s>>>(color, n, ncolor, off.p, nb, perm.p);
+    if (n > 0) SPHC_LAUNCH(k_part_place<<<(unsigned)nb, PART_BLOCK, 0, s>>>(color, n, ncolor, off.p, nb, perm.p));
     SPHC_CK(cudaGetLastError());
     return SPHC_OK;
 }
@@ -111,16 +153,16 @@ static int build_smooth_op(const DCSR& A, const int32_t* color, int ncolor, Smoo
     DBuf<int64_t> len, rp64;
     SPHC_TRY(len.alloc(A.nr + 1, s));
     SPHC_TRY(rp64.alloc(A.nr + 1, s));
-    if (A.nr > 0) k_perm_rowlen<<<grid_for(A.nr, 256), 256, 0, s>>>(A.rp.p, op.perm.p, A.nr, len.p);
+    if (A.nr > 0) SPHC_LAUNCH(k_perm_rowlen<<<grid_for(A.nr, 256), 256, 0, s>>>(A.rp.p, op.perm.p, A.nr, len.p));
     SPHC_TRY(exclusive_scan_i64(len.p, rp64.p, A.nr, s, nullptr));
     SPHC_TRY(op.rp.alloc(A.nr + 1, s));
-    k_rp_narrow<<<grid_for(A.nr + 1, 256), 256, 0, s>>>(rp64.p, op.rp.p, A.nr + 1);
+    SPHC_LAUNCH(k_rp_narrow<<<grid_for(A.nr + 1, 256), 256, 0, s>>>(rp64.p, op.rp.p, A.nr + 1));
     SPHC_TRY(op.ci.alloc(A.nnz, s));
     SPHC_TRY(op.v.alloc(A.nnz, s));
     SPHC_TRY(op.dinv.alloc(A.nr, s));
     if (A.nr > 0)
-        k_perm_copy<T><<<grid_for(A.nr * 32, 256), 256, 0, s>>>(A.rp.p, A.ci.p, A.v.p, op.perm.p, A.nr, op.rp.p,
-                                                                 op.ci.p, op.v.p, op.dinv.p);
+        SPHC_LAUNCH(k_perm_copy<T><<<grid_for(A.nr * 32, 256), 256, 0, s>>>(A.rp.p, A.ci.p, A.v.p, op.perm.p, A.nr, op.rp.p,
+                                                                 op.ci.p, op.v.p, op.dinv.p));
     SPHC_CK(cudaGetLastError());
     return SPHC_OK;
 }
@@ -139,7 +181,7 @@ static int build_vcsr(const DCSR& A, VCSR<T>& B, cudaStream_t s) {
     SPHC_TRY(B.ci.alloc(A.nnz, s));
     SPHC_TRY(B.v.alloc(A.nnz, s));
     int64_t m = A.nnz > A.nr + 1 ? A.nnz : A.nr + 1;
-    k_csr_narrow<T><<<grid_for(m, 256), 256, 0, s>>>(A.rp.p, A.v.p, A.nr, A.nnz, B.rp.p, B.v.p);
+    SPHC_LAUNCH(k_csr_narrow<T><<<grid_for(m, 256), 256, 0, s>>>(A.rp.p, A.v.p, A.nr, A.nnz, B.rp.p, B.v.p));
     if (A.nnz > 0) SPHC_CK(cudaMemcpyAsync(B.ci.p, A.ci.p, sizeof(int32_t) * A.nnz, cudaMemcpyDeviceToDevice, s));
     SPHC_CK(cudaGetLastError());
     return SPHC_OK;
@@ -174,11 +216,11 @@ static int build_vlevel(Hierarchy& H, int l, VLevel<T>& V, cudaStream_t s) {
     SPHC_TRY(V.g.alloc(nv, s));
     SPHC_TRY(V.c.alloc(nv, s));
     SPHC_TRY(V.D.alloc(ne, s));
-    if (ne > 0) k_d_pairs<<<grid_for(ne, 256), 256, 0, s>>>(L.D.rp.p, L.D.ci.p, L.D.v.p, ne, V.D.p);
+    if (ne > 0) SPHC_LAUNCH(k_d_pairs<<<grid_for(ne, 256), 256, 0, s>>>(L.D.rp.p, L.D.ci.p, L.D.v.p, ne, V.D.p));
     SPHC_TRY(V.Dt_rp.alloc(nv + 1, s));
     SPHC_TRY(V.Dt_e.alloc(L.Dt.nnz, s));
     int64_t m = L.Dt.nnz > nv + 1 ? L.Dt.nnz : nv + 1;
-    k_dt_encode<<<grid_for(m, 256), 256, 0, s>>>(L.Dt.rp.p, L.Dt.ci.p, L.Dt.v.p, nv, L.Dt.nnz, V.Dt_rp.p, V.Dt_e.p);
+    SPHC_LAUNCH(k_dt_encode<<<grid_for(m, 256), 256, 0, s>>>(L.Dt.rp.p, L.Dt.ci.p, L.Dt.v.p, nv, L.Dt.nnz, V.Dt_rp.p, V.Dt_e.p));
     SPHC_TRY(build_vcsr<T>(L.Pe, V.Pe, s));
     SPHC_TRY(build_vcsr<T>(L.PeT, V.PeT, s));
     SPHC_CK(cudaGetLastError());
@@ -319,10 +361,10 @@ static void launch_rows_sgs(const SmoothOp<T>& op, int64_t k0, int64_t k1, const
     int sub = sub_for(op.nnz, op.n);
     int64_t th = rows * sub;
     switch (sub) {
-        case 4: k_sgs_color<T, 4><<<grid_for(th, 256), 256, 0, s>>>(op.rp.p, op.ci.p, op.v.p, op.perm.p, op.dinv.p, k0, k1, b, x); break;
-        case 8: k_sgs_color<T, 8><<<grid_for(th, 256), 256, 0, s>>>(op.rp.p, op.ci.p, op.v.p, op.perm.p, op.dinv.p, k0, k1, b, x); break;
-        case 16: k_sgs_color<T, 16><<<grid_for(th, 256), 256, 0, s>>>(op.rp.p, op.ci.p, op.v.p, op.perm.p, op.dinv.p, k0, k1, b, x); break;
-        default: k_sgs_color<T, 32><<<grid_for(th, 256), 256, 0, s>>>(op.rp.p, op.ci.p, op.v.p, op.perm.p, op.dinv.p, k0, k1, b, x); break;
+        case 4: SPHC_LAUNCH(k_sgs_color<T, 4><<<grid_for(th, 256), 256, 0, s>>>(op.rp.p, op.ci.p, op.v.p, op.perm.p, op.dinv.p, k0, k1, b, x)); break;
+        case 8: SPHC_LAUNCH(k_sgs_color<T, 8><<<grid_for(th, 256), 256, 0, s>>>(op.rp.p, op.ci.p, op.v.p, op.perm.p, op.dinv.p, k0, k1, b, x)); break;
+        case 16: SPHC_LAUNCH(k_sgs_color<T, 16><<<grid_for(th, 256), 256, 0, s>>>(op.rp.p, op.ci.p, op.v.p, op.perm.p, op.dinv.p, k0, k1, b, x)); break;
+        default: SPHC_LAUNCH(k_sgs_color<T, 32><<<grid_for(th, 256), 256, 0, s>>>(op.rp.p, op.ci.p, op.v.p, op.perm.p, op.dinv.p, k0, k1, b, x)); break;
     }
 }
 template <typename T>
@@ -336,10 +378,10 @@ static void resid(const SmoothOp<T>& op, const T* b, const T* x, T* r, cudaStrea
     int sub = sub_for(op.nnz, op.n);
     int64_t th = op.n * sub;
     switch (sub) {
-        case 4: k_resid<T, 4><<<grid_for(th, 256), 256, 0, s>>>(op.rp.p, op.ci.p, op.v.p, op.perm.p, op.n, b, x, r); break;
-        case 8: k_resid<T, 8><<<grid_for(th, 256), 256, 0, s>>>(op.rp.p, op.ci.p, op.v.p, op.perm.p, op.n, b, x, r); break;
-        case 16: k_resid<T, 16><<<grid_for(th, 256), 256, 0, s>>>(op.rp.p, op.ci.p, op.v.p, op.perm.p, op.n, b, x, r); break;
-        default: k_resid<T, 32><<<grid_for(th, 256), 256, 0, s>>>(op.rp.p, op.ci.p, op.v.p, op.perm.p, op.n, b, x, r); break;
+        case 4: SPHC_LAUNCH(k_resid<T, 4><<<grid_for(th, 256), 256, 0, s>>>(op.rp.p, op.ci.p, op.v.p, op.perm.p, op.n, b, x, r)); break;
+        case 8: SPHC_LAUNCH(k_resid<T, 8><<<grid_for(th, 256), 256, 0, s>>>(op.rp.p, op.ci.p, op.v.p, op.perm.p, op.n, b, x, r)); break;
+        case 16: SPHC_LAUNCH(k_resid<T, 16><<<grid_for(th, 256), 256, 0, s>>>(op.rp.p, op.ci.p, op.v.p, op.perm.p, op.n, b, x, r)); break;
+        default: SPHC_LAUNCH(k_resid<T, 32><<<grid_for(th, 256), 256, 0, s>>>(op.rp.p, op.ci.p, op.v.p, op.perm.p, op.n, b, x, r)); break;
     }
 }
 template <typename T>
@@ -348,50 +390,68 @@ static void spmv_v(const VCSR<T>& A, const T* x, T* y, int acc, cudaStream_t s) 
     int sub = sub_for(A.nnz, A.nr);
     int64_t th = A.nr * sub;
     switch (sub) {
-        case 4: k_spmv_v<T, 4><<<grid_for(th, 256), 256, 0, s>>>(A.rp.p, A.ci.p, A.v.p, A.nr, x, y, acc); break;
-        case 8: k_spmv_v<T, 8><<<grid_for(th, 256), 256, 0, s>>>(A.rp.p, A.ci.p, A.v.p, A.nr, x, y, acc); break;
-        case 16: k_spmv_v<T, 16><<<grid_for(th, 256), 256, 0, s>>>(A.rp.p, A.ci.p, A.v.p, A.nr, x, y, acc); break;
-        default: k_spmv_v<T, 32><<<grid_for(th, 256), 256, 0, s>>>(A.rp.p, A.ci.p, A.v.p, A.nr, x, y, acc); break;
+        case 4: SPHC_LAUNCH(k_spmv_v<T, 4><<<grid_for(th, 256), 256, 0, s>>>(A.rp.p, A.ci.p, A.v.p, A.nr, x, y, acc)); break;
+        case 8: SPHC_LAUNCH(k_spmv_v<T, 8><<<grid_for(th, 256), 256, 0, s>>>(A.rp.p, A.ci.p, A.v.p, A.nr, x, y, acc)); break;
+        case 16: SPHC_LAUNCH(k_spmv_v<T, 16><<<grid_for(th, 256), 256, 0, s>>>(A.rp.p, A.ci.p, A.v.p, A.nr, x, y, acc)); break;
+        default: SPHC_LAUNCH(k_spmv_v<T, 32><<<grid_for(th, 256), 256, 0, s>>>(A.rp.p, A.ci.p, A.v.p, A.nr, x, y, acc)); break;
     }
 }
 
 // one symmetric Hiptmair sweep (Sec. 6.1): SGS on A, nodal SGS on D^T A D with c0 = 0 applied
 // to D^T r, correction x += D c, SGS on A
+// algorithmic bytes of one forward + backward sweep: the matrix once per direction and, per
+// row, its pointer, permutation, inverse diagonal, right side and one read and write of x
 template <typename T>
-static void hiptmair(VLevel<T>& V, int64_t ne, int64_t nv, cudaStream_t s) {
-    sgs(V.A, V.b.p, V.x.p, s);
+static double sgs_bytes(const SmoothOp<T>& op) {
+    return 2.0 * ((double)op.nnz * (sizeof(T) + 4) + (double)op.n * (4 + 4 + 3 * sizeof(T) + sizeof(T)));
+}
+
+template <typename T>
+static void timed_sgs(Hierarchy& H, int lev, const SmoothOp<T>& op, const T* b, T* x, cudaStream_t s) {
+    int id = -1;
+    if (H.prof.on && lev == 0) {
+        id = H.prof.find("sgs_A_level0", sgs_bytes(op));
+        H.prof.begin(id, s);
+    }
+    sgs(op, b, x, s);
+    if (id >= 0) H.prof.end(id, s);
+}
+
+template <typename T>
+static void hiptmair(Hierarchy& H, int lev, VLevel<T>& V, int64_t ne, int64_t nv, cudaStream_t s) {
+    timed_sgs(H, lev, V.A, V.b.p, V.x.p, s);
     resid(V.A, V.b.p, V.x.p, V.r.p, s);
     if (nv > 0) {
-        k_dt_gather<T><<<grid_for(nv, 256), 256, 0, s>>>(V.Dt_rp.p, V.Dt_e.p, nv, V.r.p, V.g.p);
-        k_zero<T><<<grid_for(nv, 256), 256, 0, s>>>(V.c.p, nv);
+        SPHC_LAUNCH(k_dt_gather<T><<<grid_for(nv, 256), 256, 0, s>>>(V.Dt_rp.p, V.Dt_e.p, nv, V.r.p, V.g.p));
+        SPHC_LAUNCH(k_zero<T><<<grid_for(nv, 256), 256, 0, s>>>(V.c.p, nv));
         sgs(V.An, V.g.p, V.c.p, s);
-        k_d_apply<T><<<grid_for(ne, 256), 256, 0, s>>>(V.D.p, ne, V.c.p, V.x.p);
+        SPHC_LAUNCH(k_d_apply<T><<<grid_for(ne, 256), 256, 0, s>>>(V.D.p, ne, V.c.p, V.x.p));
     }
-    sgs(V.A, V.b.p, V.x.p, s);
+    timed_sgs(H, lev, V.A, V.b.p, V.x.p, s);
 }
 
 template <typename T>
 static void vcycle_level(Hierarchy& H, std::vector<VLevel<T>>& V, int l, cudaStream_t s) {
     int64_t ne = H.L[l].A.nr, nv = H.L[l].An.nr;
     if (l == H.nlev - 1) {
-        if (ne > 0) k_dense_solve<T><<<grid_for(ne * 32, 256), 256, 0, s>>>(H.coarse_inv.p, ne, V[l].b.p, V[l].x.p);
+        if (ne > 0) SPHC_LAUNCH(k_dense_solve<T><<<grid_for(ne * 32, 256), 256, 0, s>>>(H.coarse_inv.p, ne, V[l].b.p, V[l].x.p));
         return;
     }
-    k_zero<T><<<grid_for(ne, 256), 256, 0, s>>>(V[l].x.p, ne);
-    hiptmair(V[l], ne, nv, s);
+    SPHC_LAUNCH(k_zero<T><<<grid_for(ne, 256), 256, 0, s>>>(V[l].x.p, ne));
+    hiptmair(H, l, V[l], ne, nv, s);
     resid(V[l].A, V[l].b.p, V[l].x.p, V[l].r.p, s);
     spmv_v(V[l].PeT, V[l].r.p, V[l + 1].b.p, 0, s);
     vcycle_level(H, V, l + 1, s);
     spmv_v(V[l].Pe, V[l + 1].x.p, V[l].x.p, 1, s);
-    hiptmair(V[l], ne, nv, s);
+    hiptmair(H, l, V[l], ne, nv, s);
 }
 
 int apply_vcycle(Hierarchy& H, const double* r, double* z, cudaStream_t s) {
     int64_t n = H.L[0].A.nr;
     if (H.opts.vcycle_fp32) {
-        k_cast<double, float><<<grid_for(n, 256), 256, 0, s>>>(r, H.V32[0].b.p, n);
+        SPHC_LAUNCH(k_cast<double, float><<<grid_for(n, 256), 256, 0, s>>>(r, H.V32[0].b.p, n));
         vcycle_level<float>(H, H.V32, 0, s);
-        k_cast<float, double><<<grid_for(n, 256), 256, 0, s>>>(H.V32[0].x.p, z, n);
+        SPHC_LAUNCH(k_cast<float, double><<<grid_for(n, 256), 256, 0, s>>>(H.V32[0].x.p, z, n));
     } else {
         SPHC_CK(cudaMemcpyAsync(H.V64[0].b.p, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
         vcycle_level<double>(H, H.V64, 0, s);
@@ -443,10 +503,13 @@ int pcg_solve(Hierarchy& H, const double* b, double* x, double tol, cudaStream_t
         SPHC_CK(cudaMemcpyAsync(H.p.p, H.z.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
         SPHC_TRY(dot64(H.r.p, H.z.p, n, sc + 0, s));
         double hsc[6];
+        int tid = H.prof.on ? H.prof.find("spmv_A_fp64", (double)A.nnz * 12.0 + (double)n * 24.0) : -1;
         for (it = 0; it < H.opts.max_iter;) {
+            if (tid >= 0) H.prof.begin(tid, s);
             SPHC_TRY(spmv64(A, H.p.p, H.q.p, s));
+            if (tid >= 0) H.prof.end(tid, s);
             SPHC_TRY(dot64(H.p.p, H.q.p, n, sc + 1, s));
-            k_cg_xr<<<grid_for(n, 256), 256, 0, s>>>(x, H.r.p, H.rold.p, H.p.p, H.q.p, sc, n, flexible);
+            SPHC_LAUNCH(k_cg_xr<<<grid_for(n, 256), 256, 0, s>>>(x, H.r.p, H.rold.p, H.p.p, H.q.p, sc, n, flexible));
             ++it;
             SPHC_TRY(dot64(H.r.p, H.r.p, n, sc + 2, s));
             SPHC_CK(cudaMemcpyAsync(hsc, sc, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -456,13 +519,13 @@ int pcg_solve(Hierarchy& H, const double* b, double* x, double tol, cudaStream_t
             SPHC_TRY(apply_vcycle(H, H.r.p, H.z.p, s));
             SPHC_TRY(dot64(H.r.p, H.z.p, n, sc + 3, s));
             if (flexible) SPHC_TRY(dot64(H.z.p, H.rold.p, n, sc + 4, s));
-            k_cg_p<<<grid_for(n, 256), 256, 0, s>>>(H.p.p, H.z.p, sc, n, flexible);
-            k_cg_shift<<<1, 1, 0, s>>>(sc);
+            SPHC_LAUNCH(k_cg_p<<<grid_for(n, 256), 256, 0, s>>>(H.p.p, H.z.p, sc, n, flexible));
+            SPHC_LAUNCH(k_cg_shift<<<1, 1, 0, s>>>(sc));
         }
     }
     // true residual
     SPHC_TRY(spmv64(A, x, H.q.p, s));
-    k_sub<<<grid_for(n, 256), 256, 0, s>>>(b, H.q.p, n);
+    SPHC_LAUNCH(k_sub<<<grid_for(n, 256), 256, 0, s>>>(b, H.q.p, n));
     SPHC_TRY(dot64(H.q.p, H.q.p, n, sc + 6, s));
     double hr = 0.0;
     SPHC_CK(cudaMemcpyAsync(&hr, sc + 6, sizeof(double), cudaMemcpyDeviceToHost, s));

@@ -9,6 +9,7 @@
 namespace sphc {
 
 bool g_sync_free = false;
+std::atomic<long long> g_launches{0};
 static thread_local std::string g_err;
 void set_error(const char* fmt, ...) {
     char buf[1024];
@@ -111,10 +112,10 @@ static int scan_impl(const TI* in, int64_t* out, int64_t n, cudaStream_t s, int6
     if (nt < 1) nt = 1;
     DBuf<int64_t> sums;
     SPHC_TRY(sums.alloc(nt + 1, s));
-    if (n > 0) k_scan_tiles<TI><<<(unsigned)nt, SCAN_BLOCK, 0, s>>>(in, n, sums.p);
+    if (n > 0) SPHC_LAUNCH(k_scan_tiles<TI><<<(unsigned)nt, SCAN_BLOCK, 0, s>>>(in, n, sums.p));
     else SPHC_CK(cudaMemsetAsync(sums.p, 0, sizeof(int64_t) * nt, s));
-    k_scan_sums<<<1, SCAN_BLOCK, 0, s>>>(sums.p, nt, out + n);
-    if (n > 0) k_scan_apply<TI><<<(unsigned)nt, SCAN_BLOCK, 0, s>>>(in, n, sums.p, out);
+    SPHC_LAUNCH(k_scan_sums<<<1, SCAN_BLOCK, 0, s>>>(sums.p, nt, out + n));
+    if (n > 0) SPHC_LAUNCH(k_scan_apply<TI><<<(unsigned)nt, SCAN_BLOCK, 0, s>>>(in, n, sums.p, out));
     SPHC_CK(cudaGetLastError());
     if (total_host) {
         SPHC_CK(cudaMemcpyAsync(total_host, out + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -144,7 +145,7 @@ int max_row_length(const int64_t* rp, int64_t nrows, cudaStream_t s, int64_t* ou
     DBuf<unsigned long long> m;
     SPHC_TRY(m.alloc(1, s));
     SPHC_TRY(m.zero(s));
-    if (nrows > 0) k_row_len_max<<<grid_for(nrows, 256), 256, 0, s>>>(rp, nrows, m.p);
+    if (nrows > 0) SPHC_LAUNCH(k_row_len_max<<<grid_for(nrows, 256), 256, 0, s>>>(rp, nrows, m.p));
     unsigned long long h = 0;
     SPHC_CK(cudaMemcpyAsync(&h, m.p, sizeof(h), cudaMemcpyDeviceToHost, s));
     SPHC_CK(cudaStreamSynchronize(s));
@@ -222,7 +223,7 @@ __global__ void k_segsort_block(const int64_t* rp, int64_t nrows, int32_t* keys,
 int segmented_sort(const int64_t* rp, int64_t nrows, int32_t* keys, double* vals, int64_t max_len,
                    cudaStream_t s) {
     if (nrows <= 0) return SPHC_OK;
-    k_segsort_warp<<<grid_for(nrows * 32, 256), 256, 0, s>>>(rp, nrows, keys, vals);
+    SPHC_LAUNCH(k_segsort_warp<<<grid_for(nrows * 32, 256), 256, 0, s>>>(rp, nrows, keys, vals));
     if (max_len > 32) {
         int cap = 64;
         while (cap < max_len) cap <<= 1;
@@ -233,7 +234,7 @@ int segmented_sort(const int64_t* rp, int64_t nrows, int32_t* keys, double* vals
         size_t sm = (size_t)cap * (sizeof(int32_t) + sizeof(double));
         SPHC_CK(cudaFuncSetAttribute(k_segsort_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         int grid = (int)(nrows < 65536 ? nrows : 65536);
-        k_segsort_block<<<grid, 256, sm, s>>>(rp, nrows, keys, vals, cap);
+        SPHC_LAUNCH(k_segsort_block<<<grid, 256, sm, s>>>(rp, nrows, keys, vals, cap));
     }
     SPHC_CK(cudaGetLastError());
     return SPHC_OK;
@@ -263,15 +264,15 @@ int transpose(const DCSR& A, DCSR& At, cudaStream_t s) {
     DBuf<int32_t> cnt;
     SPHC_TRY(cnt.alloc(A.nc + 1, s));
     SPHC_TRY(cnt.zero(s));
-    if (A.nnz > 0) k_col_count<<<grid_for(A.nnz, 256), 256, 0, s>>>(A.ci.p, A.nnz, cnt.p);
+    if (A.nnz > 0) SPHC_LAUNCH(k_col_count<<<grid_for(A.nnz, 256), 256, 0, s>>>(A.ci.p, A.nnz, cnt.p));
     SPHC_TRY(At.alloc(A.nc, A.nr, A.nnz, s));
     int64_t tot = 0;
     SPHC_TRY(scan_i32_to_i64(cnt.p, At.rp.p, A.nc, s, &tot));
     DBuf<unsigned long long> cur;
     SPHC_TRY(cur.alloc(A.nc + 1, s));
-    k_i64_to_u64<<<grid_for(A.nc + 1, 256), 256, 0, s>>>(At.rp.p, cur.p, A.nc + 1);
+    SPHC_LAUNCH(k_i64_to_u64<<<grid_for(A.nc + 1, 256), 256, 0, s>>>(At.rp.p, cur.p, A.nc + 1));
     if (A.nr > 0)
-        k_transpose_scatter<<<grid_for(A.nr, 256), 256, 0, s>>>(A.rp.p, A.ci.p, A.v.p, A.nr, cur.p, At.ci.p, At.v.p);
+        SPHC_LAUNCH(k_transpose_scatter<<<grid_for(A.nr, 256), 256, 0, s>>>(A.rp.p, A.ci.p, A.v.p, A.nr, cur.p, At.ci.p, At.v.p));
     SPHC_CK(cudaGetLastError());
     int64_t mx = 0;
     SPHC_TRY(max_row_length(At.rp.p, At.nr, s, &mx));
@@ -298,7 +299,7 @@ __global__ void k_diag(const int64_t* rp, const int32_t* ci, const double* v, in
     d[i] = r;
 }
 int csr_diag(const DCSR& A, double* d, cudaStream_t s) {
-    if (A.nr > 0) k_diag<<<grid_for(A.nr, 256), 256, 0, s>>>(A.rp.p, A.ci.p, A.v.p, A.nr, d);
+    if (A.nr > 0) SPHC_LAUNCH(k_diag<<<grid_for(A.nr, 256), 256, 0, s>>>(A.rp.p, A.ci.p, A.v.p, A.nr, d));
     SPHC_CK(cudaGetLastError());
     return SPHC_OK;
 }
@@ -561,9 +562,9 @@ int spgemm(const DCSR& A, const DCSR& B, DCSR& C, cudaStream_t s) {
     SPHC_TRY(bign.zero(s));
     SPHC_TRY(fail.zero(s));
     if (n > 0) {
-        k_spgemm_ub<<<grid_for(n, 256), 256, 0, s>>>(A.rp.p, A.ci.p, B.rp.p, n, ub.p);
-        k_spgemm_symbolic<<<grid_for(n, SPGEMM_WARPS), SPGEMM_WARPS * 32, 0, s>>>(
-            A.rp.p, A.ci.p, B.rp.p, B.ci.p, n, ub.p, cnt.p, big.p, bign.p);
+        SPHC_LAUNCH(k_spgemm_ub<<<grid_for(n, 256), 256, 0, s>>>(A.rp.p, A.ci.p, B.rp.p, n, ub.p));
+        SPHC_LAUNCH(k_spgemm_symbolic<<<grid_for(n, SPGEMM_WARPS), SPGEMM_WARPS * 32, 0, s>>>(
+            A.rp.p, A.ci.p, B.rp.p, B.ci.p, n, ub.p, cnt.p, big.p, bign.p));
     }
     SPHC_CK(cudaGetLastError());
     int nbig = 0;
@@ -573,8 +574,8 @@ int spgemm(const DCSR& A, const DCSR& B, DCSR& C, cudaStream_t s) {
     size_t big_num_sm = (sizeof(int32_t) + sizeof(double)) * BIG_SLOTS;
     if (nbig > 0) {
         SPHC_CK(cudaFuncSetAttribute(k_spgemm_symbolic_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big_sym_sm));
-        k_spgemm_symbolic_big<<<nbig < 4096 ? nbig : 4096, 512, big_sym_sm, s>>>(
-            A.rp.p, A.ci.p, B.rp.p, B.ci.p, big.p, nbig, cnt.p, fail.p);
+        SPHC_LAUNCH(k_spgemm_symbolic_big<<<nbig < 4096 ? nbig : 4096, 512, big_sym_sm, s>>>(
+            A.rp.p, A.ci.p, B.rp.p, B.ci.p, big.p, nbig, cnt.p, fail.p));
         int f = 0;
         SPHC_CK(cudaMemcpyAsync(&f, fail.p, sizeof(int), cudaMemcpyDeviceToHost, s));
         SPHC_CK(cudaStreamSynchronize(s));
@@ -592,12 +593,12 @@ int spgemm(const DCSR& A, const DCSR& B, DCSR& C, cudaStream_t s) {
     size_t num_sm = (sizeof(int32_t) + sizeof(double)) * HASH_SLOTS * SPGEMM_WARPS;
     SPHC_CK(cudaFuncSetAttribute(k_spgemm_numeric, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)num_sm));
     if (n > 0)
-        k_spgemm_numeric<<<grid_for(n, SPGEMM_WARPS), SPGEMM_WARPS * 32, num_sm, s>>>(
-            A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p, B.v.p, n, C.rp.p, C.ci.p, C.v.p);
+        SPHC_LAUNCH(k_spgemm_numeric<<<grid_for(n, SPGEMM_WARPS), SPGEMM_WARPS * 32, num_sm, s>>>(
+            A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p, B.v.p, n, C.rp.p, C.ci.p, C.v.p));
     if (nbig > 0) {
         SPHC_CK(cudaFuncSetAttribute(k_spgemm_numeric_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big_num_sm));
-        k_spgemm_numeric_big<<<nbig < 4096 ? nbig : 4096, 512, big_num_sm, s>>>(
-            A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p, B.v.p, big.p, nbig, C.rp.p, C.ci.p, C.v.p);
+        SPHC_LAUNCH(k_spgemm_numeric_big<<<nbig < 4096 ? nbig : 4096, 512, big_num_sm, s>>>(
+            A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p, B.v.p, big.p, nbig, C.rp.p, C.ci.p, C.v.p));
     }
     SPHC_CK(cudaGetLastError());
     return SPHC_OK;
@@ -619,7 +620,7 @@ __global__ void k_spmv64(const int64_t* rp, const int32_t* ci, const double* v, 
     if (valid && sub == 0) y[i] = s;
 }
 int spmv64(const DCSR& A, const double* x, double* y, cudaStream_t s) {
-    if (A.nr > 0) k_spmv64<<<grid_for(A.nr * 8, 256), 256, 0, s>>>(A.rp.p, A.ci.p, A.v.p, A.nr, x, y);
+    if (A.nr > 0) SPHC_LAUNCH(k_spmv64<<<grid_for(A.nr * 8, 256), 256, 0, s>>>(A.rp.p, A.ci.p, A.v.p, A.nr, x, y));
     SPHC_CK(cudaGetLastError());
     return SPHC_OK;
 }
@@ -655,8 +656,8 @@ __global__ void k_dot_final(const double* part, int np, double* out) {
 int dot64(const double* a, const double* b, int64_t n, double* result_dev, cudaStream_t s) {
     DBuf<double> part;
     SPHC_TRY(part.alloc(DOT_BLOCKS, s));
-    k_dot_part<<<DOT_BLOCKS, 256, 0, s>>>(a, b, n, part.p);
-    k_dot_final<<<1, 1024, 0, s>>>(part.p, DOT_BLOCKS, result_dev);
+    SPHC_LAUNCH(k_dot_part<<<DOT_BLOCKS, 256, 0, s>>>(a, b, n, part.p));
+    SPHC_LAUNCH(k_dot_final<<<1, 1024, 0, s>>>(part.p, DOT_BLOCKS, result_dev));
     SPHC_CK(cudaGetLastError());
     return SPHC_OK;
 }

@@ -2,6 +2,8 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -27,6 +29,15 @@ const char* last_error();
     do {                              \
         int rc_ = (call);             \
         if (rc_ != SPHC_OK) return rc_; \
+    } while (0)
+
+// ------------------------------------------------------------------ launch accounting
+// Process-wide count of kernel launches made by the library (read by sphc_launch_count).
+extern std::atomic<long long> g_launches;
+#define SPHC_LAUNCH(...)                                                   \
+    do {                                                                   \
+        ::sphc::g_launches.fetch_add(1, std::memory_order_relaxed);       \
+        __VA_ARGS__;                                                       \
     } while (0)
 
 // ------------------------------------------------------------------ stream-ordered buffers

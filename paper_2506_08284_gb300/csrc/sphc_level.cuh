@@ -59,8 +59,29 @@ int color_graph(const DCSR& G, uint64_t seed, DBuf<int32_t>& color, int* ncolors
 int aggregate(const DCSR& G, uint64_t seed, DBuf<int32_t>& agg, int64_t* nagg, cudaStream_t s);
 int power_rho(const DCSR& A, const double* diag, uint64_t seed, int iters, double* rho, cudaStream_t s);
 int coarse_gradient(const DCSR& D, const DCSR& Dt, const int32_t* agg, int64_t nagg, DCSR& DH, cudaStream_t s);
-int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext, DCSR& Annext, cudaStream_t s);
 int coarse_inverse(const DCSR& A, DBuf<double>& Ainv, cudaStream_t s);
+
+// Section timers: CUDA events recorded on the work stream around a named section; resolved
+// (cudaEventElapsedTime) when the profile is read.
+struct Timer {
+    std::string name;
+    double ms = 0.0;
+    int64_t calls = 0;
+    double bytes = 0.0;                       // algorithmic bytes of one call
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+};
+struct Profiler {
+    bool on = false;
+    std::vector<Timer> timers;
+    int find(const char* name, double bytes);
+    void begin(int id, cudaStream_t s);
+    void end(int id, cudaStream_t s);
+    int resolve();
+    ~Profiler();
+};
+
+int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext, DCSR& Annext, Profiler* prof,
+                cudaStream_t s);
 
 // solve.cu
 struct Hierarchy {
@@ -76,6 +97,7 @@ struct Hierarchy {
     DBuf<double> x, r, z, p, q, rold, scal;
     DBuf<double> cb, cx;             // coarsest right side / solution (FP64)
     double setup_ms = 0.0, solve_ms = 0.0;
+    Profiler prof;
     int last_iters = 0;
     double last_relres = 0.0;
 };

@@ -35,7 +35,7 @@ class sphc_opts(ctypes.Structure):
     _fields_ = [("max_levels", ctypes.c_int32), ("emin_iters", ctypes.c_int32), ("max_coarse", ctypes.c_int64),
                 ("emin_omega", ctypes.c_double), ("seed", ctypes.c_uint64), ("power_iters", ctypes.c_int32),
                 ("vcycle_fp32", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("flexible", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 7)]
+                ("profile", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
 
 
 class sphc_level_info(ctypes.Structure):
@@ -54,8 +54,14 @@ class sphc_stats(ctypes.Structure):
                 ("last_relres", ctypes.c_double), ("device_bytes", ctypes.c_int64)]
 
 
+class sphc_timer(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("ms", ctypes.c_double), ("calls", ctypes.c_int64),
+                ("bytes_per_call", ctypes.c_double)]
+
+
 EXPORTED = ["sphc_default_opts", "sphc_setup", "sphc_solve", "sphc_vcycle", "sphc_get_stats",
-            "sphc_get_level_info", "sphc_export_size", "sphc_export", "sphc_destroy", "sphc_last_error"]
+            "sphc_get_level_info", "sphc_export_size", "sphc_export", "sphc_destroy", "sphc_last_error",
+            "sphc_get_profile", "sphc_launch_count"]
 
 _lib = None
 
@@ -79,10 +85,13 @@ def load(path: str | None = None):
     lib.sphc_export.argtypes = [P, I, I, P, P, P, P, P]
     lib.sphc_destroy.argtypes = [P]
     lib.sphc_destroy.restype = None
+    lib.sphc_get_profile.argtypes = [P, ctypes.POINTER(sphc_timer), I, ctypes.POINTER(I)]
+    lib.sphc_launch_count.argtypes = []
+    lib.sphc_launch_count.restype = ctypes.c_int64
     lib.sphc_last_error.argtypes = []
     lib.sphc_last_error.restype = ctypes.c_char_p
     for name in EXPORTED:
-        if name not in ("sphc_destroy", "sphc_last_error"):
+        if name not in ("sphc_destroy", "sphc_last_error", "sphc_launch_count"):
             getattr(lib, name).restype = I
     if path is None:
         _lib = lib
@@ -169,6 +178,13 @@ class Handle:
         _check(load().sphc_get_level_info(self._ptr, level, ctypes.byref(li)))
         return {k: getattr(li, k) for k, _ in sphc_level_info._fields_}
 
+    def profile(self) -> dict:
+        arr = (sphc_timer * 32)()
+        n = ctypes.c_int()
+        _check(load().sphc_get_profile(self._ptr, arr, 32, ctypes.byref(n)))
+        return {arr[i].name.decode(): dict(ms=arr[i].ms, calls=arr[i].calls, bytes_per_call=arr[i].bytes_per_call)
+                for i in range(min(n.value, 32))}
+
     @property
     def nlevels(self):
         return self.stats()["n_levels"]
@@ -191,6 +207,10 @@ class Handle:
         v = np.empty(nz, np.float64)
         _check(load().sphc_export(self._ptr, level, X[what], _ptr(rp), _ptr(ci), _ptr(v), None, _stream(stream)))
         return rp, ci, v, (nr, nc)
+
+
+def launch_count() -> int:
+    return int(load().sphc_launch_count())
 
 
 def setup(A, D, coords=None, sigma_edge=None, opts=None, stream=None) -> Handle:
