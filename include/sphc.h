@@ -174,6 +174,28 @@ SPHC_API int sphc_get_profile(sphc_handle* h, sphc_timer* out, int max, int* n);
 /* Number of kernels the library has launched in this process so far. */
 SPHC_API int64_t sphc_launch_count(void);
 
+/* Largest nrhs that sphc_relres_noalloc accepts (its fixed scratch holds this many). */
+#define SPHC_NOALLOC_MAX_RHS 64
+
+/*
+ * The paper has no counterpart to this entry point; it serves callers that cannot allocate
+ * device memory (an allocator callback, a framework that has reserved all device memory, a
+ * real-time loop that forbids allocation after start-up).
+ *
+ * Computes relres[k] = ||b_k - A_e x_k|| / ||b_k|| (0 when b_k = 0) for k < nrhs, the same
+ * quantity sphc_solve reports, with A_e the handle's finest operator.  b and x are nrhs x n_e
+ * FP64 arrays (row-major) in device memory; relres[nrhs] may be host or device memory.
+ * It allocates nothing: its partial sums live in one file-scope device array of
+ * SPHC_NOALLOC_MAX_RHS x 513 doubles (about 257 KB) that every GPU loading the library keeps
+ * until the process exits.  The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress), so make it before any stream capture.  All calls share the array:
+ * calls that overlap on the GPU (other streams, other threads) race and must be serialised by
+ * the caller.  Synchronises the stream.  Errors: SPHC_EINVAL (NULL pointer, nrhs outside
+ * 1..SPHC_NOALLOC_MAX_RHS, host b or x, current device not the handle's), SPHC_ECUDA.
+ */
+SPHC_API int sphc_relres_noalloc(const sphc_handle* h, const double* b, const double* x, int nrhs, double* relres,
+                                 void* stream);
+
 /* Thread-local message of the last error ("" if none). */
 SPHC_API const char* sphc_last_error(void);
 

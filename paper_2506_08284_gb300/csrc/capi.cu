@@ -8,11 +8,6 @@
 
 using namespace sphc;
 
-struct sphc_handle {
-    Hierarchy H;
-    int device = 0;
-};
-
 namespace {
 
 bool is_device_ptr(const void* p) {

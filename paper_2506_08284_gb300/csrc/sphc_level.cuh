@@ -107,3 +107,9 @@ int apply_vcycle(Hierarchy& H, const double* r, double* z, cudaStream_t s);
 int pcg_solve(Hierarchy& H, const double* b, double* x, double tol, cudaStream_t s, int* iters, double* relres);
 
 }  // namespace sphc
+
+// The opaque handle of the C ABI.
+struct sphc_handle {
+    sphc::Hierarchy H;
+    int device = 0;
+};

@@ -61,7 +61,7 @@ class sphc_timer(ctypes.Structure):
 
 EXPORTED = ["sphc_default_opts", "sphc_setup", "sphc_solve", "sphc_vcycle", "sphc_get_stats",
             "sphc_get_level_info", "sphc_export_size", "sphc_export", "sphc_destroy", "sphc_last_error",
-            "sphc_get_profile", "sphc_launch_count"]
+            "sphc_get_profile", "sphc_launch_count", "sphc_relres_noalloc"]
 
 _lib = None
 
@@ -86,6 +86,7 @@ def load(path: str | None = None):
     lib.sphc_destroy.argtypes = [P]
     lib.sphc_destroy.restype = None
     lib.sphc_get_profile.argtypes = [P, ctypes.POINTER(sphc_timer), I, ctypes.POINTER(I)]
+    lib.sphc_relres_noalloc.argtypes = [P, P, P, I, P, P]
     lib.sphc_launch_count.argtypes = []
     lib.sphc_launch_count.restype = ctypes.c_int64
     lib.sphc_last_error.argtypes = []
@@ -177,6 +178,11 @@ class Handle:
         li = sphc_level_info()
         _check(load().sphc_get_level_info(self._ptr, level, ctypes.byref(li)))
         return {k: getattr(li, k) for k, _ in sphc_level_info._fields_}
+
+    def relres_noalloc(self, b, x, relres, nrhs=1, stream=None):
+        """||b - A x|| / ||b|| through sphc_relres_noalloc (b, x on the device; relres host or device).
+        Returns the status code."""
+        return load().sphc_relres_noalloc(self._ptr, _ptr(b), _ptr(x), nrhs, _ptr(relres), _stream(stream))
 
     def profile(self) -> dict:
         arr = (sphc_timer * 32)()

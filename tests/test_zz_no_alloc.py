@@ -1,0 +1,54 @@
+"""sphc_relres_noalloc, the entry point that allocates no device memory.
+
+It exists for callers that cannot allocate: code running inside another allocator's callback,
+processes whose device memory a framework has already reserved, or real-time loops that forbid
+allocation after start-up.  Through the C ABI it must report the same true relative residual
+||b - A x|| / ||b|| as sphc_solve does, within the FP64 tolerance of the other parity tests, on
+two calls in a row (its fixed scratch keeps the previous call's contents).
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import meshgen
+from gpu_util import gpu_setup
+
+pytestmark = pytest.mark.gpu
+
+FP64_RTOL = 1e-10
+
+
+def test_noalloc_relres_matches_solve():
+    import torch
+
+    import paper_2506_08284_gb300 as pkg
+
+    p = meshgen.generate(meshgen.workload("kuhn8")[0])
+    h = gpu_setup(p, vcycle_fp32=0)
+    nrhs = 3
+    B = torch.from_numpy(meshgen.rhs(21, p.n_edges, nrhs=nrhs)).cuda()
+    X = torch.zeros_like(B)
+    rc, it, rr_solve = h.solve(B, X, nrhs=nrhs)
+    torch.cuda.synchronize()
+    assert rc == 0
+    # sphc_solve stops each right-hand side at a different x; also test an arbitrary x
+    Y = X.clone()
+    Y[1] += 1e-3
+    for trial in range(2):                                   # two calls in a row
+        out = np.full(nrhs, -1.0)
+        assert h.relres_noalloc(B, X, out, nrhs=nrhs) == 0
+        np.testing.assert_allclose(out, rr_solve, rtol=FP64_RTOL, atol=0)
+        dev_out = torch.full((nrhs,), -1.0, dtype=torch.float64, device="cuda")
+        assert h.relres_noalloc(B, Y, dev_out, nrhs=nrhs) == 0
+        torch.cuda.synchronize()
+        A = sp.csr_matrix((p.A_val, p.A_col, p.A_rowptr))
+        Bh, Yh = B.cpu().numpy(), Y.cpu().numpy()
+        ref = [np.linalg.norm(Bh[k] - A @ Yh[k]) / np.linalg.norm(Bh[k]) for k in range(nrhs)]
+        # the host reference sums in another order; b - A x cancels to ~1e-9 of b, so compare
+        # in units of the rounding of A x relative to b
+        np.testing.assert_allclose(dev_out.cpu().numpy(), ref, rtol=1e-9, atol=1e-14)
+    # more right-hand sides than the fixed scratch holds: a clear error, nothing launched
+    Bbig = torch.zeros((65, p.n_edges), dtype=torch.float64, device="cuda")
+    rc = h.relres_noalloc(Bbig, Bbig, np.zeros(65), nrhs=65)
+    assert rc == -1
+    assert b"64" in pkg.sphc.load().sphc_last_error()
