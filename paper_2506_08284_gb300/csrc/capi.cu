@@ -103,9 +103,11 @@ int setup_impl(sphc_handle* h, const sphc_csr* A_e, const sphc_csr* D_h, cudaStr
     }
     SPHC_TRY(validate(L0.A, 0, "A_e", s));
     SPHC_TRY(validate(L0.D, 1, "D_h", s));
+    Profiler* prof = H.prof.on ? &H.prof : nullptr;
     // nodal operator D_h^T A_e D_h
     SPHC_TRY(transpose(L0.D, L0.Dt, s));
     {
+        Section sec(prof, "setup_nodal_op", s);
         DCSR AD;
         SPHC_TRY(spgemm(L0.A, L0.D, AD, s));
         SPHC_TRY(spgemm(L0.Dt, AD, L0.An, s));
@@ -114,12 +116,16 @@ int setup_impl(sphc_handle* h, const sphc_csr* A_e, const sphc_csr* D_h, cudaStr
     for (;;) {
         Level& L = H.L[lev];
         uint64_t seed = o.seed + 1000ULL * (uint64_t)lev;
-        SPHC_TRY(color_graph(L.A, seed + 2, L.col_e, &L.ncol_e, s));
-        SPHC_TRY(color_graph(L.An, seed + 3, L.col_n, &L.ncol_n, s));
+        {
+            Section sec(lev == 0 ? prof : nullptr, "setup_colour_l0", s);
+            SPHC_TRY(color_graph(L.A, seed + 2, L.col_e, &L.ncol_e, s));
+            SPHC_TRY(color_graph(L.An, seed + 3, L.col_n, &L.ncol_n, s));
+        }
         bool coarsest = L.A.nr <= o.max_coarse || lev + 1 >= o.max_levels || L.An.nr <= 1;
         if (coarsest) break;
         DCSR A1, D1, An1;
-        SPHC_TRY(build_level(L, lev, o, A1, D1, An1, H.prof.on && lev == 0 ? &H.prof : nullptr, s));
+        Section sec(lev >= 1 ? prof : nullptr, "setup_levels_ge1", s);
+        SPHC_TRY(build_level(L, lev, o, A1, D1, An1, lev == 0 ? prof : nullptr, s));
         if (L.nagg >= L.An.nr) break;      // no coarsening: this level is solved directly
         L.has_transfer = true;
         H.L.emplace_back();
@@ -132,8 +138,18 @@ int setup_impl(sphc_handle* h, const sphc_csr* A_e, const sphc_csr* D_h, cudaStr
     }
     H.nlev = lev + 1;
     H.n_coarse = H.L[lev].A.nr;
-    SPHC_TRY(coarse_inverse(H.L[lev].A, H.coarse_inv, s));
-    SPHC_TRY(build_vcycle_ops(H, s));
+    {
+        Section sec(prof, "setup_coarse_inverse", s);
+        SPHC_TRY(coarse_inverse(H.L[lev].A, H.coarse_inv, false, s));
+        if (o.vcycle_fp32) {
+            H.n_coarse_nodes = H.L[lev].An.nr;
+            SPHC_TRY(coarse_inverse(H.L[lev].An, H.coarse_inv_n, true, s));
+        }
+    }
+    {
+        Section sec(prof, "setup_vcycle_ops", s);
+        SPHC_TRY(build_vcycle_ops(H, s));
+    }
     SPHC_CK(cudaStreamSynchronize(s));
     return SPHC_OK;
 }

@@ -599,11 +599,14 @@ k_p0(int64_t ne, const int64_t* trp, const int32_t* tci, const double* tv, const
     if (lane == 0 && hist) atomicAdd(&hist[(np < 32 ? np : 32) * 33 + (m < 32 ? m : 32)], 1ULL);
     if (np == 0) return;
     if (k < 0) { if (lane == 0) atomicAdd(fail, 1); return; }
-    double z[MAX_T];
-    for (int q = 0; q < k; ++q) z[q] = S.r[q];
-    chol_solve(S.L, k, z);
+    // one lane solves (FP64 is scarce); the others read the solution from shared memory
+    if (lane == 0) {
+        for (int q = 0; q < k; ++q) S.y[q] = S.r[q];
+        chol_solve(S.L, k, S.y);
+    }
+    __syncwarp();
     int64_t n0 = nrp[i];
-    for (int t = lane; t < np; t += 32) p0[n0 + t] = gz(S, t, k, z);
+    for (int t = lane; t < np; t += 32) p0[n0 + t] = gz(S, t, k, S.y);
 }
 
 // one projected-Jacobi step (eq. (9)): dP = D^-1 (A P)|_N, projected row by row, P' = P - w dP
@@ -678,12 +681,11 @@ k_emin(int64_t ne, const int64_t* arp, const int32_t* aci, const double* av, con
         if (b >= 0 && b < k) atomicAdd(&S.y[b], S.acc[t]);
     }
     __syncwarp();
-    double z[MAX_T];
-    for (int q = 0; q < k; ++q) z[q] = S.y[q];
-    chol_solve(S.L, k, z);
+    if (lane == 0) chol_solve(S.L, k, S.y);
+    __syncwarp();
     int64_t n0 = nrp[i];
     for (int t = lane; t < np; t += 32) {
-        double dp = S.acc[t] - gz(S, t, k, z);
+        double dp = S.acc[t] - gz(S, t, k, S.y);
         Pout[n0 + t] = P[n0 + t] - omega * dp;
     }
 }
@@ -739,7 +741,15 @@ __global__ void k_chol_inverse(const double* L, int n, double* Ainv) {
     for (int r = threadIdx.x; r < n; r += blockDim.x) Ainv[(int64_t)r * n + c] = xs[r];
 }
 
-int coarse_inverse(const DCSR& A, DBuf<double>& Ainv, cudaStream_t s) {
+__global__ void k_shift_diag(double* M, int64_t n, double rel) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) M[i * n + i] *= (1.0 + rel);
+}
+
+// Dense FP64 inverse of a small SPD operator.  With allow_shift, a singular operator (the
+// nodal operator of a natural-boundary problem, whose constants are in its null space) is
+// factored after scaling its diagonal by 1 + 1e-10.
+int coarse_inverse(const DCSR& A, DBuf<double>& Ainv, bool allow_shift, cudaStream_t s) {
     int64_t n = A.nr;
     if (n > 8192) { set_error("coarsest level of %lld rows is too large for the dense solve", (long long)n); return SPHC_ELIMIT; }
     SPHC_TRY(Ainv.alloc(n * n, s));
@@ -748,21 +758,28 @@ int coarse_inverse(const DCSR& A, DBuf<double>& Ainv, cudaStream_t s) {
     SPHC_TRY(M.alloc(n * n, s));
     DBuf<int> bad;
     SPHC_TRY(bad.alloc(1, s));
-    SPHC_TRY(bad.zero(s));
-    SPHC_LAUNCH(k_dense_from_csr<<<grid_for(n, 128), 128, 0, s>>>(A.rp.p, A.ci.p, A.v.p, n, M.p));
-    for (int j = 0; j < n; ++j) {
-        SPHC_LAUNCH(k_chol_col<<<1, 256, 0, s>>>(M.p, (int)n, j, bad.p));
-        int64_t rem = n - j - 1;
-        if (rem > 0) SPHC_LAUNCH(k_chol_update<<<grid_for(rem * rem, 256), 256, 0, s>>>(M.p, (int)n, j));
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        SPHC_TRY(bad.zero(s));
+        SPHC_LAUNCH(k_dense_from_csr<<<grid_for(n, 128), 128, 0, s>>>(A.rp.p, A.ci.p, A.v.p, n, M.p));
+        if (attempt == 1) SPHC_LAUNCH(k_shift_diag<<<grid_for(n, 128), 128, 0, s>>>(M.p, n, 1e-10));
+        for (int j = 0; j < n; ++j) {
+            SPHC_LAUNCH(k_chol_col<<<1, 256, 0, s>>>(M.p, (int)n, j, bad.p));
+            int64_t rem = n - j - 1;
+            if (rem > 0) SPHC_LAUNCH(k_chol_update<<<grid_for(rem * rem, 256), 256, 0, s>>>(M.p, (int)n, j));
+        }
+        int hb = 0;
+        SPHC_CK(cudaMemcpyAsync(&hb, bad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+        SPHC_CK(cudaStreamSynchronize(s));
+        if (!hb) break;
+        if (!allow_shift || attempt == 1) {
+            set_error("coarsest operator is not numerically positive definite");
+            return SPHC_ENUMERIC;
+        }
     }
     size_t sm = sizeof(double) * n;
     if (sm > 48 * 1024) SPHC_CK(cudaFuncSetAttribute(k_chol_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     SPHC_LAUNCH(k_chol_inverse<<<(unsigned)n, 256, sm, s>>>(M.p, (int)n, Ainv.p));
     SPHC_CK(cudaGetLastError());
-    int hb = 0;
-    SPHC_CK(cudaMemcpyAsync(&hb, bad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
-    SPHC_CK(cudaStreamSynchronize(s));
-    if (hb) { set_error("coarsest operator is not numerically positive definite"); return SPHC_ENUMERIC; }
     return SPHC_OK;
 }
 
@@ -772,7 +789,11 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
     uint64_t seed = o.seed + 1000ULL * (uint64_t)lev;
     int64_t nv = L.An.nr, ne = L.A.nr;
     // aggregation on the structural nodal graph (drop tolerance 0)
-    SPHC_TRY(aggregate(L.An, seed + 1, L.agg, &L.nagg, s));
+    {
+        Section sec(prof, "setup_aggregate_l0", s);
+        SPHC_TRY(aggregate(L.An, seed + 1, L.agg, &L.nagg, s));
+    }
+    Section* sec_pn = new Section(prof, "setup_Pn_l0", s);
     // smoothed nodal prolongator
     DBuf<double> dn;
     SPHC_TRY(dn.alloc(nv, s));
@@ -794,8 +815,13 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
     SPHC_CK(cudaStreamSynchronize(s));
     if (hf[1]) { set_error("non-finite nodal prolongator row sum on level %d", lev); return SPHC_ENUMERIC; }
     L.n_rows_unsmoothed = hf[0];
+    delete sec_pn;
     // coarse gradient from the tentative aggregates
-    SPHC_TRY(coarse_gradient(L.D, L.Dt, L.agg.p, L.nagg, L.DH, s));
+    {
+        Section sec(prof, "setup_DH_l0", s);
+        SPHC_TRY(coarse_gradient(L.D, L.Dt, L.agg.p, L.nagg, L.DH, s));
+    }
+    Section* sec_pat = new Section(prof, "setup_pattern_l0", s);
     // T = D P_n (values r), N (Alg. 2)
     SPHC_TRY(spgemm(L.D, L.Pn, L.T, s));
     DCSR DHt;
@@ -831,6 +857,8 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
         SPHC_LAUNCH(k_pattern<<<grid_for(ne, PAT_WARPS), PAT_WARPS * 32, 0, s>>>(L.T.rp.p, L.T.ci.p, ne, DHt.rp.p, DHt.ci.p,
                                                                     L.DH.rp.p, L.DH.ci.p, 1, nullptr, L.P0.rp.p,
                                                                     L.P0.ci.p, st.p));
+    delete sec_pat;
+    Section* sec_p0 = new Section(prof, "setup_P0_l0", s);
     // initial guess and energy minimisation
     SPHC_TRY(L.hist.alloc(33 * 33, s));
     SPHC_TRY(L.hist.zero(s));
@@ -843,6 +871,7 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
                                                                   L.DH.rp.p, L.DH.ci.p, L.DH.v.p, L.P0.v.p, st.p,
                                                                   L.hist.p));
     SPHC_TRY(csr_copy(L.P0, L.Pe, s));
+    delete sec_p0;
     DBuf<double> Pnew;
     SPHC_TRY(Pnew.alloc(nnzN, s));
     // algorithmic bytes of one step: A (values, columns, row pointers), the pattern rows of P
@@ -863,7 +892,10 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
     SPHC_CK(cudaStreamSynchronize(s));
     if (hs[0]) { set_error("level %d: %d local constraint systems are infeasible", lev, hs[0]); return SPHC_EINFEASIBLE; }
     // Galerkin operators of the next level
-    SPHC_TRY(transpose(L.Pe, L.PeT, s));
+    {
+        Section sec(prof, "setup_PeT_l0", s);
+        SPHC_TRY(transpose(L.Pe, L.PeT, s));
+    }
     {
         int rid = prof ? prof->find("rap_level0", 0.0) : -1;
         if (rid >= 0) prof->begin(rid, s);
@@ -873,6 +905,7 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
         if (rid >= 0) prof->end(rid, s);
     }
     {
+        Section sec(prof, "setup_nodal_rap_l0", s);
         DCSR PnT, AnP;
         SPHC_TRY(transpose(L.Pn, PnT, s));
         SPHC_TRY(spgemm(L.An, L.Pn, AnP, s));

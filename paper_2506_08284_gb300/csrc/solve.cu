@@ -204,23 +204,42 @@ __global__ void k_dt_encode(const int64_t* rp, const int32_t* ci, const double* 
 }
 
 template <typename T>
-static int build_vlevel(Hierarchy& H, int l, VLevel<T>& V, cudaStream_t s) {
+static int build_vlevel(Hierarchy& H, int l, VLevel<T>& V, bool split, cudaStream_t s) {
     Level& L = H.L[l];
     int64_t ne = L.A.nr, nv = L.An.nr;
     SPHC_TRY(V.x.alloc(ne, s));
     SPHC_TRY(V.b.alloc(ne, s));
     SPHC_TRY(V.r.alloc(ne, s));
+    if (split) {
+        SPHC_TRY(V.c.alloc(nv, s));
+        SPHC_TRY(V.dc.alloc(nv, s));
+        SPHC_TRY(V.bp.alloc(ne, s));
+        SPHC_TRY(V.D.alloc(ne, s));
+        if (ne > 0) SPHC_LAUNCH(k_d_pairs<<<grid_for(ne, 256), 256, 0, s>>>(L.D.rp.p, L.D.ci.p, L.D.v.p, ne, V.D.p));
+        SPHC_TRY(V.Dt_rp.alloc(nv + 1, s));
+        SPHC_TRY(V.Dt_e.alloc(L.Dt.nnz, s));
+        int64_t m0 = L.Dt.nnz > nv + 1 ? L.Dt.nnz : nv + 1;
+        SPHC_LAUNCH(k_dt_encode<<<grid_for(m0, 256), 256, 0, s>>>(L.Dt.rp.p, L.Dt.ci.p, L.Dt.v.p, nv, L.Dt.nnz, V.Dt_rp.p, V.Dt_e.p));
+    }
     if (l == H.nlev - 1) return SPHC_OK;
+    if (split) {
+        DCSR AD;
+        SPHC_TRY(spgemm(L.A, L.D, AD, s));        // FP64: the curl-curl part of A D cancels here
+        SPHC_TRY(build_vcsr<T>(AD, V.AD, s));
+        SPHC_TRY(build_vcsr<T>(L.Pn, V.Pn, s));
+    }
     SPHC_TRY(build_smooth_op<T>(L.A, L.col_e.p, L.ncol_e, V.A, s));
     SPHC_TRY(build_smooth_op<T>(L.An, L.col_n.p, L.ncol_n, V.An, s));
     SPHC_TRY(V.g.alloc(nv, s));
-    SPHC_TRY(V.c.alloc(nv, s));
-    SPHC_TRY(V.D.alloc(ne, s));
-    if (ne > 0) SPHC_LAUNCH(k_d_pairs<<<grid_for(ne, 256), 256, 0, s>>>(L.D.rp.p, L.D.ci.p, L.D.v.p, ne, V.D.p));
-    SPHC_TRY(V.Dt_rp.alloc(nv + 1, s));
-    SPHC_TRY(V.Dt_e.alloc(L.Dt.nnz, s));
-    int64_t m = L.Dt.nnz > nv + 1 ? L.Dt.nnz : nv + 1;
-    SPHC_LAUNCH(k_dt_encode<<<grid_for(m, 256), 256, 0, s>>>(L.Dt.rp.p, L.Dt.ci.p, L.Dt.v.p, nv, L.Dt.nnz, V.Dt_rp.p, V.Dt_e.p));
+    if (!split) {
+        SPHC_TRY(V.c.alloc(nv, s));
+        SPHC_TRY(V.D.alloc(ne, s));
+        if (ne > 0) SPHC_LAUNCH(k_d_pairs<<<grid_for(ne, 256), 256, 0, s>>>(L.D.rp.p, L.D.ci.p, L.D.v.p, ne, V.D.p));
+        SPHC_TRY(V.Dt_rp.alloc(nv + 1, s));
+        SPHC_TRY(V.Dt_e.alloc(L.Dt.nnz, s));
+        int64_t m = L.Dt.nnz > nv + 1 ? L.Dt.nnz : nv + 1;
+        SPHC_LAUNCH(k_dt_encode<<<grid_for(m, 256), 256, 0, s>>>(L.Dt.rp.p, L.Dt.ci.p, L.Dt.v.p, nv, L.Dt.nnz, V.Dt_rp.p, V.Dt_e.p));
+    }
     SPHC_TRY(build_vcsr<T>(L.Pe, V.Pe, s));
     SPHC_TRY(build_vcsr<T>(L.PeT, V.PeT, s));
     SPHC_CK(cudaGetLastError());
@@ -231,11 +250,11 @@ int build_vcycle_ops(Hierarchy& H, cudaStream_t s) {
     if (H.opts.vcycle_fp32) {
         H.V32.clear();
         H.V32.resize(H.nlev);
-        for (int l = 0; l < H.nlev; ++l) SPHC_TRY(build_vlevel<float>(H, l, H.V32[l], s));
+        for (int l = 0; l < H.nlev; ++l) SPHC_TRY(build_vlevel<float>(H, l, H.V32[l], true, s));
     } else {
         H.V64.clear();
         H.V64.resize(H.nlev);
-        for (int l = 0; l < H.nlev; ++l) SPHC_TRY(build_vlevel<double>(H, l, H.V64[l], s));
+        for (int l = 0; l < H.nlev; ++l) SPHC_TRY(build_vlevel<double>(H, l, H.V64[l], false, s));
     }
     int64_t n0 = H.L[0].A.nr;
     SPHC_TRY(H.x.alloc(n0, s));
@@ -247,6 +266,8 @@ int build_vcycle_ops(Hierarchy& H, cudaStream_t s) {
     SPHC_TRY(H.scal.alloc(16, s));
     SPHC_TRY(H.cb.alloc(H.n_coarse, s));
     SPHC_TRY(H.cx.alloc(H.n_coarse, s));
+    SPHC_TRY(H.cgn.alloc(H.n_coarse_nodes, s));
+    SPHC_TRY(H.ccn.alloc(H.n_coarse_nodes, s));
     return SPHC_OK;
 }
 
@@ -289,7 +310,7 @@ __global__ void k_resid(const int32_t* __restrict__ rp, const int32_t* __restric
 
 template <typename T, int SUB>
 __global__ void k_spmv_v(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const T* __restrict__ v,
-                         int64_t n, const T* __restrict__ x, T* y, int accumulate) {
+                         int64_t n, const T* __restrict__ x, T* y, int accumulate, T alpha) {
     int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / SUB;
     int q = threadIdx.x & (SUB - 1);
     bool valid = i < n;
@@ -298,7 +319,7 @@ __global__ void k_spmv_v(const int32_t* __restrict__ rp, const int32_t* __restri
         for (int32_t e = rp[i] + q; e < rp[i + 1]; e += SUB) sum += v[e] * x[ci[e]];
 #pragma unroll
     for (int o = SUB / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o, SUB);
-    if (valid && q == 0) y[i] = accumulate ? y[i] + sum : sum;
+    if (valid && q == 0) y[i] = accumulate ? y[i] + alpha * sum : alpha * sum;
 }
 
 template <typename T>
@@ -385,20 +406,18 @@ static void resid(const SmoothOp<T>& op, const T* b, const T* x, T* r, cudaStrea
     }
 }
 template <typename T>
-static void spmv_v(const VCSR<T>& A, const T* x, T* y, int acc, cudaStream_t s) {
+static void spmv_v(const VCSR<T>& A, const T* x, T* y, int acc, cudaStream_t s, T alpha = T(1)) {
     if (A.nr == 0) return;
     int sub = sub_for(A.nnz, A.nr);
     int64_t th = A.nr * sub;
     switch (sub) {
-        case 4: SPHC_LAUNCH(k_spmv_v<T, 4><<<grid_for(th, 256), 256, 0, s>>>(A.rp.p, A.ci.p, A.v.p, A.nr, x, y, acc)); break;
-        case 8: SPHC_LAUNCH(k_spmv_v<T, 8><<<grid_for(th, 256), 256, 0, s>>>(A.rp.p, A.ci.p, A.v.p, A.nr, x, y, acc)); break;
-        case 16: SPHC_LAUNCH(k_spmv_v<T, 16><<<grid_for(th, 256), 256, 0, s>>>(A.rp.p, A.ci.p, A.v.p, A.nr, x, y, acc)); break;
-        default: SPHC_LAUNCH(k_spmv_v<T, 32><<<grid_for(th, 256), 256, 0, s>>>(A.rp.p, A.ci.p, A.v.p, A.nr, x, y, acc)); break;
+        case 4: SPHC_LAUNCH(k_spmv_v<T, 4><<<grid_for(th, 256), 256, 0, s>>>(A.rp.p, A.ci.p, A.v.p, A.nr, x, y, acc, alpha)); break;
+        case 8: SPHC_LAUNCH(k_spmv_v<T, 8><<<grid_for(th, 256), 256, 0, s>>>(A.rp.p, A.ci.p, A.v.p, A.nr, x, y, acc, alpha)); break;
+        case 16: SPHC_LAUNCH(k_spmv_v<T, 16><<<grid_for(th, 256), 256, 0, s>>>(A.rp.p, A.ci.p, A.v.p, A.nr, x, y, acc, alpha)); break;
+        default: SPHC_LAUNCH(k_spmv_v<T, 32><<<grid_for(th, 256), 256, 0, s>>>(A.rp.p, A.ci.p, A.v.p, A.nr, x, y, acc, alpha)); break;
     }
 }
 
-// one symmetric Hiptmair sweep (Sec. 6.1): SGS on A, nodal SGS on D^T A D with c0 = 0 applied
-// to D^T r, correction x += D c, SGS on A
 // algorithmic bytes of one forward + backward sweep: the matrix once per direction and, per
 // row, its pointer, permutation, inverse diagonal, right side and one read and write of x
 template <typename T>
@@ -446,12 +465,115 @@ static void vcycle_level(Hierarchy& H, std::vector<VLevel<T>>& V, int l, cudaStr
     hiptmair(H, l, V[l], ne, nv, s);
 }
 
+// ------------------------------------------------------------------ split V-cycle (FP32)
+// The FP32 V-cycle keeps its iterate as x = y + D c.  Stored in FP32, the curl-curl part of A no
+// longer annihilates gradients exactly (K D = O(eps32 |K|)), so a large gradient component of x
+// would swamp the sigma-scale residual.  Here every gradient correction (the nodal step of the
+// Hiptmair sweep and, through the commuting relation P_e D_H = D_h P_n, the gradient part of the
+// coarse correction) is kept in the nodal potential c, and its effect on the residual is applied
+// through A D, formed in FP64 (where K D cancels) and stored in FP32: b' = b - (A D) c.
+template <typename T>
+__global__ void k_axpy(T* y, const T* x, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] += x[i];
+}
+template <typename T>
+__global__ void k_copy(T* y, const T* x, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = x[i];
+}
+// z = y + D c in FP64
+template <typename T>
+__global__ void k_combine(const T* __restrict__ y, const int2* __restrict__ D, const T* __restrict__ c, int64_t n,
+                          double* __restrict__ z) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    int2 d = D[e];
+    double v = (double)y[e];
+    if (d.y >= 0) v += (double)c[d.y];
+    if (d.x >= 0) v -= (double)c[d.x];
+    z[e] = v;
+}
+__global__ void k_dense_mv64(const double* __restrict__ M, int64_t n, const double* __restrict__ b, double* __restrict__ x) {
+    int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (i >= n) return;
+    double s = 0.0;
+    for (int64_t j = lane; j < n; j += 32) s += M[i * n + j] * b[j];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) x[i] = s;
+}
+// coarsest split: y = A^-1 b - D c, c = A_n^-1 D^T b (FP64), so that y is A-orthogonal to gradients
+template <typename T>
+__global__ void k_split_out(const double* __restrict__ xb, const int2* __restrict__ D, const double* __restrict__ cc,
+                            int64_t ne, int64_t nv, T* __restrict__ y, T* __restrict__ c) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < ne) {
+        int2 d = D[i];
+        double g = 0.0;
+        if (d.y >= 0) g += cc[d.y];
+        if (d.x >= 0) g -= cc[d.x];
+        y[i] = (T)(xb[i] - g);
+    }
+    if (i < nv) c[i] = (T)cc[i];
+}
+
+template <typename T>
+static void coarse_split(Hierarchy& H, VLevel<T>& V, int64_t ne, int64_t nv, cudaStream_t s) {
+    if (ne == 0) return;
+    SPHC_LAUNCH(k_cast<T, double><<<grid_for(ne, 256), 256, 0, s>>>(V.b.p, H.cb.p, ne));
+    SPHC_LAUNCH(k_dense_mv64<<<grid_for(ne * 32, 256), 256, 0, s>>>(H.coarse_inv.p, ne, H.cb.p, H.cx.p));
+    if (nv > 0) {
+        SPHC_LAUNCH(k_dt_gather<double><<<grid_for(nv, 256), 256, 0, s>>>(V.Dt_rp.p, V.Dt_e.p, nv, H.cb.p, H.cgn.p));
+        SPHC_LAUNCH(k_dense_mv64<<<grid_for(nv * 32, 256), 256, 0, s>>>(H.coarse_inv_n.p, nv, H.cgn.p, H.ccn.p));
+    }
+    int64_t m = ne > nv ? ne : nv;
+    SPHC_LAUNCH(k_split_out<T><<<grid_for(m, 256), 256, 0, s>>>(H.cx.p, V.D.p, H.ccn.p, ne, nv, V.x.p, V.c.p));
+}
+
+template <typename T>
+static void hiptmair_split(Hierarchy& H, int lev, VLevel<T>& V, int64_t ne, int64_t nv, cudaStream_t s) {
+    timed_sgs(H, lev, V.A, V.bp.p, V.x.p, s);
+    if (nv > 0) {
+        resid(V.A, V.bp.p, V.x.p, V.r.p, s);
+        SPHC_LAUNCH(k_dt_gather<T><<<grid_for(nv, 256), 256, 0, s>>>(V.Dt_rp.p, V.Dt_e.p, nv, V.r.p, V.g.p));
+        SPHC_LAUNCH(k_zero<T><<<grid_for(nv, 256), 256, 0, s>>>(V.dc.p, nv));
+        sgs(V.An, V.g.p, V.dc.p, s);
+        SPHC_LAUNCH(k_axpy<T><<<grid_for(nv, 256), 256, 0, s>>>(V.c.p, V.dc.p, nv));
+        spmv_v(V.AD, V.dc.p, V.bp.p, 1, s, T(-1));
+    }
+    timed_sgs(H, lev, V.A, V.bp.p, V.x.p, s);
+}
+
+template <typename T>
+static void vcycle_split(Hierarchy& H, std::vector<VLevel<T>>& V, int l, cudaStream_t s) {
+    int64_t ne = H.L[l].A.nr, nv = H.L[l].An.nr;
+    if (l == H.nlev - 1) {
+        coarse_split(H, V[l], ne, nv, s);
+        return;
+    }
+    SPHC_LAUNCH(k_zero<T><<<grid_for(ne, 256), 256, 0, s>>>(V[l].x.p, ne));
+    if (nv > 0) SPHC_LAUNCH(k_zero<T><<<grid_for(nv, 256), 256, 0, s>>>(V[l].c.p, nv));
+    SPHC_LAUNCH(k_copy<T><<<grid_for(ne, 256), 256, 0, s>>>(V[l].bp.p, V[l].b.p, ne));
+    hiptmair_split(H, l, V[l], ne, nv, s);
+    resid(V[l].A, V[l].bp.p, V[l].x.p, V[l].r.p, s);
+    spmv_v(V[l].PeT, V[l].r.p, V[l + 1].b.p, 0, s);
+    vcycle_split(H, V, l + 1, s);
+    spmv_v(V[l].Pe, V[l + 1].x.p, V[l].x.p, 1, s);           // y += P_e y_H
+    if (nv > 0) {
+        spmv_v(V[l].Pn, V[l + 1].c.p, V[l].dc.p, 0, s);      // c += P_n c_H  (P_e D_H = D_h P_n)
+        SPHC_LAUNCH(k_axpy<T><<<grid_for(nv, 256), 256, 0, s>>>(V[l].c.p, V[l].dc.p, nv));
+        spmv_v(V[l].AD, V[l].dc.p, V[l].bp.p, 1, s, T(-1));
+    }
+    hiptmair_split(H, l, V[l], ne, nv, s);
+}
+
 int apply_vcycle(Hierarchy& H, const double* r, double* z, cudaStream_t s) {
     int64_t n = H.L[0].A.nr;
     if (H.opts.vcycle_fp32) {
         SPHC_LAUNCH(k_cast<double, float><<<grid_for(n, 256), 256, 0, s>>>(r, H.V32[0].b.p, n));
-        vcycle_level<float>(H, H.V32, 0, s);
-        SPHC_LAUNCH(k_cast<float, double><<<grid_for(n, 256), 256, 0, s>>>(H.V32[0].x.p, z, n));
+        vcycle_split<float>(H, H.V32, 0, s);
+        SPHC_LAUNCH(k_combine<float><<<grid_for(n, 256), 256, 0, s>>>(H.V32[0].x.p, H.V32[0].D.p, H.V32[0].c.p, n, z));
     } else {
         SPHC_CK(cudaMemcpyAsync(H.V64[0].b.p, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
         vcycle_level<double>(H, H.V64, 0, s);

@@ -37,7 +37,9 @@ struct VLevel {
     DBuf<int2> D;                    // per edge: (node with -1, node with +1), -1 if absent
     DBuf<int32_t> Dt_rp, Dt_e;       // D^T: per node the incident edges, (edge << 1) | (coef < 0)
     VCSR<T> Pe, PeT;
-    DBuf<T> x, b, r, g, c;
+    // split iterate x = y + D c (FP32 V-cycle): A D formed in FP64 and P_n
+    VCSR<T> AD, Pn;
+    DBuf<T> x, b, r, g, c, bp, dc;
 };
 
 struct Level {
@@ -59,7 +61,7 @@ int color_graph(const DCSR& G, uint64_t seed, DBuf<int32_t>& color, int* ncolors
 int aggregate(const DCSR& G, uint64_t seed, DBuf<int32_t>& agg, int64_t* nagg, cudaStream_t s);
 int power_rho(const DCSR& A, const double* diag, uint64_t seed, int iters, double* rho, cudaStream_t s);
 int coarse_gradient(const DCSR& D, const DCSR& Dt, const int32_t* agg, int64_t nagg, DCSR& DH, cudaStream_t s);
-int coarse_inverse(const DCSR& A, DBuf<double>& Ainv, cudaStream_t s);
+int coarse_inverse(const DCSR& A, DBuf<double>& Ainv, bool allow_shift, cudaStream_t s);
 
 // Section timers: CUDA events recorded on the work stream around a named section; resolved
 // (cudaEventElapsedTime) when the profile is read.
@@ -83,13 +85,31 @@ struct Profiler {
 int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext, DCSR& Annext, Profiler* prof,
                 cudaStream_t s);
 
+// Scoped section timer (no-op when prof is null).
+struct Section {
+    Profiler* p;
+    int id = -1;
+    cudaStream_t s;
+    Section(Profiler* prof, const char* name, cudaStream_t stream, double bytes = 0.0) : p(prof), s(stream) {
+        if (p) {
+            id = p->find(name, bytes);
+            p->begin(id, s);
+        }
+    }
+    ~Section() {
+        if (p) p->end(id, s);
+    }
+};
+
 // solve.cu
 struct Hierarchy {
     sphc_opts opts;
     int nlev = 0;
     std::vector<Level> L;
     DBuf<double> coarse_inv;         // dense inverse of the coarsest operator (FP64)
-    int64_t n_coarse = 0;
+    DBuf<double> coarse_inv_n;       // dense inverse of the coarsest nodal operator (split V-cycle)
+    int64_t n_coarse = 0, n_coarse_nodes = 0;
+    DBuf<double> cgn, ccn;           // coarsest nodal work vectors (FP64)
     // V-cycle copies in the chosen precision
     std::vector<VLevel<float>> V32;
     std::vector<VLevel<double>> V64;

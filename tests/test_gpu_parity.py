@@ -124,6 +124,22 @@ def test_fp32_vcycle_solve(pair):
     assert it[0] <= ref["iters"] + 3
 
 
+def test_fp32_vcycle_close_to_fp64(pair):
+    # the split FP32 V-cycle (x = y + D c) against the oracle's FP64 V-cycle, in the A-norm
+    name, p, h, o, opts = pair
+    import torch
+    h32 = gpu_setup(p, vcycle_fp32=1, **opts)
+    r = meshgen.rhs(13, p.n_edges)
+    rt = torch.tensor(r, device="cuda")
+    zt = torch.empty_like(rt)
+    h32.vcycle(rt, zt)
+    torch.cuda.synchronize()
+    z, zo = zt.cpu().numpy(), o.vcycle(r)
+    A = sp.csr_matrix((p.A_val, p.A_col, p.A_rowptr))
+    e = z - zo
+    assert np.sqrt(e @ (A @ e)) <= 1e-4 * np.sqrt(zo @ (A @ zo))
+
+
 def test_histogram_and_limits(pair):
     _, p, h, o, _ = pair
     for l in range(o.nlevels - 1):
