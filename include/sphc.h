@@ -66,8 +66,10 @@ typedef struct {
     int32_t vcycle_fp32;     /* 1: V-cycle in FP32 inside FP64 CG; 0: all FP64 (default 1) */
     int32_t max_iter;        /* CG iteration cap (default 500) */
     int32_t flexible;        /* 1: flexible (Polak-Ribiere) CG beta; 0: Fletcher-Reeves (default: = vcycle_fp32) */
-    int32_t profile;         /* 1: record CUDA-event section timers (sphc_get_profile) (default 0) */
-    int32_t reserved[6];
+    int32_t profile;         /* 1: record CUDA-event section timers (sphc_get_profile); with cg_graph the
+                                timers cover the first CG iteration, which runs outside the graph (default 0) */
+    int32_t cg_graph;        /* 1: run the CG iterations as one CUDA graph with a device-side loop (default 1) */
+    int32_t reserved[5];
 } sphc_opts;
 
 typedef struct sphc_handle sphc_handle;

@@ -170,6 +170,8 @@ int sphc_default_opts(sphc_opts* o) {
     o->vcycle_fp32 = 1;
     o->max_iter = 500;
     o->flexible = -1;
+    o->profile = 0;
+    o->cg_graph = 1;
     return SPHC_OK;
 }
 

@@ -16,17 +16,24 @@ namespace sphc {
 // every uncoloured neighbour takes the smallest colour absent from its coloured neighbours.
 static constexpr int MAX_COLORS = 256;
 
-__global__ void k_jp_round(const int64_t* rp, const int32_t* ci, int64_t n, uint64_t seed, int32_t* color,
-                           int* left, int* overflow) {
-    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= n) return;
+// One round over the rows still uncoloured (worklist `todo`); rows that stay uncoloured are
+// appended to `next`.  Decisions read colours in place: a row only colours itself once every
+// higher-priority neighbour is coloured, so the result equals the greedy colouring in priority
+// order whatever the interleaving inside a round.
+__global__ void k_jp_round(const int64_t* rp, const int32_t* ci, const int32_t* todo, int ntodo, uint64_t seed,
+                           int32_t* color, int32_t* next, int* nnext, int* overflow) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntodo) return;
+    int32_t v = todo[t];
     volatile int32_t* col = color;
-    if (col[v] >= 0) return;
     uint64_t hv = splitmix64(seed, (uint64_t)v);
     for (int64_t k = rp[v]; k < rp[v + 1]; ++k) {
         int32_t w = ci[k];
         if (w == v || col[w] >= 0) continue;
-        if (prio_greater(splitmix64(seed, (uint64_t)w), w, hv, v)) { atomicAdd(left, 1); return; }
+        if (prio_greater(splitmix64(seed, (uint64_t)w), w, hv, v)) {
+            next[atomicAdd(nnext, 1)] = v;
+            return;
+        }
     }
     uint64_t used[MAX_COLORS / 64] = {0, 0, 0, 0};
     for (int64_t k = rp[v]; k < rp[v + 1]; ++k) {
@@ -45,6 +52,10 @@ __global__ void k_fill_i32(int32_t* a, int64_t n, int32_t v) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) a[i] = v;
 }
+__global__ void k_iota_i32(int32_t* a, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = (int32_t)i;
+}
 __global__ void k_max_i32(const int32_t* a, int64_t n, int* mx) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) atomicMax(mx, a[i]);
@@ -55,17 +66,24 @@ int color_graph(const DCSR& G, uint64_t seed, DBuf<int32_t>& color, int* ncolors
     SPHC_TRY(color.alloc(n, s));
     if (n == 0) { *ncolors = 0; return SPHC_OK; }
     SPHC_LAUNCH(k_fill_i32<<<grid_for(n, 256), 256, 0, s>>>(color.p, n, -1));
+    DBuf<int32_t> la, lb;
+    SPHC_TRY(la.alloc(n, s));
+    SPHC_TRY(lb.alloc(n, s));
+    SPHC_LAUNCH(k_iota_i32<<<grid_for(n, 256), 256, 0, s>>>(la.p, n));
     DBuf<int> flags;
     SPHC_TRY(flags.alloc(3, s));
     SPHC_TRY(flags.zero(s));
     int h[3];
-    for (int round = 0; round < 100000; ++round) {
+    int ntodo = (int)n;
+    for (int round = 0; round < 100000 && ntodo > 0; ++round) {
         SPHC_CK(cudaMemsetAsync(flags.p, 0, sizeof(int), s));
-        SPHC_LAUNCH(k_jp_round<<<grid_for(n, 256), 256, 0, s>>>(G.rp.p, G.ci.p, n, seed, color.p, flags.p, flags.p + 1));
+        SPHC_LAUNCH(k_jp_round<<<grid_for(ntodo, 256), 256, 0, s>>>(G.rp.p, G.ci.p, la.p, ntodo, seed, color.p, lb.p,
+                                                                  flags.p, flags.p + 1));
         SPHC_CK(cudaMemcpyAsync(h, flags.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
         SPHC_CK(cudaStreamSynchronize(s));
         if (h[1]) { set_error("colouring needs more than %d colours", MAX_COLORS); return SPHC_ELIMIT; }
-        if (h[0] == 0) break;
+        ntodo = h[0];
+        std::swap(la.p, lb.p);
     }
     SPHC_CK(cudaMemsetAsync(flags.p + 2, 0, sizeof(int), s));
     SPHC_LAUNCH(k_max_i32<<<grid_for(n, 256), 256, 0, s>>>(color.p, n, flags.p + 2));
@@ -485,17 +503,28 @@ __global__ void k_pattern(const int64_t* trp, const int32_t* tci, int64_t ne, co
 }
 
 // ------------------------------------------------------------------ local least-norm systems
-// Per-warp view of the local system of fine row i: nodes T_i (m <= MAX_T), pattern entries
-// N_i (np <= MAX_NP) with the local indices of their coarse nodes and the signs of D_H.
+// Per-warp view of the local system of fine row i: nodes T_i (m <= MAX_T), pattern entries N_i
+// (np <= MAX_NP) with the local indices of their coarse nodes and the signs of D_H.
+//
+// The normal matrix G~^T G~ of a row is a small integer matrix (a grounded graph Laplacian).
+// FP64 throughput is scarce on this GPU, so it is factored in FP32 (LDL^T) and every solve is
+// refined three times against FP64 residuals evaluated exactly through the +-1 entries of G~;
+// each step gains about eps32 * cond, which brings the solution to FP64 accuracy.
 struct LocalSys {
     int32_t T[MAX_T];
     double r[MAX_T];
     int32_t N[MAX_NP];
     int8_t la[MAX_NP], lb[MAX_NP];    // local node (or -1) carrying -1 (la) / +1 (lb)
-    double acc[MAX_NP];               // per-entry work values
-    double y[MAX_T];
-    int G[MAX_T * MAX_T];             // integer Gram G~^T G~
-    double L[MAX_T * MAX_T];          // its Cholesky factor
+    double w[MAX_NP];                 // per-entry work values
+    double z[MAX_T];                  // solution being refined
+    double rhs[MAX_T];                // right side of the normal equations
+    double res[MAX_T];                // its FP64 residual
+    int16_t inc[2 * MAX_NP];          // node incidence lists: (entry << 1) | (coefficient < 0)
+    int inc_ptr[MAX_T + 1];
+    float xs[MAX_T];                  // FP32 right side / solution of the factored solve
+    int G[MAX_T * MAX_T];             // integer G~^T G~
+    float L[MAX_T * MAX_T];           // FP32 LDL^T (unit lower triangle below the diagonal)
+    float dinv[MAX_T];
 };
 
 // Load the row, build G~^T G~ and factor it; returns k (columns kept) or -1 on failure.
@@ -519,7 +548,7 @@ __device__ int local_setup(LocalSys& S, int64_t i, const int64_t* trp, const int
         for (int q = 0; q < len; ++q) {
             int32_t u = hci[b + q];
             int loc = -1;
-            for (int z = 0; z < m; ++z) if (S.T[z] == u) loc = z;
+            for (int zz = 0; zz < m; ++zz) if (S.T[zz] == u) loc = zz;
             if (hv[b + q] < 0) la = (int8_t)loc; else lb = (int8_t)loc;
         }
         S.la[t] = la;
@@ -538,41 +567,58 @@ __device__ int local_setup(LocalSys& S, int64_t i, const int64_t* trp, const int
         if (ib) atomicAdd(&S.G[b * k + b], 1);
         if (ia && ib) { atomicAdd(&S.G[a * k + b], -1); atomicAdd(&S.G[b * k + a], -1); }
     }
+    // incidence list of node a, built by lane a in entry order (deterministic sums below)
+    int cnt = 0;
+    if (lane < k)
+        for (int t = 0; t < np; ++t) cnt += (S.la[t] == lane) + (S.lb[t] == lane);
+    int incl = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+        int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane < k) {
+        int c = incl - cnt;
+        S.inc_ptr[lane] = c;
+        for (int t = 0; t < np; ++t) {
+            if (S.la[t] == lane) S.inc[c++] = (int16_t)((t << 1) | 1);
+            if (S.lb[t] == lane) S.inc[c++] = (int16_t)(t << 1);
+        }
+        if (lane == k - 1) S.inc_ptr[k] = c;
+    }
     __syncwarp();
-    for (int q = lane; q < k * k; q += 32) S.L[q] = (double)S.G[q];
+    for (int q = lane; q < k * k; q += 32) S.L[q] = (float)S.G[q];
     __syncwarp();
-    // right-looking Cholesky, lower triangle
     int ok = 1;
     for (int j = 0; j < k; ++j) {
-        double d = S.L[j * k + j];
-        if (!(d > 1e-9)) ok = 0;      // a disconnected local graph leaves a zero pivot
-        d = sqrt(d > 0 ? d : 1.0);
-        __syncwarp();
-        if (lane == 0) S.L[j * k + j] = d;
-        for (int r = j + 1 + lane; r < k; r += 32) S.L[r * k + j] /= d;
-        __syncwarp();
+        float d = S.L[j * k + j];
+        if (!(d > 1e-6f)) ok = 0;          // a disconnected local graph leaves a zero pivot
+        float inv = 1.0f / (d > 1e-6f ? d : 1.0f);
         int rem = k - j - 1;
         for (int q = lane; q < rem * rem; q += 32) {
             int r = j + 1 + q / rem, c = j + 1 + q % rem;
-            if (c <= r) S.L[r * k + c] -= S.L[r * k + j] * S.L[c * k + j];
+            if (c <= r) S.L[r * k + c] -= S.L[r * k + j] * S.L[c * k + j] * inv;
         }
+        __syncwarp();
+        for (int r = j + 1 + lane; r < k; r += 32) S.L[r * k + j] *= inv;
+        if (lane == 0) S.dinv[j] = inv;
         __syncwarp();
     }
     if (k > np) ok = 0;
     return ok ? k : -1;
 }
 
-// y := (L L^T)^-1 y for k unknowns (every lane computes the same result)
-__device__ inline void chol_solve(const double* L, int k, double* y) {
+// x := (L D L^T)^-1 x in FP32 (one lane)
+__device__ inline void ldl_solve32(const float* L, const float* dinv, int k, float* x) {
     for (int r = 0; r < k; ++r) {
-        double s = y[r];
-        for (int c = 0; c < r; ++c) s -= L[r * k + c] * y[c];
-        y[r] = s / L[r * k + r];
+        float s = x[r];
+        for (int c = 0; c < r; ++c) s -= L[r * k + c] * x[c];
+        x[r] = s;
     }
+    for (int r = 0; r < k; ++r) x[r] *= dinv[r];
     for (int r = k - 1; r >= 0; --r) {
-        double s = y[r];
-        for (int c = r + 1; c < k; ++c) s -= L[c * k + r] * y[c];
-        y[r] = s / L[r * k + r];
+        float s = x[r];
+        for (int c = r + 1; c < k; ++c) s -= L[c * k + r] * x[c];
+        x[r] = s;
     }
 }
 
@@ -583,6 +629,40 @@ __device__ inline double gz(const LocalSys& S, int t, int k, const double* z) {
     if (a >= 0 && a < k) v -= z[a];
     if (b >= 0 && b < k) v += z[b];
     return v;
+}
+
+// (G~^T v)_a for node a < k (one lane per node)
+__device__ inline double gtv(const LocalSys& S, int a, const double* v) {
+    double s = 0.0;
+    for (int q = S.inc_ptr[a]; q < S.inc_ptr[a + 1]; ++q) {
+        int code = S.inc[q];
+        double x = v[code >> 1];
+        s += (code & 1) ? -x : x;
+    }
+    return s;
+}
+
+// S.z = (G~^T G~)^-1 S.rhs: FP32 solve, then three FP64-residual refinement steps.  An FP64
+// instruction costs the whole warp's issue slot however many lanes are active, so every FP64
+// step is spread over the lanes; only the FP32 triangular solves run on one lane.
+__device__ void refine_solve(LocalSys& S, int k, int np) {
+    int lane = threadIdx.x & 31;
+    if (lane < k) S.xs[lane] = (float)S.rhs[lane];
+    __syncwarp();
+    if (lane == 0) ldl_solve32(S.L, S.dinv, k, S.xs);
+    __syncwarp();
+    if (lane < k) S.z[lane] = (double)S.xs[lane];
+    __syncwarp();
+    for (int step = 0; step < 3; ++step) {
+        for (int t = lane; t < np; t += 32) S.w[t] = gz(S, t, k, S.z);
+        __syncwarp();
+        if (lane < k) S.xs[lane] = (float)(S.rhs[lane] - gtv(S, lane, S.w));
+        __syncwarp();
+        if (lane == 0) ldl_solve32(S.L, S.dinv, k, S.xs);
+        __syncwarp();
+        if (lane < k) S.z[lane] += (double)S.xs[lane];
+        __syncwarp();
+    }
 }
 
 // least-norm initial guess P0_i = G~ (G~^T G~)^-1 r~_i
@@ -599,14 +679,11 @@ k_p0(int64_t ne, const int64_t* trp, const int32_t* tci, const double* tv, const
     if (lane == 0 && hist) atomicAdd(&hist[(np < 32 ? np : 32) * 33 + (m < 32 ? m : 32)], 1ULL);
     if (np == 0) return;
     if (k < 0) { if (lane == 0) atomicAdd(fail, 1); return; }
-    // one lane solves (FP64 is scarce); the others read the solution from shared memory
-    if (lane == 0) {
-        for (int q = 0; q < k; ++q) S.y[q] = S.r[q];
-        chol_solve(S.L, k, S.y);
-    }
+    if (lane < k) S.rhs[lane] = S.r[lane];
     __syncwarp();
+    refine_solve(S, k, np);
     int64_t n0 = nrp[i];
-    for (int t = lane; t < np; t += 32) p0[n0 + t] = gz(S, t, k, S.y);
+    for (int t = lane; t < np; t += 32) p0[n0 + t] = gz(S, t, k, S.z);
 }
 
 // one projected-Jacobi step (eq. (9)): dP = D^-1 (A P)|_N, projected row by row, P' = P - w dP
@@ -615,9 +692,6 @@ k_emin(int64_t ne, const int64_t* arp, const int32_t* aci, const double* av, con
        const double* tv, const int64_t* nrp, const int32_t* nci, const int64_t* hrp, const int32_t* hci,
        const double* hv, const double* P, double* Pout, double omega, int* fail) {
     extern __shared__ unsigned char smem_raw[];
-    __shared__ int64_t s_off[LOC_WARPS][32];
-    __shared__ int64_t s_bst[LOC_WARPS][32];
-    __shared__ double s_av[LOC_WARPS][32];
     int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     LocalSys& S = ((LocalSys*)smem_raw)[w];
     int64_t i = (int64_t)blockIdx.x * LOC_WARPS + w;
@@ -626,66 +700,38 @@ k_emin(int64_t ne, const int64_t* arp, const int32_t* aci, const double* av, con
     int k = local_setup(S, i, trp, tci, tv, nrp, nci, hrp, hci, hv, &m, &np);
     if (np == 0) return;
     if (k < 0) { if (lane == 0) atomicAdd(fail, 1); return; }
-    for (int t = lane; t < np; t += 32) S.acc[t] = 0.0;
-    __syncwarp();
-    // masked product (A P)_{i, N_i}: every product a_if P_fj is matched against the sorted N_i
-    double aii = 0.0;
+    // masked product (A P)_{i, N_i}: each lane owns pattern entries and searches every P row f of
+    // A's row i for its column (one FMA per match, no atomics)
     int64_t a0 = arp[i], a1 = arp[i + 1];
-    for (int64_t base = a0; base < a1; base += 32) {
-        int64_t ka = base + lane;
-        int64_t len = 0, bstart = 0;
-        double aval = 0.0;
-        if (ka < a1) {
+    double aii = 1.0;
+    for (int64_t ka = a0; ka < a1; ++ka)
+        if (aci[ka] == i) aii = av[ka];
+    double inv_aii = 1.0 / aii;
+    for (int t = lane; t < np; t += 32) {
+        int32_t j = S.N[t];
+        double acc = 0.0;
+        for (int64_t ka = a0; ka < a1; ++ka) {
             int32_t f = aci[ka];
-            bstart = nrp[f];
-            len = nrp[f + 1] - bstart;
-            aval = av[ka];
-            if (f == i) aii = aval;
-        }
-        int64_t inc = len;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int64_t tt = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += tt;
-        }
-        int64_t total = __shfl_sync(0xffffffffu, inc, 31);
-        s_off[w][lane] = inc - len;
-        s_bst[w][lane] = bstart;
-        s_av[w][lane] = aval;
-        __syncwarp();
-        for (int64_t t = lane; t < total; t += 32) {
-            int lo = 0, hi = 31;
+            int64_t lo = nrp[f], hi = nrp[f + 1] - 1;
             while (lo < hi) {
-                int mid = (lo + hi + 1) >> 1;
-                if (s_off[w][mid] <= t) lo = mid; else hi = mid - 1;
+                int64_t mid = (lo + hi) >> 1;
+                if (nci[mid] < j) lo = mid + 1; else hi = mid;
             }
-            int64_t kb = s_bst[w][lo] + (t - s_off[w][lo]);
-            int32_t j = nci[kb];
-            int l = 0, h = np - 1;
-            while (l < h) {
-                int mid = (l + h) >> 1;
-                if (S.N[mid] < j) l = mid + 1; else h = mid;
-            }
-            if (np > 0 && S.N[l] == j) atomicAdd(&S.acc[l], s_av[w][lo] * P[kb]);
+            if (lo <= hi && nci[lo] == j) acc += av[ka] * P[lo];
         }
-        __syncwarp();
-    }
-    for (int o = 16; o > 0; o >>= 1) aii += __shfl_xor_sync(0xffffffffu, aii, o);
-    for (int t = lane; t < np; t += 32) S.acc[t] /= aii;
-    if (lane < k) S.y[lane] = 0.0;
-    __syncwarp();
-    // y = G~^T dP_i
-    for (int t = lane; t < np; t += 32) {
-        int a = S.la[t], b = S.lb[t];
-        if (a >= 0 && a < k) atomicAdd(&S.y[a], -S.acc[t]);
-        if (b >= 0 && b < k) atomicAdd(&S.y[b], S.acc[t]);
+        S.w[t] = acc * inv_aii;
     }
     __syncwarp();
-    if (lane == 0) chol_solve(S.L, k, S.y);
+    // projection onto null(G~^T): dp = w - G~ (G~^T G~)^-1 G~^T w
+    if (lane < k) S.rhs[lane] = gtv(S, lane, S.w);
     __syncwarp();
+    double wt[MAX_NP / 32];
+    for (int t = lane, q = 0; t < np; t += 32, ++q) wt[q] = S.w[t];
+    __syncwarp();
+    refine_solve(S, k, np);
     int64_t n0 = nrp[i];
-    for (int t = lane; t < np; t += 32) {
-        double dp = S.acc[t] - gz(S, t, k, S.y);
+    for (int t = lane, q = 0; t < np; t += 32, ++q) {
+        double dp = wt[q] - gz(S, t, k, S.z);
         Pout[n0 + t] = P[n0 + t] - omega * dp;
     }
 }

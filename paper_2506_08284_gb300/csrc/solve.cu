@@ -9,6 +9,8 @@
 
 namespace sphc {
 
+static constexpr int DOT_PARTS = 1024;
+
 // ------------------------------------------------------------------ section timers
 int Profiler::find(const char* name, double bytes) {
     for (size_t i = 0; i < timers.size(); ++i)
@@ -268,7 +270,42 @@ int build_vcycle_ops(Hierarchy& H, cudaStream_t s) {
     SPHC_TRY(H.cx.alloc(H.n_coarse, s));
     SPHC_TRY(H.cgn.alloc(H.n_coarse_nodes, s));
     SPHC_TRY(H.ccn.alloc(H.n_coarse_nodes, s));
+    SPHC_TRY(H.dpart.alloc(DOT_PARTS, s));
+    SPHC_TRY(H.itc.alloc(4, s));
     return SPHC_OK;
+}
+
+// ------------------------------------------------------------------ dot products into persistent partials
+__global__ void k_dot_part_b(const double* a, const double* b, int64_t n, double* part) {
+    __shared__ double sw[32];
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        s += a[i] * b[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = threadIdx.x < (blockDim.x >> 5) ? sw[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) part[blockIdx.x] = s;
+    }
+}
+__global__ void k_dot_final_b(const double* part, int np, double* out) {
+    __shared__ double sw[32];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < np; i += blockDim.x) s += part[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = threadIdx.x < (blockDim.x >> 5) ? sw[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) *out = s;
+    }
+}
+static void dot_buf(Hierarchy& H, const double* a, const double* b, int64_t n, double* out, cudaStream_t s) {
+    SPHC_LAUNCH(k_dot_part_b<<<DOT_PARTS, 256, 0, s>>>(a, b, n, H.dpart.p));
+    SPHC_LAUNCH(k_dot_final_b<<<1, 1024, 0, s>>>(H.dpart.p, DOT_PARTS, out));
 }
 
 // ------------------------------------------------------------------ V-cycle kernels
@@ -428,7 +465,7 @@ static double sgs_bytes(const SmoothOp<T>& op) {
 template <typename T>
 static void timed_sgs(Hierarchy& H, int lev, const SmoothOp<T>& op, const T* b, T* x, cudaStream_t s) {
     int id = -1;
-    if (H.prof.on && lev == 0) {
+    if (H.prof.on && lev == 0 && !H.capturing) {
         id = H.prof.find("sgs_A_level0", sgs_bytes(op));
         H.prof.begin(id, s);
     }
@@ -606,7 +643,136 @@ __global__ void k_sub(const double* b, double* q, int64_t n) {
     if (i < n) q[i] = b[i] - q[i];
 }
 
+// end of one graph iteration: count it and keep looping while not converged, not broken down
+// and below the iteration cap.  itc[1]: 0 converged, 1 breakdown, 2 cap reached.
+__global__ void k_cg_check(cudaGraphConditionalHandle hnd, const double* sc, int* itc, int max_iter) {
+    int it = itc[0] + 1;
+    itc[0] = it;
+    double pq = sc[1], rr = sc[2], lim = sc[7];
+    unsigned cont = 1;
+    if (!(pq > 0.0) || !isfinite(rr)) { itc[1] = 1; cont = 0; }
+    else if (rr <= lim) { itc[1] = 0; cont = 0; }
+    else if (it >= max_iter) { itc[1] = 2; cont = 0; }
+    cudaGraphSetConditional(hnd, cont);
+}
+__global__ void k_set_limit(double* sc, double tol2) { sc[7] = tol2 * sc[5]; }
+
+// one CG iteration after the first: z = M^-1 r, p = z + beta p, q = A p, x += alpha p, r -= alpha q
+static int cg_body(Hierarchy& H, cudaGraphConditionalHandle hnd, cudaStream_t s) {
+    const DCSR& A = H.L[0].A;
+    int64_t n = A.nr;
+    int flexible = H.opts.flexible;
+    double* sc = H.scal.p;
+    SPHC_TRY(apply_vcycle(H, H.r.p, H.z.p, s));
+    dot_buf(H, H.r.p, H.z.p, n, sc + 3, s);
+    if (flexible) dot_buf(H, H.z.p, H.rold.p, n, sc + 4, s);
+    SPHC_LAUNCH(k_cg_p<<<grid_for(n, 256), 256, 0, s>>>(H.p.p, H.z.p, sc, n, flexible));
+    SPHC_LAUNCH(k_cg_shift<<<1, 1, 0, s>>>(sc));
+    SPHC_TRY(spmv64(A, H.p.p, H.q.p, s));
+    dot_buf(H, H.p.p, H.q.p, n, sc + 1, s);
+    SPHC_LAUNCH(k_cg_xr<<<grid_for(n, 256), 256, 0, s>>>(H.x.p, H.r.p, H.rold.p, H.p.p, H.q.p, sc, n, flexible));
+    dot_buf(H, H.r.p, H.r.p, n, sc + 2, s);
+    SPHC_LAUNCH(k_cg_check<<<1, 1, 0, s>>>(hnd, sc, H.itc.p, H.opts.max_iter));
+    SPHC_CK(cudaGetLastError());
+    return SPHC_OK;
+}
+
+static int build_cg_graph(Hierarchy& H) {
+    if (H.cg_exec) return SPHC_OK;
+    if (!H.cap_stream) SPHC_CK(cudaStreamCreateWithFlags(&H.cap_stream, cudaStreamNonBlocking));
+    SPHC_CK(cudaGraphCreate(&H.cg_graph, 0));
+    cudaGraphConditionalHandle hnd;
+    SPHC_CK(cudaGraphConditionalHandleCreate(&hnd, H.cg_graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = hnd;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    SPHC_CK(cudaGraphAddNode(&node, H.cg_graph, nullptr, nullptr, 0, &np));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    SPHC_CK(cudaStreamBeginCaptureToGraph(H.cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    H.capturing = true;
+    long long l0 = g_launches.load();
+    int rc = cg_body(H, hnd, H.cap_stream);
+    H.body_launches = g_launches.load() - l0;
+    g_launches.fetch_sub(H.body_launches);      // counted when the graph runs, not when captured
+    H.capturing = false;
+    cudaGraph_t captured = nullptr;
+    cudaError_t e = cudaStreamEndCapture(H.cap_stream, &captured);
+    if (rc != SPHC_OK) return rc;
+    if (e != cudaSuccess) {
+        set_error("CG graph capture failed: %s", cudaGetErrorString(e));
+        return SPHC_ECUDA;
+    }
+    SPHC_CK(cudaGraphInstantiate(&H.cg_exec, H.cg_graph, 0));
+    return SPHC_OK;
+}
+
+// CG on the device: the first iteration is enqueued directly, the rest run inside one graph
+// launch whose while node repeats an iteration until the stopping test holds.
+static int pcg_graph(Hierarchy& H, const double* b, double* x, double tol, cudaStream_t s, int* iters,
+                     double* relres) {
+    const DCSR& A = H.L[0].A;
+    int64_t n = A.nr;
+    int flexible = H.opts.flexible;
+    double* sc = H.scal.p;
+    SPHC_TRY(build_cg_graph(H));
+    SPHC_CK(cudaMemsetAsync(H.x.p, 0, sizeof(double) * n, s));
+    SPHC_CK(cudaMemcpyAsync(H.r.p, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    dot_buf(H, b, b, n, sc + 5, s);
+    double hb = 0.0;
+    SPHC_CK(cudaMemcpyAsync(&hb, sc + 5, sizeof(double), cudaMemcpyDeviceToHost, s));
+    SPHC_CK(cudaStreamSynchronize(s));
+    double bnorm = sqrt(hb);
+    int status = SPHC_OK, it = 0;
+    if (bnorm > 0.0) {
+        SPHC_TRY(apply_vcycle(H, H.r.p, H.z.p, s));
+        SPHC_CK(cudaMemcpyAsync(H.p.p, H.z.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+        dot_buf(H, H.r.p, H.z.p, n, sc + 0, s);
+        {
+            Section sec(H.prof.on ? &H.prof : nullptr, "spmv_A_fp64", s, (double)A.nnz * 12.0 + (double)n * 24.0);
+            SPHC_TRY(spmv64(A, H.p.p, H.q.p, s));
+        }
+        dot_buf(H, H.p.p, H.q.p, n, sc + 1, s);
+        SPHC_LAUNCH(k_cg_xr<<<grid_for(n, 256), 256, 0, s>>>(H.x.p, H.r.p, H.rold.p, H.p.p, H.q.p, sc, n, flexible));
+        dot_buf(H, H.r.p, H.r.p, n, sc + 2, s);
+        SPHC_LAUNCH(k_set_limit<<<1, 1, 0, s>>>(sc, tol * tol));
+        int hi[2] = {1, 0};
+        SPHC_CK(cudaMemcpyAsync(H.itc.p, hi, 2 * sizeof(int), cudaMemcpyHostToDevice, s));
+        double hsc[8];
+        SPHC_CK(cudaMemcpyAsync(hsc, sc, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        SPHC_CK(cudaStreamSynchronize(s));
+        it = 1;
+        if (!(hsc[1] > 0.0) || !std::isfinite(hsc[2])) status = SPHC_EBREAKDOWN;
+        else if (hsc[2] <= hsc[7]) status = SPHC_OK;
+        else if (it >= H.opts.max_iter) status = SPHC_ENOTCONV;
+        else {
+            SPHC_CK(cudaGraphLaunch(H.cg_exec, s));
+            SPHC_CK(cudaMemcpyAsync(hi, H.itc.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+            SPHC_CK(cudaStreamSynchronize(s));
+            it = hi[0];
+            status = hi[1] == 0 ? SPHC_OK : (hi[1] == 1 ? SPHC_EBREAKDOWN : SPHC_ENOTCONV);
+            g_launches.fetch_add(H.body_launches * (long long)(it - 1));
+        }
+    }
+    SPHC_CK(cudaMemcpyAsync(x, H.x.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    // true residual
+    SPHC_TRY(spmv64(A, H.x.p, H.q.p, s));
+    SPHC_LAUNCH(k_sub<<<grid_for(n, 256), 256, 0, s>>>(b, H.q.p, n));
+    dot_buf(H, H.q.p, H.q.p, n, sc + 6, s);
+    double hr = 0.0;
+    SPHC_CK(cudaMemcpyAsync(&hr, sc + 6, sizeof(double), cudaMemcpyDeviceToHost, s));
+    SPHC_CK(cudaStreamSynchronize(s));
+    if (iters) *iters = it;
+    if (relres) *relres = bnorm > 0 ? sqrt(hr) / bnorm : 0.0;
+    if (status == SPHC_EBREAKDOWN) set_error("CG breakdown after %d iterations", it);
+    else if (status == SPHC_ENOTCONV) set_error("CG did not reach the tolerance in %d iterations", it);
+    return status;
+}
+
 int pcg_solve(Hierarchy& H, const double* b, double* x, double tol, cudaStream_t s, int* iters, double* relres) {
+    if (H.opts.cg_graph) return pcg_graph(H, b, x, tol, s, iters, relres);
     const DCSR& A = H.L[0].A;
     int64_t n = A.nr;
     int flexible = H.opts.flexible;

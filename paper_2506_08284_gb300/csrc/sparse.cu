@@ -305,87 +305,129 @@ int csr_diag(const DCSR& A, double* d, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------------ structural SpGEMM
-static constexpr int HASH_SLOTS = 1024;      // per warp (symbolic and numeric)
-static constexpr int HASH_FILL = 768;        // rows with more unique columns go to the big path
+// Row-wise: every product a_ik * b_kj of row i is inserted into a per-warp open-addressing
+// table in shared memory.  Rows are binned by their product count so that a row touches a table
+// of matching size (small tables also give more resident warps); rows with more than
+// BIG_FILL-capable output go to a block-per-row path.  The symbolic pass counts distinct columns,
+// the numeric pass accumulates, compacts and writes each row sorted by column.
+static constexpr int MED_SLOTS = 1024;       // largest per-warp table
+static constexpr int MED_FILL = 768;         // rows with more distinct columns go to the big path
 static constexpr int BIG_SLOTS = 8192;       // per block on the big path
 static constexpr int BIG_FILL = 6144;
-static constexpr int SPGEMM_WARPS = 8;
+static constexpr int NBINS = 3;
 
 __device__ inline uint32_t hslot(int32_t key, int mask) {
     return ((uint32_t)key * 2654435761u) & (uint32_t)mask;
 }
 
 __global__ void k_spgemm_ub(const int64_t* arp, const int32_t* aci, const int64_t* brp, int64_t n,
-                            int64_t* ub) {
+                            int64_t* ub, int* bin_cnt) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int64_t s = 0;
     for (int64_t k = arp[i]; k < arp[i + 1]; ++k) s += brp[aci[k] + 1] - brp[aci[k]];
     ub[i] = s;
+    int bin = s <= 64 ? 0 : (s <= 256 ? 1 : 2);
+    atomicAdd(&bin_cnt[bin], 1);
+}
+__global__ void k_spgemm_bin(const int64_t* ub, int64_t n, const int* bin_off, int* bin_fill, int32_t* rows) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t s = ub[i];
+    int bin = s <= 64 ? 0 : (s <= 256 ? 1 : 2);
+    rows[bin_off[bin] + atomicAdd(&bin_fill[bin], 1)] = (int32_t)i;
 }
 
-// symbolic phase: unique column count per row (-1 = needs the big path)
-__global__ void __launch_bounds__(SPGEMM_WARPS * 32)
+// flattened enumeration of the products of row i, 32 A-entries at a time
+struct ProdWindow {
+    int64_t off[32];
+    int64_t bst[32];
+    double av[32];
+};
+
+__device__ inline int64_t window_load(ProdWindow& W, const int64_t* aci_brp_dummy, int64_t base, int64_t a1,
+                                      const int32_t* aci, const double* av, const int64_t* brp, int lane) {
+    (void)aci_brp_dummy;
+    int64_t ka = base + lane;
+    int64_t len = 0, bstart = 0;
+    double aval = 0.0;
+    if (ka < a1) {
+        int32_t k = aci[ka];
+        bstart = brp[k];
+        len = brp[k + 1] - bstart;
+        aval = av ? av[ka] : 0.0;
+    }
+    int64_t inc = warp_incl_scan(len);
+    W.off[lane] = inc - len;
+    W.bst[lane] = bstart;
+    W.av[lane] = aval;
+    __syncwarp();
+    return __shfl_sync(0xffffffffu, inc, 31);
+}
+__device__ inline int window_find(const ProdWindow& W, int64_t t) {
+    int lo = 0, hi = 31;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (W.off[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// symbolic: distinct column count per listed row (0 and appended to big_list on overflow)
+template <int SLOTS, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32)
 k_spgemm_symbolic(const int64_t* arp, const int32_t* aci, const int64_t* brp, const int32_t* bci,
-                  int64_t n, const int64_t* ub, int64_t* cnt, int32_t* big_list, int* big_n) {
-    __shared__ int32_t s_keys[SPGEMM_WARPS][HASH_SLOTS];
-    __shared__ int64_t s_off[SPGEMM_WARPS][32];
-    __shared__ int64_t s_bst[SPGEMM_WARPS][32];
-    __shared__ int s_cnt[SPGEMM_WARPS];
+                  const int32_t* rows, int nrows, const int64_t* ub, int64_t* cnt, int32_t* big_list, int* big_n) {
+    __shared__ int32_t s_keys[WARPS][SLOTS];
+    __shared__ ProdWindow s_win[WARPS];
+    __shared__ int s_cnt[WARPS];
     int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int64_t i = (int64_t)blockIdx.x * SPGEMM_WARPS + w;
-    if (i >= n) return;
+    int64_t li = (int64_t)blockIdx.x * WARPS + w;
+    if (li >= nrows) return;
+    int64_t i = rows[li];
     int32_t* keys = s_keys[w];
-    for (int t = lane; t < HASH_SLOTS; t += 32) keys[t] = -1;
+    int64_t ubi = ub[i];
+    int tsize = 32;
+    while (tsize < SLOTS && tsize < 2 * ubi) tsize <<= 1;
+    int tmask = tsize - 1;
+    int fill = SLOTS == MED_SLOTS ? MED_FILL : SLOTS;
+    for (int t = lane; t < tsize; t += 32) keys[t] = -1;
     if (lane == 0) s_cnt[w] = 0;
     __syncwarp();
     bool overflow = false;
     int64_t a0 = arp[i], a1 = arp[i + 1];
     for (int64_t base = a0; base < a1 && !overflow; base += 32) {
-        int64_t ka = base + lane;
-        int64_t len = 0, bstart = 0;
-        if (ka < a1) {
-            int32_t k = aci[ka];
-            bstart = brp[k];
-            len = brp[k + 1] - bstart;
-        }
-        int64_t inc = warp_incl_scan(len);
-        int64_t total = __shfl_sync(0xffffffffu, inc, 31);
-        s_off[w][lane] = inc - len;
-        s_bst[w][lane] = bstart;
-        __syncwarp();
+        int64_t total = window_load(s_win[w], nullptr, base, a1, aci, nullptr, brp, lane);
         for (int64_t t0 = 0; t0 < total; t0 += 32) {
             int64_t t = t0 + lane;
             if (t < total) {
-                int lo = 0, hi = 31;
-                while (lo < hi) {
-                    int mid = (lo + hi + 1) >> 1;
-                    if (s_off[w][mid] <= t) lo = mid; else hi = mid - 1;
-                }
-                int32_t col = bci[s_bst[w][lo] + (t - s_off[w][lo])];
-                uint32_t h = hslot(col, HASH_SLOTS - 1);
-                for (int probe = 0; probe < HASH_SLOTS; ++probe) {
-                    int32_t old = atomicCAS(&keys[h], -1, col);
-                    if (old == -1) { atomicAdd(&s_cnt[w], 1); break; }
-                    if (old == col) break;
-                    h = (h + 1) & (HASH_SLOTS - 1);
+                int lo = window_find(s_win[w], t);
+                int32_t col = bci[s_win[w].bst[lo] + (t - s_win[w].off[lo])];
+                uint32_t h = hslot(col, tmask);
+                for (int probe = 0; probe < tsize; ++probe) {
+                    int32_t cur = keys[h];
+                    if (cur == col) break;
+                    if (cur == -1) {
+                        int32_t old = atomicCAS(&keys[h], -1, col);
+                        if (old == -1) { atomicAdd(&s_cnt[w], 1); break; }
+                        if (old == col) break;
+                    }
+                    h = (h + 1) & tmask;
                 }
             }
             __syncwarp();
-            if (s_cnt[w] > HASH_FILL) { overflow = true; break; }
+            if (s_cnt[w] > fill) { overflow = true; break; }
         }
         __syncwarp();
     }
     if (lane == 0) {
         if (overflow) {
             cnt[i] = 0;
-            int q = atomicAdd(big_n, 1);
-            big_list[q] = (int32_t)i;
+            big_list[atomicAdd(big_n, 1)] = (int32_t)i;
         } else {
             cnt[i] = s_cnt[w];
         }
     }
-    (void)ub;
 }
 
 // big path symbolic: one block per listed row
@@ -421,64 +463,55 @@ __global__ void k_spgemm_symbolic_big(const int64_t* arp, const int32_t* aci, co
     }
 }
 
-// numeric phase: accumulate, compact, sort by rank and write
-__global__ void __launch_bounds__(SPGEMM_WARPS * 32)
+// numeric: accumulate in the table, compact in place, write each entry at its rank
+template <int SLOTS, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32)
 k_spgemm_numeric(const int64_t* arp, const int32_t* aci, const double* av, const int64_t* brp,
-                 const int32_t* bci, const double* bv, int64_t n, const int64_t* crp, int32_t* cci,
-                 double* cv) {
-    extern __shared__ unsigned char smem_raw[];
+                 const int32_t* bci, const double* bv, const int32_t* rows, int nrows, const int64_t* crp,
+                 int32_t* cci, double* cv, const int64_t* ub) {
+    __shared__ int32_t s_keys[WARPS][SLOTS];
+    __shared__ double s_vals[WARPS][SLOTS];
+    __shared__ ProdWindow s_win[WARPS];
     int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int32_t* keys = (int32_t*)smem_raw + w * HASH_SLOTS;
-    double* vals = (double*)(smem_raw + sizeof(int32_t) * HASH_SLOTS * SPGEMM_WARPS) + w * HASH_SLOTS;
-    __shared__ int64_t s_off[SPGEMM_WARPS][32];
-    __shared__ int64_t s_bst[SPGEMM_WARPS][32];
-    __shared__ double s_av[SPGEMM_WARPS][32];
-    int64_t i = (int64_t)blockIdx.x * SPGEMM_WARPS + w;
-    if (i >= n) return;
-    int64_t c0 = crp[i], c1 = crp[i + 1];
-    int clen = (int)(c1 - c0);
-    if (clen > HASH_FILL) return;  // big path
-    for (int t = lane; t < HASH_SLOTS; t += 32) { keys[t] = -1; vals[t] = 0.0; }
+    int64_t li = (int64_t)blockIdx.x * WARPS + w;
+    if (li >= nrows) return;
+    int64_t i = rows[li];
+    int32_t* keys = s_keys[w];
+    double* vals = s_vals[w];
+    int64_t c0 = crp[i];
+    int clen = (int)(crp[i + 1] - c0);
+    int fill = SLOTS == MED_SLOTS ? MED_FILL : SLOTS;
+    if (clen > fill) return;  // big path
+    int64_t ubi = ub[i];
+    int tsize = 32;
+    while (tsize < SLOTS && tsize < 2 * ubi) tsize <<= 1;
+    while (tsize < SLOTS && tsize < 2 * clen) tsize <<= 1;
+    int tmask = tsize - 1;
+    for (int t = lane; t < tsize; t += 32) { keys[t] = -1; vals[t] = 0.0; }
     __syncwarp();
     int64_t a0 = arp[i], a1 = arp[i + 1];
     for (int64_t base = a0; base < a1; base += 32) {
-        int64_t ka = base + lane;
-        int64_t len = 0, bstart = 0;
-        double aval = 0.0;
-        if (ka < a1) {
-            int32_t k = aci[ka];
-            bstart = brp[k];
-            len = brp[k + 1] - bstart;
-            aval = av[ka];
-        }
-        int64_t inc = warp_incl_scan(len);
-        int64_t total = __shfl_sync(0xffffffffu, inc, 31);
-        s_off[w][lane] = inc - len;
-        s_bst[w][lane] = bstart;
-        s_av[w][lane] = aval;
-        __syncwarp();
+        int64_t total = window_load(s_win[w], nullptr, base, a1, aci, av, brp, lane);
         for (int64_t t = lane; t < total; t += 32) {
-            int lo = 0, hi = 31;
-            while (lo < hi) {
-                int mid = (lo + hi + 1) >> 1;
-                if (s_off[w][mid] <= t) lo = mid; else hi = mid - 1;
-            }
-            int64_t kb = s_bst[w][lo] + (t - s_off[w][lo]);
+            int lo = window_find(s_win[w], t);
+            int64_t kb = s_win[w].bst[lo] + (t - s_win[w].off[lo]);
             int32_t col = bci[kb];
-            double prod = s_av[w][lo] * bv[kb];
-            uint32_t h = hslot(col, HASH_SLOTS - 1);
-            for (int probe = 0; probe < HASH_SLOTS; ++probe) {
-                int32_t old = atomicCAS(&keys[h], -1, col);
-                if (old == -1 || old == col) { atomicAdd(&vals[h], prod); break; }
-                h = (h + 1) & (HASH_SLOTS - 1);
+            double prod = s_win[w].av[lo] * bv[kb];
+            uint32_t h = hslot(col, tmask);
+            for (int probe = 0; probe < tsize; ++probe) {
+                int32_t cur = keys[h];
+                if (cur == col) { atomicAdd(&vals[h], prod); break; }
+                if (cur == -1) {
+                    int32_t old = atomicCAS(&keys[h], -1, col);
+                    if (old == -1 || old == col) { atomicAdd(&vals[h], prod); break; }
+                }
+                h = (h + 1) & tmask;
             }
         }
         __syncwarp();
     }
-    // compact the occupied slots in place (a lane's target never exceeds its own slot), then
-    // write each entry at its rank among the row's columns
     int count = 0;
-    for (int t0 = 0; t0 < HASH_SLOTS; t0 += 32) {
+    for (int t0 = 0; t0 < tsize; t0 += 32) {
         int32_t k = keys[t0 + lane];
         double vv = vals[t0 + lane];
         unsigned m = __ballot_sync(0xffffffffu, k >= 0);
@@ -523,7 +556,6 @@ __global__ void k_spgemm_numeric_big(const int64_t* arp, const int32_t* aci, con
             }
         }
         __syncthreads();
-        // rank by counting, comparing against the table in chunks staged in s_ck
         int64_t c0 = crp[i];
         for (int t0 = 0; t0 < BIG_SLOTS; t0 += blockDim.x) {
             int t = t0 + threadIdx.x;
@@ -545,39 +577,61 @@ __global__ void k_spgemm_numeric_big(const int64_t* arp, const int32_t* aci, con
     }
 }
 
+template <int SLOTS, int WARPS>
+static void launch_symbolic(const DCSR& A, const DCSR& B, const int32_t* rows, int nrows, const int64_t* ub,
+                            int64_t* cnt, int32_t* big, int* bign, cudaStream_t s) {
+    if (nrows <= 0) return;
+    SPHC_LAUNCH((k_spgemm_symbolic<SLOTS, WARPS><<<(nrows + WARPS - 1) / WARPS, WARPS * 32, 0, s>>>(
+        A.rp.p, A.ci.p, B.rp.p, B.ci.p, rows, nrows, ub, cnt, big, bign)));
+}
+template <int SLOTS, int WARPS>
+static void launch_numeric(const DCSR& A, const DCSR& B, DCSR& C, const int32_t* rows, int nrows, const int64_t* ub,
+                           cudaStream_t s) {
+    if (nrows <= 0) return;
+    SPHC_LAUNCH((k_spgemm_numeric<SLOTS, WARPS><<<(nrows + WARPS - 1) / WARPS, WARPS * 32, 0, s>>>(
+        A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p, B.v.p, rows, nrows, C.rp.p, C.ci.p, C.v.p, ub)));
+}
+
 int spgemm(const DCSR& A, const DCSR& B, DCSR& C, cudaStream_t s) {
     if (A.nc != B.nr) {
         set_error("spgemm: inner dimensions %lld vs %lld", (long long)A.nc, (long long)B.nr);
         return SPHC_EINVAL;
     }
     int64_t n = A.nr;
+    if (n >= (1LL << 31)) { set_error("spgemm: %lld rows exceed int32 row lists", (long long)n); return SPHC_ELIMIT; }
     DBuf<int64_t> ub, cnt;
-    DBuf<int32_t> big;
-    DBuf<int> bign, fail;
+    DBuf<int32_t> big, rows;
+    DBuf<int> flags;                 // 0 bign, 1 fail, 2..4 bin counts, 5..7 bin offsets, 8..10 bin fill
     SPHC_TRY(ub.alloc(n + 1, s));
     SPHC_TRY(cnt.alloc(n + 1, s));
     SPHC_TRY(big.alloc(n + 1, s));
-    SPHC_TRY(bign.alloc(1, s));
-    SPHC_TRY(fail.alloc(1, s));
-    SPHC_TRY(bign.zero(s));
-    SPHC_TRY(fail.zero(s));
+    SPHC_TRY(rows.alloc(n + 1, s));
+    SPHC_TRY(flags.alloc(16, s));
+    SPHC_TRY(flags.zero(s));
+    int h[16] = {0};
     if (n > 0) {
-        SPHC_LAUNCH(k_spgemm_ub<<<grid_for(n, 256), 256, 0, s>>>(A.rp.p, A.ci.p, B.rp.p, n, ub.p));
-        SPHC_LAUNCH(k_spgemm_symbolic<<<grid_for(n, SPGEMM_WARPS), SPGEMM_WARPS * 32, 0, s>>>(
-            A.rp.p, A.ci.p, B.rp.p, B.ci.p, n, ub.p, cnt.p, big.p, bign.p));
+        SPHC_LAUNCH(k_spgemm_ub<<<grid_for(n, 256), 256, 0, s>>>(A.rp.p, A.ci.p, B.rp.p, n, ub.p, flags.p + 2));
+        SPHC_CK(cudaMemcpyAsync(h, flags.p, 16 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        SPHC_CK(cudaStreamSynchronize(s));
+        int off[NBINS] = {0, h[2], h[2] + h[3]};
+        SPHC_CK(cudaMemcpyAsync(flags.p + 5, off, NBINS * sizeof(int), cudaMemcpyHostToDevice, s));
+        SPHC_LAUNCH(k_spgemm_bin<<<grid_for(n, 256), 256, 0, s>>>(ub.p, n, flags.p + 5, flags.p + 8, rows.p));
+        launch_symbolic<128, 16>(A, B, rows.p, h[2], ub.p, cnt.p, big.p, flags.p, s);
+        launch_symbolic<512, 8>(A, B, rows.p + off[1], h[3], ub.p, cnt.p, big.p, flags.p, s);
+        launch_symbolic<1024, 8>(A, B, rows.p + off[2], h[4], ub.p, cnt.p, big.p, flags.p, s);
     }
     SPHC_CK(cudaGetLastError());
     int nbig = 0;
-    SPHC_CK(cudaMemcpyAsync(&nbig, bign.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SPHC_CK(cudaMemcpyAsync(&nbig, flags.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     SPHC_CK(cudaStreamSynchronize(s));
     size_t big_sym_sm = sizeof(int32_t) * BIG_SLOTS;
     size_t big_num_sm = (sizeof(int32_t) + sizeof(double)) * BIG_SLOTS;
     if (nbig > 0) {
         SPHC_CK(cudaFuncSetAttribute(k_spgemm_symbolic_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big_sym_sm));
         SPHC_LAUNCH(k_spgemm_symbolic_big<<<nbig < 4096 ? nbig : 4096, 512, big_sym_sm, s>>>(
-            A.rp.p, A.ci.p, B.rp.p, B.ci.p, big.p, nbig, cnt.p, fail.p));
+            A.rp.p, A.ci.p, B.rp.p, B.ci.p, big.p, nbig, cnt.p, flags.p + 1));
         int f = 0;
-        SPHC_CK(cudaMemcpyAsync(&f, fail.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+        SPHC_CK(cudaMemcpyAsync(&f, flags.p + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
         SPHC_CK(cudaStreamSynchronize(s));
         if (f) {
             set_error("spgemm: a product row has more than %d columns", BIG_FILL);
@@ -590,11 +644,12 @@ int spgemm(const DCSR& A, const DCSR& B, DCSR& C, cudaStream_t s) {
     C.nnz = nnz;
     SPHC_TRY(C.ci.alloc(nnz, s));
     SPHC_TRY(C.v.alloc(nnz, s));
-    size_t num_sm = (sizeof(int32_t) + sizeof(double)) * HASH_SLOTS * SPGEMM_WARPS;
-    SPHC_CK(cudaFuncSetAttribute(k_spgemm_numeric, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)num_sm));
-    if (n > 0)
-        SPHC_LAUNCH(k_spgemm_numeric<<<grid_for(n, SPGEMM_WARPS), SPGEMM_WARPS * 32, num_sm, s>>>(
-            A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p, B.v.p, n, C.rp.p, C.ci.p, C.v.p));
+    if (n > 0) {
+        int off[NBINS] = {0, h[2], h[2] + h[3]};
+        launch_numeric<128, 16>(A, B, C, rows.p, h[2], ub.p, s);
+        launch_numeric<512, 4>(A, B, C, rows.p + off[1], h[3], ub.p, s);
+        launch_numeric<1024, 2>(A, B, C, rows.p + off[2], h[4], ub.p, s);
+    }
     if (nbig > 0) {
         SPHC_CK(cudaFuncSetAttribute(k_spgemm_numeric_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big_num_sm));
         SPHC_LAUNCH(k_spgemm_numeric_big<<<nbig < 4096 ? nbig : 4096, 512, big_num_sm, s>>>(

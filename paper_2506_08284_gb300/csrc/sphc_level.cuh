@@ -116,8 +116,21 @@ struct Hierarchy {
     // CG work vectors (FP64)
     DBuf<double> x, r, z, p, q, rold, scal;
     DBuf<double> cb, cx;             // coarsest right side / solution (FP64)
+    // CG as one CUDA graph: a device-side while loop (conditional node) around one iteration
+    DBuf<double> dpart;              // partial sums of the dot products
+    DBuf<int> itc;                   // [0] iterations, [1] status (0 converged, 1 breakdown, 2 cap)
+    cudaGraph_t cg_graph = nullptr;
+    cudaGraphExec_t cg_exec = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    bool capturing = false;          // section timers are off while a graph is being captured
+    long long body_launches = 0;     // kernels in one CG graph iteration (for the launch count)
     double setup_ms = 0.0, solve_ms = 0.0;
     Profiler prof;
+    ~Hierarchy() {
+        if (cg_exec) cudaGraphExecDestroy(cg_exec);
+        if (cg_graph) cudaGraphDestroy(cg_graph);
+        if (cap_stream) cudaStreamDestroy(cap_stream);
+    }
     int last_iters = 0;
     double last_relres = 0.0;
 };

@@ -35,7 +35,7 @@ class sphc_opts(ctypes.Structure):
     _fields_ = [("max_levels", ctypes.c_int32), ("emin_iters", ctypes.c_int32), ("max_coarse", ctypes.c_int64),
                 ("emin_omega", ctypes.c_double), ("seed", ctypes.c_uint64), ("power_iters", ctypes.c_int32),
                 ("vcycle_fp32", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("flexible", ctypes.c_int32),
-                ("profile", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("profile", ctypes.c_int32), ("cg_graph", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class sphc_level_info(ctypes.Structure):
