@@ -31,7 +31,7 @@ __global__ void k_jp_round(const int64_t* rp, const int32_t* ci, const int32_t* 
         int32_t w = ci[k];
         if (w == v || col[w] >= 0) continue;
         if (prio_greater(splitmix64(seed, (uint64_t)w), w, hv, v)) {
-            next[atomicAdd(nnext, 1)] = v;
+            next[warp_reserve(nnext)] = v;
             return;
         }
     }
@@ -119,11 +119,10 @@ __global__ void k_mis2_select(const int64_t* rp, const int32_t* ci, int64_t n, u
     state[v] = 3;
 }
 
-__global__ void k_mis2_mark(const int64_t* rp, const int32_t* ci, int64_t n, int8_t* state, int* left) {
+__global__ void k_mis2_mark(const int64_t* rp, const int32_t* ci, int64_t n, int8_t* state) {
     int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= n) return;
     int8_t sv = state[v];
-    if (sv == 0) { atomicAdd(left, 1); }
     if (sv != 3) return;
     for (int64_t k = rp[v]; k < rp[v + 1]; ++k) {
         int32_t w = ci[k];
@@ -136,9 +135,12 @@ __global__ void k_mis2_mark(const int64_t* rp, const int32_t* ci, int64_t n, int
 }
 __global__ void k_mis2_commit(int8_t* state, int64_t n, int* left) {
     int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= n) return;
-    if (state[v] == 3) state[v] = 1;
-    else if (state[v] == 0) atomicAdd(left, 1);
+    bool undecided = false;
+    if (v < n) {
+        if (state[v] == 3) state[v] = 1;
+        else undecided = state[v] == 0;
+    }
+    warp_count(left, undecided);
 }
 __global__ void k_root_flags(const int8_t* state, int64_t n, int64_t* flag) {
     int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -160,10 +162,11 @@ __global__ void k_agg_phase2(const int64_t* rp, const int32_t* ci, int64_t n, co
 __global__ void k_agg_phase3(const int64_t* rp, const int32_t* ci, int64_t n, const int32_t* cur, int32_t* nxt,
                              int* left, int* changed) {
     int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool open = v < n && cur[v] < 0;
+    warp_count(left, open);
     if (v >= n) return;
     int32_t a = cur[v];
     if (a >= 0) { nxt[v] = a; return; }
-    atomicAdd(left, 1);
     int32_t best = -1, bestc = 0;
     for (int64_t k = rp[v]; k < rp[v + 1]; ++k) {
         int32_t w = ci[k];
@@ -185,7 +188,7 @@ __global__ void k_agg_phase3(const int64_t* rp, const int32_t* ci, int64_t n, co
         if (c > bestc || (c == bestc && g < best)) { best = g; bestc = c; }
     }
     nxt[v] = best;
-    if (best >= 0) atomicAdd(changed, 1);
+    if (best >= 0) atomicAdd(changed, 1);   // rare: only nodes left after the root neighbourhoods
 }
 
 int aggregate(const DCSR& G, uint64_t seed, DBuf<int32_t>& agg, int64_t* nagg, cudaStream_t s) {
@@ -200,7 +203,7 @@ int aggregate(const DCSR& G, uint64_t seed, DBuf<int32_t>& agg, int64_t* nagg, c
     int h[2];
     for (int round = 0; round < 100000; ++round) {
         SPHC_LAUNCH(k_mis2_select<<<grid_for(n, 256), 256, 0, s>>>(G.rp.p, G.ci.p, n, seed, state.p));
-        SPHC_LAUNCH(k_mis2_mark<<<grid_for(n, 256), 256, 0, s>>>(G.rp.p, G.ci.p, n, state.p, flags.p));
+        SPHC_LAUNCH(k_mis2_mark<<<grid_for(n, 256), 256, 0, s>>>(G.rp.p, G.ci.p, n, state.p));
         SPHC_CK(cudaMemsetAsync(flags.p, 0, sizeof(int), s));
         SPHC_LAUNCH(k_mis2_commit<<<grid_for(n, 256), 256, 0, s>>>(state.p, n, flags.p));
         SPHC_CK(cudaMemcpyAsync(h, flags.p, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -467,8 +470,6 @@ __global__ void k_pattern(const int64_t* trp, const int32_t* tci, int64_t ne, co
     if (mode == 0) {
         if (lane == 0) {
             cnt[i] = np;
-            atomicMax(&stats[3], np);
-            atomicMax(&stats[4], m);
             // connectivity of the local graph
             if (m > 1) {
                 int par[MAX_T];
@@ -676,7 +677,6 @@ k_p0(int64_t ne, const int64_t* trp, const int32_t* tci, const double* tv, const
     if (i >= ne) return;
     int m, np;
     int k = local_setup(S, i, trp, tci, tv, nrp, nci, hrp, hci, hv, &m, &np);
-    if (lane == 0 && hist) atomicAdd(&hist[(np < 32 ? np : 32) * 33 + (m < 32 ? m : 32)], 1ULL);
     if (np == 0) return;
     if (k < 0) { if (lane == 0) atomicAdd(fail, 1); return; }
     if (lane < k) S.rhs[lane] = S.r[lane];
@@ -734,6 +734,20 @@ k_emin(int64_t ne, const int64_t* arp, const int32_t* aci, const double* av, con
         double dp = wt[q] - gz(S, t, k, S.z);
         Pout[n0 + t] = P[n0 + t] - omega * dp;
     }
+}
+
+// histogram of the local sub-problem sizes (|N_i|, |T_i|), clipped at 32: block-local counts
+__global__ void k_ls_hist(const int64_t* nrp, const int64_t* trp, int64_t ne, unsigned long long* hist) {
+    __shared__ unsigned int h[33 * 33];
+    for (int q = threadIdx.x; q < 33 * 33; q += blockDim.x) h[q] = 0;
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ne; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t np = nrp[i + 1] - nrp[i], m = trp[i + 1] - trp[i];
+        atomicAdd(&h[(np < 32 ? np : 32) * 33 + (m < 32 ? m : 32)], 1u);
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < 33 * 33; q += blockDim.x)
+        if (h[q]) atomicAdd(&hist[q], (unsigned long long)h[q]);
 }
 
 // ------------------------------------------------------------------ dense coarsest factor
@@ -891,14 +905,14 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
                   "on the GPU)", lev, hs[2]);
         return SPHC_EINFEASIBLE;
     }
-    L.max_np = hs[3];
-    L.max_m = hs[4];
+    SPHC_TRY(max_row_length(L.T.rp.p, ne, s, &L.max_m));
     int64_t nnzN = 0;
     SPHC_TRY(L.P0.alloc(ne, L.DH.nr, 0, s));
     SPHC_TRY(exclusive_scan_i64(ncnt.p, L.P0.rp.p, ne, s, &nnzN));
     L.P0.nnz = nnzN;
     SPHC_TRY(L.P0.ci.alloc(nnzN, s));
     SPHC_TRY(L.P0.v.alloc(nnzN, s));
+    SPHC_TRY(max_row_length(L.P0.rp.p, ne, s, &L.max_np));
     if (ne > 0)
         SPHC_LAUNCH(k_pattern<<<grid_for(ne, PAT_WARPS), PAT_WARPS * 32, 0, s>>>(L.T.rp.p, L.T.ci.p, ne, DHt.rp.p, DHt.ci.p,
                                                                     L.DH.rp.p, L.DH.ci.p, 1, nullptr, L.P0.rp.p,
@@ -908,6 +922,7 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
     // initial guess and energy minimisation
     SPHC_TRY(L.hist.alloc(33 * 33, s));
     SPHC_TRY(L.hist.zero(s));
+    if (ne > 0) SPHC_LAUNCH(k_ls_hist<<<1024, 256, 0, s>>>(L.P0.rp.p, L.T.rp.p, ne, L.hist.p));
     SPHC_TRY(st.zero(s));
     size_t sm = sizeof(LocalSys) * LOC_WARPS;
     SPHC_CK(cudaFuncSetAttribute(k_p0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));

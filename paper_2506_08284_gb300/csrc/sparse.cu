@@ -320,22 +320,143 @@ __device__ inline uint32_t hslot(int32_t key, int mask) {
     return ((uint32_t)key * 2654435761u) & (uint32_t)mask;
 }
 
+// bins: 0 at most 64 products and 64 A entries (register sort), 1 at most 256 products
+// (512-slot tables), 2 the rest (1024-slot tables / big path)
+__device__ inline int spgemm_bin_of(int64_t ub, int64_t alen) {
+    return (ub <= 64 && alen <= 64) ? 0 : (ub <= 256 ? 1 : 2);
+}
 __global__ void k_spgemm_ub(const int64_t* arp, const int32_t* aci, const int64_t* brp, int64_t n,
                             int64_t* ub, int* bin_cnt) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int64_t s = 0;
-    for (int64_t k = arp[i]; k < arp[i + 1]; ++k) s += brp[aci[k] + 1] - brp[aci[k]];
-    ub[i] = s;
-    int bin = s <= 64 ? 0 : (s <= 256 ? 1 : 2);
-    atomicAdd(&bin_cnt[bin], 1);
+    int bin = -1;
+    if (i < n) {
+        int64_t s = 0;
+        for (int64_t k = arp[i]; k < arp[i + 1]; ++k) s += brp[aci[k] + 1] - brp[aci[k]];
+        ub[i] = s;
+        bin = spgemm_bin_of(s, arp[i + 1] - arp[i]);
+    }
+    for (int b = 0; b < 3; ++b) warp_count(&bin_cnt[b], bin == b);
 }
-__global__ void k_spgemm_bin(const int64_t* ub, int64_t n, const int* bin_off, int* bin_fill, int32_t* rows) {
+__global__ void k_spgemm_bin(const int64_t* arp, const int64_t* ub, int64_t n, const int* bin_off, int* bin_fill,
+                             int32_t* rows) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    int64_t s = ub[i];
-    int bin = s <= 64 ? 0 : (s <= 256 ? 1 : 2);
-    rows[bin_off[bin] + atomicAdd(&bin_fill[bin], 1)] = (int32_t)i;
+    int bin = spgemm_bin_of(ub[i], arp[i + 1] - arp[i]);
+    unsigned m = __match_any_sync(__activemask(), bin);
+    int lane = threadIdx.x & 31;
+    int leader = __ffs(m) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(&bin_fill[bin], __popc(m));
+    base = __shfl_sync(m, base, leader);
+    rows[bin_off[bin] + base + __popc(m & ((1u << lane) - 1u))] = (int32_t)i;
+}
+
+// Rows with at most 64 products (and 64 A entries): one warp per row, the products held two per
+// lane and sorted by column with a bitonic network over the warp; equal columns are then
+// adjacent.  mode 0 counts distinct columns, mode 1 sums each run and writes the sorted row.
+static constexpr int SMALL_WARPS = 8;
+__global__ void __launch_bounds__(SMALL_WARPS * 32)
+k_spgemm_small(const int64_t* arp, const int32_t* aci, const double* av, const int64_t* brp, const int32_t* bci,
+               const double* bv, const int32_t* rows, int nrows, int mode, int64_t* cnt, const int64_t* crp,
+               int32_t* cci, double* cv) {
+    __shared__ int64_t s_off[SMALL_WARPS][64];
+    __shared__ int32_t s_key[SMALL_WARPS][64];
+    __shared__ double s_val[SMALL_WARPS][64];
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int64_t li = (int64_t)blockIdx.x * SMALL_WARPS + w;
+    if (li >= nrows) return;
+    int64_t i = rows[li];
+    int64_t a0 = arp[i];
+    int alen = (int)(arp[i + 1] - a0);
+    // product offsets of the (at most 64) A entries
+    int64_t len[2] = {0, 0};
+    for (int q = 0; q < 2; ++q) {
+        int e = lane + 32 * q;
+        if (e < alen) {
+            int32_t k = aci[a0 + e];
+            len[q] = brp[k + 1] - brp[k];
+        }
+    }
+    int64_t inc0 = warp_incl_scan(len[0]);
+    int64_t tot0 = __shfl_sync(0xffffffffu, inc0, 31);
+    int64_t inc1 = warp_incl_scan(len[1]) + tot0;
+    s_off[w][lane] = inc0 - len[0];
+    s_off[w][lane + 32] = inc1 - len[1];
+    int64_t total = __shfl_sync(0xffffffffu, inc1, 31);
+    __syncwarp();
+    // element e = 2 * lane + q holds product e (column key, value); padding keys are INT_MAX
+    int32_t key[2];
+    double val[2];
+    for (int q = 0; q < 2; ++q) {
+        int e = 2 * lane + q;
+        key[q] = 0x7fffffff;
+        val[q] = 0.0;
+        if (e < total) {
+            int lo = 0, hi = (alen < 64 ? alen : 64) - 1;
+            while (lo < hi) {
+                int mid = (lo + hi + 1) >> 1;
+                if (s_off[w][mid] <= e) lo = mid; else hi = mid - 1;
+            }
+            int32_t k = aci[a0 + lo];
+            int64_t kb = brp[k] + (e - s_off[w][lo]);
+            key[q] = bci[kb];
+            if (mode == 1) val[q] = av[a0 + lo] * bv[kb];
+        }
+    }
+    // bitonic sort of the 64 elements
+    for (int size = 2; size <= 64; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            if (stride == 1) {
+                bool up = (((2 * lane) & size) == 0);
+                if ((key[0] > key[1]) == up) {
+                    int32_t tk = key[0]; key[0] = key[1]; key[1] = tk;
+                    double tv = val[0]; val[0] = val[1]; val[1] = tv;
+                }
+            } else {
+                int ls = stride >> 1;
+                for (int q = 0; q < 2; ++q) {
+                    int e = 2 * lane + q;
+                    int32_t ok = __shfl_xor_sync(0xffffffffu, key[q], ls);
+                    double ov = mode == 1 ? __shfl_xor_sync(0xffffffffu, val[q], ls) : 0.0;
+                    bool up = ((e & size) == 0);
+                    bool lower = (e & stride) == 0;
+                    bool take_min = (up == lower);
+                    bool swap = take_min ? (ok < key[q]) : (ok > key[q]);
+                    if (swap) { key[q] = ok; val[q] = ov; }
+                }
+            }
+        }
+    }
+    s_key[w][2 * lane] = key[0];
+    s_key[w][2 * lane + 1] = key[1];
+    if (mode == 1) { s_val[w][2 * lane] = val[0]; s_val[w][2 * lane + 1] = val[1]; }
+    __syncwarp();
+    // run heads: first element of each distinct column
+    bool head[2];
+    for (int q = 0; q < 2; ++q) {
+        int e = 2 * lane + q;
+        head[q] = s_key[w][e] != 0x7fffffff && (e == 0 || s_key[w][e - 1] != s_key[w][e]);
+    }
+    unsigned m0 = __ballot_sync(0xffffffffu, head[0]);
+    unsigned m1 = __ballot_sync(0xffffffffu, head[1]);
+    int distinct = __popc(m0) + __popc(m1);
+    if (mode == 0) {
+        if (lane == 0) cnt[i] = distinct;
+        return;
+    }
+    int64_t c0 = crp[i];
+    unsigned lt = (1u << lane) - 1u;
+    for (int q = 0; q < 2; ++q) {
+        if (!head[q]) continue;
+        int e = 2 * lane + q;
+        // heads before e: elements 2*l + 0/1 for l < lane, plus element 2*lane if q == 1
+        int rank = __popc(m0 & lt) + __popc(m1 & lt) + (q == 1 && head[0] ? 1 : 0);
+        int32_t kk = s_key[w][e];
+        double sum = 0.0;
+        for (int f = e; f < 64 && s_key[w][f] == kk; ++f) sum += s_val[w][f];
+        cci[c0 + rank] = kk;
+        cv[c0 + rank] = sum;
+    }
 }
 
 // flattened enumeration of the products of row i, 32 A-entries at a time
@@ -615,8 +736,10 @@ int spgemm(const DCSR& A, const DCSR& B, DCSR& C, cudaStream_t s) {
         SPHC_CK(cudaStreamSynchronize(s));
         int off[NBINS] = {0, h[2], h[2] + h[3]};
         SPHC_CK(cudaMemcpyAsync(flags.p + 5, off, NBINS * sizeof(int), cudaMemcpyHostToDevice, s));
-        SPHC_LAUNCH(k_spgemm_bin<<<grid_for(n, 256), 256, 0, s>>>(ub.p, n, flags.p + 5, flags.p + 8, rows.p));
-        launch_symbolic<128, 16>(A, B, rows.p, h[2], ub.p, cnt.p, big.p, flags.p, s);
+        SPHC_LAUNCH(k_spgemm_bin<<<grid_for(n, 256), 256, 0, s>>>(A.rp.p, ub.p, n, flags.p + 5, flags.p + 8, rows.p));
+        if (h[2] > 0)
+            SPHC_LAUNCH(k_spgemm_small<<<(h[2] + SMALL_WARPS - 1) / SMALL_WARPS, SMALL_WARPS * 32, 0, s>>>(
+                A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p, B.v.p, rows.p, h[2], 0, cnt.p, nullptr, nullptr, nullptr));
         launch_symbolic<512, 8>(A, B, rows.p + off[1], h[3], ub.p, cnt.p, big.p, flags.p, s);
         launch_symbolic<1024, 8>(A, B, rows.p + off[2], h[4], ub.p, cnt.p, big.p, flags.p, s);
     }
@@ -646,7 +769,9 @@ int spgemm(const DCSR& A, const DCSR& B, DCSR& C, cudaStream_t s) {
     SPHC_TRY(C.v.alloc(nnz, s));
     if (n > 0) {
         int off[NBINS] = {0, h[2], h[2] + h[3]};
-        launch_numeric<128, 16>(A, B, C, rows.p, h[2], ub.p, s);
+        if (h[2] > 0)
+            SPHC_LAUNCH(k_spgemm_small<<<(h[2] + SMALL_WARPS - 1) / SMALL_WARPS, SMALL_WARPS * 32, 0, s>>>(
+                A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p, B.v.p, rows.p, h[2], 1, nullptr, C.rp.p, C.ci.p, C.v.p));
         launch_numeric<512, 4>(A, B, C, rows.p + off[1], h[3], ub.p, s);
         launch_numeric<1024, 2>(A, B, C, rows.p + off[2], h[4], ub.p, s);
     }

@@ -148,6 +148,24 @@ __device__ inline bool prio_greater(uint64_t ha, int64_t a, uint64_t hb, int64_t
     return ha > hb || (ha == hb && a < b);
 }
 
+// Warp-aggregated atomic increment: the lanes active at the call reserve consecutive slots with
+// one atomic per warp.  Returns this lane's slot.
+__device__ inline int warp_reserve(int* ctr) {
+    unsigned m = __activemask();
+    int lane = threadIdx.x & 31;
+    int leader = __ffs(m) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(ctr, __popc(m));
+    base = __shfl_sync(m, base, leader);
+    return base + __popc(m & ((1u << lane) - 1u));
+}
+// Add the number of lanes (of the full warp) with pred set: one atomic per warp.  Every lane of
+// the warp must call it.
+__device__ inline void warp_count(int* ctr, bool pred) {
+    unsigned m = __ballot_sync(0xffffffffu, pred);
+    if ((threadIdx.x & 31) == 0 && m) atomicAdd(ctr, __popc(m));
+}
+
 inline int grid_for(int64_t n, int block) {
     int64_t g = (n + block - 1) / block;
     if (g < 1) g = 1;
