@@ -108,9 +108,8 @@ int setup_impl(sphc_handle* h, const sphc_csr* A_e, const sphc_csr* D_h, cudaStr
     SPHC_TRY(transpose(L0.D, L0.Dt, s));
     {
         Section sec(prof, "setup_nodal_op", s);
-        DCSR AD;
-        SPHC_TRY(spgemm(L0.A, L0.D, AD, s));
-        SPHC_TRY(spgemm(L0.Dt, AD, L0.An, s));
+        SPHC_TRY(spgemm(L0.A, L0.D, L0.AD, s));
+        SPHC_TRY(spgemm(L0.Dt, L0.AD, L0.An, s));
     }
     int lev = 0;
     for (;;) {

@@ -509,8 +509,10 @@ __global__ void k_pattern(const int64_t* trp, const int32_t* tci, int64_t ne, co
 //
 // The normal matrix G~^T G~ of a row is a small integer matrix (a grounded graph Laplacian).
 // FP64 throughput is scarce on this GPU, so it is factored in FP32 (LDL^T) and every solve is
-// refined three times against FP64 residuals evaluated exactly through the +-1 entries of G~;
-// each step gains about eps32 * cond, which brings the solution to FP64 accuracy.
+// refined twice against FP64 residuals evaluated exactly through the +-1 entries of G~; each
+// step multiplies the error by about eps32 * cond (cond is at most a few hundred for these
+// graphs), which brings the solution to FP64 accuracy.
+constexpr int REFINE_STEPS = 2;
 struct LocalSys {
     int32_t T[MAX_T];
     double r[MAX_T];
@@ -643,7 +645,7 @@ __device__ inline double gtv(const LocalSys& S, int a, const double* v) {
     return s;
 }
 
-// S.z = (G~^T G~)^-1 S.rhs: FP32 solve, then three FP64-residual refinement steps.  An FP64
+// S.z = (G~^T G~)^-1 S.rhs: FP32 solve, then two FP64-residual refinement steps.  An FP64
 // instruction costs the whole warp's issue slot however many lanes are active, so every FP64
 // step is spread over the lanes; only the FP32 triangular solves run on one lane.
 __device__ void refine_solve(LocalSys& S, int k, int np) {
@@ -654,7 +656,7 @@ __device__ void refine_solve(LocalSys& S, int k, int np) {
     __syncwarp();
     if (lane < k) S.z[lane] = (double)S.xs[lane];
     __syncwarp();
-    for (int step = 0; step < 3; ++step) {
+    for (int step = 0; step < REFINE_STEPS; ++step) {
         for (int t = lane; t < np; t += 32) S.w[t] = gz(S, t, k, S.z);
         __syncwarp();
         if (lane < k) S.xs[lane] = (float)(S.rhs[lane] - gtv(S, lane, S.w));

@@ -152,6 +152,9 @@ static int build_smooth_op(const DCSR& A, const int32_t* color, int ncolor, Smoo
     op.ncolor = ncolor;
     if (A.nnz >= (1LL << 31)) { set_error("operator with %lld nonzeros exceeds int32 row pointers", (long long)A.nnz); return SPHC_ELIMIT; }
     SPHC_TRY(colour_partition(color, A.nr, ncolor, op.perm, op.cstart, s));
+    SPHC_TRY(op.cstart_dev.alloc(ncolor + 1, s));
+    SPHC_CK(cudaMemcpyAsync(op.cstart_dev.p, op.cstart.data(), sizeof(int64_t) * (ncolor + 1), cudaMemcpyHostToDevice, s));
+    SPHC_CK(cudaStreamSynchronize(s));
     DBuf<int64_t> len, rp64;
     SPHC_TRY(len.alloc(A.nr + 1, s));
     SPHC_TRY(rp64.alloc(A.nr + 1, s));
@@ -225,10 +228,10 @@ static int build_vlevel(Hierarchy& H, int l, VLevel<T>& V, bool split, cudaStrea
     }
     if (l == H.nlev - 1) return SPHC_OK;
     if (split) {
-        DCSR AD;
-        SPHC_TRY(spgemm(L.A, L.D, AD, s));        // FP64: the curl-curl part of A D cancels here
-        SPHC_TRY(build_vcsr<T>(AD, V.AD, s));
+        if (L.AD.nr != L.A.nr) SPHC_TRY(spgemm(L.A, L.D, L.AD, s));   // FP64: the curl-curl part cancels here
+        SPHC_TRY(build_vcsr<T>(L.AD, V.AD, s));
         SPHC_TRY(build_vcsr<T>(L.Pn, V.Pn, s));
+        L.AD = DCSR();
     }
     SPHC_TRY(build_smooth_op<T>(L.A, L.col_e.p, L.ncol_e, V.A, s));
     SPHC_TRY(build_smooth_op<T>(L.An, L.col_n.p, L.ncol_n, V.An, s));
@@ -425,8 +428,48 @@ static void launch_rows_sgs(const SmoothOp<T>& op, int64_t k0, int64_t k1, const
         default: SPHC_LAUNCH(k_sgs_color<T, 32><<<grid_for(th, 256), 256, 0, s>>>(op.rp.p, op.ci.p, op.v.p, op.perm.p, op.dinv.p, k0, k1, b, x)); break;
     }
 }
+// A whole forward + backward sweep of a small operator in one block: colours are separated by
+// block barriers instead of kernel boundaries (the coarse levels are launch-bound otherwise).
+static constexpr int SGS_BLOCK_MAX_ROWS = 2048;
+template <typename T, int SUB>
+__global__ void __launch_bounds__(1024)
+k_sgs_block(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const T* __restrict__ v,
+            const int32_t* __restrict__ perm, const T* __restrict__ dinv, const int64_t* __restrict__ cstart,
+            int ncolor, const T* __restrict__ b, T* x) {
+    int q = threadIdx.x & (SUB - 1);
+    int slot = threadIdx.x / SUB, nslot = blockDim.x / SUB;
+    for (int step = 0; step < 2 * ncolor; ++step) {
+        int c = step < ncolor ? step : 2 * ncolor - 1 - step;
+        int64_t k0 = cstart[c], k1 = cstart[c + 1];
+        for (int64_t base = k0; base < k1; base += nslot) {
+            int64_t k = base + slot;
+            bool valid = k < k1;
+            T sum = 0;
+            if (valid)
+                for (int32_t e = rp[k] + q; e < rp[k + 1]; e += SUB) sum += v[e] * x[ci[e]];
+#pragma unroll
+            for (int o = SUB / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o, SUB);
+            if (valid && q == 0) {
+                int32_t i = perm[k];
+                x[i] += (b[i] - sum) * dinv[k];
+            }
+        }
+        __syncthreads();
+    }
+}
+
 template <typename T>
 static void sgs(const SmoothOp<T>& op, const T* b, T* x, cudaStream_t s) {
+    if (op.n <= SGS_BLOCK_MAX_ROWS && op.cstart_dev.p) {
+        int sub = sub_for(op.nnz, op.n);
+        switch (sub) {
+            case 4: SPHC_LAUNCH(k_sgs_block<T, 4><<<1, 1024, 0, s>>>(op.rp.p, op.ci.p, op.v.p, op.perm.p, op.dinv.p, op.cstart_dev.p, op.ncolor, b, x)); break;
+            case 8: SPHC_LAUNCH(k_sgs_block<T, 8><<<1, 1024, 0, s>>>(op.rp.p, op.ci.p, op.v.p, op.perm.p, op.dinv.p, op.cstart_dev.p, op.ncolor, b, x)); break;
+            case 16: SPHC_LAUNCH(k_sgs_block<T, 16><<<1, 1024, 0, s>>>(op.rp.p, op.ci.p, op.v.p, op.perm.p, op.dinv.p, op.cstart_dev.p, op.ncolor, b, x)); break;
+            default: SPHC_LAUNCH(k_sgs_block<T, 32><<<1, 1024, 0, s>>>(op.rp.p, op.ci.p, op.v.p, op.perm.p, op.dinv.p, op.cstart_dev.p, op.ncolor, b, x)); break;
+        }
+        return;
+    }
     for (int c = 0; c < op.ncolor; ++c) launch_rows_sgs(op, op.cstart[c], op.cstart[c + 1], b, x, s);
     for (int c = op.ncolor - 1; c >= 0; --c) launch_rows_sgs(op, op.cstart[c], op.cstart[c + 1], b, x, s);
 }

@@ -19,6 +19,7 @@ struct SmoothOp {
     int64_t n = 0, nnz = 0;
     int ncolor = 0;
     std::vector<int64_t> cstart;     // colour c owns copy rows [cstart[c], cstart[c+1])
+    DBuf<int64_t> cstart_dev;
     DBuf<int32_t> rp, ci, perm;
     DBuf<T> v, dinv;
 };
@@ -44,6 +45,7 @@ struct VLevel {
 
 struct Level {
     DCSR A, D, An, Dt;
+    DCSR AD;                         // A D (FP64), kept from the nodal operator of level 0
     DBuf<int32_t> col_e, col_n;
     int ncol_e = 0, ncol_n = 0;
     // transfer data (absent on the coarsest level)
