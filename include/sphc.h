@@ -69,8 +69,32 @@ typedef struct {
     int32_t profile;         /* 1: record CUDA-event section timers (sphc_get_profile); with cg_graph the
                                 timers cover the first CG iteration, which runs outside the graph (default 0) */
     int32_t cg_graph;        /* 1: run the CG iterations as one CUDA graph with a device-side loop (default 1) */
-    int32_t reserved[5];
+    int32_t learned;         /* 1: learned warm start of P_e (needs mlp_params and coords) (default 0) */
+    int32_t learned_emin_iters; /* energy-minimisation steps after the learned warm start (default 0) */
+    const float* mlp_params; /* SPHC_MLP_NPARAM floats (host or device), see sphc_mlp_train */
+    int32_t reserved[4];
 } sphc_opts;
+
+/* Learned warm start (not part of the paper).  For every pattern entry (i, j) of P_e a
+ * multilayer perceptron maps SPHC_MLP_NFEAT local features (fine- and coarse-edge geometry
+ * relative to the fine edge length, the constraint values r_i, the P_n entries of the fine
+ * edge's ends, the least-norm initial value, row sizes, A_e row scaling, log10 sigma, level) to
+ * a correction of the least-norm initial guess.  The correction is projected onto the null
+ * space of the row's commuting constraints, so P_e D_H = D_h P_n holds exactly as without it.
+ * Parameters (floats, in this order): feature means [32], feature scales [32],
+ * W1 [32 x 128] (row = input), b1 [128], W2 [128 x 128], b2 [128], w3 [128], b3. */
+#define SPHC_MLP_NFEAT 32
+#define SPHC_MLP_HIDDEN 128
+#define SPHC_MLP_NPARAM 20929
+
+typedef struct {
+    int32_t steps;           /* Adam steps (default 3000) */
+    int32_t batch;           /* minibatch rows (default 4096) */
+    float lr, beta1, beta2, eps, weight_decay;   /* Adam (1e-3, 0.9, 0.999, 1e-8, 0) */
+    int32_t pad;
+    uint64_t seed;           /* minibatch sampling seed (default 1) */
+    int32_t reserved[4];
+} sphc_train_opts;
 
 typedef struct sphc_handle sphc_handle;
 
@@ -175,6 +199,29 @@ SPHC_API int sphc_get_profile(sphc_handle* h, sphc_timer* out, int max, int* n);
 
 /* Number of kernels the library has launched in this process so far. */
 SPHC_API int64_t sphc_launch_count(void);
+
+/* Fill *opts with the training defaults. */
+SPHC_API int sphc_default_train_opts(sphc_train_opts* opts);
+
+/* Train the MLP on m samples: X [m x SPHC_MLP_NFEAT] (row-major FP32) and targets y [m] (host
+ * or device).  params [SPHC_MLP_NPARAM] holds the initial parameters (including the feature
+ * means and scales, which are not trained) and receives the trained ones.  loss_history
+ * [steps] (may be NULL) receives the minibatch mean squared errors.  Synchronises the stream. */
+SPHC_API int sphc_mlp_train(const float* X, const float* y, int64_t m, const sphc_train_opts* opts, float* params,
+                            float* loss_history, void* stream);
+
+/* Apply the MLP (BF16 tensor-core inference, FP32 accumulate) to m feature rows. */
+SPHC_API int sphc_mlp_predict(const float* params, const float* X, int64_t m, float* out, void* stream);
+
+/* Gradient of the mean squared error over the B rows (X, y) with respect to params (the
+ * normalisation entries of grad are left 0), and the loss; the training kernels' backward pass. */
+SPHC_API int sphc_mlp_gradient(const float* params, const float* X, const float* y, int B, float* grad, float* loss,
+                               void* stream);
+
+/* Features [nnz(P_e) x SPHC_MLP_NFEAT] of level `level`'s pattern entries and the training
+ * target P_e - P0 [nnz(P_e)] (either pointer may be NULL; host or device).  Needs coords at
+ * setup.  Synchronises the stream. */
+SPHC_API int sphc_export_features(const sphc_handle* h, int level, float* X, float* y, void* stream);
 
 /* Largest nrhs that sphc_relres_noalloc accepts (its fixed scratch holds this many). */
 #define SPHC_NOALLOC_MAX_RHS 64

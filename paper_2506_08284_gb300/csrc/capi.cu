@@ -87,7 +87,8 @@ int validate(const DCSR& M, int gradient, const char* name, cudaStream_t s) {
     return SPHC_OK;
 }
 
-int setup_impl(sphc_handle* h, const sphc_csr* A_e, const sphc_csr* D_h, cudaStream_t s) {
+int setup_impl(sphc_handle* h, const sphc_csr* A_e, const sphc_csr* D_h, const double* coords,
+               const double* sigma_edge, cudaStream_t s) {
     Hierarchy& H = h->H;
     const sphc_opts& o = H.opts;
     H.L.clear();
@@ -103,6 +104,22 @@ int setup_impl(sphc_handle* h, const sphc_csr* A_e, const sphc_csr* D_h, cudaStr
     }
     SPHC_TRY(validate(L0.A, 0, "A_e", s));
     SPHC_TRY(validate(L0.D, 1, "D_h", s));
+    if (coords) {
+        SPHC_TRY(L0.X.alloc(L0.D.nc * 3, s));
+        SPHC_CK(cudaMemcpyAsync(L0.X.p, coords, sizeof(double) * L0.D.nc * 3, cudaMemcpyDefault, s));
+    }
+    if (sigma_edge) {
+        SPHC_TRY(L0.sig.alloc(L0.D.nr, s));
+        SPHC_CK(cudaMemcpyAsync(L0.sig.p, sigma_edge, sizeof(double) * L0.D.nr, cudaMemcpyDefault, s));
+    }
+    if (o.learned) {
+        if (!o.mlp_params || !coords) {
+            set_error("learned warm start needs opts.mlp_params and coords");
+            return SPHC_EINVAL;
+        }
+        SPHC_TRY(H.mlp.alloc(SPHC_MLP_NPARAM, s));
+        SPHC_CK(cudaMemcpyAsync(H.mlp.p, o.mlp_params, sizeof(float) * SPHC_MLP_NPARAM, cudaMemcpyDefault, s));
+    }
     Profiler* prof = H.prof.on ? &H.prof : nullptr;
     // nodal operator D_h^T A_e D_h
     SPHC_TRY(transpose(L0.D, L0.Dt, s));
@@ -123,8 +140,9 @@ int setup_impl(sphc_handle* h, const sphc_csr* A_e, const sphc_csr* D_h, cudaStr
         bool coarsest = L.A.nr <= o.max_coarse || lev + 1 >= o.max_levels || L.An.nr <= 1;
         if (coarsest) break;
         DCSR A1, D1, An1;
+        DBuf<double> X1;
         Section sec(lev >= 1 ? prof : nullptr, "setup_levels_ge1", s);
-        SPHC_TRY(build_level(L, lev, o, A1, D1, An1, lev == 0 ? prof : nullptr, s));
+        SPHC_TRY(build_level(L, lev, o, A1, D1, An1, X1, H.mlp.p, lev == 0 ? prof : nullptr, s));
         if (L.nagg >= L.An.nr) break;      // no coarsening: this level is solved directly
         L.has_transfer = true;
         H.L.emplace_back();
@@ -132,6 +150,7 @@ int setup_impl(sphc_handle* h, const sphc_csr* A_e, const sphc_csr* D_h, cudaStr
         N.A = std::move(A1);
         N.D = std::move(D1);
         N.An = std::move(An1);
+        N.X = std::move(X1);
         SPHC_TRY(transpose(N.D, N.Dt, s));
         ++lev;
     }
@@ -171,13 +190,14 @@ int sphc_default_opts(sphc_opts* o) {
     o->flexible = -1;
     o->profile = 0;
     o->cg_graph = 1;
+    o->learned = 0;
+    o->learned_emin_iters = 0;
+    o->mlp_params = nullptr;
     return SPHC_OK;
 }
 
 int sphc_setup(const sphc_csr* A_e, const sphc_csr* D_h, const double* coords, const double* sigma_edge,
                const sphc_opts* opts, void* stream, sphc_handle** out) {
-    (void)coords;
-    (void)sigma_edge;
     if (!out || !A_e || !D_h) {
         set_error("sphc_setup: NULL argument");
         return SPHC_EINVAL;
@@ -202,7 +222,7 @@ int sphc_setup(const sphc_csr* A_e, const sphc_csr* D_h, const double* coords, c
     h->H.prof.on = o.profile != 0;
     cudaStream_t s = (cudaStream_t)stream;
     auto t0 = std::chrono::steady_clock::now();
-    int rc = setup_impl(h, A_e, D_h, s);
+    int rc = setup_impl(h, A_e, D_h, coords, sigma_edge, s);
     if (rc != SPHC_OK) {
         cudaStreamSynchronize(s);
         sphc_destroy(h);
@@ -418,6 +438,34 @@ int sphc_get_profile(sphc_handle* h, sphc_timer* out, int max, int* n) {
 }
 
 int64_t sphc_launch_count(void) { return (int64_t)g_launches.load(); }
+
+__global__ void k_target(const double* pe, const double* p0, int64_t n, float* y) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < n) y[q] = (float)(pe[q] - p0[q]);
+}
+
+int sphc_export_features(const sphc_handle* h, int level, float* X, float* y, void* stream) {
+    if (!h || level < 0 || level + 1 >= h->H.nlev || !h->H.L[level].has_transfer) {
+        set_error("sphc_export_features: level %d has no prolongator", level);
+        return SPHC_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const Level& L = h->H.L[level];
+    int64_t nnz = L.P0.nnz;
+    DBuf<float> F, Y;
+    if (X) {
+        SPHC_TRY(F.alloc(nnz * SPHC_MLP_NFEAT, s));
+        SPHC_TRY(level_features(L, h->H.L[level + 1].X, level, F.p, s));
+        SPHC_CK(cudaMemcpyAsync(X, F.p, sizeof(float) * nnz * SPHC_MLP_NFEAT, cudaMemcpyDefault, s));
+    }
+    if (y) {
+        SPHC_TRY(Y.alloc(nnz, s));
+        if (nnz > 0) SPHC_LAUNCH(k_target<<<grid_for(nnz, 256), 256, 0, s>>>(L.Pe.v.p, L.P0.v.p, nnz, Y.p));
+        SPHC_CK(cudaMemcpyAsync(y, Y.p, sizeof(float) * nnz, cudaMemcpyDefault, s));
+    }
+    SPHC_CK(cudaStreamSynchronize(s));
+    return SPHC_OK;
+}
 
 const char* sphc_last_error(void) { return sphc::last_error(); }
 

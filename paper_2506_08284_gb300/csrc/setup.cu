@@ -738,6 +738,154 @@ k_emin(int64_t ne, const int64_t* arp, const int32_t* aci, const double* av, con
     }
 }
 
+// ------------------------------------------------------------------ learned warm start
+// P0' = P0 + (I - G~ (G~^T G~)^-1 G~^T) d, d the MLP correction of the row: P0' satisfies the same
+// constraints as P0 (exactly, up to the refinement's rounding).
+__global__ void __launch_bounds__(LOC_WARPS * 32)
+k_learned_p0(int64_t ne, const int64_t* trp, const int32_t* tci, const double* tv, const int64_t* nrp,
+             const int32_t* nci, const int64_t* hrp, const int32_t* hci, const double* hv, const float* corr,
+             double* p0, int* fail) {
+    extern __shared__ unsigned char smem_raw[];
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    LocalSys& S = ((LocalSys*)smem_raw)[w];
+    int64_t i = (int64_t)blockIdx.x * LOC_WARPS + w;
+    if (i >= ne) return;
+    int m, np;
+    int k = local_setup(S, i, trp, tci, tv, nrp, nci, hrp, hci, hv, &m, &np);
+    if (np == 0) return;
+    if (k < 0) { if (lane == 0) atomicAdd(fail, 1); return; }
+    int64_t n0 = nrp[i];
+    double dt[MAX_NP / 32];
+    for (int t = lane, q = 0; t < np; t += 32, ++q) {
+        dt[q] = (double)corr[n0 + t];
+        S.w[t] = dt[q];
+    }
+    __syncwarp();
+    if (lane < k) S.rhs[lane] = gtv(S, lane, S.w);
+    __syncwarp();
+    refine_solve(S, k, np);
+    for (int t = lane, q = 0; t < np; t += 32, ++q) p0[n0 + t] += dt[q] - gz(S, t, k, S.z);
+}
+
+// centroid of each aggregate (coordinates of the coarse nodes); members sorted, so the sums are
+// taken in a fixed order
+__global__ void k_centroids(const int64_t* mptr, const int32_t* members, int64_t nagg, const double* X, double* Xc) {
+    int64_t U = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (U >= nagg) return;
+    double c[3] = {0.0, 0.0, 0.0};
+    int64_t b = mptr[U], e = mptr[U + 1];
+    for (int64_t q = b; q < e; ++q)
+        for (int a = 0; a < 3; ++a) c[a] += X[3 * (int64_t)members[q] + a];
+    double inv = e > b ? 1.0 / (double)(e - b) : 0.0;
+    for (int a = 0; a < 3; ++a) Xc[3 * U + a] = c[a] * inv;
+}
+
+__device__ inline double row_lookup(const int64_t* rp, const int32_t* ci, const double* v, int64_t r, int32_t col) {
+    if (r < 0) return 0.0;
+    int64_t lo = rp[r], hi = rp[r + 1] - 1;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (ci[mid] < col) lo = mid + 1; else hi = mid;
+    }
+    return (lo <= hi && ci[lo] == col) ? v[lo] : 0.0;
+}
+
+// Features of every pattern entry (i, j) of a level (SPHC_MLP_NFEAT floats each, see sphc.h).
+// One thread per pattern entry; the row of an entry is found by binary search in nrp.
+__global__ void k_features(int64_t ne, int64_t nnzN, int lev, const int64_t* drp, const int32_t* dci, const double* dv,
+                           const int64_t* trp, const int32_t* tci, const double* tv, const int64_t* nrp,
+                           const int32_t* nci, const double* p0, const int64_t* hrp, const int32_t* hci,
+                           const double* hv, const int64_t* prp, const int32_t* pci, const double* pv,
+                           const int64_t* arp, const int32_t* aci, const double* av, const double* X,
+                           const double* Xc, const double* sig, float* F) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nnzN) return;
+    int64_t lo = 0, hi = ne - 1;                 // row i: nrp[i] <= q < nrp[i+1]
+    while (lo < hi) {
+        int64_t mid = (lo + hi + 1) >> 1;
+        if (nrp[mid] <= q) lo = mid; else hi = mid - 1;
+    }
+    int64_t i = lo;
+    float f[SPHC_MLP_NFEAT];
+    for (int a = 0; a < SPHC_MLP_NFEAT; ++a) f[a] = 0.f;
+    // fine edge ends (-1 tail u, +1 head v)
+    int64_t u = -1, v = -1;
+    for (int64_t k = drp[i]; k < drp[i + 1]; ++k) { if (dv[k] < 0) u = dci[k]; else v = dci[k]; }
+    float xu[3] = {0, 0, 0}, xv[3] = {0, 0, 0}, t[3] = {0, 0, 0};
+    bool two = u >= 0 && v >= 0;
+    if (u >= 0) for (int a = 0; a < 3; ++a) xu[a] = (float)X[3 * u + a];
+    if (v >= 0) for (int a = 0; a < 3; ++a) xv[a] = (float)X[3 * v + a];
+    float h = 1.f;
+    if (two) {
+        for (int a = 0; a < 3; ++a) t[a] = xv[a] - xu[a];
+        h = sqrtf(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+        if (!(h > 0.f)) h = 1.f;
+    }
+    float ih = 1.f / h;
+    // coarse edge ends (-1 a, +1 b)
+    int32_t j = nci[q];
+    int32_t ja = -1, jb = -1;
+    for (int64_t k = hrp[j]; k < hrp[j + 1]; ++k) { if (hv[k] < 0) ja = hci[k]; else jb = hci[k]; }
+    float xa[3] = {0, 0, 0}, xb[3] = {0, 0, 0}, T[3] = {0, 0, 0};
+    if (ja >= 0) for (int a = 0; a < 3; ++a) xa[a] = (float)Xc[3 * (int64_t)ja + a];
+    if (jb >= 0) for (int a = 0; a < 3; ++a) xb[a] = (float)Xc[3 * (int64_t)jb + a];
+    bool ctwo = ja >= 0 && jb >= 0;
+    if (ctwo) for (int a = 0; a < 3; ++a) T[a] = xb[a] - xa[a];
+    float Tn = sqrtf(T[0] * T[0] + T[1] * T[1] + T[2] * T[2]);
+    float dot = t[0] * T[0] + t[1] * T[1] + t[2] * T[2];
+    f[0] = two ? 1.f : 0.f;
+    for (int a = 0; a < 3; ++a) f[1 + a] = t[a] * ih;
+    for (int a = 0; a < 3; ++a) f[4 + a] = two ? T[a] * ih : 0.f;
+    f[7] = two ? Tn * ih : 0.f;
+    f[8] = (two && Tn > 0.f) ? dot / (h * Tn) : 0.f;
+    f[9] = (two && Tn > 0.f) ? dot / (Tn * Tn) : 0.f;
+    f[10] = ctwo ? 0.f : 1.f;
+    f[11] = (float)(nrp[i + 1] - nrp[i]) / 32.f;
+    f[12] = (float)(trp[i + 1] - trp[i]) / 16.f;
+    f[13] = ja >= 0 ? (float)row_lookup(trp, tci, tv, i, ja) : 0.f;
+    f[14] = jb >= 0 ? (float)row_lookup(trp, tci, tv, i, jb) : 0.f;
+    f[15] = ja >= 0 ? (float)row_lookup(prp, pci, pv, u, ja) : 0.f;
+    f[16] = jb >= 0 ? (float)row_lookup(prp, pci, pv, u, jb) : 0.f;
+    f[17] = ja >= 0 ? (float)row_lookup(prp, pci, pv, v, ja) : 0.f;
+    f[18] = jb >= 0 ? (float)row_lookup(prp, pci, pv, v, jb) : 0.f;
+    f[19] = (float)p0[q];
+    double aii = 0.0, l1 = 0.0;
+    for (int64_t k = arp[i]; k < arp[i + 1]; ++k) {
+        double a = av[k];
+        l1 += fabs(a);
+        if (aci[k] == i) aii = a;
+    }
+    f[20] = l1 > 0.0 ? (float)(aii / l1) : 0.f;
+    f[21] = sig ? (float)(log10(fmax(sig[i], 1e-30)) / 6.0) : 0.f;
+    f[22] = (float)lev / 8.f;
+    // midpoint offset of the coarse edge from the fine edge, in fine-edge lengths
+    if (two) {
+        float mi[3], mj[3];
+        for (int a = 0; a < 3; ++a) {
+            mi[a] = 0.5f * (xu[a] + xv[a]);
+            mj[a] = ctwo ? 0.5f * (xa[a] + xb[a]) : (ja >= 0 ? xa[a] : xb[a]);
+            f[23 + a] = (mj[a] - mi[a]) * ih;
+        }
+    }
+    float* out = F + q * SPHC_MLP_NFEAT;
+    for (int a = 0; a < SPHC_MLP_NFEAT; ++a) out[a] = f[a];
+}
+
+int level_features(const Level& L, const DBuf<double>& Xc, int lev, float* F, cudaStream_t s) {
+    if (!L.X.p || !Xc.p) {
+        set_error("features need node coordinates (pass coords to sphc_setup)");
+        return SPHC_EINVAL;
+    }
+    int64_t nnzN = L.P0.nnz, ne = L.A.nr;
+    if (nnzN > 0)
+        SPHC_LAUNCH(k_features<<<grid_for(nnzN, 256), 256, 0, s>>>(
+            ne, nnzN, lev, L.D.rp.p, L.D.ci.p, L.D.v.p, L.T.rp.p, L.T.ci.p, L.T.v.p, L.P0.rp.p, L.P0.ci.p, L.P0.v.p,
+            L.DH.rp.p, L.DH.ci.p, L.DH.v.p, L.Pn.rp.p, L.Pn.ci.p, L.Pn.v.p, L.A.rp.p, L.A.ci.p, L.A.v.p, L.X.p, Xc.p,
+            L.sig.p, F));
+    SPHC_CK(cudaGetLastError());
+    return SPHC_OK;
+}
+
 // histogram of the local sub-problem sizes (|N_i|, |T_i|), clipped at 32: block-local counts
 __global__ void k_ls_hist(const int64_t* nrp, const int64_t* trp, int64_t ne, unsigned long long* hist) {
     __shared__ unsigned int h[33 * 33];
@@ -846,8 +994,33 @@ int coarse_inverse(const DCSR& A, DBuf<double>& Ainv, bool allow_shift, cudaStre
 }
 
 // ------------------------------------------------------------------ one level of Alg. 3
-int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext, DCSR& Annext, Profiler* prof,
-                cudaStream_t s) {
+// coordinates of the next level's nodes: centroids of the aggregates
+static int coarse_coords(const Level& L, DBuf<double>& Xc, cudaStream_t s) {
+    int64_t nv = L.An.nr, nagg = L.nagg;
+    if (!L.X.p) return SPHC_OK;
+    DBuf<int32_t> cnt, members;
+    DBuf<int64_t> mptr;
+    DBuf<unsigned long long> cur;
+    SPHC_TRY(cnt.alloc(nagg + 1, s));
+    SPHC_TRY(cnt.zero(s));
+    SPHC_TRY(mptr.alloc(nagg + 1, s));
+    SPHC_TRY(members.alloc(nv, s));
+    SPHC_TRY(cur.alloc(nagg + 1, s));
+    if (nv > 0) SPHC_LAUNCH(k_count_agg<<<grid_for(nv, 256), 256, 0, s>>>(L.agg.p, nv, cnt.p));
+    SPHC_TRY(scan_i32_to_i64(cnt.p, mptr.p, nagg, s, nullptr));
+    SPHC_LAUNCH(k_i64_to_u64b<<<grid_for(nagg + 1, 256), 256, 0, s>>>(mptr.p, cur.p, nagg + 1));
+    if (nv > 0) SPHC_LAUNCH(k_scatter_agg<<<grid_for(nv, 256), 256, 0, s>>>(L.agg.p, nv, cur.p, members.p));
+    int64_t mx = 0;
+    SPHC_TRY(max_row_length(mptr.p, nagg, s, &mx));
+    SPHC_TRY(segmented_sort(mptr.p, nagg, members.p, nullptr, mx, s));
+    SPHC_TRY(Xc.alloc(nagg * 3, s));
+    if (nagg > 0) SPHC_LAUNCH(k_centroids<<<grid_for(nagg, 256), 256, 0, s>>>(mptr.p, members.p, nagg, L.X.p, Xc.p));
+    SPHC_CK(cudaGetLastError());
+    return SPHC_OK;
+}
+
+int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext, DCSR& Annext, DBuf<double>& Xnext,
+                const float* mlp_params, Profiler* prof, cudaStream_t s) {
     uint64_t seed = o.seed + 1000ULL * (uint64_t)lev;
     int64_t nv = L.An.nr, ne = L.A.nr;
     // aggregation on the structural nodal graph (drop tolerance 0)
@@ -929,12 +1102,29 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
     size_t sm = sizeof(LocalSys) * LOC_WARPS;
     SPHC_CK(cudaFuncSetAttribute(k_p0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     SPHC_CK(cudaFuncSetAttribute(k_emin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    SPHC_CK(cudaFuncSetAttribute(k_learned_p0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     if (ne > 0)
         SPHC_LAUNCH(k_p0<<<grid_for(ne, LOC_WARPS), LOC_WARPS * 32, sm, s>>>(ne, L.T.rp.p, L.T.ci.p, L.T.v.p, L.P0.rp.p, L.P0.ci.p,
                                                                   L.DH.rp.p, L.DH.ci.p, L.DH.v.p, L.P0.v.p, st.p,
                                                                   L.hist.p));
-    SPHC_TRY(csr_copy(L.P0, L.Pe, s));
     delete sec_p0;
+    SPHC_TRY(coarse_coords(L, Xnext, s));
+    int emin_iters = o.emin_iters;
+    if (o.learned) {
+        Section sec(prof, "setup_learned_l0", s);
+        if (!mlp_params) { set_error("learned warm start without MLP parameters"); return SPHC_EINVAL; }
+        DBuf<float> F, corr;
+        SPHC_TRY(F.alloc(nnzN * SPHC_MLP_NFEAT, s));
+        SPHC_TRY(corr.alloc(nnzN, s));
+        SPHC_TRY(level_features(L, Xnext, lev, F.p, s));
+        SPHC_TRY(mlp_predict(mlp_params, F.p, nnzN, corr.p, s));
+        if (ne > 0)
+            SPHC_LAUNCH(k_learned_p0<<<grid_for(ne, LOC_WARPS), LOC_WARPS * 32, sm, s>>>(
+                ne, L.T.rp.p, L.T.ci.p, L.T.v.p, L.P0.rp.p, L.P0.ci.p, L.DH.rp.p, L.DH.ci.p, L.DH.v.p, corr.p, L.P0.v.p,
+                st.p));
+        emin_iters = o.learned_emin_iters;
+    }
+    SPHC_TRY(csr_copy(L.P0, L.Pe, s));
     DBuf<double> Pnew;
     SPHC_TRY(Pnew.alloc(nnzN, s));
     // algorithmic bytes of one step: A (values, columns, row pointers), the pattern rows of P
@@ -942,7 +1132,7 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
     double emin_bytes = (double)L.A.nnz * 12.0 + (double)ne * 8.0 * 3 + (double)nnzN * (4 + 8 + 8 + 8) +
                         (double)L.T.nnz * 12.0;
     int tid = prof ? prof->find("emin_level0", emin_bytes) : -1;
-    for (int it = 0; it < o.emin_iters; ++it) {
+    for (int it = 0; it < emin_iters; ++it) {
         if (tid >= 0) prof->begin(tid, s);
         if (ne > 0)
             SPHC_LAUNCH(k_emin<<<grid_for(ne, LOC_WARPS), LOC_WARPS * 32, sm, s>>>(

@@ -46,6 +46,8 @@ struct VLevel {
 struct Level {
     DCSR A, D, An, Dt;
     DCSR AD;                         // A D (FP64), kept from the nodal operator of level 0
+    DBuf<double> X;                  // node coordinates [n_nodes x 3] (coarse levels: aggregate centroids)
+    DBuf<double> sig;                // per-edge sigma (level 0 only)
     DBuf<int32_t> col_e, col_n;
     int ncol_e = 0, ncol_n = 0;
     // transfer data (absent on the coarsest level)
@@ -84,8 +86,11 @@ struct Profiler {
     ~Profiler();
 };
 
-int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext, DCSR& Annext, Profiler* prof,
-                cudaStream_t s);
+int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext, DCSR& Annext, DBuf<double>& Xnext,
+                const float* mlp_params, Profiler* prof, cudaStream_t s);
+int level_features(const Level& L, const DBuf<double>& Xc, int lev, float* F, cudaStream_t s);
+// mlp.cu
+int mlp_predict(const float* params_dev, const float* X, int64_t m, float* out, cudaStream_t s);
 
 // Scoped section timer (no-op when prof is null).
 struct Section {
@@ -128,6 +133,7 @@ struct Hierarchy {
     long long body_launches = 0;     // kernels in one CG graph iteration (for the launch count)
     double setup_ms = 0.0, solve_ms = 0.0;
     Profiler prof;
+    DBuf<float> mlp;                 // MLP parameters on the device (learned warm start)
     ~Hierarchy() {
         if (cg_exec) cudaGraphExecDestroy(cg_exec);
         if (cg_graph) cudaGraphDestroy(cg_graph);

@@ -35,7 +35,19 @@ class sphc_opts(ctypes.Structure):
     _fields_ = [("max_levels", ctypes.c_int32), ("emin_iters", ctypes.c_int32), ("max_coarse", ctypes.c_int64),
                 ("emin_omega", ctypes.c_double), ("seed", ctypes.c_uint64), ("power_iters", ctypes.c_int32),
                 ("vcycle_fp32", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("flexible", ctypes.c_int32),
-                ("profile", ctypes.c_int32), ("cg_graph", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("profile", ctypes.c_int32), ("cg_graph", ctypes.c_int32), ("learned", ctypes.c_int32),
+                ("learned_emin_iters", ctypes.c_int32), ("mlp_params", ctypes.c_void_p),
+                ("reserved", ctypes.c_int32 * 4)]
+
+
+class sphc_train_opts(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int32), ("batch", ctypes.c_int32), ("lr", ctypes.c_float),
+                ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
+                ("weight_decay", ctypes.c_float), ("pad", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("reserved", ctypes.c_int32 * 4)]
+
+
+MLP_NFEAT, MLP_HIDDEN, MLP_NPARAM = 32, 128, 20929
 
 
 class sphc_level_info(ctypes.Structure):
@@ -61,7 +73,8 @@ class sphc_timer(ctypes.Structure):
 
 EXPORTED = ["sphc_default_opts", "sphc_setup", "sphc_solve", "sphc_vcycle", "sphc_get_stats",
             "sphc_get_level_info", "sphc_export_size", "sphc_export", "sphc_destroy", "sphc_last_error",
-            "sphc_get_profile", "sphc_launch_count", "sphc_relres_noalloc"]
+            "sphc_get_profile", "sphc_launch_count", "sphc_relres_noalloc", "sphc_default_train_opts",
+            "sphc_mlp_train", "sphc_mlp_predict", "sphc_mlp_gradient", "sphc_export_features"]
 
 _lib = None
 
@@ -87,6 +100,11 @@ def load(path: str | None = None):
     lib.sphc_destroy.restype = None
     lib.sphc_get_profile.argtypes = [P, ctypes.POINTER(sphc_timer), I, ctypes.POINTER(I)]
     lib.sphc_relres_noalloc.argtypes = [P, P, P, I, P, P]
+    lib.sphc_default_train_opts.argtypes = [ctypes.POINTER(sphc_train_opts)]
+    lib.sphc_mlp_train.argtypes = [P, P, I64, ctypes.POINTER(sphc_train_opts), P, P, P]
+    lib.sphc_mlp_predict.argtypes = [P, P, I64, P, P]
+    lib.sphc_mlp_gradient.argtypes = [P, P, P, I, P, P, P]
+    lib.sphc_export_features.argtypes = [P, I, P, P, P]
     lib.sphc_launch_count.argtypes = []
     lib.sphc_launch_count.restype = ctypes.c_int64
     lib.sphc_last_error.argtypes = []
@@ -128,9 +146,14 @@ def _stream(stream):
 
 
 def default_opts(**kw) -> sphc_opts:
+    """Options with the library defaults, overridden by keyword.  mlp_params may be a float32
+    numpy array or torch tensor; the options object keeps a reference to it."""
     o = sphc_opts()
     _check(load().sphc_default_opts(ctypes.byref(o)))
     for k, v in kw.items():
+        if k == "mlp_params" and v is not None and not isinstance(v, int):
+            o._keep = v
+            v = _ptr(v)
         setattr(o, k, v)
     return o
 
@@ -184,6 +207,14 @@ class Handle:
         Returns the status code."""
         return load().sphc_relres_noalloc(self._ptr, _ptr(b), _ptr(x), nrhs, _ptr(relres), _stream(stream))
 
+    def features(self, level=0, stream=None):
+        """(X [nnz(P_e) x 32], y = P_e - P0 [nnz(P_e)]) of a level, as numpy float32."""
+        nr, nc, nz = self.export_size(level, "Pe")
+        X = np.empty((nz, MLP_NFEAT), np.float32)
+        y = np.empty(nz, np.float32)
+        _check(load().sphc_export_features(self._ptr, level, _ptr(X), _ptr(y), _stream(stream)))
+        return X, y
+
     def profile(self) -> dict:
         arr = (sphc_timer * 32)()
         n = ctypes.c_int()
@@ -213,6 +244,43 @@ class Handle:
         v = np.empty(nz, np.float64)
         _check(load().sphc_export(self._ptr, level, X[what], _ptr(rp), _ptr(ci), _ptr(v), None, _stream(stream)))
         return rp, ci, v, (nr, nc)
+
+
+def default_train_opts(**kw) -> sphc_train_opts:
+    o = sphc_train_opts()
+    _check(load().sphc_default_train_opts(ctypes.byref(o)))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def mlp_train(X, y, params, opts=None, stream=None):
+    """Train in place on the GPU; X float32 [m, 32], y float32 [m], params float32 [NPARAM].
+    Returns the loss history."""
+    X = np.ascontiguousarray(X, np.float32)
+    y = np.ascontiguousarray(y, np.float32)
+    o = opts if opts is not None else default_train_opts()
+    hist = np.zeros(max(o.steps, 1), np.float32)
+    _check(load().sphc_mlp_train(_ptr(X), _ptr(y), X.shape[0], ctypes.byref(o), _ptr(params), _ptr(hist),
+                                 _stream(stream)))
+    return hist[:o.steps]
+
+
+def mlp_predict(params, X, stream=None):
+    X = np.ascontiguousarray(X, np.float32)
+    out = np.empty(X.shape[0], np.float32)
+    _check(load().sphc_mlp_predict(_ptr(params), _ptr(X), X.shape[0], _ptr(out), _stream(stream)))
+    return out
+
+
+def mlp_gradient(params, X, y, stream=None):
+    X = np.ascontiguousarray(X, np.float32)
+    y = np.ascontiguousarray(y, np.float32)
+    grad = np.zeros(MLP_NPARAM, np.float32)
+    loss = np.zeros(1, np.float32)
+    _check(load().sphc_mlp_gradient(_ptr(params), _ptr(X), _ptr(y), X.shape[0], _ptr(grad), _ptr(loss),
+                                    _stream(stream)))
+    return grad, float(loss[0])
 
 
 def launch_count() -> int:
