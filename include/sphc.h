@@ -72,7 +72,8 @@ typedef struct {
     int32_t learned;         /* 1: learned warm start of P_e (needs mlp_params and coords) (default 0) */
     int32_t learned_emin_iters; /* energy-minimisation steps after the learned warm start (default 0) */
     const float* mlp_params; /* SPHC_MLP_NPARAM floats (host or device), see sphc_mlp_train */
-    int32_t reserved[4];
+    int32_t autotune;        /* 1: time the smoother kernels' lanes-per-row widths at setup (default 0) */
+    int32_t reserved[3];
 } sphc_opts;
 
 /* Learned warm start (not part of the paper).  For every pattern entry (i, j) of P_e a
@@ -199,6 +200,20 @@ SPHC_API int sphc_get_profile(sphc_handle* h, sphc_timer* out, int max, int* n);
 
 /* Number of kernels the library has launched in this process so far. */
 SPHC_API int64_t sphc_launch_count(void);
+
+/* Many independent systems of uneven size (not part of the paper).  sphc_setup_batched builds
+ * one hierarchy per system (arrays of nsys descriptors; coords / sigma_edge may be NULL or hold
+ * NULL entries) and captures every system's whole CG (a device-side while loop per system) as
+ * parallel branches of one CUDA graph.  sphc_solve_batched launches that graph once per
+ * right-hand side: b[k] and x[k] are nrhs x n_e(k) FP64 arrays (host or device) of system k;
+ * iters and relres (nsys x nrhs, may be NULL) receive the CG iterations and true relative
+ * residuals.  Returns SPHC_OK if every system converged, else the first failure code. */
+typedef struct sphc_batch sphc_batch;
+SPHC_API int sphc_setup_batched(int nsys, const sphc_csr* A_e, const sphc_csr* D_h, const double* const* coords,
+                                const double* const* sigma_edge, const sphc_opts* opts, void* stream, sphc_batch** out);
+SPHC_API int sphc_solve_batched(sphc_batch* batch, const double* const* b, double* const* x, int nrhs, double tol,
+                                void* stream, int* iters, double* relres);
+SPHC_API void sphc_batch_destroy(sphc_batch* batch);
 
 /* Fill *opts with the training defaults. */
 SPHC_API int sphc_default_train_opts(sphc_train_opts* opts);

@@ -3,6 +3,8 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <string>
+#include <vector>
 
 #include "sphc_level.cuh"
 
@@ -167,6 +169,7 @@ int setup_impl(sphc_handle* h, const sphc_csr* A_e, const sphc_csr* D_h, const d
     {
         Section sec(prof, "setup_vcycle_ops", s);
         SPHC_TRY(build_vcycle_ops(H, s));
+        if (o.autotune) SPHC_TRY(autotune_vcycle(H, s));
     }
     SPHC_CK(cudaStreamSynchronize(s));
     return SPHC_OK;
@@ -193,6 +196,7 @@ int sphc_default_opts(sphc_opts* o) {
     o->learned = 0;
     o->learned_emin_iters = 0;
     o->mlp_params = nullptr;
+    o->autotune = 0;
     return SPHC_OK;
 }
 
@@ -438,6 +442,143 @@ int sphc_get_profile(sphc_handle* h, sphc_timer* out, int max, int* n) {
 }
 
 int64_t sphc_launch_count(void) { return (int64_t)g_launches.load(); }
+
+}  // extern "C"
+
+struct sphc_batch {
+    std::vector<sphc_handle*> hs;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    cudaStream_t cs = nullptr;
+    std::vector<cudaStream_t> bs;
+    std::vector<cudaEvent_t> ev;
+};
+
+static void batch_free(sphc_batch* B) {
+    if (!B) return;
+    if (B->ge) cudaGraphExecDestroy(B->ge);
+    if (B->g) cudaGraphDestroy(B->g);
+    for (auto e : B->ev) cudaEventDestroy(e);
+    for (auto st : B->bs) cudaStreamDestroy(st);
+    if (B->cs) cudaStreamDestroy(B->cs);
+    for (auto h : B->hs) sphc_destroy(h);
+    delete B;
+}
+
+static int batch_capture(sphc_batch* B) {
+    int n = (int)B->hs.size();
+    SPHC_CK(cudaStreamCreateWithFlags(&B->cs, cudaStreamNonBlocking));
+    B->bs.resize(n);
+    B->ev.resize(n + 1);
+    for (int k = 0; k < n; ++k) SPHC_CK(cudaStreamCreateWithFlags(&B->bs[k], cudaStreamNonBlocking));
+    for (int k = 0; k <= n; ++k) SPHC_CK(cudaEventCreateWithFlags(&B->ev[k], cudaEventDisableTiming));
+    SPHC_CK(cudaStreamBeginCapture(B->cs, cudaStreamCaptureModeThreadLocal));
+    cudaEventRecord(B->ev[n], B->cs);
+    int rc = SPHC_OK;
+    for (int k = 0; k < n && rc == SPHC_OK; ++k) {
+        cudaStreamWaitEvent(B->bs[k], B->ev[n], 0);
+        rc = capture_cg(B->hs[k]->H, B->bs[k]);
+        cudaEventRecord(B->ev[k], B->bs[k]);
+        cudaStreamWaitEvent(B->cs, B->ev[k], 0);
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(B->cs, &g);
+    if (rc != SPHC_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) {
+        set_error("batched CG capture failed: %s", cudaGetErrorString(e));
+        return SPHC_ECUDA;
+    }
+    B->g = g;
+    SPHC_CK(cudaGraphInstantiate(&B->ge, B->g, 0));
+    return SPHC_OK;
+}
+
+extern "C" {
+
+int sphc_setup_batched(int nsys, const sphc_csr* A_e, const sphc_csr* D_h, const double* const* coords,
+                       const double* const* sigma_edge, const sphc_opts* opts, void* stream, sphc_batch** out) {
+    if (nsys < 1 || !A_e || !D_h || !out) {
+        set_error("sphc_setup_batched: invalid argument");
+        return SPHC_EINVAL;
+    }
+    *out = nullptr;
+    sphc_batch* B = new (std::nothrow) sphc_batch();
+    if (!B) return SPHC_ENOMEM;
+    for (int k = 0; k < nsys; ++k) {
+        sphc_handle* h = nullptr;
+        int rc = sphc_setup(&A_e[k], &D_h[k], coords ? coords[k] : nullptr, sigma_edge ? sigma_edge[k] : nullptr, opts,
+                            stream, &h);
+        if (rc != SPHC_OK) {
+            std::string msg = last_error();
+            batch_free(B);
+            set_error("system %d: %s", k, msg.c_str());
+            return rc;
+        }
+        B->hs.push_back(h);
+    }
+    int rc = batch_capture(B);
+    if (rc != SPHC_OK) {
+        batch_free(B);
+        return rc;
+    }
+    *out = B;
+    return SPHC_OK;
+}
+
+int sphc_solve_batched(sphc_batch* B, const double* const* b, double* const* x, int nrhs, double tol, void* stream,
+                       int* iters, double* relres) {
+    if (!B || !b || !x || nrhs < 1 || !(tol > 0.0)) {
+        set_error("sphc_solve_batched: invalid argument");
+        return SPHC_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    int n = (int)B->hs.size();
+    double tol2 = tol * tol;
+    std::vector<int> hit(2 * n);
+    std::vector<double> hsc(2 * n);
+    int status = SPHC_OK;
+    for (int r = 0; r < nrhs; ++r) {
+        for (int k = 0; k < n; ++k) {
+            Hierarchy& H = B->hs[k]->H;
+            int64_t m = H.L[0].A.nr;
+            SPHC_CK(cudaMemcpyAsync(H.bin.p, b[k] + (int64_t)r * m, sizeof(double) * m, cudaMemcpyDefault, s));
+            SPHC_CK(cudaMemcpyAsync(H.scal.p + 8, &tol2, sizeof(double), cudaMemcpyHostToDevice, s));
+        }
+        SPHC_CK(cudaGraphLaunch(B->ge, s));
+        for (int k = 0; k < n; ++k) {
+            Hierarchy& H = B->hs[k]->H;
+            int64_t m = H.L[0].A.nr;
+            SPHC_CK(cudaMemcpyAsync(x[k] + (int64_t)r * m, H.x.p, sizeof(double) * m, cudaMemcpyDefault, s));
+            SPHC_CK(cudaMemcpyAsync(&hit[2 * k], H.itc.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+            SPHC_CK(cudaMemcpyAsync(&hsc[2 * k], H.scal.p + 5, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        }
+        SPHC_CK(cudaStreamSynchronize(s));
+        for (int k = 0; k < n; ++k) {
+            Hierarchy& H = B->hs[k]->H;
+            int it = hit[2 * k], st = hit[2 * k + 1];
+            g_launches.fetch_add(H.branch_launches + H.body_launches * (long long)it);
+            double rel = hsc[2 * k] > 0 ? sqrt(hsc[2 * k + 1]) / sqrt(hsc[2 * k]) : 0.0;
+            if (iters) iters[(int64_t)k * nrhs + r] = it;
+            if (relres) relres[(int64_t)k * nrhs + r] = rel;
+            int rc = st == 0 ? SPHC_OK : (st == 1 ? SPHC_EBREAKDOWN : SPHC_ENOTCONV);
+            if (rc != SPHC_OK && status == SPHC_OK) {
+                status = rc;
+                set_error("system %d, right side %d: %s after %d iterations", k, r,
+                          rc == SPHC_EBREAKDOWN ? "CG breakdown" : "no convergence", it);
+            }
+        }
+    }
+    return status;
+}
+
+void sphc_batch_destroy(sphc_batch* B) {
+    if (!B) return;
+    cudaDeviceSynchronize();
+    batch_free(B);
+}
 
 __global__ void k_target(const double* pe, const double* p0, int64_t n, float* y) {
     int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;

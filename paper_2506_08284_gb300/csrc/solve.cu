@@ -275,6 +275,8 @@ int build_vcycle_ops(Hierarchy& H, cudaStream_t s) {
     SPHC_TRY(H.ccn.alloc(H.n_coarse_nodes, s));
     SPHC_TRY(H.dpart.alloc(DOT_PARTS, s));
     SPHC_TRY(H.itc.alloc(4, s));
+    SPHC_TRY(H.bin.alloc(n0, s));
+
     return SPHC_OK;
 }
 
@@ -419,7 +421,7 @@ template <typename T>
 static void launch_rows_sgs(const SmoothOp<T>& op, int64_t k0, int64_t k1, const T* b, T* x, cudaStream_t s) {
     int64_t rows = k1 - k0;
     if (rows <= 0) return;
-    int sub = sub_for(op.nnz, op.n);
+    int sub = op.sub > 0 ? op.sub : sub_for(op.nnz, op.n);
     int64_t th = rows * sub;
     switch (sub) {
         case 4: SPHC_LAUNCH(k_sgs_color<T, 4><<<grid_for(th, 256), 256, 0, s>>>(op.rp.p, op.ci.p, op.v.p, op.perm.p, op.dinv.p, k0, k1, b, x)); break;
@@ -476,7 +478,7 @@ static void sgs(const SmoothOp<T>& op, const T* b, T* x, cudaStream_t s) {
 template <typename T>
 static void resid(const SmoothOp<T>& op, const T* b, const T* x, T* r, cudaStream_t s) {
     if (op.n == 0) return;
-    int sub = sub_for(op.nnz, op.n);
+    int sub = op.sub > 0 ? op.sub : sub_for(op.nnz, op.n);
     int64_t th = op.n * sub;
     switch (sub) {
         case 4: SPHC_LAUNCH(k_resid<T, 4><<<grid_for(th, 256), 256, 0, s>>>(op.rp.p, op.ci.p, op.v.p, op.perm.p, op.n, b, x, r)); break;
@@ -663,13 +665,55 @@ int apply_vcycle(Hierarchy& H, const double* r, double* z, cudaStream_t s) {
     return SPHC_OK;
 }
 
+// Autotuner: time one forward + backward sweep for each lanes-per-row width and keep the fastest
+// (the operators are stored in CSR with rows grouped by colour, so the tunable shape is the
+// number of lanes that share a row).
+template <typename T>
+static int autotune_op(SmoothOp<T>& op, DBuf<T>& bvec, DBuf<T>& xvec, cudaStream_t s) {
+    if (op.n <= SGS_BLOCK_MAX_ROWS || op.n > bvec.n || op.n > xvec.n) return SPHC_OK;
+    cudaEvent_t e0, e1;
+    SPHC_CK(cudaEventCreate(&e0));
+    SPHC_CK(cudaEventCreate(&e1));
+    SPHC_LAUNCH(k_zero<T><<<grid_for(op.n, 256), 256, 0, s>>>(bvec.p, op.n));
+    float best = 1e30f;
+    int best_sub = 0;
+    for (int sub : {4, 8, 16, 32}) {
+        op.sub = sub;
+        sgs(op, bvec.p, xvec.p, s);                   // warm-up
+        cudaEventRecord(e0, s);
+        for (int rep = 0; rep < 3; ++rep) sgs(op, bvec.p, xvec.p, s);
+        cudaEventRecord(e1, s);
+        SPHC_CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) { best = ms; best_sub = sub; }
+    }
+    op.sub = best_sub;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return SPHC_OK;
+}
+
+int autotune_vcycle(Hierarchy& H, cudaStream_t s) {
+    for (int l = 0; l + 1 < H.nlev; ++l) {
+        if (H.opts.vcycle_fp32) {
+            SPHC_TRY(autotune_op(H.V32[l].A, H.V32[l].b, H.V32[l].x, s));
+            SPHC_TRY(autotune_op(H.V32[l].An, H.V32[l].g, H.V32[l].c, s));
+        } else {
+            SPHC_TRY(autotune_op(H.V64[l].A, H.V64[l].b, H.V64[l].x, s));
+            SPHC_TRY(autotune_op(H.V64[l].An, H.V64[l].g, H.V64[l].c, s));
+        }
+    }
+    return SPHC_OK;
+}
+
 // ------------------------------------------------------------------ CG
 // scal: 0 rz, 1 pq, 2 rr, 3 rz_new, 4 z.r_old, 5 bb
 __global__ void k_cg_xr(double* x, double* r, double* rold, const double* p, const double* q, const double* sc,
                         int64_t n, int flexible) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    double alpha = sc[0] / sc[1];
+    double alpha = sc[1] > 0.0 ? sc[0] / sc[1] : 0.0;     // breakdown: leave x unchanged
     x[i] += alpha * p[i];
     if (flexible) rold[i] = r[i];
     r[i] -= alpha * q[i];
@@ -812,6 +856,92 @@ static int pcg_graph(Hierarchy& H, const double* b, double* x, double tol, cudaS
     if (status == SPHC_EBREAKDOWN) set_error("CG breakdown after %d iterations", it);
     else if (status == SPHC_ENOTCONV) set_error("CG did not reach the tolerance in %d iterations", it);
     return status;
+}
+
+// ------------------------------------------------------------------ CG captured whole (batched solves)
+// The right side is read from H.bin and tol^2 from scal[8]; x stays in H.x.  Every iteration
+// (V-cycle first) runs inside a while node whose condition a prologue kernel sets, so the whole
+// solve needs no host decision and can be one branch of a larger graph.
+__global__ void k_cg_prep(cudaGraphConditionalHandle hnd, double* sc, int* itc) {
+    sc[7] = sc[8] * sc[5];
+    sc[0] = 1.0;                         // rz of the previous iteration (p = 0 makes beta irrelevant)
+    itc[0] = 0;
+    itc[1] = sc[5] > 0.0 ? 3 : 0;        // 3: running; 0: converged (b = 0)
+    cudaGraphSetConditional(hnd, sc[5] > 0.0 ? 1u : 0u);
+}
+
+static int cg_iter_body(Hierarchy& H, cudaGraphConditionalHandle hnd, cudaStream_t s) {
+    const DCSR& A = H.L[0].A;
+    int64_t n = A.nr;
+    int flexible = H.opts.flexible;
+    double* sc = H.scal.p;
+    SPHC_TRY(apply_vcycle(H, H.r.p, H.z.p, s));
+    dot_buf(H, H.r.p, H.z.p, n, sc + 3, s);
+    if (flexible) dot_buf(H, H.z.p, H.rold.p, n, sc + 4, s);
+    SPHC_LAUNCH(k_cg_p<<<grid_for(n, 256), 256, 0, s>>>(H.p.p, H.z.p, sc, n, flexible));
+    SPHC_LAUNCH(k_cg_shift<<<1, 1, 0, s>>>(sc));
+    SPHC_TRY(spmv64(A, H.p.p, H.q.p, s));
+    dot_buf(H, H.p.p, H.q.p, n, sc + 1, s);
+    SPHC_LAUNCH(k_cg_xr<<<grid_for(n, 256), 256, 0, s>>>(H.x.p, H.r.p, H.rold.p, H.p.p, H.q.p, sc, n, flexible));
+    dot_buf(H, H.r.p, H.r.p, n, sc + 2, s);
+    SPHC_LAUNCH(k_cg_check<<<1, 1, 0, s>>>(hnd, sc, H.itc.p, H.opts.max_iter));
+    SPHC_CK(cudaGetLastError());
+    return SPHC_OK;
+}
+
+// Append the whole CG of H to the graph being captured on stream s.
+int capture_cg(Hierarchy& H, cudaStream_t s) {
+    const DCSR& A = H.L[0].A;
+    int64_t n = A.nr;
+    double* sc = H.scal.p;
+    if (!H.cap_stream) SPHC_CK(cudaStreamCreateWithFlags(&H.cap_stream, cudaStreamNonBlocking));
+    H.capturing = true;
+    long long lstart = g_launches.load();
+    SPHC_CK(cudaMemcpyAsync(H.r.p, H.bin.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    SPHC_CK(cudaMemsetAsync(H.x.p, 0, sizeof(double) * n, s));
+    SPHC_CK(cudaMemsetAsync(H.p.p, 0, sizeof(double) * n, s));
+    SPHC_CK(cudaMemsetAsync(H.rold.p, 0, sizeof(double) * n, s));
+    dot_buf(H, H.bin.p, H.bin.p, n, sc + 5, s);
+    cudaStreamCaptureStatus st;
+    cudaGraph_t g;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    SPHC_CK(cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, nullptr, &ndeps));
+    cudaGraphConditionalHandle hnd;
+    SPHC_CK(cudaGraphConditionalHandleCreate(&hnd, g, 0, 0));
+    SPHC_LAUNCH(k_cg_prep<<<1, 1, 0, s>>>(hnd, sc, H.itc.p));
+    SPHC_CK(cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, nullptr, &ndeps));
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = hnd;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    SPHC_CK(cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &np));
+    SPHC_CK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    SPHC_CK(cudaStreamBeginCaptureToGraph(H.cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    long long l0 = g_launches.load();
+    int rc = cg_iter_body(H, hnd, H.cap_stream);
+    H.body_launches = g_launches.load() - l0;
+    g_launches.fetch_sub(H.body_launches);
+    cudaGraph_t captured = nullptr;
+    cudaError_t e = cudaStreamEndCapture(H.cap_stream, &captured);
+    if (rc != SPHC_OK) { H.capturing = false; return rc; }
+    if (e != cudaSuccess) {
+        H.capturing = false;
+        set_error("CG body capture failed: %s", cudaGetErrorString(e));
+        return SPHC_ECUDA;
+    }
+    // true residual
+    SPHC_TRY(spmv64(A, H.x.p, H.q.p, s));
+    SPHC_LAUNCH(k_sub<<<grid_for(n, 256), 256, 0, s>>>(H.bin.p, H.q.p, n));
+    dot_buf(H, H.q.p, H.q.p, n, sc + 6, s);
+    H.capturing = false;
+    H.branch_launches = g_launches.load() - lstart;   // counted when the graph runs
+    g_launches.fetch_sub(H.branch_launches);
+    SPHC_CK(cudaGetLastError());
+    return SPHC_OK;
 }
 
 int pcg_solve(Hierarchy& H, const double* b, double* x, double tol, cudaStream_t s, int* iters, double* relres) {

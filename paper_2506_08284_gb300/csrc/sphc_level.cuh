@@ -18,6 +18,7 @@ template <typename T>
 struct SmoothOp {
     int64_t n = 0, nnz = 0;
     int ncolor = 0;
+    int sub = 0;                     // lanes per row (0: chosen from the mean row length)
     std::vector<int64_t> cstart;     // colour c owns copy rows [cstart[c], cstart[c+1])
     DBuf<int64_t> cstart_dev;
     DBuf<int32_t> rp, ci, perm;
@@ -121,7 +122,7 @@ struct Hierarchy {
     std::vector<VLevel<float>> V32;
     std::vector<VLevel<double>> V64;
     // CG work vectors (FP64)
-    DBuf<double> x, r, z, p, q, rold, scal;
+    DBuf<double> x, r, z, p, q, rold, scal, bin;
     DBuf<double> cb, cx;             // coarsest right side / solution (FP64)
     // CG as one CUDA graph: a device-side while loop (conditional node) around one iteration
     DBuf<double> dpart;              // partial sums of the dot products
@@ -131,6 +132,7 @@ struct Hierarchy {
     cudaStream_t cap_stream = nullptr;
     bool capturing = false;          // section timers are off while a graph is being captured
     long long body_launches = 0;     // kernels in one CG graph iteration (for the launch count)
+    long long branch_launches = 0;   // kernels of a captured CG outside its loop
     double setup_ms = 0.0, solve_ms = 0.0;
     Profiler prof;
     DBuf<float> mlp;                 // MLP parameters on the device (learned warm start)
@@ -146,6 +148,8 @@ struct Hierarchy {
 int build_vcycle_ops(Hierarchy& H, cudaStream_t s);
 int apply_vcycle(Hierarchy& H, const double* r, double* z, cudaStream_t s);
 int pcg_solve(Hierarchy& H, const double* b, double* x, double tol, cudaStream_t s, int* iters, double* relres);
+int capture_cg(Hierarchy& H, cudaStream_t s);
+int autotune_vcycle(Hierarchy& H, cudaStream_t s);
 
 }  // namespace sphc
 

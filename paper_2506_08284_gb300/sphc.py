@@ -37,7 +37,7 @@ class sphc_opts(ctypes.Structure):
                 ("vcycle_fp32", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("flexible", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("cg_graph", ctypes.c_int32), ("learned", ctypes.c_int32),
                 ("learned_emin_iters", ctypes.c_int32), ("mlp_params", ctypes.c_void_p),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("autotune", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class sphc_train_opts(ctypes.Structure):
@@ -74,7 +74,8 @@ class sphc_timer(ctypes.Structure):
 EXPORTED = ["sphc_default_opts", "sphc_setup", "sphc_solve", "sphc_vcycle", "sphc_get_stats",
             "sphc_get_level_info", "sphc_export_size", "sphc_export", "sphc_destroy", "sphc_last_error",
             "sphc_get_profile", "sphc_launch_count", "sphc_relres_noalloc", "sphc_default_train_opts",
-            "sphc_mlp_train", "sphc_mlp_predict", "sphc_mlp_gradient", "sphc_export_features"]
+            "sphc_mlp_train", "sphc_mlp_predict", "sphc_mlp_gradient", "sphc_export_features",
+            "sphc_setup_batched", "sphc_solve_batched", "sphc_batch_destroy"]
 
 _lib = None
 
@@ -105,12 +106,16 @@ def load(path: str | None = None):
     lib.sphc_mlp_predict.argtypes = [P, P, I64, P, P]
     lib.sphc_mlp_gradient.argtypes = [P, P, P, I, P, P, P]
     lib.sphc_export_features.argtypes = [P, I, P, P, P]
+    lib.sphc_setup_batched.argtypes = [I, P, P, P, P, ctypes.POINTER(sphc_opts), P, ctypes.POINTER(P)]
+    lib.sphc_solve_batched.argtypes = [P, P, P, I, ctypes.c_double, P, P, P]
+    lib.sphc_batch_destroy.argtypes = [P]
+    lib.sphc_batch_destroy.restype = None
     lib.sphc_launch_count.argtypes = []
     lib.sphc_launch_count.restype = ctypes.c_int64
     lib.sphc_last_error.argtypes = []
     lib.sphc_last_error.restype = ctypes.c_char_p
     for name in EXPORTED:
-        if name not in ("sphc_destroy", "sphc_last_error", "sphc_launch_count"):
+        if name not in ("sphc_destroy", "sphc_last_error", "sphc_launch_count", "sphc_batch_destroy"):
             getattr(lib, name).restype = I
     if path is None:
         _lib = lib
@@ -281,6 +286,49 @@ def mlp_gradient(params, X, y, stream=None):
     _check(load().sphc_mlp_gradient(_ptr(params), _ptr(X), _ptr(y), X.shape[0], _ptr(grad), _ptr(loss),
                                     _stream(stream)))
     return grad, float(loss[0])
+
+
+class Batch:
+    """Independent systems solved together (sphc_setup_batched / sphc_solve_batched)."""
+
+    def __init__(self, ptr, sizes, keep):
+        self._ptr = ctypes.c_void_p(ptr)
+        self.sizes = sizes
+        self._keep = keep
+
+    def __del__(self):
+        self.destroy()
+
+    def destroy(self):
+        if getattr(self, "_ptr", None) and self._ptr.value:
+            load().sphc_batch_destroy(self._ptr)
+            self._ptr = ctypes.c_void_p(0)
+
+    def solve(self, bs, xs, tol=1e-8, nrhs=1, stream=None):
+        """bs, xs: lists (one per system) of nrhs x n_e arrays.  Returns (status, iters, relres) with
+        iters / relres of shape [nsys, nrhs]."""
+        n = len(self.sizes)
+        bp = (ctypes.c_void_p * n)(*[_ptr(b) for b in bs])
+        xp = (ctypes.c_void_p * n)(*[_ptr(x) for x in xs])
+        it = np.zeros((n, nrhs), np.int32)
+        rr = np.zeros((n, nrhs), np.float64)
+        rc = load().sphc_solve_batched(self._ptr, bp, xp, nrhs, tol, _stream(stream), _ptr(it), _ptr(rr))
+        if rc not in (SPHC_OK, -4, -5, -8):
+            _check(rc)
+        return rc, it, rr
+
+
+def setup_batched(systems, opts=None, stream=None) -> Batch:
+    """systems: list of (A, D, coords, sigma_edge) with A, D as for setup()."""
+    n = len(systems)
+    As = (sphc_csr * n)(*[make_csr(*s[0]) for s in systems])
+    Ds = (sphc_csr * n)(*[make_csr(*s[1]) for s in systems])
+    cs = (ctypes.c_void_p * n)(*[_ptr(s[2]) if len(s) > 2 else None for s in systems])
+    ss = (ctypes.c_void_p * n)(*[_ptr(s[3]) if len(s) > 3 else None for s in systems])
+    o = opts if opts is not None else default_opts()
+    out = ctypes.c_void_p()
+    _check(load().sphc_setup_batched(n, As, Ds, cs, ss, ctypes.byref(o), _stream(stream), ctypes.byref(out)))
+    return Batch(out.value, [s[0][0] for s in systems], systems)
 
 
 def launch_count() -> int:

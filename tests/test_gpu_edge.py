@@ -98,3 +98,18 @@ def test_device_resident_inputs():
     h2.solve(meshgen.rhs(1, p.n_edges), x2)
     assert rc == 0
     np.testing.assert_allclose(x.cpu().numpy(), x2, rtol=0, atol=1e-12 * np.abs(x2).max())
+
+
+def test_autotuned_widths_give_the_same_solve():
+    spec = meshgen.MeshSpec(24, jitter=0.2, seed_jitter=9, sigma="lognormal", sigma_in=2.0, seed_sigma=10)
+    p = meshgen.generate(spec)
+    b = meshgen.rhs(3, p.n_edges)
+    res = []
+    for tune in (0, 1):
+        h = gpu_setup(p, autotune=tune)
+        x = np.zeros_like(b)
+        rc, it, rr = h.solve(b, x)
+        assert rc == 0 and rr[0] <= 1.01e-8
+        res.append((it[0], x))
+    assert abs(res[0][0] - res[1][0]) <= 1
+    assert np.linalg.norm(res[0][1] - res[1][1]) <= 1e-6 * np.linalg.norm(res[0][1])
