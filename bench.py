@@ -4,9 +4,10 @@ system per GPU (replicas; no data exchange between ranks).
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload kuhn128] [--impl mine|reference]
 
 One step = sphc_setup (the whole hierarchy: nodal operator, colourings, aggregation, P_n, D_H,
-pattern, least-norm initial guess, energy minimisation, Galerkin operators, coarse factor,
-V-cycle operators) + sphc_solve (FP32 V-cycle inside FP64 CG, x0 = 0, tol 1e-8) +
-sphc_destroy, with the inputs already resident in device memory.  `value` is seconds per
+pattern, least-norm initial guess, learned warm start of P_e, energy minimisation, Galerkin
+operators, coarse factor, V-cycle operators) + sphc_solve (FP32 V-cycle inside FP64 CG, x0 = 0,
+tol 1e-8) + sphc_destroy, with the inputs already resident in device memory.  The plain FP32
+and plain FP64 GPU paths are timed after it on the same GPU and reported under `comparators`.  `value` is seconds per
 system (lower is better); with N ranks it is the slowest rank's time divided by the systems all
 ranks processed.  `e2e` repeats the step through the same C ABI with pinned host buffers, the
 host-to-device input copies and the device-to-host copy of x inside the timed region.
@@ -46,6 +47,7 @@ def parse_args():
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-compare", action="store_true")
     return ap.parse_args()
 
 
@@ -159,6 +161,17 @@ def run_reference(args, rank):
 
 
 # ------------------------------------------------------------------ GPU arm
+def make_opts(pkg, variant, weights, profile):
+    """headline: FP32 V-cycle + learned warm start (one energy-minimisation step after it);
+    fp32_plain: FP32 V-cycle, plain least-norm P0 + one step; fp64_plain: the same in FP64."""
+    if variant == "headline" and weights is not None:
+        return pkg.sphc.default_opts(vcycle_fp32=1, learned=1, learned_emin_iters=1, mlp_params=weights,
+                                     profile=profile)
+    if variant in ("headline", "fp32_plain"):
+        return pkg.sphc.default_opts(vcycle_fp32=1, profile=profile)
+    return pkg.sphc.default_opts(vcycle_fp32=0, profile=profile)
+
+
 def main():
     args = parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -173,6 +186,7 @@ def main():
 
     import meshgen
     import paper_2506_08284_gb300 as pkg
+    from paper_2506_08284_gb300 import learned
 
     torch.cuda.set_device(local)
     dist = None
@@ -182,6 +196,7 @@ def main():
     spec, seed = meshgen.workload(args.workload)
     p = meshgen.generate(spec, nthreads=min(os.cpu_count() or 1, 32))
     b = meshgen.rhs(seed, p.n_edges)
+    weights = learned.load_weights() if os.path.exists(learned.WEIGHTS) else None
     dev = lambda a: torch.from_numpy(a).cuda()
     A = (p.n_edges, p.n_edges, dev(p.A_rowptr), dev(p.A_col), dev(p.A_val))
     D = (p.n_edges, p.n_nodes, dev(p.D_rowptr), dev(p.D_col), dev(p.D_val))
@@ -199,34 +214,51 @@ def main():
         h.destroy()
         return rc, it[0], rr[0], prof, st, info
 
-    opts = pkg.sphc.default_opts(vcycle_fp32=1, profile=1)
-    for _ in range(args.warmup):
-        step(opts, A, D, coords, sig, bd, xd)
-    torch.cuda.synchronize()
-    clk = ClockSampler(local)
-    clk.start()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    launches0 = pkg.sphc.launch_count()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    t0 = time.perf_counter()
-    results = [step(opts, A, D, coords, sig, bd, xd) for _ in range(args.steps)]
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - t0
-    if dist:
-        dist.barrier()
-    launches = pkg.sphc.launch_count() - launches0
-    clocks = clk.stop()
-    ms = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    def timed(opts, steps, warmup, sample_clocks=False):
+        for _ in range(warmup):
+            step(opts, A, D, coords, sig, bd, xd)
+        torch.cuda.synchronize()
+        clk = ClockSampler(local) if sample_clocks else None
+        if clk:
+            clk.start()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        launches0 = pkg.sphc.launch_count()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        t0 = time.perf_counter()
+        res = [step(opts, A, D, coords, sig, bd, xd) for _ in range(steps)]
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        if dist:
+            dist.barrier()
+        launches = pkg.sphc.launch_count() - launches0
+        clocks = clk.stop() if clk else None
+        ms = ev0.elapsed_time(ev1)
+        if dist:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, wall, launches, clocks, res
+
+    # headline: FP32 V-cycle + learned warm start
+    opts = make_opts(pkg, "headline", weights, 1)
+    ms, wall, launches, clocks, results = timed(opts, args.steps, args.warmup, sample_clocks=True)
     sec_per_system = ms / 1e3 / (args.steps * world)
     rc, iters, relres, prof, st, info = results[-1]
+
+    # comparators on the same GPU: plain FP32 and plain FP64 GPU paths (untimed by the driver)
+    comparators = {}
+    if not args.no_compare:
+        for name in ("fp32_plain", "fp64_plain"):
+            cms, _, _, _, cres = timed(make_opts(pkg, name, weights, 0), max(1, min(args.steps, 2)), 1)
+            c_rc, c_it, c_rr, _, c_st, _ = cres[-1]
+            comparators[name] = {"s": cms / 1e3 / (max(1, min(args.steps, 2)) * world), "iters": c_it,
+                                 "relres": c_rr, "status": c_rc, "setup_ms": c_st["setup_ms"],
+                                 "solve_ms": c_st["solve_ms"]}
+        comparators["speedup_vs_fp64_plain"] = comparators["fp64_plain"]["s"] / sec_per_system
 
     # end-to-end: the same call with pinned host buffers (copies inside the timed region)
     e2e = None
@@ -236,7 +268,7 @@ def main():
         Dh = (p.n_edges, p.n_nodes, pin(p.D_rowptr), pin(p.D_col), pin(p.D_val))
         ch, sh, bh = pin(p.coords), pin(p.sigma_edge), pin(b)
         xh = torch.zeros(p.n_edges, dtype=torch.float64).pin_memory()
-        o2 = pkg.sphc.default_opts(vcycle_fp32=1, profile=0)
+        o2 = make_opts(pkg, "headline", weights, 0)
         step(o2, Ah, Dh, ch, sh, bh, xh)
         torch.cuda.synchronize()
         t1 = time.perf_counter()
@@ -258,10 +290,16 @@ def main():
     if name in prof and prof[name]["calls"] > 0:
         t_call = prof[name]["ms"] / prof[name]["calls"] / 1e3
         achieved = prof[name]["bytes_per_call"] / t_call / 1e9
-        roof = {"bound": "hbm", "kernel": "k_sgs_color<float,8> (level-0 forward+backward multicolour SGS sweep)",
+        roof = {"bound": "hbm", "kernel": "k_sell_sgs<float> (level-0 forward+backward multicolour SGS sweep, "
+                                          "SELL-32, one launch per colour and direction)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_kind": f"{peak_kind} HBM copy", "traffic": None,
                 "algorithmic_bytes_per_launch": prof[name]["bytes_per_call"], "ms_per_launch": t_call * 1e3}
+        sp = prof.get("spmv_A_fp64")
+        if sp and sp["calls"] > 0:
+            tsp = sp["ms"] / sp["calls"] / 1e3
+            roof["cg_spmv_fp64"] = {"achieved": sp["bytes_per_call"] / tsp / 1e9,
+                                    "frac": sp["bytes_per_call"] / tsp / 1e9 / peak, "ms_per_launch": tsp * 1e3}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(p.n_edges)
@@ -272,13 +310,15 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64 CG / f32 V-cycle", "data": "synthetic",
             "config": {"workload": f"{args.workload}: {WORKLOAD_TEXT.get(args.workload, '')}",
-                       "solver": "SpHcurlAMG V-cycle (1 pre + 1 post symmetric Hiptmair) in FP64 CG, FP32 V-cycle",
+                       "solver": "SpHcurlAMG V-cycle (1 pre + 1 post symmetric Hiptmair) in FP64 CG, FP32 V-cycle, "
+                                 + ("learned warm start of P_e + 1 energy-minimisation step" if weights is not None
+                                    else "least-norm P0 + 1 energy-minimisation step (no MLP weights found)"),
                        "rhs": 1, "tol": args.tol, "l2": "inputs (A_e 2.8 GB FP64) exceed the 129 MB L2; no flush",
                        "parallelism": f"replicas x{world}"},
             "iters": iters, "relres": relres, "status": rc, "wall_s_per_step": wall / args.steps,
             "setup_ms": st["setup_ms"], "solve_ms": st["solve_ms"], "levels": st["n_levels"],
             "operator_complexity": st["operator_complexity"], "gpu_launches": int(launches),
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "comparators": comparators,
             "profile": {k: {kk: round(vv, 4) if isinstance(vv, float) else vv for kk, vv in v.items()}
                         for k, v in prof.items()},
             "level_edges": [li["n_edges"] for li in info],

@@ -112,6 +112,10 @@ typedef struct {
     double rho, omega_sa;            /* rho(D^-1 A_n) estimate and the prolongator damping */
     int64_t max_pattern_row;         /* largest |N_i| (pattern entries of one P_e row) */
     int64_t max_T_row;               /* largest |T_i| (coarse nodes of one row) */
+    /* V-cycle copies of the smoothers (sliced ELLPACK, 32-lane slices; 0 where there is none):
+     * lanes per row, entries per lane load and stored entries (nonzeros plus padding) */
+    int32_t sell_lpr_edge, sell_ch_edge, sell_lpr_node, sell_ch_node;
+    int64_t sell_stored_edge, sell_stored_node;
 } sphc_level_info;
 
 typedef struct {
@@ -191,8 +195,16 @@ SPHC_API int sphc_export_size(const sphc_handle* h, int level, int what, int64_t
 SPHC_API int sphc_export(const sphc_handle* h, int level, int what, int64_t* rowptr, int32_t* col, double* val,
                 int32_t* ivec, void* stream);
 
-/* Release the handle and every device buffer it owns (NULL is ignored). */
+/* Release the handle and every device buffer it owns (NULL is ignored).  The memory goes back to
+ * the library's memory pool of that device, which keeps it mapped for the next setup. */
 SPHC_API void sphc_destroy(sphc_handle* h);
+
+/* Return the memory the library's pool of `device` holds beyond keep_bytes to the driver
+ * (cudaMemPoolTrimTo).  Memory still owned by live handles is not affected.  Not part of the
+ * paper: the library caches device memory across setups the way a caching allocator does, and
+ * this is how a caller that needs the memory for something else gets it back.  Returns
+ * SPHC_EINVAL for a device without a pool, SPHC_ECUDA if the runtime call fails. */
+SPHC_API int sphc_trim_memory(int device, uint64_t keep_bytes);
 
 /* Copy up to max timers of the handle's profile into out (host memory); *n receives the number
  * of timers.  Synchronises on the recorded events.  Timers accumulate over the handle's life. */

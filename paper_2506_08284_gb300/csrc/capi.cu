@@ -289,7 +289,7 @@ int sphc_vcycle(sphc_handle* h, const double* r, double* z, void* stream) {
         return SPHC_EINVAL;
     }
     cudaStream_t s = (cudaStream_t)stream;
-    SPHC_TRY(apply_vcycle(h->H, r, z, s));
+    SPHC_TRY(apply_vcycle_user(h->H, r, z, s));
     SPHC_CK(cudaStreamSynchronize(s));
     return SPHC_OK;
 }
@@ -338,6 +338,17 @@ int sphc_get_level_info(const sphc_handle* h, int level, sphc_level_info* info) 
         info->max_pattern_row = L.max_np;
         info->max_T_row = L.max_m;
     }
+    const Hierarchy& H = h->H;
+    auto shape = [&](const auto& V) {
+        if (level >= (int)V.size()) return;
+        info->sell_lpr_edge = V[level].A.m.lpr * (V[level].A.m.nslice > 0);
+        info->sell_ch_edge = V[level].A.m.ch * (V[level].A.m.nslice > 0);
+        info->sell_stored_edge = V[level].A.m.stored;
+        info->sell_lpr_node = V[level].An.m.lpr * (V[level].An.m.nslice > 0);
+        info->sell_ch_node = V[level].An.m.ch * (V[level].An.m.nslice > 0);
+        info->sell_stored_node = V[level].An.m.stored;
+    };
+    if (H.opts.vcycle_fp32) shape(H.V32); else shape(H.V64);
     return SPHC_OK;
 }
 
@@ -421,6 +432,24 @@ void sphc_destroy(sphc_handle* h) {
     delete h;
     g_sync_free = false;
     cudaSetDevice(dev);
+}
+
+int sphc_trim_memory(int device, uint64_t keep_bytes) {
+    int dev = 0;
+    SPHC_CK(cudaGetDevice(&dev));
+    if (device != dev) SPHC_CK(cudaSetDevice(device));
+    cudaMemPool_t pool = device_pool();
+    cudaError_t e = pool ? cudaMemPoolTrimTo(pool, (size_t)keep_bytes) : cudaErrorInvalidValue;
+    if (device != dev) cudaSetDevice(dev);
+    if (!pool) {
+        set_error("sphc_trim_memory: no memory pool on device %d", device);
+        return SPHC_EINVAL;
+    }
+    if (e != cudaSuccess) {
+        set_error("sphc_trim_memory: %s", cudaGetErrorString(e));
+        return SPHC_ECUDA;
+    }
+    return SPHC_OK;
 }
 
 int sphc_get_profile(sphc_handle* h, sphc_timer* out, int max, int* n) {
@@ -551,7 +580,7 @@ int sphc_solve_batched(sphc_batch* B, const double* const* b, double* const* x, 
         for (int k = 0; k < n; ++k) {
             Hierarchy& H = B->hs[k]->H;
             int64_t m = H.L[0].A.nr;
-            SPHC_CK(cudaMemcpyAsync(x[k] + (int64_t)r * m, H.x.p, sizeof(double) * m, cudaMemcpyDefault, s));
+            SPHC_CK(cudaMemcpyAsync(x[k] + (int64_t)r * m, H.xo.p, sizeof(double) * m, cudaMemcpyDefault, s));
             SPHC_CK(cudaMemcpyAsync(&hit[2 * k], H.itc.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
             SPHC_CK(cudaMemcpyAsync(&hsc[2 * k], H.scal.p + 5, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
         }

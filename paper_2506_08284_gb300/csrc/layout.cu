@@ -1,0 +1,456 @@
+// V-cycle data layout: each level's edges and nodes are renumbered colour by colour (inside a
+// colour by row length, stably), and the operators the V-cycle applies are copied into that
+// numbering in the V-cycle precision, as sliced ELLPACK (SELL-32) or, where rows pad badly, CSR.
+// The setup works in the caller's numbering; only these copies and the CG vectors use the new one.
+#include "sphc_level.cuh"
+
+namespace sphc {
+
+// ------------------------------------------------------------------ stable counting partition
+static constexpr int PART_BLOCK = 1024;
+static constexpr int PART_MAXK = 256;
+
+__global__ void k_part_count(const int32_t* key, int64_t n, int nkeys, int32_t* table, int64_t nblocks) {
+    __shared__ int32_t cnt[PART_MAXK];
+    for (int c = threadIdx.x; c < nkeys; c += blockDim.x) cnt[c] = 0;
+    __syncthreads();
+    int64_t i = (int64_t)blockIdx.x * PART_BLOCK + threadIdx.x;
+    if (i < n) atomicAdd(&cnt[key[i]], 1);
+    __syncthreads();
+    for (int c = threadIdx.x; c < nkeys; c += blockDim.x) table[(int64_t)c * nblocks + blockIdx.x] = cnt[c];
+}
+// items keep their order inside a key
+__global__ void k_part_place(const int32_t* key, int64_t n, const int64_t* off, int64_t nblocks, int32_t* perm) {
+    __shared__ int32_t wcnt[PART_BLOCK / 32][PART_MAXK];
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int q = threadIdx.x; q < (PART_BLOCK / 32) * PART_MAXK; q += blockDim.x) (&wcnt[0][0])[q] = 0;
+    __syncthreads();
+    int64_t i = (int64_t)blockIdx.x * PART_BLOCK + threadIdx.x;
+    int c = i < n ? key[i] : -1;
+    unsigned m = __match_any_sync(0xffffffffu, c);
+    int rank = __popc(m & ((1u << lane) - 1u));
+    if (c >= 0 && rank == 0) wcnt[w][c] = __popc(m);
+    __syncthreads();
+    if (c >= 0) {
+        int before = 0;
+        for (int q = 0; q < w; ++q) before += wcnt[q][c];
+        perm[off[(int64_t)c * nblocks + blockIdx.x] + before + rank] = (int32_t)i;
+    }
+}
+__global__ void k_key_starts(const int64_t* off, int nkeys, int64_t nblocks, int64_t* ks) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c <= nkeys) ks[c] = off[(int64_t)c * nblocks];
+}
+
+// perm lists the items key by key (0 .. nkeys-1), each key's items in increasing order;
+// kstart[c] is the first position of key c (kstart[nkeys] = n).
+int stable_partition(const int32_t* key, int64_t n, int nkeys, DBuf<int32_t>& perm, std::vector<int64_t>& kstart,
+                     cudaStream_t s) {
+    if (nkeys < 1 || nkeys > PART_MAXK) { set_error("stable_partition: %d keys (1..%d)", nkeys, PART_MAXK); return SPHC_ELIMIT; }
+    SPHC_TRY(perm.alloc(n, s));
+    int64_t nb = (n + PART_BLOCK - 1) / PART_BLOCK;
+    if (nb < 1) nb = 1;
+    DBuf<int32_t> table;
+    DBuf<int64_t> off, ks;
+    SPHC_TRY(table.alloc((int64_t)nkeys * nb, s));
+    SPHC_TRY(off.alloc((int64_t)nkeys * nb + 1, s));
+    SPHC_TRY(ks.alloc(nkeys + 1, s));
+    SPHC_CK(cudaMemsetAsync(table.p, 0, sizeof(int32_t) * nkeys * nb, s));
+    if (n > 0) SPHC_LAUNCH(k_part_count<<<(unsigned)nb, PART_BLOCK, 0, s>>>(key, n, nkeys, table.p, nb));
+    SPHC_TRY(scan_i32_to_i64(table.p, off.p, (int64_t)nkeys * nb, s, nullptr));
+    SPHC_LAUNCH(k_key_starts<<<grid_for(nkeys + 1, 256), 256, 0, s>>>(off.p, nkeys, nb, ks.p));
+    kstart.assign(nkeys + 1, 0);
+    SPHC_CK(cudaMemcpyAsync(kstart.data(), ks.p, sizeof(int64_t) * (nkeys + 1), cudaMemcpyDeviceToHost, s));
+    if (n > 0) SPHC_LAUNCH(k_part_place<<<(unsigned)nb, PART_BLOCK, 0, s>>>(key, n, off.p, nb, perm.p));
+    SPHC_CK(cudaStreamSynchronize(s));
+    SPHC_CK(cudaGetLastError());
+    return SPHC_OK;
+}
+
+// ------------------------------------------------------------------ level order
+__global__ void k_len_key(const int64_t* rp, int64_t n, int32_t* key) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t len = rp[i + 1] - rp[i];
+    key[i] = (int32_t)(len < PART_MAXK - 1 ? len : PART_MAXK - 1);
+}
+__global__ void k_gather_key(const int32_t* color, const int32_t* p1, int64_t n, int32_t* key) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) key[k] = color[p1[k]];
+}
+__global__ void k_compose(const int32_t* p1, const int32_t* p2, int64_t n, int32_t* p, int32_t* ip) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int32_t o = p1[p2[k]];
+    p[k] = o;
+    ip[o] = (int32_t)k;
+}
+
+int level_order(const DCSR& A, const int32_t* color, int ncolor, DBuf<int32_t>& p, DBuf<int32_t>& ip,
+                std::vector<int64_t>& cstart, cudaStream_t s) {
+    int64_t n = A.nr;
+    int64_t maxlen = 0;
+    SPHC_TRY(max_row_length(A.rp.p, n, s, &maxlen));
+    int nk1 = (int)(maxlen + 1 < PART_MAXK ? maxlen + 1 : PART_MAXK);
+    DBuf<int32_t> key, p1, p2;
+    std::vector<int64_t> tmp;
+    SPHC_TRY(key.alloc(n, s));
+    if (n > 0) SPHC_LAUNCH(k_len_key<<<grid_for(n, 256), 256, 0, s>>>(A.rp.p, n, key.p));
+    SPHC_TRY(stable_partition(key.p, n, nk1, p1, tmp, s));
+    if (n > 0) SPHC_LAUNCH(k_gather_key<<<grid_for(n, 256), 256, 0, s>>>(color, p1.p, n, key.p));
+    SPHC_TRY(stable_partition(key.p, n, ncolor, p2, cstart, s));
+    SPHC_TRY(p.alloc(n, s));
+    SPHC_TRY(ip.alloc(n, s));
+    if (n > 0) SPHC_LAUNCH(k_compose<<<grid_for(n, 256), 256, 0, s>>>(p1.p, p2.p, n, p.p, ip.p));
+    SPHC_CK(cudaGetLastError());
+    return SPHC_OK;
+}
+
+// ------------------------------------------------------------------ SELL construction
+static std::vector<int64_t> slice_starts(const std::vector<int64_t>& seg, int rows_per_slice) {
+    std::vector<int64_t> segslice(seg.size(), 0);
+    for (size_t c = 0; c + 1 < seg.size(); ++c)
+        segslice[c + 1] = segslice[c] + (seg[c + 1] - seg[c] + rows_per_slice - 1) / rows_per_slice;
+    return segslice;
+}
+// slice s -> first row: the segment c with segslice[c] <= s < segslice[c+1] starts its slices at seg[c]
+__global__ void k_sell_srow(const int64_t* seg, const int64_t* segslice, int nseg, int64_t nslice, int64_t nr,
+                            int rps, int32_t* srow) {
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s > nslice) return;
+    if (s == nslice) { srow[s] = (int32_t)nr; return; }
+    int lo = 0, hi = nseg - 1;                       // largest c with segslice[c] <= s
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (segslice[mid] <= s) lo = mid; else hi = mid - 1;
+    }
+    int64_t r = seg[lo] + (s - segslice[lo]) * rps;
+    srow[s] = (int32_t)r;
+}
+// longest row of every slice (warp per slice)
+__global__ void k_sell_width(const int64_t* rp, const int32_t* rmap, const int32_t* srow, int64_t nslice, int32_t* w) {
+    int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (s >= nslice) return;
+    int lane = threadIdx.x & 31;
+    int32_t r = srow[s] + lane;
+    int len = 0;
+    if (r < srow[s + 1]) {
+        int64_t i = rmap ? rmap[r] : r;
+        len = (int)(rp[i + 1] - rp[i]);
+    }
+    len = __reduce_max_sync(0xffffffffu, len);
+    if (lane == 0) w[s] = len;
+}
+// stored entries for 1, 2 and 4 entries per load (rows per slice rps, lanes per row lpr)
+__global__ void k_sell_totals(const int32_t* w, int64_t nslice, int rps, int lpr, unsigned long long* tot) {
+    __shared__ unsigned long long t[3];
+    if (threadIdx.x < 3) t[threadIdx.x] = 0;
+    __syncthreads();
+    unsigned long long a = 0, b = 0, c = 0;
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < nslice; s += (int64_t)gridDim.x * blockDim.x) {
+        int64_t x = w[s];
+        a += rps * ((x + lpr - 1) / lpr * lpr);
+        b += rps * ((x + 2 * lpr - 1) / (2 * lpr) * (2 * lpr));
+        c += rps * ((x + 4 * lpr - 1) / (4 * lpr) * (4 * lpr));
+    }
+    atomicAdd(&t[0], a);
+    atomicAdd(&t[1], b);
+    atomicAdd(&t[2], c);
+    __syncthreads();
+    if (threadIdx.x < 3) atomicAdd(&tot[threadIdx.x], t[threadIdx.x]);
+}
+__global__ void k_sell_count(const int32_t* w, int64_t nslice, int rps, int q, int64_t* cnt) {
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < nslice) cnt[s] = (int64_t)rps * ((w[s] + q - 1) / q) * q;
+}
+// warp per slice, lane q < R per row: copy the row into its slots, pad the rest
+template <typename T>
+__global__ void k_sell_fill(const int64_t* rp, const int32_t* ci, const double* v, const int32_t* rmap,
+                            const int32_t* cmap, const int32_t* srow, const int64_t* soff, int64_t nslice, int ch,
+                            int lpr, int32_t* sci, T* sv, T* dinv) {
+    int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (s >= nslice) return;
+    int q = threadIdx.x & 31;
+    int rps = SELL_C / lpr;
+    if (q >= rps) return;
+    int32_t r = srow[s] + q;
+    int64_t o = soff[s];
+    int64_t W = (soff[s + 1] - o) / rps;
+    int64_t b = 0, len = 0, i = -1;
+    if (r < srow[s + 1]) {
+        i = rmap ? rmap[r] : r;
+        b = rp[i];
+        len = rp[i + 1] - b;
+    }
+    int32_t pad = 0;
+    for (int64_t j = 0; j < W; ++j) {
+        int64_t k = j / ch;
+        int64_t at = o + ((k / lpr) * SELL_C + q * lpr + k % lpr) * ch + j % ch;
+        if (j < len) {
+            int32_t c0 = ci[b + j];
+            int32_t c = cmap ? cmap[c0] : c0;
+            sci[at] = c;
+            sv[at] = (T)v[b + j];
+            pad = c;
+            if (dinv && c0 == i) dinv[r] = (T)(1.0 / v[b + j]);
+        } else {
+            sci[at] = pad;
+            sv[at] = (T)0;
+        }
+    }
+}
+
+// Lanes per row: the fewest that leave at most 20 entries (mean row length) to a lane, doubled
+// (down to 4 entries a lane) while a colour would occupy fewer than 16 warps per SM - small
+// coarse levels need the extra parallelism more than long loops.
+int sell_lpr_for(const DCSR& A, int ncolor) {
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm <= 0) nsm = 1;
+    double avg = A.nr > 0 ? (double)A.nnz / (double)A.nr : 0.0;
+    double rows_per_colour = (double)A.nr / (ncolor > 0 ? ncolor : 1);
+    int lpr = 1;
+    while (lpr < SELL_C && avg / lpr > 20.0) lpr *= 2;
+    while (lpr < SELL_C && avg / (2 * lpr) >= 4.0 && rows_per_colour * lpr / SELL_C < 16.0 * nsm) lpr *= 2;
+    return lpr;
+}
+
+// Entries per lane load: the widest of 4, 2, 1 whose padding stays within 10% of the
+// one-entry layout.
+int sell_pick_ch(const DCSR& A, const int32_t* rmap, const std::vector<int64_t>& seg, int lpr, cudaStream_t s, int* ch) {
+    *ch = 4;
+    int rps = SELL_C / lpr;
+    std::vector<int64_t> segslice = slice_starts(seg, rps);
+    int64_t nslice = segslice.back();
+    if (nslice == 0) return SPHC_OK;
+    DBuf<int64_t> dseg, dss;
+    DBuf<int32_t> srow, w;
+    DBuf<unsigned long long> tot;
+    SPHC_TRY(dseg.alloc(seg.size(), s));
+    SPHC_TRY(dss.alloc(seg.size(), s));
+    SPHC_TRY(srow.alloc(nslice + 1, s));
+    SPHC_TRY(w.alloc(nslice, s));
+    SPHC_TRY(tot.alloc(3, s));
+    SPHC_CK(cudaMemcpyAsync(dseg.p, seg.data(), sizeof(int64_t) * seg.size(), cudaMemcpyHostToDevice, s));
+    SPHC_CK(cudaMemcpyAsync(dss.p, segslice.data(), sizeof(int64_t) * seg.size(), cudaMemcpyHostToDevice, s));
+    SPHC_CK(cudaMemsetAsync(tot.p, 0, 3 * sizeof(unsigned long long), s));
+    SPHC_LAUNCH(k_sell_srow<<<grid_for(nslice + 1, 256), 256, 0, s>>>(dseg.p, dss.p, (int)seg.size() - 1, nslice, A.nr, rps, srow.p));
+    SPHC_LAUNCH(k_sell_width<<<grid_for(nslice * 32, 256), 256, 0, s>>>(A.rp.p, rmap, srow.p, nslice, w.p));
+    SPHC_LAUNCH(k_sell_totals<<<256, 256, 0, s>>>(w.p, nslice, rps, lpr, tot.p));
+    unsigned long long h[3];
+    SPHC_CK(cudaMemcpyAsync(h, tot.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+    SPHC_CK(cudaStreamSynchronize(s));
+    if ((double)h[2] <= 1.1 * (double)h[0]) *ch = 4;
+    else if ((double)h[1] <= 1.1 * (double)h[0]) *ch = 2;
+    else *ch = 1;
+    return SPHC_OK;
+}
+
+// S = rows rmap[0..] of A (identity if null) with columns renumbered by cmap (identity if null);
+// seg: row boundaries no slice crosses (seg[0] = 0, seg.back() = rows); segslice: first slice of
+// every segment.  dinv (if not null) receives 1 / diagonal in the new row numbering.
+template <typename T>
+int build_sell(const DCSR& A, const int32_t* rmap, const int32_t* cmap, const std::vector<int64_t>& seg, int ch,
+               int lpr, Sell<T>& S, T* dinv, std::vector<int64_t>* segslice_out, cudaStream_t s) {
+    if (ch != 1 && ch != 2 && ch != 4) { set_error("SELL: %d entries per load", ch); return SPHC_EINVAL; }
+    if (lpr < 1 || lpr > SELL_C || (lpr & (lpr - 1))) { set_error("SELL: %d lanes per row", lpr); return SPHC_EINVAL; }
+    S = Sell<T>();
+    S.nr = A.nr;
+    S.nc = A.nc;
+    S.nnz = A.nnz;
+    S.ch = ch;
+    S.lpr = lpr;
+    int rps = SELL_C / lpr;
+    std::vector<int64_t> segslice = slice_starts(seg, rps);
+    S.nslice = segslice.back();
+    if (segslice_out) *segslice_out = segslice;
+    SPHC_TRY(S.soff.alloc(S.nslice + 1, s));
+    SPHC_TRY(S.srow.alloc(S.nslice + 1, s));
+    if (S.nslice == 0) {
+        SPHC_CK(cudaMemsetAsync(S.soff.p, 0, sizeof(int64_t), s));
+        int32_t z = (int32_t)A.nr;
+        SPHC_CK(cudaMemcpyAsync(S.srow.p, &z, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        SPHC_CK(cudaStreamSynchronize(s));
+        return SPHC_OK;
+    }
+    DBuf<int64_t> dseg, dss, cnt;
+    DBuf<int32_t> w;
+    SPHC_TRY(dseg.alloc(seg.size(), s));
+    SPHC_TRY(dss.alloc(seg.size(), s));
+    SPHC_TRY(w.alloc(S.nslice, s));
+    SPHC_TRY(cnt.alloc(S.nslice, s));
+    SPHC_CK(cudaMemcpyAsync(dseg.p, seg.data(), sizeof(int64_t) * seg.size(), cudaMemcpyHostToDevice, s));
+    SPHC_CK(cudaMemcpyAsync(dss.p, segslice.data(), sizeof(int64_t) * seg.size(), cudaMemcpyHostToDevice, s));
+    SPHC_LAUNCH(k_sell_srow<<<grid_for(S.nslice + 1, 256), 256, 0, s>>>(dseg.p, dss.p, (int)seg.size() - 1, S.nslice, A.nr, rps, S.srow.p));
+    SPHC_LAUNCH(k_sell_width<<<grid_for(S.nslice * 32, 256), 256, 0, s>>>(A.rp.p, rmap, S.srow.p, S.nslice, w.p));
+    SPHC_LAUNCH(k_sell_count<<<grid_for(S.nslice, 256), 256, 0, s>>>(w.p, S.nslice, rps, lpr * ch, cnt.p));
+    SPHC_TRY(exclusive_scan_i64(cnt.p, S.soff.p, S.nslice, s, &S.stored));
+    SPHC_TRY(S.ci.alloc(S.stored, s));
+    SPHC_TRY(S.v.alloc(S.stored, s));
+    SPHC_LAUNCH(k_sell_fill<T><<<grid_for(S.nslice * 32, 256), 256, 0, s>>>(A.rp.p, A.ci.p, A.v.p, rmap, cmap, S.srow.p,
+                                                                         S.soff.p, S.nslice, ch, lpr, S.ci.p, S.v.p, dinv));
+    SPHC_CK(cudaStreamSynchronize(s));      // the host copies of seg/segslice above must outlive the copies
+    SPHC_CK(cudaGetLastError());
+    return SPHC_OK;
+}
+
+// ------------------------------------------------------------------ permuted CSR
+__global__ void k_perm_len(const int64_t* rp, const int32_t* rmap, int64_t n, int64_t* len) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int64_t i = rmap ? rmap[k] : k;
+    len[k] = rp[i + 1] - rp[i];
+}
+__global__ void k_rp_narrow32(const int64_t* a, int32_t* b, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (int32_t)a[i];
+}
+template <typename T>
+__global__ void k_perm_fill(const int64_t* rp, const int32_t* ci, const double* v, const int32_t* rmap,
+                            const int32_t* cmap, int64_t n, const int32_t* nrp, int32_t* nci, T* nv) {
+    int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (k >= n) return;
+    int64_t i = rmap ? rmap[k] : k;
+    int64_t b = rp[i], len = rp[i + 1] - b;
+    int32_t o = nrp[k];
+    for (int64_t q = lane; q < len; q += 32) {
+        int32_t c = ci[b + q];
+        nci[o + q] = cmap ? cmap[c] : c;
+        nv[o + q] = (T)v[b + q];
+    }
+}
+template <typename T>
+int build_csr_perm(const DCSR& A, const int32_t* rmap, const int32_t* cmap, VCSR<T>& B, cudaStream_t s) {
+    if (A.nnz >= (1LL << 31)) { set_error("operator with %lld nonzeros exceeds int32 row pointers", (long long)A.nnz); return SPHC_ELIMIT; }
+    B = VCSR<T>();
+    B.nr = A.nr; B.nc = A.nc; B.nnz = A.nnz;
+    DBuf<int64_t> len, rp64;
+    SPHC_TRY(len.alloc(A.nr + 1, s));
+    SPHC_TRY(rp64.alloc(A.nr + 1, s));
+    if (A.nr > 0) SPHC_LAUNCH(k_perm_len<<<grid_for(A.nr, 256), 256, 0, s>>>(A.rp.p, rmap, A.nr, len.p));
+    SPHC_TRY(exclusive_scan_i64(len.p, rp64.p, A.nr, s, nullptr));
+    SPHC_TRY(B.rp.alloc(A.nr + 1, s));
+    SPHC_LAUNCH(k_rp_narrow32<<<grid_for(A.nr + 1, 256), 256, 0, s>>>(rp64.p, B.rp.p, A.nr + 1));
+    SPHC_TRY(B.ci.alloc(A.nnz, s));
+    SPHC_TRY(B.v.alloc(A.nnz, s));
+    if (A.nr > 0)
+        SPHC_LAUNCH(k_perm_fill<T><<<grid_for(A.nr * 32, 256), 256, 0, s>>>(A.rp.p, A.ci.p, A.v.p, rmap, cmap, A.nr,
+                                                                         B.rp.p, B.ci.p, B.v.p));
+    SPHC_CK(cudaGetLastError());
+    return SPHC_OK;
+}
+
+// SELL when the slices pad to at most 1.3 x the nonzeros, CSR otherwise
+template <typename T>
+int build_xop(const DCSR& A, const int32_t* rmap, const int32_t* cmap, XOp<T>& X, cudaStream_t s) {
+    X = XOp<T>();
+    X.nr = A.nr; X.nc = A.nc; X.nnz = A.nnz;
+    std::vector<int64_t> seg{0, A.nr};
+    int ch = 4, lpr = sell_lpr_for(A, 1);
+    SPHC_TRY(sell_pick_ch(A, rmap, seg, lpr, s, &ch));
+    SPHC_TRY(build_sell<T>(A, rmap, cmap, seg, ch, lpr, X.s, nullptr, nullptr, s));
+    if ((double)X.s.stored <= 1.3 * (double)A.nnz) {
+        X.sell = true;
+        return SPHC_OK;
+    }
+    X.s = Sell<T>();
+    return build_csr_perm<T>(A, rmap, cmap, X.c, s);
+}
+
+template <typename T>
+int build_smooth(const DCSR& A, const int32_t* rmap, const int32_t* cmap, const std::vector<int64_t>& cstart, int ch,
+                 int lpr, SmoothOp<T>& op, cudaStream_t s) {
+    op.n = A.nr;
+    op.nnz = A.nnz;
+    op.ncolor = (int)cstart.size() - 1;
+    op.dinv = DBuf<T>();
+    SPHC_TRY(op.dinv.alloc(A.nr, s));
+    SPHC_TRY(op.dinv.zero(s));
+    if (lpr <= 0) lpr = sell_lpr_for(A, (int)cstart.size() - 1);
+    if (ch <= 0) SPHC_TRY(sell_pick_ch(A, rmap, cstart, lpr, s, &ch));
+    SPHC_TRY(build_sell<T>(A, rmap, cmap, cstart, ch, lpr, op.m, op.dinv.p, &op.cslice, s));
+    op.cslice_dev = DBuf<int64_t>();
+    SPHC_TRY(op.cslice_dev.alloc(op.cslice.size(), s));
+    SPHC_CK(cudaMemcpyAsync(op.cslice_dev.p, op.cslice.data(), sizeof(int64_t) * op.cslice.size(), cudaMemcpyHostToDevice, s));
+    SPHC_CK(cudaStreamSynchronize(s));
+    return SPHC_OK;
+}
+
+template int build_sell<float>(const DCSR&, const int32_t*, const int32_t*, const std::vector<int64_t>&, int, int,
+                               Sell<float>&, float*, std::vector<int64_t>*, cudaStream_t);
+template int build_sell<double>(const DCSR&, const int32_t*, const int32_t*, const std::vector<int64_t>&, int, int,
+                                Sell<double>&, double*, std::vector<int64_t>*, cudaStream_t);
+template int build_csr_perm<float>(const DCSR&, const int32_t*, const int32_t*, VCSR<float>&, cudaStream_t);
+template int build_csr_perm<double>(const DCSR&, const int32_t*, const int32_t*, VCSR<double>&, cudaStream_t);
+template int build_xop<float>(const DCSR&, const int32_t*, const int32_t*, XOp<float>&, cudaStream_t);
+template int build_xop<double>(const DCSR&, const int32_t*, const int32_t*, XOp<double>&, cudaStream_t);
+template int build_smooth<float>(const DCSR&, const int32_t*, const int32_t*, const std::vector<int64_t>&, int, int,
+                                 SmoothOp<float>&, cudaStream_t);
+template int build_smooth<double>(const DCSR&, const int32_t*, const int32_t*, const std::vector<int64_t>&, int, int,
+                                  SmoothOp<double>&, cudaStream_t);
+
+// ------------------------------------------------------------------ discrete gradient encodings
+// per edge (new numbering): (node with coefficient -1, node with +1) in the new node numbering
+__global__ void k_d_pairs_perm(const int64_t* rp, const int32_t* ci, const double* v, const int32_t* pe,
+                               const int32_t* in, int64_t ne, int2* D) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= ne) return;
+    int64_t e = pe ? pe[k] : k;
+    int2 d = make_int2(-1, -1);
+    for (int64_t q = rp[e]; q < rp[e + 1]; ++q) {
+        int32_t c = in ? in[ci[q]] : ci[q];
+        if (v[q] < 0) d.x = c; else d.y = c;
+    }
+    D[k] = d;
+}
+int build_d_pairs(const DCSR& D, const int32_t* pe, const int32_t* in, DBuf<int2>& out, cudaStream_t s) {
+    SPHC_TRY(out.alloc(D.nr, s));
+    if (D.nr > 0) SPHC_LAUNCH(k_d_pairs_perm<<<grid_for(D.nr, 256), 256, 0, s>>>(D.rp.p, D.ci.p, D.v.p, pe, in, D.nr, out.p));
+    SPHC_CK(cudaGetLastError());
+    return SPHC_OK;
+}
+__global__ void k_dt_enc(const int32_t* ci, const float* v, int64_t nnz, int32_t* enc) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < nnz) enc[q] = (ci[q] << 1) | (v[q] < 0.f ? 1 : 0);
+}
+// D^T per node (new numbering): incident edges (new numbering) as (edge << 1) | (coef < 0)
+int build_dt_enc(const DCSR& Dt, const int32_t* pn, const int32_t* ie, DBuf<int32_t>& rp, DBuf<int32_t>& enc,
+                 cudaStream_t s) {
+    VCSR<float> B;
+    SPHC_TRY(build_csr_perm<float>(Dt, pn, ie, B, s));
+    rp = std::move(B.rp);
+    SPHC_TRY(enc.alloc(B.nnz, s));
+    if (B.nnz > 0) SPHC_LAUNCH(k_dt_enc<<<grid_for(B.nnz, 256), 256, 0, s>>>(B.ci.p, B.v.p, B.nnz, enc.p));
+    SPHC_CK(cudaGetLastError());
+    return SPHC_OK;
+}
+
+// ------------------------------------------------------------------ vector renumbering
+__global__ void k_gather64(const double* src, const int32_t* p, int64_t n, double* dst) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) dst[k] = src[p[k]];
+}
+__global__ void k_scatter64(const double* src, const int32_t* p, int64_t n, double* dst) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) dst[p[k]] = src[k];
+}
+// dst[k] = src[p[k]] (p null: copy)
+int gather64(const double* src, const int32_t* p, int64_t n, double* dst, cudaStream_t s) {
+    if (n <= 0) return SPHC_OK;
+    if (!p) SPHC_CK(cudaMemcpyAsync(dst, src, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    else SPHC_LAUNCH(k_gather64<<<grid_for(n, 256), 256, 0, s>>>(src, p, n, dst));
+    SPHC_CK(cudaGetLastError());
+    return SPHC_OK;
+}
+// dst[p[k]] = src[k] (p null: copy)
+int scatter64(const double* src, const int32_t* p, int64_t n, double* dst, cudaStream_t s) {
+    if (n <= 0) return SPHC_OK;
+    if (!p) SPHC_CK(cudaMemcpyAsync(dst, src, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    else SPHC_LAUNCH(k_scatter64<<<grid_for(n, 256), 256, 0, s>>>(src, p, n, dst));
+    SPHC_CK(cudaGetLastError());
+    return SPHC_OK;
+}
+
+}  // namespace sphc

@@ -12,6 +12,7 @@
 
 #include <cuda_bf16.h>
 
+#include "features.cuh"
 #include "sphc_level.cuh"
 
 using namespace sphc;
@@ -69,8 +70,12 @@ __device__ inline void load_b(uint32_t b[2], const __nv_bfloat16* Mt, int ld, in
     b[1] = ld_pair(Mt + (n0 + g) * ld + k0 + 8 + 2 * t);
 }
 
+// FUSED: the features of tile row r (pattern entry base + r, in fine row rowof[base + r]) are
+// computed in place from the level's operators instead of being read from X.
+template <bool FUSED>
 __global__ void __launch_bounds__(INF_WARPS * 32)
-k_mlp_infer(const float* __restrict__ params, const float* __restrict__ X, int64_t m, float* __restrict__ out) {
+k_mlp_infer(const float* __restrict__ params, const float* __restrict__ X, int64_t m, FeatArgs g,
+            const int32_t* __restrict__ rowof, float* __restrict__ out) {
     extern __shared__ unsigned char smem_raw[];
     InferSmem& S = *(InferSmem*)smem_raw;
     int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -96,11 +101,24 @@ k_mlp_infer(const float* __restrict__ params, const float* __restrict__ X, int64
     __syncthreads();
     for (int64_t base = (int64_t)blockIdx.x * TILE_M; base < m; base += (int64_t)gridDim.x * TILE_M) {
         // normalised features of the tile (rows past m are zero)
-        for (int q = tid; q < TILE_M * NF; q += blockDim.x) {
-            int r = q / NF, c = q % NF;
-            int64_t row = base + r;
-            float v = row < m ? (X[row * NF + c] - S.mu[c]) * S.isd[c] : 0.f;
-            S.x[r * XS + c] = __float2bfloat16(v);
+        if (FUSED) {
+            if (tid < TILE_M) {
+                int64_t row = base + tid;
+                float f[NF];
+                if (row < m) entry_features(g, rowof[row], row, f);
+                for (int c = 0; c < NF; c += 2) {
+                    float v0 = row < m ? (f[c] - S.mu[c]) * S.isd[c] : 0.f;
+                    float v1 = row < m ? (f[c + 1] - S.mu[c + 1]) * S.isd[c + 1] : 0.f;
+                    *(uint32_t*)(S.x + tid * XS + c) = pack_bf16(__float2bfloat16(v0), __float2bfloat16(v1));
+                }
+            }
+        } else {
+            for (int q = tid; q < TILE_M * NF; q += blockDim.x) {
+                int r = q / NF, c = q % NF;
+                int64_t row = base + r;
+                float v = row < m ? (X[row * NF + c] - S.mu[c]) * S.isd[c] : 0.f;
+                S.x[r * XS + c] = __float2bfloat16(v);
+            }
         }
         __syncthreads();
         int r0 = 16 * w;
@@ -151,13 +169,42 @@ k_mlp_infer(const float* __restrict__ params, const float* __restrict__ X, int64
     }
 }
 
+static int infer_grid(int64_t m) {
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm <= 0) nsm = 1;
+    int64_t tiles = (m + TILE_M - 1) / TILE_M;
+    int64_t cap = (int64_t)nsm * 2;                   // two 92 KB blocks fit one SM
+    return (int)(tiles < cap ? tiles : cap);
+}
+
 int mlp_predict(const float* params_dev, const float* X, int64_t m, float* out, cudaStream_t s) {
     if (m <= 0) return SPHC_OK;
     size_t sm = sizeof(InferSmem);
-    SPHC_CK(cudaFuncSetAttribute(k_mlp_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    int64_t tiles = (m + TILE_M - 1) / TILE_M;
-    int grid = (int)(tiles < 152 * 8 ? tiles : 152 * 8);
-    SPHC_LAUNCH(k_mlp_infer<<<grid, INF_WARPS * 32, sm, s>>>(params_dev, X, m, out));
+    SPHC_CK(cudaFuncSetAttribute(k_mlp_infer<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    SPHC_LAUNCH(k_mlp_infer<false><<<infer_grid(m), INF_WARPS * 32, sm, s>>>(params_dev, X, m, FeatArgs(), nullptr, out));
+    SPHC_CK(cudaGetLastError());
+    return SPHC_OK;
+}
+
+// row of every pattern entry (warp per row)
+__global__ void k_row_of(const int64_t* nrp, int64_t ne, int32_t* rowof) {
+    int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (i >= ne) return;
+    for (int64_t q = nrp[i] + lane; q < nrp[i + 1]; q += 32) rowof[q] = (int32_t)i;
+}
+
+int mlp_predict_level(const float* params_dev, const FeatArgs& g, float* out, cudaStream_t s) {
+    int64_t m = g.nnzN;
+    if (m <= 0) return SPHC_OK;
+    DBuf<int32_t> rowof;
+    SPHC_TRY(rowof.alloc(m, s));
+    SPHC_LAUNCH(k_row_of<<<grid_for(g.ne * 32, 256), 256, 0, s>>>(g.nrp, g.ne, rowof.p));
+    size_t sm = sizeof(InferSmem);
+    SPHC_CK(cudaFuncSetAttribute(k_mlp_infer<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    SPHC_LAUNCH(k_mlp_infer<true><<<infer_grid(m), INF_WARPS * 32, sm, s>>>(params_dev, nullptr, m, g, rowof.p, out));
     SPHC_CK(cudaGetLastError());
     return SPHC_OK;
 }

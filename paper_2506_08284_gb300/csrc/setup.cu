@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 
+#include "features.cuh"
 #include "sphc_level.cuh"
 
 namespace sphc {
@@ -702,26 +703,35 @@ k_emin(int64_t ne, const int64_t* arp, const int32_t* aci, const double* av, con
     int k = local_setup(S, i, trp, tci, tv, nrp, nci, hrp, hci, hv, &m, &np);
     if (np == 0) return;
     if (k < 0) { if (lane == 0) atomicAdd(fail, 1); return; }
-    // masked product (A P)_{i, N_i}: each lane owns pattern entries and searches every P row f of
-    // A's row i for its column (one FMA per match, no atomics)
+    // masked product (A P)_{i, N_i}: a group of L lanes owns a pattern entry (L as large as the
+    // row allows, so the whole warp works on short rows); its lanes split A's row i and search
+    // each P row f for the entry's column (one FMA per match, no atomics), then add up.
     int64_t a0 = arp[i], a1 = arp[i + 1];
     double aii = 1.0;
     for (int64_t ka = a0; ka < a1; ++ka)
         if (aci[ka] == i) aii = av[ka];
     double inv_aii = 1.0 / aii;
-    for (int t = lane; t < np; t += 32) {
-        int32_t j = S.N[t];
+    int L = 1;
+    while (L < 32 && np * (2 * L) <= 32) L *= 2;
+    int G = 32 / L, grp = lane / L, sub = lane & (L - 1);
+    int trips = (np + G - 1) / G;
+    for (int it = 0; it < trips; ++it) {
+        int t = grp + it * G;
         double acc = 0.0;
-        for (int64_t ka = a0; ka < a1; ++ka) {
-            int32_t f = aci[ka];
-            int64_t lo = nrp[f], hi = nrp[f + 1] - 1;
-            while (lo < hi) {
-                int64_t mid = (lo + hi) >> 1;
-                if (nci[mid] < j) lo = mid + 1; else hi = mid;
+        if (t < np) {
+            int32_t j = S.N[t];
+            for (int64_t ka = a0 + sub; ka < a1; ka += L) {
+                int32_t f = aci[ka];
+                int64_t lo = nrp[f], hi = nrp[f + 1] - 1;
+                while (lo < hi) {
+                    int64_t mid = (lo + hi) >> 1;
+                    if (nci[mid] < j) lo = mid + 1; else hi = mid;
+                }
+                if (lo <= hi && nci[lo] == j) acc += av[ka] * P[lo];
             }
-            if (lo <= hi && nci[lo] == j) acc += av[ka] * P[lo];
         }
-        S.w[t] = acc * inv_aii;
+        for (int d = L >> 1; d > 0; d >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, d);
+        if (t < np && sub == 0) S.w[t] = acc * inv_aii;
     }
     __syncwarp();
     // projection onto null(G~^T): dp = w - G~ (G~^T G~)^-1 G~^T w
@@ -780,95 +790,21 @@ __global__ void k_centroids(const int64_t* mptr, const int32_t* members, int64_t
     for (int a = 0; a < 3; ++a) Xc[3 * U + a] = c[a] * inv;
 }
 
-__device__ inline double row_lookup(const int64_t* rp, const int32_t* ci, const double* v, int64_t r, int32_t col) {
-    if (r < 0) return 0.0;
-    int64_t lo = rp[r], hi = rp[r + 1] - 1;
-    while (lo < hi) {
-        int64_t mid = (lo + hi) >> 1;
-        if (ci[mid] < col) lo = mid + 1; else hi = mid;
-    }
-    return (lo <= hi && ci[lo] == col) ? v[lo] : 0.0;
-}
-
 // Features of every pattern entry (i, j) of a level (SPHC_MLP_NFEAT floats each, see sphc.h).
-// One thread per pattern entry; the row of an entry is found by binary search in nrp.
-__global__ void k_features(int64_t ne, int64_t nnzN, int lev, const int64_t* drp, const int32_t* dci, const double* dv,
-                           const int64_t* trp, const int32_t* tci, const double* tv, const int64_t* nrp,
-                           const int32_t* nci, const double* p0, const int64_t* hrp, const int32_t* hci,
-                           const double* hv, const int64_t* prp, const int32_t* pci, const double* pv,
-                           const int64_t* arp, const int32_t* aci, const double* av, const double* X,
-                           const double* Xc, const double* sig, float* F) {
+// One thread per pattern entry; the row of an entry is found by binary search in the pattern's
+// row pointers.  (The setup itself uses the fused feature + inference kernel of mlp.cu.)
+__global__ void k_features(FeatArgs g, float* F) {
     int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= nnzN) return;
-    int64_t lo = 0, hi = ne - 1;                 // row i: nrp[i] <= q < nrp[i+1]
+    if (q >= g.nnzN) return;
+    int64_t lo = 0, hi = g.ne - 1;                 // row i: nrp[i] <= q < nrp[i+1]
     while (lo < hi) {
         int64_t mid = (lo + hi + 1) >> 1;
-        if (nrp[mid] <= q) lo = mid; else hi = mid - 1;
+        if (g.nrp[mid] <= q) lo = mid; else hi = mid - 1;
     }
-    int64_t i = lo;
     float f[SPHC_MLP_NFEAT];
-    for (int a = 0; a < SPHC_MLP_NFEAT; ++a) f[a] = 0.f;
-    // fine edge ends (-1 tail u, +1 head v)
-    int64_t u = -1, v = -1;
-    for (int64_t k = drp[i]; k < drp[i + 1]; ++k) { if (dv[k] < 0) u = dci[k]; else v = dci[k]; }
-    float xu[3] = {0, 0, 0}, xv[3] = {0, 0, 0}, t[3] = {0, 0, 0};
-    bool two = u >= 0 && v >= 0;
-    if (u >= 0) for (int a = 0; a < 3; ++a) xu[a] = (float)X[3 * u + a];
-    if (v >= 0) for (int a = 0; a < 3; ++a) xv[a] = (float)X[3 * v + a];
-    float h = 1.f;
-    if (two) {
-        for (int a = 0; a < 3; ++a) t[a] = xv[a] - xu[a];
-        h = sqrtf(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
-        if (!(h > 0.f)) h = 1.f;
-    }
-    float ih = 1.f / h;
-    // coarse edge ends (-1 a, +1 b)
-    int32_t j = nci[q];
-    int32_t ja = -1, jb = -1;
-    for (int64_t k = hrp[j]; k < hrp[j + 1]; ++k) { if (hv[k] < 0) ja = hci[k]; else jb = hci[k]; }
-    float xa[3] = {0, 0, 0}, xb[3] = {0, 0, 0}, T[3] = {0, 0, 0};
-    if (ja >= 0) for (int a = 0; a < 3; ++a) xa[a] = (float)Xc[3 * (int64_t)ja + a];
-    if (jb >= 0) for (int a = 0; a < 3; ++a) xb[a] = (float)Xc[3 * (int64_t)jb + a];
-    bool ctwo = ja >= 0 && jb >= 0;
-    if (ctwo) for (int a = 0; a < 3; ++a) T[a] = xb[a] - xa[a];
-    float Tn = sqrtf(T[0] * T[0] + T[1] * T[1] + T[2] * T[2]);
-    float dot = t[0] * T[0] + t[1] * T[1] + t[2] * T[2];
-    f[0] = two ? 1.f : 0.f;
-    for (int a = 0; a < 3; ++a) f[1 + a] = t[a] * ih;
-    for (int a = 0; a < 3; ++a) f[4 + a] = two ? T[a] * ih : 0.f;
-    f[7] = two ? Tn * ih : 0.f;
-    f[8] = (two && Tn > 0.f) ? dot / (h * Tn) : 0.f;
-    f[9] = (two && Tn > 0.f) ? dot / (Tn * Tn) : 0.f;
-    f[10] = ctwo ? 0.f : 1.f;
-    f[11] = (float)(nrp[i + 1] - nrp[i]) / 32.f;
-    f[12] = (float)(trp[i + 1] - trp[i]) / 16.f;
-    f[13] = ja >= 0 ? (float)row_lookup(trp, tci, tv, i, ja) : 0.f;
-    f[14] = jb >= 0 ? (float)row_lookup(trp, tci, tv, i, jb) : 0.f;
-    f[15] = ja >= 0 ? (float)row_lookup(prp, pci, pv, u, ja) : 0.f;
-    f[16] = jb >= 0 ? (float)row_lookup(prp, pci, pv, u, jb) : 0.f;
-    f[17] = ja >= 0 ? (float)row_lookup(prp, pci, pv, v, ja) : 0.f;
-    f[18] = jb >= 0 ? (float)row_lookup(prp, pci, pv, v, jb) : 0.f;
-    f[19] = (float)p0[q];
-    double aii = 0.0, l1 = 0.0;
-    for (int64_t k = arp[i]; k < arp[i + 1]; ++k) {
-        double a = av[k];
-        l1 += fabs(a);
-        if (aci[k] == i) aii = a;
-    }
-    f[20] = l1 > 0.0 ? (float)(aii / l1) : 0.f;
-    f[21] = sig ? (float)(log10(fmax(sig[i], 1e-30)) / 6.0) : 0.f;
-    f[22] = (float)lev / 8.f;
-    // midpoint offset of the coarse edge from the fine edge, in fine-edge lengths
-    if (two) {
-        float mi[3], mj[3];
-        for (int a = 0; a < 3; ++a) {
-            mi[a] = 0.5f * (xu[a] + xv[a]);
-            mj[a] = ctwo ? 0.5f * (xa[a] + xb[a]) : (ja >= 0 ? xa[a] : xb[a]);
-            f[23 + a] = (mj[a] - mi[a]) * ih;
-        }
-    }
+    entry_features(g, lo, q, f);
     float* out = F + q * SPHC_MLP_NFEAT;
-    for (int a = 0; a < SPHC_MLP_NFEAT; ++a) out[a] = f[a];
+    for (int c = 0; c < SPHC_MLP_NFEAT; ++c) out[c] = f[c];
 }
 
 int level_features(const Level& L, const DBuf<double>& Xc, int lev, float* F, cudaStream_t s) {
@@ -876,12 +812,8 @@ int level_features(const Level& L, const DBuf<double>& Xc, int lev, float* F, cu
         set_error("features need node coordinates (pass coords to sphc_setup)");
         return SPHC_EINVAL;
     }
-    int64_t nnzN = L.P0.nnz, ne = L.A.nr;
-    if (nnzN > 0)
-        SPHC_LAUNCH(k_features<<<grid_for(nnzN, 256), 256, 0, s>>>(
-            ne, nnzN, lev, L.D.rp.p, L.D.ci.p, L.D.v.p, L.T.rp.p, L.T.ci.p, L.T.v.p, L.P0.rp.p, L.P0.ci.p, L.P0.v.p,
-            L.DH.rp.p, L.DH.ci.p, L.DH.v.p, L.Pn.rp.p, L.Pn.ci.p, L.Pn.v.p, L.A.rp.p, L.A.ci.p, L.A.v.p, L.X.p, Xc.p,
-            L.sig.p, F));
+    FeatArgs g = feat_args(L, Xc, lev);
+    if (g.nnzN > 0) SPHC_LAUNCH(k_features<<<grid_for(g.nnzN, 256), 256, 0, s>>>(g, F));
     SPHC_CK(cudaGetLastError());
     return SPHC_OK;
 }
@@ -1113,11 +1045,17 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
     if (o.learned) {
         Section sec(prof, "setup_learned_l0", s);
         if (!mlp_params) { set_error("learned warm start without MLP parameters"); return SPHC_EINVAL; }
-        DBuf<float> F, corr;
-        SPHC_TRY(F.alloc(nnzN * SPHC_MLP_NFEAT, s));
+        if (!L.X.p || !Xnext.p) {
+            set_error("the learned warm start needs node coordinates (pass coords to sphc_setup)");
+            return SPHC_EINVAL;
+        }
+        DBuf<float> corr;
         SPHC_TRY(corr.alloc(nnzN, s));
-        SPHC_TRY(level_features(L, Xnext, lev, F.p, s));
-        SPHC_TRY(mlp_predict(mlp_params, F.p, nnzN, corr.p, s));
+        {
+            Section sub(prof, "learned_mlp_l0", s);
+            SPHC_TRY(mlp_predict_level(mlp_params, feat_args(L, Xnext, lev), corr.p, s));
+        }
+        Section sub(prof, "learned_project_l0", s);
         if (ne > 0)
             SPHC_LAUNCH(k_learned_p0<<<grid_for(ne, LOC_WARPS), LOC_WARPS * 32, sm, s>>>(
                 ne, L.T.rp.p, L.T.ci.p, L.T.v.p, L.P0.rp.p, L.P0.ci.p, L.DH.rp.p, L.DH.ci.p, L.DH.v.p, corr.p, L.P0.v.p,

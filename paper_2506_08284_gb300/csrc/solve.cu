@@ -4,6 +4,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <string>
 
 #include "sphc_level.cuh"
 
@@ -53,205 +54,56 @@ Profiler::~Profiler() {
         }
 }
 
-// ------------------------------------------------------------------ stable colour partition
-static constexpr int PART_BLOCK = 1024;
-static constexpr int PART_MAXC = 256;
-
-__global__ void k_part_count(const int32_t* color, int64_t n, int ncolor, int32_t* table, int64_t nblocks) {
-    __shared__ int32_t cnt[PART_MAXC];
-    for (int c = threadIdx.x; c < ncolor; c += blockDim.x) cnt[c] = 0;
-    __syncthreads();
-    int64_t i = (int64_t)blockIdx.x * PART_BLOCK + threadIdx.x;
-    if (i < n) atomicAdd(&cnt[color[i]], 1);
-    __syncthreads();
-    for (int c = threadIdx.x; c < ncolor; c += blockDim.x) table[(int64_t)c * nblocks + blockIdx.x] = cnt[c];
-}
-// rows keep their natural order inside a colour
-__global__ void k_part_place(const int32_t* color, int64_t n, int ncolor, const int64_t* off, int64_t nblocks,
-                             int32_t* perm) {
-    __shared__ int32_t wcnt[PART_BLOCK / 32][PART_MAXC];
-    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int q = threadIdx.x; q < (PART_BLOCK / 32) * PART_MAXC; q += blockDim.x) (&wcnt[0][0])[q] = 0;
-    __syncthreads();
-    int64_t i = (int64_t)blockIdx.x * PART_BLOCK + threadIdx.x;
-    int c = i < n ? color[i] : -1;
-    unsigned m = __match_any_sync(0xffffffffu, c);
-    int rank = __popc(m & ((1u << lane) - 1u));
-    if (c >= 0 && rank == 0) wcnt[w][c] = __popc(m);
-    __syncthreads();
-    if (c >= 0) {
-        int before = 0;
-        for (int q = 0; q < w; ++q) before += wcnt[q][c];
-        perm[off[(int64_t)c * nblocks + blockIdx.x] + before + rank] = (int32_t)i;
+// ------------------------------------------------------------------ V-cycle operators
+// Level l's copies live in the numbering of H.ord[l]: the smoothers and A D take rows and columns
+// from it, P_e / P_n map the numbering of level l+1 to that of level l, P_e^T the reverse.
+static int build_orders(Hierarchy& H, cudaStream_t s) {
+    H.ord.clear();
+    H.ord.resize(H.nlev);
+    for (int l = 0; l + 1 < H.nlev; ++l) {
+        Level& L = H.L[l];
+        LevelOrder& O = H.ord[l];
+        SPHC_TRY(level_order(L.A, L.col_e.p, L.ncol_e, O.pe, O.ie, O.ce, s));
+        SPHC_TRY(level_order(L.An, L.col_n.p, L.ncol_n, O.pn, O.in, O.cn, s));
     }
-}
-
-static int colour_partition(const int32_t* color, int64_t n, int ncolor, DBuf<int32_t>& perm,
-                            std::vector<int64_t>& cstart, cudaStream_t s) {
-    if (ncolor > PART_MAXC) { set_error("too many colours (%d)", ncolor); return SPHC_ELIMIT; }
-    SPHC_TRY(perm.alloc(n, s));
-    int64_t nb = (n + PART_BLOCK - 1) / PART_BLOCK;
-    if (nb < 1) nb = 1;
-    DBuf<int32_t> table;
-    DBuf<int64_t> table64, off;
-    SPHC_TRY(table.alloc(ncolor * nb, s));
-    SPHC_TRY(off.alloc(ncolor * nb + 1, s));
-    if (n > 0) SPHC_LAUNCH(k_part_count<<<(unsigned)nb, PART_BLOCK, 0, s>>>(color, n, ncolor, table.p, nb));
-    SPHC_TRY(table64.alloc(ncolor * nb, s));
-    // widen to int64 for the scan
-    {
-        std::vector<int32_t> h(ncolor * nb);
-        SPHC_CK(cudaMemcpyAsync(h.data(), table.p, sizeof(int32_t) * h.size(), cudaMemcpyDeviceToHost, s));
-        SPHC_CK(cudaStreamSynchronize(s));
-        std::vector<int64_t> o(ncolor * nb + 1);
-        int64_t run = 0;
-        cstart.assign(ncolor + 1, 0);
-        for (int c = 0; c < ncolor; ++c) {
-            cstart[c] = run;
-            for (int64_t b = 0; b < nb; ++b) { o[c * nb + b] = run; run += h[c * nb + b]; }
-        }
-        cstart[ncolor] = run;
-        o[ncolor * nb] = run;
-        SPHC_CK(cudaMemcpyAsync(off.p, o.data(), sizeof(int64_t) * o.size(), cudaMemcpyHostToDevice, s));
-        SPHC_CK(cudaStreamSynchronize(s));
-    }
-    if (n > 0) SPHC_LAUNCH(k_part_place<<<(unsigned)nb, PART_BLOCK, 0, s>>>(color, n, ncolor, off.p, nb, perm.p));
-    SPHC_CK(cudaGetLastError());
     return SPHC_OK;
-}
-
-__global__ void k_perm_rowlen(const int64_t* rp, const int32_t* perm, int64_t n, int64_t* len) {
-    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < n) len[k] = rp[perm[k] + 1] - rp[perm[k]];
-}
-__global__ void k_rp_narrow(const int64_t* a, int32_t* b, int64_t n) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) b[i] = (int32_t)a[i];
-}
-template <typename T>
-__global__ void k_perm_copy(const int64_t* rp, const int32_t* ci, const double* v, const int32_t* perm, int64_t n,
-                            const int32_t* nrp, int32_t* nci, T* nv, T* dinv) {
-    int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
-    if (k >= n) return;
-    int64_t i = perm[k];
-    int64_t b = rp[i], len = rp[i + 1] - b;
-    int32_t o = nrp[k];
-    for (int64_t q = lane; q < len; q += 32) {
-        int32_t c = ci[b + q];
-        nci[o + q] = c;
-        nv[o + q] = (T)v[b + q];
-        if (c == i) dinv[k] = (T)(1.0 / v[b + q]);
-    }
-}
-
-template <typename T>
-static int build_smooth_op(const DCSR& A, const int32_t* color, int ncolor, SmoothOp<T>& op, cudaStream_t s) {
-    op.n = A.nr;
-    op.nnz = A.nnz;
-    op.ncolor = ncolor;
-    if (A.nnz >= (1LL << 31)) { set_error("operator with %lld nonzeros exceeds int32 row pointers", (long long)A.nnz); return SPHC_ELIMIT; }
-    SPHC_TRY(colour_partition(color, A.nr, ncolor, op.perm, op.cstart, s));
-    SPHC_TRY(op.cstart_dev.alloc(ncolor + 1, s));
-    SPHC_CK(cudaMemcpyAsync(op.cstart_dev.p, op.cstart.data(), sizeof(int64_t) * (ncolor + 1), cudaMemcpyHostToDevice, s));
-    SPHC_CK(cudaStreamSynchronize(s));
-    DBuf<int64_t> len, rp64;
-    SPHC_TRY(len.alloc(A.nr + 1, s));
-    SPHC_TRY(rp64.alloc(A.nr + 1, s));
-    if (A.nr > 0) SPHC_LAUNCH(k_perm_rowlen<<<grid_for(A.nr, 256), 256, 0, s>>>(A.rp.p, op.perm.p, A.nr, len.p));
-    SPHC_TRY(exclusive_scan_i64(len.p, rp64.p, A.nr, s, nullptr));
-    SPHC_TRY(op.rp.alloc(A.nr + 1, s));
-    SPHC_LAUNCH(k_rp_narrow<<<grid_for(A.nr + 1, 256), 256, 0, s>>>(rp64.p, op.rp.p, A.nr + 1));
-    SPHC_TRY(op.ci.alloc(A.nnz, s));
-    SPHC_TRY(op.v.alloc(A.nnz, s));
-    SPHC_TRY(op.dinv.alloc(A.nr, s));
-    if (A.nr > 0)
-        SPHC_LAUNCH(k_perm_copy<T><<<grid_for(A.nr * 32, 256), 256, 0, s>>>(A.rp.p, A.ci.p, A.v.p, op.perm.p, A.nr, op.rp.p,
-                                                                 op.ci.p, op.v.p, op.dinv.p));
-    SPHC_CK(cudaGetLastError());
-    return SPHC_OK;
-}
-
-template <typename T>
-__global__ void k_csr_narrow(const int64_t* rp, const double* v, int64_t nr, int64_t nnz, int32_t* nrp, T* nv) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i <= nr) nrp[i] = (int32_t)rp[i];
-    if (i < nnz) nv[i] = (T)v[i];
-}
-template <typename T>
-static int build_vcsr(const DCSR& A, VCSR<T>& B, cudaStream_t s) {
-    if (A.nnz >= (1LL << 31)) { set_error("transfer with %lld nonzeros exceeds int32 row pointers", (long long)A.nnz); return SPHC_ELIMIT; }
-    B.nr = A.nr; B.nc = A.nc; B.nnz = A.nnz;
-    SPHC_TRY(B.rp.alloc(A.nr + 1, s));
-    SPHC_TRY(B.ci.alloc(A.nnz, s));
-    SPHC_TRY(B.v.alloc(A.nnz, s));
-    int64_t m = A.nnz > A.nr + 1 ? A.nnz : A.nr + 1;
-    SPHC_LAUNCH(k_csr_narrow<T><<<grid_for(m, 256), 256, 0, s>>>(A.rp.p, A.v.p, A.nr, A.nnz, B.rp.p, B.v.p));
-    if (A.nnz > 0) SPHC_CK(cudaMemcpyAsync(B.ci.p, A.ci.p, sizeof(int32_t) * A.nnz, cudaMemcpyDeviceToDevice, s));
-    SPHC_CK(cudaGetLastError());
-    return SPHC_OK;
-}
-
-__global__ void k_d_pairs(const int64_t* rp, const int32_t* ci, const double* v, int64_t ne, int2* D) {
-    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= ne) return;
-    int2 d = make_int2(-1, -1);
-    for (int64_t k = rp[e]; k < rp[e + 1]; ++k) {
-        if (v[k] < 0) d.x = ci[k]; else d.y = ci[k];
-    }
-    D[e] = d;
-}
-__global__ void k_dt_encode(const int64_t* rp, const int32_t* ci, const double* v, int64_t nv, int64_t nnz,
-                            int32_t* nrp, int32_t* enc) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i <= nv) nrp[i] = (int32_t)rp[i];
-    if (i < nnz) enc[i] = (ci[i] << 1) | (v[i] < 0 ? 1 : 0);
 }
 
 template <typename T>
 static int build_vlevel(Hierarchy& H, int l, VLevel<T>& V, bool split, cudaStream_t s) {
     Level& L = H.L[l];
+    const LevelOrder& O = H.ord[l];
     int64_t ne = L.A.nr, nv = L.An.nr;
     SPHC_TRY(V.x.alloc(ne, s));
     SPHC_TRY(V.b.alloc(ne, s));
     SPHC_TRY(V.r.alloc(ne, s));
+    SPHC_TRY(V.c.alloc(nv, s));
+    SPHC_TRY(V.g.alloc(nv, s));
+    SPHC_TRY(build_d_pairs(L.D, O.pe.p, O.in.p, V.D, s));
+    SPHC_TRY(build_dt_enc(L.Dt, O.pn.p, O.ie.p, V.Dt_rp, V.Dt_e, s));
     if (split) {
-        SPHC_TRY(V.c.alloc(nv, s));
         SPHC_TRY(V.dc.alloc(nv, s));
         SPHC_TRY(V.bp.alloc(ne, s));
-        SPHC_TRY(V.D.alloc(ne, s));
-        if (ne > 0) SPHC_LAUNCH(k_d_pairs<<<grid_for(ne, 256), 256, 0, s>>>(L.D.rp.p, L.D.ci.p, L.D.v.p, ne, V.D.p));
-        SPHC_TRY(V.Dt_rp.alloc(nv + 1, s));
-        SPHC_TRY(V.Dt_e.alloc(L.Dt.nnz, s));
-        int64_t m0 = L.Dt.nnz > nv + 1 ? L.Dt.nnz : nv + 1;
-        SPHC_LAUNCH(k_dt_encode<<<grid_for(m0, 256), 256, 0, s>>>(L.Dt.rp.p, L.Dt.ci.p, L.Dt.v.p, nv, L.Dt.nnz, V.Dt_rp.p, V.Dt_e.p));
     }
     if (l == H.nlev - 1) return SPHC_OK;
+    const LevelOrder& C = H.ord[l + 1];
     if (split) {
         if (L.AD.nr != L.A.nr) SPHC_TRY(spgemm(L.A, L.D, L.AD, s));   // FP64: the curl-curl part cancels here
-        SPHC_TRY(build_vcsr<T>(L.AD, V.AD, s));
-        SPHC_TRY(build_vcsr<T>(L.Pn, V.Pn, s));
+        SPHC_TRY(build_xop<T>(L.AD, O.pe.p, O.in.p, V.AD, s));
+        SPHC_TRY(build_xop<T>(L.Pn, O.pn.p, C.in.p, V.Pn, s));
         L.AD = DCSR();
     }
-    SPHC_TRY(build_smooth_op<T>(L.A, L.col_e.p, L.ncol_e, V.A, s));
-    SPHC_TRY(build_smooth_op<T>(L.An, L.col_n.p, L.ncol_n, V.An, s));
-    SPHC_TRY(V.g.alloc(nv, s));
-    if (!split) {
-        SPHC_TRY(V.c.alloc(nv, s));
-        SPHC_TRY(V.D.alloc(ne, s));
-        if (ne > 0) SPHC_LAUNCH(k_d_pairs<<<grid_for(ne, 256), 256, 0, s>>>(L.D.rp.p, L.D.ci.p, L.D.v.p, ne, V.D.p));
-        SPHC_TRY(V.Dt_rp.alloc(nv + 1, s));
-        SPHC_TRY(V.Dt_e.alloc(L.Dt.nnz, s));
-        int64_t m = L.Dt.nnz > nv + 1 ? L.Dt.nnz : nv + 1;
-        SPHC_LAUNCH(k_dt_encode<<<grid_for(m, 256), 256, 0, s>>>(L.Dt.rp.p, L.Dt.ci.p, L.Dt.v.p, nv, L.Dt.nnz, V.Dt_rp.p, V.Dt_e.p));
-    }
-    SPHC_TRY(build_vcsr<T>(L.Pe, V.Pe, s));
-    SPHC_TRY(build_vcsr<T>(L.PeT, V.PeT, s));
+    SPHC_TRY(build_smooth<T>(L.A, O.pe.p, O.ie.p, O.ce, 0, 0, V.A, s));
+    SPHC_TRY(build_smooth<T>(L.An, O.pn.p, O.in.p, O.cn, 0, 0, V.An, s));
+    SPHC_TRY(build_xop<T>(L.Pe, O.pe.p, C.ie.p, V.Pe, s));
+    SPHC_TRY(build_xop<T>(L.PeT, C.pe.p, O.ie.p, V.PeT, s));
     SPHC_CK(cudaGetLastError());
     return SPHC_OK;
 }
 
 int build_vcycle_ops(Hierarchy& H, cudaStream_t s) {
+    SPHC_TRY(build_orders(H, s));
+    const LevelOrder& O = H.ord[0];
     if (H.opts.vcycle_fp32) {
         H.V32.clear();
         H.V32.resize(H.nlev);
@@ -261,6 +113,14 @@ int build_vcycle_ops(Hierarchy& H, cudaStream_t s) {
         H.V64.resize(H.nlev);
         for (int l = 0; l < H.nlev; ++l) SPHC_TRY(build_vlevel<double>(H, l, H.V64[l], false, s));
     }
+    // CG operator: shared with the FP64 smoother of level 0 when there is one
+    H.A0 = Sell<double>();
+    if (H.opts.vcycle_fp32 || H.nlev == 1) {
+        std::vector<int64_t> seg{0, H.L[0].A.nr};
+        int ch = 4, lpr = sell_lpr_for(H.L[0].A, 1);
+        SPHC_TRY(sell_pick_ch(H.L[0].A, O.pe.p, seg, lpr, s, &ch));
+        SPHC_TRY(build_sell<double>(H.L[0].A, O.pe.p, O.ie.p, seg, ch, lpr, H.A0, nullptr, nullptr, s));
+    }
     int64_t n0 = H.L[0].A.nr;
     SPHC_TRY(H.x.alloc(n0, s));
     SPHC_TRY(H.r.alloc(n0, s));
@@ -268,6 +128,8 @@ int build_vcycle_ops(Hierarchy& H, cudaStream_t s) {
     SPHC_TRY(H.p.alloc(n0, s));
     SPHC_TRY(H.q.alloc(n0, s));
     SPHC_TRY(H.rold.alloc(n0, s));
+    SPHC_TRY(H.bperm.alloc(n0, s));
+    SPHC_TRY(H.xo.alloc(n0, s));
     SPHC_TRY(H.scal.alloc(16, s));
     SPHC_TRY(H.cb.alloc(H.n_coarse, s));
     SPHC_TRY(H.cx.alloc(H.n_coarse, s));
@@ -276,12 +138,18 @@ int build_vcycle_ops(Hierarchy& H, cudaStream_t s) {
     SPHC_TRY(H.dpart.alloc(DOT_PARTS, s));
     SPHC_TRY(H.itc.alloc(4, s));
     SPHC_TRY(H.bin.alloc(n0, s));
-
+    SPHC_CK(cudaStreamSynchronize(s));
     return SPHC_OK;
 }
 
+static const Sell<double>& cg_op(const Hierarchy& H) {
+    return H.A0.nr == H.L[0].A.nr ? H.A0 : H.V64[0].A.m;
+}
+static const int32_t* perm0(const Hierarchy& H) { return H.ord.empty() ? nullptr : H.ord[0].pe.p; }
+
 // ------------------------------------------------------------------ dot products into persistent partials
 __global__ void k_dot_part_b(const double* a, const double* b, int64_t n, double* part) {
+    pdl_enter();
     __shared__ double sw[32];
     double s = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -296,6 +164,7 @@ __global__ void k_dot_part_b(const double* a, const double* b, int64_t n, double
     }
 }
 __global__ void k_dot_final_b(const double* part, int np, double* out) {
+    pdl_enter();
     __shared__ double sw[32];
     double s = 0.0;
     for (int i = threadIdx.x; i < np; i += blockDim.x) s += part[i];
@@ -309,50 +178,173 @@ __global__ void k_dot_final_b(const double* part, int np, double* out) {
     }
 }
 static void dot_buf(Hierarchy& H, const double* a, const double* b, int64_t n, double* out, cudaStream_t s) {
-    SPHC_LAUNCH(k_dot_part_b<<<DOT_PARTS, 256, 0, s>>>(a, b, n, H.dpart.p));
-    SPHC_LAUNCH(k_dot_final_b<<<1, 1024, 0, s>>>(H.dpart.p, DOT_PARTS, out));
+    launch_pdl(k_dot_part_b, DOT_PARTS, 256, 0, s, a, b, n, H.dpart.p);
+    launch_pdl(k_dot_final_b, 1, 1024, 0, s, H.dpart.p, DOT_PARTS, out);
 }
 
 // ------------------------------------------------------------------ V-cycle kernels
-template <typename T, int SUB>
-__global__ void k_sgs_color(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const T* __restrict__ v,
-                            const int32_t* __restrict__ perm, const T* __restrict__ dinv, int64_t k0, int64_t k1,
-                            const T* __restrict__ b, T* x) {
-    int64_t k = k0 + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / SUB);
-    int q = threadIdx.x & (SUB - 1);
-    bool valid = k < k1;
-    T sum = 0;
-    if (valid)
-        for (int32_t e = rp[k] + q; e < rp[k + 1]; e += SUB) sum += v[e] * x[ci[e]];
-#pragma unroll
-    for (int o = SUB / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o, SUB);
-    if (valid && q == 0) {
-        int32_t i = perm[k];
-        x[i] += (b[i] - sum) * dinv[k];
+// Streaming loads of ch matrix entries (evict-first: the matrix is read once per sweep and should
+// not push the iterate out of L2).
+template <typename T, int CH> struct Chunk;
+template <> struct Chunk<float, 1> {
+    static __device__ __forceinline__ void load(const float* p, float* a) { a[0] = __ldcs(p); }
+};
+template <> struct Chunk<float, 2> {
+    static __device__ __forceinline__ void load(const float* p, float* a) {
+        float2 t = __ldcs(reinterpret_cast<const float2*>(p));
+        a[0] = t.x; a[1] = t.y;
     }
+};
+template <> struct Chunk<float, 4> {
+    static __device__ __forceinline__ void load(const float* p, float* a) {
+        float4 t = __ldcs(reinterpret_cast<const float4*>(p));
+        a[0] = t.x; a[1] = t.y; a[2] = t.z; a[3] = t.w;
+    }
+};
+template <> struct Chunk<double, 1> {
+    static __device__ __forceinline__ void load(const double* p, double* a) { a[0] = __ldcs(p); }
+};
+template <> struct Chunk<double, 2> {
+    static __device__ __forceinline__ void load(const double* p, double* a) {
+        double2 t = __ldcs(reinterpret_cast<const double2*>(p));
+        a[0] = t.x; a[1] = t.y;
+    }
+};
+template <> struct Chunk<double, 4> {
+    static __device__ __forceinline__ void load(const double* p, double* a) {
+        double2 t = __ldcs(reinterpret_cast<const double2*>(p));
+        double2 u = __ldcs(reinterpret_cast<const double2*>(p) + 1);
+        a[0] = t.x; a[1] = t.y; a[2] = u.x; a[3] = u.y;
+    }
+};
+template <int CH> struct IChunk;
+template <> struct IChunk<1> {
+    static __device__ __forceinline__ void load(const int32_t* p, int32_t* c) { c[0] = __ldcs(p); }
+};
+template <> struct IChunk<2> {
+    static __device__ __forceinline__ void load(const int32_t* p, int32_t* c) {
+        int2 t = __ldcs(reinterpret_cast<const int2*>(p));
+        c[0] = t.x; c[1] = t.y;
+    }
+};
+template <> struct IChunk<4> {
+    static __device__ __forceinline__ void load(const int32_t* p, int32_t* c) {
+        int4 t = __ldcs(reinterpret_cast<const int4*>(p));
+        c[0] = t.x; c[1] = t.y; c[2] = t.z; c[3] = t.w;
+    }
+};
+
+// This lane's partial (A x)_r over the slice starting at o: `steps` loads of CH entries
+template <typename T, int CH>
+__device__ __forceinline__ T sell_part(const int32_t* __restrict__ ci, const T* __restrict__ v, int64_t o,
+                                       int64_t steps, int lane, const T* x) {
+    const T* vp = v + o + lane * CH;
+    const int32_t* cp = ci + o + lane * CH;
+    T sum = 0;
+#pragma unroll 2
+    for (int64_t q = 0; q < steps; ++q) {
+        T a[CH];
+        int32_t c[CH];
+        Chunk<T, CH>::load(vp, a);
+        IChunk<CH>::load(cp, c);
+#pragma unroll
+        for (int t = 0; t < CH; ++t) sum += a[t] * x[c[t]];
+        vp += SELL_C * CH;
+        cp += SELL_C * CH;
+    }
+    return sum;
+}
+// sum over the lpr lanes of a row (every lane of the warp must call it)
+template <typename T>
+__device__ __forceinline__ T row_reduce(T sum, int lpr) {
+    for (int d = lpr >> 1; d > 0; d >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, d);
+    return sum;
+}
+// the row of this lane in slice sl and whether this lane writes it
+struct SliceRow {
+    int32_t r;
+    bool write;
+};
+__device__ __forceinline__ SliceRow slice_row(const int32_t* __restrict__ srow, int64_t sl, int lane, int lpr) {
+    SliceRow q;
+    q.r = srow[sl] + lane / lpr;
+    q.write = (lane & (lpr - 1)) == 0 && q.r < srow[sl + 1];
+    return q;
 }
 
-template <typename T, int SUB>
-__global__ void k_resid(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const T* __restrict__ v,
-                        const int32_t* __restrict__ perm, int64_t n, const T* __restrict__ b, const T* __restrict__ x,
-                        T* __restrict__ r) {
-    int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / SUB;
-    int q = threadIdx.x & (SUB - 1);
-    bool valid = k < n;
-    T sum = 0;
-    if (valid)
-        for (int32_t e = rp[k] + q; e < rp[k + 1]; e += SUB) sum += v[e] * x[ci[e]];
-#pragma unroll
-    for (int o = SUB / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o, SUB);
-    if (valid && q == 0) {
-        int32_t i = perm[k];
-        r[i] = b[i] - sum;
+// Gauss-Seidel update of the rows of slices [s0, s1) (one colour): x_r += (b_r - (A x)_r) / a_rr
+template <typename T, int CH>
+__global__ void __launch_bounds__(256)
+k_sell_sgs(const int64_t* __restrict__ soff, const int32_t* __restrict__ srow, int64_t s0, int64_t s1, int lpr,
+           const int32_t* __restrict__ ci, const T* __restrict__ v, const T* __restrict__ dinv,
+           const T* __restrict__ b, T* x) {
+    pdl_enter();
+    int64_t sl = s0 + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (sl >= s1) return;
+    int lane = threadIdx.x & 31;
+    int64_t o = soff[sl];
+    SliceRow q = slice_row(srow, sl, lane, lpr);
+    T br = q.write ? b[q.r] : T(0), dr = q.write ? dinv[q.r] : T(0);
+    T sum = row_reduce(sell_part<T, CH>(ci, v, o, (soff[sl + 1] - o) / (SELL_C * CH), lane, x), lpr);
+    if (q.write) x[q.r] += (br - sum) * dr;
+}
+// r = b - A x over all slices
+template <typename T, int CH>
+__global__ void __launch_bounds__(256)
+k_sell_resid(const int64_t* __restrict__ soff, const int32_t* __restrict__ srow, int64_t nslice, int lpr,
+             const int32_t* __restrict__ ci, const T* __restrict__ v, const T* __restrict__ b,
+             const T* __restrict__ x, T* __restrict__ r) {
+    pdl_enter();
+    int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (sl >= nslice) return;
+    int lane = threadIdx.x & 31;
+    int64_t o = soff[sl];
+    SliceRow q = slice_row(srow, sl, lane, lpr);
+    T br = q.write ? b[q.r] : T(0);
+    T sum = row_reduce(sell_part<T, CH>(ci, v, o, (soff[sl + 1] - o) / (SELL_C * CH), lane, x), lpr);
+    if (q.write) r[q.r] = br - sum;
+}
+// y = alpha A x (+ y)
+template <typename T, int CH>
+__global__ void __launch_bounds__(256)
+k_sell_spmv(const int64_t* __restrict__ soff, const int32_t* __restrict__ srow, int64_t nslice, int lpr,
+            const int32_t* __restrict__ ci, const T* __restrict__ v, const T* __restrict__ x, T* y, int accumulate,
+            T alpha) {
+    pdl_enter();
+    int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (sl >= nslice) return;
+    int lane = threadIdx.x & 31;
+    int64_t o = soff[sl];
+    SliceRow q = slice_row(srow, sl, lane, lpr);
+    T sum = row_reduce(sell_part<T, CH>(ci, v, o, (soff[sl + 1] - o) / (SELL_C * CH), lane, x), lpr);
+    if (q.write) y[q.r] = accumulate ? y[q.r] + alpha * sum : alpha * sum;
+}
+// A whole forward + backward sweep of a small operator in one block: colours are separated by
+// block barriers instead of kernel boundaries (the coarse levels are launch-bound otherwise).
+static constexpr int SGS_BLOCK_MAX_ROWS = 2048;
+template <typename T, int CH>
+__global__ void __launch_bounds__(1024)
+k_sell_sgs_block(const int64_t* __restrict__ soff, const int32_t* __restrict__ srow,
+                 const int64_t* __restrict__ cslice, int ncolor, int lpr, const int32_t* __restrict__ ci,
+                 const T* __restrict__ v, const T* __restrict__ dinv, const T* __restrict__ b, T* x) {
+    pdl_enter();
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    for (int step = 0; step < 2 * ncolor; ++step) {
+        int c = step < ncolor ? step : 2 * ncolor - 1 - step;
+        for (int64_t sl = cslice[c] + warp; sl < cslice[c + 1]; sl += nwarp) {
+            int64_t o = soff[sl];
+            SliceRow q = slice_row(srow, sl, lane, lpr);
+            T sum = row_reduce(sell_part<T, CH>(ci, v, o, (soff[sl + 1] - o) / (SELL_C * CH), lane, x), lpr);
+            if (q.write) x[q.r] += (b[q.r] - sum) * dinv[q.r];
+        }
+        __syncthreads();
     }
 }
 
 template <typename T, int SUB>
 __global__ void k_spmv_v(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const T* __restrict__ v,
                          int64_t n, const T* __restrict__ x, T* y, int accumulate, T alpha) {
+    pdl_enter();
     int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / SUB;
     int q = threadIdx.x & (SUB - 1);
     bool valid = i < n;
@@ -367,6 +359,7 @@ __global__ void k_spmv_v(const int32_t* __restrict__ rp, const int32_t* __restri
 template <typename T>
 __global__ void k_dt_gather(const int32_t* __restrict__ rp, const int32_t* __restrict__ enc, int64_t nv,
                             const T* __restrict__ r, T* __restrict__ g) {
+    pdl_enter();
     int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= nv) return;
     T s = 0;
@@ -379,6 +372,7 @@ __global__ void k_dt_gather(const int32_t* __restrict__ rp, const int32_t* __res
 }
 template <typename T>
 __global__ void k_d_apply(const int2* __restrict__ D, int64_t ne, const T* __restrict__ c, T* __restrict__ x) {
+    pdl_enter();
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= ne) return;
     int2 d = D[e];
@@ -389,17 +383,20 @@ __global__ void k_d_apply(const int2* __restrict__ D, int64_t ne, const T* __res
 }
 template <typename T>
 __global__ void k_zero(T* a, int64_t n) {
+    pdl_enter();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) a[i] = 0;
 }
 template <typename A, typename B>
 __global__ void k_cast(const A* a, B* b, int64_t n) {
+    pdl_enter();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) b[i] = (B)a[i];
 }
 // x = Ainv b on the coarsest level (FP64 arithmetic)
 template <typename T>
 __global__ void k_dense_solve(const double* __restrict__ Ainv, int64_t n, const T* __restrict__ b, T* __restrict__ x) {
+    pdl_enter();
     int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
     if (i >= n) return;
@@ -417,94 +414,78 @@ static int sub_for(int64_t nnz, int64_t n) {
     return 32;
 }
 
-template <typename T>
-static void launch_rows_sgs(const SmoothOp<T>& op, int64_t k0, int64_t k1, const T* b, T* x, cudaStream_t s) {
-    int64_t rows = k1 - k0;
-    if (rows <= 0) return;
-    int sub = op.sub > 0 ? op.sub : sub_for(op.nnz, op.n);
-    int64_t th = rows * sub;
-    switch (sub) {
-        case 4: SPHC_LAUNCH(k_sgs_color<T, 4><<<grid_for(th, 256), 256, 0, s>>>(op.rp.p, op.ci.p, op.v.p, op.perm.p, op.dinv.p, k0, k1, b, x)); break;
-        case 8: SPHC_LAUNCH(k_sgs_color<T, 8><<<grid_for(th, 256), 256, 0, s>>>(op.rp.p, op.ci.p, op.v.p, op.perm.p, op.dinv.p, k0, k1, b, x)); break;
-        case 16: SPHC_LAUNCH(k_sgs_color<T, 16><<<grid_for(th, 256), 256, 0, s>>>(op.rp.p, op.ci.p, op.v.p, op.perm.p, op.dinv.p, k0, k1, b, x)); break;
-        default: SPHC_LAUNCH(k_sgs_color<T, 32><<<grid_for(th, 256), 256, 0, s>>>(op.rp.p, op.ci.p, op.v.p, op.perm.p, op.dinv.p, k0, k1, b, x)); break;
+static unsigned slice_grid(int64_t nslice) { return (unsigned)grid_for(nslice * 32, 256); }
+
+#define SPHC_CH_SWITCH(ch, F) \
+    switch (ch) {             \
+        case 1: F(1); break;  \
+        case 2: F(2); break;  \
+        default: F(4); break; \
     }
-}
-// A whole forward + backward sweep of a small operator in one block: colours are separated by
-// block barriers instead of kernel boundaries (the coarse levels are launch-bound otherwise).
-static constexpr int SGS_BLOCK_MAX_ROWS = 2048;
-template <typename T, int SUB>
-__global__ void __launch_bounds__(1024)
-k_sgs_block(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const T* __restrict__ v,
-            const int32_t* __restrict__ perm, const T* __restrict__ dinv, const int64_t* __restrict__ cstart,
-            int ncolor, const T* __restrict__ b, T* x) {
-    int q = threadIdx.x & (SUB - 1);
-    int slot = threadIdx.x / SUB, nslot = blockDim.x / SUB;
-    for (int step = 0; step < 2 * ncolor; ++step) {
-        int c = step < ncolor ? step : 2 * ncolor - 1 - step;
-        int64_t k0 = cstart[c], k1 = cstart[c + 1];
-        for (int64_t base = k0; base < k1; base += nslot) {
-            int64_t k = base + slot;
-            bool valid = k < k1;
-            T sum = 0;
-            if (valid)
-                for (int32_t e = rp[k] + q; e < rp[k + 1]; e += SUB) sum += v[e] * x[ci[e]];
-#pragma unroll
-            for (int o = SUB / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o, SUB);
-            if (valid && q == 0) {
-                int32_t i = perm[k];
-                x[i] += (b[i] - sum) * dinv[k];
-            }
-        }
-        __syncthreads();
-    }
-}
 
 template <typename T>
 static void sgs(const SmoothOp<T>& op, const T* b, T* x, cudaStream_t s) {
-    if (op.n <= SGS_BLOCK_MAX_ROWS && op.cstart_dev.p) {
-        int sub = sub_for(op.nnz, op.n);
-        switch (sub) {
-            case 4: SPHC_LAUNCH(k_sgs_block<T, 4><<<1, 1024, 0, s>>>(op.rp.p, op.ci.p, op.v.p, op.perm.p, op.dinv.p, op.cstart_dev.p, op.ncolor, b, x)); break;
-            case 8: SPHC_LAUNCH(k_sgs_block<T, 8><<<1, 1024, 0, s>>>(op.rp.p, op.ci.p, op.v.p, op.perm.p, op.dinv.p, op.cstart_dev.p, op.ncolor, b, x)); break;
-            case 16: SPHC_LAUNCH(k_sgs_block<T, 16><<<1, 1024, 0, s>>>(op.rp.p, op.ci.p, op.v.p, op.perm.p, op.dinv.p, op.cstart_dev.p, op.ncolor, b, x)); break;
-            default: SPHC_LAUNCH(k_sgs_block<T, 32><<<1, 1024, 0, s>>>(op.rp.p, op.ci.p, op.v.p, op.perm.p, op.dinv.p, op.cstart_dev.p, op.ncolor, b, x)); break;
-        }
+    const Sell<T>& m = op.m;
+    if (op.n == 0) return;
+    if (op.n <= SGS_BLOCK_MAX_ROWS) {
+#define F(C) launch_pdl(k_sell_sgs_block<T, C>, 1, 1024, 0, s, m.soff.p, m.srow.p, op.cslice_dev.p, op.ncolor, m.lpr, m.ci.p, m.v.p, op.dinv.p, b, x)
+        SPHC_CH_SWITCH(m.ch, F)
+#undef F
         return;
     }
-    for (int c = 0; c < op.ncolor; ++c) launch_rows_sgs(op, op.cstart[c], op.cstart[c + 1], b, x, s);
-    for (int c = op.ncolor - 1; c >= 0; --c) launch_rows_sgs(op, op.cstart[c], op.cstart[c + 1], b, x, s);
+    for (int step = 0; step < 2 * op.ncolor; ++step) {
+        int c = step < op.ncolor ? step : 2 * op.ncolor - 1 - step;
+        int64_t s0 = op.cslice[c], s1 = op.cslice[c + 1];
+        if (s1 <= s0) continue;
+#define F(C) launch_pdl(k_sell_sgs<T, C>, slice_grid(s1 - s0), 256, 0, s, m.soff.p, m.srow.p, s0, s1, m.lpr, m.ci.p, m.v.p, op.dinv.p, b, x)
+        SPHC_CH_SWITCH(m.ch, F)
+#undef F
+    }
 }
 template <typename T>
 static void resid(const SmoothOp<T>& op, const T* b, const T* x, T* r, cudaStream_t s) {
-    if (op.n == 0) return;
-    int sub = op.sub > 0 ? op.sub : sub_for(op.nnz, op.n);
-    int64_t th = op.n * sub;
-    switch (sub) {
-        case 4: SPHC_LAUNCH(k_resid<T, 4><<<grid_for(th, 256), 256, 0, s>>>(op.rp.p, op.ci.p, op.v.p, op.perm.p, op.n, b, x, r)); break;
-        case 8: SPHC_LAUNCH(k_resid<T, 8><<<grid_for(th, 256), 256, 0, s>>>(op.rp.p, op.ci.p, op.v.p, op.perm.p, op.n, b, x, r)); break;
-        case 16: SPHC_LAUNCH(k_resid<T, 16><<<grid_for(th, 256), 256, 0, s>>>(op.rp.p, op.ci.p, op.v.p, op.perm.p, op.n, b, x, r)); break;
-        default: SPHC_LAUNCH(k_resid<T, 32><<<grid_for(th, 256), 256, 0, s>>>(op.rp.p, op.ci.p, op.v.p, op.perm.p, op.n, b, x, r)); break;
-    }
+    const Sell<T>& m = op.m;
+    if (m.nslice == 0) return;
+#define F(C) launch_pdl(k_sell_resid<T, C>, slice_grid(m.nslice), 256, 0, s, m.soff.p, m.srow.p, m.nslice, m.lpr, m.ci.p, m.v.p, b, x, r)
+    SPHC_CH_SWITCH(m.ch, F)
+#undef F
 }
 template <typename T>
-static void spmv_v(const VCSR<T>& A, const T* x, T* y, int acc, cudaStream_t s, T alpha = T(1)) {
-    if (A.nr == 0) return;
+static void sell_spmv(const Sell<T>& m, const T* x, T* y, int acc, cudaStream_t s, T alpha = T(1)) {
+    if (m.nslice == 0) return;
+#define F(C) launch_pdl(k_sell_spmv<T, C>, slice_grid(m.nslice), 256, 0, s, m.soff.p, m.srow.p, m.nslice, m.lpr, m.ci.p, m.v.p, x, y, acc, alpha)
+    SPHC_CH_SWITCH(m.ch, F)
+#undef F
+}
+template <typename T>
+static void spmv_v(const XOp<T>& X, const T* x, T* y, int acc, cudaStream_t s, T alpha = T(1)) {
+    if (X.nr == 0) return;
+    if (X.sell) {
+        sell_spmv<T>(X.s, x, y, acc, s, alpha);
+        return;
+    }
+    const VCSR<T>& A = X.c;
     int sub = sub_for(A.nnz, A.nr);
     int64_t th = A.nr * sub;
     switch (sub) {
-        case 4: SPHC_LAUNCH(k_spmv_v<T, 4><<<grid_for(th, 256), 256, 0, s>>>(A.rp.p, A.ci.p, A.v.p, A.nr, x, y, acc, alpha)); break;
-        case 8: SPHC_LAUNCH(k_spmv_v<T, 8><<<grid_for(th, 256), 256, 0, s>>>(A.rp.p, A.ci.p, A.v.p, A.nr, x, y, acc, alpha)); break;
-        case 16: SPHC_LAUNCH(k_spmv_v<T, 16><<<grid_for(th, 256), 256, 0, s>>>(A.rp.p, A.ci.p, A.v.p, A.nr, x, y, acc, alpha)); break;
-        default: SPHC_LAUNCH(k_spmv_v<T, 32><<<grid_for(th, 256), 256, 0, s>>>(A.rp.p, A.ci.p, A.v.p, A.nr, x, y, acc, alpha)); break;
+        case 4: launch_pdl(k_spmv_v<T, 4>, grid_for(th, 256), 256, 0, s, A.rp.p, A.ci.p, A.v.p, A.nr, x, y, acc, alpha); break;
+        case 8: launch_pdl(k_spmv_v<T, 8>, grid_for(th, 256), 256, 0, s, A.rp.p, A.ci.p, A.v.p, A.nr, x, y, acc, alpha); break;
+        case 16: launch_pdl(k_spmv_v<T, 16>, grid_for(th, 256), 256, 0, s, A.rp.p, A.ci.p, A.v.p, A.nr, x, y, acc, alpha); break;
+        default: launch_pdl(k_spmv_v<T, 32>, grid_for(th, 256), 256, 0, s, A.rp.p, A.ci.p, A.v.p, A.nr, x, y, acc, alpha); break;
     }
 }
+// y = A x for CG (FP64, level-0 V-cycle numbering)
+static int cg_spmv(const Hierarchy& H, const double* x, double* y, cudaStream_t s) {
+    sell_spmv<double>(cg_op(H), x, y, 0, s);
+    SPHC_CK(cudaGetLastError());
+    return SPHC_OK;
+}
 
-// algorithmic bytes of one forward + backward sweep: the matrix once per direction and, per
-// row, its pointer, permutation, inverse diagonal, right side and one read and write of x
+// algorithmic bytes of one forward + backward sweep: the matrix (values and column indices)
+// once per direction and, per row, its right side, inverse diagonal and one read and write of x
 template <typename T>
 static double sgs_bytes(const SmoothOp<T>& op) {
-    return 2.0 * ((double)op.nnz * (sizeof(T) + 4) + (double)op.n * (4 + 4 + 3 * sizeof(T) + sizeof(T)));
+    return 2.0 * ((double)op.nnz * (sizeof(T) + 4) + (double)op.n * 4.0 * sizeof(T));
 }
 
 template <typename T>
@@ -523,10 +504,10 @@ static void hiptmair(Hierarchy& H, int lev, VLevel<T>& V, int64_t ne, int64_t nv
     timed_sgs(H, lev, V.A, V.b.p, V.x.p, s);
     resid(V.A, V.b.p, V.x.p, V.r.p, s);
     if (nv > 0) {
-        SPHC_LAUNCH(k_dt_gather<T><<<grid_for(nv, 256), 256, 0, s>>>(V.Dt_rp.p, V.Dt_e.p, nv, V.r.p, V.g.p));
-        SPHC_LAUNCH(k_zero<T><<<grid_for(nv, 256), 256, 0, s>>>(V.c.p, nv));
+        launch_pdl(k_dt_gather<T>, grid_for(nv, 256), 256, 0, s, V.Dt_rp.p, V.Dt_e.p, nv, V.r.p, V.g.p);
+        launch_pdl(k_zero<T>, grid_for(nv, 256), 256, 0, s, V.c.p, nv);
         sgs(V.An, V.g.p, V.c.p, s);
-        SPHC_LAUNCH(k_d_apply<T><<<grid_for(ne, 256), 256, 0, s>>>(V.D.p, ne, V.c.p, V.x.p));
+        launch_pdl(k_d_apply<T>, grid_for(ne, 256), 256, 0, s, V.D.p, ne, V.c.p, V.x.p);
     }
     timed_sgs(H, lev, V.A, V.b.p, V.x.p, s);
 }
@@ -535,10 +516,10 @@ template <typename T>
 static void vcycle_level(Hierarchy& H, std::vector<VLevel<T>>& V, int l, cudaStream_t s) {
     int64_t ne = H.L[l].A.nr, nv = H.L[l].An.nr;
     if (l == H.nlev - 1) {
-        if (ne > 0) SPHC_LAUNCH(k_dense_solve<T><<<grid_for(ne * 32, 256), 256, 0, s>>>(H.coarse_inv.p, ne, V[l].b.p, V[l].x.p));
+        if (ne > 0) launch_pdl(k_dense_solve<T>, grid_for(ne * 32, 256), 256, 0, s, H.coarse_inv.p, ne, V[l].b.p, V[l].x.p);
         return;
     }
-    SPHC_LAUNCH(k_zero<T><<<grid_for(ne, 256), 256, 0, s>>>(V[l].x.p, ne));
+    launch_pdl(k_zero<T>, grid_for(ne, 256), 256, 0, s, V[l].x.p, ne);
     hiptmair(H, l, V[l], ne, nv, s);
     resid(V[l].A, V[l].b.p, V[l].x.p, V[l].r.p, s);
     spmv_v(V[l].PeT, V[l].r.p, V[l + 1].b.p, 0, s);
@@ -556,11 +537,13 @@ static void vcycle_level(Hierarchy& H, std::vector<VLevel<T>>& V, int l, cudaStr
 // through A D, formed in FP64 (where K D cancels) and stored in FP32: b' = b - (A D) c.
 template <typename T>
 __global__ void k_axpy(T* y, const T* x, int64_t n) {
+    pdl_enter();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) y[i] += x[i];
 }
 template <typename T>
 __global__ void k_copy(T* y, const T* x, int64_t n) {
+    pdl_enter();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) y[i] = x[i];
 }
@@ -568,6 +551,7 @@ __global__ void k_copy(T* y, const T* x, int64_t n) {
 template <typename T>
 __global__ void k_combine(const T* __restrict__ y, const int2* __restrict__ D, const T* __restrict__ c, int64_t n,
                           double* __restrict__ z) {
+    pdl_enter();
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n) return;
     int2 d = D[e];
@@ -577,6 +561,7 @@ __global__ void k_combine(const T* __restrict__ y, const int2* __restrict__ D, c
     z[e] = v;
 }
 __global__ void k_dense_mv64(const double* __restrict__ M, int64_t n, const double* __restrict__ b, double* __restrict__ x) {
+    pdl_enter();
     int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
     if (i >= n) return;
@@ -589,6 +574,7 @@ __global__ void k_dense_mv64(const double* __restrict__ M, int64_t n, const doub
 template <typename T>
 __global__ void k_split_out(const double* __restrict__ xb, const int2* __restrict__ D, const double* __restrict__ cc,
                             int64_t ne, int64_t nv, T* __restrict__ y, T* __restrict__ c) {
+    pdl_enter();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < ne) {
         int2 d = D[i];
@@ -603,14 +589,14 @@ __global__ void k_split_out(const double* __restrict__ xb, const int2* __restric
 template <typename T>
 static void coarse_split(Hierarchy& H, VLevel<T>& V, int64_t ne, int64_t nv, cudaStream_t s) {
     if (ne == 0) return;
-    SPHC_LAUNCH(k_cast<T, double><<<grid_for(ne, 256), 256, 0, s>>>(V.b.p, H.cb.p, ne));
-    SPHC_LAUNCH(k_dense_mv64<<<grid_for(ne * 32, 256), 256, 0, s>>>(H.coarse_inv.p, ne, H.cb.p, H.cx.p));
+    launch_pdl(k_cast<T, double>, grid_for(ne, 256), 256, 0, s, V.b.p, H.cb.p, ne);
+    launch_pdl(k_dense_mv64, grid_for(ne * 32, 256), 256, 0, s, H.coarse_inv.p, ne, H.cb.p, H.cx.p);
     if (nv > 0) {
-        SPHC_LAUNCH(k_dt_gather<double><<<grid_for(nv, 256), 256, 0, s>>>(V.Dt_rp.p, V.Dt_e.p, nv, H.cb.p, H.cgn.p));
-        SPHC_LAUNCH(k_dense_mv64<<<grid_for(nv * 32, 256), 256, 0, s>>>(H.coarse_inv_n.p, nv, H.cgn.p, H.ccn.p));
+        launch_pdl(k_dt_gather<double>, grid_for(nv, 256), 256, 0, s, V.Dt_rp.p, V.Dt_e.p, nv, H.cb.p, H.cgn.p);
+        launch_pdl(k_dense_mv64, grid_for(nv * 32, 256), 256, 0, s, H.coarse_inv_n.p, nv, H.cgn.p, H.ccn.p);
     }
     int64_t m = ne > nv ? ne : nv;
-    SPHC_LAUNCH(k_split_out<T><<<grid_for(m, 256), 256, 0, s>>>(H.cx.p, V.D.p, H.ccn.p, ne, nv, V.x.p, V.c.p));
+    launch_pdl(k_split_out<T>, grid_for(m, 256), 256, 0, s, H.cx.p, V.D.p, H.ccn.p, ne, nv, V.x.p, V.c.p);
 }
 
 template <typename T>
@@ -618,44 +604,62 @@ static void hiptmair_split(Hierarchy& H, int lev, VLevel<T>& V, int64_t ne, int6
     timed_sgs(H, lev, V.A, V.bp.p, V.x.p, s);
     if (nv > 0) {
         resid(V.A, V.bp.p, V.x.p, V.r.p, s);
-        SPHC_LAUNCH(k_dt_gather<T><<<grid_for(nv, 256), 256, 0, s>>>(V.Dt_rp.p, V.Dt_e.p, nv, V.r.p, V.g.p));
-        SPHC_LAUNCH(k_zero<T><<<grid_for(nv, 256), 256, 0, s>>>(V.dc.p, nv));
+        launch_pdl(k_dt_gather<T>, grid_for(nv, 256), 256, 0, s, V.Dt_rp.p, V.Dt_e.p, nv, V.r.p, V.g.p);
+        launch_pdl(k_zero<T>, grid_for(nv, 256), 256, 0, s, V.dc.p, nv);
         sgs(V.An, V.g.p, V.dc.p, s);
-        SPHC_LAUNCH(k_axpy<T><<<grid_for(nv, 256), 256, 0, s>>>(V.c.p, V.dc.p, nv));
+        launch_pdl(k_axpy<T>, grid_for(nv, 256), 256, 0, s, V.c.p, V.dc.p, nv);
         spmv_v(V.AD, V.dc.p, V.bp.p, 1, s, T(-1));
     }
     timed_sgs(H, lev, V.A, V.bp.p, V.x.p, s);
 }
 
+// per-level section timers of the V-cycle (profile on, outside graph capture)
+static Profiler* vc_prof(Hierarchy& H) { return H.prof.on && !H.capturing ? &H.prof : nullptr; }
+static std::string vc_name(const char* what, int l) { return std::string(what) + "_l" + std::to_string(l); }
+
 template <typename T>
 static void vcycle_split(Hierarchy& H, std::vector<VLevel<T>>& V, int l, cudaStream_t s) {
     int64_t ne = H.L[l].A.nr, nv = H.L[l].An.nr;
+    Profiler* pr = vc_prof(H);
     if (l == H.nlev - 1) {
+        Section sec(pr, "vc_coarsest", s);
         coarse_split(H, V[l], ne, nv, s);
         return;
     }
-    SPHC_LAUNCH(k_zero<T><<<grid_for(ne, 256), 256, 0, s>>>(V[l].x.p, ne));
-    if (nv > 0) SPHC_LAUNCH(k_zero<T><<<grid_for(nv, 256), 256, 0, s>>>(V[l].c.p, nv));
-    SPHC_LAUNCH(k_copy<T><<<grid_for(ne, 256), 256, 0, s>>>(V[l].bp.p, V[l].b.p, ne));
-    hiptmair_split(H, l, V[l], ne, nv, s);
-    resid(V[l].A, V[l].bp.p, V[l].x.p, V[l].r.p, s);
-    spmv_v(V[l].PeT, V[l].r.p, V[l + 1].b.p, 0, s);
-    vcycle_split(H, V, l + 1, s);
-    spmv_v(V[l].Pe, V[l + 1].x.p, V[l].x.p, 1, s);           // y += P_e y_H
-    if (nv > 0) {
-        spmv_v(V[l].Pn, V[l + 1].c.p, V[l].dc.p, 0, s);      // c += P_n c_H  (P_e D_H = D_h P_n)
-        SPHC_LAUNCH(k_axpy<T><<<grid_for(nv, 256), 256, 0, s>>>(V[l].c.p, V[l].dc.p, nv));
-        spmv_v(V[l].AD, V[l].dc.p, V[l].bp.p, 1, s, T(-1));
+    {
+        Section sec(pr, vc_name("vc_pre", l).c_str(), s);
+        launch_pdl(k_zero<T>, grid_for(ne, 256), 256, 0, s, V[l].x.p, ne);
+        if (nv > 0) launch_pdl(k_zero<T>, grid_for(nv, 256), 256, 0, s, V[l].c.p, nv);
+        launch_pdl(k_copy<T>, grid_for(ne, 256), 256, 0, s, V[l].bp.p, V[l].b.p, ne);
+        hiptmair_split(H, l, V[l], ne, nv, s);
     }
-    hiptmair_split(H, l, V[l], ne, nv, s);
+    {
+        Section sec(pr, vc_name("vc_restrict", l).c_str(), s);
+        resid(V[l].A, V[l].bp.p, V[l].x.p, V[l].r.p, s);
+        spmv_v(V[l].PeT, V[l].r.p, V[l + 1].b.p, 0, s);
+    }
+    vcycle_split(H, V, l + 1, s);
+    {
+        Section sec(pr, vc_name("vc_prolong", l).c_str(), s);
+        spmv_v(V[l].Pe, V[l + 1].x.p, V[l].x.p, 1, s);           // y += P_e y_H
+        if (nv > 0) {
+            spmv_v(V[l].Pn, V[l + 1].c.p, V[l].dc.p, 0, s);      // c += P_n c_H  (P_e D_H = D_h P_n)
+            launch_pdl(k_axpy<T>, grid_for(nv, 256), 256, 0, s, V[l].c.p, V[l].dc.p, nv);
+            spmv_v(V[l].AD, V[l].dc.p, V[l].bp.p, 1, s, T(-1));
+        }
+    }
+    {
+        Section sec(pr, vc_name("vc_post", l).c_str(), s);
+        hiptmair_split(H, l, V[l], ne, nv, s);
+    }
 }
 
 int apply_vcycle(Hierarchy& H, const double* r, double* z, cudaStream_t s) {
     int64_t n = H.L[0].A.nr;
     if (H.opts.vcycle_fp32) {
-        SPHC_LAUNCH(k_cast<double, float><<<grid_for(n, 256), 256, 0, s>>>(r, H.V32[0].b.p, n));
+        launch_pdl(k_cast<double, float>, grid_for(n, 256), 256, 0, s, r, H.V32[0].b.p, n);
         vcycle_split<float>(H, H.V32, 0, s);
-        SPHC_LAUNCH(k_combine<float><<<grid_for(n, 256), 256, 0, s>>>(H.V32[0].x.p, H.V32[0].D.p, H.V32[0].c.p, n, z));
+        launch_pdl(k_combine<float>, grid_for(n, 256), 256, 0, s, H.V32[0].x.p, H.V32[0].D.p, H.V32[0].c.p, n, z);
     } else {
         SPHC_CK(cudaMemcpyAsync(H.V64[0].b.p, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
         vcycle_level<double>(H, H.V64, 0, s);
@@ -665,52 +669,68 @@ int apply_vcycle(Hierarchy& H, const double* r, double* z, cudaStream_t s) {
     return SPHC_OK;
 }
 
-// Autotuner: time one forward + backward sweep for each lanes-per-row width and keep the fastest
-// (the operators are stored in CSR with rows grouped by colour, so the tunable shape is the
-// number of lanes that share a row).
+// Autotuner: for every smoother too large for the one-block sweep, build its SELL copy with
+// lanes per row in {l/2, l, 2l} (l from the mean row length) and 1, 2 or 4 entries per lane load,
+// time three forward + backward sweeps of each and keep the fastest shape.
 template <typename T>
-static int autotune_op(SmoothOp<T>& op, DBuf<T>& bvec, DBuf<T>& xvec, cudaStream_t s) {
+static int autotune_op(const DCSR& A, const int32_t* rmap, const int32_t* cmap, const std::vector<int64_t>& cstart,
+                       SmoothOp<T>& op, DBuf<T>& bvec, DBuf<T>& xvec, cudaStream_t s) {
     if (op.n <= SGS_BLOCK_MAX_ROWS || op.n > bvec.n || op.n > xvec.n) return SPHC_OK;
     cudaEvent_t e0, e1;
     SPHC_CK(cudaEventCreate(&e0));
     SPHC_CK(cudaEventCreate(&e1));
-    SPHC_LAUNCH(k_zero<T><<<grid_for(op.n, 256), 256, 0, s>>>(bvec.p, op.n));
+    launch_pdl(k_zero<T>, grid_for(op.n, 256), 256, 0, s, bvec.p, op.n);
+    launch_pdl(k_zero<T>, grid_for(op.n, 256), 256, 0, s, xvec.p, op.n);
+    int l0 = sell_lpr_for(A, (int)cstart.size() - 1);
     float best = 1e30f;
-    int best_sub = 0;
-    for (int sub : {4, 8, 16, 32}) {
-        op.sub = sub;
-        sgs(op, bvec.p, xvec.p, s);                   // warm-up
-        cudaEventRecord(e0, s);
-        for (int rep = 0; rep < 3; ++rep) sgs(op, bvec.p, xvec.p, s);
-        cudaEventRecord(e1, s);
-        SPHC_CK(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best) { best = ms; best_sub = sub; }
+    int best_ch = op.m.ch, best_lpr = op.m.lpr;
+    int rc = SPHC_OK;
+    for (int lpr : {l0 / 2, l0, 2 * l0}) {
+        if (lpr < 1 || lpr > SELL_C) continue;
+        for (int ch : {1, 2, 4}) {
+            if ((ch != op.m.ch || lpr != op.m.lpr) &&
+                (rc = build_smooth<T>(A, rmap, cmap, cstart, ch, lpr, op, s)) != SPHC_OK)
+                break;
+            sgs(op, bvec.p, xvec.p, s);               // warm-up
+            cudaEventRecord(e0, s);
+            for (int rep = 0; rep < 3; ++rep) sgs(op, bvec.p, xvec.p, s);
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) { rc = SPHC_ECUDA; break; }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) { best = ms; best_ch = ch; best_lpr = lpr; }
+        }
+        if (rc != SPHC_OK) break;
     }
-    op.sub = best_sub;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (rc != SPHC_OK) return rc;
+    if (op.m.ch != best_ch || op.m.lpr != best_lpr)
+        SPHC_TRY(build_smooth<T>(A, rmap, cmap, cstart, best_ch, best_lpr, op, s));
+    return SPHC_OK;
+}
+
+template <typename T>
+static int autotune_levels(Hierarchy& H, std::vector<VLevel<T>>& V, cudaStream_t s) {
+    for (int l = 0; l + 1 < H.nlev; ++l) {
+        const Level& L = H.L[l];
+        const LevelOrder& O = H.ord[l];
+        SPHC_TRY(autotune_op<T>(L.A, O.pe.p, O.ie.p, O.ce, V[l].A, V[l].b, V[l].x, s));
+        SPHC_TRY(autotune_op<T>(L.An, O.pn.p, O.in.p, O.cn, V[l].An, V[l].g, V[l].c, s));
+    }
     return SPHC_OK;
 }
 
 int autotune_vcycle(Hierarchy& H, cudaStream_t s) {
-    for (int l = 0; l + 1 < H.nlev; ++l) {
-        if (H.opts.vcycle_fp32) {
-            SPHC_TRY(autotune_op(H.V32[l].A, H.V32[l].b, H.V32[l].x, s));
-            SPHC_TRY(autotune_op(H.V32[l].An, H.V32[l].g, H.V32[l].c, s));
-        } else {
-            SPHC_TRY(autotune_op(H.V64[l].A, H.V64[l].b, H.V64[l].x, s));
-            SPHC_TRY(autotune_op(H.V64[l].An, H.V64[l].g, H.V64[l].c, s));
-        }
-    }
-    return SPHC_OK;
+    if (H.opts.vcycle_fp32) return autotune_levels<float>(H, H.V32, s);
+    return autotune_levels<double>(H, H.V64, s);
 }
 
 // ------------------------------------------------------------------ CG
 // scal: 0 rz, 1 pq, 2 rr, 3 rz_new, 4 z.r_old, 5 bb
 __global__ void k_cg_xr(double* x, double* r, double* rold, const double* p, const double* q, const double* sc,
                         int64_t n, int flexible) {
+    pdl_enter();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double alpha = sc[1] > 0.0 ? sc[0] / sc[1] : 0.0;     // breakdown: leave x unchanged
@@ -719,13 +739,18 @@ __global__ void k_cg_xr(double* x, double* r, double* rold, const double* p, con
     r[i] -= alpha * q[i];
 }
 __global__ void k_cg_p(double* p, const double* z, const double* sc, int64_t n, int flexible) {
+    pdl_enter();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double beta = flexible ? (sc[3] - sc[4]) / sc[0] : sc[3] / sc[0];
     p[i] = z[i] + beta * p[i];
 }
-__global__ void k_cg_shift(double* sc) { sc[0] = sc[3]; }
+__global__ void k_cg_shift(double* sc) {
+    pdl_enter();
+    sc[0] = sc[3];
+}
 __global__ void k_sub(const double* b, double* q, int64_t n) {
+    pdl_enter();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) q[i] = b[i] - q[i];
 }
@@ -733,6 +758,7 @@ __global__ void k_sub(const double* b, double* q, int64_t n) {
 // end of one graph iteration: count it and keep looping while not converged, not broken down
 // and below the iteration cap.  itc[1]: 0 converged, 1 breakdown, 2 cap reached.
 __global__ void k_cg_check(cudaGraphConditionalHandle hnd, const double* sc, int* itc, int max_iter) {
+    pdl_enter();
     int it = itc[0] + 1;
     itc[0] = it;
     double pq = sc[1], rr = sc[2], lim = sc[7];
@@ -742,24 +768,26 @@ __global__ void k_cg_check(cudaGraphConditionalHandle hnd, const double* sc, int
     else if (it >= max_iter) { itc[1] = 2; cont = 0; }
     cudaGraphSetConditional(hnd, cont);
 }
-__global__ void k_set_limit(double* sc, double tol2) { sc[7] = tol2 * sc[5]; }
+__global__ void k_set_limit(double* sc, double tol2) {
+    pdl_enter();
+    sc[7] = tol2 * sc[5];
+}
 
 // one CG iteration after the first: z = M^-1 r, p = z + beta p, q = A p, x += alpha p, r -= alpha q
 static int cg_body(Hierarchy& H, cudaGraphConditionalHandle hnd, cudaStream_t s) {
-    const DCSR& A = H.L[0].A;
-    int64_t n = A.nr;
+    int64_t n = H.L[0].A.nr;
     int flexible = H.opts.flexible;
     double* sc = H.scal.p;
     SPHC_TRY(apply_vcycle(H, H.r.p, H.z.p, s));
     dot_buf(H, H.r.p, H.z.p, n, sc + 3, s);
     if (flexible) dot_buf(H, H.z.p, H.rold.p, n, sc + 4, s);
-    SPHC_LAUNCH(k_cg_p<<<grid_for(n, 256), 256, 0, s>>>(H.p.p, H.z.p, sc, n, flexible));
-    SPHC_LAUNCH(k_cg_shift<<<1, 1, 0, s>>>(sc));
-    SPHC_TRY(spmv64(A, H.p.p, H.q.p, s));
+    launch_pdl(k_cg_p, grid_for(n, 256), 256, 0, s, H.p.p, H.z.p, sc, n, flexible);
+    launch_pdl(k_cg_shift, 1, 1, 0, s, sc);
+    SPHC_TRY(cg_spmv(H, H.p.p, H.q.p, s));
     dot_buf(H, H.p.p, H.q.p, n, sc + 1, s);
-    SPHC_LAUNCH(k_cg_xr<<<grid_for(n, 256), 256, 0, s>>>(H.x.p, H.r.p, H.rold.p, H.p.p, H.q.p, sc, n, flexible));
+    launch_pdl(k_cg_xr, grid_for(n, 256), 256, 0, s, H.x.p, H.r.p, H.rold.p, H.p.p, H.q.p, sc, n, flexible);
     dot_buf(H, H.r.p, H.r.p, n, sc + 2, s);
-    SPHC_LAUNCH(k_cg_check<<<1, 1, 0, s>>>(hnd, sc, H.itc.p, H.opts.max_iter));
+    launch_pdl(k_cg_check, 1, 1, 0, s, hnd, sc, H.itc.p, H.opts.max_iter);
     SPHC_CK(cudaGetLastError());
     return SPHC_OK;
 }
@@ -796,18 +824,34 @@ static int build_cg_graph(Hierarchy& H) {
     return SPHC_OK;
 }
 
+// ||b - A x||^2 into scal[6]; x and bperm in the V-cycle numbering
+static int true_residual(Hierarchy& H, const double* xp, cudaStream_t s) {
+    int64_t n = H.L[0].A.nr;
+    SPHC_TRY(cg_spmv(H, xp, H.q.p, s));
+    launch_pdl(k_sub, grid_for(n, 256), 256, 0, s, H.bperm.p, H.q.p, n);
+    dot_buf(H, H.q.p, H.q.p, n, H.scal.p + 6, s);
+    return SPHC_OK;
+}
+static double read_relres(Hierarchy& H, double bnorm, cudaStream_t s) {
+    double hr = 0.0;
+    cudaMemcpyAsync(&hr, H.scal.p + 6, sizeof(double), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    return bnorm > 0 ? sqrt(hr) / bnorm : 0.0;
+}
+
 // CG on the device: the first iteration is enqueued directly, the rest run inside one graph
-// launch whose while node repeats an iteration until the stopping test holds.
+// launch whose while node repeats an iteration until the stopping test holds.  b and x are in
+// the caller's numbering; the iteration runs in the level-0 V-cycle numbering.
 static int pcg_graph(Hierarchy& H, const double* b, double* x, double tol, cudaStream_t s, int* iters,
                      double* relres) {
-    const DCSR& A = H.L[0].A;
-    int64_t n = A.nr;
+    int64_t n = H.L[0].A.nr;
     int flexible = H.opts.flexible;
     double* sc = H.scal.p;
     SPHC_TRY(build_cg_graph(H));
+    SPHC_TRY(gather64(b, perm0(H), n, H.bperm.p, s));
     SPHC_CK(cudaMemsetAsync(H.x.p, 0, sizeof(double) * n, s));
-    SPHC_CK(cudaMemcpyAsync(H.r.p, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-    dot_buf(H, b, b, n, sc + 5, s);
+    SPHC_CK(cudaMemcpyAsync(H.r.p, H.bperm.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    dot_buf(H, H.bperm.p, H.bperm.p, n, sc + 5, s);
     double hb = 0.0;
     SPHC_CK(cudaMemcpyAsync(&hb, sc + 5, sizeof(double), cudaMemcpyDeviceToHost, s));
     SPHC_CK(cudaStreamSynchronize(s));
@@ -818,13 +862,14 @@ static int pcg_graph(Hierarchy& H, const double* b, double* x, double tol, cudaS
         SPHC_CK(cudaMemcpyAsync(H.p.p, H.z.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
         dot_buf(H, H.r.p, H.z.p, n, sc + 0, s);
         {
-            Section sec(H.prof.on ? &H.prof : nullptr, "spmv_A_fp64", s, (double)A.nnz * 12.0 + (double)n * 24.0);
-            SPHC_TRY(spmv64(A, H.p.p, H.q.p, s));
+            const Sell<double>& A = cg_op(H);
+            Section sec(H.prof.on ? &H.prof : nullptr, "spmv_A_fp64", s, (double)A.nnz * 12.0 + (double)n * 16.0);
+            SPHC_TRY(cg_spmv(H, H.p.p, H.q.p, s));
         }
         dot_buf(H, H.p.p, H.q.p, n, sc + 1, s);
-        SPHC_LAUNCH(k_cg_xr<<<grid_for(n, 256), 256, 0, s>>>(H.x.p, H.r.p, H.rold.p, H.p.p, H.q.p, sc, n, flexible));
+        launch_pdl(k_cg_xr, grid_for(n, 256), 256, 0, s, H.x.p, H.r.p, H.rold.p, H.p.p, H.q.p, sc, n, flexible);
         dot_buf(H, H.r.p, H.r.p, n, sc + 2, s);
-        SPHC_LAUNCH(k_set_limit<<<1, 1, 0, s>>>(sc, tol * tol));
+        launch_pdl(k_set_limit, 1, 1, 0, s, sc, tol * tol);
         int hi[2] = {1, 0};
         SPHC_CK(cudaMemcpyAsync(H.itc.p, hi, 2 * sizeof(int), cudaMemcpyHostToDevice, s));
         double hsc[8];
@@ -843,26 +888,24 @@ static int pcg_graph(Hierarchy& H, const double* b, double* x, double tol, cudaS
             g_launches.fetch_add(H.body_launches * (long long)(it - 1));
         }
     }
-    SPHC_CK(cudaMemcpyAsync(x, H.x.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-    // true residual
-    SPHC_TRY(spmv64(A, H.x.p, H.q.p, s));
-    SPHC_LAUNCH(k_sub<<<grid_for(n, 256), 256, 0, s>>>(b, H.q.p, n));
-    dot_buf(H, H.q.p, H.q.p, n, sc + 6, s);
-    double hr = 0.0;
-    SPHC_CK(cudaMemcpyAsync(&hr, sc + 6, sizeof(double), cudaMemcpyDeviceToHost, s));
-    SPHC_CK(cudaStreamSynchronize(s));
+    SPHC_TRY(scatter64(H.x.p, perm0(H), n, x, s));
+    SPHC_TRY(true_residual(H, H.x.p, s));
+    double rr = read_relres(H, bnorm, s);
+    SPHC_CK(cudaGetLastError());
     if (iters) *iters = it;
-    if (relres) *relres = bnorm > 0 ? sqrt(hr) / bnorm : 0.0;
+    if (relres) *relres = rr;
     if (status == SPHC_EBREAKDOWN) set_error("CG breakdown after %d iterations", it);
     else if (status == SPHC_ENOTCONV) set_error("CG did not reach the tolerance in %d iterations", it);
     return status;
 }
 
 // ------------------------------------------------------------------ CG captured whole (batched solves)
-// The right side is read from H.bin and tol^2 from scal[8]; x stays in H.x.  Every iteration
-// (V-cycle first) runs inside a while node whose condition a prologue kernel sets, so the whole
-// solve needs no host decision and can be one branch of a larger graph.
+// The right side is read from H.bin and tol^2 from scal[8]; the solution is left in H.xo (both
+// in the caller's numbering).  Every iteration (V-cycle first) runs inside a while node whose
+// condition a prologue kernel sets, so the whole solve needs no host decision and can be one
+// branch of a larger graph.
 __global__ void k_cg_prep(cudaGraphConditionalHandle hnd, double* sc, int* itc) {
+    pdl_enter();
     sc[7] = sc[8] * sc[5];
     sc[0] = 1.0;                         // rz of the previous iteration (p = 0 makes beta irrelevant)
     itc[0] = 0;
@@ -871,37 +914,36 @@ __global__ void k_cg_prep(cudaGraphConditionalHandle hnd, double* sc, int* itc) 
 }
 
 static int cg_iter_body(Hierarchy& H, cudaGraphConditionalHandle hnd, cudaStream_t s) {
-    const DCSR& A = H.L[0].A;
-    int64_t n = A.nr;
+    int64_t n = H.L[0].A.nr;
     int flexible = H.opts.flexible;
     double* sc = H.scal.p;
     SPHC_TRY(apply_vcycle(H, H.r.p, H.z.p, s));
     dot_buf(H, H.r.p, H.z.p, n, sc + 3, s);
     if (flexible) dot_buf(H, H.z.p, H.rold.p, n, sc + 4, s);
-    SPHC_LAUNCH(k_cg_p<<<grid_for(n, 256), 256, 0, s>>>(H.p.p, H.z.p, sc, n, flexible));
-    SPHC_LAUNCH(k_cg_shift<<<1, 1, 0, s>>>(sc));
-    SPHC_TRY(spmv64(A, H.p.p, H.q.p, s));
+    launch_pdl(k_cg_p, grid_for(n, 256), 256, 0, s, H.p.p, H.z.p, sc, n, flexible);
+    launch_pdl(k_cg_shift, 1, 1, 0, s, sc);
+    SPHC_TRY(cg_spmv(H, H.p.p, H.q.p, s));
     dot_buf(H, H.p.p, H.q.p, n, sc + 1, s);
-    SPHC_LAUNCH(k_cg_xr<<<grid_for(n, 256), 256, 0, s>>>(H.x.p, H.r.p, H.rold.p, H.p.p, H.q.p, sc, n, flexible));
+    launch_pdl(k_cg_xr, grid_for(n, 256), 256, 0, s, H.x.p, H.r.p, H.rold.p, H.p.p, H.q.p, sc, n, flexible);
     dot_buf(H, H.r.p, H.r.p, n, sc + 2, s);
-    SPHC_LAUNCH(k_cg_check<<<1, 1, 0, s>>>(hnd, sc, H.itc.p, H.opts.max_iter));
+    launch_pdl(k_cg_check, 1, 1, 0, s, hnd, sc, H.itc.p, H.opts.max_iter);
     SPHC_CK(cudaGetLastError());
     return SPHC_OK;
 }
 
 // Append the whole CG of H to the graph being captured on stream s.
 int capture_cg(Hierarchy& H, cudaStream_t s) {
-    const DCSR& A = H.L[0].A;
-    int64_t n = A.nr;
+    int64_t n = H.L[0].A.nr;
     double* sc = H.scal.p;
     if (!H.cap_stream) SPHC_CK(cudaStreamCreateWithFlags(&H.cap_stream, cudaStreamNonBlocking));
     H.capturing = true;
     long long lstart = g_launches.load();
-    SPHC_CK(cudaMemcpyAsync(H.r.p, H.bin.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    SPHC_TRY(gather64(H.bin.p, perm0(H), n, H.bperm.p, s));
+    SPHC_CK(cudaMemcpyAsync(H.r.p, H.bperm.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     SPHC_CK(cudaMemsetAsync(H.x.p, 0, sizeof(double) * n, s));
     SPHC_CK(cudaMemsetAsync(H.p.p, 0, sizeof(double) * n, s));
     SPHC_CK(cudaMemsetAsync(H.rold.p, 0, sizeof(double) * n, s));
-    dot_buf(H, H.bin.p, H.bin.p, n, sc + 5, s);
+    dot_buf(H, H.bperm.p, H.bperm.p, n, sc + 5, s);
     cudaStreamCaptureStatus st;
     cudaGraph_t g;
     const cudaGraphNode_t* deps = nullptr;
@@ -909,7 +951,7 @@ int capture_cg(Hierarchy& H, cudaStream_t s) {
     SPHC_CK(cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, nullptr, &ndeps));
     cudaGraphConditionalHandle hnd;
     SPHC_CK(cudaGraphConditionalHandleCreate(&hnd, g, 0, 0));
-    SPHC_LAUNCH(k_cg_prep<<<1, 1, 0, s>>>(hnd, sc, H.itc.p));
+    launch_pdl(k_cg_prep, 1, 1, 0, s, hnd, sc, H.itc.p);
     SPHC_CK(cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, nullptr, &ndeps));
     cudaGraphNodeParams np = {};
     np.type = cudaGraphNodeTypeConditional;
@@ -933,10 +975,8 @@ int capture_cg(Hierarchy& H, cudaStream_t s) {
         set_error("CG body capture failed: %s", cudaGetErrorString(e));
         return SPHC_ECUDA;
     }
-    // true residual
-    SPHC_TRY(spmv64(A, H.x.p, H.q.p, s));
-    SPHC_LAUNCH(k_sub<<<grid_for(n, 256), 256, 0, s>>>(H.bin.p, H.q.p, n));
-    dot_buf(H, H.q.p, H.q.p, n, sc + 6, s);
+    SPHC_TRY(scatter64(H.x.p, perm0(H), n, H.xo.p, s));
+    SPHC_TRY(true_residual(H, H.x.p, s));
     H.capturing = false;
     H.branch_launches = g_launches.load() - lstart;   // counted when the graph runs
     g_launches.fetch_sub(H.branch_launches);
@@ -944,15 +984,16 @@ int capture_cg(Hierarchy& H, cudaStream_t s) {
     return SPHC_OK;
 }
 
+// CG with a host decision per iteration (no graph)
 int pcg_solve(Hierarchy& H, const double* b, double* x, double tol, cudaStream_t s, int* iters, double* relres) {
     if (H.opts.cg_graph) return pcg_graph(H, b, x, tol, s, iters, relres);
-    const DCSR& A = H.L[0].A;
-    int64_t n = A.nr;
+    int64_t n = H.L[0].A.nr;
     int flexible = H.opts.flexible;
     double* sc = H.scal.p;
-    SPHC_CK(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
-    SPHC_CK(cudaMemcpyAsync(H.r.p, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-    SPHC_TRY(dot64(b, b, n, sc + 5, s));
+    SPHC_TRY(gather64(b, perm0(H), n, H.bperm.p, s));
+    SPHC_CK(cudaMemsetAsync(H.x.p, 0, sizeof(double) * n, s));
+    SPHC_CK(cudaMemcpyAsync(H.r.p, H.bperm.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    SPHC_TRY(dot64(H.bperm.p, H.bperm.p, n, sc + 5, s));
     double hb = 0.0;
     SPHC_CK(cudaMemcpyAsync(&hb, sc + 5, sizeof(double), cudaMemcpyDeviceToHost, s));
     SPHC_CK(cudaStreamSynchronize(s));
@@ -964,13 +1005,14 @@ int pcg_solve(Hierarchy& H, const double* b, double* x, double tol, cudaStream_t
         SPHC_CK(cudaMemcpyAsync(H.p.p, H.z.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
         SPHC_TRY(dot64(H.r.p, H.z.p, n, sc + 0, s));
         double hsc[6];
-        int tid = H.prof.on ? H.prof.find("spmv_A_fp64", (double)A.nnz * 12.0 + (double)n * 24.0) : -1;
+        const Sell<double>& A = cg_op(H);
+        int tid = H.prof.on ? H.prof.find("spmv_A_fp64", (double)A.nnz * 12.0 + (double)n * 16.0) : -1;
         for (it = 0; it < H.opts.max_iter;) {
             if (tid >= 0) H.prof.begin(tid, s);
-            SPHC_TRY(spmv64(A, H.p.p, H.q.p, s));
+            SPHC_TRY(cg_spmv(H, H.p.p, H.q.p, s));
             if (tid >= 0) H.prof.end(tid, s);
             SPHC_TRY(dot64(H.p.p, H.q.p, n, sc + 1, s));
-            SPHC_LAUNCH(k_cg_xr<<<grid_for(n, 256), 256, 0, s>>>(x, H.r.p, H.rold.p, H.p.p, H.q.p, sc, n, flexible));
+            launch_pdl(k_cg_xr, grid_for(n, 256), 256, 0, s, H.x.p, H.r.p, H.rold.p, H.p.p, H.q.p, sc, n, flexible);
             ++it;
             SPHC_TRY(dot64(H.r.p, H.r.p, n, sc + 2, s));
             SPHC_CK(cudaMemcpyAsync(hsc, sc, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -980,24 +1022,30 @@ int pcg_solve(Hierarchy& H, const double* b, double* x, double tol, cudaStream_t
             SPHC_TRY(apply_vcycle(H, H.r.p, H.z.p, s));
             SPHC_TRY(dot64(H.r.p, H.z.p, n, sc + 3, s));
             if (flexible) SPHC_TRY(dot64(H.z.p, H.rold.p, n, sc + 4, s));
-            SPHC_LAUNCH(k_cg_p<<<grid_for(n, 256), 256, 0, s>>>(H.p.p, H.z.p, sc, n, flexible));
-            SPHC_LAUNCH(k_cg_shift<<<1, 1, 0, s>>>(sc));
+            launch_pdl(k_cg_p, grid_for(n, 256), 256, 0, s, H.p.p, H.z.p, sc, n, flexible);
+            launch_pdl(k_cg_shift, 1, 1, 0, s, sc);
         }
     }
-    // true residual
-    SPHC_TRY(spmv64(A, x, H.q.p, s));
-    SPHC_LAUNCH(k_sub<<<grid_for(n, 256), 256, 0, s>>>(b, H.q.p, n));
-    SPHC_TRY(dot64(H.q.p, H.q.p, n, sc + 6, s));
-    double hr = 0.0;
-    SPHC_CK(cudaMemcpyAsync(&hr, sc + 6, sizeof(double), cudaMemcpyDeviceToHost, s));
-    SPHC_CK(cudaStreamSynchronize(s));
+    SPHC_TRY(scatter64(H.x.p, perm0(H), n, x, s));
+    SPHC_TRY(true_residual(H, H.x.p, s));
+    double rr = read_relres(H, bnorm, s);
+    SPHC_CK(cudaGetLastError());
     if (iters) *iters = it;
-    if (relres) *relres = bnorm > 0 ? sqrt(hr) / bnorm : 0.0;
+    if (relres) *relres = rr;
     if (status != SPHC_OK && status != SPHC_ENOTCONV)
         set_error("CG breakdown after %d iterations", it);
     else if (status == SPHC_ENOTCONV)
         set_error("CG did not reach the tolerance in %d iterations", it);
     return status;
+}
+
+// z = M^-1 r with r and z in the caller's numbering
+int apply_vcycle_user(Hierarchy& H, const double* r, double* z, cudaStream_t s) {
+    int64_t n = H.L[0].A.nr;
+    SPHC_TRY(gather64(r, perm0(H), n, H.q.p, s));
+    SPHC_TRY(apply_vcycle(H, H.q.p, H.z.p, s));
+    SPHC_TRY(scatter64(H.z.p, perm0(H), n, z, s));
+    return SPHC_OK;
 }
 
 }  // namespace sphc

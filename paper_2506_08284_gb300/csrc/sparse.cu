@@ -3,6 +3,7 @@
 // products P_e^T A_e P_e, P_n^T A_n P_n of Sec. 2), FP64 SpMV and deterministic dots.
 #include <cstdarg>
 #include <cstdio>
+#include <mutex>
 
 #include "sphc_internal.cuh"
 
@@ -10,6 +11,32 @@ namespace sphc {
 
 bool g_sync_free = false;
 std::atomic<long long> g_launches{0};
+
+static std::mutex g_pool_mutex;
+static cudaMemPool_t g_pools[64] = {};
+cudaMemPool_t device_pool() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lock(g_pool_mutex);
+    if (!g_pools[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        uint64_t keep = ~0ULL;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        g_pools[dev] = pool;
+    }
+    return g_pools[dev];
+}
 static thread_local std::string g_err;
 void set_error(const char* fmt, ...) {
     char buf[1024];

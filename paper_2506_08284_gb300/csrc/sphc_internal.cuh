@@ -40,12 +40,41 @@ extern std::atomic<long long> g_launches;
         __VA_ARGS__;                                                       \
     } while (0)
 
+// Programmatic dependent launch: a kernel launched this way may be scheduled while the previous
+// kernel of the stream drains, hiding the launch latency of the short kernels of a V-cycle.
+// Every kernel launched with launch_pdl calls pdl_enter() first: it waits until the previous
+// kernel has completed and its writes are visible, then lets the next kernel be scheduled.
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+template <typename... P, typename... A>
+inline void launch_pdl(void (*k)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    ::sphc::g_launches.fetch_add(1, std::memory_order_relaxed);
+    cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...);
+}
+
 // ------------------------------------------------------------------ stream-ordered buffers
-// Every device buffer of the library comes from cudaMallocAsync on the caller's stream and is
-// released with cudaFreeAsync on the same stream.
+// Every device buffer of the library comes from the library's own memory pool of the current
+// device (cudaMallocFromPoolAsync on the caller's stream) and is released with cudaFreeAsync on
+// the same stream.  The pool keeps freed memory mapped (release threshold: unlimited), so a
+// setup that follows another reuses its memory instead of mapping it again; sphc_trim_memory
+// returns it to the driver.
 // When set (only while a handle is destroyed), buffers are released with the synchronous
 // cudaFree so that no stream of the caller needs to be alive at that point.
 extern bool g_sync_free;
+// the library's pool of the current device (null if it could not be created)
+cudaMemPool_t device_pool();
 
 template <typename T>
 struct DBuf {
@@ -78,7 +107,9 @@ struct DBuf {
         s = stream;
         n = count;
         if (count <= 0) return SPHC_OK;
-        cudaError_t e = cudaMallocAsync((void**)&p, sizeof(T) * (size_t)count, stream);
+        cudaMemPool_t pool = device_pool();
+        cudaError_t e = pool ? cudaMallocFromPoolAsync((void**)&p, sizeof(T) * (size_t)count, pool, stream)
+                             : cudaMallocAsync((void**)&p, sizeof(T) * (size_t)count, stream);
         if (e != cudaSuccess) {
             p = nullptr;
             n = 0;

@@ -12,20 +12,37 @@ constexpr int LOC_WARPS = 4;
 // A smoothed nodal-prolongator row whose sum does not exceed this keeps its tentative values.
 constexpr double SA_MIN_ROWSUM = 0.125;
 
-// Operator of one smoother: rows grouped by colour (row k of the copy is row perm[k] of the
-// level operator), columns in natural numbering, int32 row pointers.
+// Sliced ELLPACK for one warp per slice.  A slice holds R = 32 / lpr consecutive rows (never
+// across a colour boundary: srow[s] .. srow[s+1]) and lpr lanes share a row.  The slice is a
+// dense block of width W (a multiple of lpr * ch): chunk k = j / ch of row q (ch consecutive
+// entries j) belongs to lane q * lpr + k % lpr at step k / lpr and sits at
+// soff[s] + ((k / lpr) * 32 + q * lpr + k % lpr) * ch + j % ch, so every step of the warp reads
+// 32 * ch consecutive entries and every lane receives ch entries of its own row.  Rows shorter
+// than W are padded with value 0 and a valid column index.
+constexpr int SELL_C = 32;
+template <typename T>
+struct Sell {
+    int64_t nr = 0, nc = 0, nnz = 0, nslice = 0, stored = 0;
+    int ch = 4;                      // entries a lane loads at once (1, 2 or 4)
+    int lpr = 1;                     // lanes per row (1, 2, 4, 8, 16 or 32)
+    DBuf<int64_t> soff;              // nslice + 1
+    DBuf<int32_t> srow;              // nslice + 1
+    DBuf<int32_t> ci;
+    DBuf<T> v;
+};
+
+// Operator of one smoother in the level's V-cycle numbering (rows grouped by colour).
 template <typename T>
 struct SmoothOp {
     int64_t n = 0, nnz = 0;
     int ncolor = 0;
-    int sub = 0;                     // lanes per row (0: chosen from the mean row length)
-    std::vector<int64_t> cstart;     // colour c owns copy rows [cstart[c], cstart[c+1])
-    DBuf<int64_t> cstart_dev;
-    DBuf<int32_t> rp, ci, perm;
-    DBuf<T> v, dinv;
+    std::vector<int64_t> cslice;     // colour c owns slices [cslice[c], cslice[c+1])
+    DBuf<int64_t> cslice_dev;
+    Sell<T> m;
+    DBuf<T> dinv;
 };
 
-// Plain CSR in the V-cycle precision (transfers).
+// Plain CSR in the V-cycle precision.
 template <typename T>
 struct VCSR {
     int64_t nr = 0, nc = 0, nnz = 0;
@@ -33,14 +50,32 @@ struct VCSR {
     DBuf<T> v;
 };
 
+// Operator only multiplied (transfers, A D): SELL when its rows pad well, CSR otherwise.
+template <typename T>
+struct XOp {
+    int64_t nr = 0, nc = 0, nnz = 0;
+    bool sell = false;
+    Sell<T> s;
+    VCSR<T> c;
+};
+
+// Renumbering of one level's edges and nodes for the V-cycle: colour by colour, and inside a
+// colour by row length (stable), so that a colour sweep reads its rows, right sides and iterates
+// contiguously and a slice of 32 rows pads little.  p: new -> old, i: old -> new.  Empty on the
+// coarsest level (identity).
+struct LevelOrder {
+    DBuf<int32_t> pe, ie, pn, in;
+    std::vector<int64_t> ce, cn;     // colour starts in the new numbering
+};
+
 template <typename T>
 struct VLevel {
     SmoothOp<T> A, An;
     DBuf<int2> D;                    // per edge: (node with -1, node with +1), -1 if absent
     DBuf<int32_t> Dt_rp, Dt_e;       // D^T: per node the incident edges, (edge << 1) | (coef < 0)
-    VCSR<T> Pe, PeT;
+    XOp<T> Pe, PeT;
     // split iterate x = y + D c (FP32 V-cycle): A D formed in FP64 and P_n
-    VCSR<T> AD, Pn;
+    XOp<T> AD, Pn;
     DBuf<T> x, b, r, g, c, bp, dc;
 };
 
@@ -92,6 +127,9 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
 int level_features(const Level& L, const DBuf<double>& Xc, int lev, float* F, cudaStream_t s);
 // mlp.cu
 int mlp_predict(const float* params_dev, const float* X, int64_t m, float* out, cudaStream_t s);
+struct FeatArgs;
+// features of every pattern entry of a level computed on the fly and fed to the MLP (no feature buffer)
+int mlp_predict_level(const float* params_dev, const FeatArgs& g, float* out, cudaStream_t s);
 
 // Scoped section timer (no-op when prof is null).
 struct Section {
@@ -119,10 +157,14 @@ struct Hierarchy {
     int64_t n_coarse = 0, n_coarse_nodes = 0;
     DBuf<double> cgn, ccn;           // coarsest nodal work vectors (FP64)
     // V-cycle copies in the chosen precision
+    std::vector<LevelOrder> ord;
     std::vector<VLevel<float>> V32;
     std::vector<VLevel<double>> V64;
+    Sell<double> A0;                 // level-0 operator for CG in the V-cycle numbering (FP32 V-cycle)
     // CG work vectors (FP64)
-    DBuf<double> x, r, z, p, q, rold, scal, bin;
+    // (CG runs in the level-0 V-cycle numbering; bperm is b in that numbering, xo the batched
+    // solution scattered back to the caller's numbering)
+    DBuf<double> x, r, z, p, q, rold, scal, bin, bperm, xo;
     DBuf<double> cb, cx;             // coarsest right side / solution (FP64)
     // CG as one CUDA graph: a device-side while loop (conditional node) around one iteration
     DBuf<double> dpart;              // partial sums of the dot products
@@ -146,7 +188,30 @@ struct Hierarchy {
 };
 
 int build_vcycle_ops(Hierarchy& H, cudaStream_t s);
+// layout.cu
+int stable_partition(const int32_t* key, int64_t n, int nkeys, DBuf<int32_t>& perm, std::vector<int64_t>& kstart,
+                     cudaStream_t s);
+int level_order(const DCSR& A, const int32_t* color, int ncolor, DBuf<int32_t>& p, DBuf<int32_t>& ip,
+                std::vector<int64_t>& cstart, cudaStream_t s);
+template <typename T>
+int build_sell(const DCSR& A, const int32_t* rmap, const int32_t* cmap, const std::vector<int64_t>& seg, int ch,
+               int lpr, Sell<T>& S, T* dinv, std::vector<int64_t>* segslice, cudaStream_t s);
+template <typename T>
+int build_csr_perm(const DCSR& A, const int32_t* rmap, const int32_t* cmap, VCSR<T>& B, cudaStream_t s);
+template <typename T>
+int build_xop(const DCSR& A, const int32_t* rmap, const int32_t* cmap, XOp<T>& X, cudaStream_t s);
+template <typename T>
+int build_smooth(const DCSR& A, const int32_t* rmap, const int32_t* cmap, const std::vector<int64_t>& cstart, int ch,
+                 int lpr, SmoothOp<T>& op, cudaStream_t s);
+int sell_lpr_for(const DCSR& A, int ncolor);
+int sell_pick_ch(const DCSR& A, const int32_t* rmap, const std::vector<int64_t>& seg, int lpr, cudaStream_t s, int* ch);
+int build_d_pairs(const DCSR& D, const int32_t* pe, const int32_t* in, DBuf<int2>& out, cudaStream_t s);
+int build_dt_enc(const DCSR& Dt, const int32_t* pn, const int32_t* ie, DBuf<int32_t>& rp, DBuf<int32_t>& enc,
+                 cudaStream_t s);
+int gather64(const double* src, const int32_t* p, int64_t n, double* dst, cudaStream_t s);
+int scatter64(const double* src, const int32_t* p, int64_t n, double* dst, cudaStream_t s);
 int apply_vcycle(Hierarchy& H, const double* r, double* z, cudaStream_t s);
+int apply_vcycle_user(Hierarchy& H, const double* r, double* z, cudaStream_t s);
 int pcg_solve(Hierarchy& H, const double* b, double* x, double tol, cudaStream_t s, int* iters, double* relres);
 int capture_cg(Hierarchy& H, cudaStream_t s);
 int autotune_vcycle(Hierarchy& H, cudaStream_t s);

@@ -57,7 +57,9 @@ class sphc_level_info(ctypes.Structure):
                 ("n_colors_edge", ctypes.c_int32), ("n_colors_node", ctypes.c_int32),
                 ("n_added_edges", ctypes.c_int64), ("n_rows_unsmoothed", ctypes.c_int64),
                 ("rho", ctypes.c_double), ("omega_sa", ctypes.c_double), ("max_pattern_row", ctypes.c_int64),
-                ("max_T_row", ctypes.c_int64)]
+                ("max_T_row", ctypes.c_int64), ("sell_lpr_edge", ctypes.c_int32), ("sell_ch_edge", ctypes.c_int32),
+                ("sell_lpr_node", ctypes.c_int32), ("sell_ch_node", ctypes.c_int32),
+                ("sell_stored_edge", ctypes.c_int64), ("sell_stored_node", ctypes.c_int64)]
 
 
 class sphc_stats(ctypes.Structure):
@@ -75,7 +77,7 @@ EXPORTED = ["sphc_default_opts", "sphc_setup", "sphc_solve", "sphc_vcycle", "sph
             "sphc_get_level_info", "sphc_export_size", "sphc_export", "sphc_destroy", "sphc_last_error",
             "sphc_get_profile", "sphc_launch_count", "sphc_relres_noalloc", "sphc_default_train_opts",
             "sphc_mlp_train", "sphc_mlp_predict", "sphc_mlp_gradient", "sphc_export_features",
-            "sphc_setup_batched", "sphc_solve_batched", "sphc_batch_destroy"]
+            "sphc_setup_batched", "sphc_solve_batched", "sphc_batch_destroy", "sphc_trim_memory"]
 
 _lib = None
 
@@ -101,6 +103,7 @@ def load(path: str | None = None):
     lib.sphc_destroy.restype = None
     lib.sphc_get_profile.argtypes = [P, ctypes.POINTER(sphc_timer), I, ctypes.POINTER(I)]
     lib.sphc_relres_noalloc.argtypes = [P, P, P, I, P, P]
+    lib.sphc_trim_memory.argtypes = [I, ctypes.c_uint64]
     lib.sphc_default_train_opts.argtypes = [ctypes.POINTER(sphc_train_opts)]
     lib.sphc_mlp_train.argtypes = [P, P, I64, ctypes.POINTER(sphc_train_opts), P, P, P]
     lib.sphc_mlp_predict.argtypes = [P, P, I64, P, P]
@@ -333,6 +336,11 @@ def setup_batched(systems, opts=None, stream=None) -> Batch:
 
 def launch_count() -> int:
     return int(load().sphc_launch_count())
+
+
+def trim_memory(device: int = 0, keep_bytes: int = 0) -> int:
+    """Return the device memory the library caches beyond keep_bytes to the driver."""
+    return int(load().sphc_trim_memory(int(device), int(keep_bytes)))
 
 
 def setup(A, D, coords=None, sigma_edge=None, opts=None, stream=None) -> Handle:
