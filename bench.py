@@ -48,7 +48,32 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="run CG with a host loop instead of the CUDA graph (same kernels; for profilers "
+                         "that cannot see kernels inside graphs with conditional nodes)")
     return ap.parse_args()
+
+
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sgs_level0_traffic_kuhn128.txt")
+
+
+def sweep_traffic():
+    """DRAM bytes of one level-0 forward + backward sweep from the committed ncu capture, or None
+    when the kernel source has changed since the counters were taken."""
+    import hashlib
+    try:
+        fields = {}
+        for line in open(TRAFFIC_FILE):
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                fields[k.strip()] = v.strip()
+        src = os.path.join(ROOT, "paper_2506_08284_gb300", "csrc", "solve.cu")
+        digest = hashlib.sha1(open(src, "rb").read()).hexdigest()
+        if fields.get("solve_cu_sha1") != digest:
+            return None
+        return float(fields["dram_bytes_per_sweep"])
+    except Exception:
+        return None
 
 
 def peaks():
@@ -161,7 +186,13 @@ def run_reference(args, rank):
 
 
 # ------------------------------------------------------------------ GPU arm
-def make_opts(pkg, variant, weights, profile):
+def make_opts(pkg, variant, weights, profile, graph=True):
+    o = _make_opts(pkg, variant, weights, profile)
+    o.cg_graph = 1 if graph else 0
+    return o
+
+
+def _make_opts(pkg, variant, weights, profile):
     """headline: FP32 V-cycle + learned warm start (one energy-minimisation step after it);
     fp32_plain: FP32 V-cycle, plain least-norm P0 + one step; fp64_plain: the same in FP64."""
     if variant == "headline" and weights is not None:
@@ -244,7 +275,7 @@ def main():
         return ms, wall, launches, clocks, res
 
     # headline: FP32 V-cycle + learned warm start
-    opts = make_opts(pkg, "headline", weights, 1)
+    opts = make_opts(pkg, "headline", weights, 1, not args.no_graph)
     ms, wall, launches, clocks, results = timed(opts, args.steps, args.warmup, sample_clocks=True)
     sec_per_system = ms / 1e3 / (args.steps * world)
     rc, iters, relres, prof, st, info = results[-1]
@@ -253,7 +284,7 @@ def main():
     comparators = {}
     if not args.no_compare:
         for name in ("fp32_plain", "fp64_plain"):
-            cms, _, _, _, cres = timed(make_opts(pkg, name, weights, 0), max(1, min(args.steps, 2)), 1)
+            cms, _, _, _, cres = timed(make_opts(pkg, name, weights, 0, not args.no_graph), max(1, min(args.steps, 2)), 1)
             c_rc, c_it, c_rr, _, c_st, _ = cres[-1]
             comparators[name] = {"s": cms / 1e3 / (max(1, min(args.steps, 2)) * world), "iters": c_it,
                                  "relres": c_rr, "status": c_rc, "setup_ms": c_st["setup_ms"],
@@ -268,7 +299,7 @@ def main():
         Dh = (p.n_edges, p.n_nodes, pin(p.D_rowptr), pin(p.D_col), pin(p.D_val))
         ch, sh, bh = pin(p.coords), pin(p.sigma_edge), pin(b)
         xh = torch.zeros(p.n_edges, dtype=torch.float64).pin_memory()
-        o2 = make_opts(pkg, "headline", weights, 0)
+        o2 = make_opts(pkg, "headline", weights, 0, not args.no_graph)
         step(o2, Ah, Dh, ch, sh, bh, xh)
         torch.cuda.synchronize()
         t1 = time.perf_counter()
@@ -293,7 +324,7 @@ def main():
         roof = {"bound": "hbm", "kernel": "k_sell_sgs<float> (level-0 forward+backward multicolour SGS sweep, "
                                           "SELL-32, one launch per colour and direction)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "peak_kind": f"{peak_kind} HBM copy", "traffic": None,
+                "peak_kind": f"{peak_kind} HBM copy", "traffic": sweep_traffic(),
                 "algorithmic_bytes_per_launch": prof[name]["bytes_per_call"], "ms_per_launch": t_call * 1e3}
         sp = prof.get("spmv_A_fp64")
         if sp and sp["calls"] > 0:

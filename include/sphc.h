@@ -79,9 +79,10 @@ typedef struct {
 /* Learned warm start (not part of the paper).  For every pattern entry (i, j) of P_e a
  * multilayer perceptron maps SPHC_MLP_NFEAT local features (fine- and coarse-edge geometry
  * relative to the fine edge length, the constraint values r_i, the P_n entries of the fine
- * edge's ends, the least-norm initial value, row sizes, A_e row scaling, log10 sigma, level) to
- * a correction of the least-norm initial guess.  The correction is projected onto the null
- * space of the row's commuting constraints, so P_e D_H = D_h P_n holds exactly as without it.
+ * edge's ends, row sizes, A_e row scaling, log10 sigma, level; feature 19 is unused and 0) to a
+ * correction c of the least-norm initial guess.  The initial guess is then the point of the
+ * row's constraint set nearest to c, i.e. P0 + (I - G (G^T G)^-1 G^T) c, computed in the same
+ * local solve as P0, so P_e D_H = D_h P_n holds exactly as without it.
  * Parameters (floats, in this order): feature means [32], feature scales [32],
  * W1 [32 x 128] (row = input), b1 [128], W2 [128 x 128], b2 [128], w3 [128], b3. */
 #define SPHC_MLP_NFEAT 32

@@ -11,7 +11,7 @@ struct FeatArgs {
     int lev = 0;
     const int64_t* drp = nullptr; const int32_t* dci = nullptr; const double* dv = nullptr;   // D_h
     const int64_t* trp = nullptr; const int32_t* tci = nullptr; const double* tv = nullptr;   // T = |D_h| |P_n|
-    const int64_t* nrp = nullptr; const int32_t* nci = nullptr; const double* p0 = nullptr;   // pattern, P0
+    const int64_t* nrp = nullptr; const int32_t* nci = nullptr;                               // pattern N
     const int64_t* hrp = nullptr; const int32_t* hci = nullptr; const double* hv = nullptr;   // D_H
     const int64_t* prp = nullptr; const int32_t* pci = nullptr; const double* pv = nullptr;   // P_n
     const int64_t* arp = nullptr; const int32_t* aci = nullptr; const double* av = nullptr;   // A_e
@@ -27,7 +27,7 @@ inline FeatArgs feat_args(const Level& L, const DBuf<double>& Xc, int lev) {
     g.lev = lev;
     g.drp = L.D.rp.p; g.dci = L.D.ci.p; g.dv = L.D.v.p;
     g.trp = L.T.rp.p; g.tci = L.T.ci.p; g.tv = L.T.v.p;
-    g.nrp = L.P0.rp.p; g.nci = L.P0.ci.p; g.p0 = L.P0.v.p;
+    g.nrp = L.P0.rp.p; g.nci = L.P0.ci.p;
     g.hrp = L.DH.rp.p; g.hci = L.DH.ci.p; g.hv = L.DH.v.p;
     g.prp = L.Pn.rp.p; g.pci = L.Pn.ci.p; g.pv = L.Pn.v.p;
     g.arp = L.A.rp.p; g.aci = L.A.ci.p; g.av = L.A.v.p;
@@ -90,7 +90,8 @@ __device__ inline void entry_features(const FeatArgs& g, int64_t i, int64_t q, f
     f[16] = jb >= 0 ? (float)row_lookup(g.prp, g.pci, g.pv, u, jb) : 0.f;
     f[17] = ja >= 0 ? (float)row_lookup(g.prp, g.pci, g.pv, v, ja) : 0.f;
     f[18] = jb >= 0 ? (float)row_lookup(g.prp, g.pci, g.pv, v, jb) : 0.f;
-    f[19] = (float)g.p0[q];
+    // f[19] stays 0: the features are computed before P0 exists (the network's output is
+    // projected onto the constraints by the same kernel that computes P0)
     double aii = 0.0, l1 = 0.0;
     for (int64_t k = g.arp[i]; k < g.arp[i + 1]; ++k) {
         double x = g.av[k];

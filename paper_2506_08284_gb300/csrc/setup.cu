@@ -671,34 +671,45 @@ __device__ void refine_solve(LocalSys& S, int k, int np) {
 
 // least-norm initial guess P0_i = G~ (G~^T G~)^-1 r~_i
 __global__ void __launch_bounds__(LOC_WARPS * 32)
-k_p0(int64_t ne, const int64_t* trp, const int32_t* tci, const double* tv, const int64_t* nrp, const int32_t* nci,
-     const int64_t* hrp, const int32_t* hci, const double* hv, double* p0, int* fail, unsigned long long* hist) {
+k_p0(int64_t ne, const int32_t* rows, const int64_t* trp, const int32_t* tci, const double* tv, const int64_t* nrp,
+     const int32_t* nci, const int64_t* hrp, const int32_t* hci, const double* hv, const float* d, double* p0,
+     int* fail) {
     extern __shared__ unsigned char smem_raw[];
     int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     LocalSys& S = ((LocalSys*)smem_raw)[w];
     int64_t i = (int64_t)blockIdx.x * LOC_WARPS + w;
     if (i >= ne) return;
+    if (rows) i = rows[i];
     int m, np;
     int k = local_setup(S, i, trp, tci, tv, nrp, nci, hrp, hci, hv, &m, &np);
     if (np == 0) return;
     if (k < 0) { if (lane == 0) atomicAdd(fail, 1); return; }
-    if (lane < k) S.rhs[lane] = S.r[lane];
+    int64_t n0 = nrp[i];
+    // p = d + G~ z with (G~^T G~) z = r~ - G~^T d: the point of {G~^T p = r~} nearest to d
+    // (d = 0: the least-norm solution; d = the MLP correction: P0 + (I - G~ (G~^T G~)^-1 G~^T) d)
+    double dt[MAX_NP / 32];
+    for (int t = lane, q = 0; t < np; t += 32, ++q) {
+        dt[q] = d ? (double)d[n0 + t] : 0.0;
+        S.w[t] = dt[q];
+    }
+    __syncwarp();
+    if (lane < k) S.rhs[lane] = d ? S.r[lane] - gtv(S, lane, S.w) : S.r[lane];
     __syncwarp();
     refine_solve(S, k, np);
-    int64_t n0 = nrp[i];
-    for (int t = lane; t < np; t += 32) p0[n0 + t] = gz(S, t, k, S.z);
+    for (int t = lane, q = 0; t < np; t += 32, ++q) p0[n0 + t] = dt[q] + gz(S, t, k, S.z);
 }
 
 // one projected-Jacobi step (eq. (9)): dP = D^-1 (A P)|_N, projected row by row, P' = P - w dP
 __global__ void __launch_bounds__(LOC_WARPS * 32)
-k_emin(int64_t ne, const int64_t* arp, const int32_t* aci, const double* av, const int64_t* trp, const int32_t* tci,
-       const double* tv, const int64_t* nrp, const int32_t* nci, const int64_t* hrp, const int32_t* hci,
-       const double* hv, const double* P, double* Pout, double omega, int* fail) {
+k_emin(int64_t ne, const int32_t* rows, const int64_t* arp, const int32_t* aci, const double* av, const int64_t* trp,
+       const int32_t* tci, const double* tv, const int64_t* nrp, const int32_t* nci, const int64_t* hrp,
+       const int32_t* hci, const double* hv, const double* P, double* Pout, double omega, int* fail) {
     extern __shared__ unsigned char smem_raw[];
     int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     LocalSys& S = ((LocalSys*)smem_raw)[w];
     int64_t i = (int64_t)blockIdx.x * LOC_WARPS + w;
     if (i >= ne) return;
+    if (rows) i = rows[i];
     int m, np;
     int k = local_setup(S, i, trp, tci, tv, nrp, nci, hrp, hci, hv, &m, &np);
     if (np == 0) return;
@@ -748,35 +759,233 @@ k_emin(int64_t ne, const int64_t* arp, const int32_t* aci, const double* av, con
     }
 }
 
-// ------------------------------------------------------------------ learned warm start
-// P0' = P0 + (I - G~ (G~^T G~)^-1 G~^T) d, d the MLP correction of the row: P0' satisfies the same
-// constraints as P0 (exactly, up to the refinement's rounding).
-__global__ void __launch_bounds__(LOC_WARPS * 32)
-k_learned_p0(int64_t ne, const int64_t* trp, const int32_t* tci, const double* tv, const int64_t* nrp,
-             const int32_t* nci, const int64_t* hrp, const int32_t* hci, const double* hv, const float* corr,
-             double* p0, int* fail) {
-    extern __shared__ unsigned char smem_raw[];
-    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    LocalSys& S = ((LocalSys*)smem_raw)[w];
-    int64_t i = (int64_t)blockIdx.x * LOC_WARPS + w;
-    if (i >= ne) return;
-    int m, np;
-    int k = local_setup(S, i, trp, tci, tv, nrp, nci, hrp, hci, hv, &m, &np);
-    if (np == 0) return;
-    if (k < 0) { if (lane == 0) atomicAdd(fail, 1); return; }
-    int64_t n0 = nrp[i];
-    double dt[MAX_NP / 32];
-    for (int t = lane, q = 0; t < np; t += 32, ++q) {
-        dt[q] = (double)corr[n0 + t];
-        S.w[t] = dt[q];
+// ------------------------------------------------------------------ thread-per-row local solves
+// The local systems of a fine row are tiny: G~ has one column per kept coarse node of T_i and one
+// row per pattern entry, with a -1 and a +1 (or a single +-1) per row.  Rows with at most TK
+// coarse nodes and TNP pattern entries (every row of the fine levels of the Kuhn meshes) are
+// solved by one thread each: G~ as two bitmasks per node (entries carrying +1 / -1 there), the
+// integer G~^T G~ from popcounts, and an FP64 Cholesky factor in registers.  Larger rows go to
+// the warp-per-row kernels above through a row list.
+constexpr int TK = 8, TNP = 32;
+
+struct RowSys {
+    uint32_t pos[TK], neg[TK];
+    double r[TK];
+    double L[TK][TK];
+    int k, np;
+    int64_t n0;
+};
+
+// 1: factored; 0: infeasible; -1: too large for one thread; 2: empty row
+__device__ __forceinline__ int row_factor(int64_t i, const int64_t* __restrict__ trp, const int32_t* __restrict__ tci,
+                                          const double* __restrict__ tv, const int64_t* __restrict__ nrp,
+                                          const int32_t* __restrict__ nci, const int64_t* __restrict__ hrp,
+                                          const int32_t* __restrict__ hci, const double* __restrict__ hv, RowSys& S) {
+    int64_t t0 = trp[i];
+    int m = (int)(trp[i + 1] - t0);
+    S.n0 = nrp[i];
+    S.np = (int)(nrp[i + 1] - S.n0);
+    if (S.np == 0) return 2;
+    if (m > TK || S.np > TNP) return -1;
+    int32_t T[TK];
+#pragma unroll
+    for (int a = 0; a < TK; ++a) {
+        T[a] = a < m ? tci[t0 + a] : -1;
+        S.r[a] = a < m ? tv[t0 + a] : 0.0;
+        S.pos[a] = 0u;
+        S.neg[a] = 0u;
     }
-    __syncwarp();
-    if (lane < k) S.rhs[lane] = gtv(S, lane, S.w);
-    __syncwarp();
-    refine_solve(S, k, np);
-    for (int t = lane, q = 0; t < np; t += 32, ++q) p0[n0 + t] += dt[q] - gz(S, t, k, S.z);
+    bool single = false;
+    for (int t = 0; t < S.np; ++t) {
+        int32_t e = nci[S.n0 + t];
+        int64_t b = hrp[e];
+        int len = (int)(hrp[e + 1] - b);
+        if (len == 1) single = true;
+        for (int q = 0; q < len; ++q) {
+            int32_t u = hci[b + q];
+            bool minus = hv[b + q] < 0;
+#pragma unroll
+            for (int a = 0; a < TK; ++a)
+                if (T[a] == u) {
+                    if (minus) S.neg[a] |= 1u << t;
+                    else S.pos[a] |= 1u << t;
+                }
+        }
+    }
+    int k = single ? m : m - 1;     // Reduce_Dimension drops the largest coarse node
+    if (k < 0) k = 0;
+    S.k = k;
+    if (k > S.np) return 0;
+    // G~^T G~ (identity beyond k) and its Cholesky factor, left-looking
+#pragma unroll
+    for (int a = 0; a < TK; ++a)
+#pragma unroll
+        for (int b = 0; b <= a; ++b) {
+            double g;
+            if (a < k && b < k)
+                g = a == b ? (double)__popc(S.pos[a] | S.neg[a])
+                           : -(double)(__popc(S.pos[a] & S.neg[b]) + __popc(S.neg[a] & S.pos[b]));
+            else
+                g = a == b ? 1.0 : 0.0;
+            S.L[a][b] = g;
+        }
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < TK; ++j) {
+        double d = S.L[j][j];
+#pragma unroll
+        for (int c = 0; c < j; ++c) d -= S.L[j][c] * S.L[j][c];
+        if (!(d > 1e-6)) { ok = false; d = 1.0; }   // a disconnected local graph leaves a zero pivot
+        double lj = sqrt(d);
+        S.L[j][j] = lj;
+        double inv = 1.0 / lj;
+#pragma unroll
+        for (int r = j + 1; r < TK; ++r) {
+            double v = S.L[r][j];
+#pragma unroll
+            for (int c = 0; c < j; ++c) v -= S.L[r][c] * S.L[j][c];
+            S.L[r][j] = v * inv;
+        }
+    }
+    return ok ? 1 : 0;
+}
+// x := (L L^T)^-1 x
+__device__ __forceinline__ void row_solve(const RowSys& S, double x[TK]) {
+#pragma unroll
+    for (int a = 0; a < TK; ++a) {
+        double v = x[a];
+#pragma unroll
+        for (int c = 0; c < a; ++c) v -= S.L[a][c] * x[c];
+        x[a] = v / S.L[a][a];
+    }
+#pragma unroll
+    for (int a = TK - 1; a >= 0; --a) {
+        double v = x[a];
+#pragma unroll
+        for (int r = a + 1; r < TK; ++r) v -= S.L[r][a] * x[r];
+        x[a] = v / S.L[a][a];
+    }
+}
+// (G~ z)_t
+__device__ __forceinline__ double row_gz(const RowSys& S, int t, const double z[TK]) {
+    double v = 0.0;
+#pragma unroll
+    for (int a = 0; a < TK; ++a)
+        if (a < S.k) {
+            if ((S.pos[a] >> t) & 1u) v += z[a];
+            if ((S.neg[a] >> t) & 1u) v -= z[a];
+        }
+    return v;
+}
+// x -= G~^T v (v read from memory, one value per pattern entry)
+template <typename V>
+__device__ __forceinline__ void row_sub_gtv(const RowSys& S, const V* v, double x[TK]) {
+    for (int t = 0; t < S.np; ++t) {
+        double vt = (double)v[S.n0 + t];
+#pragma unroll
+        for (int a = 0; a < TK; ++a)
+            if (a < S.k) {
+                if ((S.pos[a] >> t) & 1u) x[a] -= vt;
+                if ((S.neg[a] >> t) & 1u) x[a] += vt;
+            }
+    }
 }
 
+// P0 of every small row: the point of {G~^T p = r~} nearest to d (d null: 0), p = d + G~ z with
+// (G~^T G~) z = r~ - G~^T d.  Rows too large for a thread are appended to `big`.
+__global__ void __launch_bounds__(128)
+k_p0_rows(int64_t ne, const int64_t* __restrict__ trp, const int32_t* __restrict__ tci, const double* __restrict__ tv,
+          const int64_t* __restrict__ nrp, const int32_t* __restrict__ nci, const int64_t* __restrict__ hrp,
+          const int32_t* __restrict__ hci, const double* __restrict__ hv, const float* __restrict__ d,
+          double* __restrict__ p0, int* fail, int32_t* big, int* nbig) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ne) return;
+    RowSys S;
+    int code = row_factor(i, trp, tci, tv, nrp, nci, hrp, hci, hv, S);
+    if (code == 2) return;
+    if (code == -1) { big[warp_reserve(nbig)] = (int32_t)i; return; }
+    if (code == 0) { atomicAdd(fail, 1); return; }
+    double z[TK];
+#pragma unroll
+    for (int a = 0; a < TK; ++a) z[a] = a < S.k ? S.r[a] : 0.0;
+    if (d) row_sub_gtv(S, d, z);
+    row_solve(S, z);
+    for (int t = 0; t < S.np; ++t) p0[S.n0 + t] = (d ? (double)d[S.n0 + t] : 0.0) + row_gz(S, t, z);
+}
+
+// masked product of eq. (9) for every row: w_{i,t} = (A P)_{i, N_i(t)} / a_ii.  A group of L lanes
+// owns a pattern entry (L as large as the row allows); its lanes split A's row i and search each
+// P row f for the entry's column (one FMA per match, no atomics), then add up.
+__global__ void __launch_bounds__(LOC_WARPS * 32)
+k_emin_product(int64_t ne, const int64_t* __restrict__ arp, const int32_t* __restrict__ aci,
+               const double* __restrict__ av, const int64_t* __restrict__ nrp, const int32_t* __restrict__ nci,
+               const double* __restrict__ P, double* __restrict__ w) {
+    int lane = threadIdx.x & 31;
+    int64_t i = (int64_t)blockIdx.x * LOC_WARPS + (threadIdx.x >> 5);
+    if (i >= ne) return;
+    int64_t n0 = nrp[i];
+    int np = (int)(nrp[i + 1] - n0);
+    if (np == 0) return;
+    int64_t a0 = arp[i], a1 = arp[i + 1];
+    double aii = 1.0;
+    int has = 0;
+    for (int64_t ka = a0 + lane; ka < a1; ka += 32)
+        if (aci[ka] == i) { aii = av[ka]; has = 1; }
+    unsigned hm = __ballot_sync(0xffffffffu, has);
+    if (hm) aii = __shfl_sync(0xffffffffu, aii, __ffs(hm) - 1);
+    double inv_aii = 1.0 / aii;
+    int L = 1;
+    while (L < 32 && np * (2 * L) <= 32) L *= 2;
+    int G = 32 / L, grp = lane / L, sub = lane & (L - 1);
+    int trips = (np + G - 1) / G;
+    for (int it = 0; it < trips; ++it) {
+        int t = grp + it * G;
+        double acc = 0.0;
+        if (t < np) {
+            int32_t j = nci[n0 + t];
+            for (int64_t ka = a0 + sub; ka < a1; ka += L) {
+                int32_t f = aci[ka];
+                int64_t lo = nrp[f], hi = nrp[f + 1] - 1;
+                while (lo < hi) {
+                    int64_t mid = (lo + hi) >> 1;
+                    if (nci[mid] < j) lo = mid + 1; else hi = mid;
+                }
+                if (lo <= hi && nci[lo] == j) acc += av[ka] * P[lo];
+            }
+        }
+        for (int dd = L >> 1; dd > 0; dd >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, dd);
+        if (t < np && sub == 0) w[n0 + t] = acc * inv_aii;
+    }
+}
+
+// projection and update of eq. (9) for every small row: dp = w - G~ (G~^T G~)^-1 G~^T w,
+// P' = P - omega dp (rows too large for a thread are handled by k_emin through a row list)
+__global__ void __launch_bounds__(128)
+k_emin_rows(int64_t ne, const int64_t* __restrict__ trp, const int32_t* __restrict__ tci,
+            const double* __restrict__ tv, const int64_t* __restrict__ nrp, const int32_t* __restrict__ nci,
+            const int64_t* __restrict__ hrp, const int32_t* __restrict__ hci, const double* __restrict__ hv,
+            const double* __restrict__ w, const double* __restrict__ P, double* __restrict__ Pout, double omega,
+            int* fail) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ne) return;
+    RowSys S;
+    int code = row_factor(i, trp, tci, tv, nrp, nci, hrp, hci, hv, S);
+    if (code == 2 || code == -1) return;
+    if (code == 0) { atomicAdd(fail, 1); return; }
+    double z[TK];
+#pragma unroll
+    for (int a = 0; a < TK; ++a) z[a] = 0.0;
+    row_sub_gtv(S, w, z);
+#pragma unroll
+    for (int a = 0; a < TK; ++a) z[a] = -z[a];
+    row_solve(S, z);
+    for (int t = 0; t < S.np; ++t) {
+        double dp = w[S.n0 + t] - row_gz(S, t, z);
+        Pout[S.n0 + t] = P[S.n0 + t] - omega * dp;
+    }
+}
+
+// ------------------------------------------------------------------ learned warm start
 // centroid of each aggregate (coordinates of the coarse nodes); members sorted, so the sums are
 // taken in a fixed order
 __global__ void k_centroids(const int64_t* mptr, const int32_t* members, int64_t nagg, const double* X, double* Xc) {
@@ -1025,6 +1234,22 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
                                                                     L.DH.rp.p, L.DH.ci.p, 1, nullptr, L.P0.rp.p,
                                                                     L.P0.ci.p, st.p));
     delete sec_pat;
+    // learned warm start: the MLP correction of every pattern entry (its features do not depend
+    // on P0), passed to the P0 kernel, which projects it onto the row constraints
+    SPHC_TRY(coarse_coords(L, Xnext, s));
+    int emin_iters = o.emin_iters;
+    DBuf<float> corr;
+    if (o.learned) {
+        Section sec(prof, "setup_learned_l0", s);
+        if (!mlp_params) { set_error("learned warm start without MLP parameters"); return SPHC_EINVAL; }
+        if (!L.X.p || !Xnext.p) {
+            set_error("the learned warm start needs node coordinates (pass coords to sphc_setup)");
+            return SPHC_EINVAL;
+        }
+        SPHC_TRY(corr.alloc(nnzN, s));
+        SPHC_TRY(mlp_predict_level(mlp_params, feat_args(L, Xnext, lev), corr.p, s));
+        emin_iters = o.learned_emin_iters;
+    }
     Section* sec_p0 = new Section(prof, "setup_P0_l0", s);
     // initial guess and energy minimisation
     SPHC_TRY(L.hist.alloc(33 * 33, s));
@@ -1034,34 +1259,26 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
     size_t sm = sizeof(LocalSys) * LOC_WARPS;
     SPHC_CK(cudaFuncSetAttribute(k_p0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     SPHC_CK(cudaFuncSetAttribute(k_emin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    SPHC_CK(cudaFuncSetAttribute(k_learned_p0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    if (ne > 0)
-        SPHC_LAUNCH(k_p0<<<grid_for(ne, LOC_WARPS), LOC_WARPS * 32, sm, s>>>(ne, L.T.rp.p, L.T.ci.p, L.T.v.p, L.P0.rp.p, L.P0.ci.p,
-                                                                  L.DH.rp.p, L.DH.ci.p, L.DH.v.p, L.P0.v.p, st.p,
-                                                                  L.hist.p));
-    delete sec_p0;
-    SPHC_TRY(coarse_coords(L, Xnext, s));
-    int emin_iters = o.emin_iters;
-    if (o.learned) {
-        Section sec(prof, "setup_learned_l0", s);
-        if (!mlp_params) { set_error("learned warm start without MLP parameters"); return SPHC_EINVAL; }
-        if (!L.X.p || !Xnext.p) {
-            set_error("the learned warm start needs node coordinates (pass coords to sphc_setup)");
-            return SPHC_EINVAL;
-        }
-        DBuf<float> corr;
-        SPHC_TRY(corr.alloc(nnzN, s));
-        {
-            Section sub(prof, "learned_mlp_l0", s);
-            SPHC_TRY(mlp_predict_level(mlp_params, feat_args(L, Xnext, lev), corr.p, s));
-        }
-        Section sub(prof, "learned_project_l0", s);
-        if (ne > 0)
-            SPHC_LAUNCH(k_learned_p0<<<grid_for(ne, LOC_WARPS), LOC_WARPS * 32, sm, s>>>(
-                ne, L.T.rp.p, L.T.ci.p, L.T.v.p, L.P0.rp.p, L.P0.ci.p, L.DH.rp.p, L.DH.ci.p, L.DH.v.p, corr.p, L.P0.v.p,
-                st.p));
-        emin_iters = o.learned_emin_iters;
+    // rows too large for the thread-per-row kernels (listed by k_p0_rows, reused by every step)
+    DBuf<int32_t> big;
+    DBuf<int> nbig;
+    SPHC_TRY(big.alloc(ne > 0 ? ne : 1, s));
+    SPHC_TRY(nbig.alloc(1, s));
+    SPHC_TRY(nbig.zero(s));
+    int hbig = 0;
+    if (ne > 0) {
+        SPHC_LAUNCH(k_p0_rows<<<grid_for(ne, 128), 128, 0, s>>>(ne, L.T.rp.p, L.T.ci.p, L.T.v.p, L.P0.rp.p, L.P0.ci.p,
+                                                               L.DH.rp.p, L.DH.ci.p, L.DH.v.p, corr.p, L.P0.v.p, st.p,
+                                                               big.p, nbig.p));
+        SPHC_CK(cudaMemcpyAsync(&hbig, nbig.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+        SPHC_CK(cudaStreamSynchronize(s));
+        if (hbig > 0)
+            SPHC_LAUNCH(k_p0<<<grid_for(hbig, LOC_WARPS), LOC_WARPS * 32, sm, s>>>(hbig, big.p, L.T.rp.p, L.T.ci.p, L.T.v.p,
+                                                                        L.P0.rp.p, L.P0.ci.p, L.DH.rp.p, L.DH.ci.p,
+                                                                        L.DH.v.p, corr.p, L.P0.v.p, st.p));
     }
+    delete sec_p0;
+    corr = DBuf<float>();
     SPHC_TRY(csr_copy(L.P0, L.Pe, s));
     DBuf<double> Pnew;
     SPHC_TRY(Pnew.alloc(nnzN, s));
@@ -1070,12 +1287,21 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
     double emin_bytes = (double)L.A.nnz * 12.0 + (double)ne * 8.0 * 3 + (double)nnzN * (4 + 8 + 8 + 8) +
                         (double)L.T.nnz * 12.0;
     int tid = prof ? prof->find("emin_level0", emin_bytes) : -1;
+    DBuf<double> W;
+    if (emin_iters > 0) SPHC_TRY(W.alloc(nnzN, s));
     for (int it = 0; it < emin_iters; ++it) {
         if (tid >= 0) prof->begin(tid, s);
-        if (ne > 0)
-            SPHC_LAUNCH(k_emin<<<grid_for(ne, LOC_WARPS), LOC_WARPS * 32, sm, s>>>(
-                ne, L.A.rp.p, L.A.ci.p, L.A.v.p, L.T.rp.p, L.T.ci.p, L.T.v.p, L.Pe.rp.p, L.Pe.ci.p, L.DH.rp.p,
-                L.DH.ci.p, L.DH.v.p, L.Pe.v.p, Pnew.p, o.emin_omega, st.p));
+        if (ne > 0) {
+            SPHC_LAUNCH(k_emin_product<<<grid_for(ne, LOC_WARPS), LOC_WARPS * 32, 0, s>>>(
+                ne, L.A.rp.p, L.A.ci.p, L.A.v.p, L.Pe.rp.p, L.Pe.ci.p, L.Pe.v.p, W.p));
+            SPHC_LAUNCH(k_emin_rows<<<grid_for(ne, 128), 128, 0, s>>>(
+                ne, L.T.rp.p, L.T.ci.p, L.T.v.p, L.Pe.rp.p, L.Pe.ci.p, L.DH.rp.p, L.DH.ci.p, L.DH.v.p, W.p, L.Pe.v.p,
+                Pnew.p, o.emin_omega, st.p));
+            if (hbig > 0)
+                SPHC_LAUNCH(k_emin<<<grid_for(hbig, LOC_WARPS), LOC_WARPS * 32, sm, s>>>(
+                    hbig, big.p, L.A.rp.p, L.A.ci.p, L.A.v.p, L.T.rp.p, L.T.ci.p, L.T.v.p, L.Pe.rp.p, L.Pe.ci.p,
+                    L.DH.rp.p, L.DH.ci.p, L.DH.v.p, L.Pe.v.p, Pnew.p, o.emin_omega, st.p));
+        }
         if (tid >= 0) prof->end(tid, s);
         std::swap(L.Pe.v.p, Pnew.p);
     }

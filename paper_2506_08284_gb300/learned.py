@@ -4,8 +4,9 @@ stored parameters.  Not part of the paper.
 
 Training recipe: meshes of n^3 cells with n uniform in [24, 64] (seed 100 + m), jitter uniform in
 [0, 0.25] h, log-normal sigma (log10 sigma ~ N(0, 2^2) clipped to [-6, 2]); targets are
-P_e - P0 after `target_emin` plain energy-minimisation steps on level 0; a fixed number of
-pattern entries is sampled from every mesh.
+P_e - P0 after `target_emin` plain energy-minimisation steps on levels 0 and 1 (the setup applies
+the network on every level); a fixed number of pattern entries is sampled from every level of
+every mesh.
 """
 from __future__ import annotations
 
@@ -93,8 +94,9 @@ if __name__ == "__main__":
     import sys
     import time
     n_meshes = int(sys.argv[1]) if len(sys.argv) > 1 else 40
+    levels = tuple(int(v) for v in sys.argv[2].split(",")) if len(sys.argv) > 2 else (0, 1)
     t0 = time.time()
-    X, y = training_set(n_meshes)
+    X, y = training_set(n_meshes, levels=levels)
     t1 = time.time()
     params, hist = train(X, y)
     t2 = time.time()
