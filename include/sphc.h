@@ -117,6 +117,9 @@ typedef struct {
      * lanes per row, entries per lane load and stored entries (nonzeros plus padding) */
     int32_t sell_lpr_edge, sell_ch_edge, sell_lpr_node, sell_ch_node;
     int64_t sell_stored_edge, sell_stored_node;
+    /* Jones-Plassmann rounds run by the edge and node colourings (8 per device-loop iteration,
+     * so up to 7 more than the rounds that coloured something) */
+    int32_t colour_rounds_edge, colour_rounds_node;
 } sphc_level_info;
 
 typedef struct {

@@ -97,6 +97,9 @@ int setup_impl(sphc_handle* h, const sphc_csr* A_e, const sphc_csr* D_h, const d
     H.L.reserve(o.max_levels > 0 ? o.max_levels : 1);
     H.L.emplace_back();
     Level& L0 = H.L[0];
+    Profiler* prof = H.prof.on ? &H.prof : nullptr;
+    Section total(prof, "setup_total", s);
+    Section* sec_in = new Section(prof, "setup_ingest", s);
     SPHC_TRY(ingest_csr(A_e, L0.A, s));
     SPHC_TRY(ingest_csr(D_h, L0.D, s));
     if (L0.A.nr != L0.A.nc || L0.D.nr != L0.A.nr) {
@@ -122,9 +125,12 @@ int setup_impl(sphc_handle* h, const sphc_csr* A_e, const sphc_csr* D_h, const d
         SPHC_TRY(H.mlp.alloc(SPHC_MLP_NPARAM, s));
         SPHC_CK(cudaMemcpyAsync(H.mlp.p, o.mlp_params, sizeof(float) * SPHC_MLP_NPARAM, cudaMemcpyDefault, s));
     }
-    Profiler* prof = H.prof.on ? &H.prof : nullptr;
+    delete sec_in;
     // nodal operator D_h^T A_e D_h
-    SPHC_TRY(transpose(L0.D, L0.Dt, s));
+    {
+        Section sec(prof, "setup_Dt_l0", s);
+        SPHC_TRY(transpose(L0.D, L0.Dt, s));
+    }
     {
         Section sec(prof, "setup_nodal_op", s);
         SPHC_TRY(spgemm(L0.A, L0.D, L0.AD, s));
@@ -135,9 +141,9 @@ int setup_impl(sphc_handle* h, const sphc_csr* A_e, const sphc_csr* D_h, const d
         Level& L = H.L[lev];
         uint64_t seed = o.seed + 1000ULL * (uint64_t)lev;
         {
-            Section sec(lev == 0 ? prof : nullptr, "setup_colour_l0", s);
-            SPHC_TRY(color_graph(L.A, seed + 2, L.col_e, &L.ncol_e, s));
-            SPHC_TRY(color_graph(L.An, seed + 3, L.col_n, &L.ncol_n, s));
+            Section sec(prof, lev == 0 ? "setup_colour_l0" : "setup_colour_ge1", s);
+            SPHC_TRY(color_graph(L.A, seed + 2, L.col_e, &L.ncol_e, s, &L.rounds_e));
+            SPHC_TRY(color_graph(L.An, seed + 3, L.col_n, &L.ncol_n, s, &L.rounds_n));
         }
         bool coarsest = L.A.nr <= o.max_coarse || lev + 1 >= o.max_levels || L.An.nr <= 1;
         if (coarsest) break;
@@ -153,6 +159,7 @@ int setup_impl(sphc_handle* h, const sphc_csr* A_e, const sphc_csr* D_h, const d
         N.D = std::move(D1);
         N.An = std::move(An1);
         N.X = std::move(X1);
+        Section sec_t(prof, "setup_Dt_ge1", s);
         SPHC_TRY(transpose(N.D, N.Dt, s));
         ++lev;
     }
@@ -325,6 +332,8 @@ int sphc_get_level_info(const sphc_handle* h, int level, sphc_level_info* info) 
     info->nnz_An = L.An.nnz;
     info->n_colors_edge = L.ncol_e;
     info->n_colors_node = L.ncol_n;
+    info->colour_rounds_edge = L.rounds_e;
+    info->colour_rounds_node = L.rounds_n;
     if (L.has_transfer) {
         info->n_aggregates = L.nagg;
         info->n_coarse_edges = L.DH.nr;

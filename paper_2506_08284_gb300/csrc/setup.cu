@@ -4,6 +4,7 @@
 //   Alg. 2, least-norm initial guess (Sec. 6.1), projected-Jacobi energy minimisation (eq. (9))
 //   with per-row commuting-constraint projections (Sec. 3, Sec. 4.2), Galerkin products (Sec. 2)
 //   and the dense coarsest factor.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 
@@ -17,80 +18,149 @@ namespace sphc {
 // every uncoloured neighbour takes the smallest colour absent from its coloured neighbours.
 static constexpr int MAX_COLORS = 256;
 
-// One round over the rows still uncoloured (worklist `todo`); rows that stay uncoloured are
-// appended to `next`.  Decisions read colours in place: a row only colours itself once every
+// The rounds run inside one CUDA graph: a conditional while node repeats {JP_UNROLL rounds,
+// advance} on the device, so no round waits for the host (an iteration of the while node costs
+// far more than a round of a small graph; rounds after the last colour has been given only
+// return).  ctrl holds {colour overflow, iterations, then one "rows still waiting" flag per round
+// of an iteration}.  A round visits every row; coloured rows return at once, so no worklist (and
+// no contended counter to append to it) is needed.
+enum { JP_OVERFLOW = 0, JP_ITERS = 1, JP_WAITING = 2 };
+static constexpr int JP_UNROLL = 8;
+static constexpr int JP_MAX_ITERS = 1 << 17;
+
+__global__ void k_prio(int64_t n, uint64_t seed, uint64_t* prio) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < n) prio[v] = splitmix64(seed, (uint64_t)v);
+}
+
+// One round.  Decisions read colours in place: a row only colours itself once every
 // higher-priority neighbour is coloured, so the result equals the greedy colouring in priority
-// order whatever the interleaving inside a round.
-__global__ void k_jp_round(const int64_t* rp, const int32_t* ci, const int32_t* todo, int ntodo, uint64_t seed,
-                           int32_t* color, int32_t* next, int* nnext, int* overflow) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= ntodo) return;
-    int32_t v = todo[t];
+// order whatever the interleaving inside a round.  A waiting row remembers where its scan stopped
+// (pos): the neighbours before it are coloured or of lower priority, which stays true, so the
+// next round resumes at the neighbour that blocked it and the scans of all rounds add up to one
+// pass over the row.
+__global__ void k_jp_round(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                           const uint64_t* __restrict__ prio, int64_t n, int* ctrl, int slot, int32_t* pos,
+                           int32_t* color) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     volatile int32_t* col = color;
-    uint64_t hv = splitmix64(seed, (uint64_t)v);
-    for (int64_t k = rp[v]; k < rp[v + 1]; ++k) {
-        int32_t w = ci[k];
-        if (w == v || col[w] >= 0) continue;
-        if (prio_greater(splitmix64(seed, (uint64_t)w), w, hv, v)) {
-            next[warp_reserve(nnext)] = v;
-            return;
+    bool waiting = false;
+    if (v < n && col[v] < 0) {
+        uint64_t hv = prio[v];
+        int64_t b = rp[v], e = rp[v + 1];
+        int64_t k = b + pos[v];
+        for (; k < e; ++k) {
+            int32_t w = ci[k];
+            if (w == v || col[w] >= 0) continue;
+            if (prio_greater(prio[w], w, hv, v)) { waiting = true; break; }
+        }
+        if (waiting) {
+            pos[v] = (int32_t)(k - b);
+        } else {
+            uint64_t used[MAX_COLORS / 64] = {0, 0, 0, 0};
+            for (int64_t q = b; q < e; ++q) {
+                int32_t w = ci[q];
+                if (w == v) continue;
+                int32_t c = col[w];
+                if (c >= 0 && c < MAX_COLORS) used[c >> 6] |= 1ULL << (c & 63);
+            }
+            int c = 0;
+            while (c < MAX_COLORS && (used[c >> 6] >> (c & 63) & 1ULL)) ++c;
+            if (c >= MAX_COLORS) { atomicExch(&ctrl[JP_OVERFLOW], 1); c = MAX_COLORS - 1; }
+            color[v] = c;
         }
     }
-    uint64_t used[MAX_COLORS / 64] = {0, 0, 0, 0};
-    for (int64_t k = rp[v]; k < rp[v + 1]; ++k) {
-        int32_t w = ci[k];
-        if (w == v) continue;
-        int32_t c = col[w];
-        if (c >= 0 && c < MAX_COLORS) used[c >> 6] |= 1ULL << (c & 63);
-    }
-    int c = 0;
-    while (c < MAX_COLORS && (used[c >> 6] >> (c & 63) & 1ULL)) ++c;
-    if (c >= MAX_COLORS) { atomicExch(overflow, 1); c = MAX_COLORS - 1; }
-    color[v] = c;
+    if (__syncthreads_or(waiting) && threadIdx.x == 0) ctrl[JP_WAITING + slot] = 1;
+}
+// another iteration while a row waited in the last round
+__global__ void k_jp_advance(cudaGraphConditionalHandle hnd, int* ctrl) {
+    int waiting = ctrl[JP_WAITING + JP_UNROLL - 1];
+    for (int q = 0; q < JP_UNROLL; ++q) ctrl[JP_WAITING + q] = 0;
+    int it = ++ctrl[JP_ITERS];
+    cudaGraphSetConditional(hnd, (waiting && it < JP_MAX_ITERS) ? 1u : 0u);
 }
 
 __global__ void k_fill_i32(int32_t* a, int64_t n, int32_t v) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) a[i] = v;
 }
-__global__ void k_iota_i32(int32_t* a, int64_t n) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) a[i] = (int32_t)i;
-}
 __global__ void k_max_i32(const int32_t* a, int64_t n, int* mx) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) atomicMax(mx, a[i]);
 }
 
-int color_graph(const DCSR& G, uint64_t seed, DBuf<int32_t>& color, int* ncolors, cudaStream_t s) {
+int color_graph(const DCSR& G, uint64_t seed, DBuf<int32_t>& color, int* ncolors, cudaStream_t s, int* rounds) {
     int64_t n = G.nr;
     SPHC_TRY(color.alloc(n, s));
     if (n == 0) { *ncolors = 0; return SPHC_OK; }
+    if (n >= (1LL << 31)) { set_error("colouring: %lld rows exceed int32", (long long)n); return SPHC_ELIMIT; }
     SPHC_LAUNCH(k_fill_i32<<<grid_for(n, 256), 256, 0, s>>>(color.p, n, -1));
-    DBuf<int32_t> la, lb;
-    SPHC_TRY(la.alloc(n, s));
-    SPHC_TRY(lb.alloc(n, s));
-    SPHC_LAUNCH(k_iota_i32<<<grid_for(n, 256), 256, 0, s>>>(la.p, n));
-    DBuf<int> flags;
-    SPHC_TRY(flags.alloc(3, s));
-    SPHC_TRY(flags.zero(s));
-    int h[3];
-    int ntodo = (int)n;
-    for (int round = 0; round < 100000 && ntodo > 0; ++round) {
-        SPHC_CK(cudaMemsetAsync(flags.p, 0, sizeof(int), s));
-        SPHC_LAUNCH(k_jp_round<<<grid_for(ntodo, 256), 256, 0, s>>>(G.rp.p, G.ci.p, la.p, ntodo, seed, color.p, lb.p,
-                                                                  flags.p, flags.p + 1));
-        SPHC_CK(cudaMemcpyAsync(h, flags.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
-        SPHC_CK(cudaStreamSynchronize(s));
-        if (h[1]) { set_error("colouring needs more than %d colours", MAX_COLORS); return SPHC_ELIMIT; }
-        ntodo = h[0];
-        std::swap(la.p, lb.p);
+    DBuf<int32_t> pos;
+    DBuf<uint64_t> prio;
+    DBuf<int> ctrl;
+    SPHC_TRY(pos.alloc(n, s));
+    SPHC_TRY(pos.zero(s));
+    SPHC_TRY(prio.alloc(n, s));
+    SPHC_TRY(ctrl.alloc(JP_WAITING + JP_UNROLL, s));
+    SPHC_TRY(ctrl.zero(s));
+    SPHC_LAUNCH(k_prio<<<grid_for(n, 256), 256, 0, s>>>(n, seed, prio.p));
+    // graph: while (rows waiting) { round; advance }
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    cudaStream_t cs = nullptr;
+    int rc = SPHC_OK;
+    auto fail = [&](cudaError_t e, const char* what) {
+        set_error("colouring graph: %s: %s", what, cudaGetErrorString(e));
+        rc = SPHC_ECUDA;
+    };
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    if (e != cudaSuccess) fail(e, "create");
+    cudaGraphConditionalHandle hnd;
+    if (rc == SPHC_OK && (e = cudaGraphConditionalHandleCreate(&hnd, g, 1, cudaGraphCondAssignDefault)) != cudaSuccess)
+        fail(e, "handle");
+    cudaGraphNodeParams np = {};
+    if (rc == SPHC_OK) {
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = hnd;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaGraphNode_t node;
+        if ((e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np)) != cudaSuccess) fail(e, "while node");
     }
-    SPHC_CK(cudaMemsetAsync(flags.p + 2, 0, sizeof(int), s));
-    SPHC_LAUNCH(k_max_i32<<<grid_for(n, 256), 256, 0, s>>>(color.p, n, flags.p + 2));
-    SPHC_CK(cudaMemcpyAsync(h + 2, flags.p + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (rc == SPHC_OK && (e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) fail(e, "stream");
+    if (rc == SPHC_OK) {
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        if ((e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+            fail(e, "capture");
+        else {
+            for (int q = 0; q < JP_UNROLL; ++q)
+                k_jp_round<<<grid_for(n, 256), 256, 0, cs>>>(G.rp.p, G.ci.p, prio.p, n, ctrl.p, q, pos.p, color.p);
+            k_jp_advance<<<1, 1, 0, cs>>>(hnd, ctrl.p);
+            cudaGraph_t captured = nullptr;
+            if ((e = cudaStreamEndCapture(cs, &captured)) != cudaSuccess) fail(e, "end capture");
+        }
+    }
+    if (rc == SPHC_OK && (e = cudaGraphInstantiate(&ge, g, 0)) != cudaSuccess) fail(e, "instantiate");
+    if (rc == SPHC_OK && (e = cudaGraphLaunch(ge, s)) != cudaSuccess) fail(e, "launch");
+    if (ge) cudaGraphExecDestroy(ge);
+    if (g) cudaGraphDestroy(g);
+    if (cs) cudaStreamDestroy(cs);
+    if (rc != SPHC_OK) return rc;
+    int h[JP_WAITING + JP_UNROLL];
+    SPHC_CK(cudaMemcpyAsync(h, ctrl.p, sizeof(h), cudaMemcpyDeviceToHost, s));
     SPHC_CK(cudaStreamSynchronize(s));
-    *ncolors = h[2] + 1;
+    g_launches.fetch_add((long long)(JP_UNROLL + 1) * h[JP_ITERS]);
+    if (rounds) *rounds = JP_UNROLL * h[JP_ITERS];
+    if (h[JP_OVERFLOW]) { set_error("colouring needs more than %d colours", MAX_COLORS); return SPHC_ELIMIT; }
+    if (h[JP_ITERS] >= JP_MAX_ITERS) {
+        set_error("colouring did not finish in %d rounds", JP_UNROLL * JP_MAX_ITERS);
+        return SPHC_ELIMIT;
+    }
+    SPHC_CK(cudaMemsetAsync(ctrl.p, 0, sizeof(int), s));
+    SPHC_LAUNCH(k_max_i32<<<grid_for(n, 256), 256, 0, s>>>(color.p, n, ctrl.p));
+    SPHC_CK(cudaMemcpyAsync(h, ctrl.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SPHC_CK(cudaStreamSynchronize(s));
+    *ncolors = h[0] + 1;
     return SPHC_OK;
 }
 
@@ -1199,7 +1269,7 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
     }
     Section* sec_pat = new Section(prof, "setup_pattern_l0", s);
     // T = D P_n (values r), N (Alg. 2)
-    SPHC_TRY(spgemm(L.D, L.Pn, L.T, s));
+    SPHC_TRY(dmul(L.D, L.Pn, L.T, s));
     DCSR DHt;
     SPHC_TRY(transpose(L.DH, DHt, s));
     DBuf<int64_t> ncnt;
@@ -1236,7 +1306,10 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
     delete sec_pat;
     // learned warm start: the MLP correction of every pattern entry (its features do not depend
     // on P0), passed to the P0 kernel, which projects it onto the row constraints
-    SPHC_TRY(coarse_coords(L, Xnext, s));
+    {
+        Section sec(prof, "setup_coords_l0", s);
+        SPHC_TRY(coarse_coords(L, Xnext, s));
+    }
     int emin_iters = o.emin_iters;
     DBuf<float> corr;
     if (o.learned) {
@@ -1279,9 +1352,11 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
     }
     delete sec_p0;
     corr = DBuf<float>();
+    Section* sec_cp = new Section(prof, "setup_copy_P0_l0", s);
     SPHC_TRY(csr_copy(L.P0, L.Pe, s));
     DBuf<double> Pnew;
     SPHC_TRY(Pnew.alloc(nnzN, s));
+    delete sec_cp;
     // algorithmic bytes of one step: A (values, columns, row pointers), the pattern rows of P
     // (columns, values), T (columns, values), the new values and two coarse-edge ends per entry
     double emin_bytes = (double)L.A.nnz * 12.0 + (double)ne * 8.0 * 3 + (double)nnzN * (4 + 8 + 8 + 8) +

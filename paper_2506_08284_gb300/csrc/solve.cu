@@ -234,15 +234,33 @@ template <> struct IChunk<4> {
     }
 };
 
-// This lane's partial (A x)_r over the slice starting at o: `steps` loads of CH entries
+// This lane's partial (A x)_r over the slice starting at o: `steps` loads of CH entries.  Four
+// steps of matrix loads are issued before their gathers, so a row costs about steps / 4 memory
+// round trips instead of steps / 2 (the small coarse-level colours are latency-bound).
 template <typename T, int CH>
 __device__ __forceinline__ T sell_part(const int32_t* __restrict__ ci, const T* __restrict__ v, int64_t o,
                                        int64_t steps, int lane, const T* x) {
+    constexpr int U = 4;
     const T* vp = v + o + lane * CH;
     const int32_t* cp = ci + o + lane * CH;
     T sum = 0;
-#pragma unroll 2
-    for (int64_t q = 0; q < steps; ++q) {
+    int64_t q = 0;
+    for (; q + U <= steps; q += U) {
+        T a[U][CH];
+        int32_t c[U][CH];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            Chunk<T, CH>::load(vp + u * SELL_C * CH, a[u]);
+            IChunk<CH>::load(cp + u * SELL_C * CH, c[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int t = 0; t < CH; ++t) sum += a[u][t] * x[c[u][t]];
+        vp += U * SELL_C * CH;
+        cp += U * SELL_C * CH;
+    }
+    for (; q < steps; ++q) {
         T a[CH];
         int32_t c[CH];
         Chunk<T, CH>::load(vp, a);

@@ -2,6 +2,7 @@
 // structural sparse matrix product (used for D_h^T A_e D_h, A_n Pbar, D_h P_n and the Galerkin
 // products P_e^T A_e P_e, P_n^T A_n P_n of Sec. 2), FP64 SpMV and deterministic dots.
 #include <cstdarg>
+#include <cstdint>
 #include <cstdio>
 #include <mutex>
 
@@ -327,6 +328,62 @@ __global__ void k_diag(const int64_t* rp, const int32_t* ci, const double* v, in
 }
 int csr_diag(const DCSR& A, double* d, cudaStream_t s) {
     if (A.nr > 0) SPHC_LAUNCH(k_diag<<<grid_for(A.nr, 256), 256, 0, s>>>(A.rp.p, A.ci.p, A.v.p, A.nr, d));
+    SPHC_CK(cudaGetLastError());
+    return SPHC_OK;
+}
+
+// ------------------------------------------------------------------ gradient times matrix
+// C = D B for a D with at most two entries per row (a discrete gradient): row i of C is the sorted
+// union of B's rows at D's columns, the values combined with D's coefficients.  Structural like
+// spgemm: every reached column is kept, even where the two contributions cancel, and a column
+// reached twice gets the sum of two products (exact in either order, as in spgemm).  Thread per
+// row; mode 0 counts, mode 1 writes.
+__global__ void k_dmul(const int64_t* __restrict__ drp, const int32_t* __restrict__ dci, const double* __restrict__ dv,
+                       int64_t n, const int64_t* __restrict__ brp, const int32_t* __restrict__ bci,
+                       const double* __restrict__ bv, int mode, int64_t* cnt, const int64_t* __restrict__ crp,
+                       int32_t* __restrict__ cci, double* __restrict__ cv) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t d0 = drp[i], dl = drp[i + 1] - d0;
+    int64_t a0 = 0, a1 = 0, b0 = 0, b1 = 0;
+    double ca = 0.0, cb = 0.0;
+    if (dl >= 1) { int32_t u = dci[d0]; a0 = brp[u]; a1 = brp[u + 1]; ca = dv[d0]; }
+    if (dl >= 2) { int32_t w = dci[d0 + 1]; b0 = brp[w]; b1 = brp[w + 1]; cb = dv[d0 + 1]; }
+    int64_t out = mode ? crp[i] : 0, c = 0;
+    int64_t ka = a0, kb = b0;
+    while (ka < a1 || kb < b1) {
+        int32_t ja = ka < a1 ? bci[ka] : INT32_MAX, jb = kb < b1 ? bci[kb] : INT32_MAX;
+        int32_t col;
+        double val;
+        if (ja < jb) { col = ja; val = ca * bv[ka]; ++ka; }
+        else if (jb < ja) { col = jb; val = cb * bv[kb]; ++kb; }
+        else { col = ja; val = ca * bv[ka] + cb * bv[kb]; ++ka; ++kb; }
+        if (mode) { cci[out + c] = col; cv[out + c] = val; }
+        ++c;
+    }
+    if (!mode) cnt[i] = c;
+}
+
+int dmul(const DCSR& D, const DCSR& B, DCSR& C, cudaStream_t s) {
+    int64_t dmax = 0;
+    SPHC_TRY(max_row_length(D.rp.p, D.nr, s, &dmax));
+    if (dmax > 2) return spgemm(D, B, C, s);
+    int64_t n = D.nr;
+    DBuf<int64_t> cnt;
+    SPHC_TRY(cnt.alloc(n + 1, s));
+    if (n > 0)
+        SPHC_LAUNCH(k_dmul<<<grid_for(n, 256), 256, 0, s>>>(D.rp.p, D.ci.p, D.v.p, n, B.rp.p, B.ci.p, B.v.p, 0, cnt.p,
+                                                           nullptr, nullptr, nullptr));
+    C = DCSR();
+    C.nr = n;
+    C.nc = B.nc;
+    SPHC_TRY(C.rp.alloc(n + 1, s));
+    SPHC_TRY(exclusive_scan_i64(cnt.p, C.rp.p, n, s, &C.nnz));
+    SPHC_TRY(C.ci.alloc(C.nnz, s));
+    SPHC_TRY(C.v.alloc(C.nnz, s));
+    if (n > 0)
+        SPHC_LAUNCH(k_dmul<<<grid_for(n, 256), 256, 0, s>>>(D.rp.p, D.ci.p, D.v.p, n, B.rp.p, B.ci.p, B.v.p, 1, nullptr,
+                                                           C.rp.p, C.ci.p, C.v.p));
     SPHC_CK(cudaGetLastError());
     return SPHC_OK;
 }

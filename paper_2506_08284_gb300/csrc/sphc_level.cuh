@@ -86,6 +86,7 @@ struct Level {
     DBuf<double> sig;                // per-edge sigma (level 0 only)
     DBuf<int32_t> col_e, col_n;
     int ncol_e = 0, ncol_n = 0;
+    int rounds_e = 0, rounds_n = 0;  // Jones-Plassmann rounds of the two colourings
     // transfer data (absent on the coarsest level)
     bool has_transfer = false;
     DBuf<int32_t> agg;
@@ -97,7 +98,7 @@ struct Level {
 };
 
 // setup.cu
-int color_graph(const DCSR& G, uint64_t seed, DBuf<int32_t>& color, int* ncolors, cudaStream_t s);
+int color_graph(const DCSR& G, uint64_t seed, DBuf<int32_t>& color, int* ncolors, cudaStream_t s, int* rounds = nullptr);
 int aggregate(const DCSR& G, uint64_t seed, DBuf<int32_t>& agg, int64_t* nagg, cudaStream_t s);
 int power_rho(const DCSR& A, const double* diag, uint64_t seed, int iters, double* rho, cudaStream_t s);
 int coarse_gradient(const DCSR& D, const DCSR& Dt, const int32_t* agg, int64_t nagg, DCSR& DH, cudaStream_t s);

@@ -59,7 +59,8 @@ class sphc_level_info(ctypes.Structure):
                 ("rho", ctypes.c_double), ("omega_sa", ctypes.c_double), ("max_pattern_row", ctypes.c_int64),
                 ("max_T_row", ctypes.c_int64), ("sell_lpr_edge", ctypes.c_int32), ("sell_ch_edge", ctypes.c_int32),
                 ("sell_lpr_node", ctypes.c_int32), ("sell_ch_node", ctypes.c_int32),
-                ("sell_stored_edge", ctypes.c_int64), ("sell_stored_node", ctypes.c_int64)]
+                ("sell_stored_edge", ctypes.c_int64), ("sell_stored_node", ctypes.c_int64),
+                ("colour_rounds_edge", ctypes.c_int32), ("colour_rounds_node", ctypes.c_int32)]
 
 
 class sphc_stats(ctypes.Structure):
