@@ -163,39 +163,53 @@ __global__ void k_sell_count(const int32_t* w, int64_t nslice, int rps, int q, i
     int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s < nslice) cnt[s] = (int64_t)rps * ((w[s] + q - 1) / q) * q;
 }
-// warp per slice, lane q < R per row: copy the row into its slots, pad the rest
+// Warp per slice.  Lane q < R first takes row q's start, length and padding column; then the
+// lanes walk the slice's stored entries in storage order (coalesced writes), each finding the
+// row q and entry j it holds: position p = (step * 32 + q * lpr + k % lpr) * ch + j % ch with
+// chunk k = j / ch = step * lpr + k % lpr.  Entries past a row's end get value 0 and the row's
+// last column (0 for an empty row).
 template <typename T>
 __global__ void k_sell_fill(const int64_t* rp, const int32_t* ci, const double* v, const int32_t* rmap,
                             const int32_t* cmap, const int32_t* srow, const int64_t* soff, int64_t nslice, int ch,
                             int lpr, int32_t* sci, T* sv, T* dinv) {
     int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (s >= nslice) return;
-    int q = threadIdx.x & 31;
+    int lane = threadIdx.x & 31;
     int rps = SELL_C / lpr;
-    if (q >= rps) return;
-    int32_t r = srow[s] + q;
-    int64_t o = soff[s];
-    int64_t W = (soff[s + 1] - o) / rps;
+    int32_t r0 = srow[s];
     int64_t b = 0, len = 0, i = -1;
-    if (r < srow[s + 1]) {
-        i = rmap ? rmap[r] : r;
+    int32_t pad = 0;
+    if (lane < rps && r0 + lane < srow[s + 1]) {
+        i = rmap ? rmap[r0 + lane] : r0 + lane;
         b = rp[i];
         len = rp[i + 1] - b;
+        if (len > 0) {
+            int32_t c0 = ci[b + len - 1];
+            pad = cmap ? cmap[c0] : c0;
+        }
     }
-    int32_t pad = 0;
-    for (int64_t j = 0; j < W; ++j) {
-        int64_t k = j / ch;
-        int64_t at = o + ((k / lpr) * SELL_C + q * lpr + k % lpr) * ch + j % ch;
-        if (j < len) {
-            int32_t c0 = ci[b + j];
-            int32_t c = cmap ? cmap[c0] : c0;
-            sci[at] = c;
-            sv[at] = (T)v[b + j];
-            pad = c;
-            if (dinv && c0 == i) dinv[r] = (T)(1.0 / v[b + j]);
+    int64_t o = soff[s];
+    int64_t total = soff[s + 1] - o;
+    for (int64_t p0 = 0; p0 < total; p0 += 32) {
+        int64_t p = p0 + lane;
+        int64_t step = p / (SELL_C * ch);
+        int rem = (int)(p % (SELL_C * ch));
+        int slotl = rem / ch, tch = rem % ch;
+        int q = slotl / lpr, kk = slotl % lpr;
+        int64_t j = (step * lpr + kk) * ch + tch;
+        int64_t bq = __shfl_sync(0xffffffffu, b, q);
+        int64_t lq = __shfl_sync(0xffffffffu, len, q);
+        int64_t iq = __shfl_sync(0xffffffffu, i, q);
+        int32_t pq = __shfl_sync(0xffffffffu, pad, q);
+        if (p >= total) continue;
+        if (j < lq) {
+            int32_t c0 = ci[bq + j];
+            sci[o + p] = cmap ? cmap[c0] : c0;
+            sv[o + p] = (T)v[bq + j];
+            if (dinv && c0 == iq) dinv[r0 + q] = (T)(1.0 / v[bq + j]);
         } else {
-            sci[at] = pad;
-            sv[at] = (T)0;
+            sci[o + p] = pq;
+            sv[o + p] = (T)0;
         }
     }
 }

@@ -33,41 +33,65 @@ __global__ void k_prio(int64_t n, uint64_t seed, uint64_t* prio) {
     if (v < n) prio[v] = splitmix64(seed, (uint64_t)v);
 }
 
-// One round.  Decisions read colours in place: a row only colours itself once every
-// higher-priority neighbour is coloured, so the result equals the greedy colouring in priority
-// order whatever the interleaving inside a round.  A waiting row remembers where its scan stopped
-// (pos): the neighbours before it are coloured or of lower priority, which stays true, so the
-// next round resumes at the neighbour that blocked it and the scans of all rounds add up to one
-// pass over the row.
+// One round; a group of G lanes handles a row (rows of coarse levels are long, and one thread
+// walking them is latency-bound).  Decisions read colours in place: a row only colours itself
+// once every higher-priority neighbour is coloured, so the result equals the greedy colouring in
+// priority order whatever the interleaving inside a round.  A waiting row remembers where its
+// scan stopped (pos, the first blocking neighbour): the neighbours before it are coloured or of
+// lower priority, which stays true, so the next round resumes there and the scans of all rounds
+// add up to one pass over the row.
+template <int G>
 __global__ void k_jp_round(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
                            const uint64_t* __restrict__ prio, int64_t n, int* ctrl, int slot, int32_t* pos,
                            int32_t* color) {
-    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int lane = threadIdx.x & 31;
+    int sub = lane & (G - 1);
+    unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+    int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
     volatile int32_t* col = color;
     bool waiting = false;
-    if (v < n && col[v] < 0) {
+    if (v < n && col[v] < 0) {                     // uniform over the group
         uint64_t hv = prio[v];
         int64_t b = rp[v], e = rp[v + 1];
-        int64_t k = b + pos[v];
-        for (; k < e; ++k) {
-            int32_t w = ci[k];
-            if (w == v || col[w] >= 0) continue;
-            if (prio_greater(prio[w], w, hv, v)) { waiting = true; break; }
+        for (int64_t k0 = b + pos[v]; k0 < e; k0 += G) {
+            int64_t k = k0 + sub;
+            bool blocks = false;
+            if (k < e) {
+                int32_t w = ci[k];
+                blocks = w != v && col[w] < 0 && prio_greater(prio[w], w, hv, v);
+            }
+            unsigned bal = (__ballot_sync(gmask, blocks) & gmask) >> (lane & ~(G - 1));
+            if (bal) {
+                waiting = true;
+                if (sub == 0) pos[v] = (int32_t)(k0 + (__ffs(bal) - 1) - b);
+                break;
+            }
         }
-        if (waiting) {
-            pos[v] = (int32_t)(k - b);
-        } else {
+        if (!waiting) {
             uint64_t used[MAX_COLORS / 64] = {0, 0, 0, 0};
-            for (int64_t q = b; q < e; ++q) {
-                int32_t w = ci[q];
+            for (int64_t k = b + sub; k < e; k += G) {
+                int32_t w = ci[k];
                 if (w == v) continue;
                 int32_t c = col[w];
-                if (c >= 0 && c < MAX_COLORS) used[c >> 6] |= 1ULL << (c & 63);
+                if (c >= 0 && c < MAX_COLORS) {
+                    if (c < 64) used[0] |= 1ULL << c;
+                    else if (c < 128) used[1] |= 1ULL << (c - 64);
+                    else if (c < 192) used[2] |= 1ULL << (c - 128);
+                    else used[3] |= 1ULL << (c - 192);
+                }
             }
-            int c = 0;
-            while (c < MAX_COLORS && (used[c >> 6] >> (c & 63) & 1ULL)) ++c;
-            if (c >= MAX_COLORS) { atomicExch(&ctrl[JP_OVERFLOW], 1); c = MAX_COLORS - 1; }
-            color[v] = c;
+#pragma unroll
+            for (int d = G / 2; d > 0; d >>= 1)
+#pragma unroll
+                for (int q = 0; q < MAX_COLORS / 64; ++q) used[q] |= __shfl_xor_sync(gmask, used[q], d);
+            if (sub == 0) {
+                int c = MAX_COLORS;
+#pragma unroll
+                for (int q = MAX_COLORS / 64 - 1; q >= 0; --q)
+                    if (~used[q]) c = 64 * q + __ffsll((long long)~used[q]) - 1;
+                if (c >= MAX_COLORS) { atomicExch(&ctrl[JP_OVERFLOW], 1); c = MAX_COLORS - 1; }
+                color[v] = c;
+            }
         }
     }
     if (__syncthreads_or(waiting) && threadIdx.x == 0) ctrl[JP_WAITING + slot] = 1;
@@ -133,8 +157,24 @@ int color_graph(const DCSR& G, uint64_t seed, DBuf<int32_t>& color, int* ncolors
         if ((e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
             fail(e, "capture");
         else {
-            for (int q = 0; q < JP_UNROLL; ++q)
-                k_jp_round<<<grid_for(n, 256), 256, 0, cs>>>(G.rp.p, G.ci.p, prio.p, n, ctrl.p, q, pos.p, color.p);
+            // lanes per row: one on large graphs (every round visits every row, so the thread
+            // count sets its fixed cost), else the mean row length rounded up to a power of two
+            double avg = (double)G.nnz / (double)n;
+            int lanes = 1;
+            if (n <= (1 << 20)) {
+                lanes = 4;
+                while (lanes < 32 && lanes < avg) lanes *= 2;
+            }
+            for (int q = 0; q < JP_UNROLL; ++q) {
+                unsigned blocks = (unsigned)grid_for(n * lanes, 256);
+                switch (lanes) {
+                    case 1: k_jp_round<1><<<blocks, 256, 0, cs>>>(G.rp.p, G.ci.p, prio.p, n, ctrl.p, q, pos.p, color.p); break;
+                    case 4: k_jp_round<4><<<blocks, 256, 0, cs>>>(G.rp.p, G.ci.p, prio.p, n, ctrl.p, q, pos.p, color.p); break;
+                    case 8: k_jp_round<8><<<blocks, 256, 0, cs>>>(G.rp.p, G.ci.p, prio.p, n, ctrl.p, q, pos.p, color.p); break;
+                    case 16: k_jp_round<16><<<blocks, 256, 0, cs>>>(G.rp.p, G.ci.p, prio.p, n, ctrl.p, q, pos.p, color.p); break;
+                    default: k_jp_round<32><<<blocks, 256, 0, cs>>>(G.rp.p, G.ci.p, prio.p, n, ctrl.p, q, pos.p, color.p); break;
+                }
+            }
             k_jp_advance<<<1, 1, 0, cs>>>(hnd, ctrl.p);
             cudaGraph_t captured = nullptr;
             if ((e = cudaStreamEndCapture(cs, &captured)) != cudaSuccess) fail(e, "end capture");
