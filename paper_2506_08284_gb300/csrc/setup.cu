@@ -1433,7 +1433,7 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
         if (rid >= 0) prof->begin(rid, s);
         DCSR AP;
         SPHC_TRY(spgemm(L.A, L.Pe, AP, s));
-        SPHC_TRY(spgemm(L.PeT, AP, Anext, s));
+        SPHC_TRY(spgemm_sym(L.PeT, AP, Anext, s));
         if (rid >= 0) prof->end(rid, s);
     }
     {
@@ -1441,7 +1441,7 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
         DCSR PnT, AnP;
         SPHC_TRY(transpose(L.Pn, PnT, s));
         SPHC_TRY(spgemm(L.An, L.Pn, AnP, s));
-        SPHC_TRY(spgemm(PnT, AnP, Annext, s));
+        SPHC_TRY(spgemm_sym(PnT, AnP, Annext, s));
     }
     SPHC_TRY(csr_copy(L.DH, Dnext, s));
     SPHC_CK(cudaGetLastError());

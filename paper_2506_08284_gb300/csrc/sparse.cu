@@ -404,18 +404,31 @@ __device__ inline uint32_t hslot(int32_t key, int mask) {
     return ((uint32_t)key * 2654435761u) & (uint32_t)mask;
 }
 
+// First position of B's row k whose column is >= floor (floor < 0: the row start).  A product
+// restricted to the upper triangle (floor = the output row) only visits these entries.
+__device__ inline int64_t row_floor(const int64_t* brp, const int32_t* bci, int32_t k, int32_t floor) {
+    int64_t lo = brp[k], hi = brp[k + 1];
+    if (floor < 0) return lo;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (bci[mid] < floor) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
 // bins: 0 at most 64 products and 64 A entries (register sort), 1 at most 256 products
 // (512-slot tables), 2 the rest (1024-slot tables / big path)
 __device__ inline int spgemm_bin_of(int64_t ub, int64_t alen) {
     return (ub <= 64 && alen <= 64) ? 0 : (ub <= 256 ? 1 : 2);
 }
-__global__ void k_spgemm_ub(const int64_t* arp, const int32_t* aci, const int64_t* brp, int64_t n,
-                            int64_t* ub, int* bin_cnt) {
+__global__ void k_spgemm_ub(const int64_t* arp, const int32_t* aci, const int64_t* brp, const int32_t* bci, int64_t n,
+                            int upper, int64_t* ub, int* bin_cnt) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int bin = -1;
     if (i < n) {
         int64_t s = 0;
-        for (int64_t k = arp[i]; k < arp[i + 1]; ++k) s += brp[aci[k] + 1] - brp[aci[k]];
+        int32_t floor = upper ? (int32_t)i : -1;
+        for (int64_t k = arp[i]; k < arp[i + 1]; ++k) s += brp[aci[k] + 1] - row_floor(brp, bci, aci[k], floor);
         ub[i] = s;
         bin = spgemm_bin_of(s, arp[i + 1] - arp[i]);
     }
@@ -441,9 +454,10 @@ __global__ void k_spgemm_bin(const int64_t* arp, const int64_t* ub, int64_t n, c
 static constexpr int SMALL_WARPS = 8;
 __global__ void __launch_bounds__(SMALL_WARPS * 32)
 k_spgemm_small(const int64_t* arp, const int32_t* aci, const double* av, const int64_t* brp, const int32_t* bci,
-               const double* bv, const int32_t* rows, int nrows, int mode, int64_t* cnt, const int64_t* crp,
+               const double* bv, const int32_t* rows, int nrows, int mode, int upper, int64_t* cnt, const int64_t* crp,
                int32_t* cci, double* cv) {
     __shared__ int64_t s_off[SMALL_WARPS][64];
+    __shared__ int64_t s_bst[SMALL_WARPS][64];
     __shared__ int32_t s_key[SMALL_WARPS][64];
     __shared__ double s_val[SMALL_WARPS][64];
     int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -454,11 +468,14 @@ k_spgemm_small(const int64_t* arp, const int32_t* aci, const double* av, const i
     int alen = (int)(arp[i + 1] - a0);
     // product offsets of the (at most 64) A entries
     int64_t len[2] = {0, 0};
+    int32_t floor = upper ? (int32_t)i : -1;
     for (int q = 0; q < 2; ++q) {
         int e = lane + 32 * q;
         if (e < alen) {
             int32_t k = aci[a0 + e];
-            len[q] = brp[k + 1] - brp[k];
+            int64_t b0 = row_floor(brp, bci, k, floor);
+            s_bst[w][e] = b0;
+            len[q] = brp[k + 1] - b0;
         }
     }
     int64_t inc0 = warp_incl_scan(len[0]);
@@ -481,8 +498,7 @@ k_spgemm_small(const int64_t* arp, const int32_t* aci, const double* av, const i
                 int mid = (lo + hi + 1) >> 1;
                 if (s_off[w][mid] <= e) lo = mid; else hi = mid - 1;
             }
-            int32_t k = aci[a0 + lo];
-            int64_t kb = brp[k] + (e - s_off[w][lo]);
+            int64_t kb = s_bst[w][lo] + (e - s_off[w][lo]);
             key[q] = bci[kb];
             if (mode == 1) val[q] = av[a0 + lo] * bv[kb];
         }
@@ -550,15 +566,14 @@ struct ProdWindow {
     double av[32];
 };
 
-__device__ inline int64_t window_load(ProdWindow& W, const int64_t* aci_brp_dummy, int64_t base, int64_t a1,
+__device__ inline int64_t window_load(ProdWindow& W, const int32_t* bci, int32_t floor, int64_t base, int64_t a1,
                                       const int32_t* aci, const double* av, const int64_t* brp, int lane) {
-    (void)aci_brp_dummy;
     int64_t ka = base + lane;
     int64_t len = 0, bstart = 0;
     double aval = 0.0;
     if (ka < a1) {
         int32_t k = aci[ka];
-        bstart = brp[k];
+        bstart = row_floor(brp, bci, k, floor);
         len = brp[k + 1] - bstart;
         aval = av ? av[ka] : 0.0;
     }
@@ -582,7 +597,8 @@ __device__ inline int window_find(const ProdWindow& W, int64_t t) {
 template <int SLOTS, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32)
 k_spgemm_symbolic(const int64_t* arp, const int32_t* aci, const int64_t* brp, const int32_t* bci,
-                  const int32_t* rows, int nrows, const int64_t* ub, int64_t* cnt, int32_t* big_list, int* big_n) {
+                  const int32_t* rows, int nrows, int upper, const int64_t* ub, int64_t* cnt, int32_t* big_list,
+                  int* big_n) {
     __shared__ int32_t s_keys[WARPS][SLOTS];
     __shared__ ProdWindow s_win[WARPS];
     __shared__ int s_cnt[WARPS];
@@ -590,6 +606,7 @@ k_spgemm_symbolic(const int64_t* arp, const int32_t* aci, const int64_t* brp, co
     int64_t li = (int64_t)blockIdx.x * WARPS + w;
     if (li >= nrows) return;
     int64_t i = rows[li];
+    int32_t floor = upper ? (int32_t)i : -1;
     int32_t* keys = s_keys[w];
     int64_t ubi = ub[i];
     int tsize = 32;
@@ -602,7 +619,7 @@ k_spgemm_symbolic(const int64_t* arp, const int32_t* aci, const int64_t* brp, co
     bool overflow = false;
     int64_t a0 = arp[i], a1 = arp[i + 1];
     for (int64_t base = a0; base < a1 && !overflow; base += 32) {
-        int64_t total = window_load(s_win[w], nullptr, base, a1, aci, nullptr, brp, lane);
+        int64_t total = window_load(s_win[w], bci, floor, base, a1, aci, nullptr, brp, lane);
         for (int64_t t0 = 0; t0 < total; t0 += 32) {
             int64_t t = t0 + lane;
             if (t < total) {
@@ -637,7 +654,7 @@ k_spgemm_symbolic(const int64_t* arp, const int32_t* aci, const int64_t* brp, co
 
 // big path symbolic: one block per listed row
 __global__ void k_spgemm_symbolic_big(const int64_t* arp, const int32_t* aci, const int64_t* brp,
-                                      const int32_t* bci, const int32_t* list, int nlist, int64_t* cnt,
+                                      const int32_t* bci, const int32_t* list, int nlist, int upper, int64_t* cnt,
                                       int* fail) {
     extern __shared__ int32_t s_big[];
     __shared__ int s_n;
@@ -646,9 +663,10 @@ __global__ void k_spgemm_symbolic_big(const int64_t* arp, const int32_t* aci, co
         for (int t = threadIdx.x; t < BIG_SLOTS; t += blockDim.x) s_big[t] = -1;
         if (threadIdx.x == 0) s_n = 0;
         __syncthreads();
+        int32_t floor = upper ? (int32_t)i : -1;
         for (int64_t ka = arp[i]; ka < arp[i + 1]; ++ka) {
             int32_t k = aci[ka];
-            for (int64_t kb = brp[k] + threadIdx.x; kb < brp[k + 1]; kb += blockDim.x) {
+            for (int64_t kb = row_floor(brp, bci, k, floor) + threadIdx.x; kb < brp[k + 1]; kb += blockDim.x) {
                 int32_t col = bci[kb];
                 uint32_t h = hslot(col, BIG_SLOTS - 1);
                 for (int probe = 0; probe < BIG_SLOTS; ++probe) {
@@ -672,7 +690,7 @@ __global__ void k_spgemm_symbolic_big(const int64_t* arp, const int32_t* aci, co
 template <int SLOTS, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32)
 k_spgemm_numeric(const int64_t* arp, const int32_t* aci, const double* av, const int64_t* brp,
-                 const int32_t* bci, const double* bv, const int32_t* rows, int nrows, const int64_t* crp,
+                 const int32_t* bci, const double* bv, const int32_t* rows, int nrows, int upper, const int64_t* crp,
                  int32_t* cci, double* cv, const int64_t* ub) {
     __shared__ int32_t s_keys[WARPS][SLOTS];
     __shared__ double s_vals[WARPS][SLOTS];
@@ -681,6 +699,7 @@ k_spgemm_numeric(const int64_t* arp, const int32_t* aci, const double* av, const
     int64_t li = (int64_t)blockIdx.x * WARPS + w;
     if (li >= nrows) return;
     int64_t i = rows[li];
+    int32_t floor = upper ? (int32_t)i : -1;
     int32_t* keys = s_keys[w];
     double* vals = s_vals[w];
     int64_t c0 = crp[i];
@@ -696,7 +715,7 @@ k_spgemm_numeric(const int64_t* arp, const int32_t* aci, const double* av, const
     __syncwarp();
     int64_t a0 = arp[i], a1 = arp[i + 1];
     for (int64_t base = a0; base < a1; base += 32) {
-        int64_t total = window_load(s_win[w], nullptr, base, a1, aci, av, brp, lane);
+        int64_t total = window_load(s_win[w], bci, floor, base, a1, aci, av, brp, lane);
         for (int64_t t = lane; t < total; t += 32) {
             int lo = window_find(s_win[w], t);
             int64_t kb = s_win[w].bst[lo] + (t - s_win[w].off[lo]);
@@ -737,7 +756,7 @@ k_spgemm_numeric(const int64_t* arp, const int32_t* aci, const double* av, const
 
 __global__ void k_spgemm_numeric_big(const int64_t* arp, const int32_t* aci, const double* av,
                                      const int64_t* brp, const int32_t* bci, const double* bv,
-                                     const int32_t* list, int nlist, const int64_t* crp, int32_t* cci,
+                                     const int32_t* list, int nlist, int upper, const int64_t* crp, int32_t* cci,
                                      double* cv) {
     extern __shared__ unsigned char smem_raw[];
     int32_t* keys = (int32_t*)smem_raw;
@@ -747,10 +766,11 @@ __global__ void k_spgemm_numeric_big(const int64_t* arp, const int32_t* aci, con
         int64_t i = list[li];
         for (int t = threadIdx.x; t < BIG_SLOTS; t += blockDim.x) { keys[t] = -1; vals[t] = 0.0; }
         __syncthreads();
+        int32_t floor = upper ? (int32_t)i : -1;
         for (int64_t ka = arp[i]; ka < arp[i + 1]; ++ka) {
             int32_t k = aci[ka];
             double a = av[ka];
-            for (int64_t kb = brp[k] + threadIdx.x; kb < brp[k + 1]; kb += blockDim.x) {
+            for (int64_t kb = row_floor(brp, bci, k, floor) + threadIdx.x; kb < brp[k + 1]; kb += blockDim.x) {
                 int32_t col = bci[kb];
                 uint32_t h = hslot(col, BIG_SLOTS - 1);
                 for (int probe = 0; probe < BIG_SLOTS; ++probe) {
@@ -783,21 +803,21 @@ __global__ void k_spgemm_numeric_big(const int64_t* arp, const int32_t* aci, con
 }
 
 template <int SLOTS, int WARPS>
-static void launch_symbolic(const DCSR& A, const DCSR& B, const int32_t* rows, int nrows, const int64_t* ub,
+static void launch_symbolic(const DCSR& A, const DCSR& B, const int32_t* rows, int nrows, int upper, const int64_t* ub,
                             int64_t* cnt, int32_t* big, int* bign, cudaStream_t s) {
     if (nrows <= 0) return;
     SPHC_LAUNCH((k_spgemm_symbolic<SLOTS, WARPS><<<(nrows + WARPS - 1) / WARPS, WARPS * 32, 0, s>>>(
-        A.rp.p, A.ci.p, B.rp.p, B.ci.p, rows, nrows, ub, cnt, big, bign)));
+        A.rp.p, A.ci.p, B.rp.p, B.ci.p, rows, nrows, upper, ub, cnt, big, bign)));
 }
 template <int SLOTS, int WARPS>
-static void launch_numeric(const DCSR& A, const DCSR& B, DCSR& C, const int32_t* rows, int nrows, const int64_t* ub,
-                           cudaStream_t s) {
+static void launch_numeric(const DCSR& A, const DCSR& B, DCSR& C, const int32_t* rows, int nrows, int upper,
+                           const int64_t* ub, cudaStream_t s) {
     if (nrows <= 0) return;
     SPHC_LAUNCH((k_spgemm_numeric<SLOTS, WARPS><<<(nrows + WARPS - 1) / WARPS, WARPS * 32, 0, s>>>(
-        A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p, B.v.p, rows, nrows, C.rp.p, C.ci.p, C.v.p, ub)));
+        A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p, B.v.p, rows, nrows, upper, C.rp.p, C.ci.p, C.v.p, ub)));
 }
 
-int spgemm(const DCSR& A, const DCSR& B, DCSR& C, cudaStream_t s) {
+static int spgemm_impl(const DCSR& A, const DCSR& B, DCSR& C, int upper, cudaStream_t s) {
     if (A.nc != B.nr) {
         set_error("spgemm: inner dimensions %lld vs %lld", (long long)A.nc, (long long)B.nr);
         return SPHC_EINVAL;
@@ -815,7 +835,7 @@ int spgemm(const DCSR& A, const DCSR& B, DCSR& C, cudaStream_t s) {
     SPHC_TRY(flags.zero(s));
     int h[16] = {0};
     if (n > 0) {
-        SPHC_LAUNCH(k_spgemm_ub<<<grid_for(n, 256), 256, 0, s>>>(A.rp.p, A.ci.p, B.rp.p, n, ub.p, flags.p + 2));
+        SPHC_LAUNCH(k_spgemm_ub<<<grid_for(n, 256), 256, 0, s>>>(A.rp.p, A.ci.p, B.rp.p, B.ci.p, n, upper, ub.p, flags.p + 2));
         SPHC_CK(cudaMemcpyAsync(h, flags.p, 16 * sizeof(int), cudaMemcpyDeviceToHost, s));
         SPHC_CK(cudaStreamSynchronize(s));
         int off[NBINS] = {0, h[2], h[2] + h[3]};
@@ -823,9 +843,9 @@ int spgemm(const DCSR& A, const DCSR& B, DCSR& C, cudaStream_t s) {
         SPHC_LAUNCH(k_spgemm_bin<<<grid_for(n, 256), 256, 0, s>>>(A.rp.p, ub.p, n, flags.p + 5, flags.p + 8, rows.p));
         if (h[2] > 0)
             SPHC_LAUNCH(k_spgemm_small<<<(h[2] + SMALL_WARPS - 1) / SMALL_WARPS, SMALL_WARPS * 32, 0, s>>>(
-                A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p, B.v.p, rows.p, h[2], 0, cnt.p, nullptr, nullptr, nullptr));
-        launch_symbolic<512, 8>(A, B, rows.p + off[1], h[3], ub.p, cnt.p, big.p, flags.p, s);
-        launch_symbolic<1024, 8>(A, B, rows.p + off[2], h[4], ub.p, cnt.p, big.p, flags.p, s);
+                A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p, B.v.p, rows.p, h[2], 0, upper, cnt.p, nullptr, nullptr, nullptr));
+        launch_symbolic<512, 8>(A, B, rows.p + off[1], h[3], upper, ub.p, cnt.p, big.p, flags.p, s);
+        launch_symbolic<1024, 8>(A, B, rows.p + off[2], h[4], upper, ub.p, cnt.p, big.p, flags.p, s);
     }
     SPHC_CK(cudaGetLastError());
     int nbig = 0;
@@ -836,7 +856,7 @@ int spgemm(const DCSR& A, const DCSR& B, DCSR& C, cudaStream_t s) {
     if (nbig > 0) {
         SPHC_CK(cudaFuncSetAttribute(k_spgemm_symbolic_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big_sym_sm));
         SPHC_LAUNCH(k_spgemm_symbolic_big<<<nbig < 4096 ? nbig : 4096, 512, big_sym_sm, s>>>(
-            A.rp.p, A.ci.p, B.rp.p, B.ci.p, big.p, nbig, cnt.p, flags.p + 1));
+            A.rp.p, A.ci.p, B.rp.p, B.ci.p, big.p, nbig, upper, cnt.p, flags.p + 1));
         int f = 0;
         SPHC_CK(cudaMemcpyAsync(&f, flags.p + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
         SPHC_CK(cudaStreamSynchronize(s));
@@ -855,15 +875,64 @@ int spgemm(const DCSR& A, const DCSR& B, DCSR& C, cudaStream_t s) {
         int off[NBINS] = {0, h[2], h[2] + h[3]};
         if (h[2] > 0)
             SPHC_LAUNCH(k_spgemm_small<<<(h[2] + SMALL_WARPS - 1) / SMALL_WARPS, SMALL_WARPS * 32, 0, s>>>(
-                A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p, B.v.p, rows.p, h[2], 1, nullptr, C.rp.p, C.ci.p, C.v.p));
-        launch_numeric<512, 4>(A, B, C, rows.p + off[1], h[3], ub.p, s);
-        launch_numeric<1024, 2>(A, B, C, rows.p + off[2], h[4], ub.p, s);
+                A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p, B.v.p, rows.p, h[2], 1, upper, nullptr, C.rp.p, C.ci.p, C.v.p));
+        launch_numeric<512, 4>(A, B, C, rows.p + off[1], h[3], upper, ub.p, s);
+        launch_numeric<1024, 2>(A, B, C, rows.p + off[2], h[4], upper, ub.p, s);
     }
     if (nbig > 0) {
         SPHC_CK(cudaFuncSetAttribute(k_spgemm_numeric_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big_num_sm));
         SPHC_LAUNCH(k_spgemm_numeric_big<<<nbig < 4096 ? nbig : 4096, 512, big_num_sm, s>>>(
-            A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p, B.v.p, big.p, nbig, C.rp.p, C.ci.p, C.v.p));
+            A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p, B.v.p, big.p, nbig, upper, C.rp.p, C.ci.p, C.v.p));
     }
+    SPHC_CK(cudaGetLastError());
+    return SPHC_OK;
+}
+
+int spgemm(const DCSR& A, const DCSR& B, DCSR& C, cudaStream_t s) { return spgemm_impl(A, B, C, 0, s); }
+
+// Full symmetric matrix from its upper triangle U (diagonal included): row i is row i of U^T
+// without its diagonal (the columns below i), then row i of U.  Both parts are sorted and
+// disjoint, so the row is their concatenation; the lower triangle holds exact copies.
+__global__ void k_sym_count(const int64_t* urp, const int64_t* trp, const int32_t* tci, int64_t n, int64_t* cnt) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t t0 = trp[i], t1 = trp[i + 1];
+    int64_t below = t1 - t0 - ((t1 > t0 && tci[t1 - 1] == i) ? 1 : 0);
+    cnt[i] = below + (urp[i + 1] - urp[i]);
+}
+__global__ void k_sym_fill(const int64_t* urp, const int32_t* uci, const double* uv, const int64_t* trp,
+                           const int32_t* tci, const double* tv, int64_t n, const int64_t* crp, int32_t* cci,
+                           double* cv) {
+    int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (i >= n) return;
+    int64_t t0 = trp[i], t1 = trp[i + 1];
+    int64_t below = t1 - t0 - ((t1 > t0 && tci[t1 - 1] == i) ? 1 : 0);
+    int64_t c0 = crp[i];
+    for (int64_t q = lane; q < below; q += 32) { cci[c0 + q] = tci[t0 + q]; cv[c0 + q] = tv[t0 + q]; }
+    int64_t u0 = urp[i], ul = urp[i + 1] - u0;
+    for (int64_t q = lane; q < ul; q += 32) { cci[c0 + below + q] = uci[u0 + q]; cv[c0 + below + q] = uv[u0 + q]; }
+}
+
+int spgemm_sym(const DCSR& A, const DCSR& B, DCSR& C, cudaStream_t s) {
+    DCSR U, Ut;
+    SPHC_TRY(spgemm_impl(A, B, U, 1, s));
+    if (U.nr != U.nc) { set_error("spgemm_sym: product is %lld x %lld", (long long)U.nr, (long long)U.nc); return SPHC_EINVAL; }
+    SPHC_TRY(transpose(U, Ut, s));
+    int64_t n = U.nr;
+    DBuf<int64_t> cnt;
+    SPHC_TRY(cnt.alloc(n + 1, s));
+    if (n > 0) SPHC_LAUNCH(k_sym_count<<<grid_for(n, 256), 256, 0, s>>>(U.rp.p, Ut.rp.p, Ut.ci.p, n, cnt.p));
+    C = DCSR();
+    C.nr = n;
+    C.nc = n;
+    SPHC_TRY(C.rp.alloc(n + 1, s));
+    SPHC_TRY(exclusive_scan_i64(cnt.p, C.rp.p, n, s, &C.nnz));
+    SPHC_TRY(C.ci.alloc(C.nnz, s));
+    SPHC_TRY(C.v.alloc(C.nnz, s));
+    if (n > 0)
+        SPHC_LAUNCH(k_sym_fill<<<grid_for(n * 32, 256), 256, 0, s>>>(U.rp.p, U.ci.p, U.v.p, Ut.rp.p, Ut.ci.p, Ut.v.p, n,
+                                                                    C.rp.p, C.ci.p, C.v.p));
     SPHC_CK(cudaGetLastError());
     return SPHC_OK;
 }

@@ -157,6 +157,9 @@ int exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t 
 int scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, cudaStream_t s, int64_t* total_host);
 // C = A * B, structural (every reached entry kept), columns sorted, FP64 values.
 int spgemm(const DCSR& A, const DCSR& B, DCSR& C, cudaStream_t s);
+// The same for a product known to be symmetric (a Galerkin product): only the upper triangle is
+// formed, the lower one is its exact mirror.
+int spgemm_sym(const DCSR& A, const DCSR& B, DCSR& C, cudaStream_t s);
 // C = D B for D with at most two entries per row (thread-per-row merge; spgemm otherwise),
 // same result as spgemm
 int dmul(const DCSR& D, const DCSR& B, DCSR& C, cudaStream_t s);
