@@ -542,7 +542,7 @@ int coarse_gradient(const DCSR& D, const DCSR& Dt, const int32_t* agg, int64_t n
 // Warp per fine row i: N_i = coarse edges whose every node lies in T_i.  mode 0 counts and
 // checks the local graph (nodes T_i, two-node edges of N_i) for connectivity; mode 1 writes
 // the sorted row.
-__global__ void k_pattern(const int64_t* trp, const int32_t* tci, int64_t ne, const int64_t* htrp,
+__global__ void k_pattern(const int64_t* trp, const int32_t* tci, int64_t ne, const int32_t* rows, const int64_t* htrp,
                           const int32_t* htci, const int64_t* hrp, const int32_t* hci, int mode, int64_t* cnt,
                           const int64_t* nrp, int32_t* nci, int* stats /*0 too big T, 1 too big N, 2 disconnected, 3 max N, 4 max T*/) {
     __shared__ int32_t s_T[PAT_WARPS][MAX_T];
@@ -551,6 +551,7 @@ __global__ void k_pattern(const int64_t* trp, const int32_t* tci, int64_t ne, co
     int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int64_t i = (int64_t)blockIdx.x * PAT_WARPS + w;
     if (i >= ne) return;
+    if (rows) i = rows[i];
     int64_t t0 = trp[i];
     int m = (int)(trp[i + 1] - t0);
     if (m > MAX_T) { if (lane == 0) { atomicExch(&stats[0], 1); if (mode == 0) cnt[i] = 0; } return; }
@@ -611,6 +612,104 @@ __global__ void k_pattern(const int64_t* trp, const int32_t* tci, int64_t ne, co
         int rank = 0;
         for (int q = 0; q < np; ++q) rank += (s_N[w][q] < e);
         nci[base + rank] = e;
+    }
+}
+
+// Thread per fine row for rows whose T_i has at most PT_K coarse nodes (larger rows go to
+// k_pattern through a row list): the same N_i, enumerated from the incidence lists of T_i's nodes
+// (each two-node edge once, from its first node).  mode 0 counts N_i and checks that the local
+// graph is connected (reachability over an 8 x 8 adjacency bitmask); mode 1 writes N_i sorted,
+// by merging the per-node lists (each sorted by edge id).
+constexpr int PT_K = 8;
+__device__ __forceinline__ int pat_local(const int32_t T[PT_K], int m, int32_t u) {
+    int c = -1;
+#pragma unroll
+    for (int a = 0; a < PT_K; ++a)
+        if (a < m && T[a] == u) c = a;
+    return c;
+}
+// is coarse edge e (listed under node J) in N_i, counted from this list?
+__device__ __forceinline__ bool pat_take(const int64_t* __restrict__ hrp, const int32_t* __restrict__ hci,
+                                         const int32_t T[PT_K], int m, int32_t e, int32_t J, int* other) {
+    int64_t b = hrp[e];
+    int len = (int)(hrp[e + 1] - b);
+    *other = -1;
+    if (len == 1) return true;
+    if (hci[b] != J) return false;
+    int c = pat_local(T, m, hci[b + 1]);
+    *other = c;
+    return c >= 0;
+}
+__global__ void __launch_bounds__(128)
+k_pattern_rows(const int64_t* __restrict__ trp, const int32_t* __restrict__ tci, int64_t ne,
+               const int64_t* __restrict__ htrp, const int32_t* __restrict__ htci, const int64_t* __restrict__ hrp,
+               const int32_t* __restrict__ hci, int mode, int64_t* cnt, const int64_t* __restrict__ nrp,
+               int32_t* __restrict__ nci, int* stats, int32_t* big, int* nbig) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ne) return;
+    int64_t t0 = trp[i];
+    int m = (int)(trp[i + 1] - t0);
+    if (m > PT_K) {
+        if (mode == 0) big[warp_reserve(nbig)] = (int32_t)i;
+        return;
+    }
+    int32_t T[PT_K];
+#pragma unroll
+    for (int a = 0; a < PT_K; ++a) T[a] = a < m ? tci[t0 + a] : -1;
+    if (mode == 0) {
+        int np = 0;
+        uint64_t adj = 0;
+#pragma unroll
+        for (int a = 0; a < PT_K; ++a) {
+            if (a >= m) continue;
+            for (int64_t k = htrp[T[a]]; k < htrp[T[a] + 1]; ++k) {
+                int c;
+                if (pat_take(hrp, hci, T, m, htci[k], T[a], &c)) {
+                    ++np;
+                    if (c >= 0) adj |= (1ull << (8 * a + c)) | (1ull << (8 * c + a));
+                }
+            }
+        }
+        if (np > MAX_NP) { atomicExch(&stats[1], 1); cnt[i] = 0; return; }
+        cnt[i] = np;
+        if (m > 1) {
+            uint32_t reach = 1u;
+            for (int it = 0; it < m; ++it) {
+                uint32_t nr = reach;
+#pragma unroll
+                for (int a = 0; a < PT_K; ++a)
+                    if ((reach >> a) & 1u) nr |= (uint32_t)((adj >> (8 * a)) & 0xffull);
+                reach = nr;
+            }
+            if (reach != (1u << m) - 1u) atomicAdd(&stats[2], 1);
+        }
+        return;
+    }
+    // mode 1: merge the per-node lists
+    int64_t cur[PT_K], end[PT_K];
+#pragma unroll
+    for (int a = 0; a < PT_K; ++a) {
+        cur[a] = a < m ? htrp[T[a]] : 0;
+        end[a] = a < m ? htrp[T[a] + 1] : 0;
+        int c;
+        while (cur[a] < end[a] && !pat_take(hrp, hci, T, m, htci[cur[a]], T[a], &c)) ++cur[a];
+    }
+    int64_t out = nrp[i];
+    for (;;) {
+        int32_t best = INT32_MAX;
+        int bi = -1;
+#pragma unroll
+        for (int a = 0; a < PT_K; ++a)
+            if (cur[a] < end[a] && htci[cur[a]] < best) { best = htci[cur[a]]; bi = a; }
+        if (bi < 0) break;
+        nci[out++] = best;
+#pragma unroll
+        for (int a = 0; a < PT_K; ++a)
+            if (a == bi) {
+                ++cur[a];
+                int c;
+                while (cur[a] < end[a] && !pat_take(hrp, hci, T, m, htci[cur[a]], T[a], &c)) ++cur[a];
+            }
     }
 }
 
@@ -1317,13 +1416,24 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
     SPHC_TRY(ncnt.alloc(ne + 1, s));
     SPHC_TRY(st.alloc(8, s));
     SPHC_TRY(st.zero(s));
+    // rows with more than PT_K coarse nodes: warp-per-row kernel through a list (st[6] counts them)
+    DBuf<int32_t> pbig;
+    SPHC_TRY(pbig.alloc(ne > 0 ? ne : 1, s));
     if (ne > 0)
-        SPHC_LAUNCH(k_pattern<<<grid_for(ne, PAT_WARPS), PAT_WARPS * 32, 0, s>>>(L.T.rp.p, L.T.ci.p, ne, DHt.rp.p, DHt.ci.p,
-                                                                    L.DH.rp.p, L.DH.ci.p, 0, ncnt.p, nullptr, nullptr,
-                                                                    st.p));
+        SPHC_LAUNCH(k_pattern_rows<<<grid_for(ne, 128), 128, 0, s>>>(L.T.rp.p, L.T.ci.p, ne, DHt.rp.p, DHt.ci.p, L.DH.rp.p,
+                                                                   L.DH.ci.p, 0, ncnt.p, nullptr, nullptr, st.p, pbig.p,
+                                                                   st.p + 6));
     int hs[8];
     SPHC_CK(cudaMemcpyAsync(hs, st.p, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
     SPHC_CK(cudaStreamSynchronize(s));
+    int npbig = hs[6];
+    if (npbig > 0) {
+        SPHC_LAUNCH(k_pattern<<<grid_for(npbig, PAT_WARPS), PAT_WARPS * 32, 0, s>>>(L.T.rp.p, L.T.ci.p, npbig, pbig.p,
+                                                                      DHt.rp.p, DHt.ci.p, L.DH.rp.p, L.DH.ci.p, 0,
+                                                                      ncnt.p, nullptr, nullptr, st.p));
+        SPHC_CK(cudaMemcpyAsync(hs, st.p, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        SPHC_CK(cudaStreamSynchronize(s));
+    }
     if (hs[0]) { set_error("level %d: a row of T exceeds %d coarse nodes", lev, MAX_T); return SPHC_ELIMIT; }
     if (hs[1]) { set_error("level %d: a row of the pattern exceeds %d coarse edges", lev, MAX_NP); return SPHC_ELIMIT; }
     if (hs[2]) {
@@ -1340,9 +1450,13 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
     SPHC_TRY(L.P0.v.alloc(nnzN, s));
     SPHC_TRY(max_row_length(L.P0.rp.p, ne, s, &L.max_np));
     if (ne > 0)
-        SPHC_LAUNCH(k_pattern<<<grid_for(ne, PAT_WARPS), PAT_WARPS * 32, 0, s>>>(L.T.rp.p, L.T.ci.p, ne, DHt.rp.p, DHt.ci.p,
-                                                                    L.DH.rp.p, L.DH.ci.p, 1, nullptr, L.P0.rp.p,
-                                                                    L.P0.ci.p, st.p));
+        SPHC_LAUNCH(k_pattern_rows<<<grid_for(ne, 128), 128, 0, s>>>(L.T.rp.p, L.T.ci.p, ne, DHt.rp.p, DHt.ci.p, L.DH.rp.p,
+                                                                   L.DH.ci.p, 1, nullptr, L.P0.rp.p, L.P0.ci.p, st.p,
+                                                                   nullptr, nullptr));
+    if (npbig > 0)
+        SPHC_LAUNCH(k_pattern<<<grid_for(npbig, PAT_WARPS), PAT_WARPS * 32, 0, s>>>(L.T.rp.p, L.T.ci.p, npbig, pbig.p,
+                                                                      DHt.rp.p, DHt.ci.p, L.DH.rp.p, L.DH.ci.p, 1,
+                                                                      nullptr, L.P0.rp.p, L.P0.ci.p, st.p));
     delete sec_pat;
     // learned warm start: the MLP correction of every pattern entry (its features do not depend
     // on P0), passed to the P0 kernel, which projects it onto the row constraints
