@@ -30,6 +30,7 @@ static_assert(P_TOTAL == SPHC_MLP_NPARAM, "parameter layout");
 constexpr int TILE_M = 128;           // rows (pattern entries) per block
 constexpr int INF_WARPS = 8;          // each warp owns 16 rows
 constexpr int XS = NF + 8;            // padded shared-memory row strides (bf16 elements)
+static_assert(INF_WARPS * 32 == 2 * TILE_M, "two threads per tile row compute its features");
 constexpr int HS = NH + 8;
 
 struct InferSmem {
@@ -102,16 +103,14 @@ k_mlp_infer(const float* __restrict__ params, const float* __restrict__ X, int64
     for (int64_t base = (int64_t)blockIdx.x * TILE_M; base < m; base += (int64_t)gridDim.x * TILE_M) {
         // normalised features of the tile (rows past m are zero)
         if (FUSED) {
-            if (tid < TILE_M) {
-                int64_t row = base + tid;
-                float f[NF];
-                if (row < m) entry_features(g, rowof[row], row, f);
-                for (int c = 0; c < NF; c += 2) {
-                    float v0 = row < m ? (f[c] - S.mu[c]) * S.isd[c] : 0.f;
-                    float v1 = row < m ? (f[c + 1] - S.mu[c + 1]) * S.isd[c + 1] : 0.f;
-                    *(uint32_t*)(S.x + tid * XS + c) = pack_bf16(__float2bfloat16(v0), __float2bfloat16(v1));
-                }
-            }
+            // two threads per entry: part 0 (geometry, row quantities) and part 1 (row lookups)
+            int r = tid % TILE_M, part = tid / TILE_M;
+            int64_t row = base + r;
+            float f[NF];
+            if (row < m) entry_features(g, rowof[row], row, f, part);
+            for (int c = 0; c < NF; ++c)
+                if (feat_part(c) == part)
+                    S.x[r * XS + c] = __float2bfloat16(row < m ? (f[c] - S.mu[c]) * S.isd[c] : 0.f);
         } else {
             for (int q = tid; q < TILE_M * NF; q += blockDim.x) {
                 int r = q / NF, c = q % NF;

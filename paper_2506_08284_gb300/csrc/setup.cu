@@ -1208,6 +1208,82 @@ __global__ void k_centroids(const int64_t* mptr, const int32_t* members, int64_t
     for (int a = 0; a < 3; ++a) Xc[3 * U + a] = c[a] * inv;
 }
 
+// Per fine row: the quantities all its pattern entries share (features.cuh).
+__global__ void k_row_feat(int64_t ne, const int64_t* __restrict__ drp, const int32_t* __restrict__ dci,
+                           const double* __restrict__ dv, const int64_t* __restrict__ arp,
+                           const int32_t* __restrict__ aci, const double* __restrict__ av,
+                           const int64_t* __restrict__ nrp, const int64_t* __restrict__ trp,
+                           const double* __restrict__ X, const double* __restrict__ sig, RowFeat* out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ne) return;
+    RowFeat R;
+    int32_t u = -1, v = -1;
+    for (int64_t k = drp[i]; k < drp[i + 1]; ++k) { if (dv[k] < 0) u = dci[k]; else v = dci[k]; }
+    R.u = u;
+    R.v = v;
+    bool two = u >= 0 && v >= 0;
+    float xu[3] = {0, 0, 0}, xv[3] = {0, 0, 0}, t[3] = {0, 0, 0};
+    if (u >= 0) for (int a = 0; a < 3; ++a) xu[a] = (float)X[3 * (int64_t)u + a];
+    if (v >= 0) for (int a = 0; a < 3; ++a) xv[a] = (float)X[3 * (int64_t)v + a];
+    float h = 1.f;
+    if (two) {
+        for (int a = 0; a < 3; ++a) t[a] = xv[a] - xu[a];
+        h = sqrtf(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+        if (!(h > 0.f)) h = 1.f;
+    }
+    R.ih = 1.f / h;
+    for (int a = 0; a < 3; ++a) {
+        R.t[a] = t[a] * R.ih;
+        R.mid[a] = 0.5f * (xu[a] + xv[a]);
+    }
+    R.two = two ? 1.f : 0.f;
+    R.nlen = (float)(nrp[i + 1] - nrp[i]) / 32.f;
+    R.tlen = (float)(trp[i + 1] - trp[i]) / 16.f;
+    float aii = 0.f, l1 = 0.f;
+    for (int64_t k = arp[i]; k < arp[i + 1]; ++k) {
+        float x = (float)av[k];
+        l1 += fabsf(x);
+        if (aci[k] == i) aii = x;
+    }
+    R.diag = l1 > 0.f ? aii / l1 : 0.f;
+    R.lsig = sig ? log10f(fmaxf((float)sig[i], 1e-30f)) / 6.f : 0.f;
+    out[i] = R;
+}
+__global__ void k_to_float(const double* a, int64_t n, float* b) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (float)a[i];
+}
+
+int feat_prepare(const Level& L, const DBuf<double>& Xc, int lev, FeatBufs& B, FeatArgs& g, cudaStream_t s) {
+    if (!L.X.p || !Xc.p) {
+        set_error("features need node coordinates (pass coords to sphc_setup)");
+        return SPHC_EINVAL;
+    }
+    int64_t ne = L.A.nr;
+    SPHC_TRY(B.tvf.alloc(L.T.nnz, s));
+    SPHC_TRY(B.pvf.alloc(L.Pn.nnz, s));
+    SPHC_TRY(B.Xcf.alloc(Xc.n, s));
+    SPHC_TRY(B.rf.alloc(ne, s));
+    if (L.T.nnz > 0) SPHC_LAUNCH(k_to_float<<<grid_for(L.T.nnz, 256), 256, 0, s>>>(L.T.v.p, L.T.nnz, B.tvf.p));
+    if (L.Pn.nnz > 0) SPHC_LAUNCH(k_to_float<<<grid_for(L.Pn.nnz, 256), 256, 0, s>>>(L.Pn.v.p, L.Pn.nnz, B.pvf.p));
+    if (Xc.n > 0) SPHC_LAUNCH(k_to_float<<<grid_for(Xc.n, 256), 256, 0, s>>>(Xc.p, Xc.n, B.Xcf.p));
+    if (ne > 0)
+        SPHC_LAUNCH(k_row_feat<<<grid_for(ne, 256), 256, 0, s>>>(ne, L.D.rp.p, L.D.ci.p, L.D.v.p, L.A.rp.p, L.A.ci.p,
+                                                                L.A.v.p, L.P0.rp.p, L.T.rp.p, L.X.p, L.sig.p, B.rf.p));
+    g = FeatArgs();
+    g.ne = ne;
+    g.nnzN = L.P0.nnz;
+    g.lev = lev;
+    g.trp = L.T.rp.p; g.tci = L.T.ci.p; g.tvf = B.tvf.p;
+    g.nrp = L.P0.rp.p; g.nci = L.P0.ci.p;
+    g.hrp = L.DH.rp.p; g.hci = L.DH.ci.p;
+    g.prp = L.Pn.rp.p; g.pci = L.Pn.ci.p; g.pvf = B.pvf.p;
+    g.Xcf = B.Xcf.p;
+    g.rf = B.rf.p;
+    SPHC_CK(cudaGetLastError());
+    return SPHC_OK;
+}
+
 // Features of every pattern entry (i, j) of a level (SPHC_MLP_NFEAT floats each, see sphc.h).
 // One thread per pattern entry; the row of an entry is found by binary search in the pattern's
 // row pointers.  (The setup itself uses the fused feature + inference kernel of mlp.cu.)
@@ -1226,12 +1302,11 @@ __global__ void k_features(FeatArgs g, float* F) {
 }
 
 int level_features(const Level& L, const DBuf<double>& Xc, int lev, float* F, cudaStream_t s) {
-    if (!L.X.p || !Xc.p) {
-        set_error("features need node coordinates (pass coords to sphc_setup)");
-        return SPHC_EINVAL;
-    }
-    FeatArgs g = feat_args(L, Xc, lev);
+    FeatBufs B;
+    FeatArgs g;
+    SPHC_TRY(feat_prepare(L, Xc, lev, B, g, s));
     if (g.nnzN > 0) SPHC_LAUNCH(k_features<<<grid_for(g.nnzN, 256), 256, 0, s>>>(g, F));
+    SPHC_CK(cudaStreamSynchronize(s));          // B is released on return
     SPHC_CK(cudaGetLastError());
     return SPHC_OK;
 }
@@ -1474,7 +1549,10 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
             return SPHC_EINVAL;
         }
         SPHC_TRY(corr.alloc(nnzN, s));
-        SPHC_TRY(mlp_predict_level(mlp_params, feat_args(L, Xnext, lev), corr.p, s));
+        FeatBufs fb;
+        FeatArgs fg;
+        SPHC_TRY(feat_prepare(L, Xnext, lev, fb, fg, s));
+        SPHC_TRY(mlp_predict_level(mlp_params, fg, corr.p, s));
         emin_iters = o.learned_emin_iters;
     }
     Section* sec_p0 = new Section(prof, "setup_P0_l0", s);
