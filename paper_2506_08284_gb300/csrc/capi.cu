@@ -150,7 +150,7 @@ int setup_impl(sphc_handle* h, const sphc_csr* A_e, const sphc_csr* D_h, const d
         DCSR A1, D1, An1;
         DBuf<double> X1;
         Section sec(lev >= 1 ? prof : nullptr, "setup_levels_ge1", s);
-        SPHC_TRY(build_level(L, lev, o, A1, D1, An1, X1, H.mlp.p, lev == 0 ? prof : nullptr, s));
+        SPHC_TRY(build_level(L, lev, o, A1, D1, An1, X1, H.mlp.p, prof, s));
         if (L.nagg >= L.An.nr) break;      // no coarsening: this level is solved directly
         L.has_transfer = true;
         H.L.emplace_back();

@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <string>
 
 #include "features.cuh"
 #include "sphc_level.cuh"
@@ -1444,16 +1445,19 @@ static int coarse_coords(const Level& L, DBuf<double>& Xc, cudaStream_t s) {
     return SPHC_OK;
 }
 
+// section name with the level index, e.g. "setup_P0_l1"
+static std::string lev_name(const char* what, int lev) { return std::string(what) + "_l" + std::to_string(lev); }
+
 int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext, DCSR& Annext, DBuf<double>& Xnext,
                 const float* mlp_params, Profiler* prof, cudaStream_t s) {
     uint64_t seed = o.seed + 1000ULL * (uint64_t)lev;
     int64_t nv = L.An.nr, ne = L.A.nr;
     // aggregation on the structural nodal graph (drop tolerance 0)
     {
-        Section sec(prof, "setup_aggregate_l0", s);
+        Section sec(prof, lev_name("setup_aggregate", lev).c_str(), s);
         SPHC_TRY(aggregate(L.An, seed + 1, L.agg, &L.nagg, s));
     }
-    Section* sec_pn = new Section(prof, "setup_Pn_l0", s);
+    Section* sec_pn = new Section(prof, lev_name("setup_Pn", lev).c_str(), s);
     // smoothed nodal prolongator
     DBuf<double> dn;
     SPHC_TRY(dn.alloc(nv, s));
@@ -1478,10 +1482,10 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
     delete sec_pn;
     // coarse gradient from the tentative aggregates
     {
-        Section sec(prof, "setup_DH_l0", s);
+        Section sec(prof, lev_name("setup_DH", lev).c_str(), s);
         SPHC_TRY(coarse_gradient(L.D, L.Dt, L.agg.p, L.nagg, L.DH, s));
     }
-    Section* sec_pat = new Section(prof, "setup_pattern_l0", s);
+    Section* sec_pat = new Section(prof, lev_name("setup_pattern", lev).c_str(), s);
     // T = D P_n (values r), N (Alg. 2)
     SPHC_TRY(dmul(L.D, L.Pn, L.T, s));
     DCSR DHt;
@@ -1536,13 +1540,13 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
     // learned warm start: the MLP correction of every pattern entry (its features do not depend
     // on P0), passed to the P0 kernel, which projects it onto the row constraints
     {
-        Section sec(prof, "setup_coords_l0", s);
+        Section sec(prof, lev_name("setup_coords", lev).c_str(), s);
         SPHC_TRY(coarse_coords(L, Xnext, s));
     }
     int emin_iters = o.emin_iters;
     DBuf<float> corr;
     if (o.learned) {
-        Section sec(prof, "setup_learned_l0", s);
+        Section sec(prof, lev_name("setup_learned", lev).c_str(), s);
         if (!mlp_params) { set_error("learned warm start without MLP parameters"); return SPHC_EINVAL; }
         if (!L.X.p || !Xnext.p) {
             set_error("the learned warm start needs node coordinates (pass coords to sphc_setup)");
@@ -1555,7 +1559,7 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
         SPHC_TRY(mlp_predict_level(mlp_params, fg, corr.p, s));
         emin_iters = o.learned_emin_iters;
     }
-    Section* sec_p0 = new Section(prof, "setup_P0_l0", s);
+    Section* sec_p0 = new Section(prof, lev_name("setup_P0", lev).c_str(), s);
     // initial guess and energy minimisation
     SPHC_TRY(L.hist.alloc(33 * 33, s));
     SPHC_TRY(L.hist.zero(s));
@@ -1584,7 +1588,7 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
     }
     delete sec_p0;
     corr = DBuf<float>();
-    Section* sec_cp = new Section(prof, "setup_copy_P0_l0", s);
+    Section* sec_cp = new Section(prof, lev_name("setup_copy_P0", lev).c_str(), s);
     SPHC_TRY(csr_copy(L.P0, L.Pe, s));
     DBuf<double> Pnew;
     SPHC_TRY(Pnew.alloc(nnzN, s));
@@ -1593,7 +1597,7 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
     // (columns, values), T (columns, values), the new values and two coarse-edge ends per entry
     double emin_bytes = (double)L.A.nnz * 12.0 + (double)ne * 8.0 * 3 + (double)nnzN * (4 + 8 + 8 + 8) +
                         (double)L.T.nnz * 12.0;
-    int tid = prof ? prof->find("emin_level0", emin_bytes) : -1;
+    int tid = prof ? prof->find(lev_name("emin_level", lev).c_str(), emin_bytes) : -1;
     DBuf<double> W;
     if (emin_iters > 0) SPHC_TRY(W.alloc(nnzN, s));
     for (int it = 0; it < emin_iters; ++it) {
@@ -1617,11 +1621,11 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
     if (hs[0]) { set_error("level %d: %d local constraint systems are infeasible", lev, hs[0]); return SPHC_EINFEASIBLE; }
     // Galerkin operators of the next level
     {
-        Section sec(prof, "setup_PeT_l0", s);
+        Section sec(prof, lev_name("setup_PeT", lev).c_str(), s);
         SPHC_TRY(transpose(L.Pe, L.PeT, s));
     }
     {
-        int rid = prof ? prof->find("rap_level0", 0.0) : -1;
+        int rid = prof ? prof->find(lev_name("rap_level", lev).c_str(), 0.0) : -1;
         if (rid >= 0) prof->begin(rid, s);
         DCSR AP;
         SPHC_TRY(spgemm(L.A, L.Pe, AP, s));
@@ -1629,7 +1633,7 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
         if (rid >= 0) prof->end(rid, s);
     }
     {
-        Section sec(prof, "setup_nodal_rap_l0", s);
+        Section sec(prof, lev_name("setup_nodal_rap", lev).c_str(), s);
         DCSR PnT, AnP;
         SPHC_TRY(transpose(L.Pn, PnT, s));
         SPHC_TRY(spgemm(L.An, L.Pn, AnP, s));

@@ -225,11 +225,11 @@ class Handle:
         return X, y
 
     def profile(self) -> dict:
-        arr = (sphc_timer * 32)()
+        arr = (sphc_timer * 256)()
         n = ctypes.c_int()
-        _check(load().sphc_get_profile(self._ptr, arr, 32, ctypes.byref(n)))
+        _check(load().sphc_get_profile(self._ptr, arr, 256, ctypes.byref(n)))
         return {arr[i].name.decode(): dict(ms=arr[i].ms, calls=arr[i].calls, bytes_per_call=arr[i].bytes_per_call)
-                for i in range(min(n.value, 32))}
+                for i in range(min(n.value, 256))}
 
     @property
     def nlevels(self):

@@ -106,3 +106,56 @@ def test_learned_warm_start_keeps_commuting_relation_and_gains(trained):
     assert res["learned0"][0] < res["P0"][0]
     assert res["learned1"][0] <= res["plain1"][0] * 1.001
     assert res["learned1"][1] <= res["plain1"][1] + 1
+
+
+def test_exported_features_follow_their_definitions():
+    """The features (include/sphc.h) restated in numpy from the exported level arrays: unit edge
+    tangent, single-node flag, row sizes, A_e row scaling, log10 sigma, and the six T / P_n
+    lookups at the coarse edge's ends (tail = lower node id, a single node is the head)."""
+    spec = meshgen.MeshSpec(10, jitter=0.15, seed_jitter=3, sigma="lognormal", sigma_in=2.0, seed_sigma=4)
+    p = meshgen.generate(spec)
+    h = _hierarchy(p, max_coarse=100)
+    X, y = h.features(0)
+    csr = lambda name: (lambda rp, ci, v, shape: sp.csr_matrix((v, ci, rp), shape=shape))(*h.export(0, name))
+    N, T, DH, Pn = csr("Pe"), csr("T"), csr("DH"), csr("Pn")
+    A = sp.csr_matrix((p.A_val, p.A_col, p.A_rowptr))
+    D = sp.csr_matrix((p.D_val, p.D_col, p.D_rowptr))
+    rows = np.repeat(np.arange(N.shape[0]), np.diff(N.indptr))
+    cols = N.indices
+    assert X.shape == (N.nnz, 32)
+    # edge ends and tangent
+    two = np.diff(D.indptr)[rows] == 2
+    np.testing.assert_array_equal(X[:, 0], two.astype(np.float32))
+    norms = np.linalg.norm(X[two, 1:4], axis=1)
+    np.testing.assert_allclose(norms, 1.0, atol=1e-5)
+    # coarse edge ends by the orientation of D_H
+    hl = np.diff(DH.indptr)[cols]
+    first = DH.indices[DH.indptr[cols]]
+    second = DH.indices[np.minimum(DH.indptr[cols] + 1, DH.nnz - 1)]
+    ja = np.where(hl == 2, first, -1)
+    jb = np.where(hl == 2, second, first)
+    np.testing.assert_array_equal(X[:, 10], (hl == 1).astype(np.float32))
+    np.testing.assert_allclose(X[:, 11], np.diff(N.indptr)[rows] / 32.0, rtol=1e-6)
+    np.testing.assert_allclose(X[:, 12], np.diff(T.indptr)[rows] / 16.0, rtol=1e-6)
+    # lookups: T at (i, ja / jb), P_n at (u / v, ja / jb)
+    Td, Pd = T.tolil(), Pn.tocsr()
+    look = lambda M, r, c: np.array([M[a, b] if a >= 0 and b >= 0 else 0.0 for a, b in zip(r, c)])
+    np.testing.assert_allclose(X[:, 13], look(Td, rows, ja), rtol=1e-6, atol=1e-7)
+    np.testing.assert_allclose(X[:, 14], look(Td, rows, jb), rtol=1e-6, atol=1e-7)
+    u = np.full(D.shape[0], -1)
+    v = np.full(D.shape[0], -1)
+    for i in range(D.shape[0]):
+        for k in range(D.indptr[i], D.indptr[i + 1]):
+            if D.data[k] < 0: u[i] = D.indices[k]
+            else: v[i] = D.indices[k]
+    np.testing.assert_allclose(X[:, 15], look(Pd, u[rows], ja), rtol=1e-6, atol=1e-7)
+    np.testing.assert_allclose(X[:, 16], look(Pd, u[rows], jb), rtol=1e-6, atol=1e-7)
+    np.testing.assert_allclose(X[:, 17], look(Pd, v[rows], ja), rtol=1e-6, atol=1e-7)
+    np.testing.assert_allclose(X[:, 18], look(Pd, v[rows], jb), rtol=1e-6, atol=1e-7)
+    assert np.all(X[:, 19] == 0)
+    # A_e row scaling and sigma
+    diag = A.diagonal()
+    l1 = np.asarray(abs(A).sum(axis=1)).ravel()
+    np.testing.assert_allclose(X[:, 20], (diag / l1)[rows], rtol=1e-5)
+    np.testing.assert_allclose(X[:, 21], (np.log10(p.sigma_edge) / 6.0)[rows], rtol=1e-5, atol=1e-6)
+    h.destroy()
