@@ -545,7 +545,8 @@ int coarse_gradient(const DCSR& D, const DCSR& Dt, const int32_t* agg, int64_t n
 // the sorted row.
 __global__ void k_pattern(const int64_t* trp, const int32_t* tci, int64_t ne, const int32_t* rows, const int64_t* htrp,
                           const int32_t* htci, const int64_t* hrp, const int32_t* hci, int mode, int64_t* cnt,
-                          const int64_t* nrp, int32_t* nci, int* stats /*0 too big T, 1 too big N, 2 disconnected, 3 max N, 4 max T*/) {
+                          const int64_t* nrp, int32_t* nci, int* stats /*0 too big T, 1 too big N, 2 disconnected*/,
+                          int32_t* bad /* disconnected rows (mode 0), or null */) {
     __shared__ int32_t s_T[PAT_WARPS][MAX_T];
     __shared__ int32_t s_N[PAT_WARPS][MAX_NP];
     __shared__ int s_n[PAT_WARPS];
@@ -602,7 +603,10 @@ __global__ void k_pattern(const int64_t* trp, const int32_t* tci, int64_t ne, co
                 }
                 int roots = 0;
                 for (int q = 0; q < m; ++q) roots += (par[q] == q);
-                if (roots > 1) atomicAdd(&stats[2], 1);
+                if (roots > 1) {
+                    int pos = atomicAdd(&stats[2], 1);
+                    if (bad) bad[pos] = (int32_t)i;
+                }
             }
         }
         return;
@@ -645,7 +649,7 @@ __global__ void __launch_bounds__(128)
 k_pattern_rows(const int64_t* __restrict__ trp, const int32_t* __restrict__ tci, int64_t ne,
                const int64_t* __restrict__ htrp, const int32_t* __restrict__ htci, const int64_t* __restrict__ hrp,
                const int32_t* __restrict__ hci, int mode, int64_t* cnt, const int64_t* __restrict__ nrp,
-               int32_t* __restrict__ nci, int* stats, int32_t* big, int* nbig) {
+               int32_t* __restrict__ nci, int* stats, int32_t* big, int* nbig, int32_t* bad) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ne) return;
     int64_t t0 = trp[i];
@@ -682,7 +686,10 @@ k_pattern_rows(const int64_t* __restrict__ trp, const int32_t* __restrict__ tci,
                     if ((reach >> a) & 1u) nr |= (uint32_t)((adj >> (8 * a)) & 0xffull);
                 reach = nr;
             }
-            if (reach != (1u << m) - 1u) atomicAdd(&stats[2], 1);
+            if (reach != (1u << m) - 1u) {
+                int pos = atomicAdd(&stats[2], 1);
+                if (bad) bad[pos] = (int32_t)i;
+            }
         }
         return;
     }
@@ -711,6 +718,197 @@ k_pattern_rows(const int64_t* __restrict__ trp, const int32_t* __restrict__ tci,
                 int c;
                 while (cur[a] < end[a] && !pat_take(hrp, hci, T, m, htci[cur[a]], T[a], &c)) ++cur[a];
             }
+    }
+}
+
+// ------------------------------------------------------------------ make_irreducible (Alg. 2)
+// For every row whose local graph (nodes T_i, two-node coarse edges of N_i) is disconnected: join
+// two components by the pair of coarse nodes (u, v) in different components with the largest
+// |Z_uv|, Z = P_n^T D_h^T D_h P_n (the columns of D_h P_n are the rows of T^T), values within a
+// relative 1e-9 of the largest counting as ties (the first pair in (a, b) order wins), until the
+// row is connected.  Z_uv is summed in increasing fine-edge order without fused multiply-add.
+// The new pairs are merged into D_H (sorted pairs first, then the single-node rows) and the
+// pattern is rebuilt; at most 8 passes.
+constexpr int IRR_WARPS = 4;
+constexpr int IRR_MAXP = MAX_T * (MAX_T - 1) / 2;
+constexpr int IRR_CAP = 4096;              // new pairs one pass may add (before removing duplicates)
+
+__global__ void __launch_bounds__(IRR_WARPS * 32)
+k_irreducible(const int32_t* __restrict__ bad, int nbad, const int64_t* __restrict__ trp,
+              const int32_t* __restrict__ tci, const int64_t* __restrict__ htrp, const int32_t* __restrict__ htci,
+              const int64_t* __restrict__ hrp, const int32_t* __restrict__ hci, const int64_t* __restrict__ mrp,
+              const int32_t* __restrict__ mci, const double* __restrict__ mv, uint64_t* pairs, int* npairs,
+              int* overflow) {
+    __shared__ int32_t s_J[IRR_WARPS][MAX_T];
+    __shared__ int32_t s_comp[IRR_WARPS][MAX_T];
+    __shared__ double s_z[IRR_WARPS][IRR_MAXP];
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int li = blockIdx.x * IRR_WARPS + w;
+    if (li >= nbad) return;
+    int64_t i = bad[li];
+    int64_t t0 = trp[i];
+    int m = (int)(trp[i + 1] - t0);
+    if (m > MAX_T) return;                 // rejected by the pattern step already
+    if (lane < m) s_J[w][lane] = tci[t0 + lane];
+    __syncwarp();
+    // components of the local graph (lane 0; union by the smaller index)
+    int nc = 0;
+    if (lane == 0) {
+        int par[MAX_T];
+        for (int q = 0; q < m; ++q) par[q] = q;
+        for (int a = 0; a < m; ++a) {
+            int32_t J = s_J[w][a];
+            for (int64_t k = htrp[J]; k < htrp[J + 1]; ++k) {
+                int32_t e = htci[k];
+                int64_t b = hrp[e];
+                if (hrp[e + 1] - b != 2 || hci[b] != J) continue;
+                int c = -1;
+                for (int q = 0; q < m; ++q) if (s_J[w][q] == hci[b + 1]) c = q;
+                if (c < 0) continue;
+                int ra = a, rc = c;
+                while (par[ra] != ra) ra = par[ra];
+                while (par[rc] != rc) rc = par[rc];
+                if (ra != rc) par[ra > rc ? ra : rc] = ra > rc ? rc : ra;
+            }
+        }
+        for (int q = 0; q < m; ++q) {
+            int r = q;
+            while (par[r] != r) r = par[r];
+            s_comp[w][q] = r;
+            nc += (r == q);
+        }
+    }
+    nc = __shfl_sync(0xffffffffu, nc, 0);
+    // |Z_uv| of every pair (a < b), in (a, b) order
+    int npair = m * (m - 1) / 2;
+    for (int p = lane; p < npair; p += 32) {
+        int a = 0, rem = p;
+        while (rem >= m - 1 - a) { rem -= m - 1 - a; ++a; }
+        int b = a + 1 + rem;
+        int32_t u = s_J[w][a], v = s_J[w][b];
+        int64_t x = mrp[u], xe = mrp[u + 1], y = mrp[v], ye = mrp[v + 1];
+        double z = 0.0;
+        while (x < xe && y < ye) {
+            if (mci[x] < mci[y]) ++x;
+            else if (mci[y] < mci[x]) ++y;
+            else { z = __dadd_rn(z, __dmul_rn(mv[x], mv[y])); ++x; ++y; }
+        }
+        s_z[w][p] = fabs(z);
+    }
+    __syncwarp();
+    while (nc > 1) {
+        double best = -1.0;
+        for (int p = lane; p < npair; p += 32) {
+            int a = 0, rem = p;
+            while (rem >= m - 1 - a) { rem -= m - 1 - a; ++a; }
+            int b = a + 1 + rem;
+            if (s_comp[w][a] != s_comp[w][b] && s_z[w][p] > best) best = s_z[w][p];
+        }
+        for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+        double thr = best * (1.0 - 1e-9);
+        int first = INT32_MAX;
+        for (int p = lane; p < npair; p += 32) {
+            int a = 0, rem = p;
+            while (rem >= m - 1 - a) { rem -= m - 1 - a; ++a; }
+            int b = a + 1 + rem;
+            if (s_comp[w][a] != s_comp[w][b] && s_z[w][p] >= thr) { first = p; break; }
+        }
+        for (int o = 16; o > 0; o >>= 1) first = min(first, __shfl_xor_sync(0xffffffffu, first, o));
+        if (first == INT32_MAX) break;     // cannot happen while nc > 1
+        if (lane == 0) {
+            int a = 0, rem = first;
+            while (rem >= m - 1 - a) { rem -= m - 1 - a; ++a; }
+            int b = a + 1 + rem;
+            int slot = atomicAdd(npairs, 1);
+            if (slot < IRR_CAP) pairs[slot] = ((uint64_t)(uint32_t)s_J[w][a] << 32) | (uint32_t)s_J[w][b];
+            else atomicExch(overflow, 1);
+            int ca = s_comp[w][a], cb = s_comp[w][b];
+            int lo = ca < cb ? ca : cb, hi = ca < cb ? cb : ca;
+            for (int q = 0; q < m; ++q) if (s_comp[w][q] == hi) s_comp[w][q] = lo;
+        }
+        --nc;
+        __syncwarp();
+    }
+}
+
+// key of a two-node coarse edge (rows [0, n2) of D_H are those edges, sorted by key)
+__device__ __forceinline__ uint64_t dh_key(const int64_t* hrp, const int32_t* hci, int64_t j) {
+    int64_t b = hrp[j];
+    return ((uint64_t)(uint32_t)hci[b] << 32) | (uint32_t)hci[b + 1];
+}
+__device__ __forceinline__ int64_t key_lower_bound(const int64_t* hrp, const int32_t* hci, int64_t n2, uint64_t key) {
+    int64_t lo = 0, hi = n2;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (dh_key(hrp, hci, mid) < key) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+// One block: sort the new pairs, drop repeats and pairs already in D_H, count the rest (*nu)
+__global__ void __launch_bounds__(1024)
+k_pairs_unique(uint64_t* pairs, int n, const int64_t* hrp, const int32_t* hci, int64_t n2, int* nu) {
+    __shared__ uint64_t s_k[IRR_CAP];
+    int n2pow = 1;
+    while (n2pow < n) n2pow <<= 1;
+    for (int t = threadIdx.x; t < n2pow; t += blockDim.x) s_k[t] = t < n ? pairs[t] : ~0ull;
+    __syncthreads();
+    for (int size = 2; size <= n2pow; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = threadIdx.x; t < n2pow; t += blockDim.x) {
+                int o = t ^ stride;
+                if (o > t) {
+                    bool up = (t & size) == 0;
+                    if ((s_k[t] > s_k[o]) == up) { uint64_t x = s_k[t]; s_k[t] = s_k[o]; s_k[o] = x; }
+                }
+            }
+            __syncthreads();
+        }
+    if (threadIdx.x == 0) {
+        int q = 0;
+        for (int t = 0; t < n; ++t) {
+            uint64_t k = s_k[t];
+            if (q > 0 && pairs[q - 1] == k) continue;
+            int64_t pos = key_lower_bound(hrp, hci, n2, k);
+            if (pos < n2 && dh_key(hrp, hci, pos) == k) continue;
+            pairs[q++] = k;
+        }
+        *nu = q;
+    }
+}
+// D_H with the nu new pairs merged: pair rows at their sorted positions, single rows after
+__global__ void k_dh_merge(const int64_t* hrp, const int32_t* hci, const double* hv, int64_t nr, int64_t n2,
+                           const uint64_t* pairs, int nu, int64_t* nrp, int32_t* nci, double* nv) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t total = nr + nu;
+    if (t > total) return;
+    int64_t npair = n2 + nu;
+    nrp[t] = t <= npair ? 2 * t : 2 * npair + (t - npair);
+    if (t == total) return;
+    if (t < nr) {
+        int64_t r;
+        if (t < n2) {
+            uint64_t k = dh_key(hrp, hci, t);
+            int lo = 0, hi = nu;                     // new pairs below k
+            while (lo < hi) { int mid = (lo + hi) >> 1; if (pairs[mid] < k) lo = mid + 1; else hi = mid; }
+            r = t + lo;
+            nci[2 * r] = hci[hrp[t]];
+            nci[2 * r + 1] = hci[hrp[t] + 1];
+            nv[2 * r] = hv[hrp[t]];
+            nv[2 * r + 1] = hv[hrp[t] + 1];
+        } else {
+            r = t + nu;
+            int64_t o = 2 * npair + (r - npair);
+            nci[o] = hci[hrp[t]];
+            nv[o] = hv[hrp[t]];
+        }
+    } else {
+        int64_t q = t - nr;                          // new pair q
+        uint64_t k = pairs[q];
+        int64_t r = q + key_lower_bound(hrp, hci, n2, k);
+        nci[2 * r] = (int32_t)(k >> 32);
+        nci[2 * r + 1] = (int32_t)(k & 0xffffffffull);
+        nv[2 * r] = -1.0;
+        nv[2 * r + 1] = 1.0;
     }
 }
 
@@ -1486,39 +1684,72 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
         SPHC_TRY(coarse_gradient(L.D, L.Dt, L.agg.p, L.nagg, L.DH, s));
     }
     Section* sec_pat = new Section(prof, lev_name("setup_pattern", lev).c_str(), s);
-    // T = D P_n (values r), N (Alg. 2)
+    // T = D P_n (values r), N (Alg. 2), made irreducible
     SPHC_TRY(dmul(L.D, L.Pn, L.T, s));
-    DCSR DHt;
-    SPHC_TRY(transpose(L.DH, DHt, s));
+    DCSR DHt, Mt;
     DBuf<int64_t> ncnt;
-    DBuf<int> st;
+    DBuf<int> st, pctl;
+    DBuf<int32_t> pbig, pbad;
+    DBuf<uint64_t> pairs;
     SPHC_TRY(ncnt.alloc(ne + 1, s));
     SPHC_TRY(st.alloc(8, s));
-    SPHC_TRY(st.zero(s));
-    // rows with more than PT_K coarse nodes: warp-per-row kernel through a list (st[6] counts them)
-    DBuf<int32_t> pbig;
     SPHC_TRY(pbig.alloc(ne > 0 ? ne : 1, s));
-    if (ne > 0)
-        SPHC_LAUNCH(k_pattern_rows<<<grid_for(ne, 128), 128, 0, s>>>(L.T.rp.p, L.T.ci.p, ne, DHt.rp.p, DHt.ci.p, L.DH.rp.p,
-                                                                   L.DH.ci.p, 0, ncnt.p, nullptr, nullptr, st.p, pbig.p,
-                                                                   st.p + 6));
-    int hs[8];
-    SPHC_CK(cudaMemcpyAsync(hs, st.p, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
-    SPHC_CK(cudaStreamSynchronize(s));
-    int npbig = hs[6];
-    if (npbig > 0) {
-        SPHC_LAUNCH(k_pattern<<<grid_for(npbig, PAT_WARPS), PAT_WARPS * 32, 0, s>>>(L.T.rp.p, L.T.ci.p, npbig, pbig.p,
-                                                                      DHt.rp.p, DHt.ci.p, L.DH.rp.p, L.DH.ci.p, 0,
-                                                                      ncnt.p, nullptr, nullptr, st.p));
+    SPHC_TRY(pbad.alloc(ne > 0 ? ne : 1, s));
+    SPHC_TRY(pctl.alloc(2, s));
+    int hs[8] = {0};
+    int npbig = 0;
+    L.n_added = 0;
+    for (int pass = 0;; ++pass) {
+        // counts of N_i and disconnected rows against the current D_H; rows with more than
+        // PT_K coarse nodes go to the warp-per-row kernel through a list (st[6] counts them)
+        SPHC_TRY(transpose(L.DH, DHt, s));
+        SPHC_TRY(st.zero(s));
+        if (ne > 0)
+            SPHC_LAUNCH(k_pattern_rows<<<grid_for(ne, 128), 128, 0, s>>>(L.T.rp.p, L.T.ci.p, ne, DHt.rp.p, DHt.ci.p,
+                                                                       L.DH.rp.p, L.DH.ci.p, 0, ncnt.p, nullptr,
+                                                                       nullptr, st.p, pbig.p, st.p + 6, pbad.p));
         SPHC_CK(cudaMemcpyAsync(hs, st.p, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
         SPHC_CK(cudaStreamSynchronize(s));
-    }
-    if (hs[0]) { set_error("level %d: a row of T exceeds %d coarse nodes", lev, MAX_T); return SPHC_ELIMIT; }
-    if (hs[1]) { set_error("level %d: a row of the pattern exceeds %d coarse edges", lev, MAX_NP); return SPHC_ELIMIT; }
-    if (hs[2]) {
-        set_error("level %d: %d rows have a reducible local coarse graph (make_irreducible is not implemented "
-                  "on the GPU)", lev, hs[2]);
-        return SPHC_EINFEASIBLE;
+        npbig = hs[6];
+        if (npbig > 0) {
+            SPHC_LAUNCH(k_pattern<<<grid_for(npbig, PAT_WARPS), PAT_WARPS * 32, 0, s>>>(
+                L.T.rp.p, L.T.ci.p, npbig, pbig.p, DHt.rp.p, DHt.ci.p, L.DH.rp.p, L.DH.ci.p, 0, ncnt.p, nullptr,
+                nullptr, st.p, pbad.p));
+            SPHC_CK(cudaMemcpyAsync(hs, st.p, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
+            SPHC_CK(cudaStreamSynchronize(s));
+        }
+        if (hs[0]) { set_error("level %d: a row of T exceeds %d coarse nodes", lev, MAX_T); return SPHC_ELIMIT; }
+        if (hs[1]) { set_error("level %d: a row of the pattern exceeds %d coarse edges", lev, MAX_NP); return SPHC_ELIMIT; }
+        int nbad = hs[2];
+        if (nbad == 0 || pass == 8) break;
+        // make_irreducible: new coarse edges joining the components of the disconnected rows
+        if (Mt.nr == 0) SPHC_TRY(transpose(L.T, Mt, s));
+        SPHC_TRY(pairs.alloc(IRR_CAP, s));
+        SPHC_TRY(pctl.zero(s));
+        SPHC_LAUNCH(k_irreducible<<<grid_for(nbad, IRR_WARPS), IRR_WARPS * 32, 0, s>>>(
+            pbad.p, nbad, L.T.rp.p, L.T.ci.p, DHt.rp.p, DHt.ci.p, L.DH.rp.p, L.DH.ci.p, Mt.rp.p, Mt.ci.p, Mt.v.p,
+            pairs.p, pctl.p, pctl.p + 1));
+        int hp[2];
+        SPHC_CK(cudaMemcpyAsync(hp, pctl.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        SPHC_CK(cudaStreamSynchronize(s));
+        if (hp[1]) {
+            set_error("level %d: make_irreducible would add more than %d coarse edges in one pass", lev, IRR_CAP);
+            return SPHC_ELIMIT;
+        }
+        if (hp[0] == 0) break;
+        int64_t n2 = L.DH.nnz - L.DH.nr;                 // two-node rows come first
+        SPHC_LAUNCH(k_pairs_unique<<<1, 1024, 0, s>>>(pairs.p, hp[0], L.DH.rp.p, L.DH.ci.p, n2, pctl.p));
+        int nu = 0;
+        SPHC_CK(cudaMemcpyAsync(&nu, pctl.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+        SPHC_CK(cudaStreamSynchronize(s));
+        if (nu == 0) break;
+        DCSR H2;
+        SPHC_TRY(H2.alloc(L.DH.nr + nu, L.DH.nc, L.DH.nnz + 2 * (int64_t)nu, s));
+        SPHC_LAUNCH(k_dh_merge<<<grid_for(L.DH.nr + nu + 1, 256), 256, 0, s>>>(L.DH.rp.p, L.DH.ci.p, L.DH.v.p, L.DH.nr,
+                                                                              n2, pairs.p, nu, H2.rp.p, H2.ci.p,
+                                                                              H2.v.p));
+        L.DH = std::move(H2);
+        L.n_added += nu;
     }
     SPHC_TRY(max_row_length(L.T.rp.p, ne, s, &L.max_m));
     int64_t nnzN = 0;
@@ -1531,11 +1762,11 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
     if (ne > 0)
         SPHC_LAUNCH(k_pattern_rows<<<grid_for(ne, 128), 128, 0, s>>>(L.T.rp.p, L.T.ci.p, ne, DHt.rp.p, DHt.ci.p, L.DH.rp.p,
                                                                    L.DH.ci.p, 1, nullptr, L.P0.rp.p, L.P0.ci.p, st.p,
-                                                                   nullptr, nullptr));
+                                                                   nullptr, nullptr, nullptr));
     if (npbig > 0)
         SPHC_LAUNCH(k_pattern<<<grid_for(npbig, PAT_WARPS), PAT_WARPS * 32, 0, s>>>(L.T.rp.p, L.T.ci.p, npbig, pbig.p,
                                                                       DHt.rp.p, DHt.ci.p, L.DH.rp.p, L.DH.ci.p, 1,
-                                                                      nullptr, L.P0.rp.p, L.P0.ci.p, st.p));
+                                                                      nullptr, L.P0.rp.p, L.P0.ci.p, st.p, nullptr));
     delete sec_pat;
     // learned warm start: the MLP correction of every pattern entry (its features do not depend
     // on P0), passed to the P0 kernel, which projects it onto the row constraints

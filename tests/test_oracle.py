@@ -344,3 +344,56 @@ def test_config1_iterations():
     h = oracle.setup_problem(p)
     r = h.solve(meshgen.rhs(seed, p.n_edges))
     assert r["status"] == 0 and r["relres"] <= 1e-8 and r["iters"] <= 30
+
+
+def test_make_irreducible_joins_every_local_graph():
+    """make_irreducible (Alg. 2, Sec. 4.2): on an input with reducible local graphs it adds coarse
+    edges; afterwards every row's local graph (T_i, two-node edges of N_i) is connected, each
+    added edge joins two coarse nodes of one T_i with Z_uv = (P_n^T D_h^T D_h P_n)_uv != 0, and
+    the prolongator still satisfies P_e D_H = D_h P_n."""
+    import scipy.sparse as sp
+    from irr_case import coupled_problem
+    p, arp, aci, av = coupled_problem()
+    o = oracle.setup(p.n_edges, p.n_nodes, (arp, aci, av), (p.D_rowptr, p.D_col, p.D_val), max_coarse=50)
+    assert o.status == 0
+    s = o.sizes(0)
+    assert s["n_infeasible0"] > 0 and s["n_added"] > 0
+    csr = lambda name: (lambda M: sp.csr_matrix((M.val, M.col, M.rowptr), shape=M.shape))(o.matrix(0, name))
+    T, DH, Pn, Pe, N = csr("T"), csr("DH"), csr("Pn"), csr("Pe"), csr("Pe")
+    D = sp.csr_matrix((p.D_val, p.D_col, p.D_rowptr), shape=(p.n_edges, p.n_nodes))
+    # every local graph connected
+    pairs = {}
+    for j in range(DH.shape[0]):
+        c = DH.indices[DH.indptr[j]:DH.indptr[j + 1]]
+        if len(c) == 2:
+            pairs[j] = (int(c[0]), int(c[1]))
+    for i in range(T.shape[0]):
+        J = list(T.indices[T.indptr[i]:T.indptr[i + 1]])
+        if len(J) <= 1:
+            continue
+        par = {u: u for u in J}
+        def find(u):
+            while par[u] != u:
+                u = par[u]
+            return u
+        for j in N.indices[N.indptr[i]:N.indptr[i + 1]]:
+            if j in pairs:
+                a, b = pairs[j]
+                par[find(a)] = find(b)
+        assert len({find(u) for u in J}) == 1, i
+    # added edges: not in the RS gradient of the aggregates, Z != 0, inside some T_i
+    Z = (T.T @ T).tocsr()
+    n2 = DH.nnz - DH.shape[0]
+    agg = o.ivec(0, "agg")
+    Pbar = sp.csr_matrix((np.ones(p.n_nodes), (np.arange(p.n_nodes), agg)), shape=(p.n_nodes, agg.max() + 1))
+    rs = (Pbar.T @ D.T @ D @ Pbar).tocsr()
+    Tsets = [set(T.indices[T.indptr[i]:T.indptr[i + 1]]) for i in range(T.shape[0])]
+    added = [pairs[j] for j in range(n2) if rs[pairs[j][0], pairs[j][1]] == 0]
+    assert len(added) == s["n_added"]
+    for u, v in added:
+        assert Z[u, v] != 0
+        assert any(u in t and v in t for t in Tsets)
+    # commuting relation
+    lhs = (Pe @ DH).toarray()
+    rhs = (D @ Pn).toarray()
+    assert np.abs(lhs - rhs).max() <= 1e-12 * max(1.0, np.abs(rhs).max())
