@@ -73,7 +73,12 @@ typedef struct {
     int32_t learned_emin_iters; /* energy-minimisation steps after the learned warm start (default 0) */
     const float* mlp_params; /* SPHC_MLP_NPARAM floats (host or device), see sphc_mlp_train */
     int32_t autotune;        /* 1: time the smoother kernels' lanes-per-row widths at setup (default 0) */
-    int32_t reserved[3];
+    int32_t sweep_form;      /* smoothers with more rows than one thread block sweeps: 0 a cost model
+                                picks between one launch per colour and one launch per sweep on a
+                                thread-block cluster (x in shared memory, where it fits); 1 always
+                                a launch per colour; 2 the cluster wherever x fits (default 0;
+                                autotune overrides it) */
+    int32_t reserved[2];
 } sphc_opts;
 
 /* Learned warm start (not part of the paper).  For every pattern entry (i, j) of P_e a
@@ -120,6 +125,9 @@ typedef struct {
     /* Jones-Plassmann rounds run by the edge and node colourings (8 per device-loop iteration,
      * so up to 7 more than the rounds that coloured something) */
     int32_t colour_rounds_edge, colour_rounds_node;
+    /* smoother sweep form: 0 one launch per colour, 1 one launch per sweep on one thread-block
+     * cluster (x held in shared memory), 2 one launch per sweep on one thread block */
+    int32_t sweep_kind_edge, sweep_kind_node;
 } sphc_level_info;
 
 typedef struct {

@@ -93,6 +93,10 @@ int setup_impl(sphc_handle* h, const sphc_csr* A_e, const sphc_csr* D_h, const d
                const double* sigma_edge, cudaStream_t s) {
     Hierarchy& H = h->H;
     const sphc_opts& o = H.opts;
+    if (o.sweep_form < 0 || o.sweep_form > 2) {
+        set_error("opts.sweep_form must be 0, 1 or 2 (got %d)", (int)o.sweep_form);
+        return SPHC_EINVAL;
+    }
     H.L.clear();
     H.L.reserve(o.max_levels > 0 ? o.max_levels : 1);
     H.L.emplace_back();
@@ -356,6 +360,8 @@ int sphc_get_level_info(const sphc_handle* h, int level, sphc_level_info* info) 
         info->sell_lpr_node = V[level].An.m.lpr * (V[level].An.m.nslice > 0);
         info->sell_ch_node = V[level].An.m.ch * (V[level].An.m.nslice > 0);
         info->sell_stored_node = V[level].An.m.stored;
+        info->sweep_kind_edge = sweep_kind(V[level].A);
+        info->sweep_kind_node = sweep_kind(V[level].An);
     };
     if (H.opts.vcycle_fp32) shape(H.V32); else shape(H.V64);
     return SPHC_OK;

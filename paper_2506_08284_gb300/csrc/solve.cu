@@ -6,9 +6,12 @@
 #include <cstring>
 #include <string>
 
+#include <cooperative_groups.h>
+
 #include "sphc_level.cuh"
 
 namespace sphc {
+namespace cg = cooperative_groups;
 
 static constexpr int DOT_PARTS = 1024;
 
@@ -70,6 +73,9 @@ static int build_orders(Hierarchy& H, cudaStream_t s) {
 }
 
 template <typename T>
+static bool cluster_sgs_chosen(const SmoothOp<T>& op, int sweep_form);
+
+template <typename T>
 static int build_vlevel(Hierarchy& H, int l, VLevel<T>& V, bool split, cudaStream_t s) {
     Level& L = H.L[l];
     const LevelOrder& O = H.ord[l];
@@ -95,6 +101,8 @@ static int build_vlevel(Hierarchy& H, int l, VLevel<T>& V, bool split, cudaStrea
     }
     SPHC_TRY(build_smooth<T>(L.A, O.pe.p, O.ie.p, O.ce, 0, 0, V.A, s));
     SPHC_TRY(build_smooth<T>(L.An, O.pn.p, O.in.p, O.cn, 0, 0, V.An, s));
+    V.A.cluster = cluster_sgs_chosen(V.A, H.opts.sweep_form) ? 1 : 0;
+    V.An.cluster = cluster_sgs_chosen(V.An, H.opts.sweep_form) ? 1 : 0;
     SPHC_TRY(build_xop<T>(L.Pe, O.pe.p, C.ie.p, V.Pe, s));
     SPHC_TRY(build_xop<T>(L.PeT, C.pe.p, O.ie.p, V.PeT, s));
     SPHC_CK(cudaGetLastError());
@@ -290,6 +298,38 @@ __device__ __forceinline__ SliceRow slice_row(const int32_t* __restrict__ srow, 
     return q;
 }
 
+// The first batch (up to four steps) of a lane's loads of one slice, loaded ahead of the barrier
+// that precedes its gathers (the cluster sweep).
+template <typename T, int CH>
+struct SellHead {
+    static constexpr int U = 4;
+    T a[U][CH];
+    int32_t c[U][CH];
+    int n;
+    __device__ __forceinline__ void load(const int32_t* __restrict__ ci, const T* __restrict__ v, int64_t o,
+                                         int64_t steps, int lane) {
+        n = steps < U ? (int)steps : U;
+        const T* vp = v + o + lane * CH;
+        const int32_t* cp = ci + o + lane * CH;
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (u < n) {
+                Chunk<T, CH>::load(vp + u * SELL_C * CH, a[u]);
+                IChunk<CH>::load(cp + u * SELL_C * CH, c[u]);
+            }
+    }
+    __device__ __forceinline__ T finish(const int32_t* __restrict__ ci, const T* __restrict__ v, int64_t o,
+                                        int64_t steps, int lane, const T* x) const {
+        T sum = 0;
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (u < n)
+#pragma unroll
+                for (int t = 0; t < CH; ++t) sum += a[u][t] * x[c[u][t]];
+        if (steps > n) sum += sell_part<T, CH>(ci, v, o + (int64_t)n * SELL_C * CH, steps - n, lane, x);
+        return sum;
+    }
+};
 // Gauss-Seidel update of the rows of slices [s0, s1) (one colour): x_r += (b_r - (A x)_r) / a_rr
 template <typename T, int CH>
 __global__ void __launch_bounds__(256)
@@ -339,7 +379,6 @@ k_sell_spmv(const int64_t* __restrict__ soff, const int32_t* __restrict__ srow, 
 }
 // A whole forward + backward sweep of a small operator in one block: colours are separated by
 // block barriers instead of kernel boundaries (the coarse levels are launch-bound otherwise).
-static constexpr int SGS_BLOCK_MAX_ROWS = 2048;
 template <typename T, int CH>
 __global__ void __launch_bounds__(1024)
 k_sell_sgs_block(const int64_t* __restrict__ soff, const int32_t* __restrict__ srow,
@@ -357,6 +396,77 @@ k_sell_sgs_block(const int64_t* __restrict__ soff, const int32_t* __restrict__ s
         }
         __syncthreads();
     }
+}
+
+// A whole forward + backward sweep of a mid-sized operator (x small enough for shared memory) on
+// one thread-block cluster.  Every CTA keeps a copy of x in its shared memory; the new value of a
+// row is stored into every copy through distributed shared memory, and a cluster barrier (release
+// / acquire) separates the colours.  The gathers of x then hit shared memory and the colours cost
+// a cluster barrier instead of a kernel boundary.  Warp gw of the cluster takes the slices
+// gw, gw + nw, ... of each colour and loads the head of its next slice before the barrier.  At
+// the end every copy holds the result; each CTA writes back a share.
+// (A deeper per-warp pipeline, with the bounds of the slice after next also in flight, measured
+// slower: 1.19 against 0.81 ms for the level-2 pre-smoothing of the 128^3 problem.)
+static constexpr int SGS_CLUSTER = 8;
+// threads per CTA: 1024 (64 registers) for FP32, 512 for FP64, which needs more registers
+template <typename T>
+struct SgsClusterThreads {
+    static constexpr int value = sizeof(T) == 4 ? 1024 : 512;
+};
+static constexpr int64_t SGS_CLUSTER_MAX_BYTES = 200 * 1024;
+template <typename T, int CH>
+__global__ void __launch_bounds__(SgsClusterThreads<T>::value)
+k_sell_sgs_cluster(const int64_t* __restrict__ soff, const int32_t* __restrict__ srow,
+                   const int64_t* __restrict__ cslice, int ncolor, int lpr, int64_t n,
+                   const int32_t* __restrict__ ci, const T* __restrict__ v, const T* __restrict__ dinv,
+                   const T* __restrict__ b, T* __restrict__ x) {
+    extern __shared__ __align__(16) unsigned char sgs_smem[];
+    T* xs = reinterpret_cast<T*>(sgs_smem);
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank(), ncta = (int)cl.num_blocks();
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = (int64_t)rank * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int64_t nw = (int64_t)ncta * (blockDim.x >> 5);
+    // the warp's current slice: its head loads, its row, and (after the wait) b_r and 1 / a_rr
+    int64_t sl = 0, end = 0, o = 0, steps = 0;
+    int32_t r = 0;
+    bool have = false, valid = false;
+    T br = 0, dr = 0;
+    SellHead<T, CH> h;
+    h.n = 0;
+    auto fetch = [&](int64_t s_, int64_t e_, bool rhs) {
+        sl = s_;
+        end = e_;
+        have = sl < end;
+        if (!have) return;
+        o = soff[sl];
+        steps = (soff[sl + 1] - o) / (SELL_C * CH);
+        r = srow[sl] + lane / lpr;
+        valid = r < srow[sl + 1];
+        h.load(ci, v, o, steps, lane);
+        if (rhs && valid) { br = b[r]; dr = dinv[r]; }
+    };
+    fetch(cslice[0] + gw, cslice[1], false);          // matrix only before the wait
+    pdl_enter();
+    if (have && valid) { br = b[r]; dr = dinv[r]; }
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) xs[i] = x[i];
+    cl.sync();
+    for (int step = 0; step < 2 * ncolor; ++step) {
+        while (have) {
+            T sum = row_reduce(h.finish(ci, v, o, steps, lane, xs), lpr);
+            if (valid) {
+                T xn = xs[r] + (br - sum) * dr;
+                for (int k = lane & (lpr - 1); k < ncta; k += lpr) *cl.map_shared_rank(xs + r, k) = xn;
+            }
+            fetch(sl + nw, end, true);
+        }
+        if (step + 1 < 2 * ncolor) {                     // head of the next colour's first slice
+            const int cn = step + 1 < ncolor ? step + 1 : 2 * ncolor - 2 - step;
+            fetch(cslice[cn] + gw, cslice[cn + 1], true);
+        }
+        cl.sync();
+    }
+    for (int64_t i = (int64_t)rank * blockDim.x + threadIdx.x; i < n; i += (int64_t)ncta * blockDim.x) x[i] = xs[i];
 }
 
 template <typename T, int SUB>
@@ -441,10 +551,91 @@ static unsigned slice_grid(int64_t nslice) { return (unsigned)grid_for(nslice * 
         default: F(4); break; \
     }
 
+// one launch of the cluster sweep (shared memory for x; programmatic launch outside capture)
+template <typename T, int CH>
+static cudaError_t launch_sgs_cluster(const SmoothOp<T>& op, const T* b, T* x, cudaStream_t s) {
+    const Sell<T>& m = op.m;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(SGS_CLUSTER);
+    cfg.blockDim = dim3(SgsClusterThreads<T>::value);
+    cfg.dynamicSmemBytes = (size_t)op.n * sizeof(T);
+    cfg.stream = s;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s, &cap);
+    cudaLaunchAttribute at[2];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = SGS_CLUSTER;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[1].val.programmaticStreamSerializationAllowed = cap == cudaStreamCaptureStatusNone ? 1 : 0;
+    cfg.attrs = at;
+    cfg.numAttrs = 2;
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return cudaLaunchKernelEx(&cfg, k_sell_sgs_cluster<T, CH>, m.soff.p, m.srow.p, op.cslice_dev.p, op.ncolor, m.lpr,
+                              op.n, m.ci.p, m.v.p, op.dinv.p, b, x);
+}
+// Whether the cluster sweep can run op on this device: x fits the shared memory of a CTA and a
+// cluster of that shape can be resident (sets the kernels' shared-memory limit on the way).
+template <typename T>
+static bool cluster_sgs_fits(const SmoothOp<T>& op) {
+    if (op.n <= SGS_BLOCK_MAX_ROWS || (int64_t)op.n * (int64_t)sizeof(T) > SGS_CLUSTER_MAX_BYTES) return false;
+    void (*ks[3])(const int64_t*, const int32_t*, const int64_t*, int, int, int64_t, const int32_t*, const T*,
+                  const T*, const T*, T*) = {k_sell_sgs_cluster<T, 1>, k_sell_sgs_cluster<T, 2>,
+                                             k_sell_sgs_cluster<T, 4>};
+    for (auto k : ks)
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SGS_CLUSTER_MAX_BYTES) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(SGS_CLUSTER);
+    cfg.blockDim = dim3(SgsClusterThreads<T>::value);
+    cfg.dynamicSmemBytes = (size_t)op.n * sizeof(T);
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = SGS_CLUSTER;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nclus = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclus, ks[0], &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return nclus > 0;
+}
+// Sweep cost model used without the autotuner (microseconds per forward + backward sweep), from
+// the 128^3 level-2 smoother (6.6K rows, 73 colours): a colour launch costs about 4 us of latency
+// and the launches stream at HBM speed; the cluster sweep pays about 2 us per colour and streams
+// at the bandwidth of its 8 SMs.
+template <typename T>
+static bool cluster_sgs_preferred(const SmoothOp<T>& op) {
+    double bytes = (double)op.m.stored * (sizeof(T) + 4);
+    double t_launch = 2.0 * op.ncolor * 4.0 + 2.0 * bytes / 5.0e6;
+    double t_cluster = 2.0 * op.ncolor * 2.0 + 2.0 * bytes / 0.5e6;
+    return t_cluster < t_launch && cluster_sgs_fits(op);
+}
+// the sweep form of op under sphc_opts.sweep_form
+template <typename T>
+static bool cluster_sgs_chosen(const SmoothOp<T>& op, int sweep_form) {
+    if (sweep_form == 1) return false;
+    if (sweep_form == 2) return cluster_sgs_fits(op);
+    return cluster_sgs_preferred(op);
+}
+
 template <typename T>
 static void sgs(const SmoothOp<T>& op, const T* b, T* x, cudaStream_t s) {
     const Sell<T>& m = op.m;
     if (op.n == 0) return;
+    if (op.cluster) {
+#define F(C) launch_sgs_cluster<T, C>(op, b, x, s)
+        SPHC_CH_SWITCH(m.ch, F)
+#undef F
+        return;
+    }
     if (op.n <= SGS_BLOCK_MAX_ROWS) {
 #define F(C) launch_pdl(k_sell_sgs_block<T, C>, 1, 1024, 0, s, m.soff.p, m.srow.p, op.cslice_dev.p, op.ncolor, m.lpr, m.ci.p, m.v.p, op.dinv.p, b, x)
         SPHC_CH_SWITCH(m.ch, F)
@@ -701,7 +892,7 @@ static int autotune_op(const DCSR& A, const int32_t* rmap, const int32_t* cmap, 
     launch_pdl(k_zero<T>, grid_for(op.n, 256), 256, 0, s, xvec.p, op.n);
     int l0 = sell_lpr_for(A, (int)cstart.size() - 1);
     float best = 1e30f;
-    int best_ch = op.m.ch, best_lpr = op.m.lpr;
+    int best_ch = op.m.ch, best_lpr = op.m.lpr, best_cluster = op.cluster;
     int rc = SPHC_OK;
     for (int lpr : {l0 / 2, l0, 2 * l0}) {
         if (lpr < 1 || lpr > SELL_C) continue;
@@ -709,14 +900,19 @@ static int autotune_op(const DCSR& A, const int32_t* rmap, const int32_t* cmap, 
             if ((ch != op.m.ch || lpr != op.m.lpr) &&
                 (rc = build_smooth<T>(A, rmap, cmap, cstart, ch, lpr, op, s)) != SPHC_OK)
                 break;
-            sgs(op, bvec.p, xvec.p, s);               // warm-up
-            cudaEventRecord(e0, s);
-            for (int rep = 0; rep < 3; ++rep) sgs(op, bvec.p, xvec.p, s);
-            cudaEventRecord(e1, s);
-            if (cudaEventSynchronize(e1) != cudaSuccess) { rc = SPHC_ECUDA; break; }
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < best) { best = ms; best_ch = ch; best_lpr = lpr; }
+            bool fits = cluster_sgs_fits(op);
+            for (int cl = 0; cl <= (fits ? 1 : 0); ++cl) {
+                op.cluster = cl;
+                sgs(op, bvec.p, xvec.p, s);               // warm-up
+                cudaEventRecord(e0, s);
+                for (int rep = 0; rep < 3; ++rep) sgs(op, bvec.p, xvec.p, s);
+                cudaEventRecord(e1, s);
+                if (cudaEventSynchronize(e1) != cudaSuccess) { rc = SPHC_ECUDA; break; }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best) { best = ms; best_ch = ch; best_lpr = lpr; best_cluster = cl; }
+            }
+            if (rc != SPHC_OK) break;
         }
         if (rc != SPHC_OK) break;
     }
@@ -725,6 +921,7 @@ static int autotune_op(const DCSR& A, const int32_t* rmap, const int32_t* cmap, 
     if (rc != SPHC_OK) return rc;
     if (op.m.ch != best_ch || op.m.lpr != best_lpr)
         SPHC_TRY(build_smooth<T>(A, rmap, cmap, cstart, best_ch, best_lpr, op, s));
+    op.cluster = best_cluster;
     return SPHC_OK;
 }
 

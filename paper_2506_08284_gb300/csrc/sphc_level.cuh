@@ -40,7 +40,18 @@ struct SmoothOp {
     DBuf<int64_t> cslice_dev;
     Sell<T> m;
     DBuf<T> dinv;
+    int cluster = 0;                 // 1: whole sweeps on one thread-block cluster (x in shared memory)
 };
+// smoothers of at most this many rows sweep in one thread block (colours separated by block
+// barriers)
+static constexpr int SGS_BLOCK_MAX_ROWS = 2048;
+// how sgs() runs op: 0 a launch per colour, 1 the cluster sweep, 2 the one-block sweep
+template <typename T>
+inline int sweep_kind(const SmoothOp<T>& op) {
+    if (op.n == 0) return 0;
+    if (op.cluster) return 1;
+    return op.n <= SGS_BLOCK_MAX_ROWS ? 2 : 0;
+}
 
 // Plain CSR in the V-cycle precision.
 template <typename T>

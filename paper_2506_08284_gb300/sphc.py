@@ -37,7 +37,7 @@ class sphc_opts(ctypes.Structure):
                 ("vcycle_fp32", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("flexible", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("cg_graph", ctypes.c_int32), ("learned", ctypes.c_int32),
                 ("learned_emin_iters", ctypes.c_int32), ("mlp_params", ctypes.c_void_p),
-                ("autotune", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("autotune", ctypes.c_int32), ("sweep_form", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class sphc_train_opts(ctypes.Structure):
@@ -60,7 +60,8 @@ class sphc_level_info(ctypes.Structure):
                 ("max_T_row", ctypes.c_int64), ("sell_lpr_edge", ctypes.c_int32), ("sell_ch_edge", ctypes.c_int32),
                 ("sell_lpr_node", ctypes.c_int32), ("sell_ch_node", ctypes.c_int32),
                 ("sell_stored_edge", ctypes.c_int64), ("sell_stored_node", ctypes.c_int64),
-                ("colour_rounds_edge", ctypes.c_int32), ("colour_rounds_node", ctypes.c_int32)]
+                ("colour_rounds_edge", ctypes.c_int32), ("colour_rounds_node", ctypes.c_int32),
+                ("sweep_kind_edge", ctypes.c_int32), ("sweep_kind_node", ctypes.c_int32)]
 
 
 class sphc_stats(ctypes.Structure):

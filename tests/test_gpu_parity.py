@@ -116,6 +116,31 @@ def test_fp64_vcycle_matches_oracle(pair):
     assert np.sqrt(e @ (A @ e)) <= FP64_RTOL * np.sqrt(zo @ (A @ zo))
 
 
+@pytest.mark.parametrize("form", [1, 2])
+def test_sweep_forms_match_oracle(pair, form):
+    # the same V-cycle with every smoother above one block swept per colour launch (1) or on one
+    # thread-block cluster (2, where x fits shared memory): both against the oracle
+    name, p, h, o, opts = pair
+    import torch
+    hf = gpu_setup(p, vcycle_fp32=0, sweep_form=form, **opts)
+    kinds = [hf.level_info(l)["sweep_kind_edge"] for l in range(hf.stats()["n_levels"] - 1)]
+    if form == 1:
+        assert 1 not in kinds
+    elif p.n_edges > 2048:
+        assert kinds[0] == 1
+    r = meshgen.rhs(11, p.n_edges)
+    rt = torch.tensor(r, device="cuda")
+    zt = torch.empty_like(rt)
+    hf.vcycle(rt, zt)
+    torch.cuda.synchronize()
+    z = zt.cpu().numpy()
+    zo = o.vcycle(r)
+    A = sp.csr_matrix((p.A_val, p.A_col, p.A_rowptr))
+    e = z - zo
+    assert np.sqrt(e @ (A @ e)) <= FP64_RTOL * np.sqrt(zo @ (A @ zo))
+    hf.destroy()
+
+
 def test_fp32_vcycle_solve(pair):
     name, p, h, o, opts = pair
     h32 = gpu_setup(p, vcycle_fp32=1, **opts)
