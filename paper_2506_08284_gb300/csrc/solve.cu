@@ -1030,8 +1030,11 @@ static int build_cg_graph(Hierarchy& H) {
     H.capturing = false;
     cudaGraph_t captured = nullptr;
     cudaError_t e = cudaStreamEndCapture(H.cap_stream, &captured);
-    if (rc != SPHC_OK) return rc;
-    if (e != cudaSuccess) {
+    if (rc != SPHC_OK || e != cudaSuccess) {
+        // the body graph of a failed capture is left as the runtime leaves it: the handle drops its
+        // reference instead of destroying a graph whose state it does not know (a one-off leak)
+        H.cg_graph = nullptr;
+        if (rc != SPHC_OK) return rc;
         set_error("CG graph capture failed: %s", cudaGetErrorString(e));
         return SPHC_ECUDA;
     }
