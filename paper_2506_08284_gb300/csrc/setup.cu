@@ -23,8 +23,8 @@ static constexpr int MAX_COLORS = 256;
 // advance} on the device, so no round waits for the host (an iteration of the while node costs
 // far more than a round of a small graph; rounds after the last colour has been given only
 // return).  ctrl holds {colour overflow, iterations, then one "rows still waiting" flag per round
-// of an iteration}.  A round visits every row; coloured rows return at once, so no worklist (and
-// no contended counter to append to it) is needed.
+// of an iteration}.  A round visits every row; coloured rows are skipped at once, so no worklist
+// (and no contended counter to append to it) is needed.
 enum { JP_OVERFLOW = 0, JP_ITERS = 1, JP_WAITING = 2 };
 static constexpr int JP_UNROLL = 8;
 static constexpr int JP_MAX_ITERS = 1 << 17;
@@ -48,10 +48,12 @@ __global__ void k_jp_round(const int64_t* __restrict__ rp, const int32_t* __rest
     int lane = threadIdx.x & 31;
     int sub = lane & (G - 1);
     unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
-    int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    const int64_t stride = ((int64_t)gridDim.x * blockDim.x) / G;
     volatile int32_t* col = color;
     bool waiting = false;
-    if (v < n && col[v] < 0) {                     // uniform over the group
+    for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G; v < n; v += stride) {
+        if (col[v] >= 0) continue;                 // uniform over the group
+        bool wv = false;
         uint64_t hv = prio[v];
         int64_t b = rp[v], e = rp[v + 1];
         for (int64_t k0 = b + pos[v]; k0 < e; k0 += G) {
@@ -63,36 +65,38 @@ __global__ void k_jp_round(const int64_t* __restrict__ rp, const int32_t* __rest
             }
             unsigned bal = (__ballot_sync(gmask, blocks) & gmask) >> (lane & ~(G - 1));
             if (bal) {
-                waiting = true;
+                wv = true;
                 if (sub == 0) pos[v] = (int32_t)(k0 + (__ffs(bal) - 1) - b);
                 break;
             }
         }
-        if (!waiting) {
-            uint64_t used[MAX_COLORS / 64] = {0, 0, 0, 0};
-            for (int64_t k = b + sub; k < e; k += G) {
-                int32_t w = ci[k];
-                if (w == v) continue;
-                int32_t c = col[w];
-                if (c >= 0 && c < MAX_COLORS) {
-                    if (c < 64) used[0] |= 1ULL << c;
-                    else if (c < 128) used[1] |= 1ULL << (c - 64);
-                    else if (c < 192) used[2] |= 1ULL << (c - 128);
-                    else used[3] |= 1ULL << (c - 192);
-                }
+        if (wv) {
+            waiting = true;
+            continue;
+        }
+        uint64_t used[MAX_COLORS / 64] = {0, 0, 0, 0};
+        for (int64_t k = b + sub; k < e; k += G) {
+            int32_t w = ci[k];
+            if (w == v) continue;
+            int32_t c = col[w];
+            if (c >= 0 && c < MAX_COLORS) {
+                if (c < 64) used[0] |= 1ULL << c;
+                else if (c < 128) used[1] |= 1ULL << (c - 64);
+                else if (c < 192) used[2] |= 1ULL << (c - 128);
+                else used[3] |= 1ULL << (c - 192);
             }
+        }
 #pragma unroll
-            for (int d = G / 2; d > 0; d >>= 1)
+        for (int d = G / 2; d > 0; d >>= 1)
 #pragma unroll
-                for (int q = 0; q < MAX_COLORS / 64; ++q) used[q] |= __shfl_xor_sync(gmask, used[q], d);
-            if (sub == 0) {
-                int c = MAX_COLORS;
+            for (int q = 0; q < MAX_COLORS / 64; ++q) used[q] |= __shfl_xor_sync(gmask, used[q], d);
+        if (sub == 0) {
+            int c = MAX_COLORS;
 #pragma unroll
-                for (int q = MAX_COLORS / 64 - 1; q >= 0; --q)
-                    if (~used[q]) c = 64 * q + __ffsll((long long)~used[q]) - 1;
-                if (c >= MAX_COLORS) { atomicExch(&ctrl[JP_OVERFLOW], 1); c = MAX_COLORS - 1; }
-                color[v] = c;
-            }
+            for (int q = MAX_COLORS / 64 - 1; q >= 0; --q)
+                if (~used[q]) c = 64 * q + __ffsll((long long)~used[q]) - 1;
+            if (c >= MAX_COLORS) { atomicExch(&ctrl[JP_OVERFLOW], 1); c = MAX_COLORS - 1; }
+            color[v] = c;
         }
     }
     if (__syncthreads_or(waiting) && threadIdx.x == 0) ctrl[JP_WAITING + slot] = 1;
@@ -153,6 +157,13 @@ int color_graph(const DCSR& G, uint64_t seed, DBuf<int32_t>& color, int* ncolors
         if ((e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np)) != cudaSuccess) fail(e, "while node");
     }
     if (rc == SPHC_OK && (e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) fail(e, "stream");
+    // rounds loop over the rows with a grid of one full wave: most rows are coloured after the
+    // first rounds, and a grid over all rows would pay block scheduling for them every round
+    // (an appended list of waiting rows measured slower: its counter is contended)
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm <= 0) nsm = 1;
     if (rc == SPHC_OK) {
         cudaGraph_t body = np.conditional.phGraph_out[0];
         if ((e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
@@ -167,7 +178,7 @@ int color_graph(const DCSR& G, uint64_t seed, DBuf<int32_t>& color, int* ncolors
                 while (lanes < 32 && lanes < avg) lanes *= 2;
             }
             for (int q = 0; q < JP_UNROLL; ++q) {
-                unsigned blocks = (unsigned)grid_for(n * lanes, 256);
+                unsigned blocks = (unsigned)std::min<int64_t>(grid_for(n * lanes, 256), (int64_t)nsm * 8);
                 switch (lanes) {
                     case 1: k_jp_round<1><<<blocks, 256, 0, cs>>>(G.rp.p, G.ci.p, prio.p, n, ctrl.p, q, pos.p, color.p); break;
                     case 4: k_jp_round<4><<<blocks, 256, 0, cs>>>(G.rp.p, G.ci.p, prio.p, n, ctrl.p, q, pos.p, color.p); break;
