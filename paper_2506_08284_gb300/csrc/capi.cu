@@ -137,7 +137,10 @@ int setup_impl(sphc_handle* h, const sphc_csr* A_e, const sphc_csr* D_h, const d
     }
     {
         Section sec(prof, "setup_nodal_op", s);
-        SPHC_TRY(spgemm(L0.A, L0.D, L0.AD, s));
+        {
+            Section sub(prof, "setup_nodal_AD", s);
+            SPHC_TRY(spgemm(L0.A, L0.D, L0.AD, s));
+        }
         SPHC_TRY(spgemm_sym(L0.Dt, L0.AD, L0.An, s));
     }
     int lev = 0;

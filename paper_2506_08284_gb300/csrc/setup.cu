@@ -1870,8 +1870,14 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
         int rid = prof ? prof->find(lev_name("rap_level", lev).c_str(), 0.0) : -1;
         if (rid >= 0) prof->begin(rid, s);
         DCSR AP;
-        SPHC_TRY(spgemm(L.A, L.Pe, AP, s));
-        SPHC_TRY(spgemm_sym(L.PeT, AP, Anext, s));
+        {
+            Section sec(prof, lev_name("rap_AP", lev).c_str(), s);
+            SPHC_TRY(spgemm(L.A, L.Pe, AP, s));
+        }
+        {
+            Section sec(prof, lev_name("rap_PtAP", lev).c_str(), s);
+            SPHC_TRY(spgemm_sym(L.PeT, AP, Anext, s));
+        }
         if (rid >= 0) prof->end(rid, s);
     }
     {

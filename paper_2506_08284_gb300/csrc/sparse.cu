@@ -421,18 +421,31 @@ __device__ inline int64_t row_floor(const int64_t* brp, const int32_t* bci, int3
 __device__ inline int spgemm_bin_of(int64_t ub, int64_t alen) {
     return (ub <= 64 && alen <= 64) ? 0 : (ub <= 256 ? 1 : 2);
 }
+// Product count (restricted to the upper triangle when `upper`) of every row, G lanes per row
+// (rows of long A rows, such as the P^T factors of coarse Galerkin products, would otherwise
+// walk their entries' binary searches one after the other); bin sizes counted per block.
+template <int G>
 __global__ void k_spgemm_ub(const int64_t* arp, const int32_t* aci, const int64_t* brp, const int32_t* bci, int64_t n,
                             int upper, int64_t* ub, int* bin_cnt) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31, sub = lane & (G - 1);
+    const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
     int bin = -1;
-    if (i < n) {
-        int64_t s = 0;
-        int32_t floor = upper ? (int32_t)i : -1;
-        for (int64_t k = arp[i]; k < arp[i + 1]; ++k) s += brp[aci[k] + 1] - row_floor(brp, bci, aci[k], floor);
-        ub[i] = s;
-        bin = spgemm_bin_of(s, arp[i + 1] - arp[i]);
+    if (i < n) {                                     // uniform over the group
+        int64_t sum = 0;
+        const int32_t floor = upper ? (int32_t)i : -1;
+        for (int64_t k = arp[i] + sub; k < arp[i + 1]; k += G) sum += brp[aci[k] + 1] - row_floor(brp, bci, aci[k], floor);
+#pragma unroll
+        for (int d = G / 2; d > 0; d >>= 1) sum += __shfl_xor_sync(gmask, sum, d);
+        if (sub == 0) {
+            ub[i] = sum;
+            bin = spgemm_bin_of(sum, arp[i + 1] - arp[i]);
+        }
     }
-    for (int b = 0; b < 3; ++b) warp_count(&bin_cnt[b], bin == b);
+    for (int b = 0; b < 3; ++b) {
+        int c = __syncthreads_count(bin == b);
+        if (threadIdx.x == 0 && c) atomicAdd(&bin_cnt[b], c);
+    }
 }
 __global__ void k_spgemm_bin(const int64_t* arp, const int64_t* ub, int64_t n, const int* bin_off, int* bin_fill,
                              int32_t* rows) {
@@ -686,7 +699,33 @@ __global__ void k_spgemm_symbolic_big(const int64_t* arp, const int32_t* aci, co
     }
 }
 
-// numeric: accumulate in the table, compact in place, write each entry at its rank
+// Sort keys[0, count) ascending, vals alongside, by one warp in shared memory: a bitonic network
+// over the next power of two (at most the table size, which is at least twice count), padded
+// with INT_MAX keys.
+__device__ inline void warp_sort_pairs(int32_t* keys, double* vals, int count, int lane) {
+    int n2 = 1;
+    while (n2 < count) n2 <<= 1;
+    for (int t = count + lane; t < n2; t += 32) keys[t] = 0x7fffffff;
+    __syncwarp();
+    for (int size = 2; size <= n2; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int q = lane; q < n2 / 2; q += 32) {
+                const int lo = q + (q & ~(stride - 1)), hi = lo + stride;   // stride is a power of two
+                const bool up = (lo & size) == 0;
+                const int32_t a = keys[lo], b = keys[hi];
+                if ((a > b) == up) {
+                    keys[lo] = b;
+                    keys[hi] = a;
+                    const double t = vals[lo];
+                    vals[lo] = vals[hi];
+                    vals[hi] = t;
+                }
+            }
+            __syncwarp();
+        }
+}
+
+// numeric: accumulate in the table, compact in place, sort, write the row
 template <int SLOTS, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32)
 k_spgemm_numeric(const int64_t* arp, const int32_t* aci, const double* av, const int64_t* brp,
@@ -745,12 +784,10 @@ k_spgemm_numeric(const int64_t* arp, const int32_t* aci, const double* av, const
         count += __popc(m);
         __syncwarp();
     }
+    warp_sort_pairs(keys, vals, count, lane);
     for (int e = lane; e < count; e += 32) {
-        int32_t k = keys[e];
-        int rank = 0;
-        for (int u = 0; u < count; ++u) rank += (keys[u] < k);
-        cci[c0 + rank] = k;
-        cv[c0 + rank] = vals[e];
+        cci[c0 + e] = keys[e];
+        cv[c0 + e] = vals[e];
     }
 }
 
@@ -835,7 +872,20 @@ static int spgemm_impl(const DCSR& A, const DCSR& B, DCSR& C, int upper, cudaStr
     SPHC_TRY(flags.zero(s));
     int h[16] = {0};
     if (n > 0) {
-        SPHC_LAUNCH(k_spgemm_ub<<<grid_for(n, 256), 256, 0, s>>>(A.rp.p, A.ci.p, B.rp.p, B.ci.p, n, upper, ub.p, flags.p + 2));
+        // lanes per row of the count: the mean A row length over 4, a power of two from 1 to 32
+        double avg = (double)A.nnz / (double)n;
+        int g = 1;
+        while (g < 32 && 4 * g < avg) g <<= 1;
+        switch (g) {
+#define UB(G) SPHC_LAUNCH(k_spgemm_ub<G><<<grid_for(n * G, 256), 256, 0, s>>>(A.rp.p, A.ci.p, B.rp.p, B.ci.p, n, upper, ub.p, flags.p + 2))
+            case 1: UB(1); break;
+            case 2: UB(2); break;
+            case 4: UB(4); break;
+            case 8: UB(8); break;
+            case 16: UB(16); break;
+            default: UB(32); break;
+#undef UB
+        }
         SPHC_CK(cudaMemcpyAsync(h, flags.p, 16 * sizeof(int), cudaMemcpyDeviceToHost, s));
         SPHC_CK(cudaStreamSynchronize(s));
         int off[NBINS] = {0, h[2], h[2] + h[3]};
