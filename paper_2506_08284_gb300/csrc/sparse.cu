@@ -463,7 +463,8 @@ __global__ void k_spgemm_bin(const int64_t* arp, const int64_t* ub, int64_t n, c
 
 // Rows with at most 64 products (and 64 A entries): one warp per row, the products held two per
 // lane and sorted by column with a bitonic network over the warp; equal columns are then
-// adjacent.  mode 0 counts distinct columns, mode 1 sums each run and writes the sorted row.
+// adjacent.  mode 0 counts distinct columns, mode 1 sums each run and writes the sorted row at
+// its place in C, mode 2 writes it (and its count) to a temporary slot of the listed row.
 static constexpr int SMALL_WARPS = 8;
 __global__ void __launch_bounds__(SMALL_WARPS * 32)
 k_spgemm_small(const int64_t* arp, const int32_t* aci, const double* av, const int64_t* brp, const int32_t* bci,
@@ -513,7 +514,7 @@ k_spgemm_small(const int64_t* arp, const int32_t* aci, const double* av, const i
             }
             int64_t kb = s_bst[w][lo] + (e - s_off[w][lo]);
             key[q] = bci[kb];
-            if (mode == 1) val[q] = av[a0 + lo] * bv[kb];
+            if (mode != 0) val[q] = av[a0 + lo] * bv[kb];
         }
     }
     // bitonic sort of the 64 elements
@@ -530,7 +531,7 @@ k_spgemm_small(const int64_t* arp, const int32_t* aci, const double* av, const i
                 for (int q = 0; q < 2; ++q) {
                     int e = 2 * lane + q;
                     int32_t ok = __shfl_xor_sync(0xffffffffu, key[q], ls);
-                    double ov = mode == 1 ? __shfl_xor_sync(0xffffffffu, val[q], ls) : 0.0;
+                    double ov = mode != 0 ? __shfl_xor_sync(0xffffffffu, val[q], ls) : 0.0;
                     bool up = ((e & size) == 0);
                     bool lower = (e & stride) == 0;
                     bool take_min = (up == lower);
@@ -542,7 +543,7 @@ k_spgemm_small(const int64_t* arp, const int32_t* aci, const double* av, const i
     }
     s_key[w][2 * lane] = key[0];
     s_key[w][2 * lane + 1] = key[1];
-    if (mode == 1) { s_val[w][2 * lane] = val[0]; s_val[w][2 * lane + 1] = val[1]; }
+    if (mode != 0) { s_val[w][2 * lane] = val[0]; s_val[w][2 * lane + 1] = val[1]; }
     __syncwarp();
     // run heads: first element of each distinct column
     bool head[2];
@@ -557,7 +558,10 @@ k_spgemm_small(const int64_t* arp, const int32_t* aci, const double* av, const i
         if (lane == 0) cnt[i] = distinct;
         return;
     }
-    int64_t c0 = crp[i];
+    // mode 1: the row at crp[i]; mode 2: at crp[li] (a temporary slot of the listed row), and the
+    // count too (the one pass of the small bin, copied into place once the row pointers exist)
+    if (mode == 2 && lane == 0) cnt[i] = distinct;
+    int64_t c0 = mode == 2 ? crp[li] : crp[i];
     unsigned lt = (1u << lane) - 1u;
     for (int q = 0; q < 2; ++q) {
         if (!head[q]) continue;
@@ -569,6 +573,24 @@ k_spgemm_small(const int64_t* arp, const int32_t* aci, const double* av, const i
         for (int f = e; f < 64 && s_key[w][f] == kk; ++f) sum += s_val[w][f];
         cci[c0 + rank] = kk;
         cv[c0 + rank] = sum;
+    }
+}
+
+// slot offsets of the listed rows: ub[rows[li]] (at most 64 each)
+__global__ void k_list_ub(const int32_t* rows, int nrows, const int64_t* ub, int64_t* out) {
+    int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (li < nrows) out[li] = ub[rows[li]];
+}
+// copy the listed rows from their temporary slots into C (warp per row)
+__global__ void k_copy_listed(const int32_t* rows, int nrows, const int64_t* toff, const int32_t* tci,
+                              const double* tv, const int64_t* crp, int32_t* cci, double* cv) {
+    int64_t li = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (li >= nrows) return;
+    int64_t i = rows[li], c0 = crp[i], len = crp[i + 1] - c0, t0 = toff[li];
+    for (int64_t e = lane; e < len; e += 32) {
+        cci[c0 + e] = tci[t0 + e];
+        cv[c0 + e] = tv[t0 + e];
     }
 }
 
@@ -864,6 +886,10 @@ static int spgemm_impl(const DCSR& A, const DCSR& B, DCSR& C, int upper, cudaStr
     DBuf<int64_t> ub, cnt;
     DBuf<int32_t> big, rows;
     DBuf<int> flags;                 // 0 bign, 1 fail, 2..4 bin counts, 5..7 bin offsets, 8..10 bin fill
+    DBuf<int64_t> toff;              // small bin: temporary slot offsets, then its rows
+    DBuf<int32_t> tci;
+    DBuf<double> tv;
+    int64_t tslots = 0;
     SPHC_TRY(ub.alloc(n + 1, s));
     SPHC_TRY(cnt.alloc(n + 1, s));
     SPHC_TRY(big.alloc(n + 1, s));
@@ -891,9 +917,18 @@ static int spgemm_impl(const DCSR& A, const DCSR& B, DCSR& C, int upper, cudaStr
         int off[NBINS] = {0, h[2], h[2] + h[3]};
         SPHC_CK(cudaMemcpyAsync(flags.p + 5, off, NBINS * sizeof(int), cudaMemcpyHostToDevice, s));
         SPHC_LAUNCH(k_spgemm_bin<<<grid_for(n, 256), 256, 0, s>>>(A.rp.p, ub.p, n, flags.p + 5, flags.p + 8, rows.p));
-        if (h[2] > 0)
+        if (h[2] > 0) {
+            // small bin in one pass: sorted rows into temporary slots of ub entries each
+            DBuf<int64_t> lub;
+            SPHC_TRY(lub.alloc(h[2], s));
+            SPHC_TRY(toff.alloc(h[2] + 1, s));               // the scan also writes the total
+            SPHC_LAUNCH(k_list_ub<<<grid_for(h[2], 256), 256, 0, s>>>(rows.p, h[2], ub.p, lub.p));
+            SPHC_TRY(exclusive_scan_i64(lub.p, toff.p, h[2], s, &tslots));
+            SPHC_TRY(tci.alloc(tslots > 0 ? tslots : 1, s));
+            SPHC_TRY(tv.alloc(tslots > 0 ? tslots : 1, s));
             SPHC_LAUNCH(k_spgemm_small<<<(h[2] + SMALL_WARPS - 1) / SMALL_WARPS, SMALL_WARPS * 32, 0, s>>>(
-                A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p, B.v.p, rows.p, h[2], 0, upper, cnt.p, nullptr, nullptr, nullptr));
+                A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p, B.v.p, rows.p, h[2], 2, upper, cnt.p, toff.p, tci.p, tv.p));
+        }
         launch_symbolic<512, 8>(A, B, rows.p + off[1], h[3], upper, ub.p, cnt.p, big.p, flags.p, s);
         launch_symbolic<1024, 8>(A, B, rows.p + off[2], h[4], upper, ub.p, cnt.p, big.p, flags.p, s);
     }
@@ -924,8 +959,8 @@ static int spgemm_impl(const DCSR& A, const DCSR& B, DCSR& C, int upper, cudaStr
     if (n > 0) {
         int off[NBINS] = {0, h[2], h[2] + h[3]};
         if (h[2] > 0)
-            SPHC_LAUNCH(k_spgemm_small<<<(h[2] + SMALL_WARPS - 1) / SMALL_WARPS, SMALL_WARPS * 32, 0, s>>>(
-                A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p, B.v.p, rows.p, h[2], 1, upper, nullptr, C.rp.p, C.ci.p, C.v.p));
+            SPHC_LAUNCH(k_copy_listed<<<grid_for((int64_t)h[2] * 32, 256), 256, 0, s>>>(rows.p, h[2], toff.p, tci.p, tv.p,
+                                                                                      C.rp.p, C.ci.p, C.v.p));
         launch_numeric<512, 4>(A, B, C, rows.p + off[1], h[3], upper, ub.p, s);
         launch_numeric<1024, 2>(A, B, C, rows.p + off[2], h[4], upper, ub.p, s);
     }
