@@ -1255,9 +1255,8 @@ __device__ __forceinline__ int row_factor(int64_t i, const int64_t* __restrict__
 #pragma unroll
         for (int c = 0; c < j; ++c) d -= S.L[j][c] * S.L[j][c];
         if (!(d > 1e-6)) { ok = false; d = 1.0; }   // a disconnected local graph leaves a zero pivot
-        double lj = sqrt(d);
-        S.L[j][j] = lj;
-        double inv = 1.0 / lj;
+        double inv = rsqrt(d);                         // the diagonal is kept as its inverse
+        S.L[j][j] = inv;
 #pragma unroll
         for (int r = j + 1; r < TK; ++r) {
             double v = S.L[r][j];
@@ -1268,21 +1267,21 @@ __device__ __forceinline__ int row_factor(int64_t i, const int64_t* __restrict__
     }
     return ok ? 1 : 0;
 }
-// x := (L L^T)^-1 x
+// x := (L L^T)^-1 x (L's diagonal holds 1 / L_aa)
 __device__ __forceinline__ void row_solve(const RowSys& S, double x[TK]) {
 #pragma unroll
     for (int a = 0; a < TK; ++a) {
         double v = x[a];
 #pragma unroll
         for (int c = 0; c < a; ++c) v -= S.L[a][c] * x[c];
-        x[a] = v / S.L[a][a];
+        x[a] = v * S.L[a][a];
     }
 #pragma unroll
     for (int a = TK - 1; a >= 0; --a) {
         double v = x[a];
 #pragma unroll
         for (int r = a + 1; r < TK; ++r) v -= S.L[r][a] * x[r];
-        x[a] = v / S.L[a][a];
+        x[a] = v * S.L[a][a];
     }
 }
 // (G~ z)_t
@@ -1310,20 +1309,60 @@ __device__ __forceinline__ void row_sub_gtv(const RowSys& S, const V* v, double 
     }
 }
 
+// The factored local system of every thread-handled row, kept from the P0 solve for the
+// energy-minimisation steps, which project onto the same constraints: the node bitmasks, the
+// number of kept constraints k (-1: no system for the row) and the lower triangle of the Cholesky
+// factor, stored structure of arrays (entry e of row i at e * ne + i).
+constexpr int TL = TK * (TK + 1) / 2;
+struct RowCache {
+    uint32_t* pm;        // 2 * TK masks
+    int8_t* k;
+    double* L;           // TL entries
+    int64_t ne;
+};
+__device__ __forceinline__ void cache_put(const RowCache& C, int64_t i, const RowSys& S) {
+#pragma unroll
+    for (int a = 0; a < TK; ++a) {
+        C.pm[(2 * a) * C.ne + i] = S.pos[a];
+        C.pm[(2 * a + 1) * C.ne + i] = S.neg[a];
+    }
+    int e = 0;
+#pragma unroll
+    for (int a = 0; a < TK; ++a)
+#pragma unroll
+        for (int b = 0; b <= a; ++b) C.L[(int64_t)(e++) * C.ne + i] = S.L[a][b];
+    C.k[i] = (int8_t)S.k;
+}
+__device__ __forceinline__ void cache_get(const RowCache& C, int64_t i, RowSys& S) {
+#pragma unroll
+    for (int a = 0; a < TK; ++a) {
+        S.pos[a] = C.pm[(2 * a) * C.ne + i];
+        S.neg[a] = C.pm[(2 * a + 1) * C.ne + i];
+    }
+    int e = 0;
+#pragma unroll
+    for (int a = 0; a < TK; ++a)
+#pragma unroll
+        for (int b = 0; b <= a; ++b) S.L[a][b] = C.L[(int64_t)(e++) * C.ne + i];
+}
+
 // P0 of every small row: the point of {G~^T p = r~} nearest to d (d null: 0), p = d + G~ z with
-// (G~^T G~) z = r~ - G~^T d.  Rows too large for a thread are appended to `big`.
+// (G~^T G~) z = r~ - G~^T d.  Rows too large for a thread are appended to `big`.  Every row's
+// factored system (or k = -1) goes to the cache.
 __global__ void __launch_bounds__(128)
 k_p0_rows(int64_t ne, const int64_t* __restrict__ trp, const int32_t* __restrict__ tci, const double* __restrict__ tv,
           const int64_t* __restrict__ nrp, const int32_t* __restrict__ nci, const int64_t* __restrict__ hrp,
           const int32_t* __restrict__ hci, const double* __restrict__ hv, const float* __restrict__ d,
-          double* __restrict__ p0, int* fail, int32_t* big, int* nbig) {
+          double* __restrict__ p0, int* fail, int32_t* big, int* nbig, RowCache cache) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ne) return;
     RowSys S;
     int code = row_factor(i, trp, tci, tv, nrp, nci, hrp, hci, hv, S);
+    if (code != 1) cache.k[i] = -1;
     if (code == 2) return;
     if (code == -1) { big[warp_reserve(nbig)] = (int32_t)i; return; }
     if (code == 0) { atomicAdd(fail, 1); return; }
+    cache_put(cache, i, S);
     double z[TK];
 #pragma unroll
     for (int a = 0; a < TK; ++a) z[a] = a < S.k ? S.r[a] : 0.0;
@@ -1378,19 +1417,20 @@ k_emin_product(int64_t ne, const int64_t* __restrict__ arp, const int32_t* __res
 }
 
 // projection and update of eq. (9) for every small row: dp = w - G~ (G~^T G~)^-1 G~^T w,
-// P' = P - omega dp (rows too large for a thread are handled by k_emin through a row list)
+// P' = P - omega dp, with the system factored by k_p0_rows (rows too large for a thread are
+// handled by k_emin through a row list)
 __global__ void __launch_bounds__(128)
-k_emin_rows(int64_t ne, const int64_t* __restrict__ trp, const int32_t* __restrict__ tci,
-            const double* __restrict__ tv, const int64_t* __restrict__ nrp, const int32_t* __restrict__ nci,
-            const int64_t* __restrict__ hrp, const int32_t* __restrict__ hci, const double* __restrict__ hv,
-            const double* __restrict__ w, const double* __restrict__ P, double* __restrict__ Pout, double omega,
-            int* fail) {
+k_emin_rows(int64_t ne, const int64_t* __restrict__ nrp, const double* __restrict__ w, const double* __restrict__ P,
+            double* __restrict__ Pout, double omega, RowCache cache) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ne) return;
+    const int k = cache.k[i];
+    if (k < 0) return;                               // empty, large (k_emin) or infeasible row
     RowSys S;
-    int code = row_factor(i, trp, tci, tv, nrp, nci, hrp, hci, hv, S);
-    if (code == 2 || code == -1) return;
-    if (code == 0) { atomicAdd(fail, 1); return; }
+    S.k = k;
+    S.n0 = nrp[i];
+    S.np = (int)(nrp[i + 1] - S.n0);
+    cache_get(cache, i, S);
     double z[TK];
 #pragma unroll
     for (int a = 0; a < TK; ++a) z[a] = 0.0;
@@ -1817,10 +1857,18 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
     SPHC_TRY(nbig.alloc(1, s));
     SPHC_TRY(nbig.zero(s));
     int hbig = 0;
+    // factored local systems, kept for the energy-minimisation steps
+    DBuf<uint32_t> cpm;
+    DBuf<int8_t> ck;
+    DBuf<double> cL;
+    SPHC_TRY(cpm.alloc(2 * TK * (ne > 0 ? ne : 1), s));
+    SPHC_TRY(ck.alloc(ne > 0 ? ne : 1, s));
+    SPHC_TRY(cL.alloc(TL * (ne > 0 ? ne : 1), s));
+    RowCache cache{cpm.p, ck.p, cL.p, ne};
     if (ne > 0) {
         SPHC_LAUNCH(k_p0_rows<<<grid_for(ne, 128), 128, 0, s>>>(ne, L.T.rp.p, L.T.ci.p, L.T.v.p, L.P0.rp.p, L.P0.ci.p,
                                                                L.DH.rp.p, L.DH.ci.p, L.DH.v.p, corr.p, L.P0.v.p, st.p,
-                                                               big.p, nbig.p));
+                                                               big.p, nbig.p, cache));
         SPHC_CK(cudaMemcpyAsync(&hbig, nbig.p, sizeof(int), cudaMemcpyDeviceToHost, s));
         SPHC_CK(cudaStreamSynchronize(s));
         if (hbig > 0)
@@ -1847,9 +1895,8 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
         if (ne > 0) {
             SPHC_LAUNCH(k_emin_product<<<grid_for(ne, LOC_WARPS), LOC_WARPS * 32, 0, s>>>(
                 ne, L.A.rp.p, L.A.ci.p, L.A.v.p, L.Pe.rp.p, L.Pe.ci.p, L.Pe.v.p, W.p));
-            SPHC_LAUNCH(k_emin_rows<<<grid_for(ne, 128), 128, 0, s>>>(
-                ne, L.T.rp.p, L.T.ci.p, L.T.v.p, L.Pe.rp.p, L.Pe.ci.p, L.DH.rp.p, L.DH.ci.p, L.DH.v.p, W.p, L.Pe.v.p,
-                Pnew.p, o.emin_omega, st.p));
+            SPHC_LAUNCH(k_emin_rows<<<grid_for(ne, 128), 128, 0, s>>>(ne, L.Pe.rp.p, W.p, L.Pe.v.p, Pnew.p, o.emin_omega,
+                                                                      cache));
             if (hbig > 0)
                 SPHC_LAUNCH(k_emin<<<grid_for(hbig, LOC_WARPS), LOC_WARPS * 32, sm, s>>>(
                     hbig, big.p, L.A.rp.p, L.A.ci.p, L.A.v.p, L.T.rp.p, L.T.ci.p, L.T.v.p, L.Pe.rp.p, L.Pe.ci.p,
