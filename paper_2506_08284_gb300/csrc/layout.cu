@@ -375,6 +375,18 @@ int build_xop(const DCSR& A, const int32_t* rmap, const int32_t* cmap, XOp<T>& X
     return build_csr_perm<T>(A, rmap, cmap, X.c, s);
 }
 
+// nonzeros of the rows rmap[k], k in [k0, k1)
+__global__ void k_rows_nnz(const int64_t* rp, const int32_t* rmap, int64_t k0, int64_t k1, unsigned long long* out) {
+    int64_t k = k0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long v = 0;
+    if (k < k1) {
+        int64_t i = rmap ? rmap[k] : k;
+        v = (unsigned long long)(rp[i + 1] - rp[i]);
+    }
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(out, v);
+}
+
 template <typename T>
 int build_smooth(const DCSR& A, const int32_t* rmap, const int32_t* cmap, const std::vector<int64_t>& cstart, int ch,
                  int lpr, SmoothOp<T>& op, cudaStream_t s) {
@@ -387,6 +399,21 @@ int build_smooth(const DCSR& A, const int32_t* rmap, const int32_t* cmap, const 
     if (lpr <= 0) lpr = sell_lpr_for(A, (int)cstart.size() - 1);
     if (ch <= 0) SPHC_TRY(sell_pick_ch(A, rmap, cstart, lpr, s, &ch));
     SPHC_TRY(build_sell<T>(A, rmap, cmap, cstart, ch, lpr, op.m, op.dinv.p, &op.cslice, s));
+    op.n_last = op.nnz_last = 0;
+    if (op.ncolor > 0) {
+        const int64_t k0 = cstart[op.ncolor - 1], k1 = cstart[op.ncolor];
+        op.n_last = k1 - k0;
+        if (k1 > k0) {
+            DBuf<unsigned long long> cnt;
+            SPHC_TRY(cnt.alloc(1, s));
+            SPHC_TRY(cnt.zero(s));
+            SPHC_LAUNCH(k_rows_nnz<<<grid_for(k1 - k0, 256), 256, 0, s>>>(A.rp.p, rmap, k0, k1, cnt.p));
+            unsigned long long h = 0;
+            SPHC_CK(cudaMemcpyAsync(&h, cnt.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+            SPHC_CK(cudaStreamSynchronize(s));
+            op.nnz_last = (int64_t)h;
+        }
+    }
     op.cslice_dev = DBuf<int64_t>();
     SPHC_TRY(op.cslice_dev.alloc(op.cslice.size(), s));
     SPHC_CK(cudaMemcpyAsync(op.cslice_dev.p, op.cslice.data(), sizeof(int64_t) * op.cslice.size(), cudaMemcpyHostToDevice, s));

@@ -377,6 +377,15 @@ k_sell_spmv(const int64_t* __restrict__ soff, const int32_t* __restrict__ srow, 
     T sum = row_reduce(sell_part<T, CH>(ci, v, o, (soff[sl + 1] - o) / (SELL_C * CH), lane, x), lpr);
     if (q.write) y[q.r] = accumulate ? y[q.r] + alpha * sum : alpha * sum;
 }
+// Colour order of a symmetric sweep: forward 0 .. C-1, then backward C-2 .. 0.  The backward
+// sweep's first colour, C-1, would repeat the update just made: a Gauss-Seidel step leaves its own
+// rows with zero residual, and rows of one colour do not couple, so that step changes nothing
+// (beyond rounding) and is left out.
+__host__ __device__ __forceinline__ int sweep_steps(int ncolor) { return ncolor > 0 ? 2 * ncolor - 1 : 0; }
+__host__ __device__ __forceinline__ int sweep_colour(int step, int ncolor) {
+    return step < ncolor ? step : 2 * ncolor - 2 - step;
+}
+
 // A whole forward + backward sweep of a small operator in one block: colours are separated by
 // block barriers instead of kernel boundaries (the coarse levels are launch-bound otherwise).
 template <typename T, int CH>
@@ -386,8 +395,8 @@ k_sell_sgs_block(const int64_t* __restrict__ soff, const int32_t* __restrict__ s
                  const T* __restrict__ v, const T* __restrict__ dinv, const T* __restrict__ b, T* x) {
     pdl_enter();
     int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    for (int step = 0; step < 2 * ncolor; ++step) {
-        int c = step < ncolor ? step : 2 * ncolor - 1 - step;
+    for (int step = 0; step < sweep_steps(ncolor); ++step) {
+        int c = sweep_colour(step, ncolor);
         for (int64_t sl = cslice[c] + warp; sl < cslice[c + 1]; sl += nwarp) {
             int64_t o = soff[sl];
             SliceRow q = slice_row(srow, sl, lane, lpr);
@@ -451,7 +460,7 @@ k_sell_sgs_cluster(const int64_t* __restrict__ soff, const int32_t* __restrict__
     if (have && valid) { br = b[r]; dr = dinv[r]; }
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) xs[i] = x[i];
     cl.sync();
-    for (int step = 0; step < 2 * ncolor; ++step) {
+    for (int step = 0; step < sweep_steps(ncolor); ++step) {
         while (have) {
             T sum = row_reduce(h.finish(ci, v, o, steps, lane, xs), lpr);
             if (valid) {
@@ -460,8 +469,8 @@ k_sell_sgs_cluster(const int64_t* __restrict__ soff, const int32_t* __restrict__
             }
             fetch(sl + nw, end, true);
         }
-        if (step + 1 < 2 * ncolor) {                     // head of the next colour's first slice
-            const int cn = step + 1 < ncolor ? step + 1 : 2 * ncolor - 2 - step;
+        if (step + 1 < sweep_steps(ncolor)) {            // head of the next colour's first slice
+            const int cn = sweep_colour(step + 1, ncolor);
             fetch(cslice[cn] + gw, cslice[cn + 1], true);
         }
         cl.sync();
@@ -642,8 +651,8 @@ static void sgs(const SmoothOp<T>& op, const T* b, T* x, cudaStream_t s) {
 #undef F
         return;
     }
-    for (int step = 0; step < 2 * op.ncolor; ++step) {
-        int c = step < op.ncolor ? step : 2 * op.ncolor - 1 - step;
+    for (int step = 0; step < sweep_steps(op.ncolor); ++step) {
+        int c = sweep_colour(step, op.ncolor);
         int64_t s0 = op.cslice[c], s1 = op.cslice[c + 1];
         if (s1 <= s0) continue;
 #define F(C) launch_pdl(k_sell_sgs<T, C>, slice_grid(s1 - s0), 256, 0, s, m.soff.p, m.srow.p, s0, s1, m.lpr, m.ci.p, m.v.p, op.dinv.p, b, x)
@@ -691,10 +700,12 @@ static int cg_spmv(const Hierarchy& H, const double* x, double* y, cudaStream_t 
 }
 
 // algorithmic bytes of one forward + backward sweep: the matrix (values and column indices)
-// once per direction and, per row, its right side, inverse diagonal and one read and write of x
+// once per direction and, per row, its right side, inverse diagonal and one read and write of x;
+// the last colour is swept once
 template <typename T>
 static double sgs_bytes(const SmoothOp<T>& op) {
-    return 2.0 * ((double)op.nnz * (sizeof(T) + 4) + (double)op.n * 4.0 * sizeof(T));
+    return (2.0 * (double)op.nnz - (double)op.nnz_last) * (sizeof(T) + 4) +
+           (2.0 * (double)op.n - (double)op.n_last) * 4.0 * sizeof(T);
 }
 
 template <typename T>

@@ -41,6 +41,7 @@ struct SmoothOp {
     Sell<T> m;
     DBuf<T> dinv;
     int cluster = 0;                 // 1: whole sweeps on one thread-block cluster (x in shared memory)
+    int64_t n_last = 0, nnz_last = 0; // rows and nonzeros of the last colour (swept once per sweep)
 };
 // smoothers of at most this many rows sweep in one thread block (colours separated by block
 // barriers)
