@@ -4,8 +4,8 @@
 // of one pattern entry from local features.  Its output always passes through the exact
 // constraint projection before use, so the commuting relation P_e D_H = D_h P_n still holds.
 //
-// Inference: BF16 weights and activations on the tensor cores (mma.sync m16n8k16, FP32
-// accumulate).  Training: FP32 forward / backward GEMM kernels and Adam.
+// Inference: bf16 weights and activations on the fifth-generation tensor cores (tcgen05 MMAs,
+// FP32 accumulators in tensor memory).  Training: FP32 forward / backward GEMM kernels and Adam.
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -14,6 +14,7 @@
 
 #include "features.cuh"
 #include "sphc_level.cuh"
+#include "tc.cuh"
 
 using namespace sphc;
 
@@ -27,59 +28,58 @@ constexpr int P_MU = 0, P_SD = NF, P_W1 = 2 * NF, P_B1 = P_W1 + NF * NH, P_W2 = 
 static_assert(P_TOTAL == SPHC_MLP_NPARAM, "parameter layout");
 
 // ------------------------------------------------------------------ inference on tensor cores
-constexpr int TILE_M = 128;           // rows (pattern entries) per block
-constexpr int INF_WARPS = 8;          // each warp owns 16 rows
-constexpr int XS = NF + 8;            // padded shared-memory row strides (bf16 elements)
-static_assert(INF_WARPS * 32 == 2 * TILE_M, "two threads per tile row compute its features");
-constexpr int HS = NH + 8;
+// Two blocks per SM walk tiles of 128 pattern entries.  Per tile: the normalised features go to
+// shared memory as the bf16 A operand (K = 32); one thread issues the first layer as tcgen05 MMAs
+// (M = 128, N = 128, FP32 accumulator D1 in tensor memory); eight warps read D1 back (warp w:
+// rows 32 (w % 4) .., columns 64 (w / 4) ..), add the bias, apply ReLU and store the bf16 hidden
+// layer as the A operand of the second layer (K = 128, accumulator D2); the output layer is a dot
+// product of ReLU(D2 + b2) with w3 in the same epilogue pattern.  Weights are staged once per block.
+constexpr int TILE_M = 128;           // pattern entries per tile (MMA M)
+constexpr int TC_THREADS = 256;       // 8 warps; two threads per tile row compute its features
+static_assert(TC_THREADS == 2 * TILE_M, "two threads per tile row compute its features");
+constexpr uint32_t TC_COLS = 256;     // half of tensor memory: D1 at column 0, D2 at column 128
+constexpr uint32_t TC_D2 = 128;
+constexpr int TC_WAIT = 1 << 20;      // polls of an MMA-completion wait before the kernel gives up
+// Dynamic shared memory per block: more than a third of an SM's, so at most two blocks share an
+// SM and their two 256-column allocations never wait for each other.
+constexpr size_t TC_SMEM = 100 * 1024;
+constexpr int TC_BLOCKS_PER_SM = 2;
 
-struct InferSmem {
-    __nv_bfloat16 x[TILE_M * XS];
-    __nv_bfloat16 w1t[NH * XS];       // W1 transposed: [out][in]
-    __nv_bfloat16 w2t[NH * HS];       // W2 transposed: [out][in]
-    __nv_bfloat16 h1[TILE_M * HS];
-    float b1[NH], b2[NH], w3[NH], mu[NF], isd[NF];
+struct __align__(1024) TcSmem {
+    __nv_bfloat16 a1[TILE_M * NF];    // features, K-major core matrices
+    unsigned char g0[1024];
+    __nv_bfloat16 w1[NH * NF];        // W1 transposed ([out][in]), K-major core matrices
+    unsigned char g1[1024];
+    __nv_bfloat16 a2[TILE_M * NH];    // hidden layer
+    unsigned char g2[1024];
+    __nv_bfloat16 w2[NH * NH];        // W2 transposed
+    unsigned char g3[1024];
+    float b1[NH], b2[NH], w3[NH], mu[NF], isd[NF], part[TILE_M];
+    uint64_t bar;
+    uint32_t tmem;
 };
+static_assert(sizeof(TcSmem) <= TC_SMEM, "shared memory layout");
 
-__device__ inline uint32_t pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi) {
-    uint32_t a = (uint32_t)__bfloat16_as_ushort(lo), b = (uint32_t)__bfloat16_as_ushort(hi);
-    return a | (b << 16);
+// element offset of (row r, column k) in a K-major bf16 operand of K columns: core matrix
+// (r / 8, k / 8) at ((r / 8) (K / 8) + k / 8) * 64 elements, rows of 8 elements inside
+__device__ __forceinline__ int cm_off(int r, int k, int K) {
+    return (((r >> 3) * (K >> 3) + (k >> 3)) << 6) + ((r & 7) << 3) + (k & 7);
 }
-__device__ inline uint32_t ld_pair(const __nv_bfloat16* p) { return *(const uint32_t*)p; }
-
-// D(16x8, f32) += A(16x16, bf16, row) * B(16x8, bf16, col)
-__device__ inline void mma_bf16(float d[4], const uint32_t a[4], const uint32_t b[2]) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-// A fragment of rows [r0, r0+16), columns [k0, k0+16) of a row-major bf16 matrix (stride ld)
-__device__ inline void load_a(uint32_t a[4], const __nv_bfloat16* M, int ld, int r0, int k0, int lane) {
-    int g = lane >> 2, t = lane & 3;
-    a[0] = ld_pair(M + (r0 + g) * ld + k0 + 2 * t);
-    a[1] = ld_pair(M + (r0 + g + 8) * ld + k0 + 2 * t);
-    a[2] = ld_pair(M + (r0 + g) * ld + k0 + 8 + 2 * t);
-    a[3] = ld_pair(M + (r0 + g + 8) * ld + k0 + 8 + 2 * t);
-}
-// B fragment of k rows [k0, k0+16), n columns [n0, n0+8) from a transposed ([n][k]) matrix
-__device__ inline void load_b(uint32_t b[2], const __nv_bfloat16* Mt, int ld, int n0, int k0, int lane) {
-    int g = lane >> 2, t = lane & 3;
-    b[0] = ld_pair(Mt + (n0 + g) * ld + k0 + 2 * t);
-    b[1] = ld_pair(Mt + (n0 + g) * ld + k0 + 8 + 2 * t);
+// descriptor of K-step ks (16 columns) of a K-major operand: adjacent core matrices are 128 bytes
+// apart along K and (K / 8) * 128 bytes apart along the rows
+__device__ __forceinline__ uint64_t op_desc(const __nv_bfloat16* M, int K, int ks) {
+    return tc_desc(reinterpret_cast<const unsigned char*>(M) + 256 * ks, 128u, (uint32_t)(K / 8) * 128u);
 }
 
 // FUSED: the features of tile row r (pattern entry base + r, in fine row rowof[base + r]) are
 // computed in place from the level's operators instead of being read from X.
 template <bool FUSED>
-__global__ void __launch_bounds__(INF_WARPS * 32)
+__global__ void __launch_bounds__(TC_THREADS, TC_BLOCKS_PER_SM)
 k_mlp_infer(const float* __restrict__ params, const float* __restrict__ X, int64_t m, FeatArgs g,
-            const int32_t* __restrict__ rowof, float* __restrict__ out) {
-    extern __shared__ unsigned char smem_raw[];
-    InferSmem& S = *(InferSmem*)smem_raw;
-    int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+            const int32_t* __restrict__ rowof, float* __restrict__ out, int* err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    TcSmem& S = *reinterpret_cast<TcSmem*>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     for (int q = tid; q < NF; q += blockDim.x) {
         S.mu[q] = params[P_MU + q];
         float sd = params[P_SD + q];
@@ -92,80 +92,114 @@ k_mlp_infer(const float* __restrict__ params, const float* __restrict__ X, int64
     }
     for (int q = tid; q < NF * NH; q += blockDim.x) {
         int i = q / NH, o = q % NH;                    // W1[i][o]
-        S.w1t[o * XS + i] = __float2bfloat16(params[P_W1 + q]);
+        S.w1[cm_off(o, i, NF)] = __float2bfloat16(params[P_W1 + q]);
     }
     for (int q = tid; q < NH * NH; q += blockDim.x) {
         int i = q / NH, o = q % NH;                    // W2[i][o]
-        S.w2t[o * HS + i] = __float2bfloat16(params[P_W2 + q]);
+        S.w2[cm_off(o, i, NH)] = __float2bfloat16(params[P_W2 + q]);
     }
-    float b3 = params[P_B3];
+    const float b3 = params[P_B3];
+    if (tid == 0) tc_bar_init(&S.bar, 1);
+    if (w == 0) {
+        tc_alloc(&S.tmem, TC_COLS);
+        tc_relinquish();
+    }
+    tc_fence_smem_to_async();
+    tc_fence_before();
     __syncthreads();
-    for (int64_t base = (int64_t)blockIdx.x * TILE_M; base < m; base += (int64_t)gridDim.x * TILE_M) {
+    tc_fence_after();
+    const uint32_t tmem = S.tmem;
+    const uint32_t idesc = tc_idesc_bf16(TILE_M, NH);
+    const int q4 = w & 3, half = w >> 2, row = 32 * q4 + lane;
+    const uint32_t lane_off = (uint32_t)(32 * q4) << 16;
+    uint32_t phase = 0;
+    bool failed = false;
+    for (int64_t base = (int64_t)blockIdx.x * TILE_M; base < m && !failed; base += (int64_t)gridDim.x * TILE_M) {
         // normalised features of the tile (rows past m are zero)
         if (FUSED) {
             // two threads per entry: part 0 (geometry, row quantities) and part 1 (row lookups)
             int r = tid % TILE_M, part = tid / TILE_M;
-            int64_t row = base + r;
+            int64_t e = base + r;
             float f[NF];
-            if (row < m) entry_features(g, rowof[row], row, f, part);
+            if (e < m) entry_features(g, rowof[e], e, f, part);
             for (int c = 0; c < NF; ++c)
                 if (feat_part(c) == part)
-                    S.x[r * XS + c] = __float2bfloat16(row < m ? (f[c] - S.mu[c]) * S.isd[c] : 0.f);
+                    S.a1[cm_off(r, c, NF)] = __float2bfloat16(e < m ? (f[c] - S.mu[c]) * S.isd[c] : 0.f);
         } else {
             for (int q = tid; q < TILE_M * NF; q += blockDim.x) {
                 int r = q / NF, c = q % NF;
-                int64_t row = base + r;
-                float v = row < m ? (X[row * NF + c] - S.mu[c]) * S.isd[c] : 0.f;
-                S.x[r * XS + c] = __float2bfloat16(v);
+                int64_t e = base + r;
+                float v = e < m ? (X[e * NF + c] - S.mu[c]) * S.isd[c] : 0.f;
+                S.a1[cm_off(r, c, NF)] = __float2bfloat16(v);
             }
         }
+        // layer 1: D1 = x W1
+        tc_fence_smem_to_async();
+        tc_fence_before();
         __syncthreads();
-        int r0 = 16 * w;
-        // layer 1: h1 = relu(x W1 + b1)
-        uint32_t a1[2][4];
-        load_a(a1[0], S.x, XS, r0, 0, lane);
-        load_a(a1[1], S.x, XS, r0, 16, lane);
-        int g = lane >> 2, t = lane & 3;
-        for (int nt = 0; nt < NH / 8; ++nt) {
-            float d[4] = {0.f, 0.f, 0.f, 0.f};
-            for (int ks = 0; ks < NF / 16; ++ks) {
-                uint32_t b[2];
-                load_b(b, S.w1t, XS, nt * 8, ks * 16, lane);
-                mma_bf16(d, a1[ks], b);
+        if (tid == 0) {
+            tc_fence_after();
+#pragma unroll
+            for (int ks = 0; ks < NF / 16; ++ks) tc_mma(tmem, op_desc(S.a1, NF, ks), op_desc(S.w1, NF, ks), idesc, ks > 0);
+            tc_commit(&S.bar);
+        }
+        bool ok = tc_bar_wait(&S.bar, phase, TC_WAIT);
+        phase ^= 1u;
+        if (__syncthreads_or(!ok)) { failed = true; break; }
+        tc_fence_after();
+        // h1 = relu(D1 + b1) -> bf16 A operand of layer 2
+#pragma unroll
+        for (int cc = 0; cc < 2; ++cc) {
+            float v[32];
+            tc_ld32(tmem + lane_off + (uint32_t)(64 * half + 32 * cc), v);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int n = 64 * half + 32 * cc + j;
+                S.a2[cm_off(row, n, NH)] = __float2bfloat16(fmaxf(v[j] + S.b1[n], 0.f));
             }
-            int c = nt * 8 + 2 * t;
-            float h00 = fmaxf(d[0] + S.b1[c], 0.f), h01 = fmaxf(d[1] + S.b1[c + 1], 0.f);
-            float h10 = fmaxf(d[2] + S.b1[c], 0.f), h11 = fmaxf(d[3] + S.b1[c + 1], 0.f);
-            *(uint32_t*)(S.h1 + (r0 + g) * HS + c) = pack_bf16(__float2bfloat16(h00), __float2bfloat16(h01));
-            *(uint32_t*)(S.h1 + (r0 + g + 8) * HS + c) = pack_bf16(__float2bfloat16(h10), __float2bfloat16(h11));
         }
-        __syncwarp();
-        // layer 2 and the output layer: y = relu(h1 W2 + b2) . w3 + b3
-        float y0 = 0.f, y1 = 0.f;             // rows r0+g and r0+g+8, partial over this lane's columns
-        uint32_t a2[NH / 16][4];
-        for (int ks = 0; ks < NH / 16; ++ks) load_a(a2[ks], S.h1, HS, r0, ks * 16, lane);
-        for (int nt = 0; nt < NH / 8; ++nt) {
-            float d[4] = {0.f, 0.f, 0.f, 0.f};
-            for (int ks = 0; ks < NH / 16; ++ks) {
-                uint32_t b[2];
-                load_b(b, S.w2t, HS, nt * 8, ks * 16, lane);
-                mma_bf16(d, a2[ks], b);
-            }
-            int c = nt * 8 + 2 * t;
-            y0 += fmaxf(d[0] + S.b2[c], 0.f) * S.w3[c] + fmaxf(d[1] + S.b2[c + 1], 0.f) * S.w3[c + 1];
-            y1 += fmaxf(d[2] + S.b2[c], 0.f) * S.w3[c] + fmaxf(d[3] + S.b2[c + 1], 0.f) * S.w3[c + 1];
-        }
-        y0 += __shfl_xor_sync(0xffffffffu, y0, 1);
-        y0 += __shfl_xor_sync(0xffffffffu, y0, 2);
-        y1 += __shfl_xor_sync(0xffffffffu, y1, 1);
-        y1 += __shfl_xor_sync(0xffffffffu, y1, 2);
-        if (t == 0) {
-            int64_t ra = base + r0 + g, rb = base + r0 + g + 8;
-            if (ra < m) out[ra] = y0 + b3;
-            if (rb < m) out[rb] = y1 + b3;
-        }
+        // layer 2: D2 = h1 W2
+        tc_fence_smem_to_async();
+        tc_fence_before();
         __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+#pragma unroll
+            for (int ks = 0; ks < NH / 16; ++ks)
+                tc_mma(tmem + TC_D2, op_desc(S.a2, NH, ks), op_desc(S.w2, NH, ks), idesc, ks > 0);
+            tc_commit(&S.bar);
+        }
+        ok = tc_bar_wait(&S.bar, phase, TC_WAIT);
+        phase ^= 1u;
+        if (__syncthreads_or(!ok)) { failed = true; break; }
+        tc_fence_after();
+        // y = relu(D2 + b2) . w3 + b3, each half of the columns by its own warps
+        float y = 0.f;
+#pragma unroll
+        for (int cc = 0; cc < 2; ++cc) {
+            float v[32];
+            tc_ld32(tmem + lane_off + TC_D2 + (uint32_t)(64 * half + 32 * cc), v);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int n = 64 * half + 32 * cc + j;
+                y += fmaxf(v[j] + S.b2[n], 0.f) * S.w3[n];
+            }
+        }
+        if (half == 1) S.part[row] = y;
+        tc_fence_before();                   // tensor-memory reads done before the next tile's MMAs
+        __syncthreads();
+        if (half == 0 && base + row < m) out[base + row] = y + S.part[row] + b3;
     }
+    if (failed) {
+        // a completion wait gave up: report, give the MMA in flight one more bounded wait, and
+        // release the tensor memory
+        if (tid == 0) atomicExch(err, 1);
+        tc_bar_wait(&S.bar, phase ^ 1u, TC_WAIT);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (w == 0) tc_dealloc(tmem, TC_COLS);
 }
 
 static int infer_grid(int64_t m) {
@@ -174,17 +208,46 @@ static int infer_grid(int64_t m) {
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (nsm <= 0) nsm = 1;
     int64_t tiles = (m + TILE_M - 1) / TILE_M;
-    int64_t cap = (int64_t)nsm * 2;                   // two 92 KB blocks fit one SM
+    int64_t cap = (int64_t)nsm * TC_BLOCKS_PER_SM;
     return (int)(tiles < cap ? tiles : cap);
+}
+
+// launch one of the inference kernels (as clusters of one CTA: the MMA commit addresses its
+// mbarrier in the cluster window) and report a completion wait that gave up
+template <bool FUSED>
+static int launch_infer(const float* params_dev, const float* X, int64_t m, const FeatArgs& g, const int32_t* rowof,
+                        float* out, cudaStream_t s) {
+    SPHC_CK(cudaFuncSetAttribute(k_mlp_infer<FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
+    DBuf<int> err;
+    SPHC_TRY(err.alloc(1, s));
+    SPHC_TRY(err.zero(s));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(infer_grid(m));
+    cfg.blockDim = dim3(TC_THREADS);
+    cfg.dynamicSmemBytes = TC_SMEM;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 1;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    SPHC_CK(cudaLaunchKernelEx(&cfg, k_mlp_infer<FUSED>, params_dev, X, m, g, rowof, out, err.p));
+    int h = 0;
+    SPHC_CK(cudaMemcpyAsync(&h, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SPHC_CK(cudaStreamSynchronize(s));
+    if (h) {
+        set_error("MLP inference: a tensor-core completion wait exceeded its limit");
+        return SPHC_ECUDA;
+    }
+    return SPHC_OK;
 }
 
 int mlp_predict(const float* params_dev, const float* X, int64_t m, float* out, cudaStream_t s) {
     if (m <= 0) return SPHC_OK;
-    size_t sm = sizeof(InferSmem);
-    SPHC_CK(cudaFuncSetAttribute(k_mlp_infer<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    SPHC_LAUNCH(k_mlp_infer<false><<<infer_grid(m), INF_WARPS * 32, sm, s>>>(params_dev, X, m, FeatArgs(), nullptr, out));
-    SPHC_CK(cudaGetLastError());
-    return SPHC_OK;
+    return launch_infer<false>(params_dev, X, m, FeatArgs(), nullptr, out, s);
 }
 
 // row of every pattern entry (warp per row)
@@ -201,11 +264,7 @@ int mlp_predict_level(const float* params_dev, const FeatArgs& g, float* out, cu
     DBuf<int32_t> rowof;
     SPHC_TRY(rowof.alloc(m, s));
     SPHC_LAUNCH(k_row_of<<<grid_for(g.ne * 32, 256), 256, 0, s>>>(g.nrp, g.ne, rowof.p));
-    size_t sm = sizeof(InferSmem);
-    SPHC_CK(cudaFuncSetAttribute(k_mlp_infer<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    SPHC_LAUNCH(k_mlp_infer<true><<<infer_grid(m), INF_WARPS * 32, sm, s>>>(params_dev, nullptr, m, g, rowof.p, out));
-    SPHC_CK(cudaGetLastError());
-    return SPHC_OK;
+    return launch_infer<true>(params_dev, nullptr, m, g, rowof.p, out, s);
 }
 
 // ------------------------------------------------------------------ training (FP32)
