@@ -153,9 +153,16 @@ k_mlp_infer(const float* __restrict__ params, const float* __restrict__ X, int64
             float v[32];
             tc_ld32(tmem + lane_off + (uint32_t)(64 * half + 32 * cc), v);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const int n = 64 * half + 32 * cc + j;
-                S.a2[cm_off(row, n, NH)] = __float2bfloat16(fmaxf(v[j] + S.b1[n], 0.f));
+            for (int j8 = 0; j8 < 32; j8 += 8) {         // 8 columns = one 16-byte row of a core matrix
+                const int n0 = 64 * half + 32 * cc + j8;
+                uint32_t pk[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const __nv_bfloat16 lo = __float2bfloat16(fmaxf(v[j8 + 2 * q] + S.b1[n0 + 2 * q], 0.f));
+                    const __nv_bfloat16 hi = __float2bfloat16(fmaxf(v[j8 + 2 * q + 1] + S.b1[n0 + 2 * q + 1], 0.f));
+                    pk[q] = (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+                }
+                *reinterpret_cast<uint4*>(&S.a2[cm_off(row, n0, NH)]) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
             }
         }
         // layer 2: D2 = h1 W2
