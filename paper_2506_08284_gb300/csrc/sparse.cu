@@ -398,7 +398,7 @@ static constexpr int MED_SLOTS = 1024;       // largest per-warp table
 static constexpr int MED_FILL = 768;         // rows with more distinct columns go to the big path
 static constexpr int BIG_SLOTS = 8192;       // per block on the big path
 static constexpr int BIG_FILL = 6144;
-static constexpr int NBINS = 3;
+static constexpr int NBINS = 4;
 
 __device__ inline uint32_t hslot(int32_t key, int mask) {
     return ((uint32_t)key * 2654435761u) & (uint32_t)mask;
@@ -416,10 +416,10 @@ __device__ inline int64_t row_floor(const int64_t* brp, const int32_t* bci, int3
     return lo;
 }
 
-// bins: 0 at most 64 products and 64 A entries (register sort), 1 at most 256 products
-// (512-slot tables), 2 the rest (1024-slot tables / big path)
+// bins: 0 at most 64 products and 64 A entries (register sort), 1 at most 128 products
+// (256-slot tables), 2 at most 256 (512-slot tables), 3 the rest (1024-slot tables / big path)
 __device__ inline int spgemm_bin_of(int64_t ub, int64_t alen) {
-    return (ub <= 64 && alen <= 64) ? 0 : (ub <= 256 ? 1 : 2);
+    return (ub <= 64 && alen <= 64) ? 0 : (ub <= 128 ? 1 : (ub <= 256 ? 2 : 3));
 }
 // Product count (restricted to the upper triangle when `upper`) of every row, G lanes per row
 // (rows of long A rows, such as the P^T factors of coarse Galerkin products, would otherwise
@@ -442,7 +442,7 @@ __global__ void k_spgemm_ub(const int64_t* arp, const int32_t* aci, const int64_
             bin = spgemm_bin_of(sum, arp[i + 1] - arp[i]);
         }
     }
-    for (int b = 0; b < 3; ++b) {
+    for (int b = 0; b < NBINS; ++b) {
         int c = __syncthreads_count(bin == b);
         if (threadIdx.x == 0 && c) atomicAdd(&bin_cnt[b], c);
     }
@@ -885,7 +885,7 @@ static int spgemm_impl(const DCSR& A, const DCSR& B, DCSR& C, int upper, cudaStr
     if (n >= (1LL << 31)) { set_error("spgemm: %lld rows exceed int32 row lists", (long long)n); return SPHC_ELIMIT; }
     DBuf<int64_t> ub, cnt;
     DBuf<int32_t> big, rows;
-    DBuf<int> flags;                 // 0 bign, 1 fail, 2..4 bin counts, 5..7 bin offsets, 8..10 bin fill
+    DBuf<int> flags;                 // 0 bign, 1 fail, 2..5 bin counts, 6..9 bin offsets, 10..13 bin fill
     DBuf<int64_t> toff;              // small bin: temporary slot offsets, then its rows
     DBuf<int32_t> tci;
     DBuf<double> tv;
@@ -914,9 +914,9 @@ static int spgemm_impl(const DCSR& A, const DCSR& B, DCSR& C, int upper, cudaStr
         }
         SPHC_CK(cudaMemcpyAsync(h, flags.p, 16 * sizeof(int), cudaMemcpyDeviceToHost, s));
         SPHC_CK(cudaStreamSynchronize(s));
-        int off[NBINS] = {0, h[2], h[2] + h[3]};
-        SPHC_CK(cudaMemcpyAsync(flags.p + 5, off, NBINS * sizeof(int), cudaMemcpyHostToDevice, s));
-        SPHC_LAUNCH(k_spgemm_bin<<<grid_for(n, 256), 256, 0, s>>>(A.rp.p, ub.p, n, flags.p + 5, flags.p + 8, rows.p));
+        int off[NBINS] = {0, h[2], h[2] + h[3], h[2] + h[3] + h[4]};
+        SPHC_CK(cudaMemcpyAsync(flags.p + 6, off, NBINS * sizeof(int), cudaMemcpyHostToDevice, s));
+        SPHC_LAUNCH(k_spgemm_bin<<<grid_for(n, 256), 256, 0, s>>>(A.rp.p, ub.p, n, flags.p + 6, flags.p + 10, rows.p));
         if (h[2] > 0) {
             // small bin in one pass: sorted rows into temporary slots of ub entries each
             DBuf<int64_t> lub;
@@ -929,8 +929,9 @@ static int spgemm_impl(const DCSR& A, const DCSR& B, DCSR& C, int upper, cudaStr
             SPHC_LAUNCH(k_spgemm_small<<<(h[2] + SMALL_WARPS - 1) / SMALL_WARPS, SMALL_WARPS * 32, 0, s>>>(
                 A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p, B.v.p, rows.p, h[2], 2, upper, cnt.p, toff.p, tci.p, tv.p));
         }
-        launch_symbolic<512, 8>(A, B, rows.p + off[1], h[3], upper, ub.p, cnt.p, big.p, flags.p, s);
-        launch_symbolic<1024, 8>(A, B, rows.p + off[2], h[4], upper, ub.p, cnt.p, big.p, flags.p, s);
+        launch_symbolic<256, 8>(A, B, rows.p + off[1], h[3], upper, ub.p, cnt.p, big.p, flags.p, s);
+        launch_symbolic<512, 8>(A, B, rows.p + off[2], h[4], upper, ub.p, cnt.p, big.p, flags.p, s);
+        launch_symbolic<1024, 8>(A, B, rows.p + off[3], h[5], upper, ub.p, cnt.p, big.p, flags.p, s);
     }
     SPHC_CK(cudaGetLastError());
     int nbig = 0;
@@ -957,12 +958,13 @@ static int spgemm_impl(const DCSR& A, const DCSR& B, DCSR& C, int upper, cudaStr
     SPHC_TRY(C.ci.alloc(nnz, s));
     SPHC_TRY(C.v.alloc(nnz, s));
     if (n > 0) {
-        int off[NBINS] = {0, h[2], h[2] + h[3]};
+        int off[NBINS] = {0, h[2], h[2] + h[3], h[2] + h[3] + h[4]};
         if (h[2] > 0)
             SPHC_LAUNCH(k_copy_listed<<<grid_for((int64_t)h[2] * 32, 256), 256, 0, s>>>(rows.p, h[2], toff.p, tci.p, tv.p,
                                                                                       C.rp.p, C.ci.p, C.v.p));
-        launch_numeric<512, 4>(A, B, C, rows.p + off[1], h[3], upper, ub.p, s);
-        launch_numeric<1024, 2>(A, B, C, rows.p + off[2], h[4], upper, ub.p, s);
+        launch_numeric<256, 4>(A, B, C, rows.p + off[1], h[3], upper, ub.p, s);
+        launch_numeric<512, 4>(A, B, C, rows.p + off[2], h[4], upper, ub.p, s);
+        launch_numeric<1024, 2>(A, B, C, rows.p + off[3], h[5], upper, ub.p, s);
     }
     if (nbig > 0) {
         SPHC_CK(cudaFuncSetAttribute(k_spgemm_numeric_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big_num_sm));
