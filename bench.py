@@ -322,7 +322,8 @@ def main():
         t_call = prof[name]["ms"] / prof[name]["calls"] / 1e3
         achieved = prof[name]["bytes_per_call"] / t_call / 1e9
         roof = {"bound": "hbm", "kernel": "k_sell_sgs<float> (level-0 forward+backward multicolour SGS sweep, "
-                                          "SELL-32, one launch per colour and direction)",
+                                          "SELL-32, one launch per colour and direction, the repeated "
+                                          "middle colour left out)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_kind": f"{peak_kind} HBM copy", "traffic": sweep_traffic(),
                 "algorithmic_bytes_per_launch": prof[name]["bytes_per_call"], "ms_per_launch": t_call * 1e3}
