@@ -38,7 +38,7 @@
  *   - Reduce_Dimension drops the column of the largest coarse node in J;
  *   - make_irreducible: per disconnected row, repeatedly join two components by the pair (u,v)
  *     with the largest |Z_uv| (values within a relative 1e-9 of the maximum tie; ties -> lowest
- *     (u,v)); all rows are judged against the same D_H, new edges are merged and N rebuilt.
+ *     (u,v)); all rows are checked against the same D_H, new edges are merged and N rebuilt.
  */
 #include <stdint.h>
 #include <stdlib.h>
