@@ -890,6 +890,7 @@ static int spgemm_impl(const DCSR& A, const DCSR& B, DCSR& C, int upper, cudaStr
     DBuf<int32_t> tci;
     DBuf<double> tv;
     int64_t tslots = 0;
+    bool small_one_pass = false;
     SPHC_TRY(ub.alloc(n + 1, s));
     SPHC_TRY(cnt.alloc(n + 1, s));
     SPHC_TRY(big.alloc(n + 1, s));
@@ -918,16 +919,28 @@ static int spgemm_impl(const DCSR& A, const DCSR& B, DCSR& C, int upper, cudaStr
         SPHC_CK(cudaMemcpyAsync(flags.p + 6, off, NBINS * sizeof(int), cudaMemcpyHostToDevice, s));
         SPHC_LAUNCH(k_spgemm_bin<<<grid_for(n, 256), 256, 0, s>>>(A.rp.p, ub.p, n, flags.p + 6, flags.p + 10, rows.p));
         if (h[2] > 0) {
-            // small bin in one pass: sorted rows into temporary slots of ub entries each
+            // small bin in one pass: sorted rows into temporary slots of ub entries each, while
+            // those slots take at most a quarter of the free device memory; else a counting pass
+            // and a writing pass
             DBuf<int64_t> lub;
             SPHC_TRY(lub.alloc(h[2], s));
             SPHC_TRY(toff.alloc(h[2] + 1, s));               // the scan also writes the total
             SPHC_LAUNCH(k_list_ub<<<grid_for(h[2], 256), 256, 0, s>>>(rows.p, h[2], ub.p, lub.p));
             SPHC_TRY(exclusive_scan_i64(lub.p, toff.p, h[2], s, &tslots));
-            SPHC_TRY(tci.alloc(tslots > 0 ? tslots : 1, s));
-            SPHC_TRY(tv.alloc(tslots > 0 ? tslots : 1, s));
-            SPHC_LAUNCH(k_spgemm_small<<<(h[2] + SMALL_WARPS - 1) / SMALL_WARPS, SMALL_WARPS * 32, 0, s>>>(
-                A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p, B.v.p, rows.p, h[2], 2, upper, cnt.p, toff.p, tci.p, tv.p));
+            size_t fr = 0, tt = 0;
+            small_one_pass = cudaMemGetInfo(&fr, &tt) == cudaSuccess &&
+                             (double)tslots * (sizeof(int32_t) + sizeof(double)) <= 0.25 * (double)fr;
+            cudaGetLastError();
+            if (small_one_pass) {
+                SPHC_TRY(tci.alloc(tslots > 0 ? tslots : 1, s));
+                SPHC_TRY(tv.alloc(tslots > 0 ? tslots : 1, s));
+                SPHC_LAUNCH(k_spgemm_small<<<(h[2] + SMALL_WARPS - 1) / SMALL_WARPS, SMALL_WARPS * 32, 0, s>>>(
+                    A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p, B.v.p, rows.p, h[2], 2, upper, cnt.p, toff.p, tci.p, tv.p));
+            } else {
+                SPHC_LAUNCH(k_spgemm_small<<<(h[2] + SMALL_WARPS - 1) / SMALL_WARPS, SMALL_WARPS * 32, 0, s>>>(
+                    A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p, B.v.p, rows.p, h[2], 0, upper, cnt.p, nullptr, nullptr,
+                    nullptr));
+            }
         }
         launch_symbolic<256, 8>(A, B, rows.p + off[1], h[3], upper, ub.p, cnt.p, big.p, flags.p, s);
         launch_symbolic<512, 8>(A, B, rows.p + off[2], h[4], upper, ub.p, cnt.p, big.p, flags.p, s);
@@ -959,9 +972,12 @@ static int spgemm_impl(const DCSR& A, const DCSR& B, DCSR& C, int upper, cudaStr
     SPHC_TRY(C.v.alloc(nnz, s));
     if (n > 0) {
         int off[NBINS] = {0, h[2], h[2] + h[3], h[2] + h[3] + h[4]};
-        if (h[2] > 0)
+        if (h[2] > 0 && small_one_pass)
             SPHC_LAUNCH(k_copy_listed<<<grid_for((int64_t)h[2] * 32, 256), 256, 0, s>>>(rows.p, h[2], toff.p, tci.p, tv.p,
                                                                                       C.rp.p, C.ci.p, C.v.p));
+        else if (h[2] > 0)
+            SPHC_LAUNCH(k_spgemm_small<<<(h[2] + SMALL_WARPS - 1) / SMALL_WARPS, SMALL_WARPS * 32, 0, s>>>(
+                A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p, B.v.p, rows.p, h[2], 1, upper, nullptr, C.rp.p, C.ci.p, C.v.p));
         launch_numeric<256, 4>(A, B, C, rows.p + off[1], h[3], upper, ub.p, s);
         launch_numeric<512, 4>(A, B, C, rows.p + off[2], h[4], upper, ub.p, s);
         launch_numeric<1024, 2>(A, B, C, rows.p + off[3], h[5], upper, ub.p, s);
