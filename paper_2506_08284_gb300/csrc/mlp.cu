@@ -45,6 +45,8 @@ constexpr int TC_WAIT = 1 << 20;      // polls of an MMA-completion wait before 
 constexpr size_t TC_SMEM = 100 * 1024;
 constexpr int TC_BLOCKS_PER_SM = 2;
 
+// Operands start on 1 KB boundaries, each followed by 1 KB that no descriptor of the layout
+// reaches (a margin should a descriptor field be read as a swizzled layout).
 struct __align__(1024) TcSmem {
     __nv_bfloat16 a1[TILE_M * NF];    // features, K-major core matrices
     unsigned char g0[1024];
