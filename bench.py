@@ -54,6 +54,23 @@ def parse_args():
     return ap.parse_args()
 
 
+# ---- aggregation over ranks (one replica system per rank, no data exchange)
+def max_over_ranks(value, dist, device):
+    """The largest of every rank's value (the slowest rank sets the job's time); value as is
+    without a process group."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def seconds_per_system(ms_slowest, steps, world):
+    """Whole-job seconds per system: every rank solves `steps` systems in the slowest rank's time."""
+    return ms_slowest / 1e3 / (steps * world)
+
+
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sgs_level0_traffic_kuhn128.txt")
 
 
@@ -267,17 +284,13 @@ def main():
             dist.barrier()
         launches = pkg.sphc.launch_count() - launches0
         clocks = clk.stop() if clk else None
-        ms = ev0.elapsed_time(ev1)
-        if dist:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ev0.elapsed_time(ev1), dist, "cuda")
         return ms, wall, launches, clocks, res
 
     # headline: FP32 V-cycle + learned warm start
     opts = make_opts(pkg, "headline", weights, 1, not args.no_graph)
     ms, wall, launches, clocks, results = timed(opts, args.steps, args.warmup, sample_clocks=True)
-    sec_per_system = ms / 1e3 / (args.steps * world)
+    sec_per_system = seconds_per_system(ms, args.steps, world)
     rc, iters, relres, prof, st, info = results[-1]
 
     # comparators on the same GPU: plain FP32 and plain FP64 GPU paths (untimed by the driver)
@@ -286,7 +299,7 @@ def main():
         for name in ("fp32_plain", "fp64_plain"):
             cms, _, _, _, cres = timed(make_opts(pkg, name, weights, 0, not args.no_graph), max(1, min(args.steps, 2)), 1)
             c_rc, c_it, c_rr, _, c_st, _ = cres[-1]
-            comparators[name] = {"s": cms / 1e3 / (max(1, min(args.steps, 2)) * world), "iters": c_it,
+            comparators[name] = {"s": seconds_per_system(cms, max(1, min(args.steps, 2)), world), "iters": c_it,
                                  "relres": c_rr, "status": c_rc, "setup_ms": c_st["setup_ms"],
                                  "solve_ms": c_st["solve_ms"]}
         comparators["speedup_vs_fp64_plain"] = comparators["fp64_plain"]["s"] / sec_per_system
@@ -306,11 +319,7 @@ def main():
         for _ in range(args.steps):
             step(o2, Ah, Dh, ch, sh, bh, xh)
         torch.cuda.synchronize()
-        te = (time.perf_counter() - t1) / args.steps
-        if dist:
-            t = torch.tensor([te], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t.item())
+        te = max_over_ranks((time.perf_counter() - t1) / args.steps, dist, "cuda")
         h2d = sum(a.nbytes for a in (p.A_rowptr, p.A_col, p.A_val, p.D_rowptr, p.D_col, p.D_val, p.coords,
                                      p.sigma_edge, b))
         e2e = {"value": te / world, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(b.nbytes)}
