@@ -42,7 +42,7 @@ enum {
     SPHC_EBREAKDOWN = -5,    /* CG breakdown: p^T A p <= 0 or not finite */
     SPHC_EINFEASIBLE = -6,   /* a local commuting-constraint system has no solution */
     SPHC_ETIMEOUT = -7,      /* a bounded device wait gave up */
-    SPHC_ESTAGNATION = -8,   /* CG made no progress for several iterations */
+    SPHC_ESTAGNATION = -8,   /* CG stagnated: two consecutive iterates are identical (Sec. 7) */
     SPHC_ENUMERIC = -9,      /* non-finite or non-positive quantity where a positive one is required */
     SPHC_ELIMIT = -10        /* a size exceeded a documented kernel limit */
 };
@@ -78,7 +78,18 @@ typedef struct {
                                 thread-block cluster (x in shared memory, where it fits); 1 always
                                 a launch per colour; 2 the cluster wherever x fits (default 0;
                                 autotune overrides it) */
-    int32_t reserved[2];
+    int32_t mlp_wait_polls;  /* polls of the learned warm start's per-tile tensor-core completion waits
+                                before the kernel gives up and setup returns SPHC_ETIMEOUT (0: the
+                                default of 2^20 blocking polls; n > 0: n non-blocking checks).  The
+                                wait that drains an MMA still in flight before the tensor memory is
+                                freed always uses the default.  A small value exists to test the
+                                timeout path without hanging anything. */
+    int32_t sell_lpr0;       /* level-0 edge smoother: lanes per row of its SELL-32 copy (1, 2, 4, 8,
+                                16 or 32; 0: chosen from the mean row length, default) */
+    int32_t sell_ch0;        /* level-0 edge smoother: entries per lane load (1, 2 or 4; 0: the widest
+                                that pads little, default).  These two fix the shape the 128^3
+                                workload gets (1 and 2) on small meshes, for parity tests. */
+    int32_t reserved[4];
 } sphc_opts;
 
 /* Learned warm start (not part of the paper).  For every pattern entry (i, j) of P_e a
@@ -137,7 +148,8 @@ typedef struct {
     double solve_ms;                 /* wall time of the last sphc_solve */
     int32_t last_iters;              /* CG iterations of the last solve (first RHS) */
     double last_relres;              /* true relative residual of the last solve (first RHS) */
-    int64_t device_bytes;            /* bytes held by the handle */
+    int64_t device_bytes;            /* bytes the handle holds: growth of the library pool's used
+                                        memory across its sphc_setup */
 } sphc_stats;
 
 /* One section timer of the profile (opts.profile = 1): total device time of the section's
@@ -189,7 +201,13 @@ SPHC_API int sphc_setup(const sphc_csr* A_e, const sphc_csr* D_h, const double* 
  * V-cycle preconditioned CG: x0 = 0, stop when ||r_k|| <= tol ||b|| (Sec. 6.1).
  * iters[nrhs] and relres[nrhs] (true residual ||b - A x|| / ||b||) may be NULL.
  * Returns SPHC_OK when every right-hand side converged, else the first failure:
- * SPHC_ENOTCONV, SPHC_EBREAKDOWN, SPHC_ESTAGNATION, SPHC_EINVAL, SPHC_ECUDA.
+ *   SPHC_ENOTCONV     opts.max_iter iterations without reaching the tolerance;
+ *   SPHC_EBREAKDOWN   p^T A p <= 0 or a non-finite residual;
+ *   SPHC_ESTAGNATION  an iteration left every entry of x unchanged (the stagnation criterion of
+ *                     Sec. 7: two consecutive iterations with the same solution), which happens
+ *                     when the tolerance lies below what FP64 rounding lets CG reach;
+ *   SPHC_EINVAL, SPHC_ECUDA.
+ * On every failure x holds the last iterate and relres its true residual.
  */
 SPHC_API int sphc_solve(sphc_handle* h, const double* b, double* x, int nrhs, double tol, void* stream,
                int* iters, double* relres);
@@ -221,6 +239,12 @@ SPHC_API int sphc_trim_memory(int device, uint64_t keep_bytes);
 /* Copy up to max timers of the handle's profile into out (host memory); *n receives the number
  * of timers.  Synchronises on the recorded events.  Timers accumulate over the handle's life. */
 SPHC_API int sphc_get_profile(sphc_handle* h, sphc_timer* out, int max, int* n);
+
+/* Device memory of the library's pool on `device`: *used = bytes currently allocated from it
+ * (live handles and temporaries in flight), *reserved = bytes the pool holds mapped (used plus
+ * the cache that sphc_trim_memory returns).  Either pointer may be NULL.  Not part of the paper.
+ * Returns SPHC_EINVAL for a device without a pool, SPHC_ECUDA if a runtime call fails. */
+SPHC_API int sphc_memory_usage(int device, int64_t* used, int64_t* reserved);
 
 /* Number of kernels the library has launched in this process so far. */
 SPHC_API int64_t sphc_launch_count(void);

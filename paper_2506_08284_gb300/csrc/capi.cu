@@ -12,6 +12,17 @@ using namespace sphc;
 
 namespace {
 
+// bytes allocated from the library pool of the current device (0 without a pool)
+int64_t pool_used() {
+    cudaMemPool_t pool = device_pool();
+    uint64_t v = 0;
+    if (!pool || cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &v) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return (int64_t)v;
+}
+
 bool is_device_ptr(const void* p) {
     if (!p) return false;
     cudaPointerAttributes a;
@@ -96,6 +107,18 @@ int setup_impl(sphc_handle* h, const sphc_csr* A_e, const sphc_csr* D_h, const d
     if (o.sweep_form < 0 || o.sweep_form > 2) {
         set_error("opts.sweep_form must be 0, 1 or 2 (got %d)", (int)o.sweep_form);
         return SPHC_EINVAL;
+    }
+    {
+        const int l = o.sell_lpr0, c = o.sell_ch0;
+        if (!(l == 0 || l == 1 || l == 2 || l == 4 || l == 8 || l == 16 || l == 32) || !(c == 0 || c == 1 || c == 2 || c == 4)) {
+            set_error("opts.sell_lpr0 must be 0 or a power of two up to 32 and opts.sell_ch0 0, 1, 2 or 4 (got %d, %d)",
+                      l, c);
+            return SPHC_EINVAL;
+        }
+        if (o.mlp_wait_polls < 0) {
+            set_error("opts.mlp_wait_polls must be >= 0 (got %d)", (int)o.mlp_wait_polls);
+            return SPHC_EINVAL;
+        }
     }
     H.L.clear();
     H.L.reserve(o.max_levels > 0 ? o.max_levels : 1);
@@ -240,6 +263,7 @@ int sphc_setup(const sphc_csr* A_e, const sphc_csr* D_h, const double* coords, c
     h->H.prof.on = o.profile != 0;
     cudaStream_t s = (cudaStream_t)stream;
     auto t0 = std::chrono::steady_clock::now();
+    int64_t used0 = pool_used();
     int rc = setup_impl(h, A_e, D_h, coords, sigma_edge, s);
     if (rc != SPHC_OK) {
         cudaStreamSynchronize(s);
@@ -247,6 +271,8 @@ int sphc_setup(const sphc_csr* A_e, const sphc_csr* D_h, const double* coords, c
         return rc;
     }
     h->H.setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    cudaStreamSynchronize(s);                 // frees of setup temporaries have completed
+    h->device_bytes = pool_used() - used0;
     *out = h;
     return SPHC_OK;
 }
@@ -320,9 +346,7 @@ int sphc_get_stats(const sphc_handle* h, sphc_stats* st) {
     st->solve_ms = H.solve_ms;
     st->last_iters = H.last_iters;
     st->last_relres = H.last_relres;
-    size_t fr = 0, total = 0;
-    cudaMemGetInfo(&fr, &total);
-    st->device_bytes = 0;
+    st->device_bytes = h->device_bytes;
     return SPHC_OK;
 }
 
@@ -490,6 +514,31 @@ int sphc_get_profile(sphc_handle* h, sphc_timer* out, int max, int* n) {
 
 int64_t sphc_launch_count(void) { return (int64_t)g_launches.load(); }
 
+int sphc_memory_usage(int device, int64_t* used, int64_t* reserved) {
+    int dev = 0;
+    SPHC_CK(cudaGetDevice(&dev));
+    if (device != dev) SPHC_CK(cudaSetDevice(device));
+    cudaMemPool_t pool = device_pool();
+    uint64_t u = 0, r = 0;
+    cudaError_t e = cudaSuccess;
+    if (pool) {
+        e = cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &u);
+        if (e == cudaSuccess) e = cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &r);
+    }
+    if (device != dev) cudaSetDevice(dev);
+    if (!pool) {
+        set_error("sphc_memory_usage: no memory pool on device %d", device);
+        return SPHC_EINVAL;
+    }
+    if (e != cudaSuccess) {
+        set_error("sphc_memory_usage: %s", cudaGetErrorString(e));
+        return SPHC_ECUDA;
+    }
+    if (used) *used = (int64_t)u;
+    if (reserved) *reserved = (int64_t)r;
+    return SPHC_OK;
+}
+
 }  // extern "C"
 
 struct sphc_batch {
@@ -610,11 +659,14 @@ int sphc_solve_batched(sphc_batch* B, const double* const* b, double* const* x, 
             double rel = hsc[2 * k] > 0 ? sqrt(hsc[2 * k + 1]) / sqrt(hsc[2 * k]) : 0.0;
             if (iters) iters[(int64_t)k * nrhs + r] = it;
             if (relres) relres[(int64_t)k * nrhs + r] = rel;
-            int rc = st == 0 ? SPHC_OK : (st == 1 ? SPHC_EBREAKDOWN : SPHC_ENOTCONV);
+            int rc = st == 0 ? SPHC_OK
+                             : (st == 1 ? SPHC_EBREAKDOWN : (st == 4 ? SPHC_ESTAGNATION : SPHC_ENOTCONV));
             if (rc != SPHC_OK && status == SPHC_OK) {
                 status = rc;
                 set_error("system %d, right side %d: %s after %d iterations", k, r,
-                          rc == SPHC_EBREAKDOWN ? "CG breakdown" : "no convergence", it);
+                          rc == SPHC_EBREAKDOWN ? "CG breakdown"
+                                                : (rc == SPHC_ESTAGNATION ? "CG stagnation" : "no convergence"),
+                          it);
             }
         }
     }

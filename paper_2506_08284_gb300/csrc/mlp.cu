@@ -78,7 +78,7 @@ __device__ __forceinline__ uint64_t op_desc(const __nv_bfloat16* M, int K, int k
 template <bool FUSED>
 __global__ void __launch_bounds__(TC_THREADS, TC_BLOCKS_PER_SM)
 k_mlp_infer(const float* __restrict__ params, const float* __restrict__ X, int64_t m, FeatArgs g,
-            const int32_t* __restrict__ rowof, float* __restrict__ out, int* err) {
+            const int32_t* __restrict__ rowof, float* __restrict__ out, int* err, int polls) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     TcSmem& S = *reinterpret_cast<TcSmem*>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -145,7 +145,7 @@ k_mlp_infer(const float* __restrict__ params, const float* __restrict__ X, int64
             for (int ks = 0; ks < NF / 16; ++ks) tc_mma(tmem, op_desc(S.a1, NF, ks), op_desc(S.w1, NF, ks), idesc, ks > 0);
             tc_commit(&S.bar);
         }
-        bool ok = tc_bar_wait(&S.bar, phase, TC_WAIT);
+        bool ok = polls > 0 ? tc_bar_poll(&S.bar, phase, polls) : tc_bar_wait(&S.bar, phase, TC_WAIT);
         phase ^= 1u;
         if (__syncthreads_or(!ok)) { failed = true; break; }
         tc_fence_after();
@@ -178,7 +178,7 @@ k_mlp_infer(const float* __restrict__ params, const float* __restrict__ X, int64
                 tc_mma(tmem + TC_D2, op_desc(S.a2, NH, ks), op_desc(S.w2, NH, ks), idesc, ks > 0);
             tc_commit(&S.bar);
         }
-        ok = tc_bar_wait(&S.bar, phase, TC_WAIT);
+        ok = polls > 0 ? tc_bar_poll(&S.bar, phase, polls) : tc_bar_wait(&S.bar, phase, TC_WAIT);
         phase ^= 1u;
         if (__syncthreads_or(!ok)) { failed = true; break; }
         tc_fence_after();
@@ -200,10 +200,10 @@ k_mlp_infer(const float* __restrict__ params, const float* __restrict__ X, int64
         if (half == 0 && base + row < m) out[base + row] = y + S.part[row] + b3;
     }
     if (failed) {
-        // a completion wait gave up: report, give the MMA in flight one more bounded wait, and
-        // release the tensor memory
+        // a completion wait gave up: report, give the MMA in flight one more wait with the full
+        // limit (it must complete before its tensor memory is freed), and release the memory
         if (tid == 0) atomicExch(err, 1);
-        tc_bar_wait(&S.bar, phase ^ 1u, TC_WAIT);
+        if (!tc_bar_wait(&S.bar, phase ^ 1u, TC_WAIT) && tid == 0) atomicExch(err, 2);
     }
     tc_fence_before();
     __syncthreads();
@@ -225,7 +225,7 @@ static int infer_grid(int64_t m) {
 // mbarrier in the cluster window) and report a completion wait that gave up
 template <bool FUSED>
 static int launch_infer(const float* params_dev, const float* X, int64_t m, const FeatArgs& g, const int32_t* rowof,
-                        float* out, cudaStream_t s) {
+                        float* out, cudaStream_t s, int polls) {
     SPHC_CK(cudaFuncSetAttribute(k_mlp_infer<FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
     DBuf<int> err;
     SPHC_TRY(err.alloc(1, s));
@@ -243,20 +243,22 @@ static int launch_infer(const float* params_dev, const float* X, int64_t m, cons
     cfg.attrs = at;
     cfg.numAttrs = 1;
     g_launches.fetch_add(1, std::memory_order_relaxed);
-    SPHC_CK(cudaLaunchKernelEx(&cfg, k_mlp_infer<FUSED>, params_dev, X, m, g, rowof, out, err.p));
+    SPHC_CK(cudaLaunchKernelEx(&cfg, k_mlp_infer<FUSED>, params_dev, X, m, g, rowof, out, err.p, polls));
     int h = 0;
     SPHC_CK(cudaMemcpyAsync(&h, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     SPHC_CK(cudaStreamSynchronize(s));
     if (h) {
-        set_error("MLP inference: a tensor-core completion wait exceeded its limit");
-        return SPHC_ECUDA;
+        set_error("MLP inference: a tensor-core completion wait exceeded its limit of %d %s polls%s",
+                  polls > 0 ? polls : TC_WAIT, polls > 0 ? "non-blocking" : "blocking",
+                  h == 2 ? " (and the drain wait before freeing tensor memory gave up too)" : "");
+        return SPHC_ETIMEOUT;
     }
     return SPHC_OK;
 }
 
 int mlp_predict(const float* params_dev, const float* X, int64_t m, float* out, cudaStream_t s) {
     if (m <= 0) return SPHC_OK;
-    return launch_infer<false>(params_dev, X, m, FeatArgs(), nullptr, out, s);
+    return launch_infer<false>(params_dev, X, m, FeatArgs(), nullptr, out, s, 0);
 }
 
 // row of every pattern entry (warp per row)
@@ -267,13 +269,13 @@ __global__ void k_row_of(const int64_t* nrp, int64_t ne, int32_t* rowof) {
     for (int64_t q = nrp[i] + lane; q < nrp[i + 1]; q += 32) rowof[q] = (int32_t)i;
 }
 
-int mlp_predict_level(const float* params_dev, const FeatArgs& g, float* out, cudaStream_t s) {
+int mlp_predict_level(const float* params_dev, const FeatArgs& g, float* out, cudaStream_t s, int polls) {
     int64_t m = g.nnzN;
     if (m <= 0) return SPHC_OK;
     DBuf<int32_t> rowof;
     SPHC_TRY(rowof.alloc(m, s));
     SPHC_LAUNCH(k_row_of<<<grid_for(g.ne * 32, 256), 256, 0, s>>>(g.nrp, g.ne, rowof.p));
-    return launch_infer<true>(params_dev, nullptr, m, g, rowof.p, out, s);
+    return launch_infer<true>(params_dev, nullptr, m, g, rowof.p, out, s, polls);
 }
 
 // ------------------------------------------------------------------ training (FP32)

@@ -46,13 +46,17 @@ int scratch_for_device(int dev, double** out) {
     return SPHC_OK;
 }
 
-bool on_device(const void* p) {
+// Where p lives: 0 host (or unknown to CUDA), 1 device memory of `dev` or managed memory, -1
+// device memory of another GPU (a kernel here would read a peer address: rejected).
+int placement(const void* p, int dev) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
-        return false;
+        return 0;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return 1;
+    if (a.type == cudaMemoryTypeDevice) return a.device == dev ? 1 : -1;
+    return 0;
 }
 
 // grid (NA_BLOCKS, nrhs): block partial sums of (b - A x)_i^2 and b_i^2 for one right-hand side
@@ -133,14 +137,20 @@ extern "C" int sphc_relres_noalloc(const sphc_handle* h, const double* b, const 
                   nrhs, SPHC_NOALLOC_MAX_RHS);
         return SPHC_EINVAL;
     }
-    if (!on_device(b) || !on_device(x)) {
-        set_error("sphc_relres_noalloc: b and x must be device pointers (host data would need a staging copy)");
-        return SPHC_EINVAL;
-    }
     int dev = 0;
     SPHC_CK(cudaGetDevice(&dev));
     if (dev != h->device) {
         set_error("sphc_relres_noalloc: the current device %d is not the handle's device %d", dev, h->device);
+        return SPHC_EINVAL;
+    }
+    int pb = placement(b, dev), px = placement(x, dev), pr = placement(relres, dev);
+    if (pb != 1 || px != 1) {
+        set_error("sphc_relres_noalloc: b and x must be memory of the handle's device %d (host data would need a "
+                  "staging copy; another GPU's memory is not read)", dev);
+        return SPHC_EINVAL;
+    }
+    if (pr < 0) {
+        set_error("sphc_relres_noalloc: relres is memory of another GPU than the handle's device %d", dev);
         return SPHC_EINVAL;
     }
     double* scratch = nullptr;
@@ -149,7 +159,7 @@ extern "C" int sphc_relres_noalloc(const sphc_handle* h, const double* b, const 
     cudaStream_t s = (cudaStream_t)stream;
     SPHC_LAUNCH(k_na_partial<<<dim3(NA_BLOCKS, nrhs), NA_THREADS, 0, s>>>(A.rp.p, A.ci.p, A.v.p, A.nr, b, x, scratch));
     SPHC_LAUNCH(k_na_final<<<nrhs, 256, 0, s>>>(scratch));
-    if (on_device(relres)) {
+    if (pr == 1) {
         SPHC_LAUNCH(k_na_gather<<<1, 64, 0, s>>>(scratch, nrhs, relres));
     } else {
         for (int k = 0; k < nrhs; ++k)

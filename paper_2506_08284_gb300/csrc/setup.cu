@@ -1838,7 +1838,7 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
         FeatBufs fb;
         FeatArgs fg;
         SPHC_TRY(feat_prepare(L, Xnext, lev, fb, fg, s));
-        SPHC_TRY(mlp_predict_level(mlp_params, fg, corr.p, s));
+        SPHC_TRY(mlp_predict_level(mlp_params, fg, corr.p, s, o.mlp_wait_polls));
         emin_iters = o.learned_emin_iters;
     }
     Section* sec_p0 = new Section(prof, lev_name("setup_P0", lev).c_str(), s);

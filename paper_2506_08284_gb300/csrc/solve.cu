@@ -99,7 +99,8 @@ static int build_vlevel(Hierarchy& H, int l, VLevel<T>& V, bool split, cudaStrea
         SPHC_TRY(build_xop<T>(L.Pn, O.pn.p, C.in.p, V.Pn, s));
         L.AD = DCSR();
     }
-    SPHC_TRY(build_smooth<T>(L.A, O.pe.p, O.ie.p, O.ce, 0, 0, V.A, s));
+    SPHC_TRY(build_smooth<T>(L.A, O.pe.p, O.ie.p, O.ce, l == 0 ? H.opts.sell_ch0 : 0, l == 0 ? H.opts.sell_lpr0 : 0,
+                             V.A, s));
     SPHC_TRY(build_smooth<T>(L.An, O.pn.p, O.in.p, O.cn, 0, 0, V.An, s));
     V.A.cluster = cluster_sgs_chosen(V.A, H.opts.sweep_form) ? 1 : 0;
     V.An.cluster = cluster_sgs_chosen(V.An, H.opts.sweep_form) ? 1 : 0;
@@ -954,15 +955,23 @@ int autotune_vcycle(Hierarchy& H, cudaStream_t s) {
 
 // ------------------------------------------------------------------ CG
 // scal: 0 rz, 1 pq, 2 rr, 3 rz_new, 4 z.r_old, 5 bb
+// x += alpha p, r -= alpha q.  *moved is set when some entry of x changed: an iteration that
+// leaves every entry unchanged is the stagnation of Sec. 7 (two consecutive iterations with the
+// same solution), which k_cg_check reports.
 __global__ void k_cg_xr(double* x, double* r, double* rold, const double* p, const double* q, const double* sc,
-                        int64_t n, int flexible) {
+                        int64_t n, int flexible, int* moved) {
     pdl_enter();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double alpha = sc[1] > 0.0 ? sc[0] / sc[1] : 0.0;     // breakdown: leave x unchanged
-    x[i] += alpha * p[i];
-    if (flexible) rold[i] = r[i];
-    r[i] -= alpha * q[i];
+    bool changed = false;
+    if (i < n) {
+        double alpha = sc[1] > 0.0 ? sc[0] / sc[1] : 0.0;     // breakdown: leave x unchanged
+        double xo = x[i], xn = xo + alpha * p[i];
+        changed = xn != xo;
+        x[i] = xn;
+        if (flexible) rold[i] = r[i];
+        r[i] -= alpha * q[i];
+    }
+    if (__syncthreads_or(changed) && threadIdx.x == 0 && *(volatile int*)moved == 0) *moved = 1;
 }
 __global__ void k_cg_p(double* p, const double* z, const double* sc, int64_t n, int flexible) {
     pdl_enter();
@@ -981,8 +990,10 @@ __global__ void k_sub(const double* b, double* q, int64_t n) {
     if (i < n) q[i] = b[i] - q[i];
 }
 
-// end of one graph iteration: count it and keep looping while not converged, not broken down
-// and below the iteration cap.  itc[1]: 0 converged, 1 breakdown, 2 cap reached.
+// end of one graph iteration: count it and keep looping while not converged, not broken down,
+// not stagnated and below the iteration cap.  itc[1]: 0 converged, 1 breakdown, 2 cap reached,
+// 4 stagnation (itc[2], set by k_cg_xr, was not: x did not change); itc[2] is cleared for the
+// next iteration.
 __global__ void k_cg_check(cudaGraphConditionalHandle hnd, const double* sc, int* itc, int max_iter) {
     pdl_enter();
     int it = itc[0] + 1;
@@ -991,8 +1002,19 @@ __global__ void k_cg_check(cudaGraphConditionalHandle hnd, const double* sc, int
     unsigned cont = 1;
     if (!(pq > 0.0) || !isfinite(rr)) { itc[1] = 1; cont = 0; }
     else if (rr <= lim) { itc[1] = 0; cont = 0; }
+    else if (itc[2] == 0) { itc[1] = 4; cont = 0; }
     else if (it >= max_iter) { itc[1] = 2; cont = 0; }
+    itc[2] = 0;
     cudaGraphSetConditional(hnd, cont);
+}
+// status code of the CG control word itc[1]
+static int cg_status(int code) {
+    switch (code) {
+        case 0: return SPHC_OK;
+        case 1: return SPHC_EBREAKDOWN;
+        case 4: return SPHC_ESTAGNATION;
+        default: return SPHC_ENOTCONV;
+    }
 }
 __global__ void k_set_limit(double* sc, double tol2) {
     pdl_enter();
@@ -1011,7 +1033,7 @@ static int cg_body(Hierarchy& H, cudaGraphConditionalHandle hnd, cudaStream_t s)
     launch_pdl(k_cg_shift, 1, 1, 0, s, sc);
     SPHC_TRY(cg_spmv(H, H.p.p, H.q.p, s));
     dot_buf(H, H.p.p, H.q.p, n, sc + 1, s);
-    launch_pdl(k_cg_xr, grid_for(n, 256), 256, 0, s, H.x.p, H.r.p, H.rold.p, H.p.p, H.q.p, sc, n, flexible);
+    launch_pdl(k_cg_xr, grid_for(n, 256), 256, 0, s, H.x.p, H.r.p, H.rold.p, H.p.p, H.q.p, sc, n, flexible, H.itc.p + 2);
     dot_buf(H, H.r.p, H.r.p, n, sc + 2, s);
     launch_pdl(k_cg_check, 1, 1, 0, s, hnd, sc, H.itc.p, H.opts.max_iter);
     SPHC_CK(cudaGetLastError());
@@ -1068,6 +1090,14 @@ static double read_relres(Hierarchy& H, double bnorm, cudaStream_t s) {
     return bnorm > 0 ? sqrt(hr) / bnorm : 0.0;
 }
 
+static void cg_error(int status, int it) {
+    if (status == SPHC_EBREAKDOWN) set_error("CG breakdown after %d iterations", it);
+    else if (status == SPHC_ENOTCONV) set_error("CG did not reach the tolerance in %d iterations", it);
+    else if (status == SPHC_ESTAGNATION)
+        set_error("CG stagnated after %d iterations: an iteration left x unchanged (tolerance below the "
+                  "FP64 rounding floor of this system)", it);
+}
+
 // CG on the device: the first iteration is enqueued directly, the rest run inside one graph
 // launch whose while node repeats an iteration until the stopping test holds.  b and x are in
 // the caller's numbering; the iteration runs in the level-0 V-cycle numbering.
@@ -1096,24 +1126,29 @@ static int pcg_graph(Hierarchy& H, const double* b, double* x, double tol, cudaS
             SPHC_TRY(cg_spmv(H, H.p.p, H.q.p, s));
         }
         dot_buf(H, H.p.p, H.q.p, n, sc + 1, s);
-        launch_pdl(k_cg_xr, grid_for(n, 256), 256, 0, s, H.x.p, H.r.p, H.rold.p, H.p.p, H.q.p, sc, n, flexible);
+        SPHC_CK(cudaMemsetAsync(H.itc.p + 2, 0, sizeof(int), s));
+        launch_pdl(k_cg_xr, grid_for(n, 256), 256, 0, s, H.x.p, H.r.p, H.rold.p, H.p.p, H.q.p, sc, n, flexible,
+                   H.itc.p + 2);
         dot_buf(H, H.r.p, H.r.p, n, sc + 2, s);
         launch_pdl(k_set_limit, 1, 1, 0, s, sc, tol * tol);
-        int hi[2] = {1, 0};
-        SPHC_CK(cudaMemcpyAsync(H.itc.p, hi, 2 * sizeof(int), cudaMemcpyHostToDevice, s));
+        int hmoved = 0;
+        SPHC_CK(cudaMemcpyAsync(&hmoved, H.itc.p + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
+        int hi[3] = {1, 0, 0};
+        SPHC_CK(cudaMemcpyAsync(H.itc.p, hi, 3 * sizeof(int), cudaMemcpyHostToDevice, s));
         double hsc[8];
         SPHC_CK(cudaMemcpyAsync(hsc, sc, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
         SPHC_CK(cudaStreamSynchronize(s));
         it = 1;
         if (!(hsc[1] > 0.0) || !std::isfinite(hsc[2])) status = SPHC_EBREAKDOWN;
         else if (hsc[2] <= hsc[7]) status = SPHC_OK;
+        else if (!hmoved) status = SPHC_ESTAGNATION;
         else if (it >= H.opts.max_iter) status = SPHC_ENOTCONV;
         else {
             SPHC_CK(cudaGraphLaunch(H.cg_exec, s));
             SPHC_CK(cudaMemcpyAsync(hi, H.itc.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
             SPHC_CK(cudaStreamSynchronize(s));
             it = hi[0];
-            status = hi[1] == 0 ? SPHC_OK : (hi[1] == 1 ? SPHC_EBREAKDOWN : SPHC_ENOTCONV);
+            status = cg_status(hi[1]);
             g_launches.fetch_add(H.body_launches * (long long)(it - 1));
         }
     }
@@ -1123,8 +1158,7 @@ static int pcg_graph(Hierarchy& H, const double* b, double* x, double tol, cudaS
     SPHC_CK(cudaGetLastError());
     if (iters) *iters = it;
     if (relres) *relres = rr;
-    if (status == SPHC_EBREAKDOWN) set_error("CG breakdown after %d iterations", it);
-    else if (status == SPHC_ENOTCONV) set_error("CG did not reach the tolerance in %d iterations", it);
+    cg_error(status, it);
     return status;
 }
 
@@ -1139,6 +1173,7 @@ __global__ void k_cg_prep(cudaGraphConditionalHandle hnd, double* sc, int* itc) 
     sc[0] = 1.0;                         // rz of the previous iteration (p = 0 makes beta irrelevant)
     itc[0] = 0;
     itc[1] = sc[5] > 0.0 ? 3 : 0;        // 3: running; 0: converged (b = 0)
+    itc[2] = 0;
     cudaGraphSetConditional(hnd, sc[5] > 0.0 ? 1u : 0u);
 }
 
@@ -1153,7 +1188,7 @@ static int cg_iter_body(Hierarchy& H, cudaGraphConditionalHandle hnd, cudaStream
     launch_pdl(k_cg_shift, 1, 1, 0, s, sc);
     SPHC_TRY(cg_spmv(H, H.p.p, H.q.p, s));
     dot_buf(H, H.p.p, H.q.p, n, sc + 1, s);
-    launch_pdl(k_cg_xr, grid_for(n, 256), 256, 0, s, H.x.p, H.r.p, H.rold.p, H.p.p, H.q.p, sc, n, flexible);
+    launch_pdl(k_cg_xr, grid_for(n, 256), 256, 0, s, H.x.p, H.r.p, H.rold.p, H.p.p, H.q.p, sc, n, flexible, H.itc.p + 2);
     dot_buf(H, H.r.p, H.r.p, n, sc + 2, s);
     launch_pdl(k_cg_check, 1, 1, 0, s, hnd, sc, H.itc.p, H.opts.max_iter);
     SPHC_CK(cudaGetLastError());
@@ -1241,13 +1276,18 @@ int pcg_solve(Hierarchy& H, const double* b, double* x, double tol, cudaStream_t
             SPHC_TRY(cg_spmv(H, H.p.p, H.q.p, s));
             if (tid >= 0) H.prof.end(tid, s);
             SPHC_TRY(dot64(H.p.p, H.q.p, n, sc + 1, s));
-            launch_pdl(k_cg_xr, grid_for(n, 256), 256, 0, s, H.x.p, H.r.p, H.rold.p, H.p.p, H.q.p, sc, n, flexible);
+            SPHC_CK(cudaMemsetAsync(H.itc.p + 2, 0, sizeof(int), s));
+            launch_pdl(k_cg_xr, grid_for(n, 256), 256, 0, s, H.x.p, H.r.p, H.rold.p, H.p.p, H.q.p, sc, n, flexible,
+                       H.itc.p + 2);
             ++it;
             SPHC_TRY(dot64(H.r.p, H.r.p, n, sc + 2, s));
+            int hmoved = 0;
+            SPHC_CK(cudaMemcpyAsync(&hmoved, H.itc.p + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
             SPHC_CK(cudaMemcpyAsync(hsc, sc, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
             SPHC_CK(cudaStreamSynchronize(s));
             if (!(hsc[1] > 0.0) || !std::isfinite(hsc[2])) { status = SPHC_EBREAKDOWN; break; }
             if (sqrt(hsc[2]) <= tol * bnorm) { status = SPHC_OK; break; }
+            if (!hmoved) { status = SPHC_ESTAGNATION; break; }
             SPHC_TRY(apply_vcycle(H, H.r.p, H.z.p, s));
             SPHC_TRY(dot64(H.r.p, H.z.p, n, sc + 3, s));
             if (flexible) SPHC_TRY(dot64(H.z.p, H.rold.p, n, sc + 4, s));
@@ -1261,10 +1301,7 @@ int pcg_solve(Hierarchy& H, const double* b, double* x, double tol, cudaStream_t
     SPHC_CK(cudaGetLastError());
     if (iters) *iters = it;
     if (relres) *relres = rr;
-    if (status != SPHC_OK && status != SPHC_ENOTCONV)
-        set_error("CG breakdown after %d iterations", it);
-    else if (status == SPHC_ENOTCONV)
-        set_error("CG did not reach the tolerance in %d iterations", it);
+    cg_error(status, it);
     return status;
 }
 

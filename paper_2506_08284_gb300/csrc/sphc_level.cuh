@@ -142,7 +142,8 @@ int level_features(const Level& L, const DBuf<double>& Xc, int lev, float* F, cu
 int mlp_predict(const float* params_dev, const float* X, int64_t m, float* out, cudaStream_t s);
 struct FeatArgs;
 // features of every pattern entry of a level computed on the fly and fed to the MLP (no feature buffer)
-int mlp_predict_level(const float* params_dev, const FeatArgs& g, float* out, cudaStream_t s);
+// polls > 0: the per-tile completion waits give up after that many non-blocking checks (SPHC_ETIMEOUT)
+int mlp_predict_level(const float* params_dev, const FeatArgs& g, float* out, cudaStream_t s, int polls = 0);
 
 // Scoped section timer (no-op when prof is null).
 struct Section {
@@ -235,4 +236,5 @@ int autotune_vcycle(Hierarchy& H, cudaStream_t s);
 struct sphc_handle {
     sphc::Hierarchy H;
     int device = 0;
+    int64_t device_bytes = 0;        // growth of the library pool's used memory across setup
 };

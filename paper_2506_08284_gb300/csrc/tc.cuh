@@ -33,6 +33,24 @@ __device__ __forceinline__ bool tc_bar_wait(uint64_t* bar, uint32_t parity, int 
         if (tc_bar_try_wait(bar, parity)) return true;
     return false;
 }
+// non-blocking check of the phase (mbarrier.test_wait returns at once)
+__device__ __forceinline__ bool tc_bar_test(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(tc_smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// false if the phase did not complete within `limit` non-blocking checks
+__device__ __forceinline__ bool tc_bar_poll(uint64_t* bar, uint32_t parity, int limit) {
+    for (int it = 0; it < limit; ++it)
+        if (tc_bar_test(bar, parity)) return true;
+    return false;
+}
 
 // ---- tensor memory (one warp, all lanes)
 __device__ __forceinline__ void tc_alloc(uint32_t* dst, uint32_t ncols) {

@@ -37,7 +37,8 @@ class sphc_opts(ctypes.Structure):
                 ("vcycle_fp32", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("flexible", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("cg_graph", ctypes.c_int32), ("learned", ctypes.c_int32),
                 ("learned_emin_iters", ctypes.c_int32), ("mlp_params", ctypes.c_void_p),
-                ("autotune", ctypes.c_int32), ("sweep_form", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("autotune", ctypes.c_int32), ("sweep_form", ctypes.c_int32), ("mlp_wait_polls", ctypes.c_int32),
+                ("sell_lpr0", ctypes.c_int32), ("sell_ch0", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 class sphc_train_opts(ctypes.Structure):
@@ -79,7 +80,8 @@ EXPORTED = ["sphc_default_opts", "sphc_setup", "sphc_solve", "sphc_vcycle", "sph
             "sphc_get_level_info", "sphc_export_size", "sphc_export", "sphc_destroy", "sphc_last_error",
             "sphc_get_profile", "sphc_launch_count", "sphc_relres_noalloc", "sphc_default_train_opts",
             "sphc_mlp_train", "sphc_mlp_predict", "sphc_mlp_gradient", "sphc_export_features",
-            "sphc_setup_batched", "sphc_solve_batched", "sphc_batch_destroy", "sphc_trim_memory"]
+            "sphc_setup_batched", "sphc_solve_batched", "sphc_batch_destroy", "sphc_trim_memory",
+            "sphc_memory_usage"]
 
 _lib = None
 
@@ -106,6 +108,7 @@ def load(path: str | None = None):
     lib.sphc_get_profile.argtypes = [P, ctypes.POINTER(sphc_timer), I, ctypes.POINTER(I)]
     lib.sphc_relres_noalloc.argtypes = [P, P, P, I, P, P]
     lib.sphc_trim_memory.argtypes = [I, ctypes.c_uint64]
+    lib.sphc_memory_usage.argtypes = [I, P, P]
     lib.sphc_default_train_opts.argtypes = [ctypes.POINTER(sphc_train_opts)]
     lib.sphc_mlp_train.argtypes = [P, P, I64, ctypes.POINTER(sphc_train_opts), P, P, P]
     lib.sphc_mlp_predict.argtypes = [P, P, I64, P, P]
@@ -139,6 +142,21 @@ def _ptr(a):
     if isinstance(a, np.ndarray):
         return a.ctypes.data
     return a.data_ptr()
+
+
+def _require_f64(name, a, need):
+    """Raise ValueError unless a is a contiguous float64 array/tensor with at least `need` entries."""
+    if isinstance(a, np.ndarray):
+        ok_t, ok_c, size = a.dtype == np.float64, a.flags["C_CONTIGUOUS"], a.size
+    else:
+        import torch
+        ok_t, ok_c, size = a.dtype == torch.float64, a.is_contiguous(), a.numel()
+    if not ok_t:
+        raise ValueError(f"{name}: float64 required")
+    if not ok_c:
+        raise ValueError(f"{name}: contiguous storage required")
+    if size < need:
+        raise ValueError(f"{name}: {size} entries, at least {need} required")
 
 
 def _stream(stream):
@@ -192,6 +210,9 @@ class Handle:
 
     def solve(self, b, x, tol=1e-8, nrhs=1, stream=None):
         """b, x: FP64 arrays/tensors of nrhs x n_e.  Returns (status, iters[], relres[])."""
+        n = self.level_info(0)["n_edges"]
+        _require_f64("b", b, nrhs * n)
+        _require_f64("x", x, nrhs * n)
         it = (ctypes.c_int * nrhs)()
         rr = (ctypes.c_double * nrhs)()
         rc = load().sphc_solve(self._ptr, _ptr(b), _ptr(x), nrhs, tol, _stream(stream), it, rr)
@@ -214,7 +235,12 @@ class Handle:
 
     def relres_noalloc(self, b, x, relres, nrhs=1, stream=None):
         """||b - A x|| / ||b|| through sphc_relres_noalloc (b, x on the device; relres host or device).
-        Returns the status code."""
+        Returns the status code.  b and x must be contiguous float64 with at least nrhs * n_e
+        entries and relres contiguous float64 with at least nrhs entries (checked here, before the
+        library reads them)."""
+        n = self.level_info(0)["n_edges"]
+        for name, a, need in (("b", b, nrhs * n), ("x", x, nrhs * n), ("relres", relres, nrhs)):
+            _require_f64(name, a, max(need, 0))
         return load().sphc_relres_noalloc(self._ptr, _ptr(b), _ptr(x), nrhs, _ptr(relres), _stream(stream))
 
     def features(self, level=0, stream=None):
@@ -338,6 +364,13 @@ def setup_batched(systems, opts=None, stream=None) -> Batch:
 
 def launch_count() -> int:
     return int(load().sphc_launch_count())
+
+
+def memory_usage(device: int = 0):
+    """(used, reserved) bytes of the library's memory pool on `device`."""
+    u, r = ctypes.c_int64(), ctypes.c_int64()
+    _check(load().sphc_memory_usage(int(device), ctypes.byref(u), ctypes.byref(r)))
+    return u.value, r.value
 
 
 def trim_memory(device: int = 0, keep_bytes: int = 0) -> int:

@@ -36,7 +36,13 @@ def test_noalloc_relres_matches_solve():
     Y[1] += 1e-3
     for trial in range(2):                                   # two calls in a row
         out = np.full(nrhs, -1.0)
+        torch.cuda.synchronize()
+        pool0, torch0 = pkg.sphc.memory_usage(0), torch.cuda.memory_allocated()
         assert h.relres_noalloc(B, X, out, nrhs=nrhs) == 0
+        torch.cuda.synchronize()
+        # the call allocated nothing: neither the library's pool nor torch's allocator moved
+        assert pkg.sphc.memory_usage(0) == pool0
+        assert torch.cuda.memory_allocated() == torch0
         # sphc_solve forms A x in its own layout and summation order; b - A x cancels to ~1e-8
         # of b, so the two agree to the rounding of A x relative to b, not to 1e-10 of the result
         np.testing.assert_allclose(out, rr_solve, rtol=FP64_RTOL, atol=1e-14)
@@ -49,6 +55,13 @@ def test_noalloc_relres_matches_solve():
         # the host reference sums in another order; b - A x cancels to ~1e-9 of b, so compare
         # in units of the rounding of A x relative to b
         np.testing.assert_allclose(dev_out.cpu().numpy(), ref, rtol=1e-9, atol=1e-14)
+    # arguments the wrapper refuses before the library could read past them
+    with pytest.raises(ValueError):
+        h.relres_noalloc(B.float(), X, np.zeros(nrhs), nrhs=nrhs)
+    with pytest.raises(ValueError):
+        h.relres_noalloc(B[:1], X, np.zeros(nrhs), nrhs=nrhs)
+    with pytest.raises(ValueError):
+        h.relres_noalloc(B, X, np.zeros(nrhs - 1), nrhs=nrhs)
     # more right-hand sides than the fixed scratch holds: a clear error, nothing launched
     Bbig = torch.zeros((65, p.n_edges), dtype=torch.float64, device="cuda")
     rc = h.relres_noalloc(Bbig, Bbig, np.zeros(65), nrhs=65)
