@@ -656,7 +656,7 @@ int sphc_solve_batched(sphc_batch* B, const double* const* b, double* const* x, 
             Hierarchy& H = B->hs[k]->H;
             int it = hit[2 * k], st = hit[2 * k + 1];
             g_launches.fetch_add(H.branch_launches + H.body_launches * (long long)it);
-            double rel = hsc[2 * k] > 0 ? sqrt(hsc[2 * k + 1]) / sqrt(hsc[2 * k]) : 0.0;
+            double rel = hsc[2 * k] == 0.0 ? 0.0 : sqrt(hsc[2 * k + 1]) / sqrt(hsc[2 * k]);
             if (iters) iters[(int64_t)k * nrhs + r] = it;
             if (relres) relres[(int64_t)k * nrhs + r] = rel;
             int rc = st == 0 ? SPHC_OK

@@ -1087,7 +1087,7 @@ static double read_relres(Hierarchy& H, double bnorm, cudaStream_t s) {
     double hr = 0.0;
     cudaMemcpyAsync(&hr, H.scal.p + 6, sizeof(double), cudaMemcpyDeviceToHost, s);
     cudaStreamSynchronize(s);
-    return bnorm > 0 ? sqrt(hr) / bnorm : 0.0;
+    return bnorm == 0.0 ? 0.0 : sqrt(hr) / bnorm;   // NaN for a non-finite b
 }
 
 static void cg_error(int status, int it) {
@@ -1116,7 +1116,7 @@ static int pcg_graph(Hierarchy& H, const double* b, double* x, double tol, cudaS
     SPHC_CK(cudaStreamSynchronize(s));
     double bnorm = sqrt(hb);
     int status = SPHC_OK, it = 0;
-    if (bnorm > 0.0) {
+    if (!(bnorm == 0.0)) {               // a non-finite b runs into the breakdown test of iteration 1
         SPHC_TRY(apply_vcycle(H, H.r.p, H.z.p, s));
         SPHC_CK(cudaMemcpyAsync(H.p.p, H.z.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
         dot_buf(H, H.r.p, H.z.p, n, sc + 0, s);
@@ -1172,9 +1172,10 @@ __global__ void k_cg_prep(cudaGraphConditionalHandle hnd, double* sc, int* itc) 
     sc[7] = sc[8] * sc[5];
     sc[0] = 1.0;                         // rz of the previous iteration (p = 0 makes beta irrelevant)
     itc[0] = 0;
-    itc[1] = sc[5] > 0.0 ? 3 : 0;        // 3: running; 0: converged (b = 0)
+    const bool run = !(sc[5] == 0.0);    // b = 0 is converged; a non-finite b breaks down in iteration 1
+    itc[1] = run ? 3 : 0;                // 3: running; 0: converged
     itc[2] = 0;
-    cudaGraphSetConditional(hnd, sc[5] > 0.0 ? 1u : 0u);
+    cudaGraphSetConditional(hnd, run ? 1u : 0u);
 }
 
 static int cg_iter_body(Hierarchy& H, cudaGraphConditionalHandle hnd, cudaStream_t s) {

@@ -61,7 +61,8 @@ def test_nonfinite_rhs_gives_ebreakdown(kuhn8):
     b[17] = np.nan
     x = np.zeros_like(b)
     rc, it, rr = h.solve(b, x, tol=1e-8)
-    assert rc == EBREAKDOWN and it[0] == 1
+    assert rc == EBREAKDOWN and it[0] == 1 and np.isnan(rr[0])
+    assert b"breakdown" in pkg.sphc.load().sphc_last_error()
     b[17] = 0.5
     rc, it, rr = h.solve(b, x, tol=1e-8)
     assert rc == 0
