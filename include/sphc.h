@@ -286,6 +286,14 @@ SPHC_API int sphc_mlp_gradient(const float* params, const float* X, const float*
  * setup.  Synchronises the stream. */
 SPHC_API int sphc_export_features(const sphc_handle* h, int level, float* X, float* y, void* stream);
 
+/* The learned warm start's inference as setup runs it (features computed inside the
+ * tensor-core kernel, no feature matrix in memory), applied with `params` (SPHC_MLP_NPARAM
+ * floats, host or device) to every pattern entry of level `level`: out[nnz(P_e)] (host or
+ * device) receives the raw network outputs, before the constraint projection.  For parity tests
+ * against the network's definition on the features of sphc_export_features.  Needs coords at
+ * setup.  Synchronises the stream.  Errors: SPHC_EINVAL, SPHC_ENOMEM, SPHC_ECUDA, SPHC_ETIMEOUT. */
+SPHC_API int sphc_mlp_predict_level(const sphc_handle* h, int level, const float* params, float* out, void* stream);
+
 /* Largest nrhs that sphc_relres_noalloc accepts (its fixed scratch holds this many). */
 #define SPHC_NOALLOC_MAX_RHS 64
 

@@ -707,6 +707,24 @@ int sphc_export_features(const sphc_handle* h, int level, float* X, float* y, vo
     return SPHC_OK;
 }
 
+int sphc_mlp_predict_level(const sphc_handle* h, int level, const float* params, float* out, void* stream) {
+    if (!h || !params || !out || level < 0 || level + 1 >= h->H.nlev || !h->H.L[level].has_transfer) {
+        set_error("sphc_mlp_predict_level: invalid argument or level %d has no prolongator", level);
+        return SPHC_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const Level& L = h->H.L[level];
+    int64_t nnz = L.P0.nnz;
+    DBuf<float> P, Y;
+    SPHC_TRY(P.alloc(SPHC_MLP_NPARAM, s));
+    SPHC_CK(cudaMemcpyAsync(P.p, params, sizeof(float) * SPHC_MLP_NPARAM, cudaMemcpyDefault, s));
+    SPHC_TRY(Y.alloc(nnz, s));
+    SPHC_TRY(level_prediction(L, h->H.L[level + 1].X, level, P.p, Y.p, s));
+    if (nnz > 0) SPHC_CK(cudaMemcpyAsync(out, Y.p, sizeof(float) * nnz, cudaMemcpyDefault, s));
+    SPHC_CK(cudaStreamSynchronize(s));
+    return SPHC_OK;
+}
+
 const char* sphc_last_error(void) { return sphc::last_error(); }
 
 }  // extern "C"

@@ -1551,6 +1551,16 @@ __global__ void k_features(FeatArgs g, float* F) {
     for (int c = 0; c < SPHC_MLP_NFEAT; ++c) out[c] = f[c];
 }
 
+// the fused tensor-core inference (features computed in the kernel) on every pattern entry
+int level_prediction(const Level& L, const DBuf<double>& Xc, int lev, const float* params_dev, float* out,
+                     cudaStream_t s) {
+    FeatBufs B;
+    FeatArgs g;
+    SPHC_TRY(feat_prepare(L, Xc, lev, B, g, s));
+    SPHC_TRY(mlp_predict_level(params_dev, g, out, s));
+    SPHC_CK(cudaStreamSynchronize(s));          // B is released on return
+    return SPHC_OK;
+}
 int level_features(const Level& L, const DBuf<double>& Xc, int lev, float* F, cudaStream_t s) {
     FeatBufs B;
     FeatArgs g;

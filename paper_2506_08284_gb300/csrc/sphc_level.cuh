@@ -138,6 +138,8 @@ struct Profiler {
 int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext, DCSR& Annext, DBuf<double>& Xnext,
                 const float* mlp_params, Profiler* prof, cudaStream_t s);
 int level_features(const Level& L, const DBuf<double>& Xc, int lev, float* F, cudaStream_t s);
+int level_prediction(const Level& L, const DBuf<double>& Xc, int lev, const float* params_dev, float* out,
+                     cudaStream_t s);
 // mlp.cu
 int mlp_predict(const float* params_dev, const float* X, int64_t m, float* out, cudaStream_t s);
 struct FeatArgs;

@@ -81,7 +81,7 @@ EXPORTED = ["sphc_default_opts", "sphc_setup", "sphc_solve", "sphc_vcycle", "sph
             "sphc_get_profile", "sphc_launch_count", "sphc_relres_noalloc", "sphc_default_train_opts",
             "sphc_mlp_train", "sphc_mlp_predict", "sphc_mlp_gradient", "sphc_export_features",
             "sphc_setup_batched", "sphc_solve_batched", "sphc_batch_destroy", "sphc_trim_memory",
-            "sphc_memory_usage"]
+            "sphc_memory_usage", "sphc_mlp_predict_level"]
 
 _lib = None
 
@@ -114,6 +114,7 @@ def load(path: str | None = None):
     lib.sphc_mlp_predict.argtypes = [P, P, I64, P, P]
     lib.sphc_mlp_gradient.argtypes = [P, P, P, I, P, P, P]
     lib.sphc_export_features.argtypes = [P, I, P, P, P]
+    lib.sphc_mlp_predict_level.argtypes = [P, I, P, P, P]
     lib.sphc_setup_batched.argtypes = [I, P, P, P, P, ctypes.POINTER(sphc_opts), P, ctypes.POINTER(P)]
     lib.sphc_solve_batched.argtypes = [P, P, P, I, ctypes.c_double, P, P, P]
     lib.sphc_batch_destroy.argtypes = [P]
@@ -250,6 +251,17 @@ class Handle:
         y = np.empty(nz, np.float32)
         _check(load().sphc_export_features(self._ptr, level, _ptr(X), _ptr(y), _stream(stream)))
         return X, y
+
+    def predict_level(self, params, level=0, stream=None):
+        """Raw outputs of the fused tensor-core inference on every pattern entry of a level
+        (numpy float32 [nnz(P_e)])."""
+        nr, nc, nz = self.export_size(level, "Pe")
+        params = np.ascontiguousarray(params, np.float32)
+        if params.size != MLP_NPARAM:
+            raise ValueError(f"params: {params.size} entries, {MLP_NPARAM} required")
+        out = np.empty(nz, np.float32)
+        _check(load().sphc_mlp_predict_level(self._ptr, level, _ptr(params), _ptr(out), _stream(stream)))
+        return out
 
     def profile(self) -> dict:
         arr = (sphc_timer * 256)()

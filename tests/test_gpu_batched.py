@@ -1,11 +1,12 @@
 """Batched uneven systems through the C ABI: every system's whole CG as one branch of a single
-CUDA graph; results match the single-system solves."""
+CUDA graph; results match the single-system solves and, system by system, the CPU oracle
+(FP64: iterations +-1 and x to 1e-9; FP32 V-cycle: x to 1e-6 of the FP64 oracle)."""
 import numpy as np
 import pytest
 
 import meshgen
 import paper_2506_08284_gb300 as pkg
-from gpu_util import gpu_setup
+from gpu_util import gpu_setup, oracle_setup
 
 pytestmark = pytest.mark.gpu
 
@@ -33,11 +34,21 @@ def test_batched_matches_single(fp32):
     assert np.all(rr <= 1.01e-8)
     for k, p in enumerate(probs):
         h = gpu_setup(p, vcycle_fp32=fp32, max_coarse=200)
+        o = oracle_setup(p, max_coarse=200)
         for r in range(nrhs):
             x1 = np.zeros(p.n_edges)
             rc1, it1, rr1 = h.solve(bs[k][r].copy(), x1)
             assert abs(it1[0] - it[k, r]) <= 1
             assert np.linalg.norm(xs[k][r] - x1) <= 1e-7 * np.linalg.norm(x1)
+            ref = o.solve(bs[k][r], tol=1e-8)
+            assert ref["status"] == 0
+            err = np.linalg.norm(xs[k][r] - ref["x"]) / np.linalg.norm(ref["x"])
+            if fp32:
+                assert err <= 1e-6, (k, r, err)
+                assert it[k, r] <= ref["iters"] + 3
+            else:
+                assert err <= 1e-9, (k, r, err)
+                assert abs(int(it[k, r]) - ref["iters"]) <= 1
         h.destroy()
     # a second solve on the same graph reuses it
     xs2 = [np.zeros_like(b) for b in bs]

@@ -30,6 +30,25 @@ def test_inference_matches_oracle():
     assert np.corrcoef(out, ref)[0, 1] > 0.9999
 
 
+@pytest.mark.parametrize("which", ["trained", "random"])
+def test_fused_inference_matches_oracle(which):
+    # the kernel setup runs: features computed in the tensor-core kernel from the level's
+    # operators, against the network's FP64 definition on the exported FP32 features
+    from paper_2506_08284_gb300 import learned
+    spec = meshgen.MeshSpec(12, jitter=0.2, seed_jitter=31, sigma="lognormal", sigma_in=2.0, seed_sigma=32)
+    p = meshgen.generate(spec)
+    params = learned.load_weights() if which == "trained" else _params(np.random.default_rng(5), 0.1)
+    h = _hierarchy(p, max_coarse=100)
+    for level in range(h.nlevels - 1):
+        X, _ = h.features(level)
+        out = h.predict_level(params, level)
+        ref = mlp.forward(np.asarray(params, np.float64), X)
+        assert out.shape == ref.shape and np.all(np.isfinite(out))
+        assert np.abs(out - ref).max() <= 3e-2 * (np.abs(ref).max() + 1e-3), level
+        assert np.corrcoef(out, ref)[0, 1] > 0.999, level
+    h.destroy()
+
+
 def test_training_gradient_matches_oracle():
     rng = np.random.default_rng(1)
     p = _params(rng)
