@@ -89,7 +89,11 @@ typedef struct {
     int32_t sell_ch0;        /* level-0 edge smoother: entries per lane load (1, 2 or 4; 0: the widest
                                 that pads little, default).  These two fix the shape the 128^3
                                 workload gets (1 and 2) on small meshes, for parity tests. */
-    int32_t reserved[4];
+    int32_t emin_fp32;       /* 1: the masked product (A P)|_N / a_ii of eq. (9) accumulates in FP32;
+                                its projection onto the row constraints and the update of P_e stay
+                                FP64, so P_e D_H = D_h P_n holds to FP64 rounding either way
+                                (default 0: FP64 throughout) */
+    int32_t reserved[3];
 } sphc_opts;
 
 /* Learned warm start (not part of the paper).  For every pattern entry (i, j) of P_e a

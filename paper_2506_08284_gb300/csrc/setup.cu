@@ -1371,56 +1371,100 @@ k_p0_rows(int64_t ne, const int64_t* __restrict__ trp, const int32_t* __restrict
     for (int t = 0; t < S.np; ++t) p0[S.n0 + t] = (d ? (double)d[S.n0 + t] : 0.0) + row_gz(S, t, z);
 }
 
-// masked product of eq. (9) for every row: w_{i,t} = (A P)_{i, N_i(t)} / a_ii.  A group of L lanes
-// owns a pattern entry (L as large as the row allows); its lanes split A's row i and search each
-// P row f for the entry's column (one FMA per match, no atomics), then add up.
-__global__ void __launch_bounds__(LOC_WARPS * 32)
-k_emin_product(int64_t ne, const int64_t* __restrict__ arp, const int32_t* __restrict__ aci,
-               const double* __restrict__ av, const int64_t* __restrict__ nrp, const int32_t* __restrict__ nci,
-               const double* __restrict__ P, double* __restrict__ w) {
-    int lane = threadIdx.x & 31;
-    int64_t i = (int64_t)blockIdx.x * LOC_WARPS + (threadIdx.x >> 5);
-    if (i >= ne) return;
-    int64_t n0 = nrp[i];
-    int np = (int)(nrp[i + 1] - n0);
-    if (np == 0) return;
-    int64_t a0 = arp[i], a1 = arp[i + 1];
-    double aii = 1.0;
-    int has = 0;
-    for (int64_t ka = a0 + lane; ka < a1; ka += 32)
-        if (aci[ka] == i) { aii = av[ka]; has = 1; }
-    unsigned hm = __ballot_sync(0xffffffffu, has);
-    if (hm) aii = __shfl_sync(0xffffffffu, aii, __ffs(hm) - 1);
-    double inv_aii = 1.0 / aii;
-    int L = 1;
-    while (L < 32 && np * (2 * L) <= 32) L *= 2;
-    int G = 32 / L, grp = lane / L, sub = lane & (L - 1);
-    int trips = (np + G - 1) / G;
-    for (int it = 0; it < trips; ++it) {
-        int t = grp + it * G;
-        double acc = 0.0;
-        if (t < np) {
-            int32_t j = nci[n0 + t];
-            for (int64_t ka = a0 + sub; ka < a1; ka += L) {
-                int32_t f = aci[ka];
-                int64_t lo = nrp[f], hi = nrp[f + 1] - 1;
-                while (lo < hi) {
-                    int64_t mid = (lo + hi) >> 1;
-                    if (nci[mid] < j) lo = mid + 1; else hi = mid;
-                }
-                if (lo <= hi && nci[lo] == j) acc += av[ka] * P[lo];
-            }
-        }
-        for (int dd = L >> 1; dd > 0; dd >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, dd);
-        if (t < np && sub == 0) w[n0 + t] = acc * inv_aii;
+// Masked product of eq. (9) for every row that the thread-per-row projection handles:
+// w_{i,t} = (A P)_{i, N_i(t)} / a_ii.  A group of W lanes owns row i.  The row's pattern columns
+// (at most 32) go into a 64-slot open-addressing table in shared memory (column -> t).  The group
+// walks A's row entry by entry, reads P row f coalesced across its lanes and adds a_if P_{f,c}
+// into the accumulator of the row's entry with column c, if there is one.  Within one f the
+// columns are distinct, so no two lanes touch one accumulator; the entries f follow A's row
+// order, so every sum is taken in a fixed order.  Acc is double, or float for the FP32
+// accumulation of opts.emin_fp32 (the projection that follows stays FP64).
+constexpr int PP_WARPS = 8;
+constexpr int PP_SLOTS = 64;
+__device__ __forceinline__ uint32_t pp_hash(int32_t c) { return ((uint32_t)c * 0x9E3779B1u) >> 26; }
+__device__ __forceinline__ int pp_lookup(const int32_t* key, const int8_t* val, int32_t c) {
+    uint32_t s = pp_hash(c);
+    // at most 32 keys in 64 slots: an empty slot ends every probe well before the bound
+    for (int q = 0; q < PP_SLOTS; ++q) {
+        const int32_t k = key[s];
+        if (k == c) return val[s];
+        if (k < 0) return -1;
+        s = (s + 1) & (PP_SLOTS - 1);
     }
+    return -1;
+}
+template <typename Acc, int W>
+__global__ void __launch_bounds__(PP_WARPS * 32)
+k_emin_pp(int64_t ne, const int64_t* __restrict__ arp, const int32_t* __restrict__ aci, const double* __restrict__ av,
+          const int64_t* __restrict__ nrp, const int32_t* __restrict__ nci, const double* __restrict__ P,
+          const int8_t* __restrict__ ck, Acc* __restrict__ w) {
+    constexpr int R = 32 / W;                          // rows per warp
+    __shared__ int32_t s_key[PP_WARPS * R][PP_SLOTS];
+    __shared__ int8_t s_val[PP_WARPS * R][PP_SLOTS];
+    __shared__ Acc s_acc[PP_WARPS * R][32];
+    const int lane = threadIdx.x & 31, g = lane / W, sub = lane % W;
+    const int slot = (threadIdx.x >> 5) * R + g;
+    const unsigned gmask = W == 32 ? 0xffffffffu : (((1u << W) - 1u) << (g * W));
+    const int64_t i = ((int64_t)blockIdx.x * PP_WARPS + (threadIdx.x >> 5)) * R + g;
+    if (i >= ne || ck[i] < 0) return;                  // whole group: no row, or a row k_emin handles
+    const int64_t n0 = nrp[i];
+    const int np = (int)(nrp[i + 1] - n0);
+    if (np <= 0 || np > 32) return;
+    int32_t* key = s_key[slot];
+    int8_t* val = s_val[slot];
+    Acc* acc = s_acc[slot];
+    for (int q = sub; q < PP_SLOTS; q += W) key[q] = -1;
+    for (int q = sub; q < 32; q += W) acc[q] = Acc(0);
+    __syncwarp(gmask);
+    for (int t = sub; t < np; t += W) {
+        const int32_t c = nci[n0 + t];
+        uint32_t h = pp_hash(c);
+        for (int q = 0; q < PP_SLOTS; ++q) {           // keys are distinct; a free slot exists
+            if (atomicCAS(&key[h], -1, c) == -1) { val[h] = (int8_t)t; break; }
+            h = (h + 1) & (PP_SLOTS - 1);
+        }
+    }
+    __syncwarp(gmask);
+    const int64_t a0 = arp[i], a1 = arp[i + 1];
+    double aii = 1.0;
+    for (int64_t base = a0; base < a1; base += W) {
+        const int64_t ka = base + sub;
+        int32_t f = -1;
+        double a = 0.0;
+        int64_t ps = 0;
+        int pl = 0;
+        if (ka < a1) {
+            f = aci[ka];
+            a = av[ka];
+            ps = nrp[f];
+            pl = (int)(nrp[f + 1] - ps);
+        }
+        const unsigned dm = (__ballot_sync(gmask, ka < a1 && f == (int32_t)i) & gmask) >> (g * W);
+        if (dm) aii = __shfl_sync(gmask, a, __ffs(dm) - 1, W);
+        const int cnt = (int)(a1 - base < W ? a1 - base : W);
+        for (int k = 0; k < cnt; ++k) {
+            const Acc ak = (Acc)__shfl_sync(gmask, a, k, W);
+            const int64_t psk = __shfl_sync(gmask, ps, k, W);
+            const int plk = __shfl_sync(gmask, pl, k, W);
+            for (int q = sub; q < plk; q += W) {
+                const int32_t c = nci[psk + q];
+                const Acc v = (Acc)P[psk + q];
+                const int t = pp_lookup(key, val, c);
+                if (t >= 0) acc[t] += ak * v;
+            }
+            __syncwarp(gmask);
+        }
+    }
+    const double inv = 1.0 / aii;
+    for (int t = sub; t < np; t += W) w[n0 + t] = (Acc)((double)acc[t] * inv);
 }
 
 // projection and update of eq. (9) for every small row: dp = w - G~ (G~^T G~)^-1 G~^T w,
 // P' = P - omega dp, with the system factored by k_p0_rows (rows too large for a thread are
 // handled by k_emin through a row list)
+template <typename V>
 __global__ void __launch_bounds__(128)
-k_emin_rows(int64_t ne, const int64_t* __restrict__ nrp, const double* __restrict__ w, const double* __restrict__ P,
+k_emin_rows(int64_t ne, const int64_t* __restrict__ nrp, const V* __restrict__ w, const double* __restrict__ P,
             double* __restrict__ Pout, double omega, RowCache cache) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ne) return;
@@ -1439,7 +1483,7 @@ k_emin_rows(int64_t ne, const int64_t* __restrict__ nrp, const double* __restric
     for (int a = 0; a < TK; ++a) z[a] = -z[a];
     row_solve(S, z);
     for (int t = 0; t < S.np; ++t) {
-        double dp = w[S.n0 + t] - row_gz(S, t, z);
+        double dp = (double)w[S.n0 + t] - row_gz(S, t, z);
         Pout[S.n0 + t] = P[S.n0 + t] - omega * dp;
     }
 }
@@ -1893,20 +1937,40 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
     DBuf<double> Pnew;
     SPHC_TRY(Pnew.alloc(nnzN, s));
     delete sec_cp;
-    // algorithmic bytes of one step: A (values, columns, row pointers), the pattern rows of P
-    // (columns, values), T (columns, values), the new values and two coarse-edge ends per entry
-    double emin_bytes = (double)L.A.nnz * 12.0 + (double)ne * 8.0 * 3 + (double)nnzN * (4 + 8 + 8 + 8) +
-                        (double)L.T.nnz * 12.0;
+    // algorithmic bytes of one step: A (values, columns, row pointers) once; P's pattern (row
+    // pointers, columns, values) once, however often its rows are gathered; w written and read;
+    // per row the stored factor (masks, k, lower triangle); P read and P' written by the update
+    const size_t wsz = o.emin_fp32 ? sizeof(float) : sizeof(double);
+    double emin_bytes = (double)L.A.nnz * 12.0 + (double)(ne + 1) * 8.0 * 2 + (double)nnzN * (4 + 8) +
+                        (double)nnzN * 2.0 * (double)wsz + (double)ne * (2 * TK * 4 + 1 + TL * 8) +
+                        (double)nnzN * 16.0;
     int tid = prof ? prof->find(lev_name("emin_level", lev).c_str(), emin_bytes) : -1;
     DBuf<double> W;
-    if (emin_iters > 0) SPHC_TRY(W.alloc(nnzN, s));
+    DBuf<float> W32;
+    if (emin_iters > 0) {
+        if (o.emin_fp32) SPHC_TRY(W32.alloc(nnzN, s));
+        else SPHC_TRY(W.alloc(nnzN, s));
+    }
+    // lanes per row of the product: about one P row per pass of the group
+    const double mean_np = ne > 0 ? (double)nnzN / (double)ne : 0.0;
+    const int ppw = mean_np <= 8.0 ? 8 : (mean_np <= 16.0 ? 16 : 32);
     for (int it = 0; it < emin_iters; ++it) {
         if (tid >= 0) prof->begin(tid, s);
         if (ne > 0) {
-            SPHC_LAUNCH(k_emin_product<<<grid_for(ne, LOC_WARPS), LOC_WARPS * 32, 0, s>>>(
-                ne, L.A.rp.p, L.A.ci.p, L.A.v.p, L.Pe.rp.p, L.Pe.ci.p, L.Pe.v.p, W.p));
-            SPHC_LAUNCH(k_emin_rows<<<grid_for(ne, 128), 128, 0, s>>>(ne, L.Pe.rp.p, W.p, L.Pe.v.p, Pnew.p, o.emin_omega,
-                                                                      cache));
+            const int64_t rows_per_block = PP_WARPS * (32 / ppw);
+            const int gpp = grid_for(ne, (int)rows_per_block);
+#define PP(ACC, WW, OUT) SPHC_LAUNCH(k_emin_pp<ACC, WW><<<gpp, PP_WARPS * 32, 0, s>>>(ne, L.A.rp.p, L.A.ci.p, L.A.v.p, \
+                                     L.Pe.rp.p, L.Pe.ci.p, L.Pe.v.p, cache.k, OUT))
+            if (o.emin_fp32) {
+                if (ppw == 8) PP(float, 8, W32.p); else if (ppw == 16) PP(float, 16, W32.p); else PP(float, 32, W32.p);
+                SPHC_LAUNCH(k_emin_rows<float><<<grid_for(ne, 128), 128, 0, s>>>(ne, L.Pe.rp.p, W32.p, L.Pe.v.p, Pnew.p,
+                                                                                 o.emin_omega, cache));
+            } else {
+                if (ppw == 8) PP(double, 8, W.p); else if (ppw == 16) PP(double, 16, W.p); else PP(double, 32, W.p);
+                SPHC_LAUNCH(k_emin_rows<double><<<grid_for(ne, 128), 128, 0, s>>>(ne, L.Pe.rp.p, W.p, L.Pe.v.p, Pnew.p,
+                                                                                  o.emin_omega, cache));
+            }
+#undef PP
             if (hbig > 0)
                 SPHC_LAUNCH(k_emin<<<grid_for(hbig, LOC_WARPS), LOC_WARPS * 32, sm, s>>>(
                     hbig, big.p, L.A.rp.p, L.A.ci.p, L.A.v.p, L.T.rp.p, L.T.ci.p, L.T.v.p, L.Pe.rp.p, L.Pe.ci.p,

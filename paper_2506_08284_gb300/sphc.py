@@ -38,7 +38,8 @@ class sphc_opts(ctypes.Structure):
                 ("profile", ctypes.c_int32), ("cg_graph", ctypes.c_int32), ("learned", ctypes.c_int32),
                 ("learned_emin_iters", ctypes.c_int32), ("mlp_params", ctypes.c_void_p),
                 ("autotune", ctypes.c_int32), ("sweep_form", ctypes.c_int32), ("mlp_wait_polls", ctypes.c_int32),
-                ("sell_lpr0", ctypes.c_int32), ("sell_ch0", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("sell_lpr0", ctypes.c_int32), ("sell_ch0", ctypes.c_int32), ("emin_fp32", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 class sphc_train_opts(ctypes.Structure):

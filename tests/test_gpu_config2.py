@@ -1,16 +1,31 @@
 """The 48^3 box-conductivity workload (753,552 unknowns, jitter +-0.2h, sigma 1 inside
 [0.25, 0.75]^3 and 1e-3 outside, RHS seed 3) on the GPU against the CPU oracle, element by
-element: every integer array of the hierarchy bit for bit, every FP64 setup value to 1e-10 of
-the largest entry, the FP64 solve to the oracle's iteration count +-1 and x to 1e-9, and the
-FP32 V-cycle solve to x within 1e-6 of the FP64 oracle.  The measured errors are printed.
+element: every integer array of the hierarchy bit for bit, the FP64 setup values to the
+accuracy FP64 allows for this input (below), the FP64 solve to the oracle's iteration count +-1,
+and the FP32 V-cycle solve to x within 1e-6 of the FP64 oracle.  The measured errors are printed.
+
+Why not 1e-10 everywhere: A_n = D_h^T A_e D_h equals D_h^T M_sigma D_h only because the
+curl-curl part annihilates gradients (K D_h = 0, Sec. 1).  In FP64 that cancellation leaves
+noise of order eps ||K|| per entry, which in the sigma = 1e-3 region is large against the
+sigma-scale entries.  The test measures that noise on the oracle's own A_n against the
+cancellation-free D_h^T M_sigma D_h (eta, relative to each row's diagonal), checks that the
+GPU's A_n carries noise of the same size, and compares the quantities computed from A_n (P_n,
+P0, P_e, x) to max(1e-10, 4 eta).  The sigma-1 cases of test_gpu_parity keep the 1e-10 bound.
 """
 import numpy as np
 import pytest
+import scipy.sparse as sp
 
 import meshgen
 from gpu_util import assert_csr_close, assert_csr_equal_pattern, gpu_setup, oracle_setup
 
 pytestmark = pytest.mark.gpu
+
+
+def _row_noise(An, exact):
+    """max over rows of max_j |An - exact|_ij / exact_ii"""
+    E = abs((An - exact).tocsr())
+    return float(np.max(E.max(axis=1).toarray().ravel() / exact.diagonal()))
 
 
 @pytest.fixture(scope="module")
@@ -21,12 +36,23 @@ def kuhn48():
     o = oracle_setup(p)
     ref = o.solve(b, tol=1e-8)
     assert ref["status"] == 0
-    return p, b, o, ref
+    M = meshgen.generate(spec, which="M")
+    D = sp.csr_matrix((p.D_val, p.D_col, p.D_rowptr), shape=(p.n_edges, p.n_nodes))
+    Mm = sp.csr_matrix((M.A_val, M.A_col, M.A_rowptr), shape=(p.n_edges, p.n_edges))
+    exact = (D.T @ (Mm @ D)).tocsr()
+    eta = _row_noise(o.matrix(0, "An").to_scipy(), exact)
+    print(f"\nconfig2 kuhn48: FP64 cancellation noise of A_n (oracle vs D^T M D, per row diagonal) = {eta:.3e}")
+    return p, b, o, ref, exact, eta
 
 
 def test_config2_fp64_hierarchy_matches_oracle(kuhn48):
-    p, b, o, ref = kuhn48
+    p, b, o, ref, exact, eta = kuhn48
+    tol = max(1e-10, 4 * eta)
     h = gpu_setup(p, vcycle_fp32=0)
+    rp, ci, v, shape = h.export(0, "An")
+    eta_gpu = _row_noise(sp.csr_matrix((v, ci, rp), shape=shape), exact)
+    print(f"config2 kuhn48: GPU A_n noise {eta_gpu:.3e}, tolerance for values computed from A_n {tol:.3e}")
+    assert eta_gpu <= 4 * eta
     assert h.nlevels == o.nlevels
     for l in range(o.nlevels):
         np.testing.assert_array_equal(h.export(l, "col_e"), o.ivec(l, "col_e"))
@@ -38,13 +64,13 @@ def test_config2_fp64_hierarchy_matches_oracle(kuhn48):
         assert_csr_close(h.export(l, "DH"), o.matrix(l, "DH"), f"L{l} D_H", 0.0)
         assert_csr_equal_pattern(h.export(l, "T"), o.matrix(l, "T"), f"L{l} T")
         for what in ("Pn", "P0", "Pe"):
-            assert_csr_close(h.export(l, what), o.matrix(l, what), f"L{l} {what}", 1e-10)
+            assert_csr_close(h.export(l, what), o.matrix(l, what), f"L{l} {what}", tol)
     h.destroy()
 
 
 @pytest.mark.parametrize("fp32", [0, 1])
 def test_config2_solve_matches_oracle(kuhn48, fp32):
-    p, b, o, ref = kuhn48
+    p, b, o, ref, exact, eta = kuhn48
     h = gpu_setup(p, vcycle_fp32=fp32)
     x = np.zeros_like(b)
     rc, it, rr = h.solve(b, x, tol=1e-8)
@@ -56,6 +82,6 @@ def test_config2_solve_matches_oracle(kuhn48, fp32):
         assert err <= 1e-6
         assert it[0] <= ref["iters"] + 3
     else:
-        assert err <= 1e-9
+        assert err <= max(1e-9, 4 * eta)
         assert abs(it[0] - ref["iters"]) <= 1
     h.destroy()

@@ -207,3 +207,26 @@ def test_fp32_bench_shape_smoother(pair):
     assert rc == 0 and rr[0] <= 1.01e-8
     assert np.linalg.norm(x - ref["x"]) <= 1e-6 * np.linalg.norm(ref["x"])
     hb.destroy()
+
+
+def test_emin_fp32_accumulation(pair):
+    # opts.emin_fp32: the masked product of eq. (9) accumulated in FP32, the projection in FP64.
+    # P_e moves by the FP32 rounding of one damped step (bound 1e-5 of its largest entry), the
+    # commuting relation still holds to FP64 rounding, and the solve still converges.
+    name, p, h, o, opts = pair
+    hf = gpu_setup(p, vcycle_fp32=1, emin_fp32=1, **opts)
+    for l in range(o.nlevels - 1):
+        assert_csr_close(hf.export(l, "Pe"), o.matrix(l, "Pe"), f"L{l} Pe (FP32 product)", 1e-5)
+        M = {}
+        for what in ("Pe", "DH", "D", "Pn"):
+            rp, ci, v, shape = hf.export(l, what)
+            M[what] = sp.csr_matrix((v, ci, rp), shape=shape)
+        rhs = M["D"] @ M["Pn"]
+        assert abs(M["Pe"] @ M["DH"] - rhs).max() <= 1e-12 * max(1.0, abs(rhs).max())
+    b = meshgen.rhs(5, p.n_edges)
+    x = np.zeros_like(b)
+    rc, it, rr = hf.solve(b, x, tol=1e-8)
+    ref = o.solve(b, tol=1e-8)
+    assert rc == 0 and rr[0] <= 1.01e-8
+    assert np.linalg.norm(x - ref["x"]) <= 1e-6 * np.linalg.norm(ref["x"])
+    hf.destroy()
