@@ -93,7 +93,10 @@ typedef struct {
                                 its projection onto the row constraints and the update of P_e stay
                                 FP64, so P_e D_H = D_h P_n holds to FP64 rounding either way
                                 (default 0: FP64 throughout) */
-    int32_t reserved[3];
+    int32_t block_rhs;       /* 1: sphc_solve with nrhs >= 2 solves the right-hand sides in blocks of up
+                                to 16, one CG per column sharing every operator read (vectors
+                                interleaved per row); 0: one right-hand side after another (default 1) */
+    int32_t reserved[2];
 } sphc_opts;
 
 /* Learned warm start (not part of the paper).  For every pattern entry (i, j) of P_e a

@@ -234,6 +234,7 @@ int sphc_default_opts(sphc_opts* o) {
     o->learned_emin_iters = 0;
     o->mlp_params = nullptr;
     o->autotune = 0;
+    o->block_rhs = 1;
     return SPHC_OK;
 }
 
@@ -289,6 +290,38 @@ int sphc_solve(sphc_handle* h, const double* b, double* x, int nrhs, double tol,
     bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
     DBuf<double> bb, xb;
     auto t0 = std::chrono::steady_clock::now();
+    if (nrhs >= 2 && H.opts.block_rhs) {
+        // blocks of up to 16 right-hand sides, each one CG per column sharing the operator reads
+        constexpr int BMAX = 16;
+        const int64_t cap = (int64_t)(nrhs < BMAX ? nrhs : BMAX) * n;
+        if (!bdev) SPHC_TRY(bb.alloc(cap, s));
+        if (!xdev) SPHC_TRY(xb.alloc(cap, s));
+        std::vector<int> it(nrhs, 0);
+        std::vector<double> rr(nrhs, 0.0);
+        int status = SPHC_OK;
+        for (int k0 = 0; k0 < nrhs; k0 += BMAX) {
+            const int m = nrhs - k0 < BMAX ? nrhs - k0 : BMAX;
+            const double* bd = b + (int64_t)k0 * n;
+            double* xd = x + (int64_t)k0 * n;
+            if (!bdev) {
+                SPHC_CK(cudaMemcpyAsync(bb.p, bd, sizeof(double) * n * m, cudaMemcpyDefault, s));
+                bd = bb.p;
+            }
+            int rc = pcg_block(H, bd, xdev ? xd : xb.p, m, tol, s, it.data() + k0, rr.data() + k0);
+            if (!xdev) SPHC_CK(cudaMemcpyAsync(xd, xb.p, sizeof(double) * n * m, cudaMemcpyDefault, s));
+            if (rc != SPHC_OK && status == SPHC_OK) status = rc;
+            if (rc == SPHC_ECUDA || rc == SPHC_ENOMEM) break;
+        }
+        SPHC_CK(cudaStreamSynchronize(s));
+        for (int k = 0; k < nrhs; ++k) {
+            if (iters) iters[k] = it[k];
+            if (relres) relres[k] = rr[k];
+        }
+        H.last_iters = it[0];
+        H.last_relres = rr[0];
+        H.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        return status;
+    }
     if (!bdev) SPHC_TRY(bb.alloc(n, s));
     if (!xdev) SPHC_TRY(xb.alloc(n, s));
     int status = SPHC_OK;

@@ -1284,28 +1284,29 @@ __device__ __forceinline__ void row_solve(const RowSys& S, double x[TK]) {
         x[a] = v * S.L[a][a];
     }
 }
-// (G~ z)_t
+// (G~ z)_t.  Row t of G~ has at most one +1 and one -1 among the kept columns, so the two values
+// are picked by integer selects and the FP64 pipe (thin on this GPU) does one subtraction.
 __device__ __forceinline__ double row_gz(const RowSys& S, int t, const double z[TK]) {
-    double v = 0.0;
+    double zh = 0.0, zt = 0.0;
 #pragma unroll
-    for (int a = 0; a < TK; ++a)
-        if (a < S.k) {
-            if ((S.pos[a] >> t) & 1u) v += z[a];
-            if ((S.neg[a] >> t) & 1u) v -= z[a];
-        }
-    return v;
+    for (int a = 0; a < TK; ++a) {
+        const bool in = a < S.k;
+        zh = in && ((S.pos[a] >> t) & 1u) ? z[a] : zh;
+        zt = in && ((S.neg[a] >> t) & 1u) ? z[a] : zt;
+    }
+    return zh - zt;
 }
-// x -= G~^T v (v read from memory, one value per pattern entry)
+// x -= G~^T v (v read from memory, one value per pattern entry): per kept column, the entries of
+// its set bits only
 template <typename V>
 __device__ __forceinline__ void row_sub_gtv(const RowSys& S, const V* v, double x[TK]) {
-    for (int t = 0; t < S.np; ++t) {
-        double vt = (double)v[S.n0 + t];
 #pragma unroll
-        for (int a = 0; a < TK; ++a)
-            if (a < S.k) {
-                if ((S.pos[a] >> t) & 1u) x[a] -= vt;
-                if ((S.neg[a] >> t) & 1u) x[a] += vt;
-            }
+    for (int a = 0; a < TK; ++a) {
+        if (a >= S.k) continue;
+        double acc = x[a];
+        for (uint32_t m = S.pos[a]; m; m &= m - 1u) acc -= (double)v[S.n0 + __ffs(m) - 1];
+        for (uint32_t m = S.neg[a]; m; m &= m - 1u) acc += (double)v[S.n0 + __ffs(m) - 1];
+        x[a] = acc;
     }
 }
 
@@ -1442,17 +1443,43 @@ k_emin_pp(int64_t ne, const int64_t* __restrict__ arp, const int32_t* __restrict
         const unsigned dm = (__ballot_sync(gmask, ka < a1 && f == (int32_t)i) & gmask) >> (g * W);
         if (dm) aii = __shfl_sync(gmask, a, __ffs(dm) - 1, W);
         const int cnt = (int)(a1 - base < W ? a1 - base : W);
-        for (int k = 0; k < cnt; ++k) {
-            const Acc ak = (Acc)__shfl_sync(gmask, a, k, W);
+        // the first W entries of every P row of the chunk, all loads in flight at once
+        int32_t cq[W];
+        Acc vq[W];
+        int maxpl = 0;
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
             const int64_t psk = __shfl_sync(gmask, ps, k, W);
             const int plk = __shfl_sync(gmask, pl, k, W);
-            for (int q = sub; q < plk; q += W) {
-                const int32_t c = nci[psk + q];
-                const Acc v = (Acc)P[psk + q];
-                const int t = pp_lookup(key, val, c);
-                if (t >= 0) acc[t] += ak * v;
+            maxpl = plk > maxpl ? plk : maxpl;
+            cq[k] = -1;
+            vq[k] = Acc(0);
+            if (k < cnt && sub < plk) {
+                cq[k] = nci[psk + sub];
+                vq[k] = (Acc)P[psk + sub];
             }
-            __syncwarp(gmask);
+        }
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            if (k < cnt) {
+                const Acc ak = (Acc)__shfl_sync(gmask, a, k, W);
+                const int t = cq[k] >= 0 ? pp_lookup(key, val, cq[k]) : -1;
+                if (t >= 0) acc[t] += ak * vq[k];
+                __syncwarp(gmask);
+            }
+        }
+        // entries of P rows longer than W (rare on fine levels)
+        if (maxpl > W) {
+            for (int k = 0; k < cnt; ++k) {
+                const Acc ak = (Acc)__shfl_sync(gmask, a, k, W);
+                const int64_t psk = __shfl_sync(gmask, ps, k, W);
+                const int plk = __shfl_sync(gmask, pl, k, W);
+                for (int q = W + sub; q < plk; q += W) {
+                    const int t = pp_lookup(key, val, nci[psk + q]);
+                    if (t >= 0) acc[t] += ak * (Acc)P[psk + q];
+                }
+                __syncwarp(gmask);
+            }
         }
     }
     const double inv = 1.0 / aii;
@@ -1961,14 +1988,22 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
             const int gpp = grid_for(ne, (int)rows_per_block);
 #define PP(ACC, WW, OUT) SPHC_LAUNCH(k_emin_pp<ACC, WW><<<gpp, PP_WARPS * 32, 0, s>>>(ne, L.A.rp.p, L.A.ci.p, L.A.v.p, \
                                      L.Pe.rp.p, L.Pe.ci.p, L.Pe.v.p, cache.k, OUT))
-            if (o.emin_fp32) {
-                if (ppw == 8) PP(float, 8, W32.p); else if (ppw == 16) PP(float, 16, W32.p); else PP(float, 32, W32.p);
-                SPHC_LAUNCH(k_emin_rows<float><<<grid_for(ne, 128), 128, 0, s>>>(ne, L.Pe.rp.p, W32.p, L.Pe.v.p, Pnew.p,
-                                                                                 o.emin_omega, cache));
-            } else {
-                if (ppw == 8) PP(double, 8, W.p); else if (ppw == 16) PP(double, 16, W.p); else PP(double, 32, W.p);
-                SPHC_LAUNCH(k_emin_rows<double><<<grid_for(ne, 128), 128, 0, s>>>(ne, L.Pe.rp.p, W.p, L.Pe.v.p, Pnew.p,
-                                                                                  o.emin_omega, cache));
+            {
+                Section sp(prof, lev_name("emin_product", lev).c_str(), s);
+                if (o.emin_fp32) {
+                    if (ppw == 8) PP(float, 8, W32.p); else if (ppw == 16) PP(float, 16, W32.p); else PP(float, 32, W32.p);
+                } else {
+                    if (ppw == 8) PP(double, 8, W.p); else if (ppw == 16) PP(double, 16, W.p); else PP(double, 32, W.p);
+                }
+            }
+            {
+                Section sr(prof, lev_name("emin_rows", lev).c_str(), s);
+                if (o.emin_fp32)
+                    SPHC_LAUNCH(k_emin_rows<float><<<grid_for(ne, 128), 128, 0, s>>>(ne, L.Pe.rp.p, W32.p, L.Pe.v.p,
+                                                                                     Pnew.p, o.emin_omega, cache));
+                else
+                    SPHC_LAUNCH(k_emin_rows<double><<<grid_for(ne, 128), 128, 0, s>>>(ne, L.Pe.rp.p, W.p, L.Pe.v.p,
+                                                                                      Pnew.p, o.emin_omega, cache));
             }
 #undef PP
             if (hbig > 0)

@@ -1,5 +1,7 @@
 // Hierarchy data structures shared by the setup (setup.cu), the solve (solve.cu) and the C ABI.
 #pragma once
+#include <memory>
+
 #include "sphc_internal.cuh"
 
 namespace sphc {
@@ -163,6 +165,25 @@ struct Section {
     }
 };
 
+// Work vectors of the block right-hand-side solve (block.cu): NB interleaved columns per vector.
+template <typename T>
+struct BlockLevel {
+    DBuf<T> x, b, r, g, c, bp, dc;
+};
+struct BlockWork {
+    int nb = 0;
+    std::vector<BlockLevel<float>> V32;
+    std::vector<BlockLevel<double>> V64;
+    DBuf<double> X, R, Z, P, Q, Rold, B;    // CG vectors (FP64, level-0 V-cycle numbering)
+    DBuf<double> cb, cx, cgn, ccn;          // coarsest-level work (FP64)
+    DBuf<double> part, sc;                  // dot-product partials; per-column scalars
+    DBuf<int> st;                           // per-column iteration counts and status
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    long long body_launches = 0;
+    ~BlockWork();
+};
+
 // solve.cu
 struct Hierarchy {
     sphc_opts opts;
@@ -194,7 +215,9 @@ struct Hierarchy {
     double setup_ms = 0.0, solve_ms = 0.0;
     Profiler prof;
     DBuf<float> mlp;                 // MLP parameters on the device (learned warm start)
+    std::unique_ptr<BlockWork> blk;  // block right-hand-side work (allocated by the first block solve)
     ~Hierarchy() {
+        blk.reset();
         if (cg_exec) cudaGraphExecDestroy(cg_exec);
         if (cg_graph) cudaGraphDestroy(cg_graph);
         if (cap_stream) cudaStreamDestroy(cap_stream);
@@ -230,6 +253,9 @@ int apply_vcycle(Hierarchy& H, const double* r, double* z, cudaStream_t s);
 int apply_vcycle_user(Hierarchy& H, const double* r, double* z, cudaStream_t s);
 int pcg_solve(Hierarchy& H, const double* b, double* x, double tol, cudaStream_t s, int* iters, double* relres);
 int capture_cg(Hierarchy& H, cudaStream_t s);
+// block.cu: nrhs <= 16 right-hand sides (device arrays, caller layout nrhs x n_e) solved together
+int pcg_block(Hierarchy& H, const double* b, double* x, int nrhs, double tol, cudaStream_t s, int* iters,
+              double* relres);
 int autotune_vcycle(Hierarchy& H, cudaStream_t s);
 
 }  // namespace sphc

@@ -57,7 +57,8 @@ def test_config2_fp64_hierarchy_matches_oracle(kuhn48):
     for l in range(o.nlevels):
         np.testing.assert_array_equal(h.export(l, "col_e"), o.ivec(l, "col_e"))
         np.testing.assert_array_equal(h.export(l, "col_n"), o.ivec(l, "col_n"))
-        assert_csr_close(h.export(l, "A"), o.matrix(l, "A"), f"L{l} A", 1e-10)
+        # level 0 is the input; coarse operators P_e^T A P_e inherit the noise of P_e
+        assert_csr_close(h.export(l, "A"), o.matrix(l, "A"), f"L{l} A", 1e-10 if l == 0 else tol)
         if not o.sizes(l)["has_transfer"]:
             continue
         np.testing.assert_array_equal(h.export(l, "agg"), o.ivec(l, "agg"))

@@ -41,8 +41,9 @@ def test_zero_rhs():
 
 
 def test_multiple_rhs():
+    # one right-hand side after another (the block solve has its own tests)
     p = meshgen.generate(meshgen.workload("kuhn8")[0])
-    h = gpu_setup(p)
+    h = gpu_setup(p, block_rhs=0)
     B = meshgen.rhs(6, p.n_edges, nrhs=3)
     X = np.zeros_like(B)
     rc, it, rr = h.solve(B, X, nrhs=3)

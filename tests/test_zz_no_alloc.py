@@ -24,7 +24,7 @@ def test_noalloc_relres_matches_solve():
     import paper_2506_08284_gb300 as pkg
 
     p = meshgen.generate(meshgen.workload("kuhn8")[0])
-    h = gpu_setup(p, vcycle_fp32=0)
+    h = gpu_setup(p, vcycle_fp32=0, block_rhs=0)
     nrhs = 3
     B = torch.from_numpy(meshgen.rhs(21, p.n_edges, nrhs=nrhs)).cuda()
     X = torch.zeros_like(B)
