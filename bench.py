@@ -48,6 +48,8 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--no-block", action="store_true", help="skip the block-of-16-right-hand-sides leg")
+    ap.add_argument("--block-rhs", type=int, default=16)
     ap.add_argument("--no-graph", action="store_true",
                     help="run CG with a host loop instead of the CUDA graph (same kernels; for profilers "
                          "that cannot see kernels inside graphs with conditional nodes)")
@@ -304,6 +306,37 @@ def main():
                                  "solve_ms": c_st["solve_ms"]}
         comparators["speedup_vs_fp64_plain"] = comparators["fp64_plain"]["s"] / sec_per_system
 
+    # block of right-hand sides on one hierarchy (config 3: seeds 6..21): one CG per column, every
+    # operator row read once per block; setup excluded, solve timed with CUDA events
+    block = None
+    if not args.no_block and args.block_rhs >= 2:
+        nb = args.block_rhs
+        Bd = dev(meshgen.rhs(seed, p.n_edges, nrhs=nb))
+        Xd = torch.zeros_like(Bd)
+        ob = make_opts(pkg, "headline", weights, 0, not args.no_graph)
+        hb = pkg.sphc.setup(A, D, coords, sig, ob, stream)
+        hb.solve(Bd, Xd, tol=args.tol, nrhs=nb, stream=stream)          # warm-up (allocates the block work)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        brc, bit, brr = hb.solve(Bd, Xd, tol=args.tol, nrhs=nb, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        bms = e0.elapsed_time(e1)
+        bst = hb.stats()
+        # the single-right-hand-side solve on the same hierarchy, for the per-RHS comparison
+        x1 = torch.zeros_like(bd)
+        e0.record(stream)
+        hb.solve(bd, x1, tol=args.tol, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        one_ms = e0.elapsed_time(e1)
+        hb.destroy()
+        block = {"nrhs": nb, "status": brc, "solve_ms": bms, "ms_per_rhs": bms / nb, "single_rhs_solve_ms": one_ms,
+                 "speedup_per_rhs": one_ms / (bms / nb), "iters": bit, "max_relres": max(brr),
+                 "setup_ms": bst["setup_ms"]}
+        del Bd, Xd
+
     # end-to-end: the same call with pinned host buffers (copies inside the timed region)
     e2e = None
     if not args.no_e2e:
@@ -360,6 +393,7 @@ def main():
             "setup_ms": st["setup_ms"], "solve_ms": st["solve_ms"], "levels": st["n_levels"],
             "operator_complexity": st["operator_complexity"], "gpu_launches": int(launches),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "comparators": comparators,
+            "speedup_vs_fp64_plain": comparators.get("speedup_vs_fp64_plain"), "rhs_block": block,
             "profile": {k: {kk: round(vv, 4) if isinstance(vv, float) else vv for kk, vv in v.items()}
                         for k, v in prof.items()},
             "level_edges": [li["n_edges"] for li in info],
