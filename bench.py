@@ -34,7 +34,108 @@ WORKLOAD_TEXT = {
               "else 1e-3, RHS seed 3",
     "kuhn8": "8^3-cell Kuhn-tet unit cube, 3,032 unknowns, no jitter, sigma 1, RHS seed 1",
 }
+WORKLOAD_TEXT["batch64"] = ("64 independent Kuhn-tet systems, cells per axis n_s uniform in 12..64 (splitmix64 seed 200+s), "
+                            "+-0.2h jitter (seed 200+s), per-tet log10 sigma ~ N(0, 2^2) clipped to [-6, 2] "
+                            "(seed 300+s), 4 RHS uniform[-1,1] each (seeds 400+4s..403+4s)")
 CPU_SAMPLE = "kuhn32"   # oracle sample for the CPU baseline (about 10 s of single-threaded work)
+
+
+def batch64_specs():
+    """The 64 systems of the batched workload: (MeshSpec, first RHS seed) per system."""
+    import meshgen
+    M = (1 << 64) - 1
+
+    def splitmix64(seed, counter):
+        z = (seed + (counter + 1) * 0x9E3779B97F4A7C15) & M
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M
+        return z ^ (z >> 31)
+
+    out = []
+    for sidx in range(64):
+        n = 12 + splitmix64(200 + sidx, 0) % 53
+        out.append((meshgen.MeshSpec(int(n), jitter=0.2, seed_jitter=200 + sidx, sigma="lognormal", sigma_in=2.0,
+                                     seed_sigma=300 + sidx), 400 + 4 * sidx))
+    return out
+
+
+def run_batch64(args, rank, world, local):
+    """Config 5: all 64 systems set up (concurrently, host threads on their own streams) and solved
+    for 4 right-hand sides each through one CUDA graph per right-hand side whose branches run every
+    system's whole CG.  One step = sphc_setup_batched + sphc_solve_batched (4 RHS) +
+    sphc_batch_destroy, inputs resident on the device.  value = systems per second (all ranks)."""
+    import numpy as np
+    import torch
+
+    import meshgen
+    import paper_2506_08284_gb300 as pkg
+    from paper_2506_08284_gb300 import learned
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    weights = learned.load_weights() if os.path.exists(learned.WEIGHTS) else None
+    dev = lambda a: torch.from_numpy(a).cuda()
+    systems, bs, xs, n_unknowns = [], [], [], 0
+    for spec, rseed in batch64_specs():
+        p = meshgen.generate(spec, nthreads=min(os.cpu_count() or 1, 32))
+        systems.append(((p.n_edges, p.n_edges, dev(p.A_rowptr), dev(p.A_col), dev(p.A_val)),
+                        (p.n_edges, p.n_nodes, dev(p.D_rowptr), dev(p.D_col), dev(p.D_val)), dev(p.coords),
+                        dev(p.sigma_edge)))
+        bs.append(dev(meshgen.rhs(rseed, p.n_edges, nrhs=4)))
+        xs.append(torch.zeros_like(bs[-1]))
+        n_unknowns += p.n_edges
+    stream = torch.cuda.current_stream()
+
+    def step(opts):
+        B = pkg.sphc.setup_batched(systems, opts, stream)
+        rc, it, rr = B.solve(bs, xs, nrhs=4, stream=stream)
+        B.destroy()
+        return rc, it, rr
+
+    def timed(opts, steps, warmup):
+        for _ in range(warmup):
+            step(opts)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        launches0 = pkg.sphc.launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = [step(opts) for _ in range(steps)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
+        return ms, pkg.sphc.launch_count() - launches0, res[-1]
+
+    clk = ClockSampler(local)
+    head = make_opts(pkg, "headline", weights, 0, True)
+    clk.start()
+    ms, launches, (rc, it, rr) = timed(head, args.steps, args.warmup)
+    clocks = clk.stop()
+    fp64_ms, _, (rc64, it64, rr64) = timed(make_opts(pkg, "fp64_plain", weights, 0, True), max(1, min(args.steps, 2)), 1)
+    fp64_steps = max(1, min(args.steps, 2))
+    value = 64 * args.steps * world / (ms / 1e3)
+    if rank == 0:
+        line = {"metric": "systems/s, setup+solve to 1e-8 residual (batched uneven systems, 4 RHS each)",
+                "value": value, "unit": "systems/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64 CG / f32 V-cycle", "data": "synthetic",
+                "config": {"workload": f"batch64: {WORKLOAD_TEXT['batch64']}", "unknowns_total": n_unknowns,
+                           "solver": "FP32 V-cycle + learned warm start in FP64 CG, one graph per RHS",
+                           "l2": "inputs exceed the 129 MB L2; no flush", "parallelism": f"replicas x{world}"},
+                "status": rc, "iters_max": int(np.max(it)), "iters_mean": float(np.mean(it)),
+                "relres_max": float(np.max(rr)), "gpu_launches": int(launches), "clocks": clocks,
+                "comparators": {"fp64_plain": {"systems_per_s": 64 * fp64_steps * world / (fp64_ms / 1e3),
+                                               "status": rc64, "iters_max": int(np.max(it64))},
+                                "speedup_vs_fp64_plain": (64 * args.steps / (ms / 1e3)) /
+                                                         (64 * fp64_steps / (fp64_ms / 1e3))}}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
 
 
 def parse_args():
@@ -229,6 +330,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.workload == "batch64":
+        run_batch64(args, rank, world, local)
         return
 
     import numpy as np

@@ -2,7 +2,10 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <algorithm>
+#include <atomic>
 #include <new>
+#include <thread>
 #include <string>
 #include <vector>
 
@@ -581,6 +584,9 @@ struct sphc_batch {
     cudaStream_t cs = nullptr;
     std::vector<cudaStream_t> bs;
     std::vector<cudaEvent_t> ev;
+    // streams the systems were set up on (their buffers were allocated stream-ordered there, so
+    // the streams live as long as the handles)
+    std::vector<cudaStream_t> ws;
 };
 
 static void batch_free(sphc_batch* B) {
@@ -591,6 +597,7 @@ static void batch_free(sphc_batch* B) {
     for (auto st : B->bs) cudaStreamDestroy(st);
     if (B->cs) cudaStreamDestroy(B->cs);
     for (auto h : B->hs) sphc_destroy(h);
+    for (auto st : B->ws) cudaStreamDestroy(st);
     delete B;
 }
 
@@ -636,18 +643,53 @@ int sphc_setup_batched(int nsys, const sphc_csr* A_e, const sphc_csr* D_h, const
     *out = nullptr;
     sphc_batch* B = new (std::nothrow) sphc_batch();
     if (!B) return SPHC_ENOMEM;
-    for (int k = 0; k < nsys; ++k) {
-        sphc_handle* h = nullptr;
-        int rc = sphc_setup(&A_e[k], &D_h[k], coords ? coords[k] : nullptr, sigma_edge ? sigma_edge[k] : nullptr, opts,
-                            stream, &h);
-        if (rc != SPHC_OK) {
-            std::string msg = last_error();
+    // The systems are set up concurrently by up to BATCH_WORKERS host threads, each on its own
+    // stream, largest systems first: a small system's setup is a chain of short kernels and host
+    // synchronisations that leaves most of the GPU idle.  Inputs the caller produced on `stream`
+    // are complete before any worker reads them.
+    constexpr int BATCH_WORKERS = 8;
+    SPHC_CK(cudaStreamSynchronize((cudaStream_t)stream));
+    int dev = 0;
+    SPHC_CK(cudaGetDevice(&dev));
+    const int nw = nsys < BATCH_WORKERS ? nsys : BATCH_WORKERS;
+    B->hs.assign(nsys, nullptr);
+    B->ws.assign(nw, nullptr);
+    for (int w = 0; w < nw; ++w) {
+        cudaError_t e = cudaStreamCreateWithFlags(&B->ws[w], cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
             batch_free(B);
-            set_error("system %d: %s", k, msg.c_str());
+            set_error("sphc_setup_batched: cudaStreamCreate: %s", cudaGetErrorString(e));
+            return SPHC_ECUDA;
+        }
+    }
+    std::vector<int> order(nsys);
+    for (int k = 0; k < nsys; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return A_e[a].nrows > A_e[b].nrows; });
+    std::vector<int> rcs(nsys, SPHC_OK);
+    std::vector<std::string> msgs(nsys);
+    std::atomic<int> next{0};
+    auto work = [&](int w) {
+        cudaSetDevice(dev);
+        for (;;) {
+            const int q = next.fetch_add(1);
+            if (q >= nsys) break;
+            const int k = order[q];
+            rcs[k] = sphc_setup(&A_e[k], &D_h[k], coords ? coords[k] : nullptr, sigma_edge ? sigma_edge[k] : nullptr,
+                                opts, B->ws[w], &B->hs[k]);
+            if (rcs[k] != SPHC_OK) msgs[k] = last_error();
+        }
+    };
+    std::vector<std::thread> threads;
+    for (int w = 1; w < nw; ++w) threads.emplace_back(work, w);
+    work(0);
+    for (auto& t : threads) t.join();
+    for (int k = 0; k < nsys; ++k)
+        if (rcs[k] != SPHC_OK) {
+            const int rc = rcs[k];
+            batch_free(B);
+            set_error("system %d: %s", k, msgs[k].c_str());
             return rc;
         }
-        B->hs.push_back(h);
-    }
     int rc = batch_capture(B);
     if (rc != SPHC_OK) {
         batch_free(B);
