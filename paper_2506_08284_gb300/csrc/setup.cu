@@ -1373,117 +1373,49 @@ k_p0_rows(int64_t ne, const int64_t* __restrict__ trp, const int32_t* __restrict
 }
 
 // Masked product of eq. (9) for every row that the thread-per-row projection handles:
-// w_{i,t} = (A P)_{i, N_i(t)} / a_ii.  A group of W lanes owns row i.  The row's pattern columns
-// (at most 32) go into a 64-slot open-addressing table in shared memory (column -> t).  The group
-// walks A's row entry by entry, reads P row f coalesced across its lanes and adds a_if P_{f,c}
-// into the accumulator of the row's entry with column c, if there is one.  Within one f the
-// columns are distinct, so no two lanes touch one accumulator; the entries f follow A's row
-// order, so every sum is taken in a fixed order.  Acc is double, or float for the FP32
-// accumulation of opts.emin_fp32 (the projection that follows stays FP64).
-constexpr int PP_WARPS = 8;
-constexpr int PP_SLOTS = 64;
-__device__ __forceinline__ uint32_t pp_hash(int32_t c) { return ((uint32_t)c * 0x9E3779B1u) >> 26; }
-__device__ __forceinline__ int pp_lookup(const int32_t* key, const int8_t* val, int32_t c) {
-    uint32_t s = pp_hash(c);
-    // at most 32 keys in 64 slots: an empty slot ends every probe well before the bound
-    for (int q = 0; q < PP_SLOTS; ++q) {
-        const int32_t k = key[s];
-        if (k == c) return val[s];
-        if (k < 0) return -1;
-        s = (s + 1) & (PP_SLOTS - 1);
-    }
-    return -1;
-}
-template <typename Acc, int W>
-__global__ void __launch_bounds__(PP_WARPS * 32)
+// w_{i,t} = (A P)_{i, N_i(t)} / a_ii, one thread per row.  The pattern columns of row i and the
+// columns of every P row f are sorted, so each P row is merged against the pattern: one pass over
+// P row f with a cursor into N_i, an FMA on every match.  The accumulators live in shared memory,
+// entry t of the block's thread q at [t][q] (a warp's threads touch consecutive words).  The
+// entries f follow A's row order, so every sum is taken in a fixed order.  Acc is double, or
+// float for the FP32 accumulation of opts.emin_fp32 (the projection that follows stays FP64).
+constexpr int PP_THREADS = 128;
+template <typename Acc>
+__global__ void __launch_bounds__(PP_THREADS)
 k_emin_pp(int64_t ne, const int64_t* __restrict__ arp, const int32_t* __restrict__ aci, const double* __restrict__ av,
           const int64_t* __restrict__ nrp, const int32_t* __restrict__ nci, const double* __restrict__ P,
           const int8_t* __restrict__ ck, Acc* __restrict__ w) {
-    constexpr int R = 32 / W;                          // rows per warp
-    __shared__ int32_t s_key[PP_WARPS * R][PP_SLOTS];
-    __shared__ int8_t s_val[PP_WARPS * R][PP_SLOTS];
-    __shared__ Acc s_acc[PP_WARPS * R][32];
-    const int lane = threadIdx.x & 31, g = lane / W, sub = lane % W;
-    const int slot = (threadIdx.x >> 5) * R + g;
-    const unsigned gmask = W == 32 ? 0xffffffffu : (((1u << W) - 1u) << (g * W));
-    const int64_t i = ((int64_t)blockIdx.x * PP_WARPS + (threadIdx.x >> 5)) * R + g;
-    if (i >= ne || ck[i] < 0) return;                  // whole group: no row, or a row k_emin handles
+    __shared__ Acc s_acc[TNP][PP_THREADS];
+    const int q = threadIdx.x;
+    const int64_t i = (int64_t)blockIdx.x * PP_THREADS + q;
+    if (i >= ne || ck[i] < 0) return;                 // no row, or a row k_emin handles
     const int64_t n0 = nrp[i];
     const int np = (int)(nrp[i + 1] - n0);
-    if (np <= 0 || np > 32) return;
-    int32_t* key = s_key[slot];
-    int8_t* val = s_val[slot];
-    Acc* acc = s_acc[slot];
-    for (int q = sub; q < PP_SLOTS; q += W) key[q] = -1;
-    for (int q = sub; q < 32; q += W) acc[q] = Acc(0);
-    __syncwarp(gmask);
-    for (int t = sub; t < np; t += W) {
-        const int32_t c = nci[n0 + t];
-        uint32_t h = pp_hash(c);
-        for (int q = 0; q < PP_SLOTS; ++q) {           // keys are distinct; a free slot exists
-            if (atomicCAS(&key[h], -1, c) == -1) { val[h] = (int8_t)t; break; }
-            h = (h + 1) & (PP_SLOTS - 1);
-        }
-    }
-    __syncwarp(gmask);
+    if (np <= 0 || np > TNP) return;
+    for (int t = 0; t < np; ++t) s_acc[t][q] = Acc(0);
+    const int32_t* key = nci + n0;
     const int64_t a0 = arp[i], a1 = arp[i + 1];
     double aii = 1.0;
-    for (int64_t base = a0; base < a1; base += W) {
-        const int64_t ka = base + sub;
-        int32_t f = -1;
-        double a = 0.0;
-        int64_t ps = 0;
-        int pl = 0;
-        if (ka < a1) {
-            f = aci[ka];
-            a = av[ka];
-            ps = nrp[f];
-            pl = (int)(nrp[f + 1] - ps);
-        }
-        const unsigned dm = (__ballot_sync(gmask, ka < a1 && f == (int32_t)i) & gmask) >> (g * W);
-        if (dm) aii = __shfl_sync(gmask, a, __ffs(dm) - 1, W);
-        const int cnt = (int)(a1 - base < W ? a1 - base : W);
-        // the first W entries of every P row of the chunk, all loads in flight at once
-        int32_t cq[W];
-        Acc vq[W];
-        int maxpl = 0;
-#pragma unroll
-        for (int k = 0; k < W; ++k) {
-            const int64_t psk = __shfl_sync(gmask, ps, k, W);
-            const int plk = __shfl_sync(gmask, pl, k, W);
-            maxpl = plk > maxpl ? plk : maxpl;
-            cq[k] = -1;
-            vq[k] = Acc(0);
-            if (k < cnt && sub < plk) {
-                cq[k] = nci[psk + sub];
-                vq[k] = (Acc)P[psk + sub];
+    for (int64_t ka = a0; ka < a1; ++ka) {
+        const int32_t f = aci[ka];
+        const double a = av[ka];
+        if (f == (int32_t)i) aii = a;
+        const Acc af = (Acc)a;
+        const int64_t pe = nrp[f + 1];
+        int t = 0;
+        int32_t kt = key[0];
+        for (int64_t e = nrp[f]; e < pe; ++e) {
+            const int32_t c = nci[e];
+            while (kt < c) {                          // advance the pattern cursor
+                if (++t >= np) break;
+                kt = key[t];
             }
-        }
-#pragma unroll
-        for (int k = 0; k < W; ++k) {
-            if (k < cnt) {
-                const Acc ak = (Acc)__shfl_sync(gmask, a, k, W);
-                const int t = cq[k] >= 0 ? pp_lookup(key, val, cq[k]) : -1;
-                if (t >= 0) acc[t] += ak * vq[k];
-                __syncwarp(gmask);
-            }
-        }
-        // entries of P rows longer than W (rare on fine levels)
-        if (maxpl > W) {
-            for (int k = 0; k < cnt; ++k) {
-                const Acc ak = (Acc)__shfl_sync(gmask, a, k, W);
-                const int64_t psk = __shfl_sync(gmask, ps, k, W);
-                const int plk = __shfl_sync(gmask, pl, k, W);
-                for (int q = W + sub; q < plk; q += W) {
-                    const int t = pp_lookup(key, val, nci[psk + q]);
-                    if (t >= 0) acc[t] += ak * (Acc)P[psk + q];
-                }
-                __syncwarp(gmask);
-            }
+            if (t >= np) break;                       // the rest of P row f lies past the pattern
+            if (kt == c) s_acc[t][q] += af * (Acc)P[e];
         }
     }
     const double inv = 1.0 / aii;
-    for (int t = sub; t < np; t += W) w[n0 + t] = (Acc)((double)acc[t] * inv);
+    for (int t = 0; t < np; ++t) w[n0 + t] = (Acc)((double)s_acc[t][q] * inv);
 }
 
 // projection and update of eq. (9) for every small row: dp = w - G~ (G~^T G~)^-1 G~^T w,
@@ -1978,23 +1910,18 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
         if (o.emin_fp32) SPHC_TRY(W32.alloc(nnzN, s));
         else SPHC_TRY(W.alloc(nnzN, s));
     }
-    // lanes per row of the product: about one P row per pass of the group
-    const double mean_np = ne > 0 ? (double)nnzN / (double)ne : 0.0;
-    const int ppw = mean_np <= 8.0 ? 8 : (mean_np <= 16.0 ? 16 : 32);
     for (int it = 0; it < emin_iters; ++it) {
         if (tid >= 0) prof->begin(tid, s);
         if (ne > 0) {
-            const int64_t rows_per_block = PP_WARPS * (32 / ppw);
-            const int gpp = grid_for(ne, (int)rows_per_block);
-#define PP(ACC, WW, OUT) SPHC_LAUNCH(k_emin_pp<ACC, WW><<<gpp, PP_WARPS * 32, 0, s>>>(ne, L.A.rp.p, L.A.ci.p, L.A.v.p, \
-                                     L.Pe.rp.p, L.Pe.ci.p, L.Pe.v.p, cache.k, OUT))
+            const int gpp = grid_for(ne, PP_THREADS);
             {
                 Section sp(prof, lev_name("emin_product", lev).c_str(), s);
-                if (o.emin_fp32) {
-                    if (ppw == 8) PP(float, 8, W32.p); else if (ppw == 16) PP(float, 16, W32.p); else PP(float, 32, W32.p);
-                } else {
-                    if (ppw == 8) PP(double, 8, W.p); else if (ppw == 16) PP(double, 16, W.p); else PP(double, 32, W.p);
-                }
+                if (o.emin_fp32)
+                    SPHC_LAUNCH(k_emin_pp<float><<<gpp, PP_THREADS, 0, s>>>(ne, L.A.rp.p, L.A.ci.p, L.A.v.p, L.Pe.rp.p,
+                                                                           L.Pe.ci.p, L.Pe.v.p, cache.k, W32.p));
+                else
+                    SPHC_LAUNCH(k_emin_pp<double><<<gpp, PP_THREADS, 0, s>>>(ne, L.A.rp.p, L.A.ci.p, L.A.v.p, L.Pe.rp.p,
+                                                                            L.Pe.ci.p, L.Pe.v.p, cache.k, W.p));
             }
             {
                 Section sr(prof, lev_name("emin_rows", lev).c_str(), s);
@@ -2005,7 +1932,6 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
                     SPHC_LAUNCH(k_emin_rows<double><<<grid_for(ne, 128), 128, 0, s>>>(ne, L.Pe.rp.p, W.p, L.Pe.v.p,
                                                                                       Pnew.p, o.emin_omega, cache));
             }
-#undef PP
             if (hbig > 0)
                 SPHC_LAUNCH(k_emin<<<grid_for(hbig, LOC_WARPS), LOC_WARPS * 32, sm, s>>>(
                     hbig, big.p, L.A.rp.p, L.A.ci.p, L.A.v.p, L.T.rp.p, L.T.ci.p, L.T.v.p, L.Pe.rp.p, L.Pe.ci.p,
