@@ -313,14 +313,15 @@ def make_opts(pkg, variant, weights, profile, graph=True):
 
 
 def _make_opts(pkg, variant, weights, profile):
-    """headline: FP32 V-cycle + learned warm start (one energy-minimisation step after it);
-    fp32_plain: FP32 V-cycle, plain least-norm P0 + one step; fp64_plain: the same in FP64."""
+    """headline: FP32 V-cycle + learned warm start (one energy-minimisation step after it, its masked
+    product accumulated in FP32); fp32_plain: FP32 V-cycle, plain least-norm P0 + one step (FP32
+    product); fp64_plain: everything in FP64."""
     if variant == "headline" and weights is not None:
-        return pkg.sphc.default_opts(vcycle_fp32=1, learned=1, learned_emin_iters=1, mlp_params=weights,
+        return pkg.sphc.default_opts(vcycle_fp32=1, emin_fp32=1, learned=1, learned_emin_iters=1, mlp_params=weights,
                                      profile=profile)
     if variant in ("headline", "fp32_plain"):
-        return pkg.sphc.default_opts(vcycle_fp32=1, profile=profile)
-    return pkg.sphc.default_opts(vcycle_fp32=0, profile=profile)
+        return pkg.sphc.default_opts(vcycle_fp32=1, emin_fp32=1, profile=profile)
+    return pkg.sphc.default_opts(vcycle_fp32=0, emin_fp32=0, profile=profile)
 
 
 def main():
