@@ -1373,49 +1373,92 @@ k_p0_rows(int64_t ne, const int64_t* __restrict__ trp, const int32_t* __restrict
 }
 
 // Masked product of eq. (9) for every row that the thread-per-row projection handles:
-// w_{i,t} = (A P)_{i, N_i(t)} / a_ii, one thread per row.  The pattern columns of row i and the
-// columns of every P row f are sorted, so each P row is merged against the pattern: one pass over
-// P row f with a cursor into N_i, an FMA on every match.  The accumulators live in shared memory,
-// entry t of the block's thread q at [t][q] (a warp's threads touch consecutive words).  The
-// entries f follow A's row order, so every sum is taken in a fixed order.  Acc is double, or
-// float for the FP32 accumulation of opts.emin_fp32 (the projection that follows stays FP64).
-constexpr int PP_THREADS = 128;
+// w_{i,t} = (A P)_{i, N_i(t)} / a_ii, one warp per row.  Lane t owns pattern entry t (column
+// key_t, accumulator in a register).  The warp walks A's row; for each entry f it loads P row f
+// across its lanes (coalesced; the next row is already in flight), and every lane finds its key
+// among the row's sorted columns by a branchless binary search over the lanes (five shuffles).
+// One FMA per lane and entry f, in A's row order: a fixed summation order, no shared memory, so
+// the L1 cache holds the P rows that neighbouring rows share.  Acc is double, or float for the
+// FP32 accumulation of opts.emin_fp32 (the projection that follows stays FP64).
+constexpr int PP_WARPS = 4;
+struct PRow {
+    int32_t c;      // column of this lane's entry (INT_MAX past the row's end)
+    double v;
+};
+__device__ __forceinline__ PRow pp_load(const int32_t* __restrict__ nci, const double* __restrict__ P, int64_t ps,
+                                        int len, int lane) {
+    PRow r;
+    r.c = 0x7fffffff;
+    r.v = 0.0;
+    if (lane < len) {
+        r.c = nci[ps + lane];
+        r.v = P[ps + lane];
+    }
+    return r;
+}
 template <typename Acc>
-__global__ void __launch_bounds__(PP_THREADS)
+__global__ void __launch_bounds__(PP_WARPS * 32)
 k_emin_pp(int64_t ne, const int64_t* __restrict__ arp, const int32_t* __restrict__ aci, const double* __restrict__ av,
           const int64_t* __restrict__ nrp, const int32_t* __restrict__ nci, const double* __restrict__ P,
           const int8_t* __restrict__ ck, Acc* __restrict__ w) {
-    __shared__ Acc s_acc[TNP][PP_THREADS];
-    const int q = threadIdx.x;
-    const int64_t i = (int64_t)blockIdx.x * PP_THREADS + q;
-    if (i >= ne || ck[i] < 0) return;                 // no row, or a row k_emin handles
+    const int lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * PP_WARPS + (threadIdx.x >> 5);
+    if (i >= ne || ck[i] < 0) return;                  // whole warp: no row, or a row k_emin handles
     const int64_t n0 = nrp[i];
     const int np = (int)(nrp[i + 1] - n0);
-    if (np <= 0 || np > TNP) return;
-    for (int t = 0; t < np; ++t) s_acc[t][q] = Acc(0);
-    const int32_t* key = nci + n0;
+    if (np <= 0 || np > 32) return;
+    const int32_t key = lane < np ? nci[n0 + lane] : -1;
+    Acc acc = Acc(0);
     const int64_t a0 = arp[i], a1 = arp[i + 1];
     double aii = 1.0;
-    for (int64_t ka = a0; ka < a1; ++ka) {
-        const int32_t f = aci[ka];
-        const double a = av[ka];
-        if (f == (int32_t)i) aii = a;
-        const Acc af = (Acc)a;
-        const int64_t pe = nrp[f + 1];
-        int t = 0;
-        int32_t kt = key[0];
-        for (int64_t e = nrp[f]; e < pe; ++e) {
-            const int32_t c = nci[e];
-            while (kt < c) {                          // advance the pattern cursor
-                if (++t >= np) break;
-                kt = key[t];
+    for (int64_t base = a0; base < a1; base += 32) {
+        // this chunk's A entries: lane k holds entry base + k and the extent of P row f
+        const int cnt = (int)(a1 - base < 32 ? a1 - base : 32);
+        int32_t f = 0;
+        double a = 0.0;
+        int64_t ps = 0;
+        int len = 0;
+        if (lane < cnt) {
+            f = aci[base + lane];
+            a = av[base + lane];
+            ps = nrp[f];
+            len = (int)(nrp[f + 1] - ps);
+        }
+        const unsigned dm = __ballot_sync(0xffffffffu, lane < cnt && f == (int32_t)i);
+        if (dm) aii = __shfl_sync(0xffffffffu, a, __ffs(dm) - 1);
+        int64_t psk = __shfl_sync(0xffffffffu, ps, 0);
+        int lenk = __shfl_sync(0xffffffffu, len, 0);
+        PRow cur = pp_load(nci, P, psk, lenk, lane);
+        for (int k = 0; k < cnt; ++k) {
+            const Acc ak = (Acc)__shfl_sync(0xffffffffu, a, k);
+            int64_t psn = 0;
+            int lenn = 0;
+            if (k + 1 < cnt) {                             // next P row in flight
+                psn = __shfl_sync(0xffffffffu, ps, k + 1);
+                lenn = __shfl_sync(0xffffffffu, len, k + 1);
             }
-            if (t >= np) break;                       // the rest of P row f lies past the pattern
-            if (kt == c) s_acc[t][q] += af * (Acc)P[e];
+            const PRow nxt = pp_load(nci, P, psn, lenn, lane);
+            for (int off = 0;;) {
+                // last lane q with c_q <= key (c sorted; lanes past the row hold INT_MAX)
+                int pos = 0;
+#pragma unroll
+                for (int half = 16; half > 0; half >>= 1) {
+                    const int32_t cm = __shfl_sync(0xffffffffu, cur.c, pos + half);
+                    pos = cm <= key ? pos + half : pos;
+                }
+                const int32_t cq = __shfl_sync(0xffffffffu, cur.c, pos);
+                const double vq = __shfl_sync(0xffffffffu, cur.v, pos);
+                if (lane < np && cq == key) acc += ak * (Acc)vq;
+                off += 32;
+                if (off >= lenk) break;                    // P rows longer than 32: next 32 entries
+                cur = pp_load(nci, P, psk + off, lenk - off, lane);
+            }
+            cur = nxt;
+            psk = psn;
+            lenk = lenn;
         }
     }
-    const double inv = 1.0 / aii;
-    for (int t = 0; t < np; ++t) w[n0 + t] = (Acc)((double)s_acc[t][q] * inv);
+    if (lane < np) w[n0 + lane] = (Acc)((double)acc / aii);
 }
 
 // projection and update of eq. (9) for every small row: dp = w - G~ (G~^T G~)^-1 G~^T w,
@@ -1913,14 +1956,14 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
     for (int it = 0; it < emin_iters; ++it) {
         if (tid >= 0) prof->begin(tid, s);
         if (ne > 0) {
-            const int gpp = grid_for(ne, PP_THREADS);
+            const int gpp = grid_for(ne, PP_WARPS);
             {
                 Section sp(prof, lev_name("emin_product", lev).c_str(), s);
                 if (o.emin_fp32)
-                    SPHC_LAUNCH(k_emin_pp<float><<<gpp, PP_THREADS, 0, s>>>(ne, L.A.rp.p, L.A.ci.p, L.A.v.p, L.Pe.rp.p,
+                    SPHC_LAUNCH(k_emin_pp<float><<<gpp, PP_WARPS * 32, 0, s>>>(ne, L.A.rp.p, L.A.ci.p, L.A.v.p, L.Pe.rp.p,
                                                                            L.Pe.ci.p, L.Pe.v.p, cache.k, W32.p));
                 else
-                    SPHC_LAUNCH(k_emin_pp<double><<<gpp, PP_THREADS, 0, s>>>(ne, L.A.rp.p, L.A.ci.p, L.A.v.p, L.Pe.rp.p,
+                    SPHC_LAUNCH(k_emin_pp<double><<<gpp, PP_WARPS * 32, 0, s>>>(ne, L.A.rp.p, L.A.ci.p, L.A.v.p, L.Pe.rp.p,
                                                                             L.Pe.ci.p, L.Pe.v.p, cache.k, W.p));
             }
             {
