@@ -1373,29 +1373,15 @@ k_p0_rows(int64_t ne, const int64_t* __restrict__ trp, const int32_t* __restrict
 }
 
 // Masked product of eq. (9) for every row that the thread-per-row projection handles:
-// w_{i,t} = (A P)_{i, N_i(t)} / a_ii, one warp per row.  Lane t owns pattern entry t (column
-// key_t, accumulator in a register).  The warp walks A's row; for each entry f it loads P row f
-// across its lanes (coalesced; the next row is already in flight), and every lane finds its key
-// among the row's sorted columns by a branchless binary search over the lanes (five shuffles).
-// One FMA per lane and entry f, in A's row order: a fixed summation order, no shared memory, so
-// the L1 cache holds the P rows that neighbouring rows share.  Acc is double, or float for the
-// FP32 accumulation of opts.emin_fp32 (the projection that follows stays FP64).
+// w_{i,t} = (A P)_{i, N_i(t)} / a_ii, one warp per row.  L lanes share pattern entry t (L the
+// largest power of two with np L <= 32) and split A's row: each lane takes every L-th entry f and
+// finds column N_i(t) in the sorted P row f by binary search.  A lane runs PP_ILP searches at
+// once, branch-free with a fixed step count for rows of up to 32 entries, so their loads overlap
+// instead of forming one long chain; a lane sums its matches in A's row order and the L lanes of
+// an entry are added in a fixed pattern, so the result does not depend on scheduling.  Acc is
+// double, or float for the FP32 accumulation of opts.emin_fp32 (the projection stays FP64).
 constexpr int PP_WARPS = 4;
-struct PRow {
-    int32_t c;      // column of this lane's entry (INT_MAX past the row's end)
-    double v;
-};
-__device__ __forceinline__ PRow pp_load(const int32_t* __restrict__ nci, const double* __restrict__ P, int64_t ps,
-                                        int len, int lane) {
-    PRow r;
-    r.c = 0x7fffffff;
-    r.v = 0.0;
-    if (lane < len) {
-        r.c = nci[ps + lane];
-        r.v = P[ps + lane];
-    }
-    return r;
-}
+constexpr int PP_ILP = 4;
 template <typename Acc>
 __global__ void __launch_bounds__(PP_WARPS * 32)
 k_emin_pp(int64_t ne, const int64_t* __restrict__ arp, const int32_t* __restrict__ aci, const double* __restrict__ av,
@@ -1407,58 +1393,68 @@ k_emin_pp(int64_t ne, const int64_t* __restrict__ arp, const int32_t* __restrict
     const int64_t n0 = nrp[i];
     const int np = (int)(nrp[i + 1] - n0);
     if (np <= 0 || np > 32) return;
-    const int32_t key = lane < np ? nci[n0 + lane] : -1;
-    Acc acc = Acc(0);
+    int L = 1;
+    while (L < 32 && np * (2 * L) <= 32) L *= 2;
+    const int t = lane / L, sub = lane & (L - 1);
+    const bool owner = t < np;
+    const int32_t key = owner ? nci[n0 + t] : -1;
     const int64_t a0 = arp[i], a1 = arp[i + 1];
-    double aii = 1.0;
-    for (int64_t base = a0; base < a1; base += 32) {
-        // this chunk's A entries: lane k holds entry base + k and the extent of P row f
-        const int cnt = (int)(a1 - base < 32 ? a1 - base : 32);
-        int32_t f = 0;
-        double a = 0.0;
-        int64_t ps = 0;
-        int len = 0;
-        if (lane < cnt) {
-            f = aci[base + lane];
-            a = av[base + lane];
-            ps = nrp[f];
-            len = (int)(nrp[f + 1] - ps);
-        }
-        const unsigned dm = __ballot_sync(0xffffffffu, lane < cnt && f == (int32_t)i);
-        if (dm) aii = __shfl_sync(0xffffffffu, a, __ffs(dm) - 1);
-        int64_t psk = __shfl_sync(0xffffffffu, ps, 0);
-        int lenk = __shfl_sync(0xffffffffu, len, 0);
-        PRow cur = pp_load(nci, P, psk, lenk, lane);
-        for (int k = 0; k < cnt; ++k) {
-            const Acc ak = (Acc)__shfl_sync(0xffffffffu, a, k);
-            int64_t psn = 0;
-            int lenn = 0;
-            if (k + 1 < cnt) {                             // next P row in flight
-                psn = __shfl_sync(0xffffffffu, ps, k + 1);
-                lenn = __shfl_sync(0xffffffffu, len, k + 1);
-            }
-            const PRow nxt = pp_load(nci, P, psn, lenn, lane);
-            for (int off = 0;;) {
-                // last lane q with c_q <= key (c sorted; lanes past the row hold INT_MAX)
-                int pos = 0;
+    Acc acc = Acc(0);
+    double aii = 0.0;
+    bool has_diag = false;
+    for (int64_t kb = a0 + sub; kb < a1; kb += (int64_t)PP_ILP * L) {
+        int64_t lo[PP_ILP];
+        int len[PP_ILP];
+        double a[PP_ILP];
 #pragma unroll
-                for (int half = 16; half > 0; half >>= 1) {
-                    const int32_t cm = __shfl_sync(0xffffffffu, cur.c, pos + half);
-                    pos = cm <= key ? pos + half : pos;
-                }
-                const int32_t cq = __shfl_sync(0xffffffffu, cur.c, pos);
-                const double vq = __shfl_sync(0xffffffffu, cur.v, pos);
-                if (lane < np && cq == key) acc += ak * (Acc)vq;
-                off += 32;
-                if (off >= lenk) break;                    // P rows longer than 32: next 32 entries
-                cur = pp_load(nci, P, psk + off, lenk - off, lane);
+        for (int j = 0; j < PP_ILP; ++j) {
+            const int64_t ka = kb + (int64_t)j * L;
+            lo[j] = 0;
+            len[j] = 0;
+            a[j] = 0.0;
+            if (ka < a1) {
+                const int32_t f = aci[ka];
+                a[j] = av[ka];
+                if (f == (int32_t)i) { aii = a[j]; has_diag = true; }
+                lo[j] = nrp[f];
+                len[j] = (int)(nrp[f + 1] - lo[j]);
             }
-            cur = nxt;
-            psk = psn;
-            lenk = lenn;
         }
+        if (!owner) continue;
+        int pos[PP_ILP];
+#pragma unroll
+        for (int j = 0; j < PP_ILP; ++j) pos[j] = 0;
+        bool longrow = false;
+#pragma unroll
+        for (int j = 0; j < PP_ILP; ++j) longrow = longrow || len[j] > 32;
+        if (!longrow) {
+            // last position with column <= key, five halving steps (rows of at most 32 entries)
+#pragma unroll
+            for (int h = 16; h > 0; h >>= 1)
+#pragma unroll
+                for (int j = 0; j < PP_ILP; ++j)
+                    if (pos[j] + h < len[j] && nci[lo[j] + pos[j] + h] <= key) pos[j] += h;
+        } else {
+#pragma unroll
+            for (int j = 0; j < PP_ILP; ++j) {
+                int lo2 = 0, hi2 = len[j];                 // first position with column >= key
+                while (lo2 < hi2) {
+                    const int mid = (lo2 + hi2) >> 1;
+                    if (nci[lo[j] + mid] < key) lo2 = mid + 1; else hi2 = mid;
+                }
+                pos[j] = lo2 < len[j] ? lo2 : 0;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < PP_ILP; ++j)
+            if (len[j] > 0 && nci[lo[j] + pos[j]] == key) acc += (Acc)a[j] * (Acc)P[lo[j] + pos[j]];
     }
-    if (lane < np) w[n0 + lane] = (Acc)((double)acc / aii);
+    // a_ii from the lane that met the diagonal entry
+    const unsigned dm = __ballot_sync(0xffffffffu, has_diag);
+    aii = __shfl_sync(0xffffffffu, aii, dm ? __ffs(dm) - 1 : 0);
+    if (!dm) aii = 1.0;
+    for (int d = L >> 1; d > 0; d >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, d);
+    if (owner && sub == 0) w[n0 + t] = (Acc)((double)acc / aii);
 }
 
 // projection and update of eq. (9) for every small row: dp = w - G~ (G~^T G~)^-1 G~^T w,
