@@ -479,6 +479,21 @@ def main():
             tsp = sp["ms"] / sp["calls"] / 1e3
             roof["cg_spmv_fp64"] = {"achieved": sp["bytes_per_call"] / tsp / 1e9,
                                     "frac": sp["bytes_per_call"] / tsp / 1e9 / peak, "ms_per_launch": tsp * 1e3}
+    # setup steps on the roofline: algorithmic bytes (each operand read once, the result written
+    # once) over the section's CUDA-event time, against the same measured HBM peak
+    setup_roof = {}
+    for key, what in (("emin_level_l0", "energy-minimisation step of eq. (9), level 0: masked product + FP64 row projection"),
+                      ("rap_level_l0", "Galerkin product P_e^T (A P_e), level 0"),
+                      ("rap_AP_l0", "A P_e, level 0"), ("rap_PtAP_l0", "P_e^T (A P_e), upper triangle mirrored, level 0"),
+                      ("setup_nodal_AD", "A_e D_h (nodal operator), level 0")):
+        t = prof.get(key)
+        if t and t["calls"] > 0 and t["bytes_per_call"] > 0:
+            sec = t["ms"] / t["calls"] / 1e3
+            ach = t["bytes_per_call"] / sec / 1e9
+            setup_roof[key] = {"what": what, "ms": t["ms"] / t["calls"], "algorithmic_bytes": t["bytes_per_call"],
+                               "achieved_gbs": ach, "frac": ach / peak}
+    if roof is not None:
+        roof["setup_steps"] = setup_roof
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(p.n_edges)

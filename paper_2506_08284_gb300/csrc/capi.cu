@@ -167,6 +167,10 @@ int setup_impl(sphc_handle* h, const sphc_csr* A_e, const sphc_csr* D_h, const d
             Section sub(prof, "setup_nodal_AD", s);
             SPHC_TRY(spgemm(L0.A, L0.D, L0.AD, s));
         }
+        if (prof) {
+            auto csr_bytes = [](const DCSR& M) { return 12.0 * (double)M.nnz + 8.0 * (double)(M.nr + 1); };
+            prof->timers[prof->find("setup_nodal_AD", 0.0)].bytes = csr_bytes(L0.A) + csr_bytes(L0.D) + csr_bytes(L0.AD);
+        }
         SPHC_TRY(spgemm_sym(L0.Dt, L0.AD, L0.An, s));
     }
     int lev = 0;

@@ -2000,6 +2000,16 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
             SPHC_TRY(spgemm_sym(L.PeT, AP, Anext, s));
         }
         if (rid >= 0) prof->end(rid, s);
+        if (prof) {
+            // algorithmic bytes: each operand read once (values, columns, row pointers), the
+            // product written once
+            auto csr_bytes = [](const DCSR& M) { return 12.0 * (double)M.nnz + 8.0 * (double)(M.nr + 1); };
+            const double b_ap = csr_bytes(L.A) + csr_bytes(L.Pe) + csr_bytes(AP);
+            const double b_ptap = csr_bytes(L.PeT) + csr_bytes(AP) + csr_bytes(Anext);
+            prof->timers[prof->find(lev_name("rap_AP", lev).c_str(), 0.0)].bytes = b_ap;
+            prof->timers[prof->find(lev_name("rap_PtAP", lev).c_str(), 0.0)].bytes = b_ptap;
+            prof->timers[rid].bytes = b_ap + b_ptap;
+        }
     }
     {
         Section sec(prof, lev_name("setup_nodal_rap", lev).c_str(), s);
