@@ -42,7 +42,7 @@ class _Opts(ctypes.Structure):
                 ("max_coarse", ctypes.c_int64), ("emin_omega", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("power_iters", ctypes.c_int32),
                 ("unsmoothed_pn", ctypes.c_int32), ("agg0", ctypes.c_void_p),
-                ("nagg0", ctypes.c_int64), ("p0_value", ctypes.c_double)]
+                ("nagg0", ctypes.c_int64), ("p0_value", ctypes.c_double), ("emin_method", ctypes.c_int32)]
 
 
 def _load():
@@ -184,7 +184,7 @@ class Hierarchy:
 
 
 def setup(ne, nv, A, D, max_levels=8, emin_iters=1, max_coarse=1000, emin_omega=0.5, seed=0,
-          power_iters=15, unsmoothed_pn=False, agg0=None, p0_value=0.0) -> Hierarchy:
+          power_iters=15, unsmoothed_pn=False, agg0=None, p0_value=0.0, emin_method=0) -> Hierarchy:
     """A, D: (rowptr, col, val) triplets of A_e (ne x ne) and D_h (ne x nv)."""
     lib = _load()
     Arp, Aci, Av = _c(A[0], np.int64), _c(A[1], np.int32), _c(A[2], np.float64)
@@ -195,7 +195,7 @@ def setup(ne, nv, A, D, max_levels=8, emin_iters=1, max_coarse=1000, emin_omega=
         aggarr = _c(agg0, np.int32)
         nagg0 = int(aggarr.max()) + 1 if aggarr.size else 0
     o = _Opts(max_levels, emin_iters, max_coarse, emin_omega, seed, power_iters, int(unsmoothed_pn),
-              None if aggarr is None else aggarr.ctypes.data, nagg0, p0_value)
+              None if aggarr is None else aggarr.ctypes.data, nagg0, p0_value, int(emin_method))
     st = ctypes.c_int()
     t0 = time.perf_counter()
     ptr = lib.orc_setup(ne, nv, _p(Arp), _p(Aci), _p(Av), _p(Drp), _p(Dci), _p(Dv), ctypes.byref(o),

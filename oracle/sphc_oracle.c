@@ -425,6 +425,7 @@ typedef struct {
     const int32_t *agg0;        /* injected level-0 aggregates (or NULL) */
     int64_t nagg0;
     double p0_value;            /* initial pattern value before the least-norm correction */
+    int32_t emin_method;        /* 0: projected Jacobi, eq. (9); 1: projected CG on the KKT system, eq. (8) */
 } orc_opts;
 
 typedef struct {
@@ -678,6 +679,75 @@ void orc_free(ohier *h) {
 #define ORC_EINFEASIBLE -6
 #define ORC_ENUMERIC -9
 
+/* The projected, D^-1-scaled gradient of the energy sum_j P_:j^T A P_:j at P (values on the
+ * pattern N): g_i = Pi_i (D^-1 A P)_{i, N_i} row by row, Pi_i the orthogonal projection onto the
+ * null space of row i's constraint matrix G~^T (Sec. 3: masking to N, then the row constraints). */
+static int projected_gradient(const olevel *L, const ocsr *N, const double *Pv, double *g, double *G, double *rt,
+                              double *tau, double *tmp) {
+    ocsr P = csr_copy(N);
+    memcpy(P.v, Pv, sizeof(double) * (size_t)N->rp[N->nr]);
+    ocsr AP = csr_spgemm(&L->A, &P);
+    int status = ORC_OK;
+    for (int64_t i = 0; i < L->A.nr && status == ORC_OK; ++i) {
+        double d = csr_diag(&L->A, i);
+        int np;
+        int k = local_system(&L->T, N, &L->DH, i, G, rt, &np);
+        if (np == 0) continue;
+        double *gi = g + N->rp[i];
+        int64_t ka = AP.rp[i];
+        for (int r = 0; r < np; ++r) {
+            int32_t j = N->ci[N->rp[i] + r];
+            while (ka < AP.rp[i + 1] && AP.ci[ka] < j) ++ka;
+            gi[r] = (ka < AP.rp[i + 1] && AP.ci[ka] == j) ? AP.v[ka] / d : 0.0;
+        }
+        if (k > 0) {
+            if (house_qr(np, k, G, tau)) { status = ORC_EINFEASIBLE; break; }
+            qr_project_null(np, k, G, tau, gi, tmp);
+        }
+    }
+    csr_free(&AP);
+    csr_free(&P);
+    return status;
+}
+/* sum_i a_ii x_i . y_i over the pattern rows: the inner product of the projected CG below in
+ * which D^-1 is the preconditioner (it scales whole rows, so it commutes with each Pi_i) */
+static double row_weighted_dot(const olevel *L, const ocsr *N, const double *x, const double *y) {
+    double s = 0.0;
+    for (int64_t i = 0; i < L->A.nr; ++i) {
+        double d = csr_diag(&L->A, i), si = 0.0;
+        for (int64_t k = N->rp[i]; k < N->rp[i + 1]; ++k) si += x[k] * y[k];
+        s += d * si;
+    }
+    return s;
+}
+/* Projected CG for the saddle-point system of eq. (8) (Sec. 3): CG on the energy restricted to
+ * corrections that keep the pattern and the row constraints, preconditioned by D^-1, started
+ * from the feasible P (so that only one projection per iteration is needed), iters steps. */
+static int emin_projected_cg(const olevel *L, const ocsr *N, double *Pv, int iters, double *G, double *rt,
+                             double *tau, double *tmp) {
+    int64_t nz = N->rp[N->nr];
+    double *z = (double *)calloc((size_t)(nz > 0 ? nz : 1), sizeof(double));
+    double *pd = (double *)calloc((size_t)(nz > 0 ? nz : 1), sizeof(double));
+    double *w = (double *)calloc((size_t)(nz > 0 ? nz : 1), sizeof(double));
+    int status = projected_gradient(L, N, Pv, w, G, rt, tau, tmp);
+    for (int64_t q = 0; q < nz; ++q) { z[q] = -w[q]; pd[q] = z[q]; }
+    double rz = row_weighted_dot(L, N, z, z);
+    for (int it = 0; it < iters && status == ORC_OK && rz > 0.0; ++it) {
+        status = projected_gradient(L, N, pd, w, G, rt, tau, tmp);
+        if (status != ORC_OK) break;
+        double pq = row_weighted_dot(L, N, pd, w);
+        if (!(pq > 0.0)) break;
+        double alpha = rz / pq;
+        for (int64_t q = 0; q < nz; ++q) { Pv[q] += alpha * pd[q]; z[q] -= alpha * w[q]; }
+        double rz_new = row_weighted_dot(L, N, z, z);
+        double beta = rz_new / rz;
+        rz = rz_new;
+        for (int64_t q = 0; q < nz; ++q) pd[q] = z[q] + beta * pd[q];
+    }
+    free(z); free(pd); free(w);
+    return status;
+}
+
 /* one level of Alg. 3 plus the emin iteration; fills L's transfer data and returns the
  * next-level operators through Anext/Dnext/Annext. */
 static int build_level(olevel *L, int lev, const orc_opts *o, ocsr *Anext, ocsr *Dnext, ocsr *Annext) {
@@ -779,7 +849,9 @@ static int build_level(olevel *L, int lev, const orc_opts *o, ocsr *Anext, ocsr 
         }
     }
     L->Pe = csr_copy(&L->P0);
-    for (int it = 0; it < o->emin_iters && status == ORC_OK; ++it) {
+    if (o->emin_method == 1 && status == ORC_OK)
+        status = emin_projected_cg(L, &N, L->Pe.v, o->emin_iters, G, rt, tau, tmp);
+    for (int it = 0; it < o->emin_iters && status == ORC_OK && o->emin_method == 0; ++it) {
         /* dP = D^-1 A P (full product), then the projection: mask to N, row constraint */
         ocsr AP = csr_spgemm(&L->A, &L->Pe);
         for (int64_t i = 0; i < ne && status == ORC_OK; ++i) {
