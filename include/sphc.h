@@ -96,7 +96,10 @@ typedef struct {
     int32_t block_rhs;       /* 1: sphc_solve with nrhs >= 2 solves the right-hand sides in blocks of up
                                 to 16, one CG per column sharing every operator read (vectors
                                 interleaved per row); 0: one right-hand side after another (default 1) */
-    int32_t reserved[2];
+    int32_t emin_method;     /* energy minimisation of P_e: 0 projected Jacobi, eq. (9), with emin_omega;
+                                1 projected CG on the KKT system of eq. (8) (Sec. 3), D^-1
+                                preconditioned, emin_iters steps (default 0) */
+    int32_t reserved[1];
 } sphc_opts;
 
 /* Learned warm start (not part of the paper).  For every pattern entry (i, j) of P_e a

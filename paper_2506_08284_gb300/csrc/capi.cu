@@ -118,6 +118,10 @@ int setup_impl(sphc_handle* h, const sphc_csr* A_e, const sphc_csr* D_h, const d
                       l, c);
             return SPHC_EINVAL;
         }
+        if (o.emin_method < 0 || o.emin_method > 1) {
+            set_error("opts.emin_method must be 0 (projected Jacobi) or 1 (projected CG) (got %d)", (int)o.emin_method);
+            return SPHC_EINVAL;
+        }
         if (o.mlp_wait_polls < 0) {
             set_error("opts.mlp_wait_polls must be >= 0 (got %d)", (int)o.mlp_wait_polls);
             return SPHC_EINVAL;

@@ -1122,7 +1122,8 @@ k_p0(int64_t ne, const int32_t* rows, const int64_t* trp, const int32_t* tci, co
 __global__ void __launch_bounds__(LOC_WARPS * 32)
 k_emin(int64_t ne, const int32_t* rows, const int64_t* arp, const int32_t* aci, const double* av, const int64_t* trp,
        const int32_t* tci, const double* tv, const int64_t* nrp, const int32_t* nci, const int64_t* hrp,
-       const int32_t* hci, const double* hv, const double* P, double* Pout, double omega, int* fail) {
+       const int32_t* hci, const double* hv, const double* P, double* Pout, double omega, int* fail,
+       int grad_only) {
     extern __shared__ unsigned char smem_raw[];
     int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     LocalSys& S = ((LocalSys*)smem_raw)[w];
@@ -1174,7 +1175,7 @@ k_emin(int64_t ne, const int32_t* rows, const int64_t* arp, const int32_t* aci, 
     int64_t n0 = nrp[i];
     for (int t = lane, q = 0; t < np; t += 32, ++q) {
         double dp = wt[q] - gz(S, t, k, S.z);
-        Pout[n0 + t] = P[n0 + t] - omega * dp;
+        Pout[n0 + t] = grad_only ? dp : P[n0 + t] - omega * dp;
     }
 }
 
@@ -1463,7 +1464,7 @@ k_emin_pp(int64_t ne, const int64_t* __restrict__ arp, const int32_t* __restrict
 template <typename V>
 __global__ void __launch_bounds__(128)
 k_emin_rows(int64_t ne, const int64_t* __restrict__ nrp, const V* __restrict__ w, const double* __restrict__ P,
-            double* __restrict__ Pout, double omega, RowCache cache) {
+            double* __restrict__ Pout, double omega, RowCache cache, int grad_only) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ne) return;
     const int k = cache.k[i];
@@ -1482,8 +1483,51 @@ k_emin_rows(int64_t ne, const int64_t* __restrict__ nrp, const V* __restrict__ w
     row_solve(S, z);
     for (int t = 0; t < S.np; ++t) {
         double dp = (double)w[S.n0 + t] - row_gz(S, t, z);
-        Pout[S.n0 + t] = P[S.n0 + t] - omega * dp;
+        Pout[S.n0 + t] = grad_only ? dp : P[S.n0 + t] - omega * dp;
     }
+}
+
+// ------------------------------------------------------------------ projected CG (Sec. 3, eq. (8))
+// partial sums of sum_i a_ii x_i . y_i over the pattern rows (thread per row, block sums in a
+// fixed order); the inner product of the D^-1-preconditioned projected CG
+__global__ void __launch_bounds__(256)
+k_wdot_rows(int64_t ne, const int64_t* __restrict__ nrp, const double* __restrict__ d, const double* __restrict__ x,
+            const double* __restrict__ y, double* __restrict__ part) {
+    __shared__ double sw[8];
+    double sacc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ne; i += (int64_t)gridDim.x * blockDim.x) {
+        double si = 0.0;
+        for (int64_t q = nrp[i]; q < nrp[i + 1]; ++q) si += x[q] * y[q];
+        sacc += d[i] * si;
+    }
+    for (int o = 16; o > 0; o >>= 1) sacc += __shfl_down_sync(0xffffffffu, sacc, o);
+    if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = sacc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += sw[w];
+        part[blockIdx.x] = t;
+    }
+}
+__global__ void k_sum_parts(const double* part, int n, double* out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < n; ++q) t += part[q];
+        *out = t;
+    }
+}
+__global__ void k_neg_copy(const double* a, double* b, double* c, int64_t n) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < n) { b[q] = -a[q]; c[q] = -a[q]; }
+}
+// P += alpha p, z -= alpha w
+__global__ void k_cg_update(double* P, const double* pd, double* z, const double* w, double alpha, int64_t n) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < n) { P[q] += alpha * pd[q]; z[q] -= alpha * w[q]; }
+}
+__global__ void k_cg_dir(double* pd, const double* z, double beta, int64_t n) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < n) pd[q] = z[q] + beta * pd[q];
 }
 
 // ------------------------------------------------------------------ learned warm start
@@ -1949,6 +1993,67 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
         if (o.emin_fp32) SPHC_TRY(W32.alloc(nnzN, s));
         else SPHC_TRY(W.alloc(nnzN, s));
     }
+    // projected gradient g = Pi D^-1 (A V)|_N of values V on the pattern (small rows by the product
+    // and thread-per-row projection kernels, large rows by k_emin)
+    auto proj_grad = [&](const double* V, double* g) -> int {
+        const int gpp = grid_for(ne, PP_WARPS);
+        if (o.emin_fp32) {
+            SPHC_LAUNCH(k_emin_pp<float><<<gpp, PP_WARPS * 32, 0, s>>>(ne, L.A.rp.p, L.A.ci.p, L.A.v.p, L.Pe.rp.p,
+                                                                      L.Pe.ci.p, V, cache.k, W32.p));
+            SPHC_LAUNCH(k_emin_rows<float><<<grid_for(ne, 128), 128, 0, s>>>(ne, L.Pe.rp.p, W32.p, V, g, 0.0, cache, 1));
+        } else {
+            SPHC_LAUNCH(k_emin_pp<double><<<gpp, PP_WARPS * 32, 0, s>>>(ne, L.A.rp.p, L.A.ci.p, L.A.v.p, L.Pe.rp.p,
+                                                                       L.Pe.ci.p, V, cache.k, W.p));
+            SPHC_LAUNCH(k_emin_rows<double><<<grid_for(ne, 128), 128, 0, s>>>(ne, L.Pe.rp.p, W.p, V, g, 0.0, cache, 1));
+        }
+        if (hbig > 0)
+            SPHC_LAUNCH(k_emin<<<grid_for(hbig, LOC_WARPS), LOC_WARPS * 32, sm, s>>>(
+                hbig, big.p, L.A.rp.p, L.A.ci.p, L.A.v.p, L.T.rp.p, L.T.ci.p, L.T.v.p, L.Pe.rp.p, L.Pe.ci.p,
+                L.DH.rp.p, L.DH.ci.p, L.DH.v.p, V, g, 0.0, st.p, 1));
+        SPHC_CK(cudaGetLastError());
+        return SPHC_OK;
+    };
+    if (o.emin_method == 1 && emin_iters > 0 && ne > 0) {
+        // projected CG on eq. (8) from the feasible P0: z = -Pi D^-1 A P, p = z, and per step
+        // w = Pi D^-1 A p, alpha = (z, z)_D / (p, w)_D, P += alpha p, z -= alpha w, beta, p = z + beta p,
+        // with (x, y)_D = sum_i a_ii x_i . y_i (the preconditioner D^-1 commutes with Pi)
+        if (tid >= 0) prof->begin(tid, s);
+        DBuf<double> dg, Z, Pd, Gv, part, sc;
+        SPHC_TRY(dg.alloc(ne, s));
+        SPHC_TRY(csr_diag(L.A, dg.p, s));
+        SPHC_TRY(Z.alloc(nnzN, s));
+        SPHC_TRY(Pd.alloc(nnzN, s));
+        SPHC_TRY(Gv.alloc(nnzN, s));
+        constexpr int WD_BLOCKS = 512;
+        SPHC_TRY(part.alloc(WD_BLOCKS, s));
+        SPHC_TRY(sc.alloc(1, s));
+        auto wdot = [&](const double* x, const double* y, double* out_host) -> int {
+            SPHC_LAUNCH(k_wdot_rows<<<WD_BLOCKS, 256, 0, s>>>(ne, L.Pe.rp.p, dg.p, x, y, part.p));
+            SPHC_LAUNCH(k_sum_parts<<<1, 32, 0, s>>>(part.p, WD_BLOCKS, sc.p));
+            SPHC_CK(cudaMemcpyAsync(out_host, sc.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+            SPHC_CK(cudaStreamSynchronize(s));
+            return SPHC_OK;
+        };
+        SPHC_TRY(proj_grad(L.Pe.v.p, Gv.p));
+        SPHC_LAUNCH(k_neg_copy<<<grid_for(nnzN, 256), 256, 0, s>>>(Gv.p, Z.p, Pd.p, nnzN));
+        double rz = 0.0;
+        SPHC_TRY(wdot(Z.p, Z.p, &rz));
+        for (int it = 0; it < emin_iters && rz > 0.0; ++it) {
+            SPHC_TRY(proj_grad(Pd.p, Gv.p));
+            double pq = 0.0;
+            SPHC_TRY(wdot(Pd.p, Gv.p, &pq));
+            if (!(pq > 0.0)) break;
+            const double alpha = rz / pq;
+            SPHC_LAUNCH(k_cg_update<<<grid_for(nnzN, 256), 256, 0, s>>>(L.Pe.v.p, Pd.p, Z.p, Gv.p, alpha, nnzN));
+            double rz_new = 0.0;
+            SPHC_TRY(wdot(Z.p, Z.p, &rz_new));
+            const double beta = rz_new / rz;
+            rz = rz_new;
+            SPHC_LAUNCH(k_cg_dir<<<grid_for(nnzN, 256), 256, 0, s>>>(Pd.p, Z.p, beta, nnzN));
+        }
+        if (tid >= 0) prof->end(tid, s);
+        emin_iters = 0;                          // done: skip the Jacobi loop below
+    }
     for (int it = 0; it < emin_iters; ++it) {
         if (tid >= 0) prof->begin(tid, s);
         if (ne > 0) {
@@ -1966,15 +2071,15 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
                 Section sr(prof, lev_name("emin_rows", lev).c_str(), s);
                 if (o.emin_fp32)
                     SPHC_LAUNCH(k_emin_rows<float><<<grid_for(ne, 128), 128, 0, s>>>(ne, L.Pe.rp.p, W32.p, L.Pe.v.p,
-                                                                                     Pnew.p, o.emin_omega, cache));
+                                                                                     Pnew.p, o.emin_omega, cache, 0));
                 else
                     SPHC_LAUNCH(k_emin_rows<double><<<grid_for(ne, 128), 128, 0, s>>>(ne, L.Pe.rp.p, W.p, L.Pe.v.p,
-                                                                                      Pnew.p, o.emin_omega, cache));
+                                                                                      Pnew.p, o.emin_omega, cache, 0));
             }
             if (hbig > 0)
                 SPHC_LAUNCH(k_emin<<<grid_for(hbig, LOC_WARPS), LOC_WARPS * 32, sm, s>>>(
                     hbig, big.p, L.A.rp.p, L.A.ci.p, L.A.v.p, L.T.rp.p, L.T.ci.p, L.T.v.p, L.Pe.rp.p, L.Pe.ci.p,
-                    L.DH.rp.p, L.DH.ci.p, L.DH.v.p, L.Pe.v.p, Pnew.p, o.emin_omega, st.p));
+                    L.DH.rp.p, L.DH.ci.p, L.DH.v.p, L.Pe.v.p, Pnew.p, o.emin_omega, st.p, 0));
         }
         if (tid >= 0) prof->end(tid, s);
         std::swap(L.Pe.v.p, Pnew.p);

@@ -230,3 +230,22 @@ def test_emin_fp32_accumulation(pair):
     assert rc == 0 and rr[0] <= 1.01e-8
     assert np.linalg.norm(x - ref["x"]) <= 1e-6 * np.linalg.norm(ref["x"])
     hf.destroy()
+
+
+@pytest.mark.parametrize("k", [1, 3])
+def test_projected_cg_prolongator_matches_oracle(pair, k):
+    # opts.emin_method = 1: projected CG on eq. (8) (Sec. 3), k steps, against the oracle's
+    name, p, h, o, opts = pair
+    hc = gpu_setup(p, vcycle_fp32=0, emin_method=1, emin_iters=k, **opts)
+    import oracle
+    oc = oracle.setup_problem(p, max_levels=8, emin_iters=k, max_coarse=opts.get("max_coarse", 1000), emin_method=1)
+    assert hc.nlevels == oc.nlevels
+    for l in range(oc.nlevels - 1):
+        assert_csr_close(hc.export(l, "Pe"), oc.matrix(l, "Pe"), f"L{l} Pe (projected CG, {k} steps)", FP64_RTOL)
+        assert_csr_close(hc.export(l + 1, "A"), oc.matrix(l + 1, "A"), f"L{l + 1} A", FP64_RTOL)
+    b = meshgen.rhs(5, p.n_edges)
+    x = np.zeros_like(b)
+    rc, it, rr = hc.solve(b, x, tol=1e-8)
+    ref = oc.solve(b, tol=1e-8)
+    assert rc == 0 and abs(it[0] - ref["iters"]) <= 1
+    hc.destroy()
