@@ -222,6 +222,15 @@ SPHC_API int sphc_setup(const sphc_csr* A_e, const sphc_csr* D_h, const double* 
 SPHC_API int sphc_solve(sphc_handle* h, const double* b, double* x, int nrhs, double tol, void* stream,
                int* iters, double* relres);
 
+/* 1-norm condition estimate of D^-1 A_e (D = diag(A_e)), which Sec. 6.1 uses (through Matlab's
+ * condest) to cap the CG tolerance at kappa / 1e16.  ||D^-1 A_e||_1 is computed exactly (A_e is
+ * symmetric: column j sums |a_ji| / a_ii); ||(D^-1 A_e)^-1||_1 is Hager's estimate (a lower bound,
+ * usually exact) from at most max_steps iterations, each two solves with the handle's CG to a
+ * relative residual of 1e-10.  kappa, norm_b (= ||D^-1 A_e||_1) and norm_binv may be NULL.  Not a
+ * hot-path call.  Errors: SPHC_EINVAL, SPHC_ENOMEM, SPHC_ECUDA, SPHC_EBREAKDOWN. */
+SPHC_API int sphc_cond_estimate(sphc_handle* h, int max_steps, double* kappa, double* norm_b, double* norm_binv,
+                                void* stream);
+
 /* Apply one V-cycle z = M^-1 r (FP64 in and out, n_e entries) with the handle's precision. */
 SPHC_API int sphc_vcycle(sphc_handle* h, const double* r, double* z, void* stream);
 

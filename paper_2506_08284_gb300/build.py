@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["sparse.cu", "setup.cu", "layout.cu", "solve.cu", "block.cu", "capi.cu", "noalloc.cu", "mlp.cu"]
+SOURCES = ["sparse.cu", "setup.cu", "layout.cu", "solve.cu", "block.cu", "capi.cu", "noalloc.cu", "mlp.cu", "cond.cu"]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
          "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden", "--expt-relaxed-constexpr"]

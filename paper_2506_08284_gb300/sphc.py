@@ -82,7 +82,7 @@ EXPORTED = ["sphc_default_opts", "sphc_setup", "sphc_solve", "sphc_vcycle", "sph
             "sphc_get_profile", "sphc_launch_count", "sphc_relres_noalloc", "sphc_default_train_opts",
             "sphc_mlp_train", "sphc_mlp_predict", "sphc_mlp_gradient", "sphc_export_features",
             "sphc_setup_batched", "sphc_solve_batched", "sphc_batch_destroy", "sphc_trim_memory",
-            "sphc_memory_usage", "sphc_mlp_predict_level"]
+            "sphc_memory_usage", "sphc_mlp_predict_level", "sphc_cond_estimate"]
 
 _lib = None
 
@@ -116,6 +116,7 @@ def load(path: str | None = None):
     lib.sphc_mlp_gradient.argtypes = [P, P, P, I, P, P, P]
     lib.sphc_export_features.argtypes = [P, I, P, P, P]
     lib.sphc_mlp_predict_level.argtypes = [P, I, P, P, P]
+    lib.sphc_cond_estimate.argtypes = [P, I, P, P, P, P]
     lib.sphc_setup_batched.argtypes = [I, P, P, P, P, ctypes.POINTER(sphc_opts), P, ctypes.POINTER(P)]
     lib.sphc_solve_batched.argtypes = [P, P, P, I, ctypes.c_double, P, P, P]
     lib.sphc_batch_destroy.argtypes = [P]
@@ -221,6 +222,13 @@ class Handle:
         if rc not in (SPHC_OK, -4, -5, -8):
             _check(rc)
         return rc, list(it), list(rr)
+
+    def cond_estimate(self, max_steps=5, stream=None):
+        """(kappa_1(D^-1 A_e) estimate, ||D^-1 A_e||_1, estimated ||(D^-1 A_e)^-1||_1)."""
+        k, nb, ni = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check(load().sphc_cond_estimate(self._ptr, int(max_steps), ctypes.byref(k), ctypes.byref(nb),
+                                         ctypes.byref(ni), _stream(stream)))
+        return k.value, nb.value, ni.value
 
     def vcycle(self, r, z, stream=None):
         _check(load().sphc_vcycle(self._ptr, _ptr(r), _ptr(z), _stream(stream)))
