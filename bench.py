@@ -206,6 +206,9 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-block", action="store_true", help="skip the block-of-16-right-hand-sides leg")
+    ap.add_argument("--oracle-check", action="store_true",
+                    help="also run the OpenMP oracle once on the full workload: its time, and the GPU headline "
+                         "solution against its solution")
     ap.add_argument("--block-rhs", type=int, default=16)
     ap.add_argument("--no-graph", action="store_true",
                     help="run CG with a host loop instead of the CUDA graph (same kernels; for profilers "
@@ -311,11 +314,20 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ CPU oracle baseline
-def cpu_baseline(target_edges, steps=1):
-    """The oracle (single-threaded FP64 C) on a bounded sample mesh, scaled to the workload by the
-    number of unknowns (AMG setup and solve are linear in the unknowns)."""
-    import meshgen
+def _oracle_openmp():
+    """Import the oracle in its OpenMP build (row-parallel loops only, bit-identical results),
+    which then runs on every host core."""
+    os.environ["SPHC_ORACLE_OPENMP"] = "1"
     import oracle
+    return oracle
+
+
+def cpu_baseline(target_edges, steps=1):
+    """The oracle (FP64 C, OpenMP build on all host cores) on a bounded sample: the workload's
+    recipe at 32^3 cells, scaled to the workload by the number of unknowns (AMG setup and solve
+    are linear in the unknowns)."""
+    import meshgen
+    oracle = _oracle_openmp()
 
     spec, seed = meshgen.workload(CPU_SAMPLE)
     p = meshgen.generate(spec)
@@ -331,9 +343,22 @@ def cpu_baseline(target_edges, steps=1):
         del h
     t = sum(ts) / len(ts)
     scale = target_edges / p.n_edges
-    return {"value": t * scale, "unit": "s", "cores": 1, "kind": "oracle",
-            "sample": f"{CPU_SAMPLE} ({p.n_edges:,} unknowns): setup+solve {t:.2f} s ({its} CG iterations), "
-                      f"scaled x{scale:.1f} by unknowns to the workload"}
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": t * scale, "unit": "s", "cores": cores, "kind": "oracle",
+            "sample": f"{CPU_SAMPLE} (the same recipe at 32^3 cells, {p.n_edges:,} unknowns): setup+solve {t:.2f} s "
+                      f"({its} CG iterations) with the OpenMP oracle on {cores} cores, scaled x{scale:.1f} by "
+                      f"unknowns to the workload"}
+
+
+def bench_config(args, world, learned_weights):
+    """The workload description shared by both arms (the reference arm times the oracle on a
+    bounded sample of this workload, named in its cpu_baseline)."""
+    return {"workload": f"{args.workload}: {WORKLOAD_TEXT.get(args.workload, '')}",
+            "solver": "SpHcurlAMG V-cycle (1 pre + 1 post symmetric Hiptmair) in FP64 CG, FP32 V-cycle, "
+                      + ("learned warm start of P_e + 1 energy-minimisation step" if learned_weights
+                         else "least-norm P0 + 1 energy-minimisation step (no MLP weights found)"),
+            "rhs": 1, "tol": args.tol, "l2": "inputs (A_e 2.8 GB FP64) exceed the 129 MB L2; no flush",
+            "parallelism": f"replicas x{world}"}
 
 
 def workload_edges(name):
@@ -344,6 +369,7 @@ def workload_edges(name):
 def run_reference(args, rank):
     if rank != 0:
         return
+    from paper_2506_08284_gb300 import learned
     target = workload_edges(args.workload)
     for _ in range(args.warmup):
         cpu_baseline(target, 1)
@@ -356,7 +382,7 @@ def run_reference(args, rank):
     line = {"metric": "setup+solve s to 1e-8 residual", "value": v, "unit": "s", "impl": "reference",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": f"{args.workload}: {WORKLOAD_TEXT.get(args.workload, '')}"},
+            "data": "synthetic", "config": bench_config(args, args.gpus, os.path.exists(learned.WEIGHTS)),
             "cpu_baseline": cb, "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -553,6 +579,41 @@ def main():
                                "achieved_gbs": ach, "frac": ach / peak}
     if roof is not None:
         roof["setup_steps"] = setup_roof
+    oracle_check = None
+    if args.oracle_check and rank == 0:
+        # the headline arm once more on this process, then the oracle on the same inputs
+        hc = pkg.sphc.setup(A, D, coords, sig, make_opts(pkg, "headline", weights, 0, not args.no_graph), stream)
+        xc = torch.zeros_like(bd)
+        crc, cit, crr = hc.solve(bd, xc, tol=args.tol, stream=stream)
+        torch.cuda.synchronize()
+        xg = xc.cpu().numpy()
+        hc.destroy()
+        oracle = _oracle_openmp()
+        import platform
+        t0 = time.perf_counter()
+        ho = oracle.setup_problem(p)
+        t1 = time.perf_counter()
+        ro = ho.solve(b, tol=args.tol)
+        t2 = time.perf_counter()
+        err = float(np.linalg.norm(xg - ro["x"]) / np.linalg.norm(ro["x"]))
+        mem = None
+        try:
+            mem = int(open("/proc/meminfo").read().split("MemTotal:")[1].split()[0]) // 1024
+        except Exception:
+            pass
+        cpu_model = platform.processor() or platform.machine()
+        try:
+            for ln in open("/proc/cpuinfo"):
+                if ln.lower().startswith(("model name", "cpu part")):
+                    cpu_model = ln.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+        oracle_check = {"oracle_setup_s": t1 - t0, "oracle_solve_s": t2 - t1, "oracle_iters": ro["iters"],
+                        "oracle_relres": ro["relres"], "cores": os.cpu_count(), "cpu": cpu_model, "ram_mib": mem,
+                        "gpu_iters": cit[0], "gpu_relres": crr[0],
+                        "x_rel_err_vs_oracle": err}
+        del ho
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(p.n_edges)
@@ -562,17 +623,13 @@ def main():
             "metric": "setup+solve s to 1e-8 residual", "value": sec_per_system, "unit": "s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64 CG / f32 V-cycle", "data": "synthetic",
-            "config": {"workload": f"{args.workload}: {WORKLOAD_TEXT.get(args.workload, '')}",
-                       "solver": "SpHcurlAMG V-cycle (1 pre + 1 post symmetric Hiptmair) in FP64 CG, FP32 V-cycle, "
-                                 + ("learned warm start of P_e + 1 energy-minimisation step" if weights is not None
-                                    else "least-norm P0 + 1 energy-minimisation step (no MLP weights found)"),
-                       "rhs": 1, "tol": args.tol, "l2": "inputs (A_e 2.8 GB FP64) exceed the 129 MB L2; no flush",
-                       "parallelism": f"replicas x{world}"},
+            "config": bench_config(args, world, weights is not None),
             "iters": iters, "relres": relres, "status": rc, "wall_s_per_step": wall / args.steps,
             "setup_ms": st["setup_ms"], "solve_ms": st["solve_ms"], "levels": st["n_levels"],
             "operator_complexity": st["operator_complexity"], "gpu_launches": int(launches),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "comparators": comparators,
             "speedup_vs_fp64_plain": comparators.get("speedup_vs_fp64_plain"), "rhs_block": block,
+            "oracle_check": oracle_check,
             "profile": {k: {kk: round(vv, 4) if isinstance(vv, float) else vv for kk, vv in v.items()}
                         for k, v in prof.items()},
             "level_edges": [li["n_edges"] for li in info],

@@ -24,14 +24,17 @@ _lib = None
 MAT = dict(A=0, D=1, An=2, Pn=3, DH=4, T=5, Pe=6, P0=7)
 
 
-def build(force: bool = False) -> str:
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile the oracle: plain (single-threaded, the tests' build) or with -fopenmp (the timed
+    CPU baseline; its pragmas split only independent rows, so results are bit-identical)."""
     src = open(_SRC, "rb").read()
     tag = hashlib.sha1(src).hexdigest()[:12]
-    so = os.path.join(_BUILD, f"liborc_{tag}.so")
+    so = os.path.join(_BUILD, f"liborc{'_omp' if openmp else ''}_{tag}.so")
     if force or not os.path.exists(so):
         os.makedirs(_BUILD, exist_ok=True)
         tmp = so + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-D_DEFAULT_SOURCE",
+        flags = ["-fopenmp"] if openmp else []
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-D_DEFAULT_SOURCE", *flags,
                                "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, so)
     return so
@@ -45,10 +48,13 @@ class _Opts(ctypes.Structure):
                 ("nagg0", ctypes.c_int64), ("p0_value", ctypes.c_double), ("emin_method", ctypes.c_int32)]
 
 
+_OPENMP = os.environ.get("SPHC_ORACLE_OPENMP", "0") == "1"
+
+
 def _load():
     global _lib
     if _lib is None:
-        lib = ctypes.CDLL(build())
+        lib = ctypes.CDLL(build(openmp=_OPENMP))
         P, I64, I32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
         lib.orc_setup.argtypes = [I64, I64, P, P, P, P, P, P, ctypes.POINTER(_Opts), P]
         lib.orc_setup.restype = P

@@ -25,6 +25,11 @@
  *   - V-cycle with one pre and one post symmetric Hiptmair sweep, direct coarsest solve
  *     (Sec. 6.1), inside CG with x0 = 0 and ||r|| <= tol ||b|| (Sec. 6.1).
  *
+ * Built plain (single-threaded) for the tests, or with -fopenmp as the timed CPU baseline: the
+ * pragmas split only loops whose rows are independent (product rows, mat-vec rows, the rows of
+ * one Gauss-Seidel colour, the per-row local solves), each row computed exactly as in the plain
+ * build, so both builds give bit-identical results.
+ *
  * Readings where the paper is open (stated once here, used throughout):
  *   - random priorities: splitmix64(seed, id); higher hash = higher priority, ties -> lower id;
  *   - Gauss-Seidel order: multicolour, colours from greedy colouring in priority order
@@ -45,6 +50,24 @@
 #include <string.h>
 #include <math.h>
 #include <stdio.h>
+#ifdef _OPENMP
+#include <omp.h>
+#define ORC_THREADS() omp_get_max_threads()
+#define ORC_TID() omp_get_thread_num()
+#else
+#define ORC_THREADS() 1
+#define ORC_TID() 0
+#endif
+
+/* a failure flag shared by the rows of a parallel loop (set once, read to skip the rest) */
+#ifdef _OPENMP
+#define ORC_FAIL(flag, code) do { _Pragma("omp atomic write") flag = (code); } while (0)
+#define ORC_FAILED(flag) orc_read_flag(&(flag))
+static int orc_read_flag(int *f) { int v; _Pragma("omp atomic read") v = *f; return v != 0; }
+#else
+#define ORC_FAIL(flag, code) do { flag = (code); } while (0)
+#define ORC_FAILED(flag) ((flag) != 0)
+#endif
 
 #define ORC_MAXLEV 16
 /* smallest row sum of the smoothed nodal prolongator that is rescaled to one */
@@ -106,49 +129,58 @@ static int cmp_i32(const void *x, const void *y) {
 /* C = A * B keeping every structurally reached entry (dense accumulator per row) */
 static ocsr csr_spgemm(const ocsr *A, const ocsr *B) {
     int64_t n = A->nr, m = B->nc;
-    int64_t *mark = (int64_t *)malloc(sizeof(int64_t) * (size_t)(m > 0 ? m : 1));
-    double *acc = (double *)calloc((size_t)(m > 0 ? m : 1), sizeof(double));
-    for (int64_t j = 0; j < m; ++j) mark[j] = -1;
-    int32_t *cols = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m > 0 ? m : 1));
+    int nth = ORC_THREADS();
+    size_t mm = (size_t)(m > 0 ? m : 1);
+    /* one dense accumulator (SPA) per thread; rows are independent */
+    int64_t *mark = (int64_t *)malloc(sizeof(int64_t) * mm * (size_t)nth);
+    double *acc = (double *)calloc(mm * (size_t)nth, sizeof(double));
+    int32_t *cols = (int32_t *)malloc(sizeof(int32_t) * mm * (size_t)nth);
+    for (size_t j = 0; j < mm * (size_t)nth; ++j) mark[j] = -1;
     /* pass 1: row sizes */
     int64_t *rp = (int64_t *)calloc((size_t)(n + 1), sizeof(int64_t));
+#pragma omp parallel for schedule(dynamic, 256)
     for (int64_t i = 0; i < n; ++i) {
+        int64_t *mk = mark + mm * (size_t)ORC_TID();
         int64_t cnt = 0;
         for (int64_t ka = A->rp[i]; ka < A->rp[i + 1]; ++ka) {
             int32_t k = A->ci[ka];
             for (int64_t kb = B->rp[k]; kb < B->rp[k + 1]; ++kb) {
                 int32_t j = B->ci[kb];
-                if (mark[j] != i) { mark[j] = i; ++cnt; }
+                if (mk[j] != i) { mk[j] = i; ++cnt; }
             }
         }
-        rp[i + 1] = rp[i] + cnt;
+        rp[i + 1] = cnt;
     }
+    for (int64_t i = 0; i < n; ++i) rp[i + 1] += rp[i];
     ocsr C = csr_alloc(n, m, rp[n]);
     memcpy(C.rp, rp, sizeof(int64_t) * (size_t)(n + 1));
     free(rp);
-    for (int64_t j = 0; j < m; ++j) mark[j] = -1;
+    for (size_t j = 0; j < mm * (size_t)nth; ++j) mark[j] = -1;
+#pragma omp parallel for schedule(dynamic, 256)
     for (int64_t i = 0; i < n; ++i) {
+        int64_t *mk = mark + mm * (size_t)ORC_TID();
+        double *ac = acc + mm * (size_t)ORC_TID();
+        int32_t *cl = cols + mm * (size_t)ORC_TID();
         int64_t cnt = 0;
         for (int64_t ka = A->rp[i]; ka < A->rp[i + 1]; ++ka) {
             int32_t k = A->ci[ka];
             double a = A->v[ka];
             for (int64_t kb = B->rp[k]; kb < B->rp[k + 1]; ++kb) {
                 int32_t j = B->ci[kb];
-                if (mark[j] != i) { mark[j] = i; acc[j] = 0.0; cols[cnt++] = j; }
-                acc[j] += a * B->v[kb];
+                if (mk[j] != i) { mk[j] = i; ac[j] = 0.0; cl[cnt++] = j; }
+                ac[j] += a * B->v[kb];
             }
         }
-        qsort(cols, (size_t)cnt, sizeof(int32_t), cmp_i32);
+        qsort(cl, (size_t)cnt, sizeof(int32_t), cmp_i32);
         for (int64_t q = 0; q < cnt; ++q) {
-            C.ci[C.rp[i] + q] = cols[q];
-            C.v[C.rp[i] + q] = acc[cols[q]];
+            C.ci[C.rp[i] + q] = cl[q];
+            C.v[C.rp[i] + q] = ac[cl[q]];
         }
     }
     free(mark); free(acc); free(cols);
     return C;
 }
 
-/* C = alpha*A + beta*B on the union pattern (rows of A and B sorted) */
 static ocsr csr_add(const ocsr *A, double alpha, const ocsr *B, double beta) {
     int64_t n = A->nr;
     int64_t *rp = (int64_t *)calloc((size_t)(n + 1), sizeof(int64_t));
@@ -188,6 +220,7 @@ static double csr_diag(const ocsr *A, int64_t i) {
 }
 
 static void csr_matvec(const ocsr *A, const double *x, double *y) {
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < A->nr; ++i) {
         double s = 0.0;
         for (int64_t k = A->rp[i]; k < A->rp[i + 1]; ++k) s += A->v[k] * x[A->ci[k]];
@@ -682,16 +715,25 @@ void orc_free(ohier *h) {
 /* The projected, D^-1-scaled gradient of the energy sum_j P_:j^T A P_:j at P (values on the
  * pattern N): g_i = Pi_i (D^-1 A P)_{i, N_i} row by row, Pi_i the orthogonal projection onto the
  * null space of row i's constraint matrix G~^T (Sec. 3: masking to N, then the row constraints). */
-static int projected_gradient(const olevel *L, const ocsr *N, const double *Pv, double *g, double *G, double *rt,
-                              double *tau, double *tmp) {
+static int projected_gradient(const olevel *L, const ocsr *N, const double *Pv, double *g, int cap) {
     ocsr P = csr_copy(N);
     memcpy(P.v, Pv, sizeof(double) * (size_t)N->rp[N->nr]);
     ocsr AP = csr_spgemm(&L->A, &P);
+    int nth = ORC_THREADS();
+    double *G = (double *)malloc(sizeof(double) * (size_t)cap * cap * (size_t)nth);
+    double *rt = (double *)malloc(sizeof(double) * (size_t)cap * (size_t)nth);
+    double *tau = (double *)malloc(sizeof(double) * (size_t)cap * (size_t)nth);
+    double *tmp = (double *)malloc(sizeof(double) * (size_t)cap * (size_t)nth);
     int status = ORC_OK;
-    for (int64_t i = 0; i < L->A.nr && status == ORC_OK; ++i) {
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t i = 0; i < L->A.nr; ++i) {
+        if (ORC_FAILED(status)) continue;
+        const size_t t = (size_t)ORC_TID();
+        double *Gt = G + t * (size_t)cap * cap, *rtt = rt + t * (size_t)cap, *taut = tau + t * (size_t)cap;
+        double *tmpt = tmp + t * (size_t)cap;
         double d = csr_diag(&L->A, i);
         int np;
-        int k = local_system(&L->T, N, &L->DH, i, G, rt, &np);
+        int k = local_system(&L->T, N, &L->DH, i, Gt, rtt, &np);
         if (np == 0) continue;
         double *gi = g + N->rp[i];
         int64_t ka = AP.rp[i];
@@ -701,10 +743,11 @@ static int projected_gradient(const olevel *L, const ocsr *N, const double *Pv, 
             gi[r] = (ka < AP.rp[i + 1] && AP.ci[ka] == j) ? AP.v[ka] / d : 0.0;
         }
         if (k > 0) {
-            if (house_qr(np, k, G, tau)) { status = ORC_EINFEASIBLE; break; }
-            qr_project_null(np, k, G, tau, gi, tmp);
+            if (house_qr(np, k, Gt, taut)) { ORC_FAIL(status, ORC_EINFEASIBLE); continue; }
+            qr_project_null(np, k, Gt, taut, gi, tmpt);
         }
     }
+    free(G); free(rt); free(tau); free(tmp);
     csr_free(&AP);
     csr_free(&P);
     return status;
@@ -723,17 +766,16 @@ static double row_weighted_dot(const olevel *L, const ocsr *N, const double *x, 
 /* Projected CG for the saddle-point system of eq. (8) (Sec. 3): CG on the energy restricted to
  * corrections that keep the pattern and the row constraints, preconditioned by D^-1, started
  * from the feasible P (so that only one projection per iteration is needed), iters steps. */
-static int emin_projected_cg(const olevel *L, const ocsr *N, double *Pv, int iters, double *G, double *rt,
-                             double *tau, double *tmp) {
+static int emin_projected_cg(const olevel *L, const ocsr *N, double *Pv, int iters, int cap) {
     int64_t nz = N->rp[N->nr];
     double *z = (double *)calloc((size_t)(nz > 0 ? nz : 1), sizeof(double));
     double *pd = (double *)calloc((size_t)(nz > 0 ? nz : 1), sizeof(double));
     double *w = (double *)calloc((size_t)(nz > 0 ? nz : 1), sizeof(double));
-    int status = projected_gradient(L, N, Pv, w, G, rt, tau, tmp);
+    int status = projected_gradient(L, N, Pv, w, cap);
     for (int64_t q = 0; q < nz; ++q) { z[q] = -w[q]; pd[q] = z[q]; }
     double rz = row_weighted_dot(L, N, z, z);
     for (int it = 0; it < iters && status == ORC_OK && rz > 0.0; ++it) {
-        status = projected_gradient(L, N, pd, w, G, rt, tau, tmp);
+        status = projected_gradient(L, N, pd, w, cap);
         if (status != ORC_OK) break;
         double pq = row_weighted_dot(L, N, pd, w);
         if (!(pq > 0.0)) break;
@@ -817,49 +859,62 @@ static int build_level(olevel *L, int lev, const orc_opts *o, ocsr *Anext, ocsr 
         if (m > maxm) maxm = m;
     }
     int cap = (maxnp > maxm ? maxnp : maxm) + 1;
-    double *G = (double *)malloc(sizeof(double) * (size_t)cap * cap);
-    double *rt = (double *)malloc(sizeof(double) * (size_t)cap);
-    double *tau = (double *)malloc(sizeof(double) * (size_t)cap);
-    double *p = (double *)malloc(sizeof(double) * (size_t)cap);
-    double *tmp = (double *)malloc(sizeof(double) * (size_t)cap);
+    int nth = ORC_THREADS();
+    /* per-thread scratch of the row-local solves (rows are independent) */
+    double *G = (double *)malloc(sizeof(double) * (size_t)cap * cap * (size_t)nth);
+    double *rt = (double *)malloc(sizeof(double) * (size_t)cap * (size_t)nth);
+    double *tau = (double *)malloc(sizeof(double) * (size_t)cap * (size_t)nth);
+    double *p = (double *)malloc(sizeof(double) * (size_t)cap * (size_t)nth);
+    double *tmp = (double *)malloc(sizeof(double) * (size_t)cap * (size_t)nth);
     int status = ORC_OK;
-    for (int64_t i = 0; i < ne && status == ORC_OK; ++i) {
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t i = 0; i < ne; ++i) {
+        if (ORC_FAILED(status)) continue;
+        const size_t t = (size_t)ORC_TID();
+        double *Gt = G + t * (size_t)cap * cap, *rtt = rt + t * (size_t)cap, *taut = tau + t * (size_t)cap;
+        double *pt = p + t * (size_t)cap, *tmpt = tmp + t * (size_t)cap;
         int np;
         int m = (int)(L->T.rp[i + 1] - L->T.rp[i]);
-        int k = local_system(&L->T, &N, &L->DH, i, G, rt, &np);
-        if (k < 0) { status = ORC_EINFEASIBLE; break; }
+        int k = local_system(&L->T, &N, &L->DH, i, Gt, rtt, &np);
+        if (k < 0) { ORC_FAIL(status, ORC_EINFEASIBLE); continue; }
+#pragma omp atomic
         L->hist[np < 32 ? np : 32][m < 32 ? m : 32]++;
         if (np == 0) continue;
-        if (k > 0 && house_qr(np, k, G, tau)) { status = ORC_EINFEASIBLE; break; }
+        if (k > 0 && house_qr(np, k, Gt, taut)) { ORC_FAIL(status, ORC_EINFEASIBLE); continue; }
         double *pi = L->P0.v + N.rp[i];
         for (int r = 0; r < np; ++r) pi[r] = o->p0_value;
         if (k > 0) {
             /* p += Q R^-T (rt - Gt^T p): Gt^T p = R^T Q^T p (first k entries) */
-            memcpy(tmp, pi, sizeof(double) * (size_t)np);
-            house_apply_qt(np, k, G, tau, tmp);
+            memcpy(tmpt, pi, sizeof(double) * (size_t)np);
+            house_apply_qt(np, k, Gt, taut, tmpt);
             double *res = (double *)malloc(sizeof(double) * (size_t)k);
             for (int c = 0; c < k; ++c) {
                 double sv = 0.0;
-                for (int q = 0; q <= c; ++q) sv += G[(size_t)c * np + q] * tmp[q];
-                res[c] = rt[c] - sv;
+                for (int q = 0; q <= c; ++q) sv += Gt[(size_t)c * np + q] * tmpt[q];
+                res[c] = rtt[c] - sv;
             }
-            qr_minnorm(np, k, G, tau, res, p);
-            for (int r = 0; r < np; ++r) pi[r] += p[r];
+            qr_minnorm(np, k, Gt, taut, res, pt);
+            for (int r = 0; r < np; ++r) pi[r] += pt[r];
             free(res);
         }
     }
     L->Pe = csr_copy(&L->P0);
     if (o->emin_method == 1 && status == ORC_OK)
-        status = emin_projected_cg(L, &N, L->Pe.v, o->emin_iters, G, rt, tau, tmp);
+        status = emin_projected_cg(L, &N, L->Pe.v, o->emin_iters, cap);
     for (int it = 0; it < o->emin_iters && status == ORC_OK && o->emin_method == 0; ++it) {
         /* dP = D^-1 A P (full product), then the projection: mask to N, row constraint */
         ocsr AP = csr_spgemm(&L->A, &L->Pe);
-        for (int64_t i = 0; i < ne && status == ORC_OK; ++i) {
+#pragma omp parallel for schedule(dynamic, 256)
+        for (int64_t i = 0; i < ne; ++i) {
+            if (ORC_FAILED(status)) continue;
+            const size_t t = (size_t)ORC_TID();
+            double *Gt = G + t * (size_t)cap * cap, *rtt = rt + t * (size_t)cap, *taut = tau + t * (size_t)cap;
+            double *tmpt = tmp + t * (size_t)cap;
             double d = csr_diag(&L->A, i);
             int np;
-            int k = local_system(&L->T, &N, &L->DH, i, G, rt, &np);
+            int k = local_system(&L->T, &N, &L->DH, i, Gt, rtt, &np);
             if (np == 0) continue;
-            double *dp = p;
+            double *dp = p + t * (size_t)cap;
             int64_t ka = AP.rp[i];
             for (int r = 0; r < np; ++r) {
                 int32_t j = N.ci[N.rp[i] + r];
@@ -867,8 +922,8 @@ static int build_level(olevel *L, int lev, const orc_opts *o, ocsr *Anext, ocsr 
                 dp[r] = (ka < AP.rp[i + 1] && AP.ci[ka] == j) ? AP.v[ka] / d : 0.0;
             }
             if (k > 0) {
-                if (house_qr(np, k, G, tau)) { status = ORC_EINFEASIBLE; break; }
-                qr_project_null(np, k, G, tau, dp, tmp);
+                if (house_qr(np, k, Gt, taut)) { ORC_FAIL(status, ORC_EINFEASIBLE); continue; }
+                qr_project_null(np, k, Gt, taut, dp, tmpt);
             }
             double *pi = L->Pe.v + N.rp[i];
             for (int r = 0; r < np; ++r) pi[r] -= o->emin_omega * dp[r];
@@ -976,6 +1031,8 @@ static void sgs_sweep(const ocsr *A, const int32_t *color, int32_t ncol, const d
     for (int dir = 0; dir < 2; ++dir)
         for (int32_t cc = 0; cc < ncol; ++cc) {
             int32_t c = dir == 0 ? cc : ncol - 1 - cc;
+            /* the rows of one colour do not couple: each reads x only at other colours */
+#pragma omp parallel for schedule(static)
             for (int64_t i = 0; i < A->nr; ++i) {
                 if (color[i] != c) continue;
                 double s = b[i], d = 0.0;
