@@ -207,6 +207,19 @@ SPHC_API int sphc_setup(const sphc_csr* A_e, const sphc_csr* D_h, const double* 
                const sphc_opts* opts, void* stream, sphc_handle** out);
 
 /*
+ * Rebuild the hierarchy for a related system: new values A_values[nnz(A_e)] (host or device) on
+ * the pattern given to sphc_setup, e.g. the next time step or nonlinear iterate.  Following the
+ * warm-start remark of Sec. 3, the structural parts are kept (colourings, aggregates, D_H, the
+ * pattern N of P_e), and the rest is recomputed from the new values: A_n, P_n, the constraint
+ * values D_h P_n, the initial guess (the previous P_e projected onto the new row constraints, in
+ * place of P0 or the learned correction), opts.emin_iters energy-minimisation steps, the Galerkin
+ * operators, the coarsest factor and the V-cycle copies.  Synchronises the stream.  Errors:
+ * SPHC_EINVAL (NULL, non-finite value, missing diagonal), SPHC_ENOMEM, SPHC_ECUDA, SPHC_ENUMERIC,
+ * SPHC_EINFEASIBLE.
+ */
+SPHC_API int sphc_setup_update(sphc_handle* h, const double* A_values, void* stream);
+
+/*
  * Solve A_e x = b for nrhs right-hand sides (b and x are nrhs x n_e, row-major, FP64) with
  * V-cycle preconditioned CG: x0 = 0, stop when ||r_k|| <= tol ||b|| (Sec. 6.1).
  * iters[nrhs] and relres[nrhs] (true residual ||b - A x|| / ||b||) may be NULL.

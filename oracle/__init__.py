@@ -58,6 +58,8 @@ def _load():
         P, I64, I32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
         lib.orc_setup.argtypes = [I64, I64, P, P, P, P, P, P, ctypes.POINTER(_Opts), P]
         lib.orc_setup.restype = P
+        lib.orc_update.argtypes = [P, P, ctypes.POINTER(_Opts), P]
+        lib.orc_update.restype = P
         lib.orc_free.argtypes = [P]
         lib.orc_free.restype = None
         lib.orc_num_levels.argtypes = [P]
@@ -167,6 +169,20 @@ class Hierarchy:
         if rc != 0:
             raise KeyError((l, name))
         return out
+
+    def update(self, A_values, max_levels=8, emin_iters=1, max_coarse=1000, emin_omega=0.5, seed=0,
+               power_iters=15, emin_method=0):
+        """Hierarchy of a related system: new values of A on this hierarchy's level-0 pattern, with
+        this hierarchy's aggregates, D_H and pattern kept and its P_e as the initial guess."""
+        av = _c(A_values, np.float64)
+        o = _Opts(max_levels, emin_iters, max_coarse, emin_omega, seed, power_iters, 0, None, 0, 0.0,
+                  int(emin_method))
+        st = ctypes.c_int()
+        t0 = time.perf_counter()
+        ptr = self._lib.orc_update(self._ptr, _p(av), ctypes.byref(o), ctypes.byref(st))
+        h = Hierarchy(ptr, time.perf_counter() - t0)
+        h._keep = (av, self)
+        return h
 
     def vcycle(self, r):
         r = _c(r, np.float64)

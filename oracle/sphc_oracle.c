@@ -708,6 +708,7 @@ void orc_free(ohier *h) {
 }
 
 #define ORC_OK 0
+#define ORC_EINVAL_REUSE -7     /* the related system did not reproduce the previous hierarchy's levels */
 #define ORC_EINVAL -1
 #define ORC_EINFEASIBLE -6
 #define ORC_ENUMERIC -9
@@ -792,12 +793,19 @@ static int emin_projected_cg(const olevel *L, const ocsr *N, double *Pv, int ite
 
 /* one level of Alg. 3 plus the emin iteration; fills L's transfer data and returns the
  * next-level operators through Anext/Dnext/Annext. */
-static int build_level(olevel *L, int lev, const orc_opts *o, ocsr *Anext, ocsr *Dnext, ocsr *Annext) {
+/* prev != NULL: a related system (new values of A on the same patterns, Sec. 3 warm-start
+ * remark).  The structural parts of prev's level are reused (aggregates, D_H, the pattern N),
+ * the initial guess starts from prev's P_e instead of the pattern value, the rest is recomputed. */
+static int build_level(olevel *L, int lev, const orc_opts *o, ocsr *Anext, ocsr *Dnext, ocsr *Annext,
+                       const olevel *prev) {
     uint64_t s = o->seed + 1000ULL * (uint64_t)lev;
     int64_t nv = L->An.nr, ne = L->A.nr;
     /* aggregation on the nodal graph (drop tolerance 0: every structural entry is strong) */
     L->agg = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nv > 0 ? nv : 1));
-    if (lev == 0 && o->agg0) {
+    if (prev) {
+        memcpy(L->agg, prev->agg, sizeof(int32_t) * (size_t)nv);
+        L->nagg = prev->nagg;
+    } else if (lev == 0 && o->agg0) {
         memcpy(L->agg, o->agg0, sizeof(int32_t) * (size_t)nv);
         L->nagg = o->nagg0;
     } else {
@@ -834,12 +842,12 @@ static int build_level(olevel *L, int lev, const orc_opts *o, ocsr *Anext, ocsr 
         L->Pn = Pn;
     }
     /* coarse gradient from the piecewise-constant aggregates */
-    L->DH = coarse_gradient(&L->D, L->agg, L->nagg);
+    L->DH = prev ? csr_copy(&prev->DH) : coarse_gradient(&L->D, L->agg, L->nagg);
     /* Alg. 2: T (with the values r = D_h P_n), N, irreducibility */
     L->T = csr_spgemm(&L->D, &L->Pn);
-    ocsr N = initial_pattern(&L->T, &L->DH);
-    L->n_added = 0;
-    for (int pass = 0; pass < 8; ++pass) {
+    ocsr N = prev ? csr_copy(&prev->Pe) : initial_pattern(&L->T, &L->DH);
+    L->n_added = prev ? prev->n_added : 0;
+    for (int pass = 0; pass < 8 && !prev; ++pass) {
         int64_t bad = 0;
         int64_t added = make_irreducible(&L->DH, &L->T, &N, &bad);
         if (pass == 0) L->n_infeasible0 = bad;
@@ -882,7 +890,7 @@ static int build_level(olevel *L, int lev, const orc_opts *o, ocsr *Anext, ocsr 
         if (np == 0) continue;
         if (k > 0 && house_qr(np, k, Gt, taut)) { ORC_FAIL(status, ORC_EINFEASIBLE); continue; }
         double *pi = L->P0.v + N.rp[i];
-        for (int r = 0; r < np; ++r) pi[r] = o->p0_value;
+        for (int r = 0; r < np; ++r) pi[r] = prev ? prev->Pe.v[N.rp[i] + r] : o->p0_value;
         if (k > 0) {
             /* p += Q R^-T (rt - Gt^T p): Gt^T p = R^T Q^T p (first k entries) */
             memcpy(tmpt, pi, sizeof(double) * (size_t)np);
@@ -975,9 +983,9 @@ static ocsr csr_from(int64_t nr, int64_t nc, const int64_t *rp, const int32_t *c
 }
 
 /* Setup of the whole hierarchy from A_e (ne x ne) and D_h (ne x nv). */
-ohier *orc_setup(int64_t ne, int64_t nv, const int64_t *A_rp, const int32_t *A_ci, const double *A_v,
-                 const int64_t *D_rp, const int32_t *D_ci, const double *D_v, const orc_opts *o,
-                 int *status) {
+static ohier *setup_hier(int64_t ne, int64_t nv, const int64_t *A_rp, const int32_t *A_ci, const double *A_v,
+                         const int64_t *D_rp, const int32_t *D_ci, const double *D_v, const orc_opts *o,
+                         const ohier *prev, int *status) {
     ohier *h = (ohier *)calloc(1, sizeof(ohier));
     olevel *L0 = &h->L[0];
     L0->A = csr_from(ne, ne, A_rp, A_ci, A_v);
@@ -999,7 +1007,9 @@ ohier *orc_setup(int64_t ne, int64_t nv, const int64_t *A_rp, const int32_t *A_c
         int coarsest = (L->A.nr <= o->max_coarse) || (lev + 1 >= o->max_levels) || (L->An.nr <= 1);
         if (coarsest) break;
         ocsr An1, D1, A1;
-        st = build_level(L, lev, o, &A1, &D1, &An1);
+        const olevel *pl = prev && lev + 1 < prev->nlev ? &prev->L[lev] : NULL;
+        if (prev && !pl) { st = ORC_EINVAL_REUSE; break; }
+        st = build_level(L, lev, o, &A1, &D1, &An1, pl);
         if (st != ORC_OK) break;
         if (L->nagg >= L->An.nr) {          /* no coarsening: stop here */
             csr_free(&A1); csr_free(&D1); csr_free(&An1);
@@ -1021,9 +1031,22 @@ ohier *orc_setup(int64_t ne, int64_t nv, const int64_t *A_rp, const int32_t *A_c
             for (int64_t k = C->A.rp[i]; k < C->A.rp[i + 1]; ++k) h->chol[i * n + C->A.ci[k]] = C->A.v[k];
         if (dense_cholesky(n, h->chol)) st = ORC_ENUMERIC;
     }
+    if (st == ORC_OK && prev && h->nlev != prev->nlev) st = ORC_EINVAL_REUSE;
     h->status = st;
     if (status) *status = st;
     return h;
+}
+
+ohier *orc_setup(int64_t ne, int64_t nv, const int64_t *A_rp, const int32_t *A_ci, const double *A_v,
+                 const int64_t *D_rp, const int32_t *D_ci, const double *D_v, const orc_opts *o,
+                 int *status) {
+    return setup_hier(ne, nv, A_rp, A_ci, A_v, D_rp, D_ci, D_v, o, NULL, status);
+}
+
+/* The hierarchy of a related system: new values A_v on prev's level-0 pattern (see build_level). */
+ohier *orc_update(const ohier *prev, const double *A_v, const orc_opts *o, int *status) {
+    const olevel *P0 = &prev->L[0];
+    return setup_hier(P0->A.nr, P0->D.nc, P0->A.rp, P0->A.ci, A_v, P0->D.rp, P0->D.ci, P0->D.v, o, prev, status);
 }
 
 /* ------------------------------------------------------------------ solve */

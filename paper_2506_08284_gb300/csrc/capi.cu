@@ -289,6 +289,56 @@ int sphc_setup(const sphc_csr* A_e, const sphc_csr* D_h, const double* coords, c
     return SPHC_OK;
 }
 
+int sphc_setup_update(sphc_handle* h, const double* A_values, void* stream) {
+    if (!h || !A_values) {
+        set_error("sphc_setup_update: NULL argument");
+        return SPHC_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    Hierarchy& H = h->H;
+    const sphc_opts& o = H.opts;
+    auto t0 = std::chrono::steady_clock::now();
+    Level& L0 = H.L[0];
+    if (L0.A.nnz > 0) SPHC_CK(cudaMemcpyAsync(L0.A.v.p, A_values, sizeof(double) * L0.A.nnz, cudaMemcpyDefault, s));
+    SPHC_TRY(validate(L0.A, 0, "A_e", s));
+    Profiler* prof = H.prof.on ? &H.prof : nullptr;
+    {
+        Section sec(prof, "update_nodal_op", s);
+        SPHC_TRY(spgemm(L0.A, L0.D, L0.AD, s));
+        SPHC_TRY(spgemm_sym(L0.Dt, L0.AD, L0.An, s));
+    }
+    for (int lev = 0; lev + 1 < H.nlev; ++lev) {
+        Level& L = H.L[lev];
+        DCSR A1, D1, An1;
+        DBuf<double> X1;
+        Section sec(prof, "update_levels", s);
+        SPHC_TRY(build_level(L, lev, o, A1, D1, An1, X1, H.mlp.p, prof, s, true));
+        H.L[lev + 1].A = std::move(A1);
+        H.L[lev + 1].An = std::move(An1);
+    }
+    {
+        Section sec(prof, "update_coarse_inverse", s);
+        const int lev = H.nlev - 1;
+        SPHC_TRY(coarse_inverse(H.L[lev].A, H.coarse_inv, false, s));
+        if (o.vcycle_fp32) SPHC_TRY(coarse_inverse(H.L[lev].An, H.coarse_inv_n, true, s));
+    }
+    // the V-cycle copies are rebuilt; the captured CG graphs refer to the old buffers
+    SPHC_CK(cudaStreamSynchronize(s));
+    if (H.cg_exec) cudaGraphExecDestroy(H.cg_exec);
+    if (H.cg_graph) cudaGraphDestroy(H.cg_graph);
+    H.cg_exec = nullptr;
+    H.cg_graph = nullptr;
+    H.blk.reset();
+    {
+        Section sec(prof, "update_vcycle_ops", s);
+        SPHC_TRY(build_vcycle_ops(H, s));
+        if (o.autotune) SPHC_TRY(autotune_vcycle(H, s));
+    }
+    SPHC_CK(cudaStreamSynchronize(s));
+    H.setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return SPHC_OK;
+}
+
 int sphc_solve(sphc_handle* h, const double* b, double* x, int nrhs, double tol, void* stream, int* iters,
                double* relres) {
     if (!h || !b || !x || nrhs < 1 || !(tol > 0.0)) {

@@ -1089,9 +1089,10 @@ __device__ void refine_solve(LocalSys& S, int k, int np) {
 }
 
 // least-norm initial guess P0_i = G~ (G~^T G~)^-1 r~_i
+template <typename DT>
 __global__ void __launch_bounds__(LOC_WARPS * 32)
 k_p0(int64_t ne, const int32_t* rows, const int64_t* trp, const int32_t* tci, const double* tv, const int64_t* nrp,
-     const int32_t* nci, const int64_t* hrp, const int32_t* hci, const double* hv, const float* d, double* p0,
+     const int32_t* nci, const int64_t* hrp, const int32_t* hci, const double* hv, const DT* d, double* p0,
      int* fail) {
     extern __shared__ unsigned char smem_raw[];
     int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1351,10 +1352,11 @@ __device__ __forceinline__ void cache_get(const RowCache& C, int64_t i, RowSys& 
 // P0 of every small row: the point of {G~^T p = r~} nearest to d (d null: 0), p = d + G~ z with
 // (G~^T G~) z = r~ - G~^T d.  Rows too large for a thread are appended to `big`.  Every row's
 // factored system (or k = -1) goes to the cache.
+template <typename DT>
 __global__ void __launch_bounds__(128)
 k_p0_rows(int64_t ne, const int64_t* __restrict__ trp, const int32_t* __restrict__ tci, const double* __restrict__ tv,
           const int64_t* __restrict__ nrp, const int32_t* __restrict__ nci, const int64_t* __restrict__ hrp,
-          const int32_t* __restrict__ hci, const double* __restrict__ hv, const float* __restrict__ d,
+          const int32_t* __restrict__ hci, const double* __restrict__ hv, const DT* __restrict__ d,
           double* __restrict__ p0, int* fail, int32_t* big, int* nbig, RowCache cache) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ne) return;
@@ -1794,11 +1796,17 @@ static int coarse_coords(const Level& L, DBuf<double>& Xc, cudaStream_t s) {
 static std::string lev_name(const char* what, int lev) { return std::string(what) + "_l" + std::to_string(lev); }
 
 int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext, DCSR& Annext, DBuf<double>& Xnext,
-                const float* mlp_params, Profiler* prof, cudaStream_t s) {
+                const float* mlp_params, Profiler* prof, cudaStream_t s, bool reuse) {
     uint64_t seed = o.seed + 1000ULL * (uint64_t)lev;
     int64_t nv = L.An.nr, ne = L.A.nr;
+    // With reuse (a related system: new values of A on the same pattern, paper Sec. 3 warm-start
+    // remark) the structural steps are kept: the aggregates, D_H and the pattern N depend only on
+    // the patterns of A and D; P_n, T, P0 and everything after are recomputed, P0 starting from
+    // the previous P_e projected onto the new constraints.
+    DBuf<double> warm;
+    if (reuse) warm = std::move(L.Pe.v);
     // aggregation on the structural nodal graph (drop tolerance 0)
-    {
+    if (!reuse) {
         Section sec(prof, lev_name("setup_aggregate", lev).c_str(), s);
         SPHC_TRY(aggregate(L.An, seed + 1, L.agg, &L.nagg, s));
     }
@@ -1826,7 +1834,7 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
     L.n_rows_unsmoothed = hf[0];
     delete sec_pn;
     // coarse gradient from the tentative aggregates
-    {
+    if (!reuse) {
         Section sec(prof, lev_name("setup_DH", lev).c_str(), s);
         SPHC_TRY(coarse_gradient(L.D, L.Dt, L.agg.p, L.nagg, L.DH, s));
     }
@@ -1845,8 +1853,8 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
     SPHC_TRY(pctl.alloc(2, s));
     int hs[8] = {0};
     int npbig = 0;
-    L.n_added = 0;
-    for (int pass = 0;; ++pass) {
+    if (!reuse) L.n_added = 0;
+    for (int pass = 0; !reuse; ++pass) {
         // counts of N_i and disconnected rows against the current D_H; rows with more than
         // PT_K coarse nodes go to the warp-per-row kernel through a list (st[6] counts them)
         SPHC_TRY(transpose(L.DH, DHt, s));
@@ -1899,7 +1907,8 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
         L.n_added += nu;
     }
     SPHC_TRY(max_row_length(L.T.rp.p, ne, s, &L.max_m));
-    int64_t nnzN = 0;
+    int64_t nnzN = reuse ? L.P0.nnz : 0;
+    if (!reuse) {
     SPHC_TRY(L.P0.alloc(ne, L.DH.nr, 0, s));
     SPHC_TRY(exclusive_scan_i64(ncnt.p, L.P0.rp.p, ne, s, &nnzN));
     L.P0.nnz = nnzN;
@@ -1914,16 +1923,17 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
         SPHC_LAUNCH(k_pattern<<<grid_for(npbig, PAT_WARPS), PAT_WARPS * 32, 0, s>>>(L.T.rp.p, L.T.ci.p, npbig, pbig.p,
                                                                       DHt.rp.p, DHt.ci.p, L.DH.rp.p, L.DH.ci.p, 1,
                                                                       nullptr, L.P0.rp.p, L.P0.ci.p, st.p, nullptr));
+    }
     delete sec_pat;
     // learned warm start: the MLP correction of every pattern entry (its features do not depend
     // on P0), passed to the P0 kernel, which projects it onto the row constraints
-    {
+    if (!reuse) {
         Section sec(prof, lev_name("setup_coords", lev).c_str(), s);
         SPHC_TRY(coarse_coords(L, Xnext, s));
     }
     int emin_iters = o.emin_iters;
     DBuf<float> corr;
-    if (o.learned) {
+    if (o.learned && !reuse) {
         Section sec(prof, lev_name("setup_learned", lev).c_str(), s);
         if (!mlp_params) { set_error("learned warm start without MLP parameters"); return SPHC_EINVAL; }
         if (!L.X.p || !Xnext.p) {
@@ -1944,7 +1954,8 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
     if (ne > 0) SPHC_LAUNCH(k_ls_hist<<<1024, 256, 0, s>>>(L.P0.rp.p, L.T.rp.p, ne, L.hist.p));
     SPHC_TRY(st.zero(s));
     size_t sm = sizeof(LocalSys) * LOC_WARPS;
-    SPHC_CK(cudaFuncSetAttribute(k_p0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    SPHC_CK(cudaFuncSetAttribute(k_p0<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    SPHC_CK(cudaFuncSetAttribute(k_p0<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     SPHC_CK(cudaFuncSetAttribute(k_emin, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     // rows too large for the thread-per-row kernels (listed by k_p0_rows, reused by every step)
     DBuf<int32_t> big;
@@ -1962,16 +1973,30 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
     SPHC_TRY(cL.alloc(TL * (ne > 0 ? ne : 1), s));
     RowCache cache{cpm.p, ck.p, cL.p, ne};
     if (ne > 0) {
-        SPHC_LAUNCH(k_p0_rows<<<grid_for(ne, 128), 128, 0, s>>>(ne, L.T.rp.p, L.T.ci.p, L.T.v.p, L.P0.rp.p, L.P0.ci.p,
-                                                               L.DH.rp.p, L.DH.ci.p, L.DH.v.p, corr.p, L.P0.v.p, st.p,
-                                                               big.p, nbig.p, cache));
+        // P0: the point of each row's constraint set nearest to the warm start (0: least-norm; the
+        // MLP correction; or, with reuse, the previous P_e)
+        if (reuse)
+            SPHC_LAUNCH(k_p0_rows<double><<<grid_for(ne, 128), 128, 0, s>>>(
+                ne, L.T.rp.p, L.T.ci.p, L.T.v.p, L.P0.rp.p, L.P0.ci.p, L.DH.rp.p, L.DH.ci.p, L.DH.v.p, warm.p, L.P0.v.p,
+                st.p, big.p, nbig.p, cache));
+        else
+            SPHC_LAUNCH(k_p0_rows<float><<<grid_for(ne, 128), 128, 0, s>>>(
+                ne, L.T.rp.p, L.T.ci.p, L.T.v.p, L.P0.rp.p, L.P0.ci.p, L.DH.rp.p, L.DH.ci.p, L.DH.v.p, corr.p, L.P0.v.p,
+                st.p, big.p, nbig.p, cache));
         SPHC_CK(cudaMemcpyAsync(&hbig, nbig.p, sizeof(int), cudaMemcpyDeviceToHost, s));
         SPHC_CK(cudaStreamSynchronize(s));
-        if (hbig > 0)
-            SPHC_LAUNCH(k_p0<<<grid_for(hbig, LOC_WARPS), LOC_WARPS * 32, sm, s>>>(hbig, big.p, L.T.rp.p, L.T.ci.p, L.T.v.p,
-                                                                        L.P0.rp.p, L.P0.ci.p, L.DH.rp.p, L.DH.ci.p,
-                                                                        L.DH.v.p, corr.p, L.P0.v.p, st.p));
+        if (hbig > 0) {
+            if (reuse)
+                SPHC_LAUNCH(k_p0<double><<<grid_for(hbig, LOC_WARPS), LOC_WARPS * 32, sm, s>>>(
+                    hbig, big.p, L.T.rp.p, L.T.ci.p, L.T.v.p, L.P0.rp.p, L.P0.ci.p, L.DH.rp.p, L.DH.ci.p, L.DH.v.p,
+                    warm.p, L.P0.v.p, st.p));
+            else
+                SPHC_LAUNCH(k_p0<float><<<grid_for(hbig, LOC_WARPS), LOC_WARPS * 32, sm, s>>>(
+                    hbig, big.p, L.T.rp.p, L.T.ci.p, L.T.v.p, L.P0.rp.p, L.P0.ci.p, L.DH.rp.p, L.DH.ci.p, L.DH.v.p,
+                    corr.p, L.P0.v.p, st.p));
+        }
     }
+    warm = DBuf<double>();
     delete sec_p0;
     corr = DBuf<float>();
     Section* sec_cp = new Section(prof, lev_name("setup_copy_P0", lev).c_str(), s);

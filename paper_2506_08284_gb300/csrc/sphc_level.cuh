@@ -137,8 +137,9 @@ struct Profiler {
     ~Profiler();
 };
 
+// reuse: keep L's aggregates, D_H and pattern, recompute the values (warm start from L.Pe)
 int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext, DCSR& Annext, DBuf<double>& Xnext,
-                const float* mlp_params, Profiler* prof, cudaStream_t s);
+                const float* mlp_params, Profiler* prof, cudaStream_t s, bool reuse = false);
 int level_features(const Level& L, const DBuf<double>& Xc, int lev, float* F, cudaStream_t s);
 int level_prediction(const Level& L, const DBuf<double>& Xc, int lev, const float* params_dev, float* out,
                      cudaStream_t s);

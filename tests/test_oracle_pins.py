@@ -185,3 +185,44 @@ def test_projected_cg_energy_minimisation():
         D, Pn = h.matrix(0, "D").to_scipy(), h.matrix(0, "Pn").to_scipy()
         rhs = D @ Pn
         assert abs(Pe @ DH - rhs).max() <= bound * max(1.0, abs(rhs).max())
+
+
+# ---------------------------------------------------------------- setup reuse (Sec. 3 warm start)
+def _related(seed_sigma):
+    return meshgen.MeshSpec(8, jitter=0.2, seed_jitter=3, sigma="lognormal", sigma_in=1.0, seed_sigma=seed_sigma)
+
+
+def test_update_with_unchanged_values_continues_the_iteration():
+    """Updating a hierarchy with the values it was built from keeps P_e feasible, so the
+    projection of the warm start is the identity (to rounding) and one more step of eq. (9)
+    follows: the result equals a fresh setup with twice the steps."""
+    p = meshgen.generate(_related(4))
+    h1 = oracle.setup_problem(p, max_coarse=100, emin_iters=1)
+    hu = h1.update(p.A_val, max_coarse=100, emin_iters=1)
+    h2 = oracle.setup_problem(p, max_coarse=100, emin_iters=2)
+    assert hu.status == 0 and hu.nlevels == h2.nlevels
+    for l in range(h2.nlevels - 1):
+        a, b = hu.matrix(l, "Pe"), h2.matrix(l, "Pe")
+        np.testing.assert_array_equal(a.col, b.col)
+        assert np.abs(a.val - b.val).max() <= 1e-12 * np.abs(b.val).max()
+
+
+def test_update_to_a_related_system():
+    """New conductivities on the same mesh: the structure is kept, the commuting relation holds
+    on every level, and the updated hierarchy solves the new system."""
+    p, q = meshgen.generate(_related(4)), meshgen.generate(_related(5))
+    np.testing.assert_array_equal(p.A_col, q.A_col)
+    h = oracle.setup_problem(p, max_coarse=100)
+    hu = h.update(q.A_val, max_coarse=100)
+    assert hu.status == 0 and hu.nlevels == h.nlevels
+    for l in range(hu.nlevels - 1):
+        np.testing.assert_array_equal(hu.ivec(l, "agg"), h.ivec(l, "agg"))
+        np.testing.assert_array_equal(hu.matrix(l, "DH").col, h.matrix(l, "DH").col)
+        Pe, DH = hu.matrix(l, "Pe").to_scipy(), hu.matrix(l, "DH").to_scipy()
+        D, Pn = hu.matrix(l, "D").to_scipy(), hu.matrix(l, "Pn").to_scipy()
+        rhs = D @ Pn
+        assert abs(Pe @ DH - rhs).max() <= 1e-12 * max(1.0, abs(rhs).max())
+    b = meshgen.rhs(3, q.n_edges)
+    r = hu.solve(b)
+    fresh = oracle.setup_problem(q, max_coarse=100).solve(b)
+    assert r["status"] == 0 and r["iters"] <= fresh["iters"] + 2
