@@ -246,9 +246,10 @@ def sweep_traffic():
             if ":" in line and not line.startswith("#"):
                 k, v = line.split(":", 1)
                 fields[k.strip()] = v.strip()
-        src = os.path.join(ROOT, "paper_2506_08284_gb300", "csrc", "solve.cu")
-        digest = hashlib.sha1(open(src, "rb").read()).hexdigest()
-        if fields.get("solve_cu_sha1") != digest:
+        h = hashlib.sha1()
+        for name in ("sell.cuh", "solve.cu"):            # the sweep kernel and its helpers
+            h.update(open(os.path.join(ROOT, "paper_2506_08284_gb300", "csrc", name), "rb").read())
+        if fields.get("sweep_src_sha1") != h.hexdigest():
             return None
         return float(fields["dram_bytes_per_sweep"])
     except Exception:
