@@ -1385,10 +1385,13 @@ k_p0_rows(int64_t ne, const int64_t* __restrict__ trp, const int32_t* __restrict
 // double, or float for the FP32 accumulation of opts.emin_fp32 (the projection stays FP64).
 constexpr int PP_WARPS = 4;
 constexpr int PP_ILP = 4;
+// P is read in the accumulation type: the FP32 mode gets an FP32 copy of P's values, converted once
+// per step, because on this GPU a double-to-float conversion per pair would run on the same thin
+// FP64 pipe as an FP64 FMA (ncu: 82 % FP64-pipe activity with per-pair conversions).
 template <typename Acc>
 __global__ void __launch_bounds__(PP_WARPS * 32)
 k_emin_pp(int64_t ne, const int64_t* __restrict__ arp, const int32_t* __restrict__ aci, const double* __restrict__ av,
-          const int64_t* __restrict__ nrp, const int32_t* __restrict__ nci, const double* __restrict__ P,
+          const int64_t* __restrict__ nrp, const int32_t* __restrict__ nci, const Acc* __restrict__ P,
           const int8_t* __restrict__ ck, Acc* __restrict__ w) {
     const int lane = threadIdx.x & 31;
     const int64_t i = (int64_t)blockIdx.x * PP_WARPS + (threadIdx.x >> 5);
@@ -1408,17 +1411,18 @@ k_emin_pp(int64_t ne, const int64_t* __restrict__ arp, const int32_t* __restrict
     for (int64_t kb = a0 + sub; kb < a1; kb += (int64_t)PP_ILP * L) {
         int64_t lo[PP_ILP];
         int len[PP_ILP];
-        double a[PP_ILP];
+        Acc a[PP_ILP];
 #pragma unroll
         for (int j = 0; j < PP_ILP; ++j) {
             const int64_t ka = kb + (int64_t)j * L;
             lo[j] = 0;
             len[j] = 0;
-            a[j] = 0.0;
+            a[j] = Acc(0);
             if (ka < a1) {
                 const int32_t f = aci[ka];
-                a[j] = av[ka];
-                if (f == (int32_t)i) { aii = a[j]; has_diag = true; }
+                const double af = av[ka];
+                a[j] = (Acc)af;
+                if (f == (int32_t)i) { aii = af; has_diag = true; }
                 lo[j] = nrp[f];
                 len[j] = (int)(nrp[f + 1] - lo[j]);
             }
@@ -1450,14 +1454,15 @@ k_emin_pp(int64_t ne, const int64_t* __restrict__ arp, const int32_t* __restrict
         }
 #pragma unroll
         for (int j = 0; j < PP_ILP; ++j)
-            if (len[j] > 0 && nci[lo[j] + pos[j]] == key) acc += (Acc)a[j] * (Acc)P[lo[j] + pos[j]];
+            if (len[j] > 0 && nci[lo[j] + pos[j]] == key) acc += a[j] * P[lo[j] + pos[j]];
     }
     // a_ii from the lane that met the diagonal entry
     const unsigned dm = __ballot_sync(0xffffffffu, has_diag);
     aii = __shfl_sync(0xffffffffu, aii, dm ? __ffs(dm) - 1 : 0);
     if (!dm) aii = 1.0;
     for (int d = L >> 1; d > 0; d >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, d);
-    if (owner && sub == 0) w[n0 + t] = (Acc)((double)acc / aii);
+    const Acc inv = (Acc)(1.0 / aii);
+    if (owner && sub == 0) w[n0 + t] = acc * inv;
 }
 
 // projection and update of eq. (9) for every small row: dp = w - G~ (G~^T G~)^-1 G~^T w,
@@ -2020,11 +2025,17 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
     }
     // projected gradient g = Pi D^-1 (A V)|_N of values V on the pattern (small rows by the product
     // and thread-per-row projection kernels, large rows by k_emin)
+    DBuf<float> P32;                            // FP32 copy of the values the product reads
+    if (o.emin_fp32 && emin_iters > 0) SPHC_TRY(P32.alloc(nnzN, s));
+    auto to_f32 = [&](const double* V) {
+        if (nnzN > 0) SPHC_LAUNCH(k_to_float<<<grid_for(nnzN, 256), 256, 0, s>>>(V, nnzN, P32.p));
+    };
     auto proj_grad = [&](const double* V, double* g) -> int {
         const int gpp = grid_for(ne, PP_WARPS);
         if (o.emin_fp32) {
+            to_f32(V);
             SPHC_LAUNCH(k_emin_pp<float><<<gpp, PP_WARPS * 32, 0, s>>>(ne, L.A.rp.p, L.A.ci.p, L.A.v.p, L.Pe.rp.p,
-                                                                      L.Pe.ci.p, V, cache.k, W32.p));
+                                                                      L.Pe.ci.p, P32.p, cache.k, W32.p));
             SPHC_LAUNCH(k_emin_rows<float><<<grid_for(ne, 128), 128, 0, s>>>(ne, L.Pe.rp.p, W32.p, V, g, 0.0, cache, 1));
         } else {
             SPHC_LAUNCH(k_emin_pp<double><<<gpp, PP_WARPS * 32, 0, s>>>(ne, L.A.rp.p, L.A.ci.p, L.A.v.p, L.Pe.rp.p,
@@ -2085,9 +2096,11 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
             const int gpp = grid_for(ne, PP_WARPS);
             {
                 Section sp(prof, lev_name("emin_product", lev).c_str(), s);
-                if (o.emin_fp32)
+                if (o.emin_fp32) {
+                    to_f32(L.Pe.v.p);
                     SPHC_LAUNCH(k_emin_pp<float><<<gpp, PP_WARPS * 32, 0, s>>>(ne, L.A.rp.p, L.A.ci.p, L.A.v.p, L.Pe.rp.p,
-                                                                           L.Pe.ci.p, L.Pe.v.p, cache.k, W32.p));
+                                                                           L.Pe.ci.p, P32.p, cache.k, W32.p));
+                }
                 else
                     SPHC_LAUNCH(k_emin_pp<double><<<gpp, PP_WARPS * 32, 0, s>>>(ne, L.A.rp.p, L.A.ci.p, L.A.v.p, L.Pe.rp.p,
                                                                             L.Pe.ci.p, L.Pe.v.p, cache.k, W.p));
