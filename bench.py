@@ -115,6 +115,57 @@ def run_paper3d(args, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def run_learned96(args, rank, local):
+    """Config 4: the learned warm start on the 96^3 test mesh (jitter 0.2h, log-normal sigma) against
+    plain energy minimisation with 1 and 4 steps: setup time, CG iterations (FP32 V-cycle),
+    A-energy trace(P_e^T A P_e) per level and the V-cycle convergence factor (30 stationary
+    iterations from a random x with b = 0, geometric mean of the last 10 A-norm ratios)."""
+    import torch
+
+    import meshgen
+    import paper_2506_08284_gb300 as pkg
+    from paper_2506_08284_gb300 import learned
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    spec, seed = meshgen.workload("kuhn96")
+    p = meshgen.generate(spec, nthreads=min(os.cpu_count() or 1, 32))
+    dev = lambda a: torch.from_numpy(a).cuda()
+    A = (p.n_edges, p.n_edges, dev(p.A_rowptr), dev(p.A_col), dev(p.A_val))
+    D = (p.n_edges, p.n_nodes, dev(p.D_rowptr), dev(p.D_col), dev(p.D_val))
+    coords, sig, b = dev(p.coords), dev(p.sigma_edge), dev(meshgen.rhs(seed, p.n_edges))
+    w = learned.load_weights()
+    arms = [("plain, 1 step", dict(emin_iters=1)), ("plain, 4 steps", dict(emin_iters=4)),
+            ("plain, projected CG 2 steps", dict(emin_method=1, emin_iters=2)),
+            ("learned, 0 steps", dict(learned=1, learned_emin_iters=0, mlp_params=w)),
+            ("learned, 1 step", dict(learned=1, learned_emin_iters=1, mlp_params=w))]
+    rows = []
+    for name, kw in arms:
+        o = pkg.sphc.default_opts(vcycle_fp32=1, emin_fp32=1, **kw)
+        for rep in range(2):                      # the second setup is timed (memory pool warm)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            h = pkg.sphc.setup(A, D, coords, sig, o, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            setup_ms = e0.elapsed_time(e1)
+            if rep == 0:
+                h.destroy()
+        x = torch.zeros_like(b)
+        rc, it, rr = h.solve(b, x, stream=stream)
+        st = h.stats()
+        energies = [h.energy(l, stream=stream) for l in range(st["n_levels"] - 1)]
+        factor = h.vcycle_factor(30, 10, seed=1, stream=stream)
+        rows.append({"arm": name, "setup_ms": setup_ms, "solve_ms": st["solve_ms"], "iters": it[0], "status": rc,
+                     "energy_per_level": energies, "vcycle_factor": factor})
+        h.destroy()
+    line = {"metric": "learned warm start vs plain energy minimisation (context)", "impl": "mine",
+            "config": {"workload": "kuhn96: 96^3-cell Kuhn-tet cube, 6,110,496 unknowns, +-0.2h jitter, log10 sigma ~ "
+                                   "N(0, 2^2) clipped to [-6, 2]"}, "rows": rows}
+    print(json.dumps(line), flush=True)
+
+
 def run_batch64(args, rank, world, local):
     """Config 5: all 64 systems set up (concurrently, host threads on their own streams) and solved
     for 4 right-hand sides each through one CUDA graph per right-hand side whose branches run every
@@ -420,6 +471,9 @@ def main():
         return
     if args.workload == "paper3d":
         run_paper3d(args, rank, local)
+        return
+    if args.workload == "learned96":
+        run_learned96(args, rank, local)
         return
 
     import numpy as np

@@ -244,6 +244,17 @@ SPHC_API int sphc_solve(sphc_handle* h, const double* b, double* x, int nrhs, do
 SPHC_API int sphc_cond_estimate(sphc_handle* h, int max_steps, double* kappa, double* norm_b, double* norm_binv,
                                 void* stream);
 
+/* Convergence factor of the V-cycle as a stationary iteration: x <- x + M^-1 (b - A_e x) with
+ * b = 0, from x uniform in [-1, 1] (splitmix64(seed, i)); *factor = geometric mean of the ratios
+ * ||x_k||_A / ||x_{k-1}||_A over the last `tail` of `iters` iterations.  Not part of the paper; the
+ * yardstick of the learned warm start.  Errors: SPHC_EINVAL, SPHC_ENOMEM, SPHC_ECUDA. */
+SPHC_API int sphc_vcycle_factor(sphc_handle* h, int iters, int tail, uint64_t seed, double* factor, void* stream);
+
+/* A-energy trace(P_e^T A_l P_e) = sum_j P_:j^T A_l P_:j of level `level`'s edge prolongator, the
+ * objective of the energy minimisation (Sec. 3, eq. (7)).  Synchronises the stream.  Errors:
+ * SPHC_EINVAL (no prolongator on that level), SPHC_ENOMEM, SPHC_ECUDA. */
+SPHC_API int sphc_prolongator_energy(const sphc_handle* h, int level, double* energy, void* stream);
+
 /* Apply one V-cycle z = M^-1 r (FP64 in and out, n_e entries) with the handle's precision. */
 SPHC_API int sphc_vcycle(sphc_handle* h, const double* r, double* z, void* stream);
 

@@ -93,6 +93,115 @@ int abs_stats(const double* a, int64_t n, DBuf<double>& pmax, DBuf<int64_t>& par
 
 }  // namespace
 
+namespace {
+__global__ void k_uniform_pm1(double* x, int64_t n, uint64_t seed) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] = 2.0 * ((double)(splitmix64(seed, (uint64_t)i) >> 11) * (1.0 / 9007199254740992.0)) - 1.0;
+}
+__global__ void k_add_to(const double* __restrict__ z, double* __restrict__ x, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] += z[i];
+}
+__global__ void k_negate(double* a, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = -a[i];
+}
+}  // namespace
+
+// V-cycle convergence factor: the stationary iteration x <- x + M^-1 (b - A x) with b = 0 from a
+// seeded random x; ratios of successive A-norms ||x_k||_A / ||x_{k-1}||_A, geometric mean of the
+// last `tail` of `iters` iterations.
+extern "C" int sphc_vcycle_factor(sphc_handle* h, int iters, int tail, uint64_t seed, double* factor, void* stream) {
+    if (!h || !factor || iters < 2 || tail < 1 || tail > iters) {
+        set_error("sphc_vcycle_factor: invalid argument");
+        return SPHC_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    Hierarchy& H = h->H;
+    const DCSR& A = H.L[0].A;
+    const int64_t n = A.nr;
+    DBuf<double> x, r, z, sc;
+    for (DBuf<double>* b : {&x, &r, &z}) SPHC_TRY(b->alloc(n, s));
+    SPHC_TRY(sc.alloc(1, s));
+    SPHC_LAUNCH(k_uniform_pm1<<<grid_for(n, 256), 256, 0, s>>>(x.p, n, seed));
+    auto anorm = [&](double* out) -> int {
+        SPHC_TRY(spmv64(A, x.p, r.p, s));
+        SPHC_TRY(dot64(x.p, r.p, n, sc.p, s));
+        double v = 0.0;
+        SPHC_CK(cudaMemcpyAsync(&v, sc.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+        SPHC_CK(cudaStreamSynchronize(s));
+        *out = sqrt(v > 0.0 ? v : 0.0);
+        return SPHC_OK;
+    };
+    double e_prev = 0.0, logsum = 0.0;
+    SPHC_TRY(anorm(&e_prev));
+    for (int k = 1; k <= iters; ++k) {
+        // r = -A x (anorm left A x in r), z = M^-1 r, x += z
+        SPHC_LAUNCH(k_negate<<<grid_for(n, 256), 256, 0, s>>>(r.p, n));
+        SPHC_TRY(apply_vcycle_user(H, r.p, z.p, s));
+        SPHC_LAUNCH(k_add_to<<<grid_for(n, 256), 256, 0, s>>>(z.p, x.p, n));
+        double e = 0.0;
+        SPHC_TRY(anorm(&e));
+        if (k > iters - tail) logsum += log(e_prev > 0.0 ? e / e_prev : 1.0);
+        e_prev = e;
+    }
+    *factor = exp(logsum / tail);
+    SPHC_CK(cudaGetLastError());
+    return SPHC_OK;
+}
+
+namespace {
+// per row i: e_i = sum_t P_it (A P)_{i, N_i(t)} (warp per row; lanes own pattern entries; a
+// binary search of column N_i(t) in every P row f of A's row i)
+__global__ void k_row_energy(int64_t ne, const int64_t* __restrict__ arp, const int32_t* __restrict__ aci,
+                             const double* __restrict__ av, const int64_t* __restrict__ prp,
+                             const int32_t* __restrict__ pci, const double* __restrict__ pv, double* __restrict__ e) {
+    const int lane = threadIdx.x & 31;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= ne) return;
+    const int64_t n0 = prp[i], n1 = prp[i + 1];
+    double sum = 0.0;
+    for (int64_t q = n0 + lane; q < n1; q += 32) {
+        const int32_t key = pci[q];
+        double ap = 0.0;
+        for (int64_t ka = arp[i]; ka < arp[i + 1]; ++ka) {
+            const int32_t f = aci[ka];
+            int64_t lo = prp[f], hi = prp[f + 1];
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (pci[mid] < key) lo = mid + 1; else hi = mid;
+            }
+            if (lo < prp[f + 1] && pci[lo] == key) ap += av[ka] * pv[lo];
+        }
+        sum += pv[q] * ap;
+    }
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) e[i] = sum;
+}
+}  // namespace
+
+// trace(P_e^T A P_e) of level `level` (the A-energy the energy minimisation of Sec. 3 reduces)
+extern "C" int sphc_prolongator_energy(const sphc_handle* h, int level, double* energy, void* stream) {
+    if (!h || !energy || level < 0 || level + 1 >= h->H.nlev || !h->H.L[level].has_transfer) {
+        set_error("sphc_prolongator_energy: level %d has no prolongator", level);
+        return SPHC_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const Level& L = h->H.L[level];
+    const int64_t n = L.A.nr;
+    DBuf<double> e, sc, ones;
+    SPHC_TRY(e.alloc(n, s));
+    SPHC_TRY(ones.alloc(n, s));
+    SPHC_TRY(sc.alloc(1, s));
+    SPHC_LAUNCH(k_row_energy<<<grid_for(n * 32, 256), 256, 0, s>>>(n, L.A.rp.p, L.A.ci.p, L.A.v.p, L.Pe.rp.p, L.Pe.ci.p,
+                                                                   L.Pe.v.p, e.p));
+    SPHC_LAUNCH(k_fill<<<grid_for(n, 256), 256, 0, s>>>(ones.p, n, 1.0));
+    SPHC_TRY(dot64(e.p, ones.p, n, sc.p, s));
+    SPHC_CK(cudaMemcpyAsync(energy, sc.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+    SPHC_CK(cudaStreamSynchronize(s));
+    return SPHC_OK;
+}
+
 extern "C" int sphc_cond_estimate(sphc_handle* h, int max_steps, double* kappa, double* norm_b, double* norm_binv,
                                   void* stream) {
     if (!h || max_steps < 1) {

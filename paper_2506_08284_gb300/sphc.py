@@ -82,7 +82,7 @@ EXPORTED = ["sphc_default_opts", "sphc_setup", "sphc_solve", "sphc_vcycle", "sph
             "sphc_get_profile", "sphc_launch_count", "sphc_relres_noalloc", "sphc_default_train_opts",
             "sphc_mlp_train", "sphc_mlp_predict", "sphc_mlp_gradient", "sphc_export_features",
             "sphc_setup_batched", "sphc_solve_batched", "sphc_batch_destroy", "sphc_trim_memory",
-            "sphc_memory_usage", "sphc_mlp_predict_level", "sphc_cond_estimate", "sphc_setup_update"]
+            "sphc_memory_usage", "sphc_mlp_predict_level", "sphc_cond_estimate", "sphc_setup_update", "sphc_vcycle_factor", "sphc_prolongator_energy"]
 
 _lib = None
 
@@ -118,6 +118,8 @@ def load(path: str | None = None):
     lib.sphc_mlp_predict_level.argtypes = [P, I, P, P, P]
     lib.sphc_cond_estimate.argtypes = [P, I, P, P, P, P]
     lib.sphc_setup_update.argtypes = [P, P, P]
+    lib.sphc_vcycle_factor.argtypes = [P, I, I, ctypes.c_uint64, P, P]
+    lib.sphc_prolongator_energy.argtypes = [P, I, P, P]
     lib.sphc_setup_batched.argtypes = [I, P, P, P, P, ctypes.POINTER(sphc_opts), P, ctypes.POINTER(P)]
     lib.sphc_solve_batched.argtypes = [P, P, P, I, ctypes.c_double, P, P, P]
     lib.sphc_batch_destroy.argtypes = [P]
@@ -228,6 +230,19 @@ class Handle:
         """Rebuild for new values of A_e on the same pattern (sphc_setup_update)."""
         _require_f64("A_values", A_values, self.level_info(0)["nnz_A"])
         _check(load().sphc_setup_update(self._ptr, _ptr(A_values), _stream(stream)))
+
+    def vcycle_factor(self, iters=30, tail=10, seed=1, stream=None):
+        """Geometric-mean A-norm contraction of the V-cycle as a stationary iteration (b = 0)."""
+        f = ctypes.c_double()
+        _check(load().sphc_vcycle_factor(self._ptr, int(iters), int(tail), int(seed), ctypes.byref(f),
+                                         _stream(stream)))
+        return f.value
+
+    def energy(self, level=0, stream=None):
+        """trace(P_e^T A P_e) of a level's edge prolongator."""
+        e = ctypes.c_double()
+        _check(load().sphc_prolongator_energy(self._ptr, int(level), ctypes.byref(e), _stream(stream)))
+        return e.value
 
     def cond_estimate(self, max_steps=5, stream=None):
         """(kappa_1(D^-1 A_e) estimate, ||D^-1 A_e||_1, estimated ||(D^-1 A_e)^-1||_1)."""
