@@ -99,6 +99,14 @@ typedef struct {
     int32_t emin_method;     /* energy minimisation of P_e: 0 projected Jacobi, eq. (9), with emin_omega;
                                 1 projected CG on the KKT system of eq. (8) (Sec. 3), D^-1
                                 preconditioned, emin_iters steps (default 0) */
+    int32_t pn_alg1;         /* 1: D_H from Alg. 1 (Gen_Piecewise_Const) applied to the smoothed P_n
+                                instead of the tentative aggregates (Sec. 4.1; default 0) */
+    double sa_theta;         /* smoothed-aggregation drop tolerance: an off-diagonal a_ij of A_n is
+                                strong when |a_ij| >= theta sqrt(a_ii a_jj); aggregation runs on the
+                                strong graph and P_n is smoothed with the filtered matrix, dropped
+                                entries lumped into the diagonal (Sec. 7; default 0: every
+                                structural entry is strong, Sec. 6.1) */
+    int32_t alg1_passes;     /* passes of Alg. 1 (default 2) */
     int32_t reserved[1];
 } sphc_opts;
 

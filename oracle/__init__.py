@@ -45,7 +45,8 @@ class _Opts(ctypes.Structure):
                 ("max_coarse", ctypes.c_int64), ("emin_omega", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("power_iters", ctypes.c_int32),
                 ("unsmoothed_pn", ctypes.c_int32), ("agg0", ctypes.c_void_p),
-                ("nagg0", ctypes.c_int64), ("p0_value", ctypes.c_double), ("emin_method", ctypes.c_int32)]
+                ("nagg0", ctypes.c_int64), ("p0_value", ctypes.c_double), ("emin_method", ctypes.c_int32),
+                ("sa_theta", ctypes.c_double), ("pn_alg1", ctypes.c_int32), ("alg1_passes", ctypes.c_int32)]
 
 
 _OPENMP = os.environ.get("SPHC_ORACLE_OPENMP", "0") == "1"
@@ -80,6 +81,8 @@ def _load():
         lib.orc_coarse_gradient.restype = I64
         lib.orc_minnorm.argtypes = [I32, I32, P, P, I32, P]
         lib.orc_project.argtypes = [I32, I32, P, I32, P]
+        lib.orc_gen_piecewise_const.argtypes = [I64, I64, P, P, P, I32, P]
+        lib.orc_gen_piecewise_const.restype = I64
         _lib = lib
     return _lib
 
@@ -176,7 +179,7 @@ class Hierarchy:
         this hierarchy's aggregates, D_H and pattern kept and its P_e as the initial guess."""
         av = _c(A_values, np.float64)
         o = _Opts(max_levels, emin_iters, max_coarse, emin_omega, seed, power_iters, 0, None, 0, 0.0,
-                  int(emin_method))
+                  int(emin_method), 0.0, 0, 2)
         st = ctypes.c_int()
         t0 = time.perf_counter()
         ptr = self._lib.orc_update(self._ptr, _p(av), ctypes.byref(o), ctypes.byref(st))
@@ -206,7 +209,8 @@ class Hierarchy:
 
 
 def setup(ne, nv, A, D, max_levels=8, emin_iters=1, max_coarse=1000, emin_omega=0.5, seed=0,
-          power_iters=15, unsmoothed_pn=False, agg0=None, p0_value=0.0, emin_method=0) -> Hierarchy:
+          power_iters=15, unsmoothed_pn=False, agg0=None, p0_value=0.0, emin_method=0, sa_theta=0.0,
+          pn_alg1=0, alg1_passes=2) -> Hierarchy:
     """A, D: (rowptr, col, val) triplets of A_e (ne x ne) and D_h (ne x nv)."""
     lib = _load()
     Arp, Aci, Av = _c(A[0], np.int64), _c(A[1], np.int32), _c(A[2], np.float64)
@@ -217,7 +221,8 @@ def setup(ne, nv, A, D, max_levels=8, emin_iters=1, max_coarse=1000, emin_omega=
         aggarr = _c(agg0, np.int32)
         nagg0 = int(aggarr.max()) + 1 if aggarr.size else 0
     o = _Opts(max_levels, emin_iters, max_coarse, emin_omega, seed, power_iters, int(unsmoothed_pn),
-              None if aggarr is None else aggarr.ctypes.data, nagg0, p0_value, int(emin_method))
+              None if aggarr is None else aggarr.ctypes.data, nagg0, p0_value, int(emin_method), float(sa_theta),
+              int(pn_alg1), int(alg1_passes))
     st = ctypes.c_int()
     t0 = time.perf_counter()
     ptr = lib.orc_setup(ne, nv, _p(Arp), _p(Aci), _p(Av), _p(Drp), _p(Dci), _p(Dv), ctypes.byref(o),
@@ -287,3 +292,12 @@ def project(G, x, singular):
     if rc < 0:
         raise RuntimeError("infeasible local system")
     return x
+
+
+def gen_piecewise_const(P: "CSR", passes=2):
+    """Alg. 1 (Gen_Piecewise_Const) under the oracle's reading: the column of each row."""
+    lib = _load()
+    rp, ci, v = _c(P.rowptr, np.int64), _c(P.col, np.int32), _c(P.val, np.float64)
+    out = np.empty(P.shape[0], np.int32)
+    lib.orc_gen_piecewise_const(P.shape[0], P.shape[1], _p(rp), _p(ci), _p(v), int(passes), _p(out))
+    return out

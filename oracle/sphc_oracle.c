@@ -367,6 +367,131 @@ static double power_rho(const ocsr *A, uint64_t seed, int iters) {
     return rho;
 }
 
+/* Drop tolerance theta > 0 (the symmetric smoothed-aggregation criterion the paper uses with
+ * MueLu in Sec. 7): off-diagonal a_ij is strong when |a_ij| >= theta sqrt(a_ii a_jj).  The filtered
+ * matrix keeps the diagonal and the strong entries; each dropped entry is added to the diagonal,
+ * in column order, so that its row sums equal A's. */
+static ocsr strength_filter(const ocsr *A, double theta) {
+    int64_t n = A->nr;
+    double *d = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    for (int64_t i = 0; i < n; ++i) d[i] = csr_diag(A, i);
+    int64_t nnz = 0;
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t k = A->rp[i]; k < A->rp[i + 1]; ++k) {
+            int32_t j = A->ci[k];
+            if (j == i || fabs(A->v[k]) >= theta * sqrt(d[i] * d[j])) ++nnz;
+        }
+    ocsr F = csr_alloc(n, A->nc, nnz);
+    int64_t q = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        double diag = d[i];
+        int64_t qd = -1;
+        for (int64_t k = A->rp[i]; k < A->rp[i + 1]; ++k) {
+            int32_t j = A->ci[k];
+            if (j == i) { qd = q; F.ci[q] = j; F.v[q++] = 0.0; }
+            else if (fabs(A->v[k]) >= theta * sqrt(d[i] * d[j])) { F.ci[q] = j; F.v[q++] = A->v[k]; }
+            else diag += A->v[k];
+        }
+        if (qd >= 0) F.v[qd] = diag;
+        F.rp[i + 1] = q;
+    }
+    free(d);
+    return F;
+}
+
+/* Alg. 1 (Gen_Piecewise_Const, Sec. 4.1): assign every row of the smoothed P (m_h x m_H) to one
+ * column, largest entries first, for the construction of D_H.  Readings (the paper leaves them
+ * open or states a sequential sweep):
+ *   - target_j = ceil(nnz(P_:j) m_h / nnz(P)) (proportional to the column's entries, summing to
+ *     about m_h); a pass assigns up to ceil(target_j / nPasses) rows to column j;
+ *   - within a pass the columns choose simultaneously: column j proposes its assignable rows
+ *     (unassigned when the pass starts) of largest |P_rj| (ties: lower row), and a row proposed by
+ *     several columns goes to the largest |P_rj| (ties: lower column);
+ *   - Greedy_Assign: each row still unassigned goes to its column of largest |P_rj| (ties: lower
+ *     column);
+ *   - safeguard: in column order, a column without rows takes its row of largest |P_rj| if that
+ *     row's column keeps another row.
+ * Returns the number of columns (m_H). */
+typedef struct { double a; int32_t r; } aent;
+static int cmp_aent(const void *x, const void *y) {
+    const aent *p = (const aent *)x, *q = (const aent *)y;
+    if (p->a != q->a) return p->a > q->a ? -1 : 1;
+    return p->r < q->r ? -1 : (p->r > q->r);
+}
+static int64_t gen_piecewise_const(const ocsr *P, int passes, int32_t *assign) {
+    int64_t m = P->nr, nc = P->nc, nnz = nnz_of(P);
+    ocsr Pt = csr_transpose(P);
+    for (int64_t r = 0; r < m; ++r) assign[r] = -1;
+    int64_t *nass = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nc > 0 ? nc : 1));
+    for (int64_t j = 0; j < nc; ++j) {
+        int64_t cnt = Pt.rp[j + 1] - Pt.rp[j];
+        int64_t target = nnz > 0 ? (cnt * m + nnz - 1) / nnz : 0;
+        nass[j] = (target + passes - 1) / passes;
+    }
+    double *best = (double *)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
+    int32_t *bcol = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m > 0 ? m : 1));
+    char *prop = (char *)calloc((size_t)(nnz > 0 ? nnz : 1), 1);
+    aent *buf = (aent *)malloc(sizeof(aent) * (size_t)(m > 0 ? m : 1));
+    for (int pass = 0; pass < passes; ++pass) {
+        memset(prop, 0, (size_t)(nnz > 0 ? nnz : 1));
+        for (int64_t r = 0; r < m; ++r) { best[r] = -1.0; bcol[r] = -1; }
+        for (int64_t j = 0; j < nc; ++j) {              /* proposals against the state at the pass start */
+            int64_t nb = 0;
+            for (int64_t k = Pt.rp[j]; k < Pt.rp[j + 1]; ++k)
+                if (assign[Pt.ci[k]] < 0) { buf[nb].a = fabs(Pt.v[k]); buf[nb].r = Pt.ci[k]; ++nb; }
+            qsort(buf, (size_t)nb, sizeof(aent), cmp_aent);
+            for (int64_t t = 0; t < nb && t < nass[j]; ++t)
+                for (int64_t k = Pt.rp[j]; k < Pt.rp[j + 1]; ++k)
+                    if (Pt.ci[k] == buf[t].r) prop[k] = 1;
+        }
+        for (int64_t j = 0; j < nc; ++j)               /* a contested row: largest |P_rj|, then lower j */
+            for (int64_t k = Pt.rp[j]; k < Pt.rp[j + 1]; ++k) {
+                if (!prop[k]) continue;
+                int32_t r = Pt.ci[k];
+                double a = fabs(Pt.v[k]);
+                if (a > best[r] || (a == best[r] && (bcol[r] < 0 || j < bcol[r]))) { best[r] = a; bcol[r] = (int32_t)j; }
+            }
+        for (int64_t r = 0; r < m; ++r) if (bcol[r] >= 0) assign[r] = bcol[r];
+    }
+    for (int64_t r = 0; r < m; ++r) {                   /* Greedy_Assign */
+        if (assign[r] >= 0) continue;
+        double ba = -1.0;
+        int32_t bj = -1;
+        for (int64_t k = P->rp[r]; k < P->rp[r + 1]; ++k) {
+            double a = fabs(P->v[k]);
+            if (a > ba || (a == ba && P->ci[k] < bj)) { ba = a; bj = P->ci[k]; }
+        }
+        assign[r] = bj;
+    }
+    int64_t *cnt = (int64_t *)calloc((size_t)(nc > 0 ? nc : 1), sizeof(int64_t));
+    for (int64_t r = 0; r < m; ++r) if (assign[r] >= 0) cnt[assign[r]]++;
+    for (int64_t j = 0; j < nc; ++j) {                  /* safeguard, in column order */
+        if (cnt[j] > 0 || Pt.rp[j + 1] == Pt.rp[j]) continue;
+        double ba = -1.0;
+        int32_t br = -1;
+        for (int64_t k = Pt.rp[j]; k < Pt.rp[j + 1]; ++k) {
+            double a = fabs(Pt.v[k]);
+            if (a > ba || (a == ba && Pt.ci[k] < br)) { ba = a; br = Pt.ci[k]; }
+        }
+        if (br >= 0 && assign[br] >= 0 && cnt[assign[br]] >= 2) { cnt[assign[br]]--; assign[br] = (int32_t)j; cnt[j]++; }
+    }
+    free(cnt); free(nass); free(best); free(bcol); free(prop); free(buf);
+    csr_free(&Pt);
+    return nc;
+}
+
+/* entry point of the tests */
+int64_t orc_gen_piecewise_const(int64_t nr, int64_t nc, const int64_t *rp, const int32_t *ci, const double *v,
+                                int passes, int32_t *assign) {
+    ocsr P = csr_alloc(nr, nc, rp[nr]);
+    memcpy(P.rp, rp, sizeof(int64_t) * (size_t)(nr + 1));
+    memcpy(P.ci, ci, sizeof(int32_t) * (size_t)rp[nr]);
+    memcpy(P.v, v, sizeof(double) * (size_t)rp[nr]);
+    int64_t r = gen_piecewise_const(&P, passes, assign);
+    csr_free(&P);
+    return r;
+}
+
 /* Pbar: one 1 per row in column agg(i) */
 static ocsr pbar_matrix(int64_t n, int64_t nagg, const int32_t *agg) {
     ocsr P = csr_alloc(n, nagg, n);
@@ -459,6 +584,9 @@ typedef struct {
     int64_t nagg0;
     double p0_value;            /* initial pattern value before the least-norm correction */
     int32_t emin_method;        /* 0: projected Jacobi, eq. (9); 1: projected CG on the KKT system, eq. (8) */
+    double sa_theta;            /* SA drop tolerance (0: every structural entry strong, Sec. 6.1) */
+    int32_t pn_alg1;            /* 1: D_H from Alg. 1 on the smoothed P_n (Sec. 4.1) */
+    int32_t alg1_passes;        /* passes of Alg. 1 */
 } orc_opts;
 
 typedef struct {
@@ -800,6 +928,10 @@ static int build_level(olevel *L, int lev, const orc_opts *o, ocsr *Anext, ocsr 
                        const olevel *prev) {
     uint64_t s = o->seed + 1000ULL * (uint64_t)lev;
     int64_t nv = L->An.nr, ne = L->A.nr;
+    /* drop tolerance: aggregation and prolongator smoothing on the filtered nodal matrix */
+    ocsr Af = {0, 0, NULL, NULL, NULL};
+    if (o->sa_theta > 0.0) Af = strength_filter(&L->An, o->sa_theta);
+    const ocsr *Ag = o->sa_theta > 0.0 ? &Af : &L->An;
     /* aggregation on the nodal graph (drop tolerance 0: every structural entry is strong) */
     L->agg = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nv > 0 ? nv : 1));
     if (prev) {
@@ -809,8 +941,8 @@ static int build_level(olevel *L, int lev, const orc_opts *o, ocsr *Anext, ocsr 
         memcpy(L->agg, o->agg0, sizeof(int32_t) * (size_t)nv);
         L->nagg = o->nagg0;
     } else {
-        L->nagg = aggregate_mis2(&L->An, s + 1, L->agg);
-        if (L->nagg < 0) return ORC_ENUMERIC;
+        L->nagg = aggregate_mis2(Ag, s + 1, L->agg);
+        if (L->nagg < 0) { if (Af.rp) csr_free(&Af); return ORC_ENUMERIC; }
     }
     /* nodal prolongator */
     ocsr Pb = pbar_matrix(nv, L->nagg, L->agg);
@@ -818,18 +950,22 @@ static int build_level(olevel *L, int lev, const orc_opts *o, ocsr *Anext, ocsr 
         L->Pn = csr_copy(&Pb);
         L->rho = 0.0; L->omega_sa = 0.0;
     } else {
-        L->rho = power_rho(&L->An, s + 4, o->power_iters);
+        L->rho = power_rho(Ag, s + 4, o->power_iters);
         L->omega_sa = 4.0 / (3.0 * L->rho);
-        ocsr APb = csr_spgemm(&L->An, &Pb);
+        ocsr APb = csr_spgemm(Ag, &Pb);
         for (int64_t i = 0; i < nv; ++i) {
-            double d = csr_diag(&L->An, i);
+            double d = csr_diag(Ag, i);
             for (int64_t k = APb.rp[i]; k < APb.rp[i + 1]; ++k) APb.v[k] /= d;
         }
         ocsr Pn = csr_add(&Pb, 1.0, &APb, -L->omega_sa);
         for (int64_t i = 0; i < nv; ++i) {
             double rs = 0.0;
             for (int64_t k = Pn.rp[i]; k < Pn.rp[i + 1]; ++k) rs += Pn.v[k];
-            if (!isfinite(rs)) { csr_free(&APb); csr_free(&Pn); csr_free(&Pb); return ORC_ENUMERIC; }
+            if (!isfinite(rs)) {
+                csr_free(&APb); csr_free(&Pn); csr_free(&Pb);
+                if (Af.rp) csr_free(&Af);
+                return ORC_ENUMERIC;
+            }
             if (rs <= SA_MIN_ROWSUM) {
                 /* smoothing left no usable row: keep the tentative row (same pattern) */
                 for (int64_t k = Pn.rp[i]; k < Pn.rp[i + 1]; ++k) Pn.v[k] = Pn.ci[k] == L->agg[i] ? 1.0 : 0.0;
@@ -841,8 +977,18 @@ static int build_level(olevel *L, int lev, const orc_opts *o, ocsr *Anext, ocsr 
         csr_free(&APb);
         L->Pn = Pn;
     }
-    /* coarse gradient from the piecewise-constant aggregates */
-    L->DH = prev ? csr_copy(&prev->DH) : coarse_gradient(&L->D, L->agg, L->nagg);
+    if (Af.rp) csr_free(&Af);
+    /* coarse gradient from the piecewise-constant aggregates, or from Alg. 1 applied to P_n */
+    if (prev) {
+        L->DH = csr_copy(&prev->DH);
+    } else if (o->pn_alg1) {
+        int32_t *pc = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nv > 0 ? nv : 1));
+        gen_piecewise_const(&L->Pn, o->alg1_passes, pc);
+        L->DH = coarse_gradient(&L->D, pc, L->nagg);
+        free(pc);
+    } else {
+        L->DH = coarse_gradient(&L->D, L->agg, L->nagg);
+    }
     /* Alg. 2: T (with the values r = D_h P_n), N, irreducibility */
     L->T = csr_spgemm(&L->D, &L->Pn);
     ocsr N = prev ? csr_copy(&prev->Pe) : initial_pattern(&L->T, &L->DH);

@@ -122,6 +122,10 @@ int setup_impl(sphc_handle* h, const sphc_csr* A_e, const sphc_csr* D_h, const d
             set_error("opts.emin_method must be 0 (projected Jacobi) or 1 (projected CG) (got %d)", (int)o.emin_method);
             return SPHC_EINVAL;
         }
+        if (!(o.sa_theta >= 0.0 && o.sa_theta < 1.0) || o.pn_alg1 < 0 || o.pn_alg1 > 1 || o.alg1_passes < 1) {
+            set_error("opts: sa_theta must lie in [0, 1), pn_alg1 be 0 or 1 and alg1_passes >= 1");
+            return SPHC_EINVAL;
+        }
         if (o.mlp_wait_polls < 0) {
             set_error("opts.mlp_wait_polls must be >= 0 (got %d)", (int)o.mlp_wait_polls);
             return SPHC_EINVAL;
@@ -246,6 +250,7 @@ int sphc_default_opts(sphc_opts* o) {
     o->mlp_params = nullptr;
     o->autotune = 0;
     o->block_rhs = 1;
+    o->alg1_passes = 2;
     return SPHC_OK;
 }
 
@@ -297,6 +302,11 @@ int sphc_setup_update(sphc_handle* h, const double* A_values, void* stream) {
     cudaStream_t s = (cudaStream_t)stream;
     Hierarchy& H = h->H;
     const sphc_opts& o = H.opts;
+    if (o.sa_theta > 0.0) {
+        set_error("sphc_setup_update: the strength graph of a drop tolerance theta > 0 depends on the values, so the "
+                  "aggregates cannot be kept; set up the new system instead");
+        return SPHC_EINVAL;
+    }
     auto t0 = std::chrono::steady_clock::now();
     Level& L0 = H.L[0];
     if (L0.A.nnz > 0) SPHC_CK(cudaMemcpyAsync(L0.A.v.p, A_values, sizeof(double) * L0.A.nnz, cudaMemcpyDefault, s));

@@ -1800,6 +1800,63 @@ static int coarse_coords(const Level& L, DBuf<double>& Xc, cudaStream_t s) {
 // section name with the level index, e.g. "setup_P0_l1"
 static std::string lev_name(const char* what, int lev) { return std::string(what) + "_l" + std::to_string(lev); }
 
+// ------------------------------------------------------------------ strength of connection (theta > 0)
+// Symmetric smoothed-aggregation criterion: an off-diagonal a_ij is strong when
+// |a_ij| >= theta sqrt(a_ii a_jj).  The filtered matrix keeps the diagonal and the strong entries
+// (columns stay sorted); every dropped entry is added to the diagonal in column order, so row
+// sums (and with them the constants in the null space) are unchanged.
+__global__ void k_strength_count(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                 const double* __restrict__ v, const double* __restrict__ d, int64_t n, double theta,
+                                 int64_t* __restrict__ cnt) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t c = 0;
+    for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+        const int32_t j = ci[k];
+        if (j == (int32_t)i || fabs(v[k]) >= theta * sqrt(d[i] * d[j])) ++c;
+    }
+    cnt[i] = c;
+}
+__global__ void k_strength_fill(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                const double* __restrict__ v, const double* __restrict__ d, int64_t n, double theta,
+                                const int64_t* __restrict__ frp, int32_t* __restrict__ fci, double* __restrict__ fv) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double diag = d[i];
+    int64_t q = frp[i], qd = -1;
+    for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+        const int32_t j = ci[k];
+        if (j == (int32_t)i) {
+            qd = q;
+            fci[q] = j;
+            fv[q++] = 0.0;
+        } else if (fabs(v[k]) >= theta * sqrt(d[i] * d[j])) {
+            fci[q] = j;
+            fv[q++] = v[k];
+        } else {
+            diag += v[k];
+        }
+    }
+    if (qd >= 0) fv[qd] = diag;
+}
+static int strength_filter(const DCSR& A, const double* d, double theta, DCSR& F, cudaStream_t s) {
+    const int64_t n = A.nr;
+    DBuf<int64_t> cnt;
+    SPHC_TRY(cnt.alloc(n + 1, s));
+    if (n > 0) SPHC_LAUNCH(k_strength_count<<<grid_for(n, 256), 256, 0, s>>>(A.rp.p, A.ci.p, A.v.p, d, n, theta, cnt.p));
+    int64_t nnz = 0;
+    SPHC_TRY(F.alloc(n, A.nc, 0, s));
+    SPHC_TRY(exclusive_scan_i64(cnt.p, F.rp.p, n, s, &nnz));
+    F.nnz = nnz;
+    SPHC_TRY(F.ci.alloc(nnz, s));
+    SPHC_TRY(F.v.alloc(nnz, s));
+    if (n > 0)
+        SPHC_LAUNCH(k_strength_fill<<<grid_for(n, 256), 256, 0, s>>>(A.rp.p, A.ci.p, A.v.p, d, n, theta, F.rp.p, F.ci.p,
+                                                                    F.v.p));
+    SPHC_CK(cudaGetLastError());
+    return SPHC_OK;
+}
+
 int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext, DCSR& Annext, DBuf<double>& Xnext,
                 const float* mlp_params, Profiler* prof, cudaStream_t s, bool reuse) {
     uint64_t seed = o.seed + 1000ULL * (uint64_t)lev;
@@ -1810,22 +1867,29 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
     // the previous P_e projected onto the new constraints.
     DBuf<double> warm;
     if (reuse) warm = std::move(L.Pe.v);
-    // aggregation on the structural nodal graph (drop tolerance 0)
-    if (!reuse) {
-        Section sec(prof, lev_name("setup_aggregate", lev).c_str(), s);
-        SPHC_TRY(aggregate(L.An, seed + 1, L.agg, &L.nagg, s));
-    }
-    Section* sec_pn = new Section(prof, lev_name("setup_Pn", lev).c_str(), s);
-    // smoothed nodal prolongator
+    // drop tolerance theta > 0: aggregation and smoothing on the filtered nodal matrix
     DBuf<double> dn;
     SPHC_TRY(dn.alloc(nv, s));
     SPHC_TRY(csr_diag(L.An, dn.p, s));
-    SPHC_TRY(power_rho(L.An, dn.p, seed + 4, o.power_iters, &L.rho, s));
+    DCSR Af;
+    if (o.sa_theta > 0.0) {
+        SPHC_TRY(strength_filter(L.An, dn.p, o.sa_theta, Af, s));
+        SPHC_TRY(csr_diag(Af, dn.p, s));
+    }
+    const DCSR& Ag = o.sa_theta > 0.0 ? Af : L.An;
+    // aggregation on the nodal graph (drop tolerance 0: every structural entry is strong)
+    if (!reuse) {
+        Section sec(prof, lev_name("setup_aggregate", lev).c_str(), s);
+        SPHC_TRY(aggregate(Ag, seed + 1, L.agg, &L.nagg, s));
+    }
+    Section* sec_pn = new Section(prof, lev_name("setup_Pn", lev).c_str(), s);
+    // smoothed nodal prolongator
+    SPHC_TRY(power_rho(Ag, dn.p, seed + 4, o.power_iters, &L.rho, s));
     L.omega_sa = 4.0 / (3.0 * L.rho);
     DCSR Pb;
     SPHC_TRY(Pb.alloc(nv, L.nagg, nv, s));
     SPHC_LAUNCH(k_pbar<<<grid_for(nv + 1, 256), 256, 0, s>>>(nv, L.agg.p, Pb.rp.p, Pb.ci.p, Pb.v.p));
-    SPHC_TRY(spgemm(L.An, Pb, L.Pn, s));
+    SPHC_TRY(spgemm(Ag, Pb, L.Pn, s));
     DBuf<int> fl;
     SPHC_TRY(fl.alloc(2, s));
     SPHC_TRY(fl.zero(s));

@@ -39,7 +39,8 @@ class sphc_opts(ctypes.Structure):
                 ("learned_emin_iters", ctypes.c_int32), ("mlp_params", ctypes.c_void_p),
                 ("autotune", ctypes.c_int32), ("sweep_form", ctypes.c_int32), ("mlp_wait_polls", ctypes.c_int32),
                 ("sell_lpr0", ctypes.c_int32), ("sell_ch0", ctypes.c_int32), ("emin_fp32", ctypes.c_int32),
-                ("block_rhs", ctypes.c_int32), ("emin_method", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
+                ("block_rhs", ctypes.c_int32), ("emin_method", ctypes.c_int32), ("pn_alg1", ctypes.c_int32),
+                ("sa_theta", ctypes.c_double), ("alg1_passes", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
 
 class sphc_train_opts(ctypes.Structure):

@@ -16,7 +16,9 @@ def gpu_setup(p, **opts):
 def oracle_setup(p, **opts):
     kw = dict(max_levels=opts.get("max_levels", 8), emin_iters=opts.get("emin_iters", 1),
               max_coarse=opts.get("max_coarse", 1000), emin_omega=opts.get("emin_omega", 0.5),
-              seed=opts.get("seed", 0), power_iters=opts.get("power_iters", 15))
+              seed=opts.get("seed", 0), power_iters=opts.get("power_iters", 15),
+              emin_method=opts.get("emin_method", 0), sa_theta=opts.get("sa_theta", 0.0),
+              pn_alg1=opts.get("pn_alg1", 0), alg1_passes=opts.get("alg1_passes", 2))
     return oracle.setup_problem(p, **kw)
 
 

@@ -226,3 +226,105 @@ def test_update_to_a_related_system():
     r = hu.solve(b)
     fresh = oracle.setup_problem(q, max_coarse=100).solve(b)
     assert r["status"] == 0 and r["iters"] <= fresh["iters"] + 2
+
+
+# ---------------------------------------------------------------- f1: drop tolerance and Alg. 1
+def test_tiny_drop_tolerance_changes_nothing():
+    # jittered, so no structural entry is exactly zero: theta = 1e-300 drops nothing and the
+    # lumping adds nothing, which must reproduce the theta = 0 hierarchy bit for bit
+    p = meshgen.generate(meshgen.MeshSpec(8, jitter=0.2, seed_jitter=9, sigma="lognormal", sigma_in=1.0, seed_sigma=2))
+    h0 = oracle.setup_problem(p, max_coarse=100)
+    h1 = oracle.setup_problem(p, max_coarse=100, sa_theta=1e-300)
+    for l in range(h0.nlevels - 1):
+        np.testing.assert_array_equal(h0.ivec(l, "agg"), h1.ivec(l, "agg"))
+        np.testing.assert_array_equal(h0.matrix(l, "Pe").val, h1.matrix(l, "Pe").val)
+
+
+def _strong_graph(An, theta):
+    d = An.diagonal()
+    C = An.tocoo()
+    keep = (C.row != C.col) & (np.abs(C.data) >= theta * np.sqrt(d[C.row] * d[C.col]))
+    return sp.csr_matrix((np.ones(keep.sum()), (C.row[keep], C.col[keep])), shape=An.shape)
+
+
+def test_drop_tolerance_aggregates_respect_the_strong_graph():
+    """theta = 0.1 on the box conductivity (1 inside, 1e-3 outside): every aggregate is connected
+    in the strong graph (restated here from A_n with the symmetric SA criterion), P_n rows sum to
+    one, and fewer aggregates straddle the material interface than with theta = 0."""
+    import scipy.sparse.csgraph as csg
+    p = meshgen.generate(meshgen.MeshSpec(12, jitter=0.15, seed_jitter=8, sigma="box", sigma_in=1.0, sigma_out=1e-3))
+    hs = {th: oracle.setup_problem(p, max_coarse=200, sa_theta=th) for th in (0.0, 0.1)}
+    h = hs[0.1]
+    An = h.matrix(0, "An").to_scipy()
+    S = _strong_graph(An, 0.1)
+    agg = h.ivec(0, "agg")
+    for a in range(agg.max() + 1):
+        nodes = np.nonzero(agg == a)[0]
+        ncomp, _ = csg.connected_components(S[nodes][:, nodes], directed=False)
+        assert ncomp == 1, a
+    Pn = h.matrix(0, "Pn").to_scipy()
+    np.testing.assert_allclose(np.asarray(Pn.sum(axis=1)).ravel(), 1.0, atol=1e-12)
+    X = p.coords
+    inside = np.all((X > 0.25 + 1 / 24) & (X < 0.75 - 1 / 24), axis=1)
+    outside = np.any((X < 0.25 - 1 / 24) | (X > 0.75 + 1 / 24), axis=1)
+    def straddling(hh):
+        g = hh.ivec(0, "agg")
+        return sum(1 for a in range(g.max() + 1) if inside[g == a].any() and outside[g == a].any())
+    assert straddling(hs[0.1]) < straddling(hs[0.0])
+
+
+def _alg1_restated(P, passes):
+    """The oracle's reading of Alg. 1, restated with numpy on a scipy CSR matrix."""
+    m, nc = P.shape
+    nnz = P.nnz
+    Pt = P.T.tocsr()
+    assign = -np.ones(m, int)
+    cnt = np.diff(Pt.indptr)
+    nass = -(-(-(-(cnt * m) // nnz)) // passes)
+    for _ in range(passes):
+        best, bcol = -np.ones(m), -np.ones(m, int)
+        props = []
+        for j in range(nc):
+            rows, vals = Pt.indices[Pt.indptr[j]:Pt.indptr[j + 1]], np.abs(Pt.data[Pt.indptr[j]:Pt.indptr[j + 1]])
+            cand = sorted((-a, r) for r, a in zip(rows, vals) if assign[r] < 0)[:nass[j]]
+            props += [(j, r, -na) for na, r in cand]
+        for j, r, a in props:
+            if a > best[r] or (a == best[r] and (bcol[r] < 0 or j < bcol[r])):
+                best[r], bcol[r] = a, j
+        assign[bcol >= 0] = bcol[bcol >= 0]
+    for r in np.nonzero(assign < 0)[0]:
+        cols, vals = P.indices[P.indptr[r]:P.indptr[r + 1]], np.abs(P.data[P.indptr[r]:P.indptr[r + 1]])
+        assign[r] = min(zip(-vals, cols))[1]
+    count = np.bincount(assign, minlength=nc)
+    for j in range(nc):
+        rows, vals = Pt.indices[Pt.indptr[j]:Pt.indptr[j + 1]], np.abs(Pt.data[Pt.indptr[j]:Pt.indptr[j + 1]])
+        if count[j] > 0 or rows.size == 0:
+            continue
+        r = min(zip(-vals, rows))[1]
+        if count[assign[r]] >= 2:
+            count[assign[r]] -= 1
+            assign[r] = j
+            count[j] += 1
+    return assign
+
+
+def test_alg1_reading_restated_and_special_case():
+    p = meshgen.generate(meshgen.MeshSpec(6, jitter=0.2, seed_jitter=2))
+    h = oracle.setup_problem(p, max_coarse=50)
+    Pn = h.matrix(0, "Pn")
+    for passes in (1, 2, 3):
+        got = oracle.gen_piecewise_const(Pn, passes)
+        np.testing.assert_array_equal(got, _alg1_restated(Pn.to_scipy(), passes))
+        S = Pn.to_scipy()
+        assert all(S[r, got[r]] != 0 for r in range(S.shape[0]))      # a column of the row
+    # Alg. 1 of a piecewise-constant P returns it: every column keeps all its rows
+    agg = h.ivec(0, "agg")
+    Pbar = oracle.CSR(np.arange(agg.size + 1, dtype=np.int64), agg.astype(np.int32), np.ones(agg.size), Pn.shape)
+    np.testing.assert_array_equal(oracle.gen_piecewise_const(Pbar, 2), agg)
+    # with Alg. 1 the hierarchy still satisfies the commuting relation and solves
+    ha = oracle.setup_problem(p, max_coarse=50, pn_alg1=1)
+    assert ha.status == 0
+    Pe, DH = ha.matrix(0, "Pe").to_scipy(), ha.matrix(0, "DH").to_scipy()
+    rhs = ha.matrix(0, "D").to_scipy() @ ha.matrix(0, "Pn").to_scipy()
+    assert abs(Pe @ DH - rhs).max() <= 1e-12 * max(1.0, abs(rhs).max())
+    assert ha.solve(meshgen.rhs(2, p.n_edges))["status"] == 0
