@@ -1857,6 +1857,157 @@ static int strength_filter(const DCSR& A, const double* d, double theta, DCSR& F
     return SPHC_OK;
 }
 
+// ------------------------------------------------------------------ Alg. 1 (Gen_Piecewise_Const)
+// Each row of the smoothed P_n (m_h x m_H) is assigned to one column for the construction of D_H
+// (Sec. 4.1).  The paper sweeps the columns one after another; here, as in the oracle, the
+// columns of a pass choose simultaneously: column j proposes its ceil(target_j / passes) rows of
+// largest |P_rj| that are unassigned when the pass starts (ties: lower row), target_j =
+// ceil(nnz(P_:j) m_h / nnz(P)); a row proposed by several columns goes to the largest |P_rj|
+// (ties: lower column).  Remaining rows go to their column of largest |P_rj| (ties: lower
+// column); a column left empty takes back its largest row where that row's column keeps another
+// (in column order).
+__global__ void k_alg1_nass(const int64_t* __restrict__ tp, int64_t nc, int64_t m, int64_t nnz, int passes,
+                            int32_t* __restrict__ nass) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nc) return;
+    const int64_t cnt = tp[j + 1] - tp[j];
+    const int64_t target = nnz > 0 ? (cnt * m + nnz - 1) / nnz : 0;
+    nass[j] = (int32_t)((target + passes - 1) / passes);
+}
+// warp per column: mark its proposals and raise best[r] to the proposal's |P_rj| (as ordered bits)
+__global__ void k_alg1_propose(const int64_t* __restrict__ tp, const int32_t* __restrict__ tr,
+                               const double* __restrict__ tv, int64_t nc, const int32_t* __restrict__ nass,
+                               const int32_t* __restrict__ assign, int8_t* __restrict__ prop,
+                               unsigned long long* __restrict__ best) {
+    const int lane = threadIdx.x & 31;
+    const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (j >= nc) return;
+    const int64_t k0 = tp[j], k1 = tp[j + 1];
+    for (int64_t k = k0 + lane; k < k1; k += 32) prop[k] = 0;
+    __syncwarp();
+    for (int t = 0; t < nass[j]; ++t) {
+        double ba = -1.0;
+        int32_t br = 0x7fffffff;
+        int64_t bk = -1;
+        for (int64_t k = k0 + lane; k < k1; k += 32) {
+            const int32_t r = tr[k];
+            if (prop[k] || assign[r] >= 0) continue;
+            const double a = fabs(tv[k]);
+            if (a > ba || (a == ba && r < br)) { ba = a; br = r; bk = k; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double oa = __shfl_xor_sync(0xffffffffu, ba, o);
+            const int32_t orr = __shfl_xor_sync(0xffffffffu, br, o);
+            const int64_t ok = __shfl_xor_sync(0xffffffffu, bk, o);
+            if (oa > ba || (oa == ba && orr < br)) { ba = oa; br = orr; bk = ok; }
+        }
+        if (bk < 0) break;                          // no assignable row left in this column
+        if (lane == 0) {
+            prop[bk] = 1;
+            atomicMax(&best[br], (unsigned long long)__double_as_longlong(ba));
+        }
+        __syncwarp();
+    }
+}
+// proposals that reach best[r]: the lowest such column wins row r
+__global__ void k_alg1_resolve(const int64_t* __restrict__ tp, const int32_t* __restrict__ tr,
+                               const double* __restrict__ tv, int64_t nc, const int8_t* __restrict__ prop,
+                               const unsigned long long* __restrict__ best, int32_t* __restrict__ bcol) {
+    const int lane = threadIdx.x & 31;
+    const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (j >= nc) return;
+    for (int64_t k = tp[j] + lane; k < tp[j + 1]; k += 32)
+        if (prop[k] && (unsigned long long)__double_as_longlong(fabs(tv[k])) == best[tr[k]])
+            atomicMin(&bcol[tr[k]], (int32_t)j);
+}
+constexpr int32_t ALG1_NONE = 0x7f7f7f7f;     // bcol before any proposal (a memset of 0x7f bytes)
+__global__ void k_alg1_commit(int64_t m, int32_t* __restrict__ assign, const int32_t* __restrict__ bcol) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < m && bcol[r] != ALG1_NONE) assign[r] = bcol[r];
+}
+__global__ void k_alg1_greedy(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                              const double* __restrict__ v, int64_t m, int32_t* __restrict__ assign,
+                              int32_t* __restrict__ count) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= m) return;
+    if (assign[r] < 0) {
+        double ba = -1.0;
+        int32_t bj = -1;
+        for (int64_t k = rp[r]; k < rp[r + 1]; ++k) {
+            const double a = fabs(v[k]);
+            if (a > ba || (a == ba && ci[k] < bj)) { ba = a; bj = ci[k]; }
+        }
+        assign[r] = bj;
+    }
+    if (assign[r] >= 0) atomicAdd(&count[assign[r]], 1);
+}
+__global__ void k_alg1_empty(const int64_t* __restrict__ tp, int64_t nc, const int32_t* __restrict__ count,
+                             int64_t* __restrict__ flag) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < nc) flag[j] = (count[j] == 0 && tp[j + 1] > tp[j]) ? 1 : 0;
+}
+// one thread, in column order over the (normally empty) list of empty columns
+__global__ void k_alg1_safeguard(const int64_t* __restrict__ tp, const int32_t* __restrict__ tr,
+                                 const double* __restrict__ tv, const int64_t* __restrict__ flag,
+                                 const int64_t* __restrict__ pos, int64_t nc, int32_t* __restrict__ assign,
+                                 int32_t* __restrict__ count) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    for (int64_t j = 0; j < nc; ++j) {
+        if (!flag[j] || count[j] > 0) continue;
+        double ba = -1.0;
+        int32_t br = -1;
+        for (int64_t k = tp[j]; k < tp[j + 1]; ++k) {
+            const double a = fabs(tv[k]);
+            if (a > ba || (a == ba && tr[k] < br)) { ba = a; br = tr[k]; }
+        }
+        if (br >= 0 && assign[br] >= 0 && count[assign[br]] >= 2) {
+            count[assign[br]]--;
+            assign[br] = (int32_t)j;
+            count[j]++;
+        }
+    }
+    (void)pos;
+}
+static int gen_piecewise_const(const DCSR& Pn, int passes, DBuf<int32_t>& assign, cudaStream_t s) {
+    const int64_t m = Pn.nr, nc = Pn.nc, nnz = Pn.nnz;
+    DCSR Pt;
+    SPHC_TRY(transpose(Pn, Pt, s));
+    DBuf<int32_t> nass, bcol, count;
+    DBuf<int8_t> prop;
+    DBuf<unsigned long long> best;
+    DBuf<int64_t> flag;
+    SPHC_TRY(assign.alloc(m > 0 ? m : 1, s));
+    SPHC_TRY(nass.alloc(nc > 0 ? nc : 1, s));
+    SPHC_TRY(bcol.alloc(m > 0 ? m : 1, s));
+    SPHC_TRY(count.alloc(nc > 0 ? nc : 1, s));
+    SPHC_TRY(prop.alloc(nnz > 0 ? nnz : 1, s));
+    SPHC_TRY(best.alloc(m > 0 ? m : 1, s));
+    SPHC_TRY(flag.alloc(nc > 0 ? nc : 1, s));
+    SPHC_CK(cudaMemsetAsync(assign.p, 0xff, sizeof(int32_t) * (m > 0 ? m : 1), s));     // -1
+    if (nc > 0) SPHC_LAUNCH(k_alg1_nass<<<grid_for(nc, 256), 256, 0, s>>>(Pt.rp.p, nc, m, nnz, passes, nass.p));
+    for (int pass = 0; pass < passes; ++pass) {
+        SPHC_TRY(best.zero(s));
+        SPHC_CK(cudaMemsetAsync(bcol.p, 0x7f, sizeof(int32_t) * (m > 0 ? m : 1), s));   // ALG1_NONE
+        if (nc > 0) {
+            SPHC_LAUNCH(k_alg1_propose<<<grid_for(nc * 32, 256), 256, 0, s>>>(Pt.rp.p, Pt.ci.p, Pt.v.p, nc, nass.p,
+                                                                             assign.p, prop.p, best.p));
+            SPHC_LAUNCH(k_alg1_resolve<<<grid_for(nc * 32, 256), 256, 0, s>>>(Pt.rp.p, Pt.ci.p, Pt.v.p, nc, prop.p,
+                                                                             best.p, bcol.p));
+        }
+        if (m > 0) SPHC_LAUNCH(k_alg1_commit<<<grid_for(m, 256), 256, 0, s>>>(m, assign.p, bcol.p));
+    }
+    SPHC_TRY(count.zero(s));
+    if (m > 0) SPHC_LAUNCH(k_alg1_greedy<<<grid_for(m, 256), 256, 0, s>>>(Pn.rp.p, Pn.ci.p, Pn.v.p, m, assign.p,
+                                                                        count.p));
+    if (nc > 0) {
+        SPHC_LAUNCH(k_alg1_empty<<<grid_for(nc, 256), 256, 0, s>>>(Pt.rp.p, nc, count.p, flag.p));
+        SPHC_LAUNCH(k_alg1_safeguard<<<1, 32, 0, s>>>(Pt.rp.p, Pt.ci.p, Pt.v.p, flag.p, nullptr, nc, assign.p,
+                                                      count.p));
+    }
+    SPHC_CK(cudaGetLastError());
+    return SPHC_OK;
+}
+
 int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext, DCSR& Annext, DBuf<double>& Xnext,
                 const float* mlp_params, Profiler* prof, cudaStream_t s, bool reuse) {
     uint64_t seed = o.seed + 1000ULL * (uint64_t)lev;
@@ -1902,10 +2053,17 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
     if (hf[1]) { set_error("non-finite nodal prolongator row sum on level %d", lev); return SPHC_ENUMERIC; }
     L.n_rows_unsmoothed = hf[0];
     delete sec_pn;
-    // coarse gradient from the tentative aggregates
+    // coarse gradient from the tentative aggregates, or from Alg. 1 applied to the smoothed P_n
     if (!reuse) {
         Section sec(prof, lev_name("setup_DH", lev).c_str(), s);
-        SPHC_TRY(coarse_gradient(L.D, L.Dt, L.agg.p, L.nagg, L.DH, s));
+        if (o.pn_alg1) {
+            DBuf<int32_t> pc;
+            SPHC_TRY(gen_piecewise_const(L.Pn, o.alg1_passes, pc, s));
+            SPHC_TRY(coarse_gradient(L.D, L.Dt, pc.p, L.nagg, L.DH, s));
+            SPHC_CK(cudaStreamSynchronize(s));
+        } else {
+            SPHC_TRY(coarse_gradient(L.D, L.Dt, L.agg.p, L.nagg, L.DH, s));
+        }
     }
     Section* sec_pat = new Section(prof, lev_name("setup_pattern", lev).c_str(), s);
     // T = D P_n (values r), N (Alg. 2), made irreducible

@@ -249,3 +249,28 @@ def test_projected_cg_prolongator_matches_oracle(pair, k):
     ref = oc.solve(b, tol=1e-8)
     assert rc == 0 and abs(it[0] - ref["iters"]) <= 1
     hc.destroy()
+
+
+@pytest.mark.parametrize("variant", [dict(sa_theta=0.02), dict(sa_theta=0.1), dict(pn_alg1=1),
+                                     dict(pn_alg1=1, sa_theta=0.05)], ids=["theta0.02", "theta0.1", "alg1",
+                                                                            "alg1_theta0.05"])
+def test_f1_variants_match_oracle(pair, variant):
+    # drop tolerance theta > 0 and Alg. 1 for D_H: integer work bit for bit, values to 1e-10
+    name, p, h, o, opts = pair
+    hv = gpu_setup(p, vcycle_fp32=0, **variant, **opts)
+    ov = oracle_setup(p, **variant, **opts)
+    assert hv.nlevels == ov.nlevels
+    for l in range(ov.nlevels):
+        if not ov.sizes(l)["has_transfer"]:
+            continue
+        np.testing.assert_array_equal(hv.export(l, "agg"), ov.ivec(l, "agg"))
+        assert_csr_close(hv.export(l, "DH"), ov.matrix(l, "DH"), f"L{l} D_H", 0.0)
+        assert_csr_equal_pattern(hv.export(l, "Pe"), ov.matrix(l, "Pe"), f"L{l} N")
+        for what in ("Pn", "Pe"):
+            assert_csr_close(hv.export(l, what), ov.matrix(l, what), f"L{l} {what}", FP64_RTOL)
+    b = meshgen.rhs(5, p.n_edges)
+    x = np.zeros_like(b)
+    rc, it, rr = hv.solve(b, x, tol=1e-8)
+    ref = ov.solve(b, tol=1e-8)
+    assert rc == 0 and ref["status"] == 0 and abs(it[0] - ref["iters"]) <= 1
+    hv.destroy()
