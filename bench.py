@@ -92,7 +92,8 @@ def run_paper3d(args, rank, local):
             x = torch.zeros_like(b)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            h = pkg.sphc.setup(A, D, opts=pkg.sphc.default_opts(vcycle_fp32=0), stream=stream)
+            h = pkg.sphc.setup(A, D, opts=pkg.sphc.default_opts(vcycle_fp32=0, pn_alg1=args.pn_alg1,
+                                                                sa_theta=args.sa_theta), stream=stream)
             torch.cuda.synchronize()
             t1 = time.perf_counter()
             kappa, _, _ = h.cond_estimate(5, stream=stream)
@@ -109,7 +110,7 @@ def run_paper3d(args, rank, local):
                          "levels": st["n_levels"], "op_complexity": round(st["operator_complexity"], 3),
                          "paper_op_complexity": oc_paper, "setup_s": t1 - t0, "solve_s": t3 - t2})
     line = {"metric": "paper 3D tet table: CG iterations (context)", "impl": "mine", "unit": "iterations",
-            "higher_is_better": False, "rows": rows,
+            "higher_is_better": False, "rows": rows, "pn_alg1": args.pn_alg1, "sa_theta": args.sa_theta,
             "note": "paper: Matlab, hardware not stated; aggregation and piecewise-constant prolongator differ "
                     "from the paper's (MIS-2 aggregates, tentative P-bar instead of Alg. 1)"}
     print(json.dumps(line), flush=True)
@@ -257,6 +258,8 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-block", action="store_true", help="skip the block-of-16-right-hand-sides leg")
+    ap.add_argument("--pn-alg1", type=int, default=0, help="paper3d: D_H from Alg. 1 on the smoothed P_n")
+    ap.add_argument("--sa-theta", type=float, default=0.0, help="paper3d: SA drop tolerance")
     ap.add_argument("--oracle-check", action="store_true",
                     help="also run the OpenMP oracle once on the full workload: its time, and the GPU headline "
                          "solution against its solution")
