@@ -111,8 +111,9 @@ def run_paper3d(args, rank, local):
                          "paper_op_complexity": oc_paper, "setup_s": t1 - t0, "solve_s": t3 - t2})
     line = {"metric": "paper 3D tet table: CG iterations (context)", "impl": "mine", "unit": "iterations",
             "higher_is_better": False, "rows": rows, "pn_alg1": args.pn_alg1, "sa_theta": args.sa_theta,
-            "note": "paper: Matlab, hardware not stated; aggregation and piecewise-constant prolongator differ "
-                    "from the paper's (MIS-2 aggregates, tentative P-bar instead of Alg. 1)"}
+            "note": "paper: Matlab, hardware not stated; aggregates differ from the paper's (MIS-2 rather than "
+                    "MueLu's phases)" + ("; D_H from Alg. 1" if args.pn_alg1 else
+                                         "; D_H from the tentative P-bar instead of Alg. 1")}
     print(json.dumps(line), flush=True)
 
 
@@ -391,7 +392,7 @@ def cpu_baseline(target_edges, steps=1):
     its = None
     for _ in range(steps):
         t0 = time.perf_counter()
-        h = oracle.setup_problem(p)
+        h = oracle.setup_problem(p, sa_theta=SA_THETA)
         r = h.solve(b, tol=1e-8)
         ts.append(time.perf_counter() - t0)
         its = r["iters"]
@@ -413,7 +414,8 @@ def bench_config(args, world, learned_weights):
                       + ("learned warm start of P_e + 1 energy-minimisation step" if learned_weights
                          else "least-norm P0 + 1 energy-minimisation step (no MLP weights found)"),
             "rhs": 1, "tol": args.tol, "l2": "inputs (A_e 2.8 GB FP64) exceed the 129 MB L2; no flush",
-            "parallelism": f"replicas x{world}"}
+            "parallelism": f"replicas x{world}",
+            **({"sa_theta": args.sa_theta} if args.sa_theta > 0 else {})}
 
 
 def workload_edges(name):
@@ -443,9 +445,13 @@ def run_reference(args, rank):
 
 
 # ------------------------------------------------------------------ GPU arm
+SA_THETA = 0.0      # drop tolerance of every GPU arm (--sa-theta)
+
+
 def make_opts(pkg, variant, weights, profile, graph=True):
     o = _make_opts(pkg, variant, weights, profile)
     o.cg_graph = 1 if graph else 0
+    o.sa_theta = SA_THETA
     return o
 
 
@@ -462,7 +468,9 @@ def _make_opts(pkg, variant, weights, profile):
 
 
 def main():
+    global SA_THETA
     args = parse_args()
+    SA_THETA = args.sa_theta
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

@@ -76,8 +76,13 @@ typedef struct {
     int32_t sweep_form;      /* smoothers with more rows than one thread block sweeps: 0 a cost model
                                 picks between one launch per colour and one launch per sweep on a
                                 thread-block cluster (x in shared memory, where it fits); 1 always
-                                a launch per colour; 2 the cluster wherever x fits (default 0;
-                                autotune overrides it) */
+                                a launch per colour; 2 the cluster wherever x fits; 3 one cooperative
+                                launch per sweep over the whole GPU with a grid barrier between
+                                colours (slower than form 0 on the meshes measured; default 0;
+                                autotune overrides it with forms 1 and 2).  A grid sweep whose barrier
+                                wait runs out of polls makes the solve or V-cycle call that ran it
+                                return SPHC_ETIMEOUT; the batched solve's graph always uses
+                                per-colour launches instead */
     int32_t mlp_wait_polls;  /* polls of the learned warm start's per-tile tensor-core completion waits
                                 before the kernel gives up and setup returns SPHC_ETIMEOUT (0: the
                                 default of 2^20 blocking polls; n > 0: n non-blocking checks).  The
@@ -107,7 +112,8 @@ typedef struct {
                                 entries lumped into the diagonal (Sec. 7; default 0: every
                                 structural entry is strong, Sec. 6.1) */
     int32_t alg1_passes;     /* passes of Alg. 1 (default 2) */
-    int32_t reserved[1];
+    int32_t grid_wait_polls; /* polls of a grid sweep's barrier wait before it gives up and the call
+                                returns SPHC_ETIMEOUT (0: the default, 4194304, well over a second) */
 } sphc_opts;
 
 /* Learned warm start (not part of the paper).  For every pattern entry (i, j) of P_e a
@@ -155,7 +161,8 @@ typedef struct {
      * so up to 7 more than the rounds that coloured something) */
     int32_t colour_rounds_edge, colour_rounds_node;
     /* smoother sweep form: 0 one launch per colour, 1 one launch per sweep on one thread-block
-     * cluster (x held in shared memory), 2 one launch per sweep on one thread block */
+     * cluster (x held in shared memory), 2 one launch per sweep on one thread block, 3 one
+     * cooperative launch per sweep over the whole GPU (grid barrier between colours) */
     int32_t sweep_kind_edge, sweep_kind_node;
 } sphc_level_info;
 
@@ -263,8 +270,18 @@ SPHC_API int sphc_vcycle_factor(sphc_handle* h, int iters, int tail, uint64_t se
  * SPHC_EINVAL (no prolongator on that level), SPHC_ENOMEM, SPHC_ECUDA. */
 SPHC_API int sphc_prolongator_energy(const sphc_handle* h, int level, double* energy, void* stream);
 
-/* Apply one V-cycle z = M^-1 r (FP64 in and out, n_e entries) with the handle's precision. */
+/* Apply one V-cycle z = M^-1 r (FP64 in and out, n_e entries) with the handle's precision.
+ * Errors: SPHC_EINVAL, SPHC_ECUDA, SPHC_ETIMEOUT (a grid sweep's barrier wait gave up). */
 SPHC_API int sphc_vcycle(sphc_handle* h, const double* r, double* z, void* stream);
+
+/* Diagnostic of the grid barrier that separates the colours of the persistent smoother sweep
+ * (sphc_opts.sweep_form): one cooperative grid (all SMs) passes three barriers that count
+ * `extra_arrivals` more arrivals than it has thread blocks, each wait limited to `polls` polls
+ * (0: the sweep's default).  With extra_arrivals > 0 no barrier can complete, every wait gives up
+ * and *timed_out = 1; with 0 the barriers complete and *timed_out = 0.  Either way the kernel
+ * returns and the device stays usable.  Synchronises the stream.  Errors: SPHC_EINVAL (negative
+ * argument, or the device has no cooperative launch), SPHC_ENOMEM, SPHC_ECUDA. */
+SPHC_API int sphc_grid_barrier_check(int extra_arrivals, int polls, int* timed_out, void* stream);
 
 SPHC_API int sphc_get_stats(const sphc_handle* h, sphc_stats* stats);
 SPHC_API int sphc_get_level_info(const sphc_handle* h, int level, sphc_level_info* info);

@@ -107,8 +107,8 @@ int setup_impl(sphc_handle* h, const sphc_csr* A_e, const sphc_csr* D_h, const d
                const double* sigma_edge, cudaStream_t s) {
     Hierarchy& H = h->H;
     const sphc_opts& o = H.opts;
-    if (o.sweep_form < 0 || o.sweep_form > 2) {
-        set_error("opts.sweep_form must be 0, 1 or 2 (got %d)", (int)o.sweep_form);
+    if (o.sweep_form < 0 || o.sweep_form > 3) {
+        set_error("opts.sweep_form must be 0, 1, 2 or 3 (got %d)", (int)o.sweep_form);
         return SPHC_EINVAL;
     }
     {
@@ -122,8 +122,9 @@ int setup_impl(sphc_handle* h, const sphc_csr* A_e, const sphc_csr* D_h, const d
             set_error("opts.emin_method must be 0 (projected Jacobi) or 1 (projected CG) (got %d)", (int)o.emin_method);
             return SPHC_EINVAL;
         }
-        if (!(o.sa_theta >= 0.0 && o.sa_theta < 1.0) || o.pn_alg1 < 0 || o.pn_alg1 > 1 || o.alg1_passes < 1) {
-            set_error("opts: sa_theta must lie in [0, 1), pn_alg1 be 0 or 1 and alg1_passes >= 1");
+        if (!(o.sa_theta >= 0.0 && o.sa_theta < 1.0) || o.pn_alg1 < 0 || o.pn_alg1 > 1 || o.alg1_passes < 1 ||
+            o.grid_wait_polls < 0) {
+            set_error("opts: sa_theta must lie in [0, 1), pn_alg1 be 0 or 1, alg1_passes >= 1 and grid_wait_polls >= 0");
             return SPHC_EINVAL;
         }
         if (o.mlp_wait_polls < 0) {
@@ -173,7 +174,7 @@ int setup_impl(sphc_handle* h, const sphc_csr* A_e, const sphc_csr* D_h, const d
         Section sec(prof, "setup_nodal_op", s);
         {
             Section sub(prof, "setup_nodal_AD", s);
-            SPHC_TRY(spgemm(L0.A, L0.D, L0.AD, s));
+            SPHC_TRY(amul_d(L0.A, L0.D, L0.AD, s));
         }
         if (prof) {
             auto csr_bytes = [](const DCSR& M) { return 12.0 * (double)M.nnz + 8.0 * (double)(M.nr + 1); };
@@ -314,7 +315,7 @@ int sphc_setup_update(sphc_handle* h, const double* A_values, void* stream) {
     Profiler* prof = H.prof.on ? &H.prof : nullptr;
     {
         Section sec(prof, "update_nodal_op", s);
-        SPHC_TRY(spgemm(L0.A, L0.D, L0.AD, s));
+        SPHC_TRY(amul_d(L0.A, L0.D, L0.AD, s));
         SPHC_TRY(spgemm_sym(L0.Dt, L0.AD, L0.An, s));
     }
     for (int lev = 0; lev + 1 < H.nlev; ++lev) {
@@ -436,6 +437,16 @@ int sphc_vcycle(sphc_handle* h, const double* r, double* z, void* stream) {
     SPHC_TRY(apply_vcycle_user(h->H, r, z, s));
     SPHC_CK(cudaStreamSynchronize(s));
     return SPHC_OK;
+}
+
+int sphc_grid_barrier_check(int extra_arrivals, int polls, int* timed_out, void* stream) {
+    if (extra_arrivals < 0 || polls < 0 || !timed_out) {
+        set_error("sphc_grid_barrier_check: invalid argument");
+        return SPHC_EINVAL;
+    }
+    *timed_out = 0;
+    return grid_barrier_check(extra_arrivals, polls > 0 ? (unsigned)polls : GRID_BAR_POLLS, timed_out,
+                              (cudaStream_t)stream);
 }
 
 int sphc_get_stats(const sphc_handle* h, sphc_stats* st) {

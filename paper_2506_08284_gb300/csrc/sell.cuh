@@ -57,12 +57,20 @@ template <> struct IChunk<4> {
     }
 };
 
+// x read through L2 only (ld.global.cg).  The persistent grid sweep rewrites x between its colours
+// and other SMs' L1 caches may still hold the old lines; L2 is coherent across the GPU.
+template <typename T>
+struct L2Read {
+    const T* p;
+    __device__ __forceinline__ T operator[](int64_t i) const { return __ldcg(p + i); }
+};
+
 // This lane's partial (A x)_r over the slice starting at o: `steps` loads of CH entries.  Four
 // steps of matrix loads are issued before their gathers, so a row costs about steps / 4 memory
 // round trips instead of steps / 2 (the small coarse-level colours are latency-bound).
-template <typename T, int CH>
+template <typename T, int CH, typename X>
 __device__ __forceinline__ T sell_part(const int32_t* __restrict__ ci, const T* __restrict__ v, int64_t o,
-                                       int64_t steps, int lane, const T* x) {
+                                       int64_t steps, int lane, X x) {
     constexpr int U = 4;
     const T* vp = v + o + lane * CH;
     const int32_t* cp = ci + o + lane * CH;
@@ -133,8 +141,9 @@ struct SellHead {
                 IChunk<CH>::load(cp + u * SELL_C * CH, c[u]);
             }
     }
+    template <typename X>
     __device__ __forceinline__ T finish(const int32_t* __restrict__ ci, const T* __restrict__ v, int64_t o,
-                                        int64_t steps, int lane, const T* x) const {
+                                        int64_t steps, int lane, X x) const {
         T sum = 0;
 #pragma unroll
         for (int u = 0; u < U; ++u)

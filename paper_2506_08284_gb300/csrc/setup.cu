@@ -1390,9 +1390,9 @@ constexpr int PP_ILP = 4;
 // FP64 pipe as an FP64 FMA (ncu: 82 % FP64-pipe activity with per-pair conversions).
 template <typename Acc>
 __global__ void __launch_bounds__(PP_WARPS * 32)
-k_emin_pp(int64_t ne, const int64_t* __restrict__ arp, const int32_t* __restrict__ aci, const double* __restrict__ av,
-          const int64_t* __restrict__ nrp, const int32_t* __restrict__ nci, const Acc* __restrict__ P,
-          const int8_t* __restrict__ ck, Acc* __restrict__ w) {
+k_emin_pp(int64_t ne, const int64_t* __restrict__ arp, const int32_t* __restrict__ aci, const Acc* __restrict__ av,
+          const Acc* __restrict__ dinv, const int64_t* __restrict__ nrp, const int32_t* __restrict__ nci,
+          const Acc* __restrict__ P, const int8_t* __restrict__ ck, Acc* __restrict__ w) {
     const int lane = threadIdx.x & 31;
     const int64_t i = (int64_t)blockIdx.x * PP_WARPS + (threadIdx.x >> 5);
     if (i >= ne || ck[i] < 0) return;                  // whole warp: no row, or a row k_emin handles
@@ -1406,8 +1406,6 @@ k_emin_pp(int64_t ne, const int64_t* __restrict__ arp, const int32_t* __restrict
     const int32_t key = owner ? nci[n0 + t] : -1;
     const int64_t a0 = arp[i], a1 = arp[i + 1];
     Acc acc = Acc(0);
-    double aii = 0.0;
-    bool has_diag = false;
     for (int64_t kb = a0 + sub; kb < a1; kb += (int64_t)PP_ILP * L) {
         int64_t lo[PP_ILP];
         int len[PP_ILP];
@@ -1420,9 +1418,7 @@ k_emin_pp(int64_t ne, const int64_t* __restrict__ arp, const int32_t* __restrict
             a[j] = Acc(0);
             if (ka < a1) {
                 const int32_t f = aci[ka];
-                const double af = av[ka];
-                a[j] = (Acc)af;
-                if (f == (int32_t)i) { aii = af; has_diag = true; }
+                a[j] = av[ka];
                 lo[j] = nrp[f];
                 len[j] = (int)(nrp[f + 1] - lo[j]);
             }
@@ -1456,13 +1452,25 @@ k_emin_pp(int64_t ne, const int64_t* __restrict__ arp, const int32_t* __restrict
         for (int j = 0; j < PP_ILP; ++j)
             if (len[j] > 0 && nci[lo[j] + pos[j]] == key) acc += a[j] * P[lo[j] + pos[j]];
     }
-    // a_ii from the lane that met the diagonal entry
-    const unsigned dm = __ballot_sync(0xffffffffu, has_diag);
-    aii = __shfl_sync(0xffffffffu, aii, dm ? __ffs(dm) - 1 : 0);
-    if (!dm) aii = 1.0;
     for (int d = L >> 1; d > 0; d >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, d);
-    const Acc inv = (Acc)(1.0 / aii);
-    if (owner && sub == 0) w[n0 + t] = acc * inv;
+    if (owner && sub == 0) w[n0 + t] = acc * dinv[i];
+}
+
+// 1 / a_ii of every row (1 where the row has no diagonal entry), in FP64 and rounded to FP32: the
+// D^-1 of eq. (9), formed once per level for the masked product
+__global__ void k_diag_inv(int64_t n, const int64_t* __restrict__ arp, const int32_t* __restrict__ aci,
+                           const double* __restrict__ av, double* __restrict__ dinv, float* __restrict__ dinvf) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double aii = 1.0;
+    for (int64_t k = arp[i]; k < arp[i + 1]; ++k)
+        if (aci[k] == (int32_t)i) {
+            aii = av[k];
+            break;
+        }
+    const double d = 1.0 / aii;
+    dinv[i] = d;
+    if (dinvf) dinvf[i] = (float)d;
 }
 
 // projection and update of eq. (9) for every small row: dp = w - G~ (G~^T G~)^-1 G~^T w,
@@ -2231,11 +2239,12 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
     DBuf<double> Pnew;
     SPHC_TRY(Pnew.alloc(nnzN, s));
     delete sec_cp;
-    // algorithmic bytes of one step: A (values, columns, row pointers) once; P's pattern (row
-    // pointers, columns, values) once, however often its rows are gathered; w written and read;
-    // per row the stored factor (masks, k, lower triangle); P read and P' written by the update
+    // algorithmic bytes of one step: A (values in the product's precision, columns, row pointers)
+    // once; P's pattern (row pointers, columns, values) once, however often its rows are gathered;
+    // w written and read; per row the stored factor (masks, k, lower triangle); P read and P'
+    // written by the update
     const size_t wsz = o.emin_fp32 ? sizeof(float) : sizeof(double);
-    double emin_bytes = (double)L.A.nnz * 12.0 + (double)(ne + 1) * 8.0 * 2 + (double)nnzN * (4 + 8) +
+    double emin_bytes = (double)L.A.nnz * (4.0 + (double)wsz) + (double)(ne + 1) * 8.0 * 2 + (double)nnzN * (4 + 8) +
                         (double)nnzN * 2.0 * (double)wsz + (double)ne * (2 * TK * 4 + 1 + TL * 8) +
                         (double)nnzN * 16.0;
     int tid = prof ? prof->find(lev_name("emin_level", lev).c_str(), emin_bytes) : -1;
@@ -2248,7 +2257,19 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
     // projected gradient g = Pi D^-1 (A V)|_N of values V on the pattern (small rows by the product
     // and thread-per-row projection kernels, large rows by k_emin)
     DBuf<float> P32;                            // FP32 copy of the values the product reads
-    if (o.emin_fp32 && emin_iters > 0) SPHC_TRY(P32.alloc(nnzN, s));
+    DBuf<float> A32, Dinv32;                    // FP32 copies of A's values and of 1 / a_ii
+    DBuf<double> Dinv;
+    if (emin_iters > 0 && ne > 0) {
+        SPHC_TRY(Dinv.alloc(ne, s));
+        if (o.emin_fp32) {
+            SPHC_TRY(P32.alloc(nnzN, s));
+            SPHC_TRY(A32.alloc(L.A.nnz, s));
+            SPHC_TRY(Dinv32.alloc(ne, s));
+            if (L.A.nnz > 0) SPHC_LAUNCH(k_to_float<<<grid_for(L.A.nnz, 256), 256, 0, s>>>(L.A.v.p, L.A.nnz, A32.p));
+        }
+        SPHC_LAUNCH(k_diag_inv<<<grid_for(ne, 256), 256, 0, s>>>(ne, L.A.rp.p, L.A.ci.p, L.A.v.p, Dinv.p,
+                                                                  o.emin_fp32 ? Dinv32.p : nullptr));
+    }
     auto to_f32 = [&](const double* V) {
         if (nnzN > 0) SPHC_LAUNCH(k_to_float<<<grid_for(nnzN, 256), 256, 0, s>>>(V, nnzN, P32.p));
     };
@@ -2256,11 +2277,11 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
         const int gpp = grid_for(ne, PP_WARPS);
         if (o.emin_fp32) {
             to_f32(V);
-            SPHC_LAUNCH(k_emin_pp<float><<<gpp, PP_WARPS * 32, 0, s>>>(ne, L.A.rp.p, L.A.ci.p, L.A.v.p, L.Pe.rp.p,
+            SPHC_LAUNCH(k_emin_pp<float><<<gpp, PP_WARPS * 32, 0, s>>>(ne, L.A.rp.p, L.A.ci.p, A32.p, Dinv32.p, L.Pe.rp.p,
                                                                       L.Pe.ci.p, P32.p, cache.k, W32.p));
             SPHC_LAUNCH(k_emin_rows<float><<<grid_for(ne, 128), 128, 0, s>>>(ne, L.Pe.rp.p, W32.p, V, g, 0.0, cache, 1));
         } else {
-            SPHC_LAUNCH(k_emin_pp<double><<<gpp, PP_WARPS * 32, 0, s>>>(ne, L.A.rp.p, L.A.ci.p, L.A.v.p, L.Pe.rp.p,
+            SPHC_LAUNCH(k_emin_pp<double><<<gpp, PP_WARPS * 32, 0, s>>>(ne, L.A.rp.p, L.A.ci.p, L.A.v.p, Dinv.p, L.Pe.rp.p,
                                                                        L.Pe.ci.p, V, cache.k, W.p));
             SPHC_LAUNCH(k_emin_rows<double><<<grid_for(ne, 128), 128, 0, s>>>(ne, L.Pe.rp.p, W.p, V, g, 0.0, cache, 1));
         }
@@ -2320,11 +2341,11 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
                 Section sp(prof, lev_name("emin_product", lev).c_str(), s);
                 if (o.emin_fp32) {
                     to_f32(L.Pe.v.p);
-                    SPHC_LAUNCH(k_emin_pp<float><<<gpp, PP_WARPS * 32, 0, s>>>(ne, L.A.rp.p, L.A.ci.p, L.A.v.p, L.Pe.rp.p,
+                    SPHC_LAUNCH(k_emin_pp<float><<<gpp, PP_WARPS * 32, 0, s>>>(ne, L.A.rp.p, L.A.ci.p, A32.p, Dinv32.p, L.Pe.rp.p,
                                                                            L.Pe.ci.p, P32.p, cache.k, W32.p));
                 }
                 else
-                    SPHC_LAUNCH(k_emin_pp<double><<<gpp, PP_WARPS * 32, 0, s>>>(ne, L.A.rp.p, L.A.ci.p, L.A.v.p, L.Pe.rp.p,
+                    SPHC_LAUNCH(k_emin_pp<double><<<gpp, PP_WARPS * 32, 0, s>>>(ne, L.A.rp.p, L.A.ci.p, L.A.v.p, Dinv.p, L.Pe.rp.p,
                                                                             L.Pe.ci.p, L.Pe.v.p, cache.k, W.p));
             }
             {

@@ -74,6 +74,8 @@ static int build_orders(Hierarchy& H, cudaStream_t s) {
 
 template <typename T>
 static bool cluster_sgs_chosen(const SmoothOp<T>& op, int sweep_form);
+template <typename T>
+static int grid_sgs_chosen(const SmoothOp<T>& op, int sweep_form);
 
 template <typename T>
 static int build_vlevel(Hierarchy& H, int l, VLevel<T>& V, bool split, cudaStream_t s) {
@@ -94,7 +96,7 @@ static int build_vlevel(Hierarchy& H, int l, VLevel<T>& V, bool split, cudaStrea
     if (l == H.nlev - 1) return SPHC_OK;
     const LevelOrder& C = H.ord[l + 1];
     if (split) {
-        if (L.AD.nr != L.A.nr) SPHC_TRY(spgemm(L.A, L.D, L.AD, s));   // FP64: the curl-curl part cancels here
+        if (L.AD.nr != L.A.nr) SPHC_TRY(amul_d(L.A, L.D, L.AD, s));   // FP64: the curl-curl part cancels here
         SPHC_TRY(build_xop<T>(L.AD, O.pe.p, O.in.p, V.AD, s));
         SPHC_TRY(build_xop<T>(L.Pn, O.pn.p, C.in.p, V.Pn, s));
         L.AD = DCSR();
@@ -104,6 +106,10 @@ static int build_vlevel(Hierarchy& H, int l, VLevel<T>& V, bool split, cudaStrea
     SPHC_TRY(build_smooth<T>(L.An, O.pn.p, O.in.p, O.cn, 0, 0, V.An, s));
     V.A.cluster = cluster_sgs_chosen(V.A, H.opts.sweep_form) ? 1 : 0;
     V.An.cluster = cluster_sgs_chosen(V.An, H.opts.sweep_form) ? 1 : 0;
+    V.A.grid = grid_sgs_chosen(V.A, H.opts.sweep_form);
+    V.An.grid = grid_sgs_chosen(V.An, H.opts.sweep_form);
+    V.A.bar = V.An.bar = H.gbar.p;
+    V.A.polls = V.An.polls = H.opts.grid_wait_polls > 0 ? (unsigned)H.opts.grid_wait_polls : GRID_BAR_POLLS;
     SPHC_TRY(build_xop<T>(L.Pe, O.pe.p, C.ie.p, V.Pe, s));
     SPHC_TRY(build_xop<T>(L.PeT, C.pe.p, O.ie.p, V.PeT, s));
     SPHC_CK(cudaGetLastError());
@@ -112,6 +118,8 @@ static int build_vlevel(Hierarchy& H, int l, VLevel<T>& V, bool split, cudaStrea
 
 int build_vcycle_ops(Hierarchy& H, cudaStream_t s) {
     SPHC_TRY(build_orders(H, s));
+    SPHC_TRY(H.gbar.alloc(1, s));
+    SPHC_TRY(H.gbar.zero(s));
     const LevelOrder& O = H.ord[0];
     if (H.opts.vcycle_fp32) {
         H.V32.clear();
@@ -331,6 +339,101 @@ k_sell_sgs_cluster(const int64_t* __restrict__ soff, const int32_t* __restrict__
     for (int64_t i = (int64_t)rank * blockDim.x + threadIdx.x; i < n; i += (int64_t)ncta * blockDim.x) x[i] = xs[i];
 }
 
+// A whole forward + backward sweep of a large operator as one persistent kernel: every CTA of a
+// co-resident (cooperative) grid works on each colour in turn, and a grid barrier replaces the
+// kernel boundary between colours.  Mid-sized levels (tens of colours of a few thousand rows each)
+// are latency-bound when every colour is its own launch: the launch, the drain of the previous
+// kernel and the first loads of the matrix make up most of a colour.  Here the head of each warp's
+// first slice of the next colour (matrix entries, b and 1 / a_rr) is loaded before the barrier, so
+// a colour costs the gathers of x, the update and the barrier.  x stays in global memory (L2) and
+// is read through L2 only; every CTA writes the rows it updates.
+//
+// The barrier counts arrivals in bar->count; the last CTA to arrive resets it and advances
+// bar->gen (release); the others poll gen (acquire).  Every poll loop has an iteration limit: a
+// CTA that gives up, or sees another CTA's give-up in bar->err, sets bar->err and leaves the
+// kernel, so all CTAs return and the host reads the error word after the solve.
+template <typename T>
+struct SgsGridThreads {
+    static constexpr int value = sizeof(T) == 4 ? 1024 : 512;
+};
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+// every thread of every CTA calls it; false when a wait gave up (the caller returns)
+__device__ __forceinline__ bool grid_barrier(GridBar* bar, unsigned nblocks, unsigned max_polls) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned g = ld_acquire_u32(&bar->gen);      // cannot advance before this CTA arrives
+        __threadfence();                                   // the CTA's writes (ordered by the block barrier)
+        if (atomicAdd(&bar->count, 1u) == nblocks - 1) {
+            atomicExch(&bar->count, 0u);
+            st_release_u32(&bar->gen, g + 1);
+        } else {
+            for (unsigned polls = 0; ld_acquire_u32(&bar->gen) == g; ++polls) {
+                if (*(volatile int*)&bar->err != 0 || polls >= max_polls) {
+                    atomicExch(&bar->err, 1);
+                    ok = 0;
+                    break;
+                }
+                if (polls >= 1024) __nanosleep(64);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+template <typename T, int CH>
+__global__ void __launch_bounds__(SgsGridThreads<T>::value)
+k_sell_sgs_grid(const int64_t* __restrict__ soff, const int32_t* __restrict__ srow,
+                const int64_t* __restrict__ cslice, int ncolor, int lpr, const int32_t* __restrict__ ci,
+                const T* __restrict__ v, const T* __restrict__ dinv, const T* __restrict__ b, T* x, GridBar* bar,
+                unsigned max_polls) {
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const L2Read<T> xr{x};
+    int64_t sl = 0, end = 0, o = 0, steps = 0;
+    int32_t r = 0;
+    bool have = false, valid = false;
+    T br = 0, dr = 0;
+    SellHead<T, CH> h;
+    h.n = 0;
+    auto fetch = [&](int64_t s_, int64_t e_) {
+        sl = s_;
+        end = e_;
+        have = sl < end;
+        if (!have) return;
+        o = soff[sl];
+        steps = (soff[sl + 1] - o) / (SELL_C * CH);
+        r = srow[sl] + lane / lpr;
+        valid = r < srow[sl + 1];
+        h.load(ci, v, o, steps, lane);
+        if (valid) { br = b[r]; dr = dinv[r]; }
+    };
+    fetch(cslice[0] + gw, cslice[1]);
+    for (int step = 0; step < sweep_steps(ncolor); ++step) {
+        while (have) {
+            T sum = row_reduce(h.finish(ci, v, o, steps, lane, xr), lpr);
+            if (valid && (lane & (lpr - 1)) == 0) x[r] = xr[r] + (br - sum) * dr;
+            fetch(sl + nw, end);
+        }
+        if (step + 1 < sweep_steps(ncolor)) {            // head of the next colour's first slice
+            const int cn = sweep_colour(step + 1, ncolor);
+            fetch(cslice[cn] + gw, cslice[cn + 1]);
+            if (!grid_barrier(bar, gridDim.x, max_polls)) return;
+        }
+    }
+}
+
 template <typename T, int SUB>
 __global__ void k_spmv_v(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const T* __restrict__ v,
                          int64_t n, const T* __restrict__ x, T* y, int accumulate, T alpha) {
@@ -483,10 +586,97 @@ static bool cluster_sgs_preferred(const SmoothOp<T>& op) {
 // the sweep form of op under sphc_opts.sweep_form
 template <typename T>
 static bool cluster_sgs_chosen(const SmoothOp<T>& op, int sweep_form) {
-    if (sweep_form == 1) return false;
+    if (sweep_form == 1 || sweep_form == 3) return false;
     if (sweep_form == 2) return cluster_sgs_fits(op);
     return cluster_sgs_preferred(op);
 }
+
+// The grid barrier on its own: `rounds` barriers of a cooperative grid that counts `extra`
+// arrivals more than it has CTAs (extra > 0: a wait nothing can end, so every CTA gives up after
+// max_polls polls and sets bar->err).
+__global__ void k_grid_barrier_check(GridBar* bar, unsigned extra, unsigned max_polls, int rounds) {
+    for (int k = 0; k < rounds; ++k)
+        if (!grid_barrier(bar, gridDim.x + extra, max_polls)) return;
+}
+int grid_barrier_check(int extra, unsigned max_polls, int* timed_out, cudaStream_t s) {
+    int dev = 0, nsm = 0, coop = 0, per_sm = 0;
+    SPHC_CK(cudaGetDevice(&dev));
+    SPHC_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    SPHC_CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    SPHC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid_barrier_check, 256, 0));
+    if (!coop || per_sm < 1) {
+        set_error("grid barrier check: the device does not run cooperative launches");
+        return SPHC_EINVAL;
+    }
+    DBuf<GridBar> bar;
+    SPHC_TRY(bar.alloc(1, s));
+    SPHC_TRY(bar.zero(s));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nsm * per_sm);
+    cfg.blockDim = dim3(256);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    SPHC_CK(cudaLaunchKernelEx(&cfg, k_grid_barrier_check, bar.p, (unsigned)extra, max_polls, 3));
+    GridBar hb = {};
+    SPHC_CK(cudaMemcpyAsync(&hb, bar.p, sizeof(GridBar), cudaMemcpyDeviceToHost, s));
+    SPHC_CK(cudaStreamSynchronize(s));
+    *timed_out = hb.err != 0;
+    return SPHC_OK;
+}
+
+// one cooperative launch of the grid sweep (one CTA per resident slot; the cooperative launch
+// makes the runtime check that the whole grid is resident at once)
+template <typename T, int CH>
+static cudaError_t launch_sgs_grid(const SmoothOp<T>& op, const T* b, T* x, cudaStream_t s) {
+    const Sell<T>& m = op.m;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(op.grid);
+    cfg.blockDim = dim3(SgsGridThreads<T>::value);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return cudaLaunchKernelEx(&cfg, k_sell_sgs_grid<T, CH>, m.soff.p, m.srow.p, op.cslice_dev.p, op.ncolor, m.lpr,
+                              m.ci.p, m.v.p, op.dinv.p, b, x, op.bar, op.polls);
+}
+// CTAs of op's grid sweep that can be resident at once on this device (0: it cannot run)
+template <typename T>
+static int grid_sgs_blocks(const SmoothOp<T>& op) {
+    void (*k)(const int64_t*, const int32_t*, const int64_t*, int, int, const int32_t*, const T*, const T*,
+              const T*, T*, GridBar*, unsigned) =
+        op.m.ch == 1 ? k_sell_sgs_grid<T, 1> : (op.m.ch == 2 ? k_sell_sgs_grid<T, 2> : k_sell_sgs_grid<T, 4>);
+    int dev = 0, nsm = 0, coop = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, SgsGridThreads<T>::value, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return coop ? nsm * per_sm : 0;
+}
+// Whether the grid sweep runs op: only where sphc_opts.sweep_form 3 asks for it, for every
+// smoother above one block.  The cost model does not pick it: on the 128^3 problem's level 1
+// (571K rows, 47 colours of about 8 MB of matrix each) a colour took about 12 us in the grid
+// sweep against 8.7 us as its own launch.  The grid barrier alone costs 2.7 us (152 CTAs), and one
+// CTA of 1024 threads per SM keeps fewer matrix loads in flight than a launch of the whole colour.
+template <typename T>
+static int grid_sgs_chosen(const SmoothOp<T>& op, int sweep_form) {
+    if (sweep_form != 3 || op.n <= SGS_BLOCK_MAX_ROWS || op.ncolor < 2) return 0;
+    return grid_sgs_blocks(op);
+}
+
+// Grid sweeps are not captured into the batched solve's multi-branch graph (its branches run
+// concurrently and persistent grids would compete for the SMs): capture_cg turns them off on its
+// thread while it captures.
+static thread_local bool g_grid_sweep_off = false;
 
 template <typename T>
 static void sgs(const SmoothOp<T>& op, const T* b, T* x, cudaStream_t s) {
@@ -494,6 +684,12 @@ static void sgs(const SmoothOp<T>& op, const T* b, T* x, cudaStream_t s) {
     if (op.n == 0) return;
     if (op.cluster) {
 #define F(C) launch_sgs_cluster<T, C>(op, b, x, s)
+        SPHC_CH_SWITCH(m.ch, F)
+#undef F
+        return;
+    }
+    if (op.grid && op.bar && !g_grid_sweep_off) {
+#define F(C) launch_sgs_grid<T, C>(op, b, x, s)
         SPHC_CH_SWITCH(m.ch, F)
 #undef F
         return;
@@ -756,6 +952,7 @@ static int autotune_op(const DCSR& A, const int32_t* rmap, const int32_t* cmap, 
     launch_pdl(k_zero<T>, grid_for(op.n, 256), 256, 0, s, xvec.p, op.n);
     int l0 = sell_lpr_for(A, (int)cstart.size() - 1);
     float best = 1e30f;
+    op.grid = 0;                                      // the tuner chooses between the other forms
     int best_ch = op.m.ch, best_lpr = op.m.lpr, best_cluster = op.cluster;
     int rc = SPHC_OK;
     for (int lpr : {l0 / 2, l0, 2 * l0}) {
@@ -892,7 +1089,49 @@ static int cg_body(Hierarchy& H, cudaGraphConditionalHandle hnd, cudaStream_t s)
     return SPHC_OK;
 }
 
+// Whether some smoother of H runs the grid sweep, and turning them all back into per-colour
+// launches (the CG graph is then captured again).
+template <typename T>
+static bool any_grid(const std::vector<VLevel<T>>& V) {
+    for (const auto& v : V)
+        if (v.A.grid || v.An.grid) return true;
+    return false;
+}
+template <typename T>
+static void grid_off(std::vector<VLevel<T>>& V) {
+    for (auto& v : V) v.A.grid = v.An.grid = 0;
+}
+static bool has_grid_sweeps(const Hierarchy& H) { return any_grid(H.V32) || any_grid(H.V64); }
+
+// SPHC_ETIMEOUT when a grid sweep gave up at its barrier since the last check (the barrier is then
+// reset for the next solve), else SPHC_OK.  Synchronises s.
+int grid_sweep_status(Hierarchy& H, cudaStream_t s) {
+    if (!H.gbar.p || !has_grid_sweeps(H)) return SPHC_OK;
+    GridBar hb = {};
+    SPHC_CK(cudaMemcpyAsync(&hb, H.gbar.p, sizeof(GridBar), cudaMemcpyDeviceToHost, s));
+    SPHC_CK(cudaStreamSynchronize(s));
+    if (hb.err == 0) return SPHC_OK;
+    SPHC_TRY(H.gbar.zero(s));
+    set_error("a smoother sweep gave up waiting at its grid barrier (%u polls): the V-cycle result is invalid",
+              H.opts.grid_wait_polls > 0 ? (unsigned)H.opts.grid_wait_polls : GRID_BAR_POLLS);
+    return SPHC_ETIMEOUT;
+}
+
+static int build_cg_graph_once(Hierarchy& H);
+// The CG graph; if capturing the cooperative grid sweeps into it fails, they become per-colour
+// launches and the graph is captured again.
 static int build_cg_graph(Hierarchy& H) {
+    const int rc = build_cg_graph_once(H);
+    if (rc != SPHC_ECUDA || !has_grid_sweeps(H)) return rc;
+    cudaGetLastError();
+    if (H.cg_graph && !H.cg_exec) cudaGraphDestroy(H.cg_graph);
+    H.cg_graph = nullptr;
+    grid_off(H.V32);
+    grid_off(H.V64);
+    return build_cg_graph_once(H);
+}
+
+static int build_cg_graph_once(Hierarchy& H) {
     if (H.cg_exec) return SPHC_OK;
     if (!H.cap_stream) SPHC_CK(cudaStreamCreateWithFlags(&H.cap_stream, cudaStreamNonBlocking));
     SPHC_CK(cudaGraphCreate(&H.cg_graph, 0));
@@ -1011,6 +1250,7 @@ static int pcg_graph(Hierarchy& H, const double* b, double* x, double tol, cudaS
     if (iters) *iters = it;
     if (relres) *relres = rr;
     cg_error(status, it);
+    SPHC_TRY(grid_sweep_status(H, s));
     return status;
 }
 
@@ -1049,7 +1289,14 @@ static int cg_iter_body(Hierarchy& H, cudaGraphConditionalHandle hnd, cudaStream
 }
 
 // Append the whole CG of H to the graph being captured on stream s.
+static int capture_cg_impl(Hierarchy& H, cudaStream_t s);
 int capture_cg(Hierarchy& H, cudaStream_t s) {
+    g_grid_sweep_off = true;
+    const int rc = capture_cg_impl(H, s);
+    g_grid_sweep_off = false;
+    return rc;
+}
+static int capture_cg_impl(Hierarchy& H, cudaStream_t s) {
     int64_t n = H.L[0].A.nr;
     double* sc = H.scal.p;
     if (!H.cap_stream) SPHC_CK(cudaStreamCreateWithFlags(&H.cap_stream, cudaStreamNonBlocking));
@@ -1155,6 +1402,7 @@ int pcg_solve(Hierarchy& H, const double* b, double* x, double tol, cudaStream_t
     if (iters) *iters = it;
     if (relres) *relres = rr;
     cg_error(status, it);
+    SPHC_TRY(grid_sweep_status(H, s));
     return status;
 }
 
@@ -1164,7 +1412,7 @@ int apply_vcycle_user(Hierarchy& H, const double* r, double* z, cudaStream_t s) 
     SPHC_TRY(gather64(r, perm0(H), n, H.q.p, s));
     SPHC_TRY(apply_vcycle(H, H.q.p, H.z.p, s));
     SPHC_TRY(scatter64(H.z.p, perm0(H), n, z, s));
-    return SPHC_OK;
+    return grid_sweep_status(H, s);
 }
 
 }  // namespace sphc

@@ -1,6 +1,7 @@
 // Sparse building blocks of the setup phase: scans, transposes, segmented sorts, the
 // structural sparse matrix product (used for D_h^T A_e D_h, A_n Pbar, D_h P_n and the Galerkin
 // products P_e^T A_e P_e, P_n^T A_n P_n of Sec. 2), FP64 SpMV and deterministic dots.
+#include <cstdlib>
 #include <cstdarg>
 #include <cstdint>
 #include <cstdio>
@@ -362,6 +363,103 @@ __global__ void k_dmul(const int64_t* __restrict__ drp, const int32_t* __restric
         ++c;
     }
     if (!mode) cnt[i] = c;
+}
+
+// ------------------------------------------------------------------ matrix times gradient
+// C = A D for D with at most two entries per row and A rows of at most 32 entries: warp per row.
+// Lane k takes A's entry k (column f) and the one or two node ids of D's row f.  The distinct
+// nodes of the row come out in ascending order from a warp min-reduction over the lanes' ids
+// (one round per node, which then leaves the candidate set); two ballots per round record the
+// lanes that reach it, kept by lane c % 32 for the c-th node.  In the fill pass each lane then
+// adds up its node's products a_if d_fn over those lanes in ascending lane order, i.e. in A's row
+// order, the order a sparse accumulator walking A's row uses.  Mode 0 counts the nodes of each
+// row, mode 1 writes them.
+constexpr int AD_WARPS = 8;
+__global__ void __launch_bounds__(AD_WARPS * 32)
+k_amul_d(const int64_t* __restrict__ arp, const int32_t* __restrict__ aci, const double* __restrict__ av, int64_t n,
+         const int64_t* __restrict__ drp, const int32_t* __restrict__ dci, const double* __restrict__ dv, int mode,
+         int64_t* __restrict__ cnt, const int64_t* __restrict__ crp, int32_t* __restrict__ cci,
+         double* __restrict__ cv) {
+    __shared__ double s_val[AD_WARPS][64];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t i = (int64_t)blockIdx.x * AD_WARPS + w;
+    if (i >= n) return;
+    const int NONE = 0x7fffffff;
+    int k0 = NONE, k1 = NONE;
+    const int64_t a0 = arp[i];
+    if (lane < arp[i + 1] - a0) {
+        const int32_t f = aci[a0 + lane];
+        const int64_t d0 = drp[f], dl = drp[f + 1] - d0;
+        if (dl > 0) k0 = dci[d0];
+        if (dl > 1) k1 = dci[d0 + 1];
+        if (mode != 0) {
+            const double a = av[a0 + lane];
+            s_val[w][lane] = dl > 0 ? a * dv[d0] : 0.0;
+            s_val[w][32 + lane] = dl > 1 ? a * dv[d0 + 1] : 0.0;
+        }
+    }
+    unsigned lo0 = 0, lo1 = 0, hi0 = 0, hi1 = 0;     // ballots of node lane and node lane + 32
+    int node_lo = NONE, node_hi = NONE;
+    int c = 0;
+    for (;;) {
+        const int m = __reduce_min_sync(0xffffffffu, k0 < k1 ? k0 : k1);
+        if (m == NONE) break;
+        const unsigned b0 = __ballot_sync(0xffffffffu, k0 == m), b1 = __ballot_sync(0xffffffffu, k1 == m);
+        if (lane == (c & 31)) {
+            if (c < 32) { lo0 = b0; lo1 = b1; node_lo = m; }
+            else { hi0 = b0; hi1 = b1; node_hi = m; }
+        }
+        if (k0 == m) k0 = NONE;
+        if (k1 == m) k1 = NONE;
+        ++c;
+    }
+    if (mode == 0) {
+        if (lane == 0) cnt[i] = c;
+        return;
+    }
+    __syncwarp();
+    const int64_t out = crp[i];
+    for (int r = 0; r < 2; ++r) {
+        const int slot = lane + 32 * r;
+        if (slot >= c) break;
+        const unsigned b0 = r ? hi0 : lo0, b1 = r ? hi1 : lo1;
+        unsigned any = b0 | b1;
+        double sum = 0.0;
+        while (any) {
+            const int l = __ffs(any) - 1;
+            any &= any - 1;
+            if ((b0 >> l) & 1u) sum += s_val[w][l];
+            if ((b1 >> l) & 1u) sum += s_val[w][32 + l];
+        }
+        cci[out + slot] = r ? node_hi : node_lo;
+        cv[out + slot] = sum;
+    }
+}
+
+int amul_d(const DCSR& A, const DCSR& D, DCSR& C, cudaStream_t s) {
+    int64_t amax = 0, dmax = 0;
+    SPHC_TRY(max_row_length(A.rp.p, A.nr, s, &amax));
+    SPHC_TRY(max_row_length(D.rp.p, D.nr, s, &dmax));
+    if (amax > 32 || dmax > 2) return spgemm(A, D, C, s);
+    const int64_t n = A.nr;
+    DBuf<int64_t> cnt;
+    SPHC_TRY(cnt.alloc(n + 1, s));
+    const int g = grid_for(n, AD_WARPS);
+    if (n > 0)
+        SPHC_LAUNCH(k_amul_d<<<g, AD_WARPS * 32, 0, s>>>(A.rp.p, A.ci.p, A.v.p, n, D.rp.p, D.ci.p, D.v.p, 0, cnt.p,
+                                                        nullptr, nullptr, nullptr));
+    C = DCSR();
+    C.nr = n;
+    C.nc = D.nc;
+    SPHC_TRY(C.rp.alloc(n + 1, s));
+    SPHC_TRY(exclusive_scan_i64(cnt.p, C.rp.p, n, s, &C.nnz));
+    SPHC_TRY(C.ci.alloc(C.nnz, s));
+    SPHC_TRY(C.v.alloc(C.nnz, s));
+    if (n > 0)
+        SPHC_LAUNCH(k_amul_d<<<g, AD_WARPS * 32, 0, s>>>(A.rp.p, A.ci.p, A.v.p, n, D.rp.p, D.ci.p, D.v.p, 1, nullptr,
+                                                        C.rp.p, C.ci.p, C.v.p));
+    SPHC_CK(cudaGetLastError());
+    return SPHC_OK;
 }
 
 int dmul(const DCSR& D, const DCSR& B, DCSR& C, cudaStream_t s) {
@@ -752,7 +850,7 @@ template <int SLOTS, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32)
 k_spgemm_numeric(const int64_t* arp, const int32_t* aci, const double* av, const int64_t* brp,
                  const int32_t* bci, const double* bv, const int32_t* rows, int nrows, int upper, const int64_t* crp,
-                 int32_t* cci, double* cv, const int64_t* ub) {
+                 int32_t* cci, double* cv) {
     __shared__ int32_t s_keys[WARPS][SLOTS];
     __shared__ double s_vals[WARPS][SLOTS];
     __shared__ ProdWindow s_win[WARPS];
@@ -767,9 +865,7 @@ k_spgemm_numeric(const int64_t* arp, const int32_t* aci, const double* av, const
     int clen = (int)(crp[i + 1] - c0);
     int fill = SLOTS == MED_SLOTS ? MED_FILL : SLOTS;
     if (clen > fill) return;  // big path
-    int64_t ubi = ub[i];
-    int tsize = 32;
-    while (tsize < SLOTS && tsize < 2 * ubi) tsize <<= 1;
+    int tsize = 32;                              // at most half full: the row's length is known
     while (tsize < SLOTS && tsize < 2 * clen) tsize <<= 1;
     int tmask = tsize - 1;
     for (int t = lane; t < tsize; t += 32) { keys[t] = -1; vals[t] = 0.0; }
@@ -870,13 +966,90 @@ static void launch_symbolic(const DCSR& A, const DCSR& B, const int32_t* rows, i
 }
 template <int SLOTS, int WARPS>
 static void launch_numeric(const DCSR& A, const DCSR& B, DCSR& C, const int32_t* rows, int nrows, int upper,
-                           const int64_t* ub, cudaStream_t s) {
+                           cudaStream_t s) {
     if (nrows <= 0) return;
     SPHC_LAUNCH((k_spgemm_numeric<SLOTS, WARPS><<<(nrows + WARPS - 1) / WARPS, WARPS * 32, 0, s>>>(
-        A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p, B.v.p, rows, nrows, upper, C.rp.p, C.ci.p, C.v.p, ub)));
+        A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p, B.v.p, rows, nrows, upper, C.rp.p, C.ci.p, C.v.p)));
+}
+
+// Numeric bins by output row length (known once the symbolic pass has run): a row's table holds
+// at most twice its columns, so rows with many products but few columns (the P^T (A P) rows of a
+// Galerkin product: thousands of products, tens of columns) take small tables and many warps
+// share an SM.  Bin b holds rows of at most 32 << b columns (tables of 64 << b slots); rows above
+// MED_FILL columns are on the big path.
+static constexpr int NUM_BINS = 5;
+static constexpr int NUM_REBIN_MIN_ROWS = 1 << 16;
+__device__ inline int numeric_bin_of(int64_t clen) {
+    if (clen > MED_FILL) return -1;
+    int b = 0;
+    while (b < NUM_BINS - 1 && clen > (32 << b)) ++b;
+    return b;
+}
+__global__ void k_numeric_bin_count(const int32_t* rows, int nrows, const int64_t* crp, int* bin_cnt) {
+    const int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int bin = -1;
+    if (li < nrows) {
+        const int32_t i = rows[li];
+        bin = numeric_bin_of(crp[i + 1] - crp[i]);
+    }
+    for (int b = 0; b < NUM_BINS; ++b) {
+        const int c = __syncthreads_count(bin == b);
+        if (threadIdx.x == 0 && c) atomicAdd(&bin_cnt[b], c);
+    }
+}
+__global__ void k_numeric_bin_fill(const int32_t* rows, int nrows, const int64_t* crp, const int* bin_off,
+                                   int* bin_fill, int32_t* out) {
+    const int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (li >= nrows) return;
+    const int32_t i = rows[li];
+    const int bin = numeric_bin_of(crp[i + 1] - crp[i]);
+    if (bin < 0) return;
+    const unsigned m = __match_any_sync(__activemask(), bin);
+    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(&bin_fill[bin], __popc(m));
+    base = __shfl_sync(m, base, leader);
+    out[bin_off[bin] + base + __popc(m & ((1u << lane) - 1u))] = i;
+}
+// the numeric pass of the listed rows (their row pointers in C already set), binned by length
+static int numeric_by_length(const DCSR& A, const DCSR& B, DCSR& C, const int32_t* rows, int nrows, int upper,
+                             cudaStream_t s) {
+    if (nrows <= 0) return SPHC_OK;
+    DBuf<int> cnt;                       // 0..4 counts, 5..9 offsets, 10..14 fill
+    DBuf<int32_t> list;
+    SPHC_TRY(cnt.alloc(3 * NUM_BINS, s));
+    SPHC_TRY(cnt.zero(s));
+    SPHC_TRY(list.alloc(nrows, s));
+    SPHC_LAUNCH(k_numeric_bin_count<<<grid_for(nrows, 256), 256, 0, s>>>(rows, nrows, C.rp.p, cnt.p));
+    int h[NUM_BINS] = {0};
+    SPHC_CK(cudaMemcpyAsync(h, cnt.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+    SPHC_CK(cudaStreamSynchronize(s));
+    int off[NUM_BINS];
+    off[0] = 0;
+    for (int b = 1; b < NUM_BINS; ++b) off[b] = off[b - 1] + h[b - 1];
+    SPHC_CK(cudaMemcpyAsync(cnt.p + NUM_BINS, off, sizeof(off), cudaMemcpyHostToDevice, s));
+    SPHC_LAUNCH(k_numeric_bin_fill<<<grid_for(nrows, 256), 256, 0, s>>>(rows, nrows, C.rp.p, cnt.p + NUM_BINS,
+                                                                         cnt.p + 2 * NUM_BINS, list.p));
+    launch_numeric<64, 16>(A, B, C, list.p + off[0], h[0], upper, s);
+    launch_numeric<128, 16>(A, B, C, list.p + off[1], h[1], upper, s);
+    launch_numeric<256, 8>(A, B, C, list.p + off[2], h[2], upper, s);
+    launch_numeric<512, 4>(A, B, C, list.p + off[3], h[3], upper, s);
+    launch_numeric<1024, 2>(A, B, C, list.p + off[4], h[4], upper, s);
+    SPHC_CK(cudaGetLastError());
+    return SPHC_OK;
+}
+
+// Test switches of the path choices below, read from the environment variable SPHC_SPGEMM_PATHS
+// (a bit mask, 0 when unset): 1 the small bin's counting and writing passes instead of its one
+// pass into temporary slots; 2 the numeric pass binned by row length whatever the number of rows;
+// 4 never binned by row length.  Every path gives the same matrix.
+static int spgemm_path_flags() {
+    const char* e = getenv("SPHC_SPGEMM_PATHS");
+    return e ? atoi(e) : 0;
 }
 
 static int spgemm_impl(const DCSR& A, const DCSR& B, DCSR& C, int upper, cudaStream_t s) {
+    const int paths = spgemm_path_flags();
     if (A.nc != B.nr) {
         set_error("spgemm: inner dimensions %lld vs %lld", (long long)A.nc, (long long)B.nr);
         return SPHC_EINVAL;
@@ -928,7 +1101,7 @@ static int spgemm_impl(const DCSR& A, const DCSR& B, DCSR& C, int upper, cudaStr
             SPHC_LAUNCH(k_list_ub<<<grid_for(h[2], 256), 256, 0, s>>>(rows.p, h[2], ub.p, lub.p));
             SPHC_TRY(exclusive_scan_i64(lub.p, toff.p, h[2], s, &tslots));
             size_t fr = 0, tt = 0;
-            small_one_pass = cudaMemGetInfo(&fr, &tt) == cudaSuccess &&
+            small_one_pass = !(paths & 1) && cudaMemGetInfo(&fr, &tt) == cudaSuccess &&
                              (double)tslots * (sizeof(int32_t) + sizeof(double)) <= 0.25 * (double)fr;
             cudaGetLastError();
             if (small_one_pass) {
@@ -978,9 +1151,17 @@ static int spgemm_impl(const DCSR& A, const DCSR& B, DCSR& C, int upper, cudaStr
         else if (h[2] > 0)
             SPHC_LAUNCH(k_spgemm_small<<<(h[2] + SMALL_WARPS - 1) / SMALL_WARPS, SMALL_WARPS * 32, 0, s>>>(
                 A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p, B.v.p, rows.p, h[2], 1, upper, nullptr, C.rp.p, C.ci.p, C.v.p));
-        launch_numeric<256, 4>(A, B, C, rows.p + off[1], h[3], upper, ub.p, s);
-        launch_numeric<512, 4>(A, B, C, rows.p + off[2], h[4], upper, ub.p, s);
-        launch_numeric<1024, 2>(A, B, C, rows.p + off[3], h[5], upper, ub.p, s);
+        // Re-binned by length where the rows fill the GPU many times over; a few thousand rows
+        // of long product lists (the Galerkin product of a mid level) run better as one launch
+        // per product-count bin than split over length bins that each wait for their longest row.
+        const int nmed = h[3] + h[4] + h[5];
+        if ((paths & 2) || (!(paths & 4) && nmed >= NUM_REBIN_MIN_ROWS)) {
+            SPHC_TRY(numeric_by_length(A, B, C, rows.p + off[1], nmed, upper, s));
+        } else {
+            launch_numeric<256, 4>(A, B, C, rows.p + off[1], h[3], upper, s);
+            launch_numeric<512, 4>(A, B, C, rows.p + off[2], h[4], upper, s);
+            launch_numeric<1024, 2>(A, B, C, rows.p + off[3], h[5], upper, s);
+        }
     }
     if (nbig > 0) {
         SPHC_CK(cudaFuncSetAttribute(k_spgemm_numeric_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)big_num_sm));

@@ -164,6 +164,9 @@ int spgemm_sym(const DCSR& A, const DCSR& B, DCSR& C, cudaStream_t s);
 // C = D B for D with at most two entries per row (thread-per-row merge; spgemm otherwise),
 // same result as spgemm
 int dmul(const DCSR& D, const DCSR& B, DCSR& C, cudaStream_t s);
+// C = A D for a D with at most two entries per row and A rows of at most 32 entries (warp-per-row
+// sort; spgemm otherwise), same entries as spgemm
+int amul_d(const DCSR& A, const DCSR& D, DCSR& C, cudaStream_t s);
 // At = A^T, rows sorted.
 int transpose(const DCSR& A, DCSR& At, cudaStream_t s);
 // copy a CSR

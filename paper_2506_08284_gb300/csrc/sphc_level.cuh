@@ -33,6 +33,18 @@ struct Sell {
     DBuf<T> v;
 };
 
+// State of the grid barrier of the persistent sweep (device memory, zeroed when the V-cycle
+// operators are built): arrivals at the current barrier, its generation, and an error word that a
+// wait sets when it gives up.
+struct GridBar {
+    unsigned count;
+    unsigned gen;
+    int err;
+    int pad;
+};
+// polls of a barrier wait before it gives up, unless sphc_opts.grid_wait_polls says otherwise
+static constexpr unsigned GRID_BAR_POLLS = 1u << 22;
+
 // Operator of one smoother in the level's V-cycle numbering (rows grouped by colour).
 template <typename T>
 struct SmoothOp {
@@ -43,16 +55,21 @@ struct SmoothOp {
     Sell<T> m;
     DBuf<T> dinv;
     int cluster = 0;                 // 1: whole sweeps on one thread-block cluster (x in shared memory)
+    int grid = 0;                    // co-resident CTAs of the persistent grid sweep (0: not used)
+    GridBar* bar = nullptr;          // its barrier state
+    unsigned polls = 0;              // polls of a barrier wait before it gives up
     int64_t n_last = 0, nnz_last = 0; // rows and nonzeros of the last colour (swept once per sweep)
 };
 // smoothers of at most this many rows sweep in one thread block (colours separated by block
 // barriers)
 static constexpr int SGS_BLOCK_MAX_ROWS = 2048;
-// how sgs() runs op: 0 a launch per colour, 1 the cluster sweep, 2 the one-block sweep
+// how sgs() runs op: 0 a launch per colour, 1 the cluster sweep, 2 the one-block sweep, 3 the
+// persistent grid sweep
 template <typename T>
 inline int sweep_kind(const SmoothOp<T>& op) {
     if (op.n == 0) return 0;
     if (op.cluster) return 1;
+    if (op.grid) return 3;
     return op.n <= SGS_BLOCK_MAX_ROWS ? 2 : 0;
 }
 
@@ -207,6 +224,7 @@ struct Hierarchy {
     // CG as one CUDA graph: a device-side while loop (conditional node) around one iteration
     DBuf<double> dpart;              // partial sums of the dot products
     DBuf<int> itc;                   // [0] iterations, [1] status (0 converged, 1 breakdown, 2 cap)
+    DBuf<GridBar> gbar;              // barrier of the persistent grid sweeps (shared: they run in turn)
     cudaGraph_t cg_graph = nullptr;
     cudaGraphExec_t cg_exec = nullptr;
     cudaStream_t cap_stream = nullptr;
@@ -251,6 +269,7 @@ int build_dt_enc(const DCSR& Dt, const int32_t* pn, const int32_t* ie, DBuf<int3
 int gather64(const double* src, const int32_t* p, int64_t n, double* dst, cudaStream_t s);
 int scatter64(const double* src, const int32_t* p, int64_t n, double* dst, cudaStream_t s);
 int apply_vcycle(Hierarchy& H, const double* r, double* z, cudaStream_t s);
+int grid_barrier_check(int extra, unsigned max_polls, int* timed_out, cudaStream_t s);
 int apply_vcycle_user(Hierarchy& H, const double* r, double* z, cudaStream_t s);
 int pcg_solve(Hierarchy& H, const double* b, double* x, double tol, cudaStream_t s, int* iters, double* relres);
 int capture_cg(Hierarchy& H, cudaStream_t s);

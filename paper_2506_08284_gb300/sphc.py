@@ -40,7 +40,7 @@ class sphc_opts(ctypes.Structure):
                 ("autotune", ctypes.c_int32), ("sweep_form", ctypes.c_int32), ("mlp_wait_polls", ctypes.c_int32),
                 ("sell_lpr0", ctypes.c_int32), ("sell_ch0", ctypes.c_int32), ("emin_fp32", ctypes.c_int32),
                 ("block_rhs", ctypes.c_int32), ("emin_method", ctypes.c_int32), ("pn_alg1", ctypes.c_int32),
-                ("sa_theta", ctypes.c_double), ("alg1_passes", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
+                ("sa_theta", ctypes.c_double), ("alg1_passes", ctypes.c_int32), ("grid_wait_polls", ctypes.c_int32)]
 
 
 class sphc_train_opts(ctypes.Structure):
@@ -83,7 +83,8 @@ EXPORTED = ["sphc_default_opts", "sphc_setup", "sphc_solve", "sphc_vcycle", "sph
             "sphc_get_profile", "sphc_launch_count", "sphc_relres_noalloc", "sphc_default_train_opts",
             "sphc_mlp_train", "sphc_mlp_predict", "sphc_mlp_gradient", "sphc_export_features",
             "sphc_setup_batched", "sphc_solve_batched", "sphc_batch_destroy", "sphc_trim_memory",
-            "sphc_memory_usage", "sphc_mlp_predict_level", "sphc_cond_estimate", "sphc_setup_update", "sphc_vcycle_factor", "sphc_prolongator_energy"]
+            "sphc_memory_usage", "sphc_mlp_predict_level", "sphc_cond_estimate", "sphc_setup_update", "sphc_vcycle_factor", "sphc_prolongator_energy",
+            "sphc_grid_barrier_check"]
 
 _lib = None
 
@@ -121,6 +122,7 @@ def load(path: str | None = None):
     lib.sphc_setup_update.argtypes = [P, P, P]
     lib.sphc_vcycle_factor.argtypes = [P, I, I, ctypes.c_uint64, P, P]
     lib.sphc_prolongator_energy.argtypes = [P, I, P, P]
+    lib.sphc_grid_barrier_check.argtypes = [I, I, P, P]
     lib.sphc_setup_batched.argtypes = [I, P, P, P, P, ctypes.POINTER(sphc_opts), P, ctypes.POINTER(P)]
     lib.sphc_solve_batched.argtypes = [P, P, P, I, ctypes.c_double, P, P, P]
     lib.sphc_batch_destroy.argtypes = [P]
@@ -414,6 +416,15 @@ def memory_usage(device: int = 0):
     u, r = ctypes.c_int64(), ctypes.c_int64()
     _check(load().sphc_memory_usage(int(device), ctypes.byref(u), ctypes.byref(r)))
     return u.value, r.value
+
+
+def grid_barrier_check(extra_arrivals: int, polls: int = 0, stream=None) -> bool:
+    """Run the persistent sweep's grid barrier three times on the current device, counting
+    `extra_arrivals` arrivals more than there are thread blocks; True when the waits gave up
+    (always, for extra_arrivals > 0)."""
+    t = ctypes.c_int()
+    _check(load().sphc_grid_barrier_check(int(extra_arrivals), int(polls), ctypes.byref(t), _stream(stream)))
+    return bool(t.value)
 
 
 def trim_memory(device: int = 0, keep_bytes: int = 0) -> int:

@@ -119,18 +119,19 @@ def test_fp64_vcycle_matches_oracle(pair):
         assert np.abs(e).max() <= FP64_RTOL * np.abs(zo).max()
 
 
-@pytest.mark.parametrize("form", [1, 2])
+@pytest.mark.parametrize("form", [1, 2, 3])
 def test_sweep_forms_match_oracle(pair, form):
-    # the same V-cycle with every smoother above one block swept per colour launch (1) or on one
-    # thread-block cluster (2, where x fits shared memory): both against the oracle
+    # the same V-cycle with every smoother above one block swept per colour launch (1), on one
+    # thread-block cluster (2, where x fits shared memory) or as one cooperative grid with a grid
+    # barrier between colours (3): all against the oracle
     name, p, h, o, opts = pair
     import torch
     hf = gpu_setup(p, vcycle_fp32=0, sweep_form=form, **opts)
     kinds = [hf.level_info(l)["sweep_kind_edge"] for l in range(hf.stats()["n_levels"] - 1)]
     if form == 1:
-        assert 1 not in kinds
+        assert 1 not in kinds and 3 not in kinds
     elif p.n_edges > 2048:
-        assert kinds[0] == 1
+        assert kinds[0] == (1 if form == 2 else 3)
     r = meshgen.rhs(11, p.n_edges)
     rt = torch.tensor(r, device="cuda")
     zt = torch.empty_like(rt)
