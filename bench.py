@@ -604,14 +604,18 @@ def main():
         o2 = make_opts(pkg, "headline", weights, 0, not args.no_graph)
         step(o2, Ah, Dh, ch, sh, bh, xh)
         torch.cuda.synchronize()
+        eclk = ClockSampler(local)
+        eclk.start()
         t1 = time.perf_counter()
-        for _ in range(args.steps):
-            step(o2, Ah, Dh, ch, sh, bh, xh)
+        eres = [step(o2, Ah, Dh, ch, sh, bh, xh) for _ in range(args.steps)]
         torch.cuda.synchronize()
         te = max_over_ranks((time.perf_counter() - t1) / args.steps, dist, "cuda")
+        eclocks = eclk.stop()
         h2d = sum(a.nbytes for a in (p.A_rowptr, p.A_col, p.A_val, p.D_rowptr, p.D_col, p.D_val, p.coords,
                                      p.sigma_edge, b))
-        e2e = {"value": te / world, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(b.nbytes)}
+        e_st = eres[-1][4]
+        e2e = {"value": te / world, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(b.nbytes),
+               "last_step_setup_ms": e_st["setup_ms"], "last_step_solve_ms": e_st["solve_ms"], "clocks": eclocks}
 
     peak, peak_kind = peaks()
     roof = None
