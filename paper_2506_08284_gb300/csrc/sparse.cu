@@ -854,6 +854,7 @@ k_spgemm_numeric(const int64_t* arp, const int32_t* aci, const double* av, const
     __shared__ int32_t s_keys[WARPS][SLOTS];
     __shared__ double s_vals[WARPS][SLOTS];
     __shared__ ProdWindow s_win[WARPS];
+    __shared__ double s_fa[WARPS][32], s_fb[WARPS][32];     // this round's factors, per lane
     int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int64_t li = (int64_t)blockIdx.x * WARPS + w;
     if (li >= nrows) return;
@@ -871,23 +872,49 @@ k_spgemm_numeric(const int64_t* arp, const int32_t* aci, const double* av, const
     for (int t = lane; t < tsize; t += 32) { keys[t] = -1; vals[t] = 0.0; }
     __syncwarp();
     int64_t a0 = arp[i], a1 = arp[i + 1];
+    // Products go round by round, 32 at a time in product order (A's row, then each B row).  A
+    // lane finds (or claims) its column's slot; the lanes of one slot are matched, and the lowest
+    // of them adds their a_ik b_kj to the slot with fused multiply-adds in lane order.  No FP64
+    // atomics, and each column's sum is taken in product order.
     for (int64_t base = a0; base < a1; base += 32) {
         int64_t total = window_load(s_win[w], bci, floor, base, a1, aci, av, brp, lane);
-        for (int64_t t = lane; t < total; t += 32) {
-            int lo = window_find(s_win[w], t);
-            int64_t kb = s_win[w].bst[lo] + (t - s_win[w].off[lo]);
-            int32_t col = bci[kb];
-            double prod = s_win[w].av[lo] * bv[kb];
-            uint32_t h = hslot(col, tmask);
-            for (int probe = 0; probe < tsize; ++probe) {
-                int32_t cur = keys[h];
-                if (cur == col) { atomicAdd(&vals[h], prod); break; }
-                if (cur == -1) {
-                    int32_t old = atomicCAS(&keys[h], -1, col);
-                    if (old == -1 || old == col) { atomicAdd(&vals[h], prod); break; }
+        for (int64_t t0 = 0; t0 < total; t0 += 32) {
+            const int64_t t = t0 + lane;
+            int slot = -1;
+            double fa = 0.0, fb = 0.0;
+            if (t < total) {
+                int lo = window_find(s_win[w], t);
+                int64_t kb = s_win[w].bst[lo] + (t - s_win[w].off[lo]);
+                int32_t col = bci[kb];
+                fa = s_win[w].av[lo];
+                fb = bv[kb];
+                uint32_t h = hslot(col, tmask);
+                for (int probe = 0; probe < tsize; ++probe) {
+                    int32_t cur = keys[h];
+                    if (cur == col) { slot = (int)h; break; }
+                    if (cur == -1) {
+                        int32_t old = atomicCAS(&keys[h], -1, col);
+                        if (old == -1 || old == col) { slot = (int)h; break; }
+                    }
+                    h = (h + 1) & tmask;
                 }
-                h = (h + 1) & tmask;
             }
+            s_fa[w][lane] = fa;
+            s_fb[w][lane] = fb;
+            const unsigned act = __ballot_sync(0xffffffffu, slot >= 0);
+            __syncwarp();
+            if (slot >= 0) {
+                const unsigned grp = __match_any_sync(act, slot);
+                if (lane == __ffs(grp) - 1) {
+                    double v = vals[slot];
+                    for (unsigned g = grp; g; g &= g - 1) {
+                        const int l = __ffs(g) - 1;
+                        v = fma(s_fa[w][l], s_fb[w][l], v);
+                    }
+                    vals[slot] = v;
+                }
+            }
+            __syncwarp();
         }
         __syncwarp();
     }
