@@ -1,6 +1,7 @@
 // Sparse building blocks of the setup phase: scans, transposes, segmented sorts, the
 // structural sparse matrix product (used for D_h^T A_e D_h, A_n Pbar, D_h P_n and the Galerkin
 // products P_e^T A_e P_e, P_n^T A_n P_n of Sec. 2), FP64 SpMV and deterministic dots.
+#include <algorithm>
 #include <cstdlib>
 #include <cstdarg>
 #include <cstdint>
@@ -845,6 +846,84 @@ __device__ inline void warp_sort_pairs(int32_t* keys, double* vals, int count, i
         }
 }
 
+// Accumulate row i's products into a warp's table (keys, vals; tsize slots, all empty).  Products
+// go round by round, 32 at a time in product order (A's row, then each B row).  A lane finds (or
+// claims) its column's slot; the lanes of one slot are matched, and the lowest of them adds their
+// a_ik b_kj to the slot with fused multiply-adds in lane order.  No FP64 atomics, and each
+// column's sum is taken in product order.  Returns the number of columns, or -1 as soon as it
+// exceeds `limit` (the table then stops growing: limit + 32 <= tsize).
+__device__ inline int accumulate_row(int64_t i, int32_t floor, const int64_t* arp, const int32_t* aci,
+                                     const double* av, const int64_t* brp, const int32_t* bci, const double* bv,
+                                     int32_t* keys, double* vals, int tsize, int limit, ProdWindow& win,
+                                     double* fa_s, double* fb_s, int lane) {
+    const int tmask = tsize - 1;
+    int count = 0;
+    const int64_t a0 = arp[i], a1 = arp[i + 1];
+    for (int64_t base = a0; base < a1; base += 32) {
+        const int64_t total = window_load(win, bci, floor, base, a1, aci, av, brp, lane);
+        for (int64_t t0 = 0; t0 < total; t0 += 32) {
+            const int64_t t = t0 + lane;
+            int slot = -1;
+            bool ins = false;
+            double fa = 0.0, fb = 0.0;
+            if (t < total) {
+                const int lo = window_find(win, t);
+                const int64_t kb = win.bst[lo] + (t - win.off[lo]);
+                const int32_t col = bci[kb];
+                fa = win.av[lo];
+                fb = bv[kb];
+                uint32_t h = hslot(col, tmask);
+                for (int probe = 0; probe < tsize; ++probe) {
+                    const int32_t cur = keys[h];
+                    if (cur == col) { slot = (int)h; break; }
+                    if (cur == -1) {
+                        const int32_t old = atomicCAS(&keys[h], -1, col);
+                        if (old == -1 || old == col) { slot = (int)h; ins = old == -1; break; }
+                    }
+                    h = (h + 1) & tmask;
+                }
+            }
+            fa_s[lane] = fa;
+            fb_s[lane] = fb;
+            const unsigned act = __ballot_sync(0xffffffffu, slot >= 0);
+            count += __popc(__ballot_sync(0xffffffffu, ins));
+            __syncwarp();
+            if (slot >= 0) {
+                const unsigned grp = __match_any_sync(act, slot);
+                if (lane == __ffs(grp) - 1) {
+                    double v = vals[slot];
+                    for (unsigned g = grp; g; g &= g - 1) {
+                        const int l = __ffs(g) - 1;
+                        v = fma(fa_s[l], fb_s[l], v);
+                    }
+                    vals[slot] = v;
+                }
+            }
+            __syncwarp();
+            if (count > limit) return -1;
+        }
+        __syncwarp();
+    }
+    return count;
+}
+// Move the table's keys to its front (order kept), then sort them with their values; returns
+// the count.
+__device__ inline int compact_sort(int32_t* keys, double* vals, int tsize, int lane) {
+    int count = 0;
+    for (int t0 = 0; t0 < tsize; t0 += 32) {
+        const int32_t k = keys[t0 + lane];
+        const double vv = vals[t0 + lane];
+        const unsigned m = __ballot_sync(0xffffffffu, k >= 0);
+        const int pos = count + __popc(m & ((1u << lane) - 1u));
+        __syncwarp();
+        if (k >= 0) { keys[pos] = k; vals[pos] = vv; }
+        count += __popc(m);
+        __syncwarp();
+    }
+    warp_sort_pairs(keys, vals, count, lane);
+    return count;
+}
+
 // numeric: accumulate in the table, compact in place, sort, write the row
 template <int SLOTS, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32)
@@ -868,72 +947,92 @@ k_spgemm_numeric(const int64_t* arp, const int32_t* aci, const double* av, const
     if (clen > fill) return;  // big path
     int tsize = 32;                              // at most half full: the row's length is known
     while (tsize < SLOTS && tsize < 2 * clen) tsize <<= 1;
-    int tmask = tsize - 1;
     for (int t = lane; t < tsize; t += 32) { keys[t] = -1; vals[t] = 0.0; }
     __syncwarp();
-    int64_t a0 = arp[i], a1 = arp[i + 1];
-    // Products go round by round, 32 at a time in product order (A's row, then each B row).  A
-    // lane finds (or claims) its column's slot; the lanes of one slot are matched, and the lowest
-    // of them adds their a_ik b_kj to the slot with fused multiply-adds in lane order.  No FP64
-    // atomics, and each column's sum is taken in product order.
-    for (int64_t base = a0; base < a1; base += 32) {
-        int64_t total = window_load(s_win[w], bci, floor, base, a1, aci, av, brp, lane);
-        for (int64_t t0 = 0; t0 < total; t0 += 32) {
-            const int64_t t = t0 + lane;
-            int slot = -1;
-            double fa = 0.0, fb = 0.0;
-            if (t < total) {
-                int lo = window_find(s_win[w], t);
-                int64_t kb = s_win[w].bst[lo] + (t - s_win[w].off[lo]);
-                int32_t col = bci[kb];
-                fa = s_win[w].av[lo];
-                fb = bv[kb];
-                uint32_t h = hslot(col, tmask);
-                for (int probe = 0; probe < tsize; ++probe) {
-                    int32_t cur = keys[h];
-                    if (cur == col) { slot = (int)h; break; }
-                    if (cur == -1) {
-                        int32_t old = atomicCAS(&keys[h], -1, col);
-                        if (old == -1 || old == col) { slot = (int)h; break; }
-                    }
-                    h = (h + 1) & tmask;
-                }
-            }
-            s_fa[w][lane] = fa;
-            s_fb[w][lane] = fb;
-            const unsigned act = __ballot_sync(0xffffffffu, slot >= 0);
-            __syncwarp();
-            if (slot >= 0) {
-                const unsigned grp = __match_any_sync(act, slot);
-                if (lane == __ffs(grp) - 1) {
-                    double v = vals[slot];
-                    for (unsigned g = grp; g; g &= g - 1) {
-                        const int l = __ffs(g) - 1;
-                        v = fma(s_fa[w][l], s_fb[w][l], v);
-                    }
-                    vals[slot] = v;
-                }
-            }
-            __syncwarp();
-        }
-        __syncwarp();
-    }
-    int count = 0;
-    for (int t0 = 0; t0 < tsize; t0 += 32) {
-        int32_t k = keys[t0 + lane];
-        double vv = vals[t0 + lane];
-        unsigned m = __ballot_sync(0xffffffffu, k >= 0);
-        int pos = count + __popc(m & ((1u << lane) - 1u));
-        __syncwarp();
-        if (k >= 0) { keys[pos] = k; vals[pos] = vv; }
-        count += __popc(m);
-        __syncwarp();
-    }
-    warp_sort_pairs(keys, vals, count, lane);
+    accumulate_row(i, floor, arp, aci, av, brp, bci, bv, keys, vals, tsize, tsize, s_win[w], s_fa[w], s_fb[w], lane);
+    const int count = compact_sort(keys, vals, tsize, lane);
     for (int e = lane; e < count; e += 32) {
         cci[c0 + e] = keys[e];
         cv[c0 + e] = vals[e];
     }
+}
+
+// One pass for rows whose product count exceeds the register-sort bin: accumulate in a table of TS
+// slots; a row of at most TS / 2 columns is sorted and written to a temporary arena (sub-arena
+// blockIdx % SPG_SUBS, reserved by that sub-arena's bump counter; its offset goes to moff[li], its
+// length to cnt[i]).  A row with more columns, or one its sub-arena has no room for, gets
+// moff[li] = -1 and joins the overflow list for the counting and numeric passes.
+static constexpr int SPG_SUBS = 64;
+template <int TS, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32)
+k_spgemm_onepass(const int64_t* arp, const int32_t* aci, const double* av, const int64_t* brp, const int32_t* bci,
+                 const double* bv, const int32_t* rows, int nrows, int upper, int64_t* cnt, int64_t* moff,
+                 int32_t* tci, double* tv, unsigned long long* cursors, int64_t sub_cap, int32_t* ovf, int* novf) {
+    __shared__ int32_t s_keys[WARPS][TS];
+    __shared__ double s_vals[WARPS][TS];
+    __shared__ ProdWindow s_win[WARPS];
+    __shared__ double s_fa[WARPS][32], s_fb[WARPS][32];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t li = (int64_t)blockIdx.x * WARPS + w;
+    if (li >= nrows) return;
+    const int32_t i = rows[li];
+    int32_t* keys = s_keys[w];
+    double* vals = s_vals[w];
+    for (int t = lane; t < TS; t += 32) { keys[t] = -1; vals[t] = 0.0; }
+    __syncwarp();
+    int count = accumulate_row(i, upper ? i : -1, arp, aci, av, brp, bci, bv, keys, vals, TS, TS / 2, s_win[w],
+                               s_fa[w], s_fb[w], lane);
+    int64_t dst = -1;
+    if (count >= 0) {
+        count = compact_sort(keys, vals, TS, lane);
+        const int sub = blockIdx.x % SPG_SUBS;
+        unsigned long long at = 0;
+        if (lane == 0) at = atomicAdd(&cursors[sub], (unsigned long long)count);
+        at = __shfl_sync(0xffffffffu, at, 0);
+        if ((int64_t)at + count <= sub_cap) dst = (int64_t)sub * sub_cap + (int64_t)at;
+    }
+    if (dst < 0) {
+        if (lane == 0) {
+            moff[li] = -1;
+            ovf[atomicAdd(novf, 1)] = i;
+        }
+        return;
+    }
+    for (int e = lane; e < count; e += 32) {
+        tci[dst + e] = keys[e];
+        tv[dst + e] = vals[e];
+    }
+    if (lane == 0) {
+        moff[li] = dst;
+        cnt[i] = count;
+    }
+}
+// copy the one-pass rows (moff >= 0) from the arena into C (warp per row)
+__global__ void k_copy_arena(const int32_t* rows, int nrows, const int64_t* moff, const int32_t* tci, const double* tv,
+                             const int64_t* crp, int32_t* cci, double* cv) {
+    const int64_t li = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (li >= nrows) return;
+    const int64_t t0 = moff[li];
+    if (t0 < 0) return;
+    const int64_t i = rows[li], c0 = crp[i], len = crp[i + 1] - c0;
+    for (int64_t e = lane; e < len; e += 32) {
+        cci[c0 + e] = tci[t0 + e];
+        cv[c0 + e] = tv[t0 + e];
+    }
+}
+// bound on the columns of the listed rows that the one pass keeps: sum of min(products, cap)
+__global__ void k_sum_capped(const int32_t* rows, int nrows, const int64_t* ub, int64_t cap_small, int64_t cap_big,
+                             int64_t big_from, unsigned long long* out) {
+    const int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long v = 0;
+    if (li < nrows) {
+        const int64_t u = ub[rows[li]];
+        const int64_t cap = u > big_from ? cap_big : cap_small;
+        v = (unsigned long long)(u < cap ? u : cap);
+    }
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(out, v);
 }
 
 __global__ void k_spgemm_numeric_big(const int64_t* arp, const int32_t* aci, const double* av,
@@ -1069,7 +1168,9 @@ static int numeric_by_length(const DCSR& A, const DCSR& B, DCSR& C, const int32_
 // Test switches of the path choices below, read from the environment variable SPHC_SPGEMM_PATHS
 // (a bit mask, 0 when unset): 1 the small bin's counting and writing passes instead of its one
 // pass into temporary slots; 2 the numeric pass binned by row length whatever the number of rows;
-// 4 never binned by row length.  Every path gives the same matrix.
+// 4 never binned by row length; 8 the hash bins through counting and numeric passes instead of
+// their one pass into an arena (bits 2 and 4 apply then); 16 sub-arenas of 64 entries, so that
+// most one-pass rows take the overflow path.  Every path gives the same matrix.
 static int spgemm_path_flags() {
     const char* e = getenv("SPHC_SPGEMM_PATHS");
     return e ? atoi(e) : 0;
@@ -1091,6 +1192,12 @@ static int spgemm_impl(const DCSR& A, const DCSR& B, DCSR& C, int upper, cudaStr
     DBuf<double> tv;
     int64_t tslots = 0;
     bool small_one_pass = false;
+    // rows of the hash bins in one pass into an arena (k_spgemm_onepass), overflow rows listed
+    DBuf<int64_t> moff;
+    DBuf<int32_t> mci, ovf;
+    DBuf<double> mv;
+    DBuf<unsigned long long> curs;
+    bool med_one_pass = false;
     SPHC_TRY(ub.alloc(n + 1, s));
     SPHC_TRY(cnt.alloc(n + 1, s));
     SPHC_TRY(big.alloc(n + 1, s));
@@ -1142,11 +1249,65 @@ static int spgemm_impl(const DCSR& A, const DCSR& B, DCSR& C, int upper, cudaStr
                     nullptr));
             }
         }
-        launch_symbolic<256, 8>(A, B, rows.p + off[1], h[3], upper, ub.p, cnt.p, big.p, flags.p, s);
-        launch_symbolic<512, 8>(A, B, rows.p + off[2], h[4], upper, ub.p, cnt.p, big.p, flags.p, s);
-        launch_symbolic<1024, 8>(A, B, rows.p + off[3], h[5], upper, ub.p, cnt.p, big.p, flags.p, s);
+        // The hash bins in one pass where the arena fits a quarter of the free memory: its size is
+        // the sum over the rows of min(products, columns a table keeps), at most four times the
+        // larger operand's nonzeros (rows that find their sub-arena full fall back).  Otherwise,
+        // and for the overflow rows, a counting pass first.
+        const int nmed = h[3] + h[4] + h[5];
+        if (nmed > 0 && !(paths & 8)) {
+            DBuf<unsigned long long> bsum;
+            SPHC_TRY(bsum.alloc(1, s));
+            SPHC_TRY(bsum.zero(s));
+            SPHC_LAUNCH(k_sum_capped<<<grid_for(nmed, 256), 256, 0, s>>>(rows.p + off[1], nmed, ub.p, 64, 256, 256,
+                                                                          bsum.p));
+            unsigned long long hb = 0;
+            SPHC_CK(cudaMemcpyAsync(&hb, bsum.p, sizeof(hb), cudaMemcpyDeviceToHost, s));
+            SPHC_CK(cudaStreamSynchronize(s));
+            const int64_t cap_total = std::min<int64_t>((int64_t)hb, 4 * std::max<int64_t>(A.nnz, B.nnz));
+            const int64_t sub_cap = (paths & 16) ? 64 : (cap_total + SPG_SUBS - 1) / SPG_SUBS + 512;
+            size_t fr = 0, tt = 0;
+            med_one_pass = cudaMemGetInfo(&fr, &tt) == cudaSuccess &&
+                           (double)SPG_SUBS * (double)sub_cap * (sizeof(int32_t) + sizeof(double)) <= 0.25 * (double)fr;
+            cudaGetLastError();
+            if (med_one_pass) {
+                SPHC_TRY(moff.alloc(nmed, s));
+                SPHC_TRY(ovf.alloc(nmed, s));
+                SPHC_TRY(mci.alloc((int64_t)SPG_SUBS * sub_cap, s));
+                SPHC_TRY(mv.alloc((int64_t)SPG_SUBS * sub_cap, s));
+                SPHC_TRY(curs.alloc(SPG_SUBS, s));
+                SPHC_TRY(curs.zero(s));
+                const int part[3] = {h[3], h[4], h[5]};
+                int64_t first = 0;
+                for (int b = 0; b < 3; ++b) {
+                    const int nr = part[b];
+                    if (nr > 0) {
+                        const int32_t* rl = rows.p + off[1] + first;
+                        if (b < 2)
+                            SPHC_LAUNCH((k_spgemm_onepass<128, 16><<<(nr + 15) / 16, 512, 0, s>>>(
+                                A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p, B.v.p, rl, nr, upper, cnt.p, moff.p + first,
+                                mci.p, mv.p, curs.p, sub_cap, ovf.p, flags.p + 14)));
+                        else
+                            SPHC_LAUNCH((k_spgemm_onepass<512, 4><<<(nr + 3) / 4, 128, 0, s>>>(
+                                A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p, B.v.p, rl, nr, upper, cnt.p, moff.p + first,
+                                mci.p, mv.p, curs.p, sub_cap, ovf.p, flags.p + 14)));
+                    }
+                    first += nr;
+                }
+            }
+        }
+        if (!med_one_pass) {
+            launch_symbolic<256, 8>(A, B, rows.p + off[1], h[3], upper, ub.p, cnt.p, big.p, flags.p, s);
+            launch_symbolic<512, 8>(A, B, rows.p + off[2], h[4], upper, ub.p, cnt.p, big.p, flags.p, s);
+            launch_symbolic<1024, 8>(A, B, rows.p + off[3], h[5], upper, ub.p, cnt.p, big.p, flags.p, s);
+        }
     }
     SPHC_CK(cudaGetLastError());
+    int novf = 0;
+    if (med_one_pass) {
+        SPHC_CK(cudaMemcpyAsync(&novf, flags.p + 14, sizeof(int), cudaMemcpyDeviceToHost, s));
+        SPHC_CK(cudaStreamSynchronize(s));
+        if (novf > 0) launch_symbolic<1024, 8>(A, B, ovf.p, novf, upper, ub.p, cnt.p, big.p, flags.p, s);
+    }
     int nbig = 0;
     SPHC_CK(cudaMemcpyAsync(&nbig, flags.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     SPHC_CK(cudaStreamSynchronize(s));
@@ -1182,7 +1343,12 @@ static int spgemm_impl(const DCSR& A, const DCSR& B, DCSR& C, int upper, cudaStr
         // of long product lists (the Galerkin product of a mid level) run better as one launch
         // per product-count bin than split over length bins that each wait for their longest row.
         const int nmed = h[3] + h[4] + h[5];
-        if ((paths & 2) || (!(paths & 4) && nmed >= NUM_REBIN_MIN_ROWS)) {
+        if (med_one_pass) {
+            if (nmed > 0)
+                SPHC_LAUNCH(k_copy_arena<<<grid_for((int64_t)nmed * 32, 256), 256, 0, s>>>(
+                    rows.p + off[1], nmed, moff.p, mci.p, mv.p, C.rp.p, C.ci.p, C.v.p));
+            if (novf > 0) SPHC_TRY(numeric_by_length(A, B, C, ovf.p, novf, upper, s));
+        } else if ((paths & 2) || (!(paths & 4) && nmed >= NUM_REBIN_MIN_ROWS)) {
             SPHC_TRY(numeric_by_length(A, B, C, rows.p + off[1], nmed, upper, s));
         } else {
             launch_numeric<256, 4>(A, B, C, rows.p + off[1], h[3], upper, s);

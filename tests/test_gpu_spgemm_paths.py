@@ -1,9 +1,11 @@
 """Every path of the structural SpGEMM gives the same hierarchy, forced through the test switch
 SPHC_SPGEMM_PATHS (a bit mask read at each product): 1 the small-row bin's counting and writing
 passes instead of its one pass into temporary slots; 2 the numeric pass binned by output row
-length for any number of rows; 4 never binned by length.  The default choice depends on the free
-device memory (1) and on the number of rows (2, 4), so the small test meshes would otherwise
-exercise one branch only.  Each forced path against the CPU oracle: integer patterns bit for bit,
+length for any number of rows; 4 never binned by length; 8 the hash bins through counting and
+numeric passes instead of their one pass into an arena; 16 sub-arenas so small that most one-pass
+rows overflow into the counting path.  The default choices depend on the free device memory and
+on the number of rows, so the small test meshes would otherwise exercise one branch only (the
+coarse levels' long rows also overflow the one-pass tables by themselves).  Each forced path against the CPU oracle: integer patterns bit for bit,
 FP64 values (A_l, A_n, P_n, P_e on every level) to 1e-10 of the largest entry."""
 import pytest
 
@@ -22,7 +24,7 @@ def case():
     return p, oracle_setup(p, **OPTS)
 
 
-@pytest.mark.parametrize("paths", ["1", "2", "4", "3", "5"])
+@pytest.mark.parametrize("paths", ["0", "1", "16", "17", "8", "10", "12", "11", "13"])
 def test_spgemm_paths_match_oracle(case, paths, monkeypatch):
     p, o = case
     monkeypatch.setenv("SPHC_SPGEMM_PATHS", paths)
