@@ -189,14 +189,17 @@ __global__ void k_sell_fill(const int64_t* rp, const int32_t* ci, const double* 
         }
     }
     int64_t o = soff[s];
-    int64_t total = soff[s + 1] - o;
-    for (int64_t p0 = 0; p0 < total; p0 += 32) {
-        int64_t p = p0 + lane;
-        int64_t step = p / (SELL_C * ch);
-        int rem = (int)(p % (SELL_C * ch));
-        int slotl = rem / ch, tch = rem % ch;
-        int q = slotl / lpr, kk = slotl % lpr;
-        int64_t j = (step * lpr + kk) * ch + tch;
+    const int total = (int)(soff[s + 1] - o);        // one slice: far below 2^31 entries
+    // ch and lpr are powers of two (1, 2, 4 and 1 .. 32): shifts and masks, not divisions
+    const int lch = ch == 1 ? 0 : (ch == 2 ? 1 : 2);
+    const int llpr = __ffs(lpr) - 1;
+    for (int p0 = 0; p0 < total; p0 += 32) {
+        const int p = p0 + lane;
+        const int step = p >> (5 + lch);
+        const int rem = p & ((SELL_C << lch) - 1);
+        const int slotl = rem >> lch, tch = rem & (ch - 1);
+        const int q = slotl >> llpr, kk = slotl & (lpr - 1);
+        const int64_t j = ((int64_t)step * lpr + kk) * ch + tch;
         int64_t bq = __shfl_sync(0xffffffffu, b, q);
         int64_t lq = __shfl_sync(0xffffffffu, len, q);
         int64_t iq = __shfl_sync(0xffffffffu, i, q);
@@ -322,16 +325,17 @@ __global__ void k_rp_narrow32(const int64_t* a, int32_t* b, int64_t n) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) b[i] = (int32_t)a[i];
 }
-template <typename T>
+// G lanes per row (the mean row length rounded up to a power of two, 4 to 32)
+template <typename T, int G>
 __global__ void k_perm_fill(const int64_t* rp, const int32_t* ci, const double* v, const int32_t* rmap,
                             const int32_t* cmap, int64_t n, const int32_t* nrp, int32_t* nci, T* nv) {
-    int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
+    int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    int lane = threadIdx.x & (G - 1);
     if (k >= n) return;
     int64_t i = rmap ? rmap[k] : k;
     int64_t b = rp[i], len = rp[i + 1] - b;
     int32_t o = nrp[k];
-    for (int64_t q = lane; q < len; q += 32) {
+    for (int64_t q = lane; q < len; q += G) {
         int32_t c = ci[b + q];
         nci[o + q] = cmap ? cmap[c] : c;
         nv[o + q] = (T)v[b + q];
@@ -351,9 +355,16 @@ int build_csr_perm(const DCSR& A, const int32_t* rmap, const int32_t* cmap, VCSR
     SPHC_LAUNCH(k_rp_narrow32<<<grid_for(A.nr + 1, 256), 256, 0, s>>>(rp64.p, B.rp.p, A.nr + 1));
     SPHC_TRY(B.ci.alloc(A.nnz, s));
     SPHC_TRY(B.v.alloc(A.nnz, s));
-    if (A.nr > 0)
-        SPHC_LAUNCH(k_perm_fill<T><<<grid_for(A.nr * 32, 256), 256, 0, s>>>(A.rp.p, A.ci.p, A.v.p, rmap, cmap, A.nr,
-                                                                         B.rp.p, B.ci.p, B.v.p));
+    if (A.nr > 0) {
+        const double avg = (double)A.nnz / (double)A.nr;
+#define PF(G) SPHC_LAUNCH((k_perm_fill<T, G><<<grid_for(A.nr * G, 256), 256, 0, s>>>(A.rp.p, A.ci.p, A.v.p, rmap, cmap, \
+                                                                                     A.nr, B.rp.p, B.ci.p, B.v.p)))
+        if (avg <= 6) PF(4);
+        else if (avg <= 12) PF(8);
+        else if (avg <= 24) PF(16);
+        else PF(32);
+#undef PF
+    }
     SPHC_CK(cudaGetLastError());
     return SPHC_OK;
 }

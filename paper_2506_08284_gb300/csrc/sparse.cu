@@ -290,6 +290,111 @@ __global__ void k_i64_to_u64(const int64_t* a, unsigned long long* b, int64_t n)
     if (i < n) b[i] = (unsigned long long)a[i];
 }
 
+// Test switches of the path choices of the sparse products and the transpose, read from the
+// environment variable SPHC_SPGEMM_PATHS (a bit mask, 0 when unset): 1 the small bin's counting
+// and writing passes instead of its one pass into temporary slots; 2 the numeric pass binned by
+// row length whatever the number of rows; 4 never binned by row length; 8 the hash bins through
+// counting and numeric passes instead of their one pass into an arena (bits 2 and 4 apply then);
+// 16 sub-arenas of 64 entries, so that most one-pass rows take the overflow path; 32 every
+// transpose by the radix sort.  Every path gives the same matrix.
+static int spgemm_path_flags() {
+    const char* e = getenv("SPHC_SPGEMM_PATHS");
+    return e ? atoi(e) : 0;
+}
+
+// ------------------------------------------------------------------ transpose by stable radix sort
+// The entries of A, in row-major order, are sorted by column with a stable least-significant-digit
+// radix sort of (column, entry index) pairs, RX_BITS bits a pass: per pass, per-block digit
+// histograms, one scan of them (digit-major, block-minor), and a stable scatter (warp match for the
+// rank inside a warp, per-warp counts for the warps before it).  Equal columns keep their entries'
+// order, so every row of A^T comes out sorted by A's row index: the segmented sort of the
+// scatter-based transpose is not needed.  Then A^T's row index and value of each sorted entry are
+// gathered.
+static constexpr int RX_BLOCK = 1024, RX_BITS = 8, RX_KEYS = 1 << RX_BITS;
+static constexpr int64_t TRANSPOSE_RADIX_MIN_NNZ = 1 << 20;     // smaller: scatter + segmented sort
+__global__ void k_rx_init(const int32_t* ci, int64_t nnz, int2* it) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < nnz) it[e] = make_int2(ci[e], (int32_t)e);
+}
+__global__ void k_rx_count(const int2* it, int64_t n, int shift, int32_t* table, int64_t nb) {
+    __shared__ int32_t cnt[RX_KEYS];
+    for (int c = threadIdx.x; c < RX_KEYS; c += blockDim.x) cnt[c] = 0;
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * RX_BLOCK + threadIdx.x;
+    const int c = i < n ? (it[i].x >> shift) & (RX_KEYS - 1) : -1;
+    const unsigned m = __match_any_sync(0xffffffffu, c);     // one add per digit and warp
+    if (c >= 0 && (threadIdx.x & 31) == __ffs(m) - 1) atomicAdd(&cnt[c], __popc(m));
+    __syncthreads();
+    for (int c = threadIdx.x; c < RX_KEYS; c += blockDim.x) table[(int64_t)c * nb + blockIdx.x] = cnt[c];
+}
+__global__ void __launch_bounds__(RX_BLOCK)
+k_rx_place(const int2* in, int64_t n, int shift, const int64_t* off, int64_t nb, int2* out) {
+    __shared__ int32_t wcnt[RX_BLOCK / 32][RX_KEYS];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int q = threadIdx.x; q < (RX_BLOCK / 32) * RX_KEYS; q += blockDim.x) (&wcnt[0][0])[q] = 0;
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * RX_BLOCK + threadIdx.x;
+    const int2 item = i < n ? in[i] : make_int2(0, 0);
+    const int c = i < n ? (item.x >> shift) & (RX_KEYS - 1) : -1;
+    const unsigned m = __match_any_sync(0xffffffffu, c);
+    const int rank = __popc(m & ((1u << lane) - 1u));
+    if (c >= 0 && rank == 0) wcnt[w][c] = __popc(m);
+    __syncthreads();
+    if (c >= 0) {
+        int before = 0;
+        for (int q = 0; q < w; ++q) before += wcnt[q][c];
+        out[off[(int64_t)c * nb + blockIdx.x] + before + rank] = item;
+    }
+}
+// row index of every entry (G lanes per row)
+template <int G>
+__global__ void k_entry_rows(const int64_t* rp, int64_t nr, int32_t* rowof) {
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    if (i >= nr) return;
+    for (int64_t k = rp[i] + (threadIdx.x & (G - 1)); k < rp[i + 1]; k += G) rowof[k] = (int32_t)i;
+}
+__global__ void k_rx_gather(const int2* it, int64_t nnz, const int32_t* rowof, const double* v, int32_t* tci,
+                            double* tv) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nnz) return;
+    const int32_t e = it[k].y;
+    tci[k] = rowof[e];
+    tv[k] = v[e];
+}
+static int transpose_radix(const DCSR& A, DCSR& At, cudaStream_t s) {
+    const int64_t nnz = A.nnz, nb = (nnz + RX_BLOCK - 1) / RX_BLOCK;
+    int bits = 1;
+    while (bits < 31 && (1LL << bits) < A.nc) ++bits;
+    const int passes = (bits + RX_BITS - 1) / RX_BITS;
+    DBuf<int2> it0, it1;
+    DBuf<int32_t> table, rowof;
+    DBuf<int64_t> off;
+    SPHC_TRY(it0.alloc(nnz, s));
+    SPHC_TRY(it1.alloc(nnz, s));
+    SPHC_TRY(table.alloc((int64_t)RX_KEYS * nb, s));
+    SPHC_TRY(off.alloc((int64_t)RX_KEYS * nb + 1, s));
+    SPHC_LAUNCH(k_rx_init<<<grid_for(nnz, 256), 256, 0, s>>>(A.ci.p, nnz, it0.p));
+    int2* in = it0.p;
+    int2* out = it1.p;
+    for (int ps = 0; ps < passes; ++ps) {
+        const int shift = ps * RX_BITS;
+        SPHC_LAUNCH(k_rx_count<<<(unsigned)nb, RX_BLOCK, 0, s>>>(in, nnz, shift, table.p, nb));
+        SPHC_TRY(scan_i32_to_i64(table.p, off.p, (int64_t)RX_KEYS * nb, s, nullptr));
+        SPHC_LAUNCH(k_rx_place<<<(unsigned)nb, RX_BLOCK, 0, s>>>(in, nnz, shift, off.p, nb, out));
+        std::swap(in, out);
+    }
+    SPHC_TRY(rowof.alloc(nnz, s));
+    const double avg = (double)nnz / (double)(A.nr > 0 ? A.nr : 1);
+    if (A.nr > 0) {
+        if (avg <= 6) SPHC_LAUNCH(k_entry_rows<4><<<grid_for(A.nr * 4, 256), 256, 0, s>>>(A.rp.p, A.nr, rowof.p));
+        else if (avg <= 12) SPHC_LAUNCH(k_entry_rows<8><<<grid_for(A.nr * 8, 256), 256, 0, s>>>(A.rp.p, A.nr, rowof.p));
+        else SPHC_LAUNCH(k_entry_rows<32><<<grid_for(A.nr * 32, 256), 256, 0, s>>>(A.rp.p, A.nr, rowof.p));
+    }
+    SPHC_LAUNCH(k_rx_gather<<<grid_for(nnz, 256), 256, 0, s>>>(in, nnz, rowof.p, A.v.p, At.ci.p, At.v.p));
+    SPHC_CK(cudaGetLastError());
+    return SPHC_OK;
+}
+
 int transpose(const DCSR& A, DCSR& At, cudaStream_t s) {
     DBuf<int32_t> cnt;
     SPHC_TRY(cnt.alloc(A.nc + 1, s));
@@ -298,14 +403,18 @@ int transpose(const DCSR& A, DCSR& At, cudaStream_t s) {
     SPHC_TRY(At.alloc(A.nc, A.nr, A.nnz, s));
     int64_t tot = 0;
     SPHC_TRY(scan_i32_to_i64(cnt.p, At.rp.p, A.nc, s, &tot));
+    int64_t mx = 0;
+    SPHC_TRY(max_row_length(At.rp.p, At.nr, s, &mx));
+    // long rows of A^T (whose segmented sort takes a block per row) by the radix sort
+    if (A.nnz > 0 && A.nnz < (1LL << 31) &&
+        ((spgemm_path_flags() & 32) || (mx > 32 && A.nnz >= TRANSPOSE_RADIX_MIN_NNZ)))
+        return transpose_radix(A, At, s);
     DBuf<unsigned long long> cur;
     SPHC_TRY(cur.alloc(A.nc + 1, s));
     SPHC_LAUNCH(k_i64_to_u64<<<grid_for(A.nc + 1, 256), 256, 0, s>>>(At.rp.p, cur.p, A.nc + 1));
     if (A.nr > 0)
         SPHC_LAUNCH(k_transpose_scatter<<<grid_for(A.nr, 256), 256, 0, s>>>(A.rp.p, A.ci.p, A.v.p, A.nr, cur.p, At.ci.p, At.v.p));
     SPHC_CK(cudaGetLastError());
-    int64_t mx = 0;
-    SPHC_TRY(max_row_length(At.rp.p, At.nr, s, &mx));
     SPHC_TRY(segmented_sort(At.rp.p, At.nr, At.ci.p, At.v.p, mx, s));
     return SPHC_OK;
 }
@@ -376,6 +485,14 @@ __global__ void k_dmul(const int64_t* __restrict__ drp, const int32_t* __restric
 // order, the order a sparse accumulator walking A's row uses.  Mode 0 counts the nodes of each
 // row, mode 1 writes them.
 constexpr int AD_WARPS = 8;
+// a * d, by a sign flip when d is +1 or -1 (every entry of a discrete gradient), compared and
+// flipped on the bit patterns so that the FP64 pipe only sees the rare other values
+__device__ __forceinline__ double times_unit(double a, double d) {
+    const unsigned long long db = (unsigned long long)__double_as_longlong(d);
+    if (db == 0x3FF0000000000000ULL) return a;
+    if (db == 0xBFF0000000000000ULL) return __longlong_as_double(__double_as_longlong(a) ^ (long long)(1ULL << 63));
+    return a * d;
+}
 __global__ void __launch_bounds__(AD_WARPS * 32)
 k_amul_d(const int64_t* __restrict__ arp, const int32_t* __restrict__ aci, const double* __restrict__ av, int64_t n,
          const int64_t* __restrict__ drp, const int32_t* __restrict__ dci, const double* __restrict__ dv, int mode,
@@ -395,8 +512,8 @@ k_amul_d(const int64_t* __restrict__ arp, const int32_t* __restrict__ aci, const
         if (dl > 1) k1 = dci[d0 + 1];
         if (mode != 0) {
             const double a = av[a0 + lane];
-            s_val[w][lane] = dl > 0 ? a * dv[d0] : 0.0;
-            s_val[w][32 + lane] = dl > 1 ? a * dv[d0 + 1] : 0.0;
+            s_val[w][lane] = dl > 0 ? times_unit(a, dv[d0]) : 0.0;
+            s_val[w][32 + lane] = dl > 1 ? times_unit(a, dv[d0 + 1]) : 0.0;
         }
     }
     unsigned lo0 = 0, lo1 = 0, hi0 = 0, hi1 = 0;     // ballots of node lane and node lane + 32
@@ -424,13 +541,16 @@ k_amul_d(const int64_t* __restrict__ arp, const int32_t* __restrict__ aci, const
         const int slot = lane + 32 * r;
         if (slot >= c) break;
         const unsigned b0 = r ? hi0 : lo0, b1 = r ? hi1 : lo1;
+        // a lane reaches a node through one of its two D entries (the two nodes of an edge
+        // differ): pick that product, then one FP64 add per further lane, the first term as is
         unsigned any = b0 | b1;
-        double sum = 0.0;
+        int l = __ffs(any) - 1;
+        any &= any - 1;
+        double sum = s_val[w][((b0 >> l) & 1u) ? l : 32 + l];
         while (any) {
-            const int l = __ffs(any) - 1;
+            l = __ffs(any) - 1;
             any &= any - 1;
-            if ((b0 >> l) & 1u) sum += s_val[w][l];
-            if ((b1 >> l) & 1u) sum += s_val[w][32 + l];
+            sum += s_val[w][((b0 >> l) & 1u) ? l : 32 + l];
         }
         cci[out + slot] = r ? node_hi : node_lo;
         cv[out + slot] = sum;
@@ -1165,16 +1285,6 @@ static int numeric_by_length(const DCSR& A, const DCSR& B, DCSR& C, const int32_
     return SPHC_OK;
 }
 
-// Test switches of the path choices below, read from the environment variable SPHC_SPGEMM_PATHS
-// (a bit mask, 0 when unset): 1 the small bin's counting and writing passes instead of its one
-// pass into temporary slots; 2 the numeric pass binned by row length whatever the number of rows;
-// 4 never binned by row length; 8 the hash bins through counting and numeric passes instead of
-// their one pass into an arena (bits 2 and 4 apply then); 16 sub-arenas of 64 entries, so that
-// most one-pass rows take the overflow path.  Every path gives the same matrix.
-static int spgemm_path_flags() {
-    const char* e = getenv("SPHC_SPGEMM_PATHS");
-    return e ? atoi(e) : 0;
-}
 
 static int spgemm_impl(const DCSR& A, const DCSR& B, DCSR& C, int upper, cudaStream_t s) {
     const int paths = spgemm_path_flags();
