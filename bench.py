@@ -703,6 +703,8 @@ def main():
             "profile": {k: {kk: round(vv, 4) if isinstance(vv, float) else vv for kk, vv in v.items()}
                         for k, v in prof.items()},
             "level_edges": [li["n_edges"] for li in info],
+            "level_colours": [[li["n_colors_edge"], li["n_colors_node"], li["colour_rounds_edge"], li["colour_rounds_node"]]
+                              for li in info],
         }
         print(json.dumps(line), flush=True)
     if dist:

@@ -188,8 +188,8 @@ int setup_impl(sphc_handle* h, const sphc_csr* A_e, const sphc_csr* D_h, const d
         uint64_t seed = o.seed + 1000ULL * (uint64_t)lev;
         {
             Section sec(prof, lev == 0 ? "setup_colour_l0" : "setup_colour_ge1", s);
-            SPHC_TRY(color_graph(L.A, seed + 2, L.col_e, &L.ncol_e, s, &L.rounds_e));
-            SPHC_TRY(color_graph(L.An, seed + 3, L.col_n, &L.ncol_n, s, &L.rounds_n));
+            SPHC_TRY(color_graph(L.A, seed + 2, L.col_e, &L.ncol_e, s, &L.rounds_e, prof, lev == 0 ? "e_l0" : "e_ge1"));
+            SPHC_TRY(color_graph(L.An, seed + 3, L.col_n, &L.ncol_n, s, &L.rounds_n, prof, lev == 0 ? "n_l0" : "n_ge1"));
         }
         bool coarsest = L.A.nr <= o.max_coarse || lev + 1 >= o.max_levels || L.An.nr <= 1;
         if (coarsest) break;

@@ -27,6 +27,10 @@ static constexpr int MAX_COLORS = 256;
 // (and no contended counter to append to it) is needed.
 enum { JP_OVERFLOW = 0, JP_ITERS = 1, JP_WAITING = 2 };
 static constexpr int JP_UNROLL = 8;
+// blocks of a round per SM (eight waves of resident blocks): a waiting row's re-check is a chain of
+// dependent loads, so more rows in flight pay for the extra block scheduling (level-0 edge graph
+// at 128^3: 8 blocks/SM 28.1 ms, 32 22.1, 64 20.0, 128 21.2, 256 24.5 ms over its 37 rounds)
+static constexpr int JP_BLOCKS_PER_SM = 64;
 static constexpr int JP_MAX_ITERS = 1 << 17;
 
 __global__ void k_prio(int64_t n, uint64_t seed, uint64_t* prio) {
@@ -118,7 +122,11 @@ __global__ void k_max_i32(const int32_t* a, int64_t n, int* mx) {
     if (i < n) atomicMax(mx, a[i]);
 }
 
-int color_graph(const DCSR& G, uint64_t seed, DBuf<int32_t>& color, int* ncolors, cudaStream_t s, int* rounds) {
+int color_graph(const DCSR& G, uint64_t seed, DBuf<int32_t>& color, int* ncolors, cudaStream_t s, int* rounds,
+                Profiler* prof, const char* tag) {
+    const std::string tg = tag ? tag : "";
+    Profiler* pr = tag ? prof : nullptr;
+    std::unique_ptr<Section> sec_build(new Section(pr, ("colour_build_" + tg).c_str(), s));
     int64_t n = G.nr;
     SPHC_TRY(color.alloc(n, s));
     if (n == 0) { *ncolors = 0; return SPHC_OK; }
@@ -157,9 +165,10 @@ int color_graph(const DCSR& G, uint64_t seed, DBuf<int32_t>& color, int* ncolors
         if ((e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np)) != cudaSuccess) fail(e, "while node");
     }
     if (rc == SPHC_OK && (e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) fail(e, "stream");
-    // rounds loop over the rows with a grid of one full wave: most rows are coloured after the
-    // first rounds, and a grid over all rows would pay block scheduling for them every round
-    // (an appended list of waiting rows measured slower: its counter is contended)
+    // rounds loop over the rows with a grid capped at JP_BLOCKS_PER_SM blocks per SM: a round
+    // colours only about 6 % of the rows of a mesh graph (37 rounds at level 0 of the 128^3
+    // problem), and every waiting row re-checks its blocking neighbour each round (an appended
+    // list of waiting rows measured slower: its counter is contended)
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -178,7 +187,7 @@ int color_graph(const DCSR& G, uint64_t seed, DBuf<int32_t>& color, int* ncolors
                 while (lanes < 32 && lanes < avg) lanes *= 2;
             }
             for (int q = 0; q < JP_UNROLL; ++q) {
-                unsigned blocks = (unsigned)std::min<int64_t>(grid_for(n * lanes, 256), (int64_t)nsm * 8);
+                unsigned blocks = (unsigned)std::min<int64_t>(grid_for(n * lanes, 256), (int64_t)nsm * JP_BLOCKS_PER_SM);
                 switch (lanes) {
                     case 1: k_jp_round<1><<<blocks, 256, 0, cs>>>(G.rp.p, G.ci.p, prio.p, n, ctrl.p, q, pos.p, color.p); break;
                     case 4: k_jp_round<4><<<blocks, 256, 0, cs>>>(G.rp.p, G.ci.p, prio.p, n, ctrl.p, q, pos.p, color.p); break;
@@ -193,6 +202,8 @@ int color_graph(const DCSR& G, uint64_t seed, DBuf<int32_t>& color, int* ncolors
         }
     }
     if (rc == SPHC_OK && (e = cudaGraphInstantiate(&ge, g, 0)) != cudaSuccess) fail(e, "instantiate");
+    sec_build.reset();
+    Section sec_rounds(pr, ("colour_rounds_" + tg).c_str(), s);
     if (rc == SPHC_OK && (e = cudaGraphLaunch(ge, s)) != cudaSuccess) fail(e, "launch");
     if (ge) cudaGraphExecDestroy(ge);
     if (g) cudaGraphDestroy(g);

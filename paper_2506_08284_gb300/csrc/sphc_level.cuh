@@ -129,7 +129,11 @@ struct Level {
 };
 
 // setup.cu
-int color_graph(const DCSR& G, uint64_t seed, DBuf<int32_t>& color, int* ncolors, cudaStream_t s, int* rounds = nullptr);
+struct Profiler;
+// prof (optional): sub-timers "colour_build_<tag>" (graph of the rounds built and instantiated) and
+// "colour_rounds_<tag>" (the rounds and the colour count)
+int color_graph(const DCSR& G, uint64_t seed, DBuf<int32_t>& color, int* ncolors, cudaStream_t s, int* rounds = nullptr,
+                Profiler* prof = nullptr, const char* tag = nullptr);
 int aggregate(const DCSR& G, uint64_t seed, DBuf<int32_t>& agg, int64_t* nagg, cudaStream_t s);
 int power_rho(const DCSR& A, const double* diag, uint64_t seed, int iters, double* rho, cudaStream_t s);
 int coarse_gradient(const DCSR& D, const DCSR& Dt, const int32_t* agg, int64_t nagg, DCSR& DH, cudaStream_t s);
