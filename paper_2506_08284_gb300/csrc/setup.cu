@@ -1261,9 +1261,13 @@ __device__ __forceinline__ int row_factor(int64_t i, const int64_t* __restrict__
                 g = a == b ? 1.0 : 0.0;
             S.L[a][b] = g;
         }
+    // Columns and rows from k on are the identity padding of the unrolled loops (their entries of
+    // L stay 1 on the diagonal and 0 elsewhere): they are skipped, which leaves every entry of the
+    // k x k factor as it is and saves the FP64 work of the padding (k is mostly 4..6 of TK = 8).
     bool ok = true;
 #pragma unroll
     for (int j = 0; j < TK; ++j) {
+        if (j >= k) continue;
         double d = S.L[j][j];
 #pragma unroll
         for (int c = 0; c < j; ++c) d -= S.L[j][c] * S.L[j][c];
@@ -1272,6 +1276,7 @@ __device__ __forceinline__ int row_factor(int64_t i, const int64_t* __restrict__
         S.L[j][j] = inv;
 #pragma unroll
         for (int r = j + 1; r < TK; ++r) {
+            if (r >= k) continue;
             double v = S.L[r][j];
 #pragma unroll
             for (int c = 0; c < j; ++c) v -= S.L[r][c] * S.L[j][c];
@@ -1281,9 +1286,12 @@ __device__ __forceinline__ int row_factor(int64_t i, const int64_t* __restrict__
     return ok ? 1 : 0;
 }
 // x := (L L^T)^-1 x (L's diagonal holds 1 / L_aa)
+// (only the k x k system: the padding rows of x are 0 and stay 0)
 __device__ __forceinline__ void row_solve(const RowSys& S, double x[TK]) {
+    const int k = S.k;
 #pragma unroll
     for (int a = 0; a < TK; ++a) {
+        if (a >= k) continue;
         double v = x[a];
 #pragma unroll
         for (int c = 0; c < a; ++c) v -= S.L[a][c] * x[c];
@@ -1291,9 +1299,11 @@ __device__ __forceinline__ void row_solve(const RowSys& S, double x[TK]) {
     }
 #pragma unroll
     for (int a = TK - 1; a >= 0; --a) {
+        if (a >= k) continue;
         double v = x[a];
 #pragma unroll
-        for (int r = a + 1; r < TK; ++r) v -= S.L[r][a] * x[r];
+        for (int r = a + 1; r < TK; ++r)
+            if (r < k) v -= S.L[r][a] * x[r];
         x[a] = v * S.L[a][a];
     }
 }

@@ -940,32 +940,6 @@ __global__ void k_spgemm_symbolic_big(const int64_t* arp, const int32_t* aci, co
     }
 }
 
-// Sort keys[0, count) ascending, vals alongside, by one warp in shared memory: a bitonic network
-// over the next power of two (at most the table size, which is at least twice count), padded
-// with INT_MAX keys.
-__device__ inline void warp_sort_pairs(int32_t* keys, double* vals, int count, int lane) {
-    int n2 = 1;
-    while (n2 < count) n2 <<= 1;
-    for (int t = count + lane; t < n2; t += 32) keys[t] = 0x7fffffff;
-    __syncwarp();
-    for (int size = 2; size <= n2; size <<= 1)
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int q = lane; q < n2 / 2; q += 32) {
-                const int lo = q + (q & ~(stride - 1)), hi = lo + stride;   // stride is a power of two
-                const bool up = (lo & size) == 0;
-                const int32_t a = keys[lo], b = keys[hi];
-                if ((a > b) == up) {
-                    keys[lo] = b;
-                    keys[hi] = a;
-                    const double t = vals[lo];
-                    vals[lo] = vals[hi];
-                    vals[hi] = t;
-                }
-            }
-            __syncwarp();
-        }
-}
-
 // Accumulate row i's products into a warp's table (keys, vals; tsize slots, all empty).  Products
 // go round by round, 32 at a time in product order (A's row, then each B row).  A lane finds (or
 // claims) its column's slot; the lanes of one slot are matched, and the lowest of them adds their
@@ -1026,9 +1000,8 @@ __device__ inline int accumulate_row(int64_t i, int32_t floor, const int64_t* ar
     }
     return count;
 }
-// Move the table's keys to its front (order kept), then sort them with their values; returns
-// the count.
-__device__ inline int compact_sort(int32_t* keys, double* vals, int tsize, int lane) {
+// Move the table's keys to its front (order kept); returns the count.
+__device__ inline int compact_keys(int32_t* keys, double* vals, int tsize, int lane) {
     int count = 0;
     for (int t0 = 0; t0 < tsize; t0 += 32) {
         const int32_t k = keys[t0 + lane];
@@ -1040,11 +1013,22 @@ __device__ inline int compact_sort(int32_t* keys, double* vals, int tsize, int l
         count += __popc(m);
         __syncwarp();
     }
-    warp_sort_pairs(keys, vals, count, lane);
     return count;
 }
-
-// numeric: accumulate in the table, compact in place, sort, write the row
+// Write the count distinct keys (compacted, unsorted) and their values in ascending key order:
+// a key's place is the number of smaller keys (broadcast reads of the list), cheaper than a
+// sorting network for the few dozen to few hundred columns of a product row.
+__device__ inline void write_ranked(const int32_t* keys, const double* vals, int count, int lane, int32_t* oc,
+                                    double* ov) {
+    for (int e = lane; e < count; e += 32) {
+        const int32_t k = keys[e];
+        int rank = 0;
+        for (int j = 0; j < count; ++j) rank += keys[j] < k ? 1 : 0;
+        oc[rank] = k;
+        ov[rank] = vals[e];
+    }
+}
+// numeric: accumulate in the table, compact in place, write the row in column order
 template <int SLOTS, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32)
 k_spgemm_numeric(const int64_t* arp, const int32_t* aci, const double* av, const int64_t* brp,
@@ -1070,15 +1054,13 @@ k_spgemm_numeric(const int64_t* arp, const int32_t* aci, const double* av, const
     for (int t = lane; t < tsize; t += 32) { keys[t] = -1; vals[t] = 0.0; }
     __syncwarp();
     accumulate_row(i, floor, arp, aci, av, brp, bci, bv, keys, vals, tsize, tsize, s_win[w], s_fa[w], s_fb[w], lane);
-    const int count = compact_sort(keys, vals, tsize, lane);
-    for (int e = lane; e < count; e += 32) {
-        cci[c0 + e] = keys[e];
-        cv[c0 + e] = vals[e];
-    }
+    const int count = compact_keys(keys, vals, tsize, lane);
+    __syncwarp();
+    write_ranked(keys, vals, count, lane, cci + c0, cv + c0);
 }
 
 // One pass for rows whose product count exceeds the register-sort bin: accumulate in a table of TS
-// slots; a row of at most TS / 2 columns is sorted and written to a temporary arena (sub-arena
+// slots; a row of at most TS / 2 columns is written in column order to a temporary arena (sub-arena
 // blockIdx % SPG_SUBS, reserved by that sub-arena's bump counter; its offset goes to moff[li], its
 // length to cnt[i]).  A row with more columns, or one its sub-arena has no room for, gets
 // moff[li] = -1 and joins the overflow list for the counting and numeric passes.
@@ -1104,7 +1086,8 @@ k_spgemm_onepass(const int64_t* arp, const int32_t* aci, const double* av, const
                                s_fa[w], s_fb[w], lane);
     int64_t dst = -1;
     if (count >= 0) {
-        count = compact_sort(keys, vals, TS, lane);
+        count = compact_keys(keys, vals, TS, lane);
+        __syncwarp();
         const int sub = blockIdx.x % SPG_SUBS;
         unsigned long long at = 0;
         if (lane == 0) at = atomicAdd(&cursors[sub], (unsigned long long)count);
@@ -1118,10 +1101,7 @@ k_spgemm_onepass(const int64_t* arp, const int32_t* aci, const double* av, const
         }
         return;
     }
-    for (int e = lane; e < count; e += 32) {
-        tci[dst + e] = keys[e];
-        tv[dst + e] = vals[e];
-    }
+    write_ranked(keys, vals, count, lane, tci + dst, tv + dst);
     if (lane == 0) {
         moff[li] = dst;
         cnt[i] = count;
