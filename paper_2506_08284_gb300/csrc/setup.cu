@@ -229,40 +229,57 @@ int color_graph(const DCSR& G, uint64_t seed, DBuf<int32_t>& color, int* ncolors
 
 // ------------------------------------------------------------------ aggregation
 // state: 0 undecided, 1 root, 2 decided, 3 root chosen in the current round
+// G lanes per node split its neighbours w; each lane walks w and w's neighbours.  After every
+// stripe of G neighbours the group's ballot ends the walk once any lane met a blocking node, so the
+// group's trip count stays uniform.
+template <int G>
 __global__ void k_mis2_select(const int64_t* rp, const int32_t* ci, int64_t n, uint64_t seed, int8_t* state) {
-    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= n) return;
+    const int lane = threadIdx.x & 31, sub = lane & (G - 1);
+    const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+    const int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    if (v >= n) return;                              // uniform over the group
     volatile int8_t* st = state;
     if (st[v] != 0) return;
-    uint64_t hv = splitmix64(seed, (uint64_t)v);
-    for (int64_t k = rp[v]; k < rp[v + 1]; ++k) {
-        int32_t w = ci[k];
-        if (w == v) continue;
-        for (int q = 0; q < 2; ++q) {
-            // q = 0: w itself, q = 1: w's neighbours
-            int64_t b = q == 0 ? 0 : rp[w], e = q == 0 ? 1 : rp[w + 1];
-            for (int64_t k2 = b; k2 < e; ++k2) {
-                int32_t u = q == 0 ? w : ci[k2];
-                if (u == v) continue;
-                int8_t su = st[u];
-                if (su == 1 || su == 3) return;
-                if (su == 0 && prio_greater(splitmix64(seed, (uint64_t)u), u, hv, v)) return;
+    const uint64_t hv = splitmix64(seed, (uint64_t)v);
+    const int64_t b0 = rp[v], e0 = rp[v + 1];
+    for (int64_t k0 = b0; k0 < e0; k0 += G) {
+        bool blocked = false;
+        const int64_t k = k0 + sub;
+        if (k < e0) {
+            const int32_t w = ci[k];
+            if (w != v) {
+                for (int q = 0; q < 2 && !blocked; ++q) {
+                    // q = 0: w itself, q = 1: w's neighbours
+                    const int64_t b = q == 0 ? 0 : rp[w], e = q == 0 ? 1 : rp[w + 1];
+                    for (int64_t k2 = b; k2 < e; ++k2) {
+                        const int32_t u = q == 0 ? w : ci[k2];
+                        if (u == v) continue;
+                        const int8_t su = st[u];
+                        if (su == 1 || su == 3 ||
+                            (su == 0 && prio_greater(splitmix64(seed, (uint64_t)u), u, hv, v))) {
+                            blocked = true;
+                            break;
+                        }
+                    }
+                }
             }
         }
+        if (__any_sync(gmask, blocked)) return;
     }
-    state[v] = 3;
+    if (sub == 0) state[v] = 3;
 }
 
+template <int G>
 __global__ void k_mis2_mark(const int64_t* rp, const int32_t* ci, int64_t n, int8_t* state) {
-    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int sub = threadIdx.x & (G - 1);
+    const int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
     if (v >= n) return;
-    int8_t sv = state[v];
-    if (sv != 3) return;
-    for (int64_t k = rp[v]; k < rp[v + 1]; ++k) {
-        int32_t w = ci[k];
+    if (state[v] != 3) return;
+    for (int64_t k = rp[v] + sub; k < rp[v + 1]; k += G) {
+        const int32_t w = ci[k];
         if (w != v && state[w] == 0) state[w] = 2;
         for (int64_t k2 = rp[w]; k2 < rp[w + 1]; ++k2) {
-            int32_t u = ci[k2];
+            const int32_t u = ci[k2];
             if (u != v && state[u] == 0) state[u] = 2;
         }
     }
@@ -335,9 +352,26 @@ int aggregate(const DCSR& G, uint64_t seed, DBuf<int32_t>& agg, int64_t* nagg, c
     DBuf<int> flags;
     SPHC_TRY(flags.alloc(2, s));
     int h[2];
+    // lanes per node: the mean degree rounded up to a power of two (at most 32) on graphs of up to
+    // 2^20 nodes, whose distance-2 walks are long and few; 4 on larger graphs
+    const double deg = (double)G.nnz / (double)n;
+    int lanes = 4;
+    if (n <= (1 << 20)) {
+        lanes = 1;
+        while (lanes < 32 && lanes < deg) lanes *= 2;
+    }
     for (int round = 0; round < 100000; ++round) {
-        SPHC_LAUNCH(k_mis2_select<<<grid_for(n, 256), 256, 0, s>>>(G.rp.p, G.ci.p, n, seed, state.p));
-        SPHC_LAUNCH(k_mis2_mark<<<grid_for(n, 256), 256, 0, s>>>(G.rp.p, G.ci.p, n, state.p));
+        switch (lanes) {
+#define MIS(L) SPHC_LAUNCH(k_mis2_select<L><<<grid_for(n * L, 256), 256, 0, s>>>(G.rp.p, G.ci.p, n, seed, state.p)); \
+               SPHC_LAUNCH(k_mis2_mark<L><<<grid_for(n * L, 256), 256, 0, s>>>(G.rp.p, G.ci.p, n, state.p)); break;
+            case 1: MIS(1)
+            case 2: MIS(2)
+            case 4: MIS(4)
+            case 8: MIS(8)
+            case 16: MIS(16)
+            default: MIS(32)
+#undef MIS
+        }
         SPHC_CK(cudaMemsetAsync(flags.p, 0, sizeof(int), s));
         SPHC_LAUNCH(k_mis2_commit<<<grid_for(n, 256), 256, 0, s>>>(state.p, n, flags.p));
         SPHC_CK(cudaMemcpyAsync(h, flags.p, sizeof(int), cudaMemcpyDeviceToHost, s));
