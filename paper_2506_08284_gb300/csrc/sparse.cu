@@ -296,7 +296,8 @@ __global__ void k_i64_to_u64(const int64_t* a, unsigned long long* b, int64_t n)
 // row length whatever the number of rows; 4 never binned by row length; 8 the hash bins through
 // counting and numeric passes instead of their one pass into an arena (bits 2 and 4 apply then);
 // 16 sub-arenas of 64 entries, so that most one-pass rows take the overflow path; 32 every
-// transpose by the radix sort.  Every path gives the same matrix.
+// transpose by the radix sort; 64 the 256-slot one-pass tables for every upper-triangle product.
+// Every path gives the same matrix.
 static int spgemm_path_flags() {
     const char* e = getenv("SPHC_SPGEMM_PATHS");
     return e ? atoi(e) : 0;
@@ -1107,16 +1108,17 @@ k_spgemm_onepass(const int64_t* arp, const int32_t* aci, const double* av, const
         cnt[i] = count;
     }
 }
-// copy the one-pass rows (moff >= 0) from the arena into C (warp per row)
+// copy the one-pass rows (moff >= 0) from the arena into C (G lanes per row)
+template <int G>
 __global__ void k_copy_arena(const int32_t* rows, int nrows, const int64_t* moff, const int32_t* tci, const double* tv,
                              const int64_t* crp, int32_t* cci, double* cv) {
-    const int64_t li = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
+    const int64_t li = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    const int lane = threadIdx.x & (G - 1);
     if (li >= nrows) return;
     const int64_t t0 = moff[li];
     if (t0 < 0) return;
     const int64_t i = rows[li], c0 = crp[i], len = crp[i + 1] - c0;
-    for (int64_t e = lane; e < len; e += 32) {
+    for (int64_t e = lane; e < len; e += G) {
         cci[c0 + e] = tci[t0 + e];
         cv[c0 + e] = tv[t0 + e];
     }
@@ -1348,8 +1350,13 @@ static int spgemm_impl(const DCSR& A, const DCSR& B, DCSR& C, int upper, cudaStr
             DBuf<unsigned long long> bsum;
             SPHC_TRY(bsum.alloc(1, s));
             SPHC_TRY(bsum.zero(s));
-            SPHC_LAUNCH(k_sum_capped<<<grid_for(nmed, 256), 256, 0, s>>>(rows.p + off[1], nmed, ub.p, 64, 256, 256,
-                                                                          bsum.p));
+            // Upper triangles keep about half of a row's columns: on products with many long rows
+            // (the Galerkin product of the finest level) tables of 256 slots (at most 128 columns)
+            // let twice the warps hide the latency of the gathered B rows; a mid level's few long
+            // rows overflow them more often than that gains.
+            const bool small_tables = upper && ((paths & 64) || h[5] >= NUM_REBIN_MIN_ROWS);
+            SPHC_LAUNCH(k_sum_capped<<<grid_for(nmed, 256), 256, 0, s>>>(rows.p + off[1], nmed, ub.p, 64,
+                                                                          small_tables ? 128 : 256, 256, bsum.p));
             unsigned long long hb = 0;
             SPHC_CK(cudaMemcpyAsync(&hb, bsum.p, sizeof(hb), cudaMemcpyDeviceToHost, s));
             SPHC_CK(cudaStreamSynchronize(s));
@@ -1374,6 +1381,10 @@ static int spgemm_impl(const DCSR& A, const DCSR& B, DCSR& C, int upper, cudaStr
                         const int32_t* rl = rows.p + off[1] + first;
                         if (b < 2)
                             SPHC_LAUNCH((k_spgemm_onepass<128, 16><<<(nr + 15) / 16, 512, 0, s>>>(
+                                A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p, B.v.p, rl, nr, upper, cnt.p, moff.p + first,
+                                mci.p, mv.p, curs.p, sub_cap, ovf.p, flags.p + 14)));
+                        else if (small_tables)  // see below
+                            SPHC_LAUNCH((k_spgemm_onepass<256, 8><<<(nr + 7) / 8, 256, 0, s>>>(
                                 A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p, B.v.p, rl, nr, upper, cnt.p, moff.p + first,
                                 mci.p, mv.p, curs.p, sub_cap, ovf.p, flags.p + 14)));
                         else
@@ -1434,9 +1445,16 @@ static int spgemm_impl(const DCSR& A, const DCSR& B, DCSR& C, int upper, cudaStr
         // per product-count bin than split over length bins that each wait for their longest row.
         const int nmed = h[3] + h[4] + h[5];
         if (med_one_pass) {
-            if (nmed > 0)
-                SPHC_LAUNCH(k_copy_arena<<<grid_for((int64_t)nmed * 32, 256), 256, 0, s>>>(
-                    rows.p + off[1], nmed, moff.p, mci.p, mv.p, C.rp.p, C.ci.p, C.v.p));
+            if (nmed > 0) {
+                // lanes per row from the mean output row
+                const double avg = (double)nnz / (double)(n > 0 ? n : 1);
+#define CA(G) SPHC_LAUNCH((k_copy_arena<G><<<grid_for((int64_t)nmed * G, 256), 256, 0, s>>>( \
+                    rows.p + off[1], nmed, moff.p, mci.p, mv.p, C.rp.p, C.ci.p, C.v.p)))
+                if (avg <= 12) CA(8);
+                else if (avg <= 24) CA(16);
+                else CA(32);
+#undef CA
+            }
             if (novf > 0) SPHC_TRY(numeric_by_length(A, B, C, ovf.p, novf, upper, s));
         } else if ((paths & 2) || (!(paths & 4) && nmed >= NUM_REBIN_MIN_ROWS)) {
             SPHC_TRY(numeric_by_length(A, B, C, rows.p + off[1], nmed, upper, s));

@@ -4,7 +4,8 @@ passes instead of its one pass into temporary slots; 2 the numeric pass binned b
 length for any number of rows; 4 never binned by length; 8 the hash bins through counting and
 numeric passes instead of their one pass into an arena; 16 sub-arenas so small that most one-pass
 rows overflow into the counting path; 32 every transpose by the stable radix sort (by default only
-large transposes with long rows take it).  The default choices depend on the free device memory and
+large transposes with long rows take it); 64 the smaller one-pass tables of the upper-triangle
+products (by default only on products of many rows).  The default choices depend on the free device memory and
 on the number of rows, so the small test meshes would otherwise exercise one branch only (the
 coarse levels' long rows also overflow the one-pass tables by themselves).  Each forced path against the CPU oracle: integer patterns bit for bit,
 FP64 values (A_l, A_n, P_n, P_e on every level) to 1e-10 of the largest entry."""
@@ -25,7 +26,7 @@ def case():
     return p, oracle_setup(p, **OPTS)
 
 
-@pytest.mark.parametrize("paths", ["0", "1", "16", "17", "8", "10", "12", "11", "13", "32", "49"])
+@pytest.mark.parametrize("paths", ["0", "1", "16", "17", "8", "10", "12", "11", "13", "32", "49", "64", "80"])
 def test_spgemm_paths_match_oracle(case, paths, monkeypatch):
     p, o = case
     monkeypatch.setenv("SPHC_SPGEMM_PATHS", paths)
