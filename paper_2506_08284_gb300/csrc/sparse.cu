@@ -313,6 +313,7 @@ static int spgemm_path_flags() {
 // gathered.
 static constexpr int RX_BLOCK = 1024, RX_BITS = 8, RX_KEYS = 1 << RX_BITS;
 static constexpr int64_t TRANSPOSE_RADIX_MIN_NNZ = 1 << 20;     // smaller: scatter + segmented sort
+static constexpr double TRANSPOSE_RADIX_MIN_MEAN = 24.0;         // mean row length of A^T
 __global__ void k_rx_init(const int32_t* ci, int64_t nnz, int2* it) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e < nnz) it[e] = make_int2(ci[e], (int32_t)e);
@@ -354,6 +355,17 @@ __global__ void k_entry_rows(const int64_t* rp, int64_t nr, int32_t* rowof) {
     if (i >= nr) return;
     for (int64_t k = rp[i] + (threadIdx.x & (G - 1)); k < rp[i + 1]; k += G) rowof[k] = (int32_t)i;
 }
+// row pointers of A^T from the sorted keys: row c starts at the first key >= c
+__global__ void k_rx_rowptr(const int2* it, int64_t nnz, int64_t nc, int64_t* trp) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c > nc) return;
+    int64_t lo = 0, hi = nnz;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (it[mid].x < c) lo = mid + 1; else hi = mid;
+    }
+    trp[c] = lo;
+}
 __global__ void k_rx_gather(const int2* it, int64_t nnz, const int32_t* rowof, const double* v, int32_t* tci,
                             double* tv) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -392,11 +404,20 @@ static int transpose_radix(const DCSR& A, DCSR& At, cudaStream_t s) {
         else SPHC_LAUNCH(k_entry_rows<32><<<grid_for(A.nr * 32, 256), 256, 0, s>>>(A.rp.p, A.nr, rowof.p));
     }
     SPHC_LAUNCH(k_rx_gather<<<grid_for(nnz, 256), 256, 0, s>>>(in, nnz, rowof.p, A.v.p, At.ci.p, At.v.p));
+    SPHC_LAUNCH(k_rx_rowptr<<<grid_for(A.nc + 1, 256), 256, 0, s>>>(in, nnz, A.nc, At.rp.p));
     SPHC_CK(cudaGetLastError());
     return SPHC_OK;
 }
 
 int transpose(const DCSR& A, DCSR& At, cudaStream_t s) {
+    // long rows of A^T (whose segmented sort takes a block per row) by the radix sort, which also
+    // gives A^T's row pointers: chosen by the mean row length of A^T
+    if (A.nnz > 0 && A.nnz < (1LL << 31) &&
+        ((spgemm_path_flags() & 32) ||
+         (A.nnz >= TRANSPOSE_RADIX_MIN_NNZ && (double)A.nnz > TRANSPOSE_RADIX_MIN_MEAN * (double)A.nc))) {
+        SPHC_TRY(At.alloc(A.nc, A.nr, A.nnz, s));
+        return transpose_radix(A, At, s);
+    }
     DBuf<int32_t> cnt;
     SPHC_TRY(cnt.alloc(A.nc + 1, s));
     SPHC_TRY(cnt.zero(s));
@@ -406,10 +427,6 @@ int transpose(const DCSR& A, DCSR& At, cudaStream_t s) {
     SPHC_TRY(scan_i32_to_i64(cnt.p, At.rp.p, A.nc, s, &tot));
     int64_t mx = 0;
     SPHC_TRY(max_row_length(At.rp.p, At.nr, s, &mx));
-    // long rows of A^T (whose segmented sort takes a block per row) by the radix sort
-    if (A.nnz > 0 && A.nnz < (1LL << 31) &&
-        ((spgemm_path_flags() & 32) || (mx > 32 && A.nnz >= TRANSPOSE_RADIX_MIN_NNZ)))
-        return transpose_radix(A, At, s);
     DBuf<unsigned long long> cur;
     SPHC_TRY(cur.alloc(A.nc + 1, s));
     SPHC_LAUNCH(k_i64_to_u64<<<grid_for(A.nc + 1, 256), 256, 0, s>>>(At.rp.p, cur.p, A.nc + 1));
