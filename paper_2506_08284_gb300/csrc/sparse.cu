@@ -699,9 +699,9 @@ __global__ void k_spgemm_bin(const int64_t* arp, const int64_t* ub, int64_t n, c
 }
 
 // Rows with at most 64 products (and 64 A entries): one warp per row, the products held two per
-// lane and sorted by column with a bitonic network over the warp; equal columns are then
-// adjacent.  mode 0 counts distinct columns, mode 1 sums each run and writes the sorted row at
-// its place in C, mode 2 writes it (and its count) to a temporary slot of the listed row.
+// lane; the distinct columns are taken in ascending order by warp min-reductions.  mode 0 counts
+// distinct columns, mode 1 writes the row at its place in C, mode 2 writes it (and its count) to
+// a temporary slot of the listed row.
 static constexpr int SMALL_WARPS = 8;
 __global__ void __launch_bounds__(SMALL_WARPS * 32)
 k_spgemm_small(const int64_t* arp, const int32_t* aci, const double* av, const int64_t* brp, const int32_t* bci,
@@ -709,7 +709,6 @@ k_spgemm_small(const int64_t* arp, const int32_t* aci, const double* av, const i
                int32_t* cci, double* cv) {
     __shared__ int64_t s_off[SMALL_WARPS][64];
     __shared__ int64_t s_bst[SMALL_WARPS][64];
-    __shared__ int32_t s_key[SMALL_WARPS][64];
     __shared__ double s_val[SMALL_WARPS][64];
     int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int64_t li = (int64_t)blockIdx.x * SMALL_WARPS + w;
@@ -754,43 +753,31 @@ k_spgemm_small(const int64_t* arp, const int32_t* aci, const double* av, const i
             if (mode != 0) val[q] = av[a0 + lo] * bv[kb];
         }
     }
-    // bitonic sort of the 64 elements
-    for (int size = 2; size <= 64; size <<= 1) {
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            if (stride == 1) {
-                bool up = (((2 * lane) & size) == 0);
-                if ((key[0] > key[1]) == up) {
-                    int32_t tk = key[0]; key[0] = key[1]; key[1] = tk;
-                    double tv = val[0]; val[0] = val[1]; val[1] = tv;
-                }
-            } else {
-                int ls = stride >> 1;
-                for (int q = 0; q < 2; ++q) {
-                    int e = 2 * lane + q;
-                    int32_t ok = __shfl_xor_sync(0xffffffffu, key[q], ls);
-                    double ov = mode != 0 ? __shfl_xor_sync(0xffffffffu, val[q], ls) : 0.0;
-                    bool up = ((e & size) == 0);
-                    bool lower = (e & stride) == 0;
-                    bool take_min = (up == lower);
-                    bool swap = take_min ? (ok < key[q]) : (ok > key[q]);
-                    if (swap) { key[q] = ok; val[q] = ov; }
-                }
-            }
+    // The distinct columns come out in ascending order from warp min-reductions over the lanes'
+    // two keys (one round per column, which then leaves the candidates); two ballots per round
+    // record the lanes that hold it, kept by lane c % 32 for the c-th column.  Each owner lane then
+    // adds its column's products in product order (element 2 lane + q), the order a sparse
+    // accumulator walking A's row and B's rows uses.
+    if (mode != 0) {
+        s_val[w][2 * lane] = val[0];
+        s_val[w][2 * lane + 1] = val[1];
+    }
+    int32_t k0 = key[0], k1 = key[1];
+    unsigned lo0 = 0, lo1 = 0, hi0 = 0, hi1 = 0;
+    int32_t col_lo = 0, col_hi = 0;
+    int distinct = 0;
+    for (;;) {
+        const int32_t m = __reduce_min_sync(0xffffffffu, k0 < k1 ? k0 : k1);
+        if (m == 0x7fffffff) break;
+        const unsigned b0 = __ballot_sync(0xffffffffu, k0 == m), b1 = __ballot_sync(0xffffffffu, k1 == m);
+        if (lane == (distinct & 31)) {
+            if (distinct < 32) { lo0 = b0; lo1 = b1; col_lo = m; }
+            else { hi0 = b0; hi1 = b1; col_hi = m; }
         }
+        if (k0 == m) k0 = 0x7fffffff;
+        if (k1 == m) k1 = 0x7fffffff;
+        ++distinct;
     }
-    s_key[w][2 * lane] = key[0];
-    s_key[w][2 * lane + 1] = key[1];
-    if (mode != 0) { s_val[w][2 * lane] = val[0]; s_val[w][2 * lane + 1] = val[1]; }
-    __syncwarp();
-    // run heads: first element of each distinct column
-    bool head[2];
-    for (int q = 0; q < 2; ++q) {
-        int e = 2 * lane + q;
-        head[q] = s_key[w][e] != 0x7fffffff && (e == 0 || s_key[w][e - 1] != s_key[w][e]);
-    }
-    unsigned m0 = __ballot_sync(0xffffffffu, head[0]);
-    unsigned m1 = __ballot_sync(0xffffffffu, head[1]);
-    int distinct = __popc(m0) + __popc(m1);
     if (mode == 0) {
         if (lane == 0) cnt[i] = distinct;
         return;
@@ -798,18 +785,22 @@ k_spgemm_small(const int64_t* arp, const int32_t* aci, const double* av, const i
     // mode 1: the row at crp[i]; mode 2: at crp[li] (a temporary slot of the listed row), and the
     // count too (the one pass of the small bin, copied into place once the row pointers exist)
     if (mode == 2 && lane == 0) cnt[i] = distinct;
-    int64_t c0 = mode == 2 ? crp[li] : crp[i];
-    unsigned lt = (1u << lane) - 1u;
-    for (int q = 0; q < 2; ++q) {
-        if (!head[q]) continue;
-        int e = 2 * lane + q;
-        // heads before e: elements 2*l + 0/1 for l < lane, plus element 2*lane if q == 1
-        int rank = __popc(m0 & lt) + __popc(m1 & lt) + (q == 1 && head[0] ? 1 : 0);
-        int32_t kk = s_key[w][e];
+    const int64_t c0 = mode == 2 ? crp[li] : crp[i];
+    __syncwarp();
+    for (int r = 0; r < 2; ++r) {
+        const int slot = lane + 32 * r;
+        if (slot >= distinct) break;
+        const unsigned b0 = r ? hi0 : lo0, b1 = r ? hi1 : lo1;
+        unsigned any = b0 | b1;
         double sum = 0.0;
-        for (int f = e; f < 64 && s_key[w][f] == kk; ++f) sum += s_val[w][f];
-        cci[c0 + rank] = kk;
-        cv[c0 + rank] = sum;
+        while (any) {
+            const int l = __ffs(any) - 1;
+            any &= any - 1;
+            if ((b0 >> l) & 1u) sum += s_val[w][2 * l];
+            if ((b1 >> l) & 1u) sum += s_val[w][2 * l + 1];
+        }
+        cci[c0 + slot] = r ? col_hi : col_lo;
+        cv[c0 + slot] = sum;
     }
 }
 
