@@ -369,21 +369,37 @@ int build_csr_perm(const DCSR& A, const int32_t* rmap, const int32_t* cmap, VCSR
     return SPHC_OK;
 }
 
+// Layout switches of the transfer operators, read from SPHC_XOP_LAYOUT (a bit mask; 0 or unset in
+// normal use) so that tests reach every form at small sizes: 1 CSR for every operator, 2 the
+// lanes-per-row product for every CSR operator, 4 the row-block product for every CSR operator.
+static int xop_layout_flags() {
+    const char* e = getenv("SPHC_XOP_LAYOUT");
+    return e ? atoi(e) : 0;
+}
+// mean row length up to which a CSR operator takes the row-block product (a warp's 32 rows then
+// fit in one or two tiles of staged products)
+static constexpr int64_t ROWS32_MAX_MEAN = 24;
+
 // SELL when the slices pad to at most 1.3 x the nonzeros, CSR otherwise
 template <typename T>
 int build_xop(const DCSR& A, const int32_t* rmap, const int32_t* cmap, XOp<T>& X, cudaStream_t s) {
     X = XOp<T>();
     X.nr = A.nr; X.nc = A.nc; X.nnz = A.nnz;
-    std::vector<int64_t> seg{0, A.nr};
-    int ch = 4, lpr = sell_lpr_for(A, 1);
-    SPHC_TRY(sell_pick_ch(A, rmap, seg, lpr, s, &ch));
-    SPHC_TRY(build_sell<T>(A, rmap, cmap, seg, ch, lpr, X.s, nullptr, nullptr, s));
-    if ((double)X.s.stored <= 1.3 * (double)A.nnz) {
-        X.sell = true;
-        return SPHC_OK;
+    const int flags = xop_layout_flags();
+    if (!(flags & 1)) {
+        std::vector<int64_t> seg{0, A.nr};
+        int ch = 4, lpr = sell_lpr_for(A, 1);
+        SPHC_TRY(sell_pick_ch(A, rmap, seg, lpr, s, &ch));
+        SPHC_TRY(build_sell<T>(A, rmap, cmap, seg, ch, lpr, X.s, nullptr, nullptr, s));
+        if ((double)X.s.stored <= 1.3 * (double)A.nnz) {
+            X.sell = true;
+            return SPHC_OK;
+        }
+        X.s = Sell<T>();
     }
-    X.s = Sell<T>();
-    return build_csr_perm<T>(A, rmap, cmap, X.c, s);
+    SPHC_TRY(build_csr_perm<T>(A, rmap, cmap, X.c, s));
+    X.c.rows32 = (flags & 4) || (!(flags & 2) && A.nnz <= ROWS32_MAX_MEAN * A.nr);
+    return SPHC_OK;
 }
 
 // nonzeros of the rows rmap[k], k in [k0, k1)

@@ -91,15 +91,24 @@ __device__ __forceinline__ T sell_part(const int32_t* __restrict__ ci, const T* 
         vp += U * SELL_C * CH;
         cp += U * SELL_C * CH;
     }
-    for (; q < steps; ++q) {
-        T a[CH];
-        int32_t c[CH];
-        Chunk<T, CH>::load(vp, a);
-        IChunk<CH>::load(cp, c);
+    // The last steps - q < U steps: all their matrix loads are issued before the first gather, so
+    // the tail costs one more round trip, not one per step (a coarse level's lanes often hold only
+    // 2 or 3 steps).  The sum takes the products in the same order as a step-by-step loop.
+    const int rem = (int)(steps - q);
+    if (rem > 0) {
+        T a[U - 1][CH];
+        int32_t c[U - 1][CH];
 #pragma unroll
-        for (int t = 0; t < CH; ++t) sum += a[t] * x[c[t]];
-        vp += SELL_C * CH;
-        cp += SELL_C * CH;
+        for (int u = 0; u < U - 1; ++u)
+            if (u < rem) {
+                Chunk<T, CH>::load(vp + u * SELL_C * CH, a[u]);
+                IChunk<CH>::load(cp + u * SELL_C * CH, c[u]);
+            }
+#pragma unroll
+        for (int u = 0; u < U - 1; ++u)
+            if (u < rem)
+#pragma unroll
+                for (int t = 0; t < CH; ++t) sum += a[u][t] * x[c[u][t]];
     }
     return sum;
 }

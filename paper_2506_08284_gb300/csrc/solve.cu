@@ -448,6 +448,49 @@ __global__ void k_spmv_v(const int32_t* __restrict__ rp, const int32_t* __restri
     for (int o = SUB / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o, SUB);
     if (valid && q == 0) y[i] = accumulate ? y[i] + alpha * sum : alpha * sum;
 }
+// The same product for short rows (up to a few dozen entries): a warp takes 32 consecutive rows,
+// whose entries are one contiguous range.  The warp streams that range in tiles of 32 * ROWS_U
+// entries (coalesced loads, ROWS_U per lane in flight before the gathers), stages the products in
+// shared memory, and lane k then sums row k's products in entry order.  Lanes per row with strided
+// loops keep one load per lane in flight, which leaves the fine-level prolongation latency-bound.
+static constexpr int ROWS_U = 16, ROWS_WARPS = 8;
+template <typename T>
+__global__ void __launch_bounds__(ROWS_WARPS * 32)
+k_spmv_rows32(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const T* __restrict__ v, int64_t n,
+              const T* __restrict__ x, T* y, int accumulate, T alpha) {
+    constexpr int TILE = 32 * ROWS_U;
+    __shared__ T sp[ROWS_WARPS][TILE];
+    pdl_enter();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t r0 = ((int64_t)blockIdx.x * ROWS_WARPS + w) * 32;
+    if (r0 >= n) return;                                   // uniform over the warp
+    const int64_t r = r0 + lane;
+    const int nrow = (int)(n - r0 < 32 ? n - r0 : 32);
+    const bool valid = lane < nrow;
+    const int32_t rs = valid ? rp[r] : 0, re = valid ? rp[r + 1] : 0;
+    const int32_t e0 = __shfl_sync(0xffffffffu, rs, 0), e1 = __shfl_sync(0xffffffffu, re, nrow - 1);
+    T* s = sp[w];
+    T sum = 0;
+    for (int32_t t0 = e0; t0 < e1; t0 += TILE) {
+        const int32_t tn = e1 - t0 < TILE ? e1 - t0 : TILE;
+        T a[ROWS_U];
+        int32_t c[ROWS_U];
+#pragma unroll
+        for (int u = 0; u < ROWS_U; ++u)
+            if (u * 32 + lane < tn) {
+                a[u] = __ldcs(v + t0 + u * 32 + lane);
+                c[u] = __ldcs(ci + t0 + u * 32 + lane);
+            }
+#pragma unroll
+        for (int u = 0; u < ROWS_U; ++u)
+            if (u * 32 + lane < tn) s[u * 32 + lane] = a[u] * x[c[u]];
+        __syncwarp();
+        const int32_t lo = (rs > t0 ? rs : t0) - t0, hi = (re < t0 + tn ? re : t0 + tn) - t0;
+        for (int32_t k = lo; k < hi; ++k) sum += s[k];
+        __syncwarp();
+    }
+    if (valid) y[r] = accumulate ? y[r] + alpha * sum : alpha * sum;
+}
 
 template <typename T>
 __global__ void k_dt_gather(const int32_t* __restrict__ rp, const int32_t* __restrict__ enc, int64_t nv,
@@ -732,6 +775,11 @@ static void spmv_v(const XOp<T>& X, const T* x, T* y, int acc, cudaStream_t s, T
         return;
     }
     const VCSR<T>& A = X.c;
+    if (A.rows32) {
+        launch_pdl(k_spmv_rows32<T>, (unsigned)((A.nr + 32 * ROWS_WARPS - 1) / (32 * ROWS_WARPS)), ROWS_WARPS * 32, 0, s,
+                   A.rp.p, A.ci.p, A.v.p, A.nr, x, y, acc, alpha);
+        return;
+    }
     int sub = sub_for(A.nnz, A.nr);
     int64_t th = A.nr * sub;
     switch (sub) {

@@ -79,6 +79,7 @@ struct VCSR {
     int64_t nr = 0, nc = 0, nnz = 0;
     DBuf<int32_t> rp, ci;
     DBuf<T> v;
+    bool rows32 = false;  // products by the row-block kernel (short rows), else lanes per row
 };
 
 // Operator only multiplied (transfers, A D): SELL when its rows pad well, CSR otherwise.
