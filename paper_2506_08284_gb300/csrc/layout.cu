@@ -167,11 +167,14 @@ __global__ void k_sell_count(const int32_t* w, int64_t nslice, int rps, int q, i
 // lanes walk the slice's stored entries in storage order (coalesced writes), each finding the
 // row q and entry j it holds: position p = (step * 32 + q * lpr + k % lpr) * ch + j % ch with
 // chunk k = j / ch = step * lpr + k % lpr.  Entries past a row's end get value 0 and the row's
-// last column (0 for an empty row).
+// last column (0 for an empty row).  Each trip of the loop handles FILL_U positions a lane and
+// issues all their loads before the column-map gathers and the stores.
+static constexpr int FILL_U = 4;
 template <typename T>
-__global__ void k_sell_fill(const int64_t* rp, const int32_t* ci, const double* v, const int32_t* rmap,
-                            const int32_t* cmap, const int32_t* srow, const int64_t* soff, int64_t nslice, int ch,
-                            int lpr, int32_t* sci, T* sv, T* dinv) {
+__global__ void k_sell_fill(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci, const double* __restrict__ v,
+                            const int32_t* __restrict__ rmap, const int32_t* __restrict__ cmap,
+                            const int32_t* __restrict__ srow, const int64_t* __restrict__ soff, int64_t nslice, int ch,
+                            int lpr, int32_t* __restrict__ sci, T* __restrict__ sv, T* __restrict__ dinv) {
     int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (s >= nslice) return;
     int lane = threadIdx.x & 31;
@@ -193,26 +196,42 @@ __global__ void k_sell_fill(const int64_t* rp, const int32_t* ci, const double* 
     // ch and lpr are powers of two (1, 2, 4 and 1 .. 32): shifts and masks, not divisions
     const int lch = ch == 1 ? 0 : (ch == 2 ? 1 : 2);
     const int llpr = __ffs(lpr) - 1;
-    for (int p0 = 0; p0 < total; p0 += 32) {
-        const int p = p0 + lane;
-        const int step = p >> (5 + lch);
-        const int rem = p & ((SELL_C << lch) - 1);
-        const int slotl = rem >> lch, tch = rem & (ch - 1);
-        const int q = slotl >> llpr, kk = slotl & (lpr - 1);
-        const int64_t j = ((int64_t)step * lpr + kk) * ch + tch;
-        int64_t bq = __shfl_sync(0xffffffffu, b, q);
-        int64_t lq = __shfl_sync(0xffffffffu, len, q);
-        int64_t iq = __shfl_sync(0xffffffffu, i, q);
-        int32_t pq = __shfl_sync(0xffffffffu, pad, q);
-        if (p >= total) continue;
-        if (j < lq) {
-            int32_t c0 = ci[bq + j];
-            sci[o + p] = cmap ? cmap[c0] : c0;
-            sv[o + p] = (T)v[bq + j];
-            if (dinv && c0 == iq) dinv[r0 + q] = (T)(1.0 / v[bq + j]);
-        } else {
-            sci[o + p] = pq;
-            sv[o + p] = (T)0;
+    for (int p0 = 0; p0 < total; p0 += 32 * FILL_U) {
+        int32_t c[FILL_U], pq[FILL_U], q[FILL_U];
+        double a[FILL_U];
+        bool in[FILL_U], diag[FILL_U];
+#pragma unroll
+        for (int u = 0; u < FILL_U; ++u) {
+            const int p = p0 + u * 32 + lane;
+            const int step = p >> (5 + lch);
+            const int rem = p & ((SELL_C << lch) - 1);
+            const int slotl = rem >> lch, tch = rem & (ch - 1);
+            q[u] = slotl >> llpr;
+            const int kk = slotl & (lpr - 1);
+            const int64_t j = ((int64_t)step * lpr + kk) * ch + tch;
+            const int64_t bq = __shfl_sync(0xffffffffu, b, q[u]);
+            const int64_t lq = __shfl_sync(0xffffffffu, len, q[u]);
+            const int64_t iq = __shfl_sync(0xffffffffu, i, q[u]);
+            pq[u] = __shfl_sync(0xffffffffu, pad, q[u]);
+            in[u] = p < total && j < lq;
+            c[u] = 0;
+            a[u] = 0.0;
+            if (in[u]) {
+                c[u] = ci[bq + j];
+                a[u] = v[bq + j];
+            }
+            diag[u] = in[u] && c[u] == iq;
+        }
+#pragma unroll
+        for (int u = 0; u < FILL_U; ++u)
+            if (in[u] && cmap) c[u] = cmap[c[u]];
+#pragma unroll
+        for (int u = 0; u < FILL_U; ++u) {
+            const int p = p0 + u * 32 + lane;
+            if (p >= total) continue;
+            sci[o + p] = in[u] ? c[u] : pq[u];
+            sv[o + p] = (T)a[u];
+            if (dinv && diag[u]) dinv[r0 + q[u]] = (T)(1.0 / a[u]);
         }
     }
 }
@@ -237,8 +256,10 @@ int sell_lpr_for(const DCSR& A, int ncolor) {
 
 // Entries per lane load: the widest of 4, 2, 1 whose padding stays within 10% of the
 // one-entry layout.
-int sell_pick_ch(const DCSR& A, const int32_t* rmap, const std::vector<int64_t>& seg, int lpr, cudaStream_t s, int* ch) {
+int sell_pick_ch(const DCSR& A, const int32_t* rmap, const std::vector<int64_t>& seg, int lpr, cudaStream_t s, int* ch,
+                 int64_t* stored) {
     *ch = 4;
+    if (stored) *stored = 0;
     int rps = SELL_C / lpr;
     std::vector<int64_t> segslice = slice_starts(seg, rps);
     int64_t nslice = segslice.back();
@@ -263,6 +284,7 @@ int sell_pick_ch(const DCSR& A, const int32_t* rmap, const std::vector<int64_t>&
     if ((double)h[2] <= 1.1 * (double)h[0]) *ch = 4;
     else if ((double)h[1] <= 1.1 * (double)h[0]) *ch = 2;
     else *ch = 1;
+    if (stored) *stored = (int64_t)h[*ch == 4 ? 2 : (*ch == 2 ? 1 : 0)];
     return SPHC_OK;
 }
 
@@ -326,19 +348,31 @@ __global__ void k_rp_narrow32(const int64_t* a, int32_t* b, int64_t n) {
     if (i < n) b[i] = (int32_t)a[i];
 }
 // G lanes per row (the mean row length rounded up to a power of two, 4 to 32)
+// (two entries a lane per trip, both loaded before their column-map gathers and stores)
 template <typename T, int G>
-__global__ void k_perm_fill(const int64_t* rp, const int32_t* ci, const double* v, const int32_t* rmap,
-                            const int32_t* cmap, int64_t n, const int32_t* nrp, int32_t* nci, T* nv) {
+__global__ void k_perm_fill(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci, const double* __restrict__ v,
+                            const int32_t* __restrict__ rmap, const int32_t* __restrict__ cmap, int64_t n,
+                            const int32_t* __restrict__ nrp, int32_t* __restrict__ nci, T* __restrict__ nv) {
     int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
     int lane = threadIdx.x & (G - 1);
     if (k >= n) return;
     int64_t i = rmap ? rmap[k] : k;
     int64_t b = rp[i], len = rp[i + 1] - b;
     int32_t o = nrp[k];
-    for (int64_t q = lane; q < len; q += G) {
-        int32_t c = ci[b + q];
-        nci[o + q] = cmap ? cmap[c] : c;
-        nv[o + q] = (T)v[b + q];
+    for (int64_t q = lane; q < len; q += 2 * G) {
+        const bool two = q + G < len;
+        int32_t c0 = ci[b + q], c1 = two ? ci[b + q + G] : 0;
+        double a0 = v[b + q], a1 = two ? v[b + q + G] : 0.0;
+        if (cmap) {
+            c0 = cmap[c0];
+            if (two) c1 = cmap[c1];
+        }
+        nci[o + q] = c0;
+        nv[o + q] = (T)a0;
+        if (two) {
+            nci[o + q + G] = c1;
+            nv[o + q + G] = (T)a1;
+        }
     }
 }
 template <typename T>
@@ -389,13 +423,13 @@ int build_xop(const DCSR& A, const int32_t* rmap, const int32_t* cmap, XOp<T>& X
     if (!(flags & 1)) {
         std::vector<int64_t> seg{0, A.nr};
         int ch = 4, lpr = sell_lpr_for(A, 1);
-        SPHC_TRY(sell_pick_ch(A, rmap, seg, lpr, s, &ch));
-        SPHC_TRY(build_sell<T>(A, rmap, cmap, seg, ch, lpr, X.s, nullptr, nullptr, s));
-        if ((double)X.s.stored <= 1.3 * (double)A.nnz) {
+        int64_t stored = 0;
+        SPHC_TRY(sell_pick_ch(A, rmap, seg, lpr, s, &ch, &stored));
+        if ((double)stored <= 1.3 * (double)A.nnz) {
+            SPHC_TRY(build_sell<T>(A, rmap, cmap, seg, ch, lpr, X.s, nullptr, nullptr, s));
             X.sell = true;
             return SPHC_OK;
         }
-        X.s = Sell<T>();
     }
     SPHC_TRY(build_csr_perm<T>(A, rmap, cmap, X.c, s));
     X.c.rows32 = (flags & 4) || (!(flags & 2) && A.nnz <= ROWS32_MAX_MEAN * A.nr);

@@ -267,7 +267,8 @@ template <typename T>
 int build_smooth(const DCSR& A, const int32_t* rmap, const int32_t* cmap, const std::vector<int64_t>& cstart, int ch,
                  int lpr, SmoothOp<T>& op, cudaStream_t s);
 int sell_lpr_for(const DCSR& A, int ncolor);
-int sell_pick_ch(const DCSR& A, const int32_t* rmap, const std::vector<int64_t>& seg, int lpr, cudaStream_t s, int* ch);
+int sell_pick_ch(const DCSR& A, const int32_t* rmap, const std::vector<int64_t>& seg, int lpr, cudaStream_t s, int* ch,
+                 int64_t* stored = nullptr);
 int build_d_pairs(const DCSR& D, const int32_t* pe, const int32_t* in, DBuf<int2>& out, cudaStream_t s);
 int build_dt_enc(const DCSR& Dt, const int32_t* pn, const int32_t* ie, DBuf<int32_t>& rp, DBuf<int32_t>& enc,
                  cudaStream_t s);
