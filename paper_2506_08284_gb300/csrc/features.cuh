@@ -42,14 +42,38 @@ struct FeatBufs {
 // Fill B from level L (coarse coordinates Xc) and point g at it.
 int feat_prepare(const Level& L, const DBuf<double>& Xc, int lev, FeatBufs& B, FeatArgs& g, cudaStream_t s);
 
-__device__ inline float row_lookup_f(const int64_t* rp, const int32_t* ci, const float* v, int64_t r, int32_t col) {
-    if (r < 0) return 0.f;
-    int64_t lo = rp[r], hi = rp[r + 1] - 1;
-    while (lo < hi) {
-        int64_t mid = (lo + hi) >> 1;
-        if (ci[mid] < col) lo = mid + 1; else hi = mid;
+// NL lookups at once: entry k is the value at column col[k] of the row [lo[k], lo[k] + n[k]) of a
+// CSR operator with sorted columns (ci[k], v[k]), 0 where the row lacks it (n[k] = 0 for an absent
+// row).  The searches halve their ranges in lockstep, so each step issues all NL probes before any
+// is used: about log2(row length) + 1 dependent loads in all instead of that many per lookup.  Each
+// search is a plain lower bound, so it finds the entry a one-at-a-time binary search finds.
+template <int NL>
+__device__ inline void row_lookups_f(const int32_t* const (&ci)[NL], const float* const (&v)[NL], int64_t (&lo)[NL],
+                                     int64_t (&n)[NL], const int32_t (&col)[NL], float (&out)[NL]) {
+    int64_t end[NL];
+#pragma unroll
+    for (int k = 0; k < NL; ++k) end[k] = lo[k] + n[k];
+    for (;;) {
+        bool more = false;
+        int32_t c[NL];
+#pragma unroll
+        for (int k = 0; k < NL; ++k) c[k] = n[k] > 0 ? ci[k][lo[k] + (n[k] >> 1)] : 0;
+#pragma unroll
+        for (int k = 0; k < NL; ++k) {
+            if (n[k] > 0) {
+                const int64_t half = n[k] >> 1;
+                if (c[k] < col[k]) { lo[k] += half + 1; n[k] -= half + 1; }
+                else n[k] = half;
+            }
+            more |= n[k] > 0;
+        }
+        if (!more) break;
     }
-    return (lo <= hi && ci[lo] == col) ? v[lo] : 0.f;
+    int32_t c[NL];
+#pragma unroll
+    for (int k = 0; k < NL; ++k) c[k] = lo[k] < end[k] ? ci[k][lo[k]] : -1;
+#pragma unroll
+    for (int k = 0; k < NL; ++k) out[k] = (lo[k] < end[k] && c[k] == col[k]) ? v[k][lo[k]] : 0.f;
 }
 
 // Features 13-18 (the six row lookups) form part 1, the rest part 0, so that two threads can
@@ -89,12 +113,22 @@ __device__ inline void entry_features(const FeatArgs& g, int64_t i, int64_t q, f
     f[11] = R.nlen;
     f[12] = R.tlen;
     if (part != 0) {
-        f[13] = ja >= 0 ? row_lookup_f(g.trp, g.tci, g.tvf, i, ja) : 0.f;
-        f[14] = jb >= 0 ? row_lookup_f(g.trp, g.tci, g.tvf, i, jb) : 0.f;
-        f[15] = ja >= 0 ? row_lookup_f(g.prp, g.pci, g.pvf, R.u, ja) : 0.f;
-        f[16] = jb >= 0 ? row_lookup_f(g.prp, g.pci, g.pvf, R.u, jb) : 0.f;
-        f[17] = ja >= 0 ? row_lookup_f(g.prp, g.pci, g.pvf, R.v, ja) : 0.f;
-        f[18] = jb >= 0 ? row_lookup_f(g.prp, g.pci, g.pvf, R.v, jb) : 0.f;
+        // T row i at ja, jb; P_n row u at ja, jb; P_n row v at ja, jb (absent rows and ends: 0)
+        const int32_t* const cis[6] = {g.tci, g.tci, g.pci, g.pci, g.pci, g.pci};
+        const float* const vs[6] = {g.tvf, g.tvf, g.pvf, g.pvf, g.pvf, g.pvf};
+        const int64_t rows[6] = {i, i, R.u, R.u, R.v, R.v};
+        const int32_t cols[6] = {ja, jb, ja, jb, ja, jb};
+        int64_t lo[6], n[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const int64_t* rp = k < 2 ? g.trp : g.prp;
+            const bool on = rows[k] >= 0 && cols[k] >= 0;
+            lo[k] = on ? rp[rows[k]] : 0;
+            n[k] = on ? rp[rows[k] + 1] - lo[k] : 0;
+        }
+        float r6[6];
+        row_lookups_f<6>(cis, vs, lo, n, cols, r6);
+        for (int k = 0; k < 6; ++k) f[13 + k] = r6[k];
     }
     if (part == 1) return;
     // f[19] stays 0: the features are computed before P0 exists (the network's output is
