@@ -678,10 +678,22 @@ __global__ void k_pattern(const int64_t* trp, const int32_t* tci, int64_t ne, co
 
 // Thread per fine row for rows whose T_i has at most PT_K coarse nodes (larger rows go to
 // k_pattern through a row list): the same N_i, enumerated from the incidence lists of T_i's nodes
-// (each two-node edge once, from its first node).  mode 0 counts N_i and checks that the local
-// graph is connected (reachability over an 8 x 8 adjacency bitmask); mode 1 writes N_i sorted,
-// by merging the per-node lists (each sorted by edge id).
+// (each two-node edge once, from its first node).  A coarse edge's nodes come from E2 (first node,
+// second node or -1), one load per incidence; each node's list is read four entries at a time.
+// mode 0 counts N_i and checks that the local graph is connected (reachability over an 8 x 8
+// adjacency bitmask); mode 1 collects N_i (up to PT_NMAX edges) and writes each edge at its rank,
+// so the row comes out sorted; a longer N_i is written by merging the per-node lists (each sorted
+// by edge id).
 constexpr int PT_K = 8;
+constexpr int PT_NMAX = 48;
+__global__ void k_edge_pairs(const int64_t* __restrict__ hrp, const int32_t* __restrict__ hci, int64_t nE,
+                             int2* __restrict__ E2) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nE) return;
+    int64_t b = hrp[e];
+    int len = (int)(hrp[e + 1] - b);
+    E2[e] = make_int2(len >= 1 ? hci[b] : -1, len == 2 ? hci[b + 1] : -1);
+}
 __device__ __forceinline__ int pat_local(const int32_t T[PT_K], int m, int32_t u) {
     int c = -1;
 #pragma unroll
@@ -689,23 +701,20 @@ __device__ __forceinline__ int pat_local(const int32_t T[PT_K], int m, int32_t u
         if (a < m && T[a] == u) c = a;
     return c;
 }
-// is coarse edge e (listed under node J) in N_i, counted from this list?
-__device__ __forceinline__ bool pat_take(const int64_t* __restrict__ hrp, const int32_t* __restrict__ hci,
-                                         const int32_t T[PT_K], int m, int32_t e, int32_t J, int* other) {
-    int64_t b = hrp[e];
-    int len = (int)(hrp[e + 1] - b);
+// is coarse edge e with nodes p (listed under node J) in N_i, counted from this list?
+__device__ __forceinline__ bool pat_take(int2 p, const int32_t T[PT_K], int m, int32_t J, int* other) {
     *other = -1;
-    if (len == 1) return true;
-    if (hci[b] != J) return false;
-    int c = pat_local(T, m, hci[b + 1]);
+    if (p.y < 0) return true;
+    if (p.x != J) return false;
+    int c = pat_local(T, m, p.y);
     *other = c;
     return c >= 0;
 }
 __global__ void __launch_bounds__(128)
 k_pattern_rows(const int64_t* __restrict__ trp, const int32_t* __restrict__ tci, int64_t ne,
-               const int64_t* __restrict__ htrp, const int32_t* __restrict__ htci, const int64_t* __restrict__ hrp,
-               const int32_t* __restrict__ hci, int mode, int64_t* cnt, const int64_t* __restrict__ nrp,
-               int32_t* __restrict__ nci, int* stats, int32_t* big, int* nbig, int32_t* bad) {
+               const int64_t* __restrict__ htrp, const int32_t* __restrict__ htci, const int2* __restrict__ E2,
+               int mode, int64_t* cnt, const int64_t* __restrict__ nrp, int32_t* __restrict__ nci, int* stats,
+               int32_t* big, int* nbig, int32_t* bad) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ne) return;
     int64_t t0 = trp[i];
@@ -717,20 +726,36 @@ k_pattern_rows(const int64_t* __restrict__ trp, const int32_t* __restrict__ tci,
     int32_t T[PT_K];
 #pragma unroll
     for (int a = 0; a < PT_K; ++a) T[a] = a < m ? tci[t0 + a] : -1;
-    if (mode == 0) {
-        int np = 0;
-        uint64_t adj = 0;
+    int64_t kb[PT_K], ke[PT_K];
 #pragma unroll
-        for (int a = 0; a < PT_K; ++a) {
-            if (a >= m) continue;
-            for (int64_t k = htrp[T[a]]; k < htrp[T[a] + 1]; ++k) {
+    for (int a = 0; a < PT_K; ++a) {
+        kb[a] = a < m ? htrp[T[a]] : 0;
+        ke[a] = a < m ? htrp[T[a] + 1] : 0;
+    }
+    int32_t N[PT_NMAX];
+    int np = 0;
+    uint64_t adj = 0;
+#pragma unroll
+    for (int a = 0; a < PT_K; ++a) {
+        for (int64_t k0 = kb[a]; k0 < ke[a]; k0 += 4) {
+            int32_t e[4];
+            int2 pr[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) e[u] = k0 + u < ke[a] ? htci[k0 + u] : -1;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) pr[u] = e[u] >= 0 ? E2[e[u]] : make_int2(-1, -1);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
                 int c;
-                if (pat_take(hrp, hci, T, m, htci[k], T[a], &c)) {
+                if (e[u] >= 0 && pat_take(pr[u], T, m, T[a], &c)) {
+                    if (np < PT_NMAX) N[np] = e[u];
                     ++np;
                     if (c >= 0) adj |= (1ull << (8 * a + c)) | (1ull << (8 * c + a));
                 }
             }
         }
+    }
+    if (mode == 0) {
         if (np > MAX_NP) { atomicExch(&stats[1], 1); cnt[i] = 0; return; }
         cnt[i] = np;
         if (m > 1) {
@@ -749,22 +774,29 @@ k_pattern_rows(const int64_t* __restrict__ trp, const int32_t* __restrict__ tci,
         }
         return;
     }
-    // mode 1: merge the per-node lists
-    int64_t cur[PT_K], end[PT_K];
+    int64_t out = nrp[i];
+    if (np <= PT_NMAX) {
+        for (int t = 0; t < np; ++t) {
+            int rank = 0;
+            for (int q = 0; q < np; ++q) rank += N[q] < N[t];
+            nci[out + rank] = N[t];
+        }
+        return;
+    }
+    // a long N_i: merge the per-node lists
+    int64_t cur[PT_K];
 #pragma unroll
     for (int a = 0; a < PT_K; ++a) {
-        cur[a] = a < m ? htrp[T[a]] : 0;
-        end[a] = a < m ? htrp[T[a] + 1] : 0;
+        cur[a] = kb[a];
         int c;
-        while (cur[a] < end[a] && !pat_take(hrp, hci, T, m, htci[cur[a]], T[a], &c)) ++cur[a];
+        while (cur[a] < ke[a] && !pat_take(E2[htci[cur[a]]], T, m, T[a], &c)) ++cur[a];
     }
-    int64_t out = nrp[i];
     for (;;) {
         int32_t best = INT32_MAX;
         int bi = -1;
 #pragma unroll
         for (int a = 0; a < PT_K; ++a)
-            if (cur[a] < end[a] && htci[cur[a]] < best) { best = htci[cur[a]]; bi = a; }
+            if (cur[a] < ke[a] && htci[cur[a]] < best) { best = htci[cur[a]]; bi = a; }
         if (bi < 0) break;
         nci[out++] = best;
 #pragma unroll
@@ -772,7 +804,7 @@ k_pattern_rows(const int64_t* __restrict__ trp, const int32_t* __restrict__ tci,
             if (a == bi) {
                 ++cur[a];
                 int c;
-                while (cur[a] < end[a] && !pat_take(hrp, hci, T, m, htci[cur[a]], T[a], &c)) ++cur[a];
+                while (cur[a] < ke[a] && !pat_take(E2[htci[cur[a]]], T, m, T[a], &c)) ++cur[a];
             }
     }
 }
@@ -2136,6 +2168,7 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
     DBuf<int> st, pctl;
     DBuf<int32_t> pbig, pbad;
     DBuf<uint64_t> pairs;
+    DBuf<int2> E2;
     SPHC_TRY(ncnt.alloc(ne + 1, s));
     SPHC_TRY(st.alloc(8, s));
     SPHC_TRY(pbig.alloc(ne > 0 ? ne : 1, s));
@@ -2148,11 +2181,13 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
         // counts of N_i and disconnected rows against the current D_H; rows with more than
         // PT_K coarse nodes go to the warp-per-row kernel through a list (st[6] counts them)
         SPHC_TRY(transpose(L.DH, DHt, s));
+        SPHC_TRY(E2.alloc(L.DH.nr > 0 ? L.DH.nr : 1, s));
+        if (L.DH.nr > 0) SPHC_LAUNCH(k_edge_pairs<<<grid_for(L.DH.nr, 256), 256, 0, s>>>(L.DH.rp.p, L.DH.ci.p, L.DH.nr, E2.p));
         SPHC_TRY(st.zero(s));
         if (ne > 0)
             SPHC_LAUNCH(k_pattern_rows<<<grid_for(ne, 128), 128, 0, s>>>(L.T.rp.p, L.T.ci.p, ne, DHt.rp.p, DHt.ci.p,
-                                                                       L.DH.rp.p, L.DH.ci.p, 0, ncnt.p, nullptr,
-                                                                       nullptr, st.p, pbig.p, st.p + 6, pbad.p));
+                                                                       E2.p, 0, ncnt.p, nullptr, nullptr, st.p,
+                                                                       pbig.p, st.p + 6, pbad.p));
         SPHC_CK(cudaMemcpyAsync(hs, st.p, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
         SPHC_CK(cudaStreamSynchronize(s));
         npbig = hs[6];
@@ -2206,9 +2241,9 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
     SPHC_TRY(L.P0.v.alloc(nnzN, s));
     SPHC_TRY(max_row_length(L.P0.rp.p, ne, s, &L.max_np));
     if (ne > 0)
-        SPHC_LAUNCH(k_pattern_rows<<<grid_for(ne, 128), 128, 0, s>>>(L.T.rp.p, L.T.ci.p, ne, DHt.rp.p, DHt.ci.p, L.DH.rp.p,
-                                                                   L.DH.ci.p, 1, nullptr, L.P0.rp.p, L.P0.ci.p, st.p,
-                                                                   nullptr, nullptr, nullptr));
+        SPHC_LAUNCH(k_pattern_rows<<<grid_for(ne, 128), 128, 0, s>>>(L.T.rp.p, L.T.ci.p, ne, DHt.rp.p, DHt.ci.p, E2.p,
+                                                                   1, nullptr, L.P0.rp.p, L.P0.ci.p, st.p, nullptr,
+                                                                   nullptr, nullptr));
     if (npbig > 0)
         SPHC_LAUNCH(k_pattern<<<grid_for(npbig, PAT_WARPS), PAT_WARPS * 32, 0, s>>>(L.T.rp.p, L.T.ci.p, npbig, pbig.p,
                                                                       DHt.rp.p, DHt.ci.p, L.DH.rp.p, L.DH.ci.p, 1,
