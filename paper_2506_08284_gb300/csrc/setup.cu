@@ -1274,11 +1274,25 @@ struct RowSys {
     int64_t n0;
 };
 
-// 1: factored; 0: infeasible; -1: too large for one thread; 2: empty row
+// Coarse edge e of D_H as two codes 2 node + (value < 0), the second -1 for a single-node row:
+// one 8-byte load per pattern entry instead of a row pointer and then its entries.
+__global__ void k_edge_codes(const int64_t* __restrict__ hrp, const int32_t* __restrict__ hci,
+                             const double* __restrict__ hv, int64_t nE, int2* __restrict__ E) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nE) return;
+    int64_t b = hrp[e];
+    int len = (int)(hrp[e + 1] - b);
+    int2 c = make_int2(-1, -1);
+    if (len >= 1) c.x = 2 * hci[b] + (hv[b] < 0 ? 1 : 0);
+    if (len >= 2) c.y = 2 * hci[b + 1] + (hv[b + 1] < 0 ? 1 : 0);
+    E[e] = c;
+}
+
+// 1: factored; 0: infeasible; -1: too large for one thread; 2: empty row.  The row's pattern
+// entries are read four at a time (their edge ids, then their codes), so the loads overlap.
 __device__ __forceinline__ int row_factor(int64_t i, const int64_t* __restrict__ trp, const int32_t* __restrict__ tci,
                                           const double* __restrict__ tv, const int64_t* __restrict__ nrp,
-                                          const int32_t* __restrict__ nci, const int64_t* __restrict__ hrp,
-                                          const int32_t* __restrict__ hci, const double* __restrict__ hv, RowSys& S) {
+                                          const int32_t* __restrict__ nci, const int2* __restrict__ E, RowSys& S) {
     int64_t t0 = trp[i];
     int m = (int)(trp[i + 1] - t0);
     S.n0 = nrp[i];
@@ -1294,20 +1308,31 @@ __device__ __forceinline__ int row_factor(int64_t i, const int64_t* __restrict__
         S.neg[a] = 0u;
     }
     bool single = false;
-    for (int t = 0; t < S.np; ++t) {
-        int32_t e = nci[S.n0 + t];
-        int64_t b = hrp[e];
-        int len = (int)(hrp[e + 1] - b);
-        if (len == 1) single = true;
-        for (int q = 0; q < len; ++q) {
-            int32_t u = hci[b + q];
-            bool minus = hv[b + q] < 0;
+    for (int t0 = 0; t0 < S.np; t0 += 4) {
+        int32_t e[4];
+        int2 c[4];
 #pragma unroll
-            for (int a = 0; a < TK; ++a)
-                if (T[a] == u) {
-                    if (minus) S.neg[a] |= 1u << t;
-                    else S.pos[a] |= 1u << t;
-                }
+        for (int u = 0; u < 4; ++u) e[u] = t0 + u < S.np ? nci[S.n0 + t0 + u] : -1;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) c[u] = e[u] >= 0 ? E[e[u]] : make_int2(-1, -1);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (e[u] < 0) continue;
+            const int t = t0 + u;
+            if (c[u].x >= 0 && c[u].y < 0) single = true;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int32_t code = q == 0 ? c[u].x : c[u].y;
+                if (code < 0) continue;
+                const int32_t nd = code >> 1;
+                const bool minus = code & 1;
+#pragma unroll
+                for (int a = 0; a < TK; ++a)
+                    if (T[a] == nd) {
+                        if (minus) S.neg[a] |= 1u << t;
+                        else S.pos[a] |= 1u << t;
+                    }
+            }
         }
     }
     int k = single ? m : m - 1;     // Reduce_Dimension drops the largest coarse node
@@ -1442,13 +1467,12 @@ __device__ __forceinline__ void cache_get(const RowCache& C, int64_t i, RowSys& 
 template <typename DT>
 __global__ void __launch_bounds__(128)
 k_p0_rows(int64_t ne, const int64_t* __restrict__ trp, const int32_t* __restrict__ tci, const double* __restrict__ tv,
-          const int64_t* __restrict__ nrp, const int32_t* __restrict__ nci, const int64_t* __restrict__ hrp,
-          const int32_t* __restrict__ hci, const double* __restrict__ hv, const DT* __restrict__ d,
-          double* __restrict__ p0, int* fail, int32_t* big, int* nbig, RowCache cache) {
+          const int64_t* __restrict__ nrp, const int32_t* __restrict__ nci, const int2* __restrict__ E,
+          const DT* __restrict__ d, double* __restrict__ p0, int* fail, int32_t* big, int* nbig, RowCache cache) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ne) return;
     RowSys S;
-    int code = row_factor(i, trp, tci, tv, nrp, nci, hrp, hci, hv, S);
+    int code = row_factor(i, trp, tci, tv, nrp, nci, E, S);
     if (code != 1) cache.k[i] = -1;
     if (code == 2) return;
     if (code == -1) { big[warp_reserve(nbig)] = (int32_t)i; return; }
@@ -2297,17 +2321,21 @@ int build_level(Level& L, int lev, const sphc_opts& o, DCSR& Anext, DCSR& Dnext,
     SPHC_TRY(ck.alloc(ne > 0 ? ne : 1, s));
     SPHC_TRY(cL.alloc(TL * (ne > 0 ? ne : 1), s));
     RowCache cache{cpm.p, ck.p, cL.p, ne};
+    DBuf<int2> ecodes;
+    SPHC_TRY(ecodes.alloc(L.DH.nr > 0 ? L.DH.nr : 1, s));
+    if (L.DH.nr > 0)
+        SPHC_LAUNCH(k_edge_codes<<<grid_for(L.DH.nr, 256), 256, 0, s>>>(L.DH.rp.p, L.DH.ci.p, L.DH.v.p, L.DH.nr, ecodes.p));
     if (ne > 0) {
         // P0: the point of each row's constraint set nearest to the warm start (0: least-norm; the
         // MLP correction; or, with reuse, the previous P_e)
         if (reuse)
             SPHC_LAUNCH(k_p0_rows<double><<<grid_for(ne, 128), 128, 0, s>>>(
-                ne, L.T.rp.p, L.T.ci.p, L.T.v.p, L.P0.rp.p, L.P0.ci.p, L.DH.rp.p, L.DH.ci.p, L.DH.v.p, warm.p, L.P0.v.p,
-                st.p, big.p, nbig.p, cache));
+                ne, L.T.rp.p, L.T.ci.p, L.T.v.p, L.P0.rp.p, L.P0.ci.p, ecodes.p, warm.p, L.P0.v.p, st.p, big.p,
+                nbig.p, cache));
         else
             SPHC_LAUNCH(k_p0_rows<float><<<grid_for(ne, 128), 128, 0, s>>>(
-                ne, L.T.rp.p, L.T.ci.p, L.T.v.p, L.P0.rp.p, L.P0.ci.p, L.DH.rp.p, L.DH.ci.p, L.DH.v.p, corr.p, L.P0.v.p,
-                st.p, big.p, nbig.p, cache));
+                ne, L.T.rp.p, L.T.ci.p, L.T.v.p, L.P0.rp.p, L.P0.ci.p, ecodes.p, corr.p, L.P0.v.p, st.p, big.p,
+                nbig.p, cache));
         SPHC_CK(cudaMemcpyAsync(&hbig, nbig.p, sizeof(int), cudaMemcpyDeviceToHost, s));
         SPHC_CK(cudaStreamSynchronize(s));
         if (hbig > 0) {
