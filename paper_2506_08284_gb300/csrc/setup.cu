@@ -404,6 +404,10 @@ __global__ void k_uniform_vec(double* v, int64_t n, uint64_t seed) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) v[i] = (double)(splitmix64(seed, (uint64_t)i) >> 11) * (1.0 / 9007199254740992.0);
 }
+__global__ void k_scale_dinv(double* w, const double* d, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) w[i] /= d[i];
+}
 __global__ void k_normalise(double* v, const double* w, const double* ww, int64_t n) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double nw = sqrt(*ww);
@@ -419,9 +423,12 @@ int power_rho(const DCSR& A, const double* diag, uint64_t seed, int iters, doubl
     SPHC_TRY(sc.alloc(2, s));
     SPHC_LAUNCH(k_uniform_vec<<<grid_for(n, 256), 256, 0, s>>>(v.p, n, seed));
     double h[2] = {1.0, 1.0};
-    // w = D^-1 A v in one pass; only the last iteration's v . v is read
+    // only the last iteration's v . v is read.  (Dividing by the diagonal inside the SpMV's store
+    // measured slower: there one lane in eight runs the FP64 division sequence, so the thin FP64
+    // pipe executes it once per four rows instead of once per 32.)
     for (int it = 0; it < iters; ++it) {
-        SPHC_TRY(spmv64(A, v.p, w.p, s, diag));
+        SPHC_TRY(spmv64(A, v.p, w.p, s));
+        SPHC_LAUNCH(k_scale_dinv<<<grid_for(n, 256), 256, 0, s>>>(w.p, diag, n));
         if (it + 1 == iters) SPHC_TRY(dot64(v.p, v.p, n, sc.p, s));
         SPHC_TRY(dot64(w.p, w.p, n, sc.p + 1, s));
         SPHC_LAUNCH(k_normalise<<<grid_for(n, 256), 256, 0, s>>>(v.p, w.p, sc.p + 1, n));

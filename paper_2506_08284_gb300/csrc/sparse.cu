@@ -1531,9 +1531,8 @@ int spgemm_sym(const DCSR& A, const DCSR& B, DCSR& C, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------------ FP64 SpMV, dots
-// y = A x, or y_i = (A x)_i / div_i when div is given
 __global__ void k_spmv64(const int64_t* rp, const int32_t* ci, const double* v, int64_t n, const double* x,
-                         double* y, const double* div) {
+                         double* y) {
     int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t i = g >> 3;
     int sub = threadIdx.x & 7;
@@ -1544,10 +1543,10 @@ __global__ void k_spmv64(const int64_t* rp, const int32_t* ci, const double* v, 
     s += __shfl_xor_sync(0xffffffffu, s, 4);
     s += __shfl_xor_sync(0xffffffffu, s, 2);
     s += __shfl_xor_sync(0xffffffffu, s, 1);
-    if (valid && sub == 0) y[i] = div ? s / div[i] : s;
+    if (valid && sub == 0) y[i] = s;
 }
-int spmv64(const DCSR& A, const double* x, double* y, cudaStream_t s, const double* div) {
-    if (A.nr > 0) SPHC_LAUNCH(k_spmv64<<<grid_for(A.nr * 8, 256), 256, 0, s>>>(A.rp.p, A.ci.p, A.v.p, A.nr, x, y, div));
+int spmv64(const DCSR& A, const double* x, double* y, cudaStream_t s) {
+    if (A.nr > 0) SPHC_LAUNCH(k_spmv64<<<grid_for(A.nr * 8, 256), 256, 0, s>>>(A.rp.p, A.ci.p, A.v.p, A.nr, x, y));
     SPHC_CK(cudaGetLastError());
     return SPHC_OK;
 }

@@ -174,7 +174,7 @@ int csr_copy(const DCSR& A, DCSR& B, cudaStream_t s);
 // diag(A) into d (FP64)
 int csr_diag(const DCSR& A, double* d, cudaStream_t s);
 // y = A x (FP64)
-int spmv64(const DCSR& A, const double* x, double* y, cudaStream_t s, const double* div = nullptr);
+int spmv64(const DCSR& A, const double* x, double* y, cudaStream_t s);
 // deterministic dot product into a device scalar
 int dot64(const double* a, const double* b, int64_t n, double* result_dev, cudaStream_t s);
 // sort each row segment [rp[i], rp[i+1]) of (key, val) pairs by key (keys unique per row)
