@@ -69,7 +69,7 @@ def run_paper3d(args, rank, local):
     28^3 and 82^3 nodes, constant sigma, FP64 V-cycle in PCG, tolerance 1e-8 capped at
     kappa_1(D^-1 A) / 1e16 (kappa by the library's Hager estimate).  One JSON line: CG iterations,
     operator complexity and setup + solve seconds beside the paper's counts (Matlab, hardware not
-    stated).  Context, not a bench value: the driver's headline is the default workload."""
+    stated).  Context, not a bench value: the headline is the default workload."""
     import numpy as np
     import torch
 
@@ -551,7 +551,7 @@ def main():
     sec_per_system = seconds_per_system(ms, args.steps, world)
     rc, iters, relres, prof, st, info = results[-1]
 
-    # comparators on the same GPU: plain FP32 and plain FP64 GPU paths (untimed by the driver)
+    # comparators on the same GPU: plain FP32 and plain FP64 GPU paths (outside the timed steps)
     comparators = {}
     if not args.no_compare:
         for name in ("fp32_plain", "fp64_plain"):
