@@ -288,6 +288,30 @@ def seconds_per_system(ms_slowest, steps, world):
     return ms_slowest / 1e3 / (steps * world)
 
 
+def pinned_h2d_gbs(stream, nbytes=1 << 30, reps=3):
+    """This machine's host-to-device rate for one plain copy of a pinned buffer (best of `reps`, CUDA
+    events on `stream`), outside the timed steps: the end-to-end figure moves with it.  None when
+    the buffers cannot be had."""
+    import torch
+    try:
+        h = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+        d = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        best = None
+        with torch.cuda.stream(stream):
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                d.copy_(h, non_blocking=True)
+                e1.record(stream)
+                e1.synchronize()
+                ms = e0.elapsed_time(e1)
+                best = ms if best is None else min(best, ms)
+        del h, d
+        return nbytes / (best / 1e3) / 1e9 if best else None
+    except Exception:
+        return None
+
+
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sgs_level0_traffic_kuhn128.txt")
 
 
@@ -615,7 +639,8 @@ def main():
                                      p.sigma_edge, b))
         e_st = eres[-1][4]
         e2e = {"value": te / world, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(b.nbytes),
-               "last_step_setup_ms": e_st["setup_ms"], "last_step_solve_ms": e_st["solve_ms"], "clocks": eclocks}
+               "last_step_setup_ms": e_st["setup_ms"], "last_step_solve_ms": e_st["solve_ms"], "clocks": eclocks,
+               "h2d_copy_gbs": pinned_h2d_gbs(stream)}
 
     peak, peak_kind = peaks()
     roof = None
